@@ -1,0 +1,232 @@
+"""Seeded synthetic inputs: conductor surface meshes, AIM grid boxes and random vectors.
+
+This module produces the geometry and random numbers that both the CUDA path and the
+test-side reference consume. It holds none of the boundary-element arithmetic: no basis
+functions, no integrals, no Green's functions. Everything here is a plain description of
+closed, outward-oriented triangle surfaces (Sec. II: "S is meshed with triangular
+elements") and of the uniform auxiliary grid box (Sec. III-A item 1).
+
+Units: every length is in micrometres. A mesh is a tuple of
+  verts  float64 [nv, 3]
+  tris   int32   [nt, 3]   counter-clockwise seen from outside (outward normal)
+  obj    int32   [nt]      conductor index of each triangle, objects contiguous.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MU = 1e-6  # one micrometre in metres: the length unit of every mesh here
+
+
+@dataclass
+class Mesh:
+    verts: np.ndarray
+    tris: np.ndarray
+    obj: np.ndarray
+    nobj: int
+    # per-object conductivity (S/m); relative permittivity and permeability are 1
+    sigma: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def nt(self) -> int:
+        return int(self.tris.shape[0])
+
+    @property
+    def nv(self) -> int:
+        return int(self.verts.shape[0])
+
+
+@dataclass
+class Grid:
+    origin: np.ndarray  # float64 [3]
+    h: np.ndarray       # float64 [3]
+    n: np.ndarray       # int64 [3]  (nx, ny, nz)
+
+    @property
+    def npts(self) -> int:
+        return int(np.prod(self.n))
+
+
+# ----------------------------------------------------------------------------------
+# primitive surfaces
+# ----------------------------------------------------------------------------------
+def box(lo, size, div):
+    """Closed surface of the box [lo, lo+size] with div[a] equal intervals along axis a.
+
+    Every face is cut into div[b] x div[c] quads, each split along the same diagonal into two
+    triangles; all triangles are counter-clockwise seen from outside.
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    size = np.asarray(size, dtype=np.float64)
+    div = [int(d) for d in div]
+    vid: dict[tuple[int, int, int], int] = {}
+    verts: list[np.ndarray] = []
+
+    def vertex(ijk):
+        key = tuple(int(v) for v in ijk)
+        i = vid.get(key)
+        if i is None:
+            i = len(verts)
+            vid[key] = i
+            verts.append(lo + size * np.array(key, dtype=np.float64) / np.array(div, dtype=np.float64))
+        return i
+
+    tris = []
+    for a in range(3):
+        for side in (0, 1):
+            b, c = (a + 1) % 3, (a + 2) % 3
+            if side == 0:
+                b, c = c, b  # e_b x e_c = -e_a on the low face
+            for u in range(div[b]):
+                for v in range(div[c]):
+                    def p(du, dv):
+                        ijk = [0, 0, 0]
+                        ijk[a] = side * div[a]
+                        ijk[b] = u + du
+                        ijk[c] = v + dv
+                        return vertex(ijk)
+                    p00, p10, p11, p01 = p(0, 0), p(1, 0), p(1, 1), p(0, 1)
+                    tris.append((p00, p10, p11))
+                    tris.append((p00, p11, p01))
+    return np.array(verts, dtype=np.float64), np.array(tris, dtype=np.int32)
+
+
+def icosphere(radius, subdiv, center=(0.0, 0.0, 0.0)):
+    """Sphere surface: an icosahedron refined subdiv times by midpoint splitting."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t),
+         (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(x, dtype=np.float64) / np.linalg.norm(x) for x in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+             (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+             (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        cache: dict[tuple[int, int], int] = {}
+
+        def mid(i, j):
+            key = (min(i, j), max(i, j))
+            k = cache.get(key)
+            if k is None:
+                m = verts[i] + verts[j]
+                verts.append(m / np.linalg.norm(m))
+                k = len(verts) - 1
+                cache[key] = k
+            return k
+        nf = []
+        for (a, b, c) in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.array(verts) * radius + np.asarray(center, dtype=np.float64)
+    F = np.array(faces, dtype=np.int32)
+    # orient outward
+    cen = np.asarray(center, dtype=np.float64)
+    p0, p1, p2 = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    s = np.einsum("ij,ij->i", np.cross(p1 - p0, p2 - p0), (p0 + p1 + p2) / 3.0 - cen)
+    F[s < 0] = F[s < 0][:, [0, 2, 1]]
+    return V, F
+
+
+def merge(parts, sigmas):
+    """Concatenate closed surfaces into one multi-object mesh (objects in input order)."""
+    verts, tris, obj = [], [], []
+    off = 0
+    for i, (V, F) in enumerate(parts):
+        verts.append(V)
+        tris.append(F + off)
+        obj.append(np.full(F.shape[0], i, dtype=np.int32))
+        off += V.shape[0]
+    return Mesh(np.concatenate(verts), np.concatenate(tris).astype(np.int32),
+                np.concatenate(obj), len(parts), np.asarray(sigmas, dtype=np.float64))
+
+
+def grid_box(mesh: Mesh, h, margin=1, frac=1.0 / 12.0) -> Grid:
+    """Smallest uniform grid whose order-2 (3x3x3) stencils around any surface point fit.
+
+    The origin sits `margin + frac` spacings below the mesh's bounding box, so that centroids of
+    structured meshes (multiples of a sixth of a cell) never fall half-way between two nodes.
+    """
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), (3,)).copy()
+    lo = mesh.verts.min(axis=0)
+    hi = mesh.verts.max(axis=0)
+    origin = lo - (margin + frac) * h
+    # largest anchor: floor((hi - origin)/h + 0.5); stencil reaches anchor + margin
+    top = np.floor((hi - origin) / h + 0.5).astype(np.int64) + margin
+    n = top + 1
+    return Grid(origin, h, n)
+
+
+# ----------------------------------------------------------------------------------
+# the workloads
+# ----------------------------------------------------------------------------------
+SIGMA_CU = 5.8e7
+SIGMA_AU = 4.1e7
+
+
+def bar_mesh(w, t, length, a, sigma=SIGMA_CU, lo=(0.0, 0.0, 0.0)) -> Mesh:
+    """One rectangular bar w x t x length (um), structured squares of side a split in two."""
+    div = (round(w / a), round(t / a), round(length / a))
+    V, F = box(lo, (w, t, length), div)
+    return merge([(V, F)], [sigma])
+
+
+def copper_bar() -> tuple[Mesh, Grid, float]:
+    """Copper bar 2x2x20 um, 0.5 um squares (1344 triangles, 2016 edges), 10 GHz,
+    AIM grid spacing 0.5 um."""
+    m = bar_mesh(2.0, 2.0, 20.0, 0.5)
+    return m, grid_box(m, 0.5), 10e9
+
+
+def bar_array_lengths(seed=0, count=16):
+    rng = np.random.default_rng(seed)
+    return np.round(rng.uniform(5.0, 40.0, count) * 2.0) / 2.0
+
+
+def bar_array(seed=0, nx=4, ny=4, pitch=5.0, cross=1.0, a=0.5, sigma=SIGMA_CU) -> Mesh:
+    """nx x ny copper bars, cross-section cross x cross um, pitch `pitch` um, seeded lengths
+    uniform in [5, 40] um rounded to 0.5 um, 0.5 um squares."""
+    Ls = bar_array_lengths(seed, nx * ny)
+    parts = []
+    for i in range(nx):
+        for j in range(ny):
+            L = float(Ls[i * ny + j])
+            parts.append(box((i * pitch, j * pitch, 0.0), (cross, cross, L),
+                             (round(cross / a), round(cross / a), round(L / a))))
+    return merge(parts, [sigma] * len(parts))
+
+
+def bar_array_config(seed=0, freq=10e9) -> tuple[Mesh, Grid, float]:
+    """4x4 array of copper bars (precision-study workload); grid spacing 0.5 um."""
+    m = bar_array(seed)
+    return m, grid_box(m, 0.5), freq
+
+
+def small_bars(nbars=2, length=3.0, a=0.5, pitch=2.5, sigma=SIGMA_CU) -> Mesh:
+    """A few short 1x1 um bars in a row (test-sized multi-object mesh)."""
+    parts = [box((i * pitch, 0.0, 0.0), (1.0, 1.0, length + 0.5 * i),
+                 (round(1.0 / a), round(1.0 / a), round((length + 0.5 * i) / a)))
+             for i in range(nbars)]
+    return merge(parts, [sigma] * nbars)
+
+
+def sphere_mesh(radius=1.0, subdiv=2, sigma=1e5) -> Mesh:
+    V, F = icosphere(radius, subdiv)
+    return merge([(V, F)], [sigma])
+
+
+# ----------------------------------------------------------------------------------
+# random vectors / matrices (seeded)
+# ----------------------------------------------------------------------------------
+def rand_cvec(n, seed, dtype=np.complex128):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(dtype)
+
+
+def rand_blocks(sizes, seed):
+    """Random complex square blocks (list of [n_i, n_i] complex128)."""
+    rng = np.random.default_rng(seed)
+    return [(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(max(n, 1))
+            for n in sizes]

@@ -1,0 +1,122 @@
+"""Pins of the Galerkin matrices and the SLIM system (Sec. II)."""
+import numpy as np
+import pytest
+
+from oracle import operators as op, quad
+from oracle.rwg import from_mesh
+from paper_2108_03991_gb300 import synth
+
+
+@pytest.fixture(scope="module")
+def small():
+    m = synth.bar_mesh(1.0, 1.0, 2.0, 0.5)
+    return m, from_mesh(m)
+
+
+def _plane_wave_coeffs(rw, k, k0, mur=1.0):
+    """RWG coefficients (L2 projection) of n x E and n x H for the interior plane wave
+    E = y exp(-j k x), H = z (k / (k0 mur)) exp(-j k x) (E in units of eta0)."""
+    b, w = quad.radon7()
+    X = rw.verts[rw.tris]
+    pts = quad.rule_points(X, b).reshape(-1, 3)
+    nrm = np.repeat(rw.normal[:, None, :], 7, axis=1).reshape(-1, 3)
+    E = np.zeros((pts.shape[0], 3), complex)
+    E[:, 1] = np.exp(-1j * k * pts[:, 0])
+    H = np.zeros((pts.shape[0], 3), complex)
+    H[:, 2] = (k / (k0 * mur)) * np.exp(-1j * k * pts[:, 0])
+    G = op.gram_matrix(rw).toarray()
+    ce = np.linalg.solve(G, op.project_tangential(rw, lambda r: np.cross(nrm, E)))
+    ch = np.linalg.solve(G, op.project_tangential(rw, lambda r: np.cross(nrm, H)))
+    return ce, ch
+
+
+def test_ix_antisymmetric(small):
+    _, rw = small
+    ix = op.ix_matrix(rw)
+    assert abs(ix + ix.T).max() == 0.0
+    assert np.all(np.diff(ix.indptr) == 4)  # four nonzeros per row
+
+
+def test_lA_symmetry():
+    rw = from_mesh(synth.bar_mesh(1.0, 1.0, 4.0, 0.5))
+    k0 = op.k0_of(10e9)
+    LA = op.dense_rwg(rw, k0, "A")
+    # reciprocity: exact for well-separated pairs (same rule both ways), quadrature-level
+    # for near pairs (closed-form inner / 7-point outer)
+    c = 0.5 * (rw.centroid[rw.et[:, 0]] + rw.centroid[rw.et[:, 1]])
+    dist = np.linalg.norm(c[:, None] - c[None], axis=-1)
+    far = dist > 3 * rw.diam.max()
+    assert far.sum() > 1000
+    assert np.max(np.abs(LA - LA.T)[far]) <= 1e-13 * np.abs(LA).max()
+    assert np.max(np.abs(LA - LA.T)) <= 2e-3 * np.abs(LA).max()
+
+
+def test_interior_plane_wave_Z(small):
+    """P2 for Z (Eq. MFIEinZin): the interior plane wave of the conductor satisfies e = Zhat h
+    to discretisation accuracy; flipping the sign of K breaks it at O(1)."""
+    _, rw = small
+    freq = 10e9
+    k0 = op.k0_of(freq)
+    epsc = op.eps_rc(5.8e7, freq)
+    k = op.k_medium(k0, epsc)
+    ix = op.ix_matrix(rw).toarray()
+    L = op.dense_rwg(rw, k, "L")
+    K = op.dense_rwg(rw, k, "K")
+    ce, ch = _plane_wave_coeffs(rw, k, k0)
+    Z = -np.linalg.solve(L, K + 0.5 * ix) / (1j * k0 * epsc)
+    err = np.linalg.norm(Z @ ch - ce) / np.linalg.norm(ce)
+    Zbad = -np.linalg.solve(L, -K + 0.5 * ix) / (1j * k0 * epsc)
+    bad = np.linalg.norm(Zbad @ ch - ce) / np.linalg.norm(ce)
+    assert err < 0.12 and bad > 0.5
+
+
+def test_interior_plane_wave_Y(small):
+    """P2 for Y_eq (Eq. EFIEeqYeq), at a frequency where k0 h is moderate."""
+    _, rw = small
+    freq = 30e12
+    k0 = op.k0_of(freq)
+    ix = op.ix_matrix(rw).toarray()
+    L = op.dense_rwg(rw, k0, "L")
+    K = op.dense_rwg(rw, k0, "K")
+    ce, ch = _plane_wave_coeffs(rw, k0, k0)
+    Y = np.linalg.solve(L, K + 0.5 * ix) / (1j * k0)
+    err = np.linalg.norm(Y @ ce - ch) / np.linalg.norm(ch)
+    Ybad = np.linalg.solve(L, -K + 0.5 * ix) / (1j * k0)
+    bad = np.linalg.norm(Ybad @ ce - ch) / np.linalg.norm(ch)
+    assert err < 0.08 and bad > 0.5
+
+
+def test_transparent_object_YZ_identity(small):
+    """P3: an object with the background's material is invisible, so H_eq = H, i.e.
+    Yhat Zhat h = h for an admissible interior field h."""
+    _, rw = small
+    freq = 30e12
+    k0 = op.k0_of(freq)
+    ix = op.ix_matrix(rw).toarray()
+    L = op.dense_rwg(rw, k0, "L")
+    K = op.dense_rwg(rw, k0, "K")
+    M = np.linalg.solve(L, K + 0.5 * ix)
+    Z = -M / (1j * k0)
+    Y = M / (1j * k0)
+    _, ch = _plane_wave_coeffs(rw, k0, k0)
+    assert np.linalg.norm(Y @ (Z @ ch) - ch) / np.linalg.norm(ch) < 0.1
+
+
+def test_sequence_matches_assembled_system(small):
+    """The sequence of Sec. II-C equals the block matrix of Eq. (AEFIEoutJ) with C of Eq. (Cdef)
+    assembled by matrix products."""
+    _, rw = small
+    freq = 10e9
+    S, LA, LP = op.dense_system(rw, freq, [5.8e7])
+    Z = S.Zs[0]
+    Y = S.Ys[0]
+    ix = S.ix.toarray()
+    fd = S.fd.toarray()
+    k0 = S.k0
+    C = (-1j * k0 * LA @ Y + ix) @ Z
+    A = np.block([[1j * k0 * LA + C, -fd.T @ LP],
+                  [fd @ (np.eye(rw.ne) - Y @ Z), 1j * k0 * np.eye(rw.nt)]])
+    x = synth.rand_cvec(rw.ne + rw.nt, 4)
+    y1 = A @ x
+    y2 = S.matvec(x)
+    assert np.linalg.norm(y1 - y2) <= 1e-12 * np.linalg.norm(y1)
