@@ -1,0 +1,287 @@
+"""Benchmark: SLIM system matvecs per second on one GB300 (and N independent replicas).
+
+Workload: the precision-study structure — a 4 x 4 array of copper bars (1 x 1 um cross-section,
+5 um pitch, seeded lengths uniform in 5-40 um, 0.5 um mesh: 11,888 triangles, 17,832 RWG
+edges, 16 objects), 10 GHz, AIM grid spacing 0.5 um, order-2 stencils, near radius 2 cells.
+A step is one system matrix-vector product of Eq. (AEFIEoutJ) in complex FP32 (internal blocks
+Z and Y_eq, AIM projection, FFT convolution, interpolation, near region, sparse terms).
+Inputs (Z and Y alone are ~320 MB) exceed the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle on the host cores (a bounded sample of the same
+workload, scaled to the full workload's matvec cost).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "matvecs/s (HBM roofline %) and time to 1e-6 residual, chosen vs plain, 1 GB300"
+UNIT = "matvecs/s"
+WORKLOAD = "4x4 Cu bar array (seed 0), 17832 RWG + 11888 pulse unknowns, 10 GHz, AIM 0.5 um grid"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.rows = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for k, nme in enumerate(names):
+                    if r[3 + k].lower().startswith("active"):
+                        reasons.add(nme)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(seconds=15.0):
+    """The FP64 oracle (O-AIM system matvec) on one bar of the workload, timed on the host
+    cores and scaled to the full workload by the ratio of dense internal-block elements
+    (the dominant cost of both)."""
+    import numpy as np
+
+    from oracle import aim as oaim, operators as op
+    from oracle.rwg import from_mesh
+    from paper_2108_03991_gb300 import synth
+
+    full = synth.bar_array(0)
+    Ls = synth.bar_array_lengths(0)
+    i = int(np.argmin(Ls))
+    L = float(Ls[i])
+    sample = synth.bar_mesh(1.0, 1.0, L, 0.5)
+    grid = synth.grid_box(sample, 0.5)
+    freq = 10e9
+    rw = from_mesh(sample)
+    A = oaim.Aim(rw, grid.origin, grid.h, grid.n, op.k0_of(freq)).build_near()
+    Zs, Ys = op.internal_blocks(rw, freq, sample.sigma)
+    S = op.SlimSystem(rw, freq, Zs, Ys, A.LA, A.LPhi)
+    x = synth.rand_cvec(S.n, 1)
+    S.matvec(x)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        S.matvec(x)
+        n += 1
+    dt = (time.perf_counter() - t0) / n
+    rwf = from_mesh(full)
+    full_cost = sum((b - a) ** 2 for a, b in rwf.obj_edge_ranges())
+    samp_cost = rw.ne ** 2
+    rate = 1.0 / dt * samp_cost / full_cost
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one {L:g} um bar of the array ({rw.ne} edges): {1.0 / dt:.2f} matvecs/s, "
+                      f"scaled by the internal-block elements ({samp_cost} of {full_cost})"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    cb = None
+    for _ in range(max(1, args.steps)):
+        cb = oracle_baseline(seconds=max(5.0, 40.0 / max(1, args.steps)))
+        steps.append(cb["value"])
+    v = sum(steps) / len(steps)
+    cb["value"] = v
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+        "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                    "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_03991_gb300 import api, build, synth
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+
+    mesh, grid, freq = synth.bar_array_config(0, 10e9)
+    t0 = time.perf_counter()
+    ctx = api.Context(mesh, grid, freq)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    s = torch.cuda.current_stream()
+    x = torch.from_numpy(synth.rand_cvec(ctx.n, 1 + rank)).to(torch.complex64).to(dev)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        ctx.matvec(x, y, prec=api.BEM_C32)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(s)
+        for _ in range(args.steps):
+            ctx.matvec(x, y, prec=api.BEM_C32)
+        ev1.record(s)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        # dominant kernel: the block-diagonal GEMV (two launches per internal_apply)
+        e = torch.empty(ctx.ne, dtype=torch.complex64, device=dev)
+        heq = torch.empty_like(e)
+        h = x[:ctx.ne].contiguous()
+        for _ in range(3):
+            ctx.internal(h, e, heq, prec=api.BEM_C32)
+        torch.cuda.synchronize()
+        ev0.record(s)
+        for _ in range(args.steps):
+            ctx.internal(h, e, heq, prec=api.BEM_C32)
+        ev1.record(s)
+        torch.cuda.synchronize()
+        gemv_ms = ev0.elapsed_time(ev1) / (2 * args.steps)
+        # end to end: pinned host x -> device, matvec, device -> pinned host y
+        xh = x.cpu().pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        xd = torch.empty_like(x)
+        for _ in range(3):
+            xd.copy_(xh, non_blocking=True)
+            ctx.matvec(xd, y, prec=api.BEM_C32)
+            yh.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        ev0.record(s)
+        for _ in range(args.steps):
+            xd.copy_(xh, non_blocking=True)
+            ctx.matvec(xd, y, prec=api.BEM_C32)
+            yh.copy_(y, non_blocking=True)
+        ev1.record(s)
+        torch.cuda.synchronize()
+        e2e_ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms, e2e_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = float(t[0]), float(t[1])
+
+    solve = None
+    if not args.no_solve and rank == 0:
+        solve = {}
+        b = ctx.rhs_plane_wave(prec=api.BEM_C64)
+        for name, mode in (("plain_fp64", api.BEM_C64), ("chosen_fp32", api.BEM_C32)):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            xs, info = ctx.solve(b, tol=1e-6, restart=200, max_iter=3000, prec_mode=mode,
+                                 time_limit_s=120.0)
+            torch.cuda.synchronize()
+            solve[name] = {"seconds": time.perf_counter() - t1, "iters": info["iters"],
+                           "resid_true": info["resid_true"], "status": info["status"]}
+
+    if rank == 0:
+        hbm, src = peaks()
+        ZY = ctx.zy_bytes_c32 // 2  # bytes of Z (or Y) in FP32, one GEMV launch
+        gemv_bytes = ZY + 2 * 8 * ctx.ne
+        achieved = gemv_bytes / (gemv_ms * 1e-3) / 1e9
+        cpu = None
+        if not args.no_cpu:
+            cpu = oracle_baseline(seconds=15.0)
+        value = world * 1e3 / ms
+        launches_per_step = 11
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "unknowns": ctx.n, "ne": ctx.ne, "nt": ctx.nt,
+                       "objects": ctx.nobj, "grid": list(ctx.grid_n), "fft": list(ctx.padded),
+                       "nnz_near": [ctx.nnz_A, ctx.nnz_P], "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (Z, Y ~%.0f MB)" % (ctx.zy_bytes_c32 / 1e6),
+                       "setup_s": setup_s},
+            "roofline": {"kernel": "k_gemv (block-diagonal Z / Y_eq)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": src, "traffic": None,
+                         "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms},
+            "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * ctx.n,
+                    "d2h_bytes_per_step": 8 * ctx.n},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "solve": solve,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

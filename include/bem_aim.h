@@ -1,0 +1,173 @@
+/*
+ * bem_aim.h - C ABI of the GB300 SLIM boundary-element library (libbem_aim.so).
+ *
+ * The library applies the system matrix of the SLIM formulation (Marek, Sharma, Triverio,
+ * "A Parallel Boundary Element Method for the Electromagnetic Analysis of Large Structures
+ * With Lossy Conductors", Sec. II-C, Eq. AEFIEoutJ) and solves it with GMRES (Sec. III-E).
+ * The external operators L^A and L^Phi are applied with the adaptive integral method
+ * (Sec. III-A item 1, Eq. AIM_L); the internal problem uses dense per-object matrices
+ * Z_i (Eq. MFIEinZin) and Y_i,eq (Eq. EFIEeqYeq), block-diagonal over objects (Sec. II-C).
+ *
+ * Conventions shared by every call
+ *  - Lengths are in micrometres; frequency in Hz; time convention exp(j w t).
+ *  - Complex vectors are interleaved (re, im): float pairs for BEM_C32, double pairs for BEM_C64.
+ *  - Unknown ordering: edges (RWG functions) sorted by object, then by the vertex pair (a<b);
+ *    triangles (pulse functions) in input order. Objects must be contiguous in the triangle
+ *    list, so each object's edges form one contiguous range.
+ *  - The system vector is x = [h; q] of length N = N_E + N_T: h the n x H coefficients,
+ *    q = c0 * rho_Delta. The internal vector e = E/eta0 has length N_E.
+ *  - Pointers named x, y, h, e, heq, b, sigma, phi are DEVICE pointers owned by the caller
+ *    (for example torch tensors); the library never frees them. Calls taking a `stream`
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream) are asynchronous on it.
+ *  - Return value: BEM_OK (0), a positive status (BEM_ENOCONV) or a negative error code. The
+ *    message of the last error on the calling thread is returned by bem_last_error().
+ */
+#ifndef BEM_AIM_H
+#define BEM_AIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BEM_OK 0
+#define BEM_ENOCONV 1     /* GMRES stopped at max_iter / time limit; x holds the best iterate */
+#define BEM_EINVAL (-1)   /* null pointer, NaN, bad size or option */
+#define BEM_EMESH (-2)    /* open / non-manifold / inconsistently oriented surface */
+#define BEM_EGRID (-3)    /* an AIM stencil falls outside the grid, or grid too large */
+#define BEM_ENOMEM (-4)   /* device allocation failed */
+#define BEM_ECUDA (-5)    /* a CUDA runtime or library call failed */
+#define BEM_ESOLVER (-6)  /* singular internal matrix in the LU factorisation */
+
+enum { BEM_C32 = 0, BEM_C64 = 1 };
+enum { AIM_OP_LA = 0, AIM_OP_LPHI = 1, AIM_OP_SYSTEM = 2 };
+
+typedef struct aim_ctx aim_ctx;
+
+/* Material of one conductor (Sec. II: permittivity, permeability, conductivity). */
+typedef struct {
+  double sigma; /* S/m */
+  double eps_r;
+  double mu_r;
+} bem_material;
+
+/* Surface mesh of all conductors (Sec. II: S meshed with triangles; multiple objects
+ * S = union S_i, Sec. II-C). Triangles are counter-clockwise seen from outside. The
+ * background is vacuum. All arrays are HOST arrays, copied by aim_setup. */
+typedef struct {
+  int32_t nv;
+  const double* xyz;         /* [nv][3] */
+  int32_t nt;
+  const int32_t* tri;        /* [nt][3] */
+  const int32_t* obj_of_tri; /* [nt], non-decreasing, values 0..nobj-1 */
+  int32_t nobj;
+  const bem_material* mat;   /* [nobj] */
+} bem_mesh;
+
+/* Uniform auxiliary AIM grid (Sec. III-A item 1). Node (i,j,k) sits at origin + (i,j,k)*h.
+ * order must be 2 (3x3x3 stencils) and r_near the near-region radius in cells (max-norm of
+ * anchor differences). */
+typedef struct {
+  double origin[3];
+  double h[3];
+  int32_t n[3];
+  int32_t order;
+  int32_t r_near;
+} aim_grid;
+
+/* Build every setup product on the current CUDA device: RWG data, projection stencils,
+ * FFT of the grid Green's function, precorrected near-region matrices L^A_NR and L^Phi_NR
+ * (Sec. III-A item 1, Phillips 1997), the dense internal matrices Z_i and Y_i,eq of every
+ * object (Eqs. MFIEinZin, EFIEeqYeq; FP64 integrals, LU by cuSOLVER), in FP64 and FP32 copies.
+ * On success *out owns all device memory; release it with aim_destroy.
+ * Errors: BEM_EINVAL, BEM_EMESH, BEM_EGRID, BEM_ENOMEM, BEM_ECUDA, BEM_ESOLVER. */
+int aim_setup(const bem_mesh* mesh, const aim_grid* grid, double freq_hz, aim_ctx** out);
+
+/* Free every device and host resource of ctx (NULL is allowed). */
+void aim_destroy(aim_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* bem_last_error(void);
+
+/* Sizes: info[0]=N_E, [1]=N_T, [2]=nobj, [3..5]=grid n, [6..8]=padded FFT lengths,
+ * [9]=nnz(L^A_NR), [10]=nnz(L^Phi_NR), [11]=bytes of Z and Y (C32), [12]=max n_i.
+ * Writes min(n, 13) entries. */
+int aim_info(const aim_ctx* ctx, int64_t* info, int n);
+
+/* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)
+ * or AIM_OP_SYSTEM (the SLIM system of Eq. AEFIEoutJ, vectors of N_E + N_T):
+ *   e = Z h, h_eq = Y e, j = h - h_eq,
+ *   y1 = j k0 L^A j + I_x e - (F D)^T L^Phi q,  y2 = F D j + j k0 q.
+ * x and y must not alias. prec selects the arithmetic (BEM_C32 or BEM_C64). */
+int aim_matvec(aim_ctx* ctx, int which, const void* x, void* y, int prec, void* stream);
+
+/* The internal problem (Sec. II-B, Eqs. MFIEinZin, EFIEeqYeq): e = Z h, h_eq = Y e, for
+ * nrhs right-hand sides stored one after another (each N_E long). heq may be NULL. */
+int internal_apply(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, int prec,
+                   void* stream);
+
+/* The grid step H of Eq. AIM_L alone: phi_c = sum_b G_grid(a - b) sigma_c(b) (linear
+ * convolution) for ncomp (1..4) grids of n[0]*n[1]*n[2] points (x fastest) stored one after
+ * another. sigma and phi may alias. */
+int aim_conv(aim_ctx* ctx, const void* sigma, void* phi, int ncomp, int prec, void* stream);
+
+/* y_i = A_i x_i for nblk square blocks (Sec. II-C block-diagonal Z, Y_eq). n: HOST array of
+ * block sizes. A: DEVICE array, block i row-major with leading dimension ld_i = n_i rounded up
+ * to a multiple of 4, blocks one after another (offsets sum of n_j*ld_j). x, y: nrhs vectors of
+ * sum n_i each. */
+int bem_blockdiag_gemv(int nblk, const int32_t* n, const void* A, const void* x, void* y,
+                       int nrhs, int prec, void* stream);
+
+/* Copy a setup product to HOST memory `out` (capacity cap bytes, at least the size needed):
+ *   what 0: Z_i (complex double, row-major n_i x n_i), index = object
+ *   what 1: Y_i (same)
+ *   what 2: near-region L^A_NR as CSR: int64 rowptr[N_E+1], int32 col[nnz], complex double
+ *           val[nnz], packed one after another
+ *   what 3: near-region L^Phi_NR (same layout, N_T rows)
+ *   what 4: RWG projection weights, double [N_E][3][27]
+ *   what 5: pulse projection weights, double [N_T][27]
+ *   what 6: stencil anchors, int32 [N_E + N_T][3]
+ *   what 7: edge table, int32 [N_E][6] = (a, b, T+, T-, v+, v-)
+ * Returns the number of bytes needed when out is NULL. */
+int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
+
+/* b = [<f_m, E_inc>/eta0 ; 0] for E_inc = pol exp(-j k0 khat . r) (unit amplitude, V/m),
+ * Sec. II-A right-hand side. pol and khat are host arrays of 3 doubles. */
+int bem_rhs_plane_wave(aim_ctx* ctx, const double* pol, const double* khat, void* b, int prec,
+                       void* stream);
+
+/* Options of bem_solve. prec_mode: BEM_C64 (plain: FP64 everywhere) or BEM_C32 (system
+ * matvec in complex FP32, Arnoldi and Givens in FP64). */
+typedef struct {
+  double tol;          /* relative residual target, e.g. 1e-6 */
+  int32_t restart;     /* Krylov subspace size before restart, 1..512 */
+  int32_t max_iter;
+  int32_t prec_mode;
+  int32_t precond;     /* 0 = none */
+  double time_limit_s; /* <= 0: none */
+} bem_solve_opts;
+
+typedef struct {
+  int32_t iters;
+  double resid_est;   /* Arnoldi estimate at exit */
+  double resid_true;  /* ||b - A x|| / ||b|| with the FP64 system matvec */
+  double seconds;
+} bem_solve_info;
+
+/* Solve A x = b (Eq. AEFIEoutJ) with restarted GMRES on the device (Sec. III-E). b and x
+ * are complex double device vectors of N_E + N_T. Returns BEM_OK when the true residual
+ * reaches tol, BEM_ENOCONV (positive) when max_iter or the time limit stops it first. */
+int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
+              bem_solve_info* info, void* stream);
+
+/* Work lists for uneven block-diagonal products (Sec. III-C): LPT (Alg. 1) and the modified
+ * Part_Schedule (Alg. 2). W: HOST task weights sorted in decreasing order (W_i = n_i^2);
+ * P processors; p_cutoff <= 0 selects the original Part_Schedule. Outputs: Pi[ntask]
+ * processors per task; returns the schedule length C_max (negative on error). */
+double bem_part_schedule(int ntask, const double* W, int P, int p_cutoff, int32_t* Pi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_AIM_H */

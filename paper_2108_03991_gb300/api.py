@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libbem_aim.so (argument marshalling only).
+
+Every computation runs in the CUDA library; device buffers are torch tensors (complex64 for
+BEM_C32, complex128 for BEM_C64) and the current torch stream is passed through. Loading fails
+loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+BEM_C32, BEM_C64 = 0, 1
+AIM_OP_LA, AIM_OP_LPHI, AIM_OP_SYSTEM = 0, 1, 2
+BEM_OK, BEM_ENOCONV = 0, 1
+ERRORS = {-1: "BEM_EINVAL", -2: "BEM_EMESH", -3: "BEM_EGRID", -4: "BEM_ENOMEM",
+          -5: "BEM_ECUDA", -6: "BEM_ESOLVER"}
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbem_aim.so")
+
+SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec",
+           "internal_apply", "aim_conv", "bem_blockdiag_gemv", "aim_export",
+           "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule"]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Material(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("eps_r", C.c_double), ("mu_r", C.c_double)]
+
+
+class MeshC(C.Structure):
+    _fields_ = [("nv", C.c_int32), ("xyz", C.POINTER(C.c_double)), ("nt", C.c_int32),
+                ("tri", C.POINTER(C.c_int32)), ("obj_of_tri", C.POINTER(C.c_int32)),
+                ("nobj", C.c_int32), ("mat", C.POINTER(Material))]
+
+
+class GridC(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("h", C.c_double * 3), ("n", C.c_int32 * 3),
+                ("order", C.c_int32), ("r_near", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32),
+                ("prec_mode", C.c_int32), ("precond", C.c_int32), ("time_limit_s", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("resid_est", C.c_double), ("resid_true", C.c_double),
+                ("seconds", C.c_double)]
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2108_03991_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.aim_setup.argtypes = [C.POINTER(MeshC), C.POINTER(GridC), d, C.POINTER(vp)]
+        L.aim_destroy.argtypes = [vp]
+        L.aim_destroy.restype = None
+        L.bem_last_error.restype = C.c_char_p
+        L.aim_info.argtypes = [vp, C.POINTER(i64), C.c_int]
+        L.aim_matvec.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
+        L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
+        L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
+        L.bem_blockdiag_gemv.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int, C.c_int, vp]
+        L.aim_export.argtypes = [vp, C.c_int, C.c_int, vp, i64]
+        L.aim_export.restype = i64
+        L.bem_rhs_plane_wave.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.c_int, vp]
+        L.bem_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+        L.bem_part_schedule.argtypes = [C.c_int, C.POINTER(d), C.c_int, C.c_int, C.POINTER(i32)]
+        L.bem_part_schedule.restype = d
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc < 0:
+        raise BemError(rc, lib().bem_last_error().decode())
+    return rc
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def cdtype(prec):
+    import torch
+    return torch.complex64 if prec == BEM_C32 else torch.complex128
+
+
+def part_schedule(W, P, p_cutoff=20):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    Pi = np.zeros(W.size, dtype=np.int32)
+    cmax = lib().bem_part_schedule(W.size, W.ctypes.data_as(C.POINTER(C.c_double)), int(P),
+                                   int(p_cutoff), Pi.ctypes.data_as(C.POINTER(C.c_int32)))
+    if cmax < 0:
+        raise BemError(-1, lib().bem_last_error().decode())
+    return Pi, cmax
+
+
+def blockdiag_gemv(sizes, A, x, y, nrhs=1, prec=BEM_C32):
+    n = np.ascontiguousarray(sizes, dtype=np.int32)
+    dt = cdtype(prec)
+    _check(lib().bem_blockdiag_gemv(n.size, n.ctypes.data_as(C.POINTER(C.c_int32)), _ptr(A, dt),
+                                    _ptr(x, dt), _ptr(y, dt), int(nrhs), prec, _stream()))
+    return y
+
+
+def pack_blocks(blocks, dtype):
+    """Row-major blocks with leading dimension n rounded up to 4, concatenated (numpy)."""
+    out = []
+    for B in blocks:
+        n = B.shape[0]
+        ld = (n + 3) // 4 * 4
+        P = np.zeros((n, ld), dtype=dtype)
+        P[:, :n] = B
+        out.append(P.ravel())
+    return np.concatenate(out)
+
+
+class Context:
+    """One aim_setup context on the current CUDA device."""
+
+    def __init__(self, mesh, grid, freq, r_near=2):
+        L = lib()
+        self._keep = []
+        xyz = np.ascontiguousarray(mesh.verts, dtype=np.float64)
+        tri = np.ascontiguousarray(mesh.tris, dtype=np.int32)
+        obj = np.ascontiguousarray(mesh.obj, dtype=np.int32)
+        mats = (Material * mesh.nobj)(*[Material(float(s), 1.0, 1.0) for s in mesh.sigma])
+        self._keep += [xyz, tri, obj, mats]
+        m = MeshC(xyz.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)), tri.shape[0],
+                  tri.ctypes.data_as(C.POINTER(C.c_int32)), obj.ctypes.data_as(C.POINTER(C.c_int32)),
+                  mesh.nobj, mats)
+        g = GridC((C.c_double * 3)(*grid.origin), (C.c_double * 3)(*grid.h),
+                  (C.c_int32 * 3)(*[int(v) for v in grid.n]), 2, int(r_near))
+        h = C.c_void_p()
+        _check(L.aim_setup(C.byref(m), C.byref(g), float(freq), C.byref(h)))
+        self.h = h
+        info = (C.c_int64 * 13)()
+        _check(L.aim_info(h, info, 13))
+        self.info = list(info)
+        self.ne, self.nt, self.nobj = info[0], info[1], info[2]
+        self.n = self.ne + self.nt
+        self.grid_n = tuple(info[3:6])
+        self.padded = tuple(info[6:9])
+        self.nnz_A, self.nnz_P = info[9], info[10]
+        self.zy_bytes_c32 = info[11]
+        self.ng = int(np.prod(self.grid_n))
+
+    def close(self):
+        if self.h:
+            lib().aim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- products ----------------------------------------------------------------
+    def matvec(self, x, y=None, which=AIM_OP_SYSTEM, prec=BEM_C32):
+        import torch
+        n = {AIM_OP_LA: self.ne, AIM_OP_LPHI: self.nt, AIM_OP_SYSTEM: self.n}[which]
+        if y is None:
+            y = torch.empty(n, dtype=cdtype(prec), device=x.device)
+        if x.numel() != n or y.numel() != n:
+            raise ValueError("vector length mismatch")
+        _check(lib().aim_matvec(self.h, which, _ptr(x, cdtype(prec)), _ptr(y, cdtype(prec)), prec,
+                                _stream()))
+        return y
+
+    def internal(self, h, e=None, heq=None, nrhs=1, prec=BEM_C32, want_heq=True):
+        import torch
+        dt = cdtype(prec)
+        if e is None:
+            e = torch.empty_like(h)
+        if heq is None and want_heq:
+            heq = torch.empty_like(h)
+        _check(lib().internal_apply(self.h, _ptr(h, dt), _ptr(e, dt),
+                                    _ptr(heq, dt) if heq is not None else None, int(nrhs), prec,
+                                    _stream()))
+        return e, heq
+
+    def conv(self, sigma, phi=None, ncomp=1, prec=BEM_C32):
+        import torch
+        if phi is None:
+            phi = torch.empty_like(sigma)
+        _check(lib().aim_conv(self.h, _ptr(sigma, cdtype(prec)), _ptr(phi, cdtype(prec)), int(ncomp),
+                              prec, _stream()))
+        return phi
+
+    def rhs_plane_wave(self, pol=(1.0, 0.0, 0.0), khat=(0.0, 0.0, 1.0), prec=BEM_C64, device="cuda"):
+        import torch
+        b = torch.empty(self.n, dtype=cdtype(prec), device=device)
+        p = (C.c_double * 3)(*pol)
+        k = (C.c_double * 3)(*khat)
+        _check(lib().bem_rhs_plane_wave(self.h, p, k, _ptr(b), prec, _stream()))
+        return b
+
+    def solve(self, b, x=None, tol=1e-6, restart=100, max_iter=1000, prec_mode=BEM_C64,
+              time_limit_s=0.0):
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        o = SolveOpts(tol, restart, max_iter, prec_mode, 0, time_limit_s)
+        inf = SolveInfo()
+        rc = _check(lib().bem_solve(self.h, _ptr(b, torch.complex128), _ptr(x, torch.complex128),
+                                    C.byref(o), C.byref(inf), _stream()))
+        return x, {"status": rc, "iters": inf.iters, "resid_est": inf.resid_est,
+                   "resid_true": inf.resid_true, "seconds": inf.seconds}
+
+    # ---- set-up products (host copies) ----------------------------------------------
+    def _export(self, what, index=0):
+        L = lib()
+        need = L.aim_export(self.h, what, index, None, 0)
+        _check(need)
+        buf = np.empty(need, dtype=np.uint8)
+        _check(L.aim_export(self.h, what, index, buf.ctypes.data_as(C.c_void_p), need))
+        return buf
+
+    def Z(self, i):
+        b = self._export(0, i).view(np.complex128)
+        n = int(round(np.sqrt(b.size)))
+        return b.reshape(n, n)
+
+    def Y(self, i):
+        b = self._export(1, i).view(np.complex128)
+        n = int(round(np.sqrt(b.size)))
+        return b.reshape(n, n)
+
+    def near(self, which):
+        b = self._export(2 if which == "A" else 3)
+        nr = (self.ne if which == "A" else self.nt) + 1
+        row = b[:nr * 8].view(np.int64)
+        nnz = int(row[-1])
+        col = b[nr * 8:nr * 8 + nnz * 4].view(np.int32)
+        val = b[nr * 8 + nnz * 4:].view(np.complex128)
+        return row, col, val
+
+    def weights(self):
+        WA = self._export(4).view(np.float64).reshape(self.ne, 3, 27)
+        WP = self._export(5).view(np.float64).reshape(self.nt, 27)
+        return WA, WP
+
+    def anchors(self):
+        return self._export(6).view(np.int32).reshape(-1, 3)
+
+    def edges(self):
+        return self._export(7).view(np.int32).reshape(self.ne, 6)

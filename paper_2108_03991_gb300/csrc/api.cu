@@ -1,0 +1,273 @@
+// extern "C" entry points of libbem_aim.so (declared and documented in include/bem_aim.h).
+#include <cstdarg>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace bem {
+
+static thread_local char g_err[1024] = {0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int dalloc(aim_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BEM_ENOMEM : BEM_ECUDA;
+  }
+  c->allocs.push_back(*p);
+  return BEM_OK;
+}
+
+static int check_ctx(const aim_ctx* c, const char* who) {
+  if (!c) {
+    set_error("%s: null context", who);
+    return BEM_EINVAL;
+  }
+  return BEM_OK;
+}
+
+static int check_prec(int prec, const char* who) {
+  if (prec != BEM_C32 && prec != BEM_C64) {
+    set_error("%s: prec must be BEM_C32 or BEM_C64", who);
+    return BEM_EINVAL;
+  }
+  return BEM_OK;
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" {
+
+const char* bem_last_error(void) { return g_err; }
+
+int aim_setup(const bem_mesh* mesh, const aim_grid* grid, double freq_hz, aim_ctx** out) {
+  g_err[0] = 0;
+  if (!out) {
+    set_error("aim_setup: null output pointer");
+    return BEM_EINVAL;
+  }
+  *out = nullptr;
+  if (!(freq_hz > 0) || !std::isfinite(freq_hz)) {
+    set_error("aim_setup: frequency must be positive");
+    return BEM_EINVAL;
+  }
+  aim_ctx* c = new aim_ctx();
+  cudaGetDevice(&c->device);
+  c->freq = freq_hz;
+  c->k0 = k0_of(freq_hz);
+  int rc = build_geometry(c, mesh, grid);
+  if (rc == BEM_OK) rc = setup_device(c);
+  if (rc != BEM_OK) {
+    aim_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return BEM_OK;
+}
+
+void aim_destroy(aim_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  free_geo_store(c);
+  delete c;
+}
+
+int aim_info(const aim_ctx* c, int64_t* info, int n) {
+  BEM_TRY(check_ctx(c, "aim_info"));
+  if (!info || n < 0) {
+    set_error("aim_info: bad output");
+    return BEM_EINVAL;
+  }
+  int maxn = 0;
+  for (int i = 0; i < c->nobj; ++i) maxn = std::max(maxn, c->e1[i] - c->e0[i]);
+  int64_t v[13] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
+                   c->rowA.empty() ? 0 : c->rowA.back(), c->rowP.empty() ? 0 : c->rowP.back(),
+                   2 * c->zelems * 8, maxn};
+  for (int i = 0; i < n && i < 13; ++i) info[i] = v[i];
+  return BEM_OK;
+}
+
+int aim_matvec(aim_ctx* c, int which, const void* x, void* y, int prec, void* stream) {
+  BEM_TRY(check_ctx(c, "aim_matvec"));
+  BEM_TRY(check_prec(prec, "aim_matvec"));
+  if (!x || !y || x == y) {
+    set_error("aim_matvec: x and y must be distinct device pointers");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  return prec == BEM_C32 ? matvec<float>(c, which, x, y, s) : matvec<double>(c, which, x, y, s);
+}
+
+int internal_apply(aim_ctx* c, const void* h, void* e, void* heq, int nrhs, int prec, void* stream) {
+  BEM_TRY(check_ctx(c, "internal_apply"));
+  BEM_TRY(check_prec(prec, "internal_apply"));
+  if (!h || !e || nrhs < 1 || h == e || heq == e || heq == h) {
+    set_error("internal_apply: bad pointers or nrhs");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  return prec == BEM_C32 ? internal<float>(c, h, e, heq, nrhs, s) : internal<double>(c, h, e, heq, nrhs, s);
+}
+
+int aim_conv(aim_ctx* c, const void* sigma, void* phi, int ncomp, int prec, void* stream) {
+  BEM_TRY(check_ctx(c, "aim_conv"));
+  BEM_TRY(check_prec(prec, "aim_conv"));
+  if (!sigma || !phi || ncomp < 1 || ncomp > 4) {
+    set_error("aim_conv: bad pointers or ncomp");
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  return prec == BEM_C32 ? conv<float>(c, sigma, phi, ncomp, s) : conv<double>(c, sigma, phi, ncomp, s);
+}
+
+int bem_blockdiag_gemv(int nblk, const int32_t* n, const void* A, const void* x, void* y, int nrhs,
+                       int prec, void* stream) {
+  BEM_TRY(check_prec(prec, "bem_blockdiag_gemv"));
+  if (nblk < 1 || !n || !A || !x || !y || nrhs < 1 || x == y) {
+    set_error("bem_blockdiag_gemv: bad arguments");
+    return BEM_EINVAL;
+  }
+  std::vector<int32_t> nn(n, n + nblk), xo(nblk), ld(nblk);
+  std::vector<int64_t> off(nblk);
+  int64_t o = 0;
+  int32_t xs = 0;
+  for (int i = 0; i < nblk; ++i) {
+    if (nn[i] < 1) {
+      set_error("bem_blockdiag_gemv: block sizes must be positive");
+      return BEM_EINVAL;
+    }
+    ld[i] = (int32_t)round_up(nn[i], 4);
+    off[i] = o;
+    xo[i] = xs;
+    o += (int64_t)nn[i] * ld[i];
+    xs += nn[i];
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<GemvTask> tasks;
+  build_gemv_tasks(nn, off, xo, ld, nsm, &tasks);
+  GemvTask* d = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  BEM_CUDA(cudaMallocAsync((void**)&d, tasks.size() * sizeof(GemvTask), s));
+  BEM_CUDA(cudaMemcpyAsync(d, tasks.data(), tasks.size() * sizeof(GemvTask), cudaMemcpyHostToDevice, s));
+  int rc = prec == BEM_C32
+               ? run_gemv<float>(d, (int)tasks.size(), (const float2*)A, (const float2*)x, (float2*)y, nrhs, xs, nullptr, s)
+               : run_gemv<double>(d, (int)tasks.size(), (const double2*)A, (const double2*)x, (double2*)y, nrhs, xs, nullptr, s);
+  cudaFreeAsync(d, s);
+  // the host task vector must outlive the asynchronous copy
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+int64_t aim_export(const aim_ctx* c, int what, int index, void* out, int64_t cap) {
+  if (check_ctx(c, "aim_export") != BEM_OK) return BEM_EINVAL;
+  auto copy_dev = [&](const void* src, int64_t bytes, char* dst) -> int {
+    cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      set_error("aim_export: %s", cudaGetErrorString(e));
+      return BEM_ECUDA;
+    }
+    return BEM_OK;
+  };
+  if (what == 0 || what == 1) {
+    if (index < 0 || index >= c->nobj) {
+      set_error("aim_export: object index out of range");
+      return BEM_EINVAL;
+    }
+    const int n = c->e1[index] - c->e0[index], ld = c->zld[index];
+    int64_t need = (int64_t)n * n * 16;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    std::vector<double2> tmp((size_t)n * ld);
+    const double2* src = (what == 0 ? c->f64.Z : c->f64.Y) + c->zoff[index];
+    if (copy_dev(src, (int64_t)tmp.size() * 16, (char*)tmp.data())) return BEM_ECUDA;
+    double2* o = (double2*)out;
+    for (int r = 0; r < n; ++r)
+      for (int k = 0; k < n; ++k) o[(int64_t)r * n + k] = tmp[(int64_t)r * ld + k];
+    return need;
+  }
+  if (what == 2 || what == 3) {
+    const std::vector<int64_t>& row = what == 2 ? c->rowA : c->rowP;
+    const std::vector<int32_t>& col = what == 2 ? c->colA : c->colP;
+    const int64_t nnz = row.back(), nr = (int64_t)row.size();
+    int64_t need = nr * 8 + nnz * 4 + nnz * 16;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    char* o = (char*)out;
+    memcpy(o, row.data(), nr * 8);
+    memcpy(o + nr * 8, col.data(), nnz * 4);
+    if (copy_dev(what == 2 ? (const void*)c->f64.LA : (const void*)c->f64.LP, nnz * 16, o + nr * 8 + nnz * 4))
+      return BEM_ECUDA;
+    return need;
+  }
+  if (what == 4 || what == 5) {
+    int64_t need = what == 4 ? (int64_t)c->ne * 81 * 8 : (int64_t)c->nt * 27 * 8;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    if (copy_dev(what == 4 ? (const void*)c->f64.WA : (const void*)c->f64.WP, need, (char*)out)) return BEM_ECUDA;
+    return need;
+  }
+  if (what == 6) {
+    int64_t need = (int64_t)c->anc.size() * 4;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    memcpy(out, c->anc.data(), need);
+    return need;
+  }
+  if (what == 7) {
+    int64_t need = (int64_t)c->ne * 6 * 4;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    int32_t* o = (int32_t*)out;
+    for (int n = 0; n < c->ne; ++n) {
+      o[6 * n] = c->ev[2 * n]; o[6 * n + 1] = c->ev[2 * n + 1];
+      o[6 * n + 2] = c->et[2 * n]; o[6 * n + 3] = c->et[2 * n + 1];
+      o[6 * n + 4] = c->eopp[2 * n]; o[6 * n + 5] = c->eopp[2 * n + 1];
+    }
+    return need;
+  }
+  set_error("aim_export: unknown item %d", what);
+  return BEM_EINVAL;
+}
+
+int bem_rhs_plane_wave(aim_ctx* c, const double* pol, const double* khat, void* b, int prec,
+                       void* stream) {
+  BEM_TRY(check_ctx(c, "bem_rhs_plane_wave"));
+  BEM_TRY(check_prec(prec, "bem_rhs_plane_wave"));
+  if (!pol || !khat || !b) {
+    set_error("bem_rhs_plane_wave: null pointer");
+    return BEM_EINVAL;
+  }
+  return rhs_plane_wave(c, pol, khat, b, prec, (cudaStream_t)stream);
+}
+
+int bem_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,
+              void* stream) {
+  BEM_TRY(check_ctx(c, "bem_solve"));
+  if (!b || !x || !o || b == x) {
+    set_error("bem_solve: bad pointers");
+    return BEM_EINVAL;
+  }
+  if (!(o->tol > 0) || o->restart < 1 || o->restart > 512 || o->max_iter < 1) {
+    set_error("bem_solve: bad options");
+    return BEM_EINVAL;
+  }
+  BEM_TRY(check_prec(o->prec_mode, "bem_solve"));
+  return gmres_solve(c, b, x, o, info, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,212 @@
+// Shared definitions of the GB300 SLIM library: error handling, complex helpers, context.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/bem_aim.h"
+
+namespace bem {
+
+void set_error(const char* fmt, ...);
+
+#define BEM_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      ::bem::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(_e)); \
+      return BEM_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+#define BEM_TRY(call)            \
+  do {                           \
+    int _r = (call);             \
+    if (_r < 0) return _r;       \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// complex arithmetic on float2 / double2 (interleaved re, im)
+// ---------------------------------------------------------------------------------------
+template <typename R> struct C2;
+template <> struct C2<float> { typedef float2 T; };
+template <> struct C2<double> { typedef double2 T; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <typename V> __host__ __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename V> __host__ __device__ __forceinline__ V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename V> __host__ __device__ __forceinline__ V cmul(V a, V b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __host__ __device__ __forceinline__ V cconj(V a) { return mk(a.x, -a.y); }
+template <typename V> __host__ __device__ __forceinline__ V czero();
+template <> __host__ __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <typename V, typename R> __host__ __device__ __forceinline__ V cscale(V a, R s) {
+  return mk(a.x * s, a.y * s);
+}
+// a += b * c
+template <typename V> __host__ __device__ __forceinline__ void cfma(V& a, V b, V c) {
+  a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+  a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+__device__ __forceinline__ void cfma(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+  a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+
+template <typename V> __device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+static inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------------------------------
+// one FFT length: radix plan and twiddle table e^{-2 pi i k / P}
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxStages = 16;
+struct FftPlan {
+  int P = 0;
+  int nst = 0;
+  int rad[kMaxStages] = {0};
+};
+bool make_fft_plan(int P, FftPlan* plan);
+int smooth_length(int need);  // smallest length >= need whose factors are 2, 3, 5, 7
+
+// ---------------------------------------------------------------------------------------
+// precision-specific device buffers
+// ---------------------------------------------------------------------------------------
+template <typename R> struct PrecBuf {
+  typedef typename C2<R>::T V;
+  V* Z = nullptr;      // packed row-major blocks (ld_i = round_up(n_i, 4))
+  V* Y = nullptr;
+  R* WA = nullptr;     // [ne][3][27] projection weights of RWG functions
+  R* WP = nullptr;     // [nt][27] projection weights of pulses
+  V* LA = nullptr;     // near-region values (CSR, shared structure with the host arrays)
+  V* LP = nullptr;
+  V* Ghat = nullptr;   // octant of the scaled FFT of the circulant grid kernel
+  V* tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables of the three axes
+  R* ix = nullptr;     // [ne][4] I_x values
+  R* fdE = nullptr;    // [ne][2] (l/A+, l/A-) : (F D)^T rows
+  R* fdT = nullptr;    // [nt][3] signed l/A for the triangle's edges : F D rows
+  // workspaces
+  V* sigma = nullptr;  // [4][ng]
+  V* ws = nullptr;     // [4][Pz][Py][Px]
+  V* e = nullptr;      // [ne]
+  V* heq = nullptr;    // [ne]
+  V* j = nullptr;      // [ne]
+  V* p = nullptr;      // [nt]
+  V* xin = nullptr;    // [ne + nt] conversion buffer for mixed precision
+  V* yout = nullptr;
+};
+
+struct GemvTask {  // a run of rows of one block
+  int64_t aoff;    // element offset of the block
+  int32_t xoff;    // first unknown of the block
+  int32_t n;       // block size
+  int32_t ld;
+  int32_t row0;
+  int32_t nrows;
+};
+
+}  // namespace bem
+
+struct aim_ctx {
+  int device = 0;
+  int ne = 0, nt = 0, nobj = 0, nv = 0;
+  int gn[3] = {0, 0, 0};
+  int gp[3] = {0, 0, 0};  // padded FFT lengths
+  double go[3], gh[3];
+  int64_t ng = 0;
+  int r_near = 2;
+  double freq = 0, k0 = 0;
+  // host copies
+  std::vector<double> verts;          // [nv*3]
+  std::vector<int32_t> tris;          // [nt*3]
+  std::vector<int32_t> obj_t;
+  std::vector<bem_material> mat;
+  std::vector<int32_t> ev, et, eopp;  // [ne*2]
+  std::vector<int32_t> obj_e;
+  std::vector<double> elen, area, normal, centroid, diam;
+  std::vector<int32_t> t_edges, t_esign, t_evert;  // [nt*3]
+  std::vector<int32_t> e0, e1, t0, t1;             // object ranges
+  std::vector<int32_t> anc;                        // [(ne+nt)*3]
+  std::vector<int64_t> rowA, rowP;                 // near CSR row pointers
+  std::vector<int32_t> colA, colP;
+  std::vector<int64_t> zoff;                       // element offset of block i
+  std::vector<int32_t> zld;
+  int64_t zelems = 0;
+  std::vector<bem::GemvTask> tasks;
+  bem::FftPlan plan[3];
+  // device: integer tables
+  int32_t* d_nodeE = nullptr;  // [ne] linear index of the anchor node
+  int32_t* d_nodeT = nullptr;  // [nt]
+  int64_t* d_rowA = nullptr;
+  int32_t* d_colA = nullptr;
+  int64_t* d_rowP = nullptr;
+  int32_t* d_colP = nullptr;
+  int32_t* d_ixcol = nullptr;  // [ne][4]
+  int32_t* d_et = nullptr;     // [ne][2]
+  int32_t* d_tedge = nullptr;  // [nt][3]
+  bem::GemvTask* d_tasks = nullptr;
+  int ntasks = 0;
+  bem::PrecBuf<float> f32;
+  bem::PrecBuf<double> f64;
+  std::vector<void*> allocs;   // every device allocation, freed by aim_destroy
+  void* geo_store = nullptr;   // device geometry descriptor (set-up kernels, right-hand sides)
+};
+
+namespace bem {
+int dalloc(aim_ctx* c, void** p, size_t bytes);
+template <typename T> int dalloc_t(aim_ctx* c, T** p, size_t count) {
+  return dalloc(c, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+template <typename T> int upload(aim_ctx* c, T** p, const T* host, size_t count) {
+  BEM_TRY(dalloc_t(c, p, count));
+  if (count) BEM_CUDA(cudaMemcpy(*p, host, count * sizeof(T), cudaMemcpyHostToDevice));
+  return BEM_OK;
+}
+
+// geometry (host, geom.cpp)
+int build_geometry(aim_ctx* c, const bem_mesh* m, const aim_grid* g);
+// scheduling (host, sched.cpp)
+void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
+                      const std::vector<int32_t>& xoff, const std::vector<int32_t>& ld,
+                      int nsm, std::vector<GemvTask>* tasks);
+// setup (setup.cu)
+int setup_device(aim_ctx* c);
+// hot path (hot.cu)
+template <typename R>
+int run_gemv(const GemvTask* d_tasks, int ntasks, const typename C2<R>::T* A,
+             const typename C2<R>::T* x, typename C2<R>::T* y, int nrhs, int64_t vstride,
+             const typename C2<R>::T* hsub, cudaStream_t s);
+template <typename R> int matvec(aim_ctx* c, int which, const void* x, void* y, cudaStream_t s);
+template <typename R> int internal(aim_ctx* c, const void* h, void* e, void* heq, int nrhs,
+                                   cudaStream_t s);
+template <typename R> int conv(aim_ctx* c, const void* sigma, void* phi, int ncomp,
+                               cudaStream_t s);
+// fft (fft.cu)
+template <typename R>
+int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename C2<R>::T* phi,
+             int ncomp, cudaStream_t s);
+template <typename R> int make_twiddles(aim_ctx* c, PrecBuf<R>& b);
+int make_ghat(aim_ctx* c);
+int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
+                   cudaStream_t st);
+void free_geo_store(aim_ctx* c);
+double k0_of(double f);
+// solver (gmres.cu)
+int gmres_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,
+                cudaStream_t s);
+}  // namespace bem

@@ -1,0 +1,275 @@
+// Restarted GMRES on the device (Sec. III-E: the solver only needs products with the system
+// matrix of Eq. AEFIEoutJ). Arnoldi with classical Gram-Schmidt applied twice (CGS2) in FP64,
+// Givens rotations and the small triangular solve in FP64 on the device. The system matvec
+// runs in complex FP64 (prec_mode BEM_C64, the plain method) or complex FP32 (BEM_C32); in the
+// FP32 mode every restart recomputes the residual with the FP64 matvec, so the outer loop is an
+// iterative refinement and the reported true residual is an FP64 one.
+#include <chrono>
+
+#include "common.cuh"
+
+namespace bem {
+
+static constexpr int kChunks = 304;  // 2 x 152 SMs
+
+__global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int nv,
+                       const double2* __restrict__ w, int64_t n, double2* __restrict__ partial) {
+  __shared__ double2 red[8];
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+  for (int j = 0; j < nv; ++j) {
+    double2 acc = make_double2(0, 0);
+    const double2* v = V + j * ldv;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      double2 a = v[i], b = w[i];
+      acc.x += a.x * b.x + a.y * b.y;  // conj(a) b
+      acc.y += a.x * b.y - a.y * b.x;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 s = make_double2(0, 0);
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { s.x += red[k].x; s.y += red[k].y; }
+      partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// h[j] = sum of partials; if acc != nullptr: acc[j] += h[j]
+__global__ void k_reduce(const double2* __restrict__ partial, int nchunks, int nv, double2* h,
+                         double2* acc) {
+  const int j = blockIdx.x;
+  if (j >= nv) return;
+  double2 s = make_double2(0, 0);
+  for (int i = threadIdx.x; i < nchunks; i += blockDim.x) {
+    s.x += partial[(int64_t)j * nchunks + i].x;
+    s.y += partial[(int64_t)j * nchunks + i].y;
+  }
+  s = warp_sum(s);
+  __shared__ double2 red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0, 0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { t.x += red[k].x; t.y += red[k].y; }
+    h[j] = t;
+    if (acc) { acc[j].x += t.x; acc[j].y += t.y; }
+  }
+}
+
+// w += sign * sum_j h[j] V[j]
+__global__ void k_axpy_basis(const double2* __restrict__ V, int64_t ldv, int nv,
+                             const double2* __restrict__ h, double sign, double2* w, int64_t n) {
+  extern __shared__ double2 hs[];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 acc = w[i];
+    for (int j = 0; j < nv; ++j) {
+      double2 v = V[j * ldv + i], c = hs[j];
+      acc.x += sign * (c.x * v.x - c.y * v.y);
+      acc.y += sign * (c.x * v.y + c.y * v.x);
+    }
+    w[i] = acc;
+  }
+}
+
+// out = in * (1 / |norm2|)  where nrm2 holds |w|^2 (as the real part of a dot product)
+__global__ void k_normalize(const double2* __restrict__ in, const double2* nrm2, double2* out,
+                            double* hsub, int64_t n) {
+  const double nr = sqrt(fmax(nrm2->x, 0.0));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && hsub) *hsub = nr;
+  const double s = nr > 0 ? 1.0 / nr : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_double2(in[i].x * s, in[i].y * s);
+}
+
+__global__ void k_sub(const double2* a, const double2* b, double2* o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
+__global__ void k_to32(const double2* a, float2* o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void k_to64(const float2* a, double2* o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = make_double2(a[i].x, a[i].y);
+}
+
+// Givens step for column k of H (leading dimension ldh = m + 1), one thread.
+// Rotation (c, s) acts as (x, y) -> (conj(c) x + conj(s) y, -s x + c y).
+__global__ void k_givens(double2* H, int ldh, int k, const double* hsub, double2* cs, double2* sn,
+                         double2* g, double* resid) {
+  double2* col = H + (int64_t)k * ldh;
+  col[k + 1] = make_double2(*hsub, 0.0);
+  for (int i = 0; i < k; ++i) {
+    double2 a = col[i], b = col[i + 1], c = cs[i], s = sn[i];
+    double2 t = cadd(cmul(cconj(c), a), cmul(cconj(s), b));
+    col[i + 1] = csub(cmul(c, b), cmul(s, a));
+    col[i] = t;
+  }
+  double2 a = col[k], b = col[k + 1];
+  double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+  double2 c = den > 0 ? make_double2(a.x / den, a.y / den) : make_double2(1, 0);
+  double2 s = den > 0 ? make_double2(b.x / den, b.y / den) : make_double2(0, 0);
+  cs[k] = c;
+  sn[k] = s;
+  col[k] = make_double2(den, 0.0);
+  col[k + 1] = make_double2(0, 0);
+  double2 gk = g[k];
+  g[k + 1] = mk(-(s.x * gk.x - s.y * gk.y), -(s.x * gk.y + s.y * gk.x));
+  g[k] = cmul(cconj(c), gk);
+  *resid = sqrt(g[k + 1].x * g[k + 1].x + g[k + 1].y * g[k + 1].y);
+}
+
+// y = R^{-1} g for the leading k x k upper-triangular block, one thread
+__global__ void k_backsolve(const double2* H, int ldh, int k, const double2* g, double2* y) {
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i];
+    for (int j = i + 1; j < k; ++j) s = csub(s, cmul(H[(int64_t)j * ldh + i], y[j]));
+    double2 d = H[(int64_t)i * ldh + i];
+    double dd = d.x * d.x + d.y * d.y;
+    y[i] = dd > 0 ? cmul(s, make_double2(d.x / dd, -d.y / dd)) : make_double2(0, 0);
+  }
+}
+
+__global__ void k_set_g0(double2* g, int m1, const double* beta) {
+  for (int i = threadIdx.x; i < m1; i += blockDim.x) g[i] = make_double2(i == 0 ? *beta : 0.0, 0.0);
+}
+
+struct GmWork {
+  double2 *V = nullptr, *w = nullptr, *r = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr,
+          *g = nullptr, *h = nullptr, *hacc = nullptr, *partial = nullptr, *y = nullptr;
+  double* dsc = nullptr;  // [0] = subdiagonal, [1] = residual estimate, [2] = beta
+  std::vector<void*> mem;
+  ~GmWork() { for (void* p : mem) cudaFree(p); }
+  template <typename T> int alloc(T** p, size_t n) {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+    if (e != cudaSuccess) { set_error("gmres workspace: %s", cudaGetErrorString(e)); return BEM_ENOMEM; }
+    mem.push_back(*p);
+    return BEM_OK;
+  }
+};
+
+static int dot_into(const double2* V, int64_t ldv, int nv, const double2* w, int64_t n, GmWork& W,
+                    double2* h, double2* acc, cudaStream_t s) {
+  k_dots<<<kChunks, 256, 0, s>>>(V, ldv, nv, w, n, W.partial);
+  k_reduce<<<nv, 256, 0, s>>>(W.partial, kChunks, nv, h, acc);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// y = A x in FP64 (plain) or through the FP32 matvec
+static int sys_apply(aim_ctx* c, int prec, const double2* x, double2* y, cudaStream_t s) {
+  const int64_t n = (int64_t)c->ne + c->nt;
+  if (prec == BEM_C64) return matvec<double>(c, AIM_OP_SYSTEM, x, y, s);
+  k_to32<<<kChunks, 256, 0, s>>>(x, c->f32.xin, n);
+  BEM_TRY(matvec<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s));
+  k_to64<<<kChunks, 256, 0, s>>>(c->f32.yout, y, n);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, bem_solve_info* info,
+                cudaStream_t s) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const double2* b = (const double2*)bv;
+  double2* x = (double2*)xv;
+  const int64_t n = (int64_t)c->ne + c->nt;
+  const int m = o->restart;
+  const int ldh = m + 1;
+  GmWork W;
+  BEM_TRY(W.alloc(&W.V, (size_t)(m + 1) * n));
+  BEM_TRY(W.alloc(&W.w, n));
+  BEM_TRY(W.alloc(&W.r, n));
+  BEM_TRY(W.alloc(&W.H, (size_t)ldh * m));
+  BEM_TRY(W.alloc(&W.cs, m));
+  BEM_TRY(W.alloc(&W.sn, m));
+  BEM_TRY(W.alloc(&W.g, m + 1));
+  BEM_TRY(W.alloc(&W.h, m + 1));
+  BEM_TRY(W.alloc(&W.hacc, m + 1));
+  BEM_TRY(W.alloc(&W.y, m + 1));
+  BEM_TRY(W.alloc(&W.partial, (size_t)(m + 1) * kChunks));
+  BEM_TRY(W.alloc(&W.dsc, 8));
+  BEM_CUDA(cudaMemsetAsync(W.H, 0, sizeof(double2) * ldh * m, s));
+  // ||b||
+  BEM_TRY(dot_into(b, n, 1, b, n, W, W.h, nullptr, s));
+  double2 bb;
+  BEM_CUDA(cudaMemcpyAsync(&bb, W.h, sizeof(double2), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(std::max(bb.x, 0.0));
+  int iters = 0;
+  double est = 1.0, truer = 1.0;
+  int status = BEM_ENOCONV;
+  if (bnorm == 0) {
+    BEM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double2), s));
+    status = BEM_OK;
+    est = truer = 0;
+  }
+  while (status != BEM_OK && iters < o->max_iter) {
+    // r = b - A x (FP64 matvec), beta = ||r||
+    BEM_TRY(matvec<double>(c, AIM_OP_SYSTEM, x, W.w, s));
+    k_sub<<<kChunks, 256, 0, s>>>(b, W.w, W.r, n);
+    BEM_TRY(dot_into(W.r, n, 1, W.r, n, W, W.h, nullptr, s));
+    k_normalize<<<kChunks, 256, 0, s>>>(W.r, W.h, W.V, W.dsc + 2, n);
+    double beta;
+    BEM_CUDA(cudaMemcpyAsync(&beta, W.dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    truer = beta / bnorm;
+    est = truer;
+    if (truer <= o->tol) { status = BEM_OK; break; }
+    if (o->time_limit_s > 0 && std::chrono::duration<double>(clk::now() - t0).count() > o->time_limit_s) break;
+    k_set_g0<<<1, 256, 0, s>>>(W.g, m + 1, W.dsc + 2);
+    int k = 0;
+    for (; k < m && iters < o->max_iter; ++k) {
+      const double2* vk = W.V + (int64_t)k * n;
+      BEM_TRY(sys_apply(c, o->prec_mode, vk, W.w, s));
+      // CGS2: h = V^H w, w -= V h, twice; accumulate into column k of H
+      double2* Hk = W.H + (int64_t)k * ldh;
+      BEM_CUDA(cudaMemsetAsync(Hk, 0, sizeof(double2) * (k + 1), s));
+      for (int pass = 0; pass < 2; ++pass) {
+        BEM_TRY(dot_into(W.V, n, k + 1, W.w, n, W, W.h, Hk, s));
+        k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>(W.V, n, k + 1, W.h, -1.0, W.w, n);
+      }
+      BEM_TRY(dot_into(W.w, n, 1, W.w, n, W, W.h, nullptr, s));
+      k_normalize<<<kChunks, 256, 0, s>>>(W.w, W.h, W.V + (int64_t)(k + 1) * n, W.dsc, n);
+      k_givens<<<1, 1, 0, s>>>(W.H, ldh, k, W.dsc, W.cs, W.sn, W.g, W.dsc + 1);
+      BEM_CUDA(cudaGetLastError());
+      double res;
+      BEM_CUDA(cudaMemcpyAsync(&res, W.dsc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaStreamSynchronize(s));
+      ++iters;
+      est = res / bnorm;
+      if (est <= o->tol) { ++k; break; }
+      if (o->time_limit_s > 0 && std::chrono::duration<double>(clk::now() - t0).count() > o->time_limit_s) { ++k; break; }
+    }
+    // x += V[:k] y, y = R^{-1} g
+    k_backsolve<<<1, 1, 0, s>>>(W.H, ldh, k, W.g, W.y);
+    k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>(W.V, n, k, W.y, 1.0, x, n);
+    BEM_CUDA(cudaGetLastError());
+    if (o->time_limit_s > 0 && std::chrono::duration<double>(clk::now() - t0).count() > o->time_limit_s) break;
+  }
+  // true residual with the FP64 matvec
+  BEM_TRY(matvec<double>(c, AIM_OP_SYSTEM, x, W.w, s));
+  k_sub<<<kChunks, 256, 0, s>>>(b, W.w, W.r, n);
+  BEM_TRY(dot_into(W.r, n, 1, W.r, n, W, W.h, nullptr, s));
+  double2 rr;
+  BEM_CUDA(cudaMemcpyAsync(&rr, W.h, sizeof(double2), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA(cudaStreamSynchronize(s));
+  truer = bnorm > 0 ? std::sqrt(std::max(rr.x, 0.0)) / bnorm : 0.0;
+  status = truer <= o->tol ? BEM_OK : BEM_ENOCONV;
+  if (info) {
+    info->iters = iters;
+    info->resid_est = est;
+    info->resid_true = truer;
+    info->seconds = std::chrono::duration<double>(clk::now() - t0).count();
+  }
+  return status;
+}
+
+}  // namespace bem

@@ -1,0 +1,302 @@
+// Hot path: the system matrix-vector product of Eq. (AEFIEoutJ), applied as a sequence
+// (never assembled), in complex FP32 or FP64:
+//   e = Z h                     block-diagonal GEMV over objects        (Eq. MFIEinZin)
+//   j = h - Y e                 block-diagonal GEMV, fused subtraction  (Eqs. EFIEeqYeq, Jdeltadis)
+//   sigma = P [j; q]            27-node stencil scatter (3 RWG components + pulses)
+//   phi = H sigma               zero-padded FFT convolution (fft.cu)
+//   p = W_Phi phi + L^Phi_NR q  ;  y2 = F D j + j k0 q          (one warp per triangle)
+//   a = W phi + L^A_NR j        ;  y1 = j k0 a + I_x e - (F D)^T p  (one warp per edge)
+// Sec. III-A item 1 (Eq. AIM_L) gives L = L_NR + W H P; Sec. II-C (Eq. Cdef) gives the
+// combination C = (-j k0 L^A Y + I_x/eta0) Z.
+#include "common.cuh"
+
+namespace bem {
+
+// ---------------------------------------------------------------------------------------
+// block-diagonal GEMV: one warp per row, 16-byte vector loads, x read through the L1 cache
+// ---------------------------------------------------------------------------------------
+template <typename R> struct Vec16;
+template <> struct Vec16<float> { typedef float4 T; static constexpr int kCplx = 2; };
+template <> struct Vec16<double> { typedef double2 T; static constexpr int kCplx = 1; };
+
+template <typename R, int NRHS>
+__global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks,
+                                              const typename C2<R>::T* __restrict__ A,
+                                              const typename C2<R>::T* __restrict__ x,
+                                              typename C2<R>::T* __restrict__ y, int64_t vstride,
+                                              const typename C2<R>::T* __restrict__ hsub) {
+  typedef typename C2<R>::T V;
+  typedef typename Vec16<R>::T L16;
+  constexpr int CP = Vec16<R>::kCplx;
+  const GemvTask t = tasks[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const V* xb = x + t.xoff;
+  for (int rr = warp; rr < t.nrows; rr += 8) {
+    const int row = t.row0 + rr;
+    const L16* arow = reinterpret_cast<const L16*>(A + t.aoff + (int64_t)row * t.ld);
+    V acc[NRHS];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
+    const int nvec = (t.n + CP - 1) / CP;
+#pragma unroll 4
+    for (int v = lane; v < nvec; v += 32) {
+      L16 a = __ldg(arow + v);
+      const int col = v * CP;
+      if constexpr (CP == 2) {
+        V a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) {
+          V x0 = __ldg(xb + r * vstride + col);
+          cfma(acc[r], a0, x0);
+          if (col + 1 < t.n) {
+            V x1 = __ldg(xb + r * vstride + col + 1);
+            cfma(acc[r], a1, x1);
+          }
+        }
+      } else {
+        V a0 = mk(a.x, a.y);
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) cfma(acc[r], a0, __ldg(xb + r * vstride + col));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      V s = warp_sum(acc[r]);
+      if (lane == 0) {
+        int64_t o = r * vstride + t.xoff + row;
+        y[o] = hsub ? csub(hsub[o], s) : s;
+      }
+    }
+  }
+}
+
+template <typename R>
+int run_gemv(const GemvTask* d_tasks, int ntasks, const typename C2<R>::T* A,
+             const typename C2<R>::T* x, typename C2<R>::T* y, int nrhs, int64_t vstride,
+             const typename C2<R>::T* hsub, cudaStream_t s) {
+  if (ntasks == 0) return BEM_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += 4) {
+    const int nr = std::min(4, nrhs - r0);
+    const int64_t o = r0 * vstride;
+    const typename C2<R>::T* hs = hsub ? hsub + o : nullptr;
+    switch (nr) {
+      case 1: k_gemv<R, 1><<<ntasks, 256, 0, s>>>(d_tasks, A, x + o, y + o, vstride, hs); break;
+      case 2: k_gemv<R, 2><<<ntasks, 256, 0, s>>>(d_tasks, A, x + o, y + o, vstride, hs); break;
+      case 3: k_gemv<R, 3><<<ntasks, 256, 0, s>>>(d_tasks, A, x + o, y + o, vstride, hs); break;
+      default: k_gemv<R, 4><<<ntasks, 256, 0, s>>>(d_tasks, A, x + o, y + o, vstride, hs); break;
+    }
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int run_gemv<float>(const GemvTask*, int, const float2*, const float2*, float2*, int,
+                             int64_t, const float2*, cudaStream_t);
+template int run_gemv<double>(const GemvTask*, int, const double2*, const double2*, double2*, int,
+                              int64_t, const double2*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+// projection P: scatter with atomics, one thread per (source, stencil node)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int node_offset(int k, int nx, int ny) {
+  return ((k / 9 - 1) * ny + ((k / 3) % 3 - 1)) * nx + (k % 3 - 1);
+}
+
+template <typename R>
+__global__ void k_scatter_e(const R* __restrict__ WA, const int32_t* __restrict__ node,
+                            const typename C2<R>::T* __restrict__ j, typename C2<R>::T* sigma,
+                            int ne, int nx, int ny, int64_t ng) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ne * 27) return;
+  const int m = (int)(idx / 27), k = (int)(idx - (int64_t)m * 27);
+  const typename C2<R>::T v = j[m];
+  const int64_t nd = node[m] + node_offset(k, nx, ny);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R w = WA[(int64_t)m * 81 + c * 27 + k];
+    R* o = reinterpret_cast<R*>(sigma + c * ng + nd);
+    atomicAdd(o, w * v.x);
+    atomicAdd(o + 1, w * v.y);
+  }
+}
+
+template <typename R>
+__global__ void k_scatter_t(const R* __restrict__ WP, const int32_t* __restrict__ node,
+                            const typename C2<R>::T* __restrict__ q, typename C2<R>::T* sigma,
+                            int nt, int nx, int ny) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nt * 27) return;
+  const int t = (int)(idx / 27), k = (int)(idx - (int64_t)t * 27);
+  const typename C2<R>::T v = q[t];
+  const R w = WP[(int64_t)t * 27 + k];
+  R* o = reinterpret_cast<R*>(sigma + node[t] + node_offset(k, nx, ny));
+  atomicAdd(o, w * v.x);
+  atomicAdd(o + 1, w * v.y);
+}
+
+// ---------------------------------------------------------------------------------------
+// interpolation W + near region + combination, one warp per output row
+// ---------------------------------------------------------------------------------------
+template <typename V, typename R>
+__device__ __forceinline__ V jk0(V a, R k0) { return mk(-k0 * a.y, k0 * a.x); }
+
+// mode 0: y[t] = p_t (L^Phi alone); mode 1: p[t] = p_t and y2_t into y[ne + t]
+template <typename R>
+__global__ void __launch_bounds__(256) k_rows_t(
+    const R* __restrict__ WP, const int32_t* __restrict__ node,
+    const typename C2<R>::T* __restrict__ phi, const int64_t* __restrict__ rowP,
+    const int32_t* __restrict__ colP, const typename C2<R>::T* __restrict__ LP,
+    const typename C2<R>::T* __restrict__ q, const R* __restrict__ fdT,
+    const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ j, int nt, int ne,
+    int nx, int ny, R k0, int mode, typename C2<R>::T* __restrict__ p, typename C2<R>::T* __restrict__ y) {
+  typedef typename C2<R>::T V;
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= nt) return;
+  V acc = czero<V>();
+  if (lane < 27) {
+    const R w = WP[(int64_t)t * 27 + lane];
+    const V f = phi[node[t] + node_offset(lane, nx, ny)];
+    acc = mk(w * f.x, w * f.y);
+  }
+  for (int64_t i = rowP[t] + lane; i < rowP[t + 1]; i += 32) cfma(acc, LP[i], q[colP[i]]);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    if (mode == 0) {
+      y[t] = acc;
+    } else {
+      p[t] = acc;
+      V s = jk0(q[t], k0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V jj = j[tedge[3 * t + i]];
+        const R c = fdT[3 * t + i];
+        s.x += c * jj.x;
+        s.y += c * jj.y;
+      }
+      y[ne + t] = s;
+    }
+  }
+}
+
+// mode 0: y[m] = a_m (L^A alone); mode 1: y1_m = j k0 a_m + (I_x e)_m - ((F D)^T p)_m
+template <typename R>
+__global__ void __launch_bounds__(256) k_rows_e(
+    const R* __restrict__ WA, const int32_t* __restrict__ node,
+    const typename C2<R>::T* __restrict__ phi, int64_t ng, const int64_t* __restrict__ rowA,
+    const int32_t* __restrict__ colA, const typename C2<R>::T* __restrict__ LA,
+    const typename C2<R>::T* __restrict__ j, const R* __restrict__ ix,
+    const int32_t* __restrict__ ixcol, const typename C2<R>::T* __restrict__ e,
+    const R* __restrict__ fdE, const int32_t* __restrict__ et,
+    const typename C2<R>::T* __restrict__ p, int ne, int nx, int ny, R k0, int mode,
+    typename C2<R>::T* __restrict__ y) {
+  typedef typename C2<R>::T V;
+  const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (m >= ne) return;
+  V acc = czero<V>();
+  if (lane < 27) {
+    const int64_t nd = node[m] + node_offset(lane, nx, ny);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R w = WA[(int64_t)m * 81 + c * 27 + lane];
+      const V f = phi[c * ng + nd];
+      acc.x += w * f.x;
+      acc.y += w * f.y;
+    }
+  }
+  for (int64_t i = rowA[m] + lane; i < rowA[m + 1]; i += 32) cfma(acc, LA[i], j[colA[i]]);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    if (mode == 0) {
+      y[m] = acc;
+    } else {
+      V s = jk0(acc, k0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const V ev = e[ixcol[4 * m + i]];
+        const R c = ix[4 * m + i];
+        s.x += c * ev.x;
+        s.y += c * ev.y;
+      }
+      const V pp = p[et[2 * m]], pm = p[et[2 * m + 1]];
+      const R cp = fdE[2 * m], cm = fdE[2 * m + 1];
+      s.x += -cp * pp.x + cm * pm.x;
+      s.y += -cp * pp.y + cm * pm.y;
+      y[m] = s;
+    }
+  }
+}
+
+static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename R> PrecBuf<R>& buf(aim_ctx* c);
+template <> PrecBuf<float>& buf<float>(aim_ctx* c) { return c->f32; }
+template <> PrecBuf<double>& buf<double>(aim_ctx* c) { return c->f64; }
+
+template <typename R>
+int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
+  typedef typename C2<R>::T V;
+  PrecBuf<R>& b = buf<R>(c);
+  const V* x = static_cast<const V*>(xv);
+  V* y = static_cast<V*>(yv);
+  const int ne = c->ne, nt = c->nt, nx = c->gn[0], ny = c->gn[1];
+  const int64_t ng = c->ng;
+  const R k0 = (R)c->k0;
+  if (which == AIM_OP_LA) {
+    BEM_CUDA(cudaMemsetAsync(b.sigma, 0, 3 * ng * sizeof(V), s));
+    k_scatter_e<R><<<nb((int64_t)ne * 27, 256), 256, 0, s>>>(b.WA, c->d_nodeE, x, b.sigma, ne, nx, ny, ng);
+    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, s));
+    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
+                                          x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
+                                          nx, ny, k0, 0, y);
+  } else if (which == AIM_OP_LPHI) {
+    V* sq = b.sigma + 3 * ng;
+    BEM_CUDA(cudaMemsetAsync(sq, 0, ng * sizeof(V), s));
+    k_scatter_t<R><<<nb((int64_t)nt * 27, 256), 256, 0, s>>>(b.WP, c->d_nodeT, x, sq, nt, nx, ny);
+    BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, s));
+    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x,
+                                          b.fdT, c->d_tedge, nullptr, nt, ne, nx, ny, k0, 0, nullptr, y);
+  } else if (which == AIM_OP_SYSTEM) {
+    const V* h = x;
+    const V* q = x + ne;
+    BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Z, h, b.e, 1, ne, nullptr, s));
+    BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Y, b.e, b.j, 1, ne, h, s));
+    BEM_CUDA(cudaMemsetAsync(b.sigma, 0, 4 * ng * sizeof(V), s));
+    k_scatter_e<R><<<nb((int64_t)ne * 27, 256), 256, 0, s>>>(b.WA, c->d_nodeE, b.j, b.sigma, ne, nx, ny, ng);
+    k_scatter_t<R><<<nb((int64_t)nt * 27, 256), 256, 0, s>>>(b.WP, c->d_nodeT, q, b.sigma + 3 * ng, nt, nx, ny);
+    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 4, s));
+    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, b.sigma + 3 * ng, c->d_rowP, c->d_colP,
+                                          b.LP, q, b.fdT, c->d_tedge, b.j, nt, ne, nx, ny, k0, 1,
+                                          b.p, y);
+    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
+                                          b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p, ne, nx,
+                                          ny, k0, 1, y);
+  } else {
+    set_error("aim_matvec: unknown operator %d", which);
+    return BEM_EINVAL;
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int matvec<float>(aim_ctx*, int, const void*, void*, cudaStream_t);
+template int matvec<double>(aim_ctx*, int, const void*, void*, cudaStream_t);
+
+template <typename R>
+int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStream_t s) {
+  typedef typename C2<R>::T V;
+  PrecBuf<R>& b = buf<R>(c);
+  BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
+  if (heqv) BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Y, (const V*)ev, (V*)heqv, nrhs, c->ne, nullptr, s));
+  return BEM_OK;
+}
+template int internal<float>(aim_ctx*, const void*, void*, void*, int, cudaStream_t);
+template int internal<double>(aim_ctx*, const void*, void*, void*, int, cudaStream_t);
+
+template <typename R>
+int conv(aim_ctx* c, const void* sigma, void* phi, int ncomp, cudaStream_t s) {
+  typedef typename C2<R>::T V;
+  PrecBuf<R>& b = buf<R>(c);
+  return fft_conv<R>(c, b, (const V*)sigma, (V*)phi, ncomp, s);
+}
+template int conv<float>(aim_ctx*, const void*, void*, int, cudaStream_t);
+template int conv<double>(aim_ctx*, const void*, void*, int, cudaStream_t);
+
+}  // namespace bem

@@ -1,0 +1,700 @@
+// Device set-up (FP64): projection stencils, the dense internal matrices Z_i and Y_i,eq, and
+// the precorrected near-region matrices L^A_NR and L^Phi_NR.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+
+#include "common.cuh"
+#include "quad.cuh"
+
+namespace bem {
+
+void build_ix_fd(const aim_ctx* c, std::vector<int32_t>* ixcol, std::vector<double>* ixval,
+                 std::vector<double>* fdE, std::vector<double>* fdT);
+
+// ---------------------------------------------------------------------------------------
+// rules (host)
+// ---------------------------------------------------------------------------------------
+static void radon7_host(double* out) {  // (l1, l2, l3, w) x 7, weights sum to one
+  const double s = std::sqrt(15.0);
+  const double a1 = (6.0 - s) / 21.0, a2 = (6.0 + s) / 21.0;
+  const double w1 = (155.0 - s) / 1200.0, w2 = (155.0 + s) / 1200.0;
+  const double pts[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40.0},
+                            {a1, a1, 1 - 2 * a1, w1}, {a1, 1 - 2 * a1, a1, w1}, {1 - 2 * a1, a1, a1, w1},
+                            {a2, a2, 1 - 2 * a2, w2}, {a2, 1 - 2 * a2, a2, w2}, {1 - 2 * a2, a2, a2, w2}};
+  for (int i = 0; i < 7; ++i)
+    for (int k = 0; k < 4; ++k) out[4 * i + k] = pts[i][k];
+}
+
+static void subdivide4_host(const double* in, int nq, double* out) {
+  const double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double m01[3], m12[3], m20[3];
+  for (int a = 0; a < 3; ++a) {
+    m01[a] = 0.5 * (V[0][a] + V[1][a]);
+    m12[a] = 0.5 * (V[1][a] + V[2][a]);
+    m20[a] = 0.5 * (V[2][a] + V[0][a]);
+  }
+  const double* subs[4][3] = {{V[0], m01, m20}, {m01, V[1], m12}, {m20, m12, V[2]}, {m01, m12, m20}};
+  int o = 0;
+  for (int s = 0; s < 4; ++s)
+    for (int q = 0; q < nq; ++q, ++o) {
+      for (int a = 0; a < 3; ++a)
+        out[4 * o + a] = in[4 * q] * subs[s][0][a] + in[4 * q + 1] * subs[s][1][a] + in[4 * q + 2] * subs[s][2][a];
+      out[4 * o + 3] = in[4 * q + 3] / 4.0;
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+static void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// collapsed (Duffy) product rule with 5 x 5 points: l1 = u, l2 = v (1 - u), weight 2 wu wv (1 - u)
+static void gauss_tri5_host(double* out) {
+  double x[5], w[5];
+  gauss_legendre(5, x, w);
+  int o = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j, ++o) {
+      double u = 0.5 * (x[i] + 1.0), v = 0.5 * (x[j] + 1.0);
+      double wu = 0.5 * w[i], wv = 0.5 * w[j];
+      out[4 * o] = u;
+      out[4 * o + 1] = v * (1.0 - u);
+      out[4 * o + 2] = 1.0 - out[4 * o] - out[4 * o + 1];
+      out[4 * o + 3] = 2.0 * wu * wv * (1.0 - u);
+    }
+}
+
+static int upload_rules() {
+  double r7[28], r28[112], gl[100];
+  radon7_host(r7);
+  subdivide4_host(r7, 7, r28);
+  gauss_tri5_host(gl);
+  BEM_CUDA(cudaMemcpyToSymbol(c_r7, r7, sizeof(r7)));
+  BEM_CUDA(cudaMemcpyToSymbol(c_r28, r28, sizeof(r28)));
+  BEM_CUDA(cudaMemcpyToSymbol(c_gl, gl, sizeof(gl)));
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// device geometry (FP64)
+// ---------------------------------------------------------------------------------------
+struct DGeo {
+  const double* verts;
+  const int32_t* tris;
+  const double* nrm;
+  const double* area;
+  const double* diam;
+  const double* cen;
+  const int32_t* et;    // [ne][2]
+  const int32_t* eopp;  // [ne][2]
+  const double* elen;
+  const int32_t* anc;   // [(ne+nt)][3]
+  double go[3], gh[3];
+};
+
+__device__ __forceinline__ void lag3(double u, double* l) {
+  l[0] = 0.5 * u * (u - 1.0);
+  l[1] = 1.0 - u * u;
+  l[2] = 0.5 * u * (u + 1.0);
+}
+
+// P[m][c][k] = int f_m,c(r) l_k(r) dS  (Lagrange polynomial of stencil node k of m's anchor);
+// one thread per (RWG, node), exact 25-point rule.
+__global__ void k_weights_e(DGeo g, int ne, double* W64, float* W32) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ne * 27) return;
+  int m = (int)(idx / 27), k = (int)(idx % 27);
+  int kx = k % 3, ky = (k / 3) % 3, kz = k / 9;
+  double org[3];
+  for (int a = 0; a < 3; ++a) org[a] = g.go[a] + g.anc[3 * m + a] * g.gh[a];
+  double acc[3] = {0, 0, 0};
+  for (int side = 0; side < 2; ++side) {
+    int t = g.et[2 * m + side];
+    const double* v = &g.verts[3 * g.eopp[2 * m + side]];
+    double cf = (side == 0 ? 1.0 : -1.0) * g.elen[m] / (2.0 * g.area[t]);
+    double X[3][3];
+    for (int q = 0; q < 3; ++q)
+      for (int a = 0; a < 3; ++a) X[q][a] = g.verts[3 * g.tris[3 * t + q] + a];
+    for (int q = 0; q < 25; ++q) {
+      double r[3];
+      for (int a = 0; a < 3; ++a) r[a] = c_gl[4 * q] * X[0][a] + c_gl[4 * q + 1] * X[1][a] + c_gl[4 * q + 2] * X[2][a];
+      double lx[3], ly[3], lz[3];
+      lag3((r[0] - org[0]) / g.gh[0], lx);
+      lag3((r[1] - org[1]) / g.gh[1], ly);
+      lag3((r[2] - org[2]) / g.gh[2], lz);
+      double wl = c_gl[4 * q + 3] * g.area[t] * lx[kx] * ly[ky] * lz[kz] * cf;
+      for (int a = 0; a < 3; ++a) acc[a] += wl * (r[a] - v[a]);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    W64[(int64_t)m * 81 + a * 27 + k] = acc[a];
+    W32[(int64_t)m * 81 + a * 27 + k] = (float)acc[a];
+  }
+}
+
+// P_Phi[t][k] = int_t l_k(r) dS
+__global__ void k_weights_t(DGeo g, int ne, int nt, double* W64, float* W32) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nt * 27) return;
+  int t = (int)(idx / 27), k = (int)(idx % 27);
+  int kx = k % 3, ky = (k / 3) % 3, kz = k / 9;
+  double org[3];
+  for (int a = 0; a < 3; ++a) org[a] = g.go[a] + g.anc[3 * (ne + t) + a] * g.gh[a];
+  double X[3][3];
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) X[q][a] = g.verts[3 * g.tris[3 * t + q] + a];
+  double acc = 0;
+  for (int q = 0; q < 25; ++q) {
+    double r[3];
+    for (int a = 0; a < 3; ++a) r[a] = c_gl[4 * q] * X[0][a] + c_gl[4 * q + 1] * X[1][a] + c_gl[4 * q + 2] * X[2][a];
+    double lx[3], ly[3], lz[3];
+    lag3((r[0] - org[0]) / g.gh[0], lx);
+    lag3((r[1] - org[1]) / g.gh[1], ly);
+    lag3((r[2] - org[2]) / g.gh[2], lz);
+    acc += c_gl[4 * q + 3] * g.area[t] * lx[kx] * ly[ky] * lz[kz];
+  }
+  W64[(int64_t)t * 27 + k] = acc;
+  W32[(int64_t)t * 27 + k] = (float)acc;
+}
+
+// ---------------------------------------------------------------------------------------
+// RWG entries from triangle-pair moments
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void half_rwg(const DGeo& g, int n, int t, double* sgn, const double** v) {
+  if (g.et[2 * n] == t) { *sgn = 1.0; *v = &g.verts[3 * g.eopp[2 * n]]; }
+  else { *sgn = -1.0; *v = &g.verts[3 * g.eopp[2 * n + 1]]; }
+}
+
+// kind 0: int int f.f G ; kind 1: L (with -k^-2 div div) ; returns K too when wantK
+__device__ void rwg_pair(const DGeo& g, int m, int n, double kr, double ki, bool isL, bool wantK,
+                         double2* Lval, double2* Kval) {
+  double2 L = {0, 0}, K = {0, 0};
+  // 1/k^2 for the divergence term
+  double den = kr * kr + ki * ki;
+  double2 ik2 = make_double2((kr * kr - ki * ki) / (den * den), -2.0 * kr * ki / (den * den));
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      int t = g.et[2 * m + a], s = g.et[2 * n + b];
+      Tri T, S;
+      load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t, &T);
+      load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, s, &S);
+      Moments M;
+      pair_moments(T, S, kr, ki, true, wantK, false, &M);
+      double sm, sn;
+      const double *va, *vb;
+      half_rwg(g, m, t, &sm, &va);
+      half_rwg(g, n, s, &sn, &vb);
+      double cf = sm * sn * g.elen[m] * g.elen[n] / (4.0 * g.area[t] * g.area[s]);
+      double2 v = M.M2;
+      for (int q = 0; q < 3; ++q) {
+        v.x += -M.M1[q].x * vb[q] - va[q] * M.M1p[q].x;
+        v.y += -M.M1[q].y * vb[q] - va[q] * M.M1p[q].y;
+      }
+      double vv = d_dot(va, vb);
+      v.x += vv * M.M0.x;
+      v.y += vv * M.M0.y;
+      L.x += cf * v.x;
+      L.y += cf * v.y;
+      if (isL) {
+        double dv = sm * sn * g.elen[m] * g.elen[n] / (g.area[t] * g.area[s]);
+        double2 t2 = cmul(M.M0, ik2);
+        L.x -= dv * t2.x;
+        L.y -= dv * t2.y;
+      }
+      if (wantK) {
+        double bxa[3];
+        d_cross(vb, va, bxa);
+        double2 kv = {0, 0};
+        for (int q = 0; q < 3; ++q) {
+          kv.x += M.U[q].x * (vb[q] - va[q]) + M.Vs[q].x * bxa[q];
+          kv.y += M.U[q].y * (vb[q] - va[q]) + M.Vs[q].y * bxa[q];
+        }
+        K.x += cf * kv.x;
+        K.y += cf * kv.y;
+      }
+    }
+  *Lval = L;
+  if (Kval) *Kval = K;
+}
+
+// Dense internal matrices of one object (column-major, n x n): Lc = L_k, Bc = K_k + I_x/2.
+__global__ void k_obj_LK(DGeo g, int e0, int n, double kr, double ki, const int32_t* ixcol,
+                         const double* ixval, double2* Lc, double2* Bc) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  int i = (int)(idx % n), j = (int)(idx / n);  // column-major: consecutive threads walk a column
+  int m = e0 + i, nn = e0 + j;
+  double2 L, K;
+  rwg_pair(g, m, nn, kr, ki, true, true, &L, &K);
+  for (int q = 0; q < 4; ++q)
+    if (ixcol[4 * m + q] == nn) K.x += 0.5 * ixval[4 * m + q];
+  Lc[idx] = L;
+  Bc[idx] = K;
+}
+
+// Store alpha * X (column-major) into the packed row-major block (FP64 and FP32 copies).
+__global__ void k_store_block(const double2* X, int n, int ld, double2 alpha, double2* Z64,
+                              float2* Z32) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * ld) return;
+  int r = (int)(idx / ld), col = (int)(idx % ld);
+  double2 v = make_double2(0, 0);
+  if (col < n) v = cmul(alpha, X[r + (int64_t)col * n]);
+  Z64[idx] = v;
+  Z32[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+// Near region of L^A: exact entry minus the grid's own contribution
+//   sum_c sum_{a,b} P_c[m,a] G_grid(anc_m + o_a - anc_n - o_b) P_c[n,b].
+// gtab holds G_grid at offsets (dx, dy, dz) in [-(R+2), R+2]^3.
+__global__ void k_near_LA(DGeo g, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                          const double* WA, const double2* gtab, int R, double k0, double2* v64,
+                          float2* v32) {
+  extern __shared__ double2 sg[];
+  const int span = 2 * R + 5;
+  for (int i = threadIdx.x; i < span * span * span; i += blockDim.x) sg[i] = gtab[i];
+  __syncthreads();
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nnz) return;
+  int m = rows[idx], n = cols[idx];
+  double2 L;
+  rwg_pair(g, m, n, k0, 0.0, false, false, &L, nullptr);
+  int D[3];
+  for (int a = 0; a < 3; ++a) D[a] = g.anc[3 * m + a] - g.anc[3 * n + a];
+  double2 pre = {0, 0};
+  const int h = R + 2;
+  for (int ka = 0; ka < 27; ++ka) {
+    int ax = ka % 3 - 1, ay = (ka / 3) % 3 - 1, az = ka / 9 - 1;
+    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int kb = 0; kb < 27; ++kb) {
+      int bx = kb % 3 - 1, by = (kb / 3) % 3 - 1, bz = kb / 9 - 1;
+      int dx = D[0] + ax - bx + h, dy = D[1] + ay - by + h, dz = D[2] + az - bz + h;
+      double2 G = sg[(dz * span + dy) * span + dx];
+      for (int c = 0; c < 3; ++c) {
+        double w = WA[(int64_t)n * 81 + c * 27 + kb];
+        acc[c].x += G.x * w;
+        acc[c].y += G.y * w;
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      double w = WA[(int64_t)m * 81 + c * 27 + ka];
+      pre.x += w * acc[c].x;
+      pre.y += w * acc[c].y;
+    }
+  }
+  double2 v = make_double2(L.x - pre.x, L.y - pre.y);
+  v64[idx] = v;
+  v32[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void k_near_LP(DGeo g, int ne, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                          const double* WP, const double2* gtab, int R, double k0, double2* v64,
+                          float2* v32) {
+  extern __shared__ double2 sg[];
+  const int span = 2 * R + 5;
+  for (int i = threadIdx.x; i < span * span * span; i += blockDim.x) sg[i] = gtab[i];
+  __syncthreads();
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nnz) return;
+  int t = rows[idx], s = cols[idx];
+  Tri T, S;
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t, &T);
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, s, &S);
+  Moments M;
+  pair_moments(T, S, k0, 0.0, false, false, true, &M);
+  int D[3];
+  for (int a = 0; a < 3; ++a) D[a] = g.anc[3 * (ne + t) + a] - g.anc[3 * (ne + s) + a];
+  double2 pre = {0, 0};
+  const int h = R + 2;
+  for (int ka = 0; ka < 27; ++ka) {
+    int ax = ka % 3 - 1, ay = (ka / 3) % 3 - 1, az = ka / 9 - 1;
+    double2 acc = {0, 0};
+    for (int kb = 0; kb < 27; ++kb) {
+      int bx = kb % 3 - 1, by = (kb / 3) % 3 - 1, bz = kb / 9 - 1;
+      int dx = D[0] + ax - bx + h, dy = D[1] + ay - by + h, dz = D[2] + az - bz + h;
+      double2 G = sg[(dz * span + dy) * span + dx];
+      double w = WP[(int64_t)s * 27 + kb];
+      acc.x += G.x * w;
+      acc.y += G.y * w;
+    }
+    double w = WP[(int64_t)t * 27 + ka];
+    pre.x += w * acc.x;
+    pre.y += w * acc.y;
+  }
+  double2 v = make_double2(M.M0.x - pre.x, M.M0.y - pre.y);
+  v64[idx] = v;
+  v32[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+// ---------------------------------------------------------------------------------------
+// plane-wave right-hand side: b_m = <f_m, pol exp(-j k0 khat.r)> / eta0 (7-point rule)
+// ---------------------------------------------------------------------------------------
+template <typename V>
+__global__ void k_rhs_pw(DGeo g, int ne, int nt, double k0, double px, double py, double pz,
+                         double kx, double ky, double kz, double inv_eta0, V* b) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= ne + nt) return;
+  if (m >= ne) { b[m] = czero<V>(); return; }
+  double2 acc = {0, 0};
+  const double pol[3] = {px, py, pz}, kh[3] = {kx, ky, kz};
+  for (int side = 0; side < 2; ++side) {
+    int t = g.et[2 * m + side];
+    Tri T;
+    load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t, &T);
+    const double* v = &g.verts[3 * g.eopp[2 * m + side]];
+    double cf = (side == 0 ? 1.0 : -1.0) * g.elen[m] / (2.0 * g.area[t]) * g.area[t];
+    for (int q = 0; q < 7; ++q) {
+      double r[3];
+      rule_point(T, c_r7, q, r);
+      double fp = 0;
+      for (int a = 0; a < 3; ++a) fp += (r[a] - v[a]) * pol[a];
+      double s, co;
+      sincos(k0 * d_dot(kh, r), &s, &co);
+      double w = c_r7[4 * q + 3] * cf * fp * inv_eta0;
+      acc.x += w * co;
+      acc.y -= w * s;
+    }
+  }
+  b[m] = mk((decltype(b[m].x))acc.x, (decltype(b[m].x))acc.y);
+}
+
+// ---------------------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------------------
+struct DevGeoStore {
+  double *verts, *nrm, *area, *diam, *cen, *elen;
+  int32_t *tris, *et, *eopp, *anc;
+};
+
+static DGeo make_dgeo(aim_ctx* c, const DevGeoStore& s) {
+  DGeo g;
+  g.verts = s.verts; g.tris = s.tris; g.nrm = s.nrm; g.area = s.area; g.diam = s.diam;
+  g.cen = s.cen; g.et = s.et; g.eopp = s.eopp; g.elen = s.elen; g.anc = s.anc;
+  for (int a = 0; a < 3; ++a) { g.go[a] = c->go[a]; g.gh[a] = c->gh[a]; }
+  return g;
+}
+
+static int geo_upload(aim_ctx* c, DevGeoStore* s) {
+  BEM_TRY(upload(c, &s->verts, c->verts.data(), c->verts.size()));
+  BEM_TRY(upload(c, &s->nrm, c->normal.data(), c->normal.size()));
+  BEM_TRY(upload(c, &s->area, c->area.data(), c->area.size()));
+  BEM_TRY(upload(c, &s->diam, c->diam.data(), c->diam.size()));
+  BEM_TRY(upload(c, &s->cen, c->centroid.data(), c->centroid.size()));
+  BEM_TRY(upload(c, &s->elen, c->elen.data(), c->elen.size()));
+  BEM_TRY(upload(c, &s->tris, c->tris.data(), c->tris.size()));
+  BEM_TRY(upload(c, &s->et, c->et.data(), c->et.size()));
+  BEM_TRY(upload(c, &s->eopp, c->eopp.data(), c->eopp.size()));
+  BEM_TRY(upload(c, &s->anc, c->anc.data(), c->anc.size()));
+  return BEM_OK;
+}
+
+static const double kC0 = 299792458.0;
+static const double kMu0 = 4e-7 * 3.14159265358979323846;
+static const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+static const double kEll = 1e-6;
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct SolverScratch {
+  cusolverDnHandle_t h = nullptr;
+  cusolverDnParams_t p = nullptr;
+  ~SolverScratch() {
+    if (p) cusolverDnDestroyParams(p);
+    if (h) cusolverDnDestroy(h);
+  }
+};
+
+// X <- L^{-1} B for column-major n x n matrices (in place in B), LU with partial pivoting.
+static int lu_solve(SolverScratch& ss, double2* L, double2* B, int n, int64_t* ipiv, int* dinfo,
+                    void** dwork, size_t* dwsize, std::vector<char>* hwork) {
+  size_t dws = 0, hws = 0;
+  if (cusolverDnXgetrf_bufferSize(ss.h, ss.p, n, n, CUDA_C_64F, L, n, CUDA_C_64F, &dws, &hws) !=
+      CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnXgetrf_bufferSize failed");
+    return BEM_ECUDA;
+  }
+  if (dws > *dwsize) {
+    if (*dwork) cudaFree(*dwork);
+    *dwork = nullptr;
+    BEM_CUDA(cudaMalloc(dwork, dws));
+    *dwsize = dws;
+  }
+  if (hws > hwork->size()) hwork->resize(hws);
+  if (cusolverDnXgetrf(ss.h, ss.p, n, n, CUDA_C_64F, L, n, ipiv, CUDA_C_64F, *dwork, dws,
+                       hwork->data(), hws, dinfo) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnXgetrf failed");
+    return BEM_ECUDA;
+  }
+  int hinfo = 0;
+  BEM_CUDA(cudaMemcpy(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hinfo != 0) {
+    set_error("singular internal matrix (getrf info %d)", hinfo);
+    return BEM_ESOLVER;
+  }
+  if (cusolverDnXgetrs(ss.h, ss.p, CUBLAS_OP_N, n, n, CUDA_C_64F, L, n, ipiv, CUDA_C_64F, B, n,
+                       dinfo) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnXgetrs failed");
+    return BEM_ECUDA;
+  }
+  return BEM_OK;
+}
+
+static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, const double* d_ixval) {
+  const int nobj = c->nobj;
+  c->zoff.assign(nobj, 0);
+  c->zld.assign(nobj, 0);
+  int64_t off = 0;
+  int nmax = 0;
+  for (int i = 0; i < nobj; ++i) {
+    int n = c->e1[i] - c->e0[i];
+    c->zld[i] = (int32_t)round_up(n, 4);
+    c->zoff[i] = off;
+    off += (int64_t)n * c->zld[i];
+    nmax = std::max(nmax, n);
+  }
+  c->zelems = off;
+  BEM_TRY(dalloc_t(c, &c->f64.Z, off));
+  BEM_TRY(dalloc_t(c, &c->f64.Y, off));
+  BEM_TRY(dalloc_t(c, &c->f32.Z, off));
+  BEM_TRY(dalloc_t(c, &c->f32.Y, off));
+  double2 *L = nullptr, *B = nullptr;
+  int64_t* ipiv = nullptr;
+  int* dinfo = nullptr;
+  size_t nn = (size_t)nmax * nmax;
+  BEM_CUDA(cudaMalloc(&L, nn * sizeof(double2)));
+  BEM_CUDA(cudaMalloc(&B, nn * sizeof(double2)));
+  BEM_CUDA(cudaMalloc(&ipiv, nmax * sizeof(int64_t)));
+  BEM_CUDA(cudaMalloc(&dinfo, sizeof(int)));
+  SolverScratch ss;
+  void* dwork = nullptr;
+  size_t dwsize = 0;
+  std::vector<char> hwork;
+  int rc = BEM_OK;
+  if (cusolverDnCreate(&ss.h) != CUSOLVER_STATUS_SUCCESS || cusolverDnCreateParams(&ss.p) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnCreate failed");
+    rc = BEM_ECUDA;
+  }
+  const double w = 2.0 * kPi * c->freq;
+  for (int i = 0; i < nobj && rc == BEM_OK; ++i) {
+    const int n = c->e1[i] - c->e0[i];
+    const bem_material& mt = c->mat[i];
+    // conductor: eps_rc = eps_r - j sigma/(w eps0); k_i = k0 sqrt(eps_rc mu_r), Im k_i <= 0
+    std::complex<double> epsc(mt.eps_r, -mt.sigma / (w * kEps0));
+    std::complex<double> ki = c->k0 * std::sqrt(epsc * mt.mu_r);
+    if (ki.imag() > 0) ki = -ki;
+    for (int pass = 0; pass < 2 && rc == BEM_OK; ++pass) {
+      // pass 0: Z = -(1/(j k0 eps_rc)) L_{k_i}^{-1}(K_{k_i} + I_x/2)
+      // pass 1: Y = (1/(j k0 mu_rl)) L_{k0}^{-1}(K_{k0} + I_x/2), background vacuum
+      std::complex<double> k = pass == 0 ? ki : std::complex<double>(c->k0, 0.0);
+      k_obj_LK<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[i], n, k.real(), k.imag(), d_ixcol,
+                                                   d_ixval, L, B);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_error("k_obj_LK: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; break; }
+      rc = lu_solve(ss, L, B, n, ipiv, dinfo, &dwork, &dwsize, &hwork);
+      if (rc != BEM_OK) break;
+      std::complex<double> jk0(0.0, c->k0);
+      std::complex<double> alpha = pass == 0 ? -1.0 / (jk0 * epsc) : 1.0 / jk0;
+      double2 al = make_double2(alpha.real(), alpha.imag());
+      k_store_block<<<nblk((int64_t)n * c->zld[i], 256), 256>>>(
+          B, n, c->zld[i], al, (pass == 0 ? c->f64.Z : c->f64.Y) + c->zoff[i],
+          (pass == 0 ? c->f32.Z : c->f32.Y) + c->zoff[i]);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) { set_error("k_store_block: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; }
+    }
+  }
+  cudaDeviceSynchronize();
+  cudaFree(L);
+  cudaFree(B);
+  cudaFree(ipiv);
+  cudaFree(dinfo);
+  if (dwork) cudaFree(dwork);
+  return rc;
+}
+
+static int setup_near(aim_ctx* c, const DGeo& g) {
+  const int R = c->r_near;
+  const int span = 2 * R + 5;
+  std::vector<double2> gt((size_t)span * span * span);
+  for (int dz = -R - 2; dz <= R + 2; ++dz)
+    for (int dy = -R - 2; dy <= R + 2; ++dy)
+      for (int dx = -R - 2; dx <= R + 2; ++dx) {
+        double x = dx * c->gh[0], y = dy * c->gh[1], z = dz * c->gh[2];
+        double Rr = std::sqrt(x * x + y * y + z * z);
+        double2 v = make_double2(0, 0);
+        if (Rr > 0) {
+          double s = std::sin(c->k0 * Rr), co = std::cos(c->k0 * Rr);
+          v = make_double2(co / (4 * kPi * Rr), -s / (4 * kPi * Rr));
+        }
+        gt[((dz + R + 2) * span + (dy + R + 2)) * span + (dx + R + 2)] = v;
+      }
+  double2* d_gt = nullptr;
+  BEM_TRY(upload(c, &d_gt, gt.data(), gt.size()));
+  const size_t smem = gt.size() * sizeof(double2);
+  // L^A_NR
+  {
+    int64_t nnz = c->rowA.back();
+    std::vector<int32_t> rows(nnz);
+    for (int m = 0; m < c->ne; ++m)
+      for (int64_t i = c->rowA[m]; i < c->rowA[m + 1]; ++i) rows[i] = m;
+    int32_t* d_rows = nullptr;
+    BEM_TRY(upload(c, &d_rows, rows.data(), rows.size()));
+    BEM_TRY(upload(c, &c->d_rowA, c->rowA.data(), c->rowA.size()));
+    BEM_TRY(upload(c, &c->d_colA, c->colA.data(), c->colA.size()));
+    BEM_TRY(dalloc_t(c, &c->f64.LA, nnz));
+    BEM_TRY(dalloc_t(c, &c->f32.LA, nnz));
+    if (nnz)
+      k_near_LA<<<nblk(nnz, 128), 128, smem>>>(g, nnz, d_rows, c->d_colA, c->f64.WA, d_gt, R, c->k0,
+                                               c->f64.LA, c->f32.LA);
+    BEM_CUDA(cudaGetLastError());
+  }
+  // L^Phi_NR
+  {
+    int64_t nnz = c->rowP.back();
+    std::vector<int32_t> rows(nnz);
+    for (int t = 0; t < c->nt; ++t)
+      for (int64_t i = c->rowP[t]; i < c->rowP[t + 1]; ++i) rows[i] = t;
+    int32_t* d_rows = nullptr;
+    BEM_TRY(upload(c, &d_rows, rows.data(), rows.size()));
+    BEM_TRY(upload(c, &c->d_rowP, c->rowP.data(), c->rowP.size()));
+    BEM_TRY(upload(c, &c->d_colP, c->colP.data(), c->colP.size()));
+    BEM_TRY(dalloc_t(c, &c->f64.LP, nnz));
+    BEM_TRY(dalloc_t(c, &c->f32.LP, nnz));
+    if (nnz)
+      k_near_LP<<<nblk(nnz, 128), 128, smem>>>(g, c->ne, nnz, d_rows, c->d_colP, c->f64.WP, d_gt, R,
+                                               c->k0, c->f64.LP, c->f32.LP);
+    BEM_CUDA(cudaGetLastError());
+  }
+  BEM_CUDA(cudaDeviceSynchronize());
+  return BEM_OK;
+}
+
+int setup_device(aim_ctx* c) {
+  BEM_TRY(upload_rules());
+  DevGeoStore s;
+  BEM_TRY(geo_upload(c, &s));
+  DGeo g = make_dgeo(c, s);
+  // projection stencils
+  BEM_TRY(dalloc_t(c, &c->f64.WA, (size_t)c->ne * 81));
+  BEM_TRY(dalloc_t(c, &c->f32.WA, (size_t)c->ne * 81));
+  BEM_TRY(dalloc_t(c, &c->f64.WP, (size_t)c->nt * 27));
+  BEM_TRY(dalloc_t(c, &c->f32.WP, (size_t)c->nt * 27));
+  k_weights_e<<<nblk((int64_t)c->ne * 27, 256), 256>>>(g, c->ne, c->f64.WA, c->f32.WA);
+  k_weights_t<<<nblk((int64_t)c->nt * 27, 256), 256>>>(g, c->ne, c->nt, c->f64.WP, c->f32.WP);
+  BEM_CUDA(cudaGetLastError());
+  // anchor node indices
+  {
+    std::vector<int32_t> nodeE(c->ne), nodeT(c->nt);
+    for (int i = 0; i < c->ne + c->nt; ++i) {
+      const int32_t* a = &c->anc[3 * (size_t)i];
+      int32_t v = (int32_t)(((int64_t)a[2] * c->gn[1] + a[1]) * c->gn[0] + a[0]);
+      if (i < c->ne) nodeE[i] = v; else nodeT[i - c->ne] = v;
+    }
+    BEM_TRY(upload(c, &c->d_nodeE, nodeE.data(), nodeE.size()));
+    BEM_TRY(upload(c, &c->d_nodeT, nodeT.data(), nodeT.size()));
+  }
+  // sparse tables
+  std::vector<int32_t> ixcol;
+  std::vector<double> ixval, fdE, fdT;
+  build_ix_fd(c, &ixcol, &ixval, &fdE, &fdT);
+  BEM_TRY(upload(c, &c->d_ixcol, ixcol.data(), ixcol.size()));
+  BEM_TRY(upload(c, &c->f64.ix, ixval.data(), ixval.size()));
+  BEM_TRY(upload(c, &c->f64.fdE, fdE.data(), fdE.size()));
+  BEM_TRY(upload(c, &c->f64.fdT, fdT.data(), fdT.size()));
+  {
+    std::vector<float> a(ixval.begin(), ixval.end()), b(fdE.begin(), fdE.end()), d(fdT.begin(), fdT.end());
+    BEM_TRY(upload(c, &c->f32.ix, a.data(), a.size()));
+    BEM_TRY(upload(c, &c->f32.fdE, b.data(), b.size()));
+    BEM_TRY(upload(c, &c->f32.fdT, d.data(), d.size()));
+  }
+  BEM_TRY(upload(c, &c->d_et, c->et.data(), c->et.size()));
+  BEM_TRY(upload(c, &c->d_tedge, c->t_edges.data(), c->t_edges.size()));
+  // internal problem
+  BEM_TRY(setup_internal(c, g, c->d_ixcol, c->f64.ix));
+  // near region
+  BEM_TRY(setup_near(c, g));
+  // grid Green's function
+  BEM_TRY(make_twiddles<float>(c, c->f32));
+  BEM_TRY(make_twiddles<double>(c, c->f64));
+  BEM_TRY(make_ghat(c));
+  // GEMV work list
+  {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<int32_t> n(c->nobj), xo(c->nobj);
+    for (int i = 0; i < c->nobj; ++i) { n[i] = c->e1[i] - c->e0[i]; xo[i] = c->e0[i]; }
+    build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, &c->tasks);
+    c->ntasks = (int)c->tasks.size();
+    BEM_TRY(upload(c, &c->d_tasks, c->tasks.data(), c->tasks.size()));
+  }
+  // workspaces
+  const size_t P = (size_t)c->gp[0] * c->gp[1] * c->gp[2];
+  BEM_TRY(dalloc_t(c, &c->f32.sigma, 4 * (size_t)c->ng));
+  BEM_TRY(dalloc_t(c, &c->f64.sigma, 4 * (size_t)c->ng));
+  BEM_TRY(dalloc_t(c, &c->f32.ws, 4 * P));
+  BEM_TRY(dalloc_t(c, &c->f64.ws, 4 * P));
+  const size_t ntot = (size_t)c->ne + c->nt;
+  BEM_TRY(dalloc_t(c, &c->f32.e, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f64.e, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f32.heq, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f64.heq, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f32.j, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f64.j, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f32.p, c->nt));
+  BEM_TRY(dalloc_t(c, &c->f64.p, c->nt));
+  BEM_TRY(dalloc_t(c, &c->f32.xin, ntot));
+  BEM_TRY(dalloc_t(c, &c->f32.yout, ntot));
+  BEM_CUDA(cudaDeviceSynchronize());
+  c->geo_store = new DGeo(g);
+  return BEM_OK;
+}
+
+int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
+                   cudaStream_t st) {
+  const DGeo& g = *reinterpret_cast<const DGeo*>(c->geo_store);
+  const double inv_eta0 = 1.0 / (kMu0 * kC0);
+  int n = c->ne + c->nt;
+  if (prec == BEM_C64)
+    k_rhs_pw<double2><<<nblk(n, 128), 128, 0, st>>>(g, c->ne, c->nt, c->k0, pol[0], pol[1], pol[2],
+                                                    kh[0], kh[1], kh[2], inv_eta0, (double2*)b);
+  else
+    k_rhs_pw<float2><<<nblk(n, 128), 128, 0, st>>>(g, c->ne, c->nt, c->k0, pol[0], pol[1], pol[2],
+                                                   kh[0], kh[1], kh[2], inv_eta0, (float2*)b);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+void free_geo_store(aim_ctx* c) {
+  delete reinterpret_cast<DGeo*>(c->geo_store);
+  c->geo_store = nullptr;
+}
+
+double k0_of(double f) { return 2.0 * kPi * f / kC0 * kEll; }
+
+}  // namespace bem

@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded
+inputs. Tolerances: complex FP32 results within 1e-5 (relative, 2-norm) of the oracle's FP64
+result on matvecs; FP64 results within 1e-10 where both sides take the same arithmetic
+(stencils, near region, convolution), looser where an LU solve of an ill-conditioned matrix
+amplifies rounding (Z, Y; cond(L_l) ~ (k0 h)^-2 at these frequencies)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import aim as oaim, blockops, gmres as ogmres, operators as op  # noqa: E402
+from oracle.rwg import from_mesh  # noqa: E402
+from paper_2108_03991_gb300 import api, synth  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_03991_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+# ---------------------------------------------------------------------------------------
+# block-diagonal GEMV (internal problem) on random blocks: ragged sizes and several RHS
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-13)])
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_blockdiag_gemv_random(dev, prec, tol, nrhs):
+    sizes = [1, 3, 5, 17, 64, 129, 1000, 7, 2053]
+    blocks = synth.rand_blocks(sizes, 11)
+    N = sum(sizes)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    x = np.stack([synth.rand_cvec(N, 20 + r) for r in range(nrhs)])
+    ref = np.stack([blockops.block_gemv(blocks, offs, x[r]) for r in range(nrhs)])
+    dt = api.cdtype(prec)
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    A = torch.from_numpy(api.pack_blocks(blocks, npdt)).to(dev)
+    xd = torch.from_numpy(x.astype(npdt).ravel()).to(dev)
+    yd = torch.zeros(nrhs * N, dtype=dt, device=dev)
+    api.blockdiag_gemv(sizes, A, xd, yd, nrhs, prec)
+    got = yd.cpu().numpy().reshape(nrhs, N)
+    for r in range(nrhs):
+        assert rel(got[r], ref[r]) < tol
+
+
+# ---------------------------------------------------------------------------------------
+# a small two-object problem, set up on both sides
+# ---------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def prob(dev):
+    mesh = synth.small_bars(2, 2.0)
+    grid = synth.grid_box(mesh, 0.5)
+    freq = 10e9
+    ctx = api.Context(mesh, grid, freq)
+    rw = from_mesh(mesh)
+    k0 = op.k0_of(freq)
+    A = oaim.Aim(rw, grid.origin, grid.h, grid.n, k0).build_near()
+    Zs, Ys = op.internal_blocks(rw, freq, mesh.sigma)
+    S = op.SlimSystem(rw, freq, Zs, Ys, A.LA, A.LPhi)
+    return dict(mesh=mesh, grid=grid, freq=freq, ctx=ctx, rw=rw, aim=A, S=S, k0=k0)
+
+
+def test_integer_tables_bit_exact(prob):
+    ctx, rw, A = prob["ctx"], prob["rw"], prob["aim"]
+    E = ctx.edges()
+    assert np.array_equal(E[:, 0:2], rw.ev) and np.array_equal(E[:, 2:4], rw.et)
+    assert np.array_equal(E[:, 4:6], rw.eopp)
+    anc = ctx.anchors()
+    assert np.array_equal(anc[:rw.ne], A.anc_e) and np.array_equal(anc[rw.ne:], A.anc_t)
+    row, col, _ = ctx.near("A")
+    M, N = A.near_e
+    assert np.array_equal(np.repeat(np.arange(rw.ne), np.diff(row)), M)
+    assert np.array_equal(col, N)
+
+
+def test_projection_weights(prob):
+    WA, WP = prob["ctx"].weights()
+    A = prob["aim"]
+    assert np.max(np.abs(WA - A.WA)) <= 1e-13 * np.max(np.abs(A.WA))
+    assert np.max(np.abs(WP - A.WP)) <= 1e-13 * np.max(np.abs(A.WP))
+
+
+def test_near_region_values(prob):
+    A = prob["aim"]
+    _, _, va = prob["ctx"].near("A")
+    _, _, vp = prob["ctx"].near("P")
+    assert rel(va, A.LNR_A.data) < 1e-11
+    assert rel(vp, A.LNR_P.data) < 1e-11
+
+
+def test_internal_blocks(prob):
+    S, ctx = prob["S"], prob["ctx"]
+    for i in range(ctx.nobj):
+        assert rel(ctx.Z(i), S.Zs[i]) < 1e-9
+        # Y_eq involves L_{k0}^{-1} with cond ~ (k0 h)^-2 ~ 1e8 here
+        assert rel(ctx.Y(i), S.Ys[i]) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 2e-6), (api.BEM_C64, 1e-12)])
+def test_grid_convolution(prob, prec, tol):
+    ctx, A = prob["ctx"], prob["aim"]
+    s = np.stack([synth.rand_cvec(ctx.ng, 40 + c) for c in range(4)])
+    ref = np.stack([A.conv(s[c]) for c in range(4)])
+    dt = api.cdtype(prec)
+    sd = torch.from_numpy(s.ravel()).to(dt).cuda()
+    got = ctx.conv(sd, ncomp=4, prec=prec).cpu().numpy().reshape(4, -1)
+    assert rel(got, ref) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-11)])
+def test_matvec_LA_LPhi(prob, prec, tol):
+    ctx, A, rw = prob["ctx"], prob["aim"], prob["rw"]
+    dt = api.cdtype(prec)
+    j = synth.rand_cvec(rw.ne, 1)
+    q = synth.rand_cvec(rw.nt, 2)
+    ya = ctx.matvec(torch.from_numpy(j).to(dt).cuda(), which=api.AIM_OP_LA, prec=prec).cpu().numpy()
+    yp = ctx.matvec(torch.from_numpy(q).to(dt).cuda(), which=api.AIM_OP_LPHI, prec=prec).cpu().numpy()
+    assert rel(ya, A.LA(j)) < tol
+    assert rel(yp, A.LPhi(q)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-7)])
+def test_system_matvec(prob, prec, tol):
+    """The full SLIM matvec (Eq. AEFIEoutJ). The FP64 bound reflects the Y_eq set-up
+    discrepancy (ill-conditioned L_l), not the matvec arithmetic."""
+    ctx, S = prob["ctx"], prob["S"]
+    x = synth.rand_cvec(ctx.n, 5)
+    y = ctx.matvec(torch.from_numpy(x).to(api.cdtype(prec)).cuda(), prec=prec).cpu().numpy()
+    assert rel(y, S.matvec(x)) < tol
+
+
+def test_system_matvec_c32_vs_gpu_c64(prob):
+    """FP32 arithmetic error alone (same set-up products on both sides)."""
+    ctx = prob["ctx"]
+    x = synth.rand_cvec(ctx.n, 6)
+    y32 = ctx.matvec(torch.from_numpy(x).to(torch.complex64).cuda(), prec=api.BEM_C32).cpu().numpy()
+    y64 = ctx.matvec(torch.from_numpy(x).cuda(), prec=api.BEM_C64).cpu().numpy()
+    assert rel(y32, y64) < 1e-5
+
+
+def test_internal_apply_nrhs(prob):
+    ctx, S = prob["ctx"], prob["S"]
+    h = np.stack([synth.rand_cvec(ctx.ne, 50 + r) for r in range(3)])
+    e, heq = ctx.internal(torch.from_numpy(h.ravel()).cuda(), nrhs=3, prec=api.BEM_C64)
+    e = e.cpu().numpy().reshape(3, -1)
+    heq = heq.cpu().numpy().reshape(3, -1)
+    for r in range(3):
+        eo = blockops.block_gemv(S.Zs, [a for a, _ in S.ranges], h[r])
+        assert rel(e[r], eo) < 1e-9
+        assert rel(heq[r], blockops.block_gemv(S.Ys, [a for a, _ in S.ranges], e[r])) < 1e-6
+
+
+def test_plane_wave_rhs(prob):
+    ctx, rw, k0 = prob["ctx"], prob["rw"], prob["k0"]
+    b = ctx.rhs_plane_wave(prec=api.BEM_C64).cpu().numpy()
+    ref = np.concatenate([op.plane_wave_rhs(rw, k0) / op.ETA0, np.zeros(rw.nt)])
+    assert rel(b, ref) < 1e-13
+
+
+@pytest.mark.parametrize("mode", [api.BEM_C64, api.BEM_C32])
+def test_gmres_solve(prob, mode):
+    """Device GMRES reaches a true FP64 residual of 1e-6 and agrees with the oracle's solution
+    of its own system to 1e-4."""
+    ctx, S = prob["ctx"], prob["S"]
+    b = ctx.rhs_plane_wave(prec=api.BEM_C64)
+    x, info = ctx.solve(b, tol=1e-6, restart=100, max_iter=2000, prec_mode=mode)
+    assert info["status"] == api.BEM_OK and info["resid_true"] <= 1e-6
+    bn = b.cpu().numpy()
+    xo, it, hist = ogmres.gmres(S.matvec, bn, tol=1e-10, restart=300, max_iter=4000)
+    xg = x.cpu().numpy()
+    ne = ctx.ne
+    assert rel(xg[:ne], xo[:ne]) < 1e-4
+
+
+def test_errors_are_reported(dev):
+    mesh = synth.small_bars(1, 2.0)
+    grid = synth.grid_box(mesh, 0.5)
+    grid.origin = grid.origin + 0.75  # stencils fall outside
+    with pytest.raises(api.BemError) as ei:
+        api.Context(mesh, grid, 10e9)
+    assert ei.value.code == -3
+    V, F = synth.box((0, 0, 0), (1, 1, 1), (2, 2, 2))
+    bad = synth.merge([(V, F[:-1])], [5.8e7])
+    with pytest.raises(api.BemError) as ei:
+        api.Context(bad, synth.grid_box(bad, 0.5), 10e9)
+    assert ei.value.code == -2
