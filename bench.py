@@ -151,6 +151,27 @@ def run_reference(args, rank, world):
                                     "d2h_bytes_per_step": 0}}))
 
 
+def ncu_case(args):
+    """Small case for profiler captures: the block-diagonal GEMV alone on random blocks with the
+    workload's block sizes (one of Z or Y_eq: ~200 MB in FP32, larger than L2)."""
+    import numpy as np
+    import torch
+
+    from paper_2108_03991_gb300 import api, build, synth
+    build.build()
+    mesh = synth.bar_array(0)
+    sizes = [int(np.sum(mesh.obj == i)) * 3 // 2 for i in range(mesh.nobj)]
+    N = sum(sizes)
+    A = torch.from_numpy(api.pack_blocks(synth.rand_blocks(sizes, 3), np.complex64)).cuda()
+    x = torch.from_numpy(synth.rand_cvec(N, 4).astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.steps):
+        api.blockdiag_gemv(sizes, A, x, y, 1, api.BEM_C32)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "gemv", "blocks": len(sizes), "rows": N,
+                      "bytes": int(A.numel() * 8)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,9 +180,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ncu-case", default=None, choices=["gemv"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.ncu_case:
+        return ncu_case(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
