@@ -119,6 +119,18 @@ int aim_conv(aim_ctx* ctx, const void* sigma, void* phi, int ncomp, int prec, vo
 int bem_blockdiag_gemv(int nblk, const int32_t* n, const void* A, const void* x, void* y,
                        int nrhs, int prec, void* stream);
 
+/* The same product as bem_blockdiag_gemv for callers that cannot allocate device memory (the
+ * paper has no counterpart). bem_blockdiag_gemv allocates its row-panel work list on every
+ * call; this variant allocates nothing and keeps the list in a fixed 1 MiB device array built
+ * into the library, which every GPU that loads the library holds until exit. It takes the
+ * same arguments and gives the same result. Limit: at most 32768 panels of 16 rows, i.e. the
+ * sum over blocks of ceil(n_i / 16) <= 32768 (up to 524,288 rows); larger inputs return
+ * BEM_EINVAL with a message. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture. All calls share
+ * the one array: calls whose GPU work overlaps (other streams, other threads) race on it. */
+int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const void* x, void* y,
+                               int nrhs, int prec, void* stream);
+
 /* Copy a setup product to HOST memory `out` (capacity cap bytes, at least the size needed):
  *   what 0: Z_i (complex double, row-major n_i x n_i), index = object
  *   what 1: Y_i (same)

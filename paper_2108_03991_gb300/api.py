@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbem_aim.
 
 SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec",
            "internal_apply", "aim_conv", "bem_blockdiag_gemv", "aim_export",
-           "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule"]
+           "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule", "bem_blockdiag_gemv_noalloc"]
 
 
 class BemError(RuntimeError):
@@ -73,6 +73,8 @@ def lib():
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int, C.c_int, vp]
+        L.bem_blockdiag_gemv_noalloc.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int,
+                                                 C.c_int, vp]
         L.aim_export.argtypes = [vp, C.c_int, C.c_int, vp, i64]
         L.aim_export.restype = i64
         L.bem_rhs_plane_wave.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.c_int, vp]
@@ -123,6 +125,16 @@ def blockdiag_gemv(sizes, A, x, y, nrhs=1, prec=BEM_C32):
     dt = cdtype(prec)
     _check(lib().bem_blockdiag_gemv(n.size, n.ctypes.data_as(C.POINTER(C.c_int32)), _ptr(A, dt),
                                     _ptr(x, dt), _ptr(y, dt), int(nrhs), prec, _stream()))
+    return y
+
+
+def blockdiag_gemv_noalloc(sizes, A, x, y, nrhs=1, prec=BEM_C32):
+    """bem_blockdiag_gemv without any device allocation (fixed scratch inside the library)."""
+    n = np.ascontiguousarray(sizes, dtype=np.int32)
+    dt = cdtype(prec)
+    _check(lib().bem_blockdiag_gemv_noalloc(n.size, n.ctypes.data_as(C.POINTER(C.c_int32)),
+                                            _ptr(A, dt), _ptr(x, dt), _ptr(y, dt), int(nrhs),
+                                            prec, _stream()))
     return y
 
 
