@@ -152,13 +152,31 @@ def run_reference(args, rank, world):
 
 
 def ncu_case(args):
-    """Small case for profiler captures: the block-diagonal GEMV alone on random blocks with the
-    workload's block sizes (one of Z or Y_eq: ~200 MB in FP32, larger than L2)."""
+    """Small cases for profiler captures.
+    gemv: the block-diagonal GEMV alone on random blocks with the workload's block sizes (one of
+          Z or Y_eq: ~200 MB in FP32, larger than L2);
+    aim:  the grid convolution (4 components) on the workload's AIM grid, set up on two small
+          boxes at opposite corners of the array's bounding box (same grid, tiny set-up)."""
     import numpy as np
     import torch
 
     from paper_2108_03991_gb300 import api, build, synth
     build.build()
+    if args.ncu_case == "aim":
+        full = synth.bar_array(0)
+        hi = full.verts.max(axis=0)
+        parts = [synth.box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (2, 2, 2)),
+                 synth.box(tuple(hi - 1.0), (1.0, 1.0, 1.0), (2, 2, 2))]
+        mesh = synth.merge(parts, [synth.SIGMA_CU] * 2)
+        ctx = api.Context(mesh, synth.grid_box(full, 0.5), 10e9)
+        s = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.ng, c) for c in range(4)])
+                             .astype(np.complex64)).cuda()
+        phi = torch.empty_like(s)
+        for _ in range(args.steps):
+            ctx.conv(s, phi, ncomp=4, prec=api.BEM_C32)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "aim", "grid": list(ctx.grid_n), "fft": list(ctx.padded)}))
+        return
     mesh = synth.bar_array(0)
     sizes = [int(np.sum(mesh.obj == i)) * 3 // 2 for i in range(mesh.nobj)]
     N = sum(sizes)
@@ -180,7 +198,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ncu-case", default=None, choices=["gemv"])
+    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -280,7 +298,8 @@ def main():
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
         value = world * 1e3 / ms
-        launches_per_step = 11
+        # per system matvec: 2 GEMV, 2 scatter, 2 x 3 FFT passes, 2 row kernels (+2 memsets)
+        launches_per_step = 12
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -156,9 +156,17 @@ typedef struct {
   int32_t restart;     /* Krylov subspace size before restart, 1..512 */
   int32_t max_iter;
   int32_t prec_mode;
-  int32_t precond;     /* 0 = none */
+  int32_t precond;     /* 0 = none, 1 = block-diagonal (bem_precond_apply), on the right */
   double time_limit_s; /* <= 0: none */
 } bem_solve_opts;
+
+/* u = M r with the block-diagonal preconditioner M = blockdiag(A_ii^{-1}): A_ii is the system
+ * of Eq. AEFIEoutJ restricted to object i's unknowns [h_i; q_i] with the object's exact dense
+ * L^A and L^Phi (the paper's own constraint preconditioner, from Qian 2009, is not given in the
+ * paper; this is the fallback). The first call (or the first bem_solve with precond = 1) builds
+ * the inverses: FP64 integrals, cuBLAS products and cuSOLVER LU, stored in FP64 and FP32.
+ * r, u: device vectors of N_E + N_T in the precision prec; they must not alias. */
+int bem_precond_apply(aim_ctx* ctx, const void* r, void* u, int prec, void* stream);
 
 typedef struct {
   int32_t iters;

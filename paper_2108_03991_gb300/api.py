@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbem_aim.
 
 SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec",
            "internal_apply", "aim_conv", "bem_blockdiag_gemv", "aim_export",
-           "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule", "bem_blockdiag_gemv_noalloc"]
+           "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule", "bem_blockdiag_gemv_noalloc",
+           "bem_precond_apply"]
 
 
 class BemError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
         L.aim_export.restype = i64
         L.bem_rhs_plane_wave.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.c_int, vp]
         L.bem_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+        L.bem_precond_apply.argtypes = [vp, vp, vp, C.c_int, vp]
         L.bem_part_schedule.argtypes = [C.c_int, C.POINTER(d), C.c_int, C.c_int, C.POINTER(i32)]
         L.bem_part_schedule.restype = d
         _LIB = L
@@ -231,12 +233,21 @@ class Context:
         _check(lib().bem_rhs_plane_wave(self.h, p, k, _ptr(b), prec, _stream()))
         return b
 
+    def precond(self, r, u=None, prec=BEM_C32):
+        """u = M_bd r, the block-diagonal preconditioner (built on first use)."""
+        import torch
+        if u is None:
+            u = torch.empty_like(r)
+        _check(lib().bem_precond_apply(self.h, _ptr(r, cdtype(prec)), _ptr(u, cdtype(prec)), prec,
+                                       _stream()))
+        return u
+
     def solve(self, b, x=None, tol=1e-6, restart=100, max_iter=1000, prec_mode=BEM_C64,
-              time_limit_s=0.0):
+              time_limit_s=0.0, precond=0):
         import torch
         if x is None:
             x = torch.zeros_like(b)
-        o = SolveOpts(tol, restart, max_iter, prec_mode, 0, time_limit_s)
+        o = SolveOpts(tol, restart, max_iter, prec_mode, int(precond), time_limit_s)
         inf = SolveInfo()
         rc = _check(lib().bem_solve(self.h, _ptr(b, torch.complex128), _ptr(x, torch.complex128),
                                     C.byref(o), C.byref(inf), _stream()))

@@ -81,6 +81,7 @@ void aim_destroy(aim_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  release_streams(c);
   free_geo_store(c);
   delete c;
 }
@@ -108,7 +109,7 @@ int aim_matvec(aim_ctx* c, int which, const void* x, void* y, int prec, void* st
     return BEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  return prec == BEM_C32 ? matvec<float>(c, which, x, y, s) : matvec<double>(c, which, x, y, s);
+  return prec == BEM_C32 ? matvec_graph<float>(c, which, x, y, s) : matvec_graph<double>(c, which, x, y, s);
 }
 
 int internal_apply(aim_ctx* c, const void* h, void* e, void* heq, int nrhs, int prec, void* stream) {
@@ -158,17 +159,33 @@ int bem_blockdiag_gemv(int nblk, const int32_t* n, const void* A, const void* x,
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  std::vector<GemvTask> tasks;
-  build_gemv_tasks(nn, off, xo, ld, nsm, &tasks);
-  GemvTask* d = nullptr;
+  // the same persistent, Part_Schedule-built launch as the context's internal products
+  std::vector<RowInfo> rows;
+  std::vector<int2> segs;
+  std::vector<int32_t> cseg;
+  double ratio = 0;
+  const int ncta = nsm * kGemvCtasPerSm;
+  build_gemv_plan(nn, off, ld, ncta, &rows, &segs, &cseg, &ratio);
+  const size_t b0 = rows.size() * sizeof(RowInfo), b1 = segs.size() * sizeof(int2),
+               b2 = cseg.size() * sizeof(int32_t);
+  const size_t o1 = round_up(b0, 256), o2 = o1 + round_up(b1, 256);
+  char* d = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
-  BEM_CUDA(cudaMallocAsync((void**)&d, tasks.size() * sizeof(GemvTask), s));
-  BEM_CUDA(cudaMemcpyAsync(d, tasks.data(), tasks.size() * sizeof(GemvTask), cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMallocAsync((void**)&d, o2 + b2, s));
+  BEM_CUDA(cudaMemcpyAsync(d, rows.data(), b0, cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(d + o1, segs.data(), b1, cudaMemcpyHostToDevice, s));
+  BEM_CUDA(cudaMemcpyAsync(d + o2, cseg.data(), b2, cudaMemcpyHostToDevice, s));
+  GemvPlan p;
+  p.rows = (RowInfo*)d;
+  p.segs = (int2*)(d + o1);
+  p.cta_seg = (int32_t*)(d + o2);
+  p.ncta = ncta;
+  p.nrows = (int)rows.size();
   int rc = prec == BEM_C32
-               ? run_gemv<float>(d, (int)tasks.size(), (const float2*)A, (const float2*)x, (float2*)y, nrhs, xs, nullptr, s)
-               : run_gemv<double>(d, (int)tasks.size(), (const double2*)A, (const double2*)x, (double2*)y, nrhs, xs, nullptr, s);
+               ? run_gemv_plan<float>(p, (const float2*)A, (const float2*)x, (float2*)y, nrhs, xs, nullptr, s)
+               : run_gemv_plan<double>(p, (const double2*)A, (const double2*)x, (double2*)y, nrhs, xs, nullptr, s);
   cudaFreeAsync(d, s);
-  // the host task vector must outlive the asynchronous copy
+  // the host vectors must outlive the asynchronous copies
   cudaStreamSynchronize(s);
   return rc;
 }
@@ -255,6 +272,18 @@ int bem_rhs_plane_wave(aim_ctx* c, const double* pol, const double* khat, void* 
   return rhs_plane_wave(c, pol, khat, b, prec, (cudaStream_t)stream);
 }
 
+int bem_precond_apply(aim_ctx* c, const void* r, void* u, int prec, void* stream) {
+  BEM_TRY(check_ctx(c, "bem_precond_apply"));
+  BEM_TRY(check_prec(prec, "bem_precond_apply"));
+  if (!r || !u || r == u) {
+    set_error("bem_precond_apply: r and u must be distinct device pointers");
+    return BEM_EINVAL;
+  }
+  BEM_TRY(setup_precond(c));
+  cudaStream_t s = (cudaStream_t)stream;
+  return prec == BEM_C32 ? precond_apply<float>(c, r, u, s) : precond_apply<double>(c, r, u, s);
+}
+
 int bem_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,
               void* stream) {
   BEM_TRY(check_ctx(c, "bem_solve"));
@@ -262,7 +291,8 @@ int bem_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_s
     set_error("bem_solve: bad pointers");
     return BEM_EINVAL;
   }
-  if (!(o->tol > 0) || o->restart < 1 || o->restart > 512 || o->max_iter < 1) {
+  if (!(o->tol > 0) || o->restart < 1 || o->restart > 512 || o->max_iter < 1 || o->precond < 0 ||
+      o->precond > 1) {
     set_error("bem_solve: bad options");
     return BEM_EINVAL;
   }

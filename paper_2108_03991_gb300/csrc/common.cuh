@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -93,6 +94,8 @@ template <typename R> struct PrecBuf {
   V* Y = nullptr;
   R* WA = nullptr;     // [ne][3][27] projection weights of RWG functions
   R* WP = nullptr;     // [nt][27] projection weights of pulses
+  R* WAT = nullptr;    // [nnzPe][3] the same weights in grid-node-major (CSR) order
+  R* WPT = nullptr;    // [nnzPt]
   V* LA = nullptr;     // near-region values (CSR, shared structure with the host arrays)
   V* LP = nullptr;
   V* Ghat = nullptr;   // octant of the scaled FFT of the circulant grid kernel
@@ -119,6 +122,29 @@ struct GemvTask {  // a run of rows of one block
   int32_t row0;
   int32_t nrows;
 };
+
+struct RowInfo {   // one row of the block-diagonal matrix (global row = output index)
+  int64_t aoff;    // element offset of the row's first entry
+  int32_t n;       // row length (block size)
+  int32_t xoff;    // first unknown of the block
+};
+
+// Persistent launch of a block-diagonal product built from a schedule C (Sec. III-C): one CTA
+// per processor p executes the row panels listed in row p of C, segments
+// [seg[cta_seg[p]], ..., seg[cta_seg[p+1]-1]], each a range [r0, r1) of global rows.
+struct GemvPlan {
+  RowInfo* rows = nullptr;   // device [nrows]
+  int2* segs = nullptr;      // device [nseg]
+  int32_t* cta_seg = nullptr;// device [ncta + 1]
+  int ncta = 0;
+  int nrows = 0;
+  double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
+};
+void build_gemv_plan(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
+                     const std::vector<int32_t>& ld, int ncta, std::vector<RowInfo>* rows,
+                     std::vector<int2>* segs, std::vector<int32_t>* cta_seg, double* ratio);
+constexpr int kGemvThreads = 256;
+constexpr int kGemvCtasPerSm = 6;
 
 }  // namespace bem
 
@@ -148,10 +174,16 @@ struct aim_ctx {
   std::vector<int32_t> zld;
   int64_t zelems = 0;
   std::vector<bem::GemvTask> tasks;
+  bem::GemvPlan gplan;
   bem::FftPlan plan[3];
   // device: integer tables
   int32_t* d_nodeE = nullptr;  // [ne] linear index of the anchor node
   int32_t* d_nodeT = nullptr;  // [nt]
+  // projection P as grid-node-major CSR (row = grid node, entries = sources touching it)
+  int32_t* d_prowE = nullptr;  // [ng + 1]
+  int32_t* d_pcolE = nullptr;  // [27 ne] source (RWG) index
+  int32_t* d_prowT = nullptr;  // [ng + 1]
+  int32_t* d_pcolT = nullptr;  // [27 nt] source (triangle) index
   int64_t* d_rowA = nullptr;
   int32_t* d_colA = nullptr;
   int64_t* d_rowP = nullptr;
@@ -165,6 +197,31 @@ struct aim_ctx {
   bem::PrecBuf<double> f64;
   std::vector<void*> allocs;   // every device allocation, freed by aim_destroy
   void* geo_store = nullptr;   // device geometry descriptor (set-up kernels, right-hand sides)
+  // streams for the two-branch matvec and its CUDA-graph capture
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  struct GKey {
+    int which, prec;
+    const void* x;
+    void* y;
+    bool operator<(const GKey& o) const {
+      if (which != o.which) return which < o.which;
+      if (prec != o.prec) return prec < o.prec;
+      if (x != o.x) return x < o.x;
+      return y < o.y;
+    }
+  };
+  std::map<GKey, cudaGraphExec_t> graphs;  // captured matvecs, keyed by operator and buffers
+  bool use_graphs = true;
+  // block-diagonal preconditioner: explicit inverses of the per-object blocks A_ii, packed
+  // row-major in object-major unknown order ([h_i; q_i] per object), built on first use
+  bool pc_ready = false;
+  bem::GemvPlan pcplan;
+  float2* pc32 = nullptr;
+  double2* pc64 = nullptr;
+  int32_t* d_pcperm = nullptr;  // object-major position -> system index
+  float2* pcw32[2] = {nullptr, nullptr};
+  double2* pcw64[2] = {nullptr, nullptr};
 };
 
 namespace bem {
@@ -191,7 +248,17 @@ template <typename R>
 int run_gemv(const GemvTask* d_tasks, int ntasks, const typename C2<R>::T* A,
              const typename C2<R>::T* x, typename C2<R>::T* y, int nrhs, int64_t vstride,
              const typename C2<R>::T* hsub, cudaStream_t s);
+template <typename R>
+int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
+                  typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
+                  cudaStream_t s);
 template <typename R> int matvec(aim_ctx* c, int which, const void* x, void* y, cudaStream_t s);
+// matvec through a cached CUDA graph (captured on first use for these buffers)
+template <typename R> int matvec_graph(aim_ctx* c, int which, const void* x, void* y,
+                                       cudaStream_t s);
+int init_streams(aim_ctx* c);
+void release_streams(aim_ctx* c);
+int fft_init_attrs();
 template <typename R> int internal(aim_ctx* c, const void* h, void* e, void* heq, int nrhs,
                                    cudaStream_t s);
 template <typename R> int conv(aim_ctx* c, const void* sigma, void* phi, int ncomp,
@@ -199,11 +266,13 @@ template <typename R> int conv(aim_ctx* c, const void* sigma, void* phi, int nco
 // fft (fft.cu)
 template <typename R>
 int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename C2<R>::T* phi,
-             int ncomp, cudaStream_t s);
+             int ncomp, typename C2<R>::T* ws, cudaStream_t s);
 template <typename R> int make_twiddles(aim_ctx* c, PrecBuf<R>& b);
 int make_ghat(aim_ctx* c);
 int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
                    cudaStream_t st);
+int setup_precond(aim_ctx* c);
+template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cudaStream_t s);
 void free_geo_store(aim_ctx* c);
 double k0_of(double f);
 // solver (gmres.cu)

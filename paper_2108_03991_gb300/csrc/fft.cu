@@ -2,16 +2,19 @@
 // convolution of the grid sources with the grid Green's function by zero-padded FFTs.
 //
 // Layout: grid data [comp][nz][ny][nx] (x fastest); padded workspace [comp][Pz][Py][Px] with
-// P >= 2n - 1 per axis (factors 2, 3, 5, 7). The convolution runs as five batched 1-D passes
-// that skip the zero padding:
-//   X forward  : ny*nz lines of nx inputs  -> Px outputs
-//   Y forward  : Px*nz lines of ny inputs  -> Py outputs
-//   Z fused    : Px*Py lines: forward FFT of nz inputs, times Ghat, inverse FFT, nz outputs
-//   Y inverse  : Px*nz lines of Py inputs  -> ny outputs
-//   X inverse  : ny*nz lines of Px inputs  -> nx outputs
-// Ghat is stored as one octant (the circulant kernel is even along every axis) with the
-// 1/(Px Py Pz) normalisation folded in. Each pass stages TL lines in shared memory and runs a
-// Stockham autosort FFT (mixed radix 4, 2, 3, 5, 7; twiddles from a per-axis table).
+// P >= 2n - 1 per axis (factors 2, 3, 5). When one padded x-y plane fits in shared memory the
+// convolution is three passes that skip the zero padding:
+//   plane forward : per z < nz, load the nx*ny plane, FFT the ny non-zero rows (length Px) and
+//                   then all Px columns (length Py), store the Px*Py plane
+//   z fused       : per (x, y), forward FFT of the nz planes (length Pz), times Ghat, inverse
+//                   FFT, store the first nz outputs
+//   plane inverse : per z < nz, inverse FFT of all columns, then of the ny rows that are kept,
+//                   store the nx*ny plane
+// Larger planes fall back to five batched 1-D passes (x, y, z-fused, y, x) with the same
+// pruning. Ghat is one octant (the circulant kernel is even along every axis) with the
+// 1/(Px Py Pz) normalisation folded in. Every transform is a Stockham autosort FFT in shared
+// memory with radix-8/4/2/3/5 butterflies and twiddles from a per-axis table; line pitches
+// are padded by one element to keep strided staging free of bank conflicts.
 #include <algorithm>
 #include <cmath>
 
@@ -23,7 +26,7 @@ bool make_fft_plan(int P, FftPlan* plan) {
   plan->P = P;
   plan->nst = 0;
   int n = P;
-  const int rads[5] = {4, 2, 3, 5, 7};
+  const int rads[5] = {8, 4, 2, 3, 5};
   for (int r : rads)
     while (n % r == 0) {
       if (plan->nst >= kMaxStages) return false;
@@ -36,79 +39,139 @@ bool make_fft_plan(int P, FftPlan* plan) {
 int smooth_length(int need) {
   for (int m = std::max(need, 1);; ++m) {
     int n = m;
-    for (int r : {2, 3, 5, 7})
+    for (int r : {2, 3, 5})
       while (n % r == 0) n /= r;
     if (n == 1) return m;
   }
 }
 
-struct LinePass {
-  int P, nin, nout;
-  int64_t ies, oes;
-  int n0, n1;
-  int64_t is0, is1, is2;
-  int64_t os0, os1, os2;
-  int fused;        // 1: forward, multiply by Ghat, inverse
-  int inverse;      // plain pass direction
-  int TL;           // lines per CTA
-  int gx, gy;       // octant dims (Px/2+1, Py/2+1) for the fused pass
-  int Px, Py;
-  FftPlan plan;
-};
-
-template <typename V>
-__device__ __forceinline__ V tw_get(const V* tw, int idx, bool inv) {
-  V w = tw[idx];
-  if (inv) w.y = -w.y;
-  return w;
+// ---------------------------------------------------------------------------------------
+// butterflies (forward: exp(-2 pi i / R); inverse: conjugate)
+// ---------------------------------------------------------------------------------------
+template <typename V> __device__ __forceinline__ V mul_mi(V a, bool inv) {  // * (-i) or * (+i)
+  return inv ? mk(-a.y, a.x) : mk(a.y, -a.x);
 }
 
-// one Stockham stage on TL lines: src -> dst
-template <typename V>
-__device__ __forceinline__ void stage(const V* src, V* dst, const V* tw, int P, int TL, int R,
-                                      int Ns, bool inv) {
+template <typename V> __device__ __forceinline__ void bfly2(V* v) {
+  V a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename V> __device__ __forceinline__ void bfly3(V* v, bool inv) {
+  typedef decltype(v[0].x) R;
+  const R h = (R)0.86602540378443864676;  // sin(2 pi / 3)
+  V t1 = cadd(v[1], v[2]);
+  V d = csub(v[1], v[2]);
+  V t2 = mul_mi(mk(h * d.x, h * d.y), inv);
+  V m = mk(v[0].x - (R)0.5 * t1.x, v[0].y - (R)0.5 * t1.y);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, t2);
+  v[2] = csub(m, t2);
+}
+
+template <typename V> __device__ __forceinline__ void bfly4(V* v, bool inv) {
+  V y0 = cadd(v[0], v[2]), y1 = csub(v[0], v[2]), y2 = cadd(v[1], v[3]);
+  V y3 = mul_mi(csub(v[1], v[3]), inv);
+  v[0] = cadd(y0, y2);
+  v[1] = cadd(y1, y3);
+  v[2] = csub(y0, y2);
+  v[3] = csub(y1, y3);
+}
+
+template <typename V> __device__ __forceinline__ void bfly5(V* v, bool inv) {
+  typedef decltype(v[0].x) R;
+  const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;  // cos 2pi/5, 4pi/5
+  const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;   // sin 2pi/5, 4pi/5
+  V t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  V a1 = mk(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+  V a2 = mk(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+  V b1 = mk(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+  V b2 = mk(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+  V ib1 = mul_mi(b1, inv), ib2 = mul_mi(b2, inv);  // (-i) b forward
+  v[0] = cadd(v[0], cadd(t1, t2));
+  v[1] = cadd(a1, ib1);
+  v[4] = csub(a1, ib1);
+  v[2] = cadd(a2, ib2);
+  v[3] = csub(a2, ib2);
+}
+
+template <typename V> __device__ __forceinline__ void bfly8(V* v, bool inv) {
+  typedef decltype(v[0].x) R;
+  const R r2 = (R)0.70710678118654752440;
+  V e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+  bfly4(e, inv);
+  bfly4(o, inv);
+  // w8^k o[k]: w8 = exp(-i pi/4) forward
+  V w1 = inv ? mk(r2 * (o[1].x - o[1].y), r2 * (o[1].x + o[1].y))
+             : mk(r2 * (o[1].x + o[1].y), r2 * (o[1].y - o[1].x));
+  V w2 = mul_mi(o[2], inv);
+  V w3 = inv ? mk(-r2 * (o[3].x + o[3].y), r2 * (o[3].x - o[3].y))
+             : mk(r2 * (o[3].y - o[3].x), -r2 * (o[3].x + o[3].y));
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], w1);
+  v[5] = csub(e[1], w1);
+  v[2] = cadd(e[2], w2);
+  v[6] = csub(e[2], w2);
+  v[3] = cadd(e[3], w3);
+  v[7] = csub(e[3], w3);
+}
+
+// One Stockham stage over nlines lines held in shared memory. Element e of line l sits at
+// base[l * lstride + e * estride]. line_fast selects the thread mapping (consecutive threads
+// on consecutive lines, for lines that are adjacent in memory; otherwise on consecutive
+// butterflies of one line).
+template <typename V, int R>
+__device__ __forceinline__ void stage_r(const V* src, V* dst, const V* tw, int P, int Ns,
+                                        int nlines, int lstride, int estride, bool line_fast,
+                                        bool inv) {
   const int m = P / R;
-  const int stride_tw = P / (Ns * R);
-  for (int idx = threadIdx.x; idx < TL * m; idx += blockDim.x) {
-    const int l = idx / m, j = idx - l * m;
-    const V* s = src + (int64_t)l * P;
-    V* d = dst + (int64_t)l * P;
+  const int stw = P / (Ns * R);
+  const int total = nlines * m;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int l, j;
+    if (line_fast) { j = idx / nlines; l = idx - j * nlines; }
+    else { l = idx / m; j = idx - l * m; }
     const int k = j % Ns;
-    V v[7];
-    for (int r = 0; r < R; ++r) {
-      V x = s[j + r * m];
-      if (Ns > 1 && r > 0) x = cmul(x, tw_get(tw, r * k * stride_tw, inv));
-      v[r] = x;
-    }
-    const int base = (j / Ns) * Ns * R + k;
-    if (R == 2) {
-      d[base] = cadd(v[0], v[1]);
-      d[base + Ns] = csub(v[0], v[1]);
-    } else if (R == 4) {
-      V y0 = cadd(v[0], v[2]), y1 = csub(v[0], v[2]), y2 = cadd(v[1], v[3]), y3 = csub(v[1], v[3]);
-      // forward: y3 * (-i); inverse: y3 * (+i)
-      y3 = inv ? mk(-y3.y, y3.x) : mk(y3.y, -y3.x);
-      d[base] = cadd(y0, y2);
-      d[base + Ns] = cadd(y1, y3);
-      d[base + 2 * Ns] = csub(y0, y2);
-      d[base + 3 * Ns] = csub(y1, y3);
-    } else {
-      const int step = P / R;  // e^{-2 pi i q / R} = tw[q * P / R]
-      for (int q = 0; q < R; ++q) {
-        V acc = v[0];
-        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], tw_get(tw, ((r * q) % R) * step, inv)));
-        d[base + q * Ns] = acc;
+    const V* s = src + l * lstride;
+    V* d = dst + l * lstride;
+    V v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[(j + r * m) * estride];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        V w = tw[r * k * stw];
+        if (inv) w.y = -w.y;
+        v[r] = cmul(v[r], w);
       }
     }
+    if (R == 2) bfly2(v);
+    else if (R == 3) bfly3(v, inv);
+    else if (R == 4) bfly4(v, inv);
+    else if (R == 5) bfly5(v, inv);
+    else bfly8(v, inv);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[(base + r * Ns) * estride] = v[r];
   }
 }
 
+// all stages of plan pl; returns the buffer holding the result (a or b)
 template <typename V>
-__device__ __forceinline__ V* run_stages(V* a, V* b, const V* tw, const LinePass& p, bool inv) {
+__device__ V* fft_smem(V* a, V* b, const V* tw, const FftPlan& pl, int nlines, int lstride,
+                       int estride, bool line_fast, bool inv) {
   int Ns = 1;
-  for (int st = 0; st < p.plan.nst; ++st) {
-    const int R = p.plan.rad[st];
-    stage(a, b, tw, p.P, p.TL, R, Ns, inv);
+  for (int st = 0; st < pl.nst; ++st) {
+    const int R = pl.rad[st];
+    switch (R) {
+      case 2: stage_r<V, 2>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
+      case 3: stage_r<V, 3>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
+      case 4: stage_r<V, 4>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
+      case 5: stage_r<V, 5>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
+      default: stage_r<V, 8>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
+    }
     __syncthreads();
     V* t = a;
     a = b;
@@ -118,93 +181,215 @@ __device__ __forceinline__ V* run_stages(V* a, V* b, const V* tw, const LinePass
   return a;
 }
 
+// ---------------------------------------------------------------------------------------
+// plane passes (x and y together, one padded plane per CTA)
+// ---------------------------------------------------------------------------------------
+struct PlaneArgs {
+  int nx, ny, nz, Px, Py, Pz;
+  int64_t ng, P3;
+  FftPlan px, py, pz;
+  int gx, gy;  // octant dims of Ghat (Px/2+1, Py/2+1)
+  int TL;      // lines per CTA in the z pass
+};
+
 template <typename V>
-__global__ void __launch_bounds__(256) k_fft_lines(const V* in, V* out,
-                                                   const V* __restrict__ twg, const V* __restrict__ ghat,
-                                                   LinePass p) {
+__global__ void __launch_bounds__(512) k_plane_fwd(const V* __restrict__ sigma, V* __restrict__ ws,
+                                                   const V* __restrict__ twx, const V* __restrict__ twy,
+                                                   PlaneArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  V* tx = reinterpret_cast<V*>(smem_raw);
+  V* ty = tx + a.Px;
+  const int pitch = a.Px + 1;
+  V* A = ty + a.Py;
+  V* B = A + a.Py * pitch;
+  const int z = blockIdx.x, c = blockIdx.y;
+  for (int i = threadIdx.x; i < a.Px; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
+  const V* src = sigma + c * a.ng + (int64_t)z * a.ny * a.nx;
+  for (int i = threadIdx.x; i < a.Py * a.Px; i += blockDim.x) {
+    const int y = i / a.Px, x = i - y * a.Px;
+    V v = czero<V>();
+    if (y < a.ny && x < a.nx) v = src[y * a.nx + x];
+    A[y * pitch + x] = v;
+    B[y * pitch + x] = czero<V>();
+  }
+  __syncthreads();
+  // rows (only the ny non-zero ones), then all columns
+  V* r = fft_smem(A, B, tx, a.px, a.ny, pitch, 1, false, false);
+  V* o = (r == A) ? B : A;
+  r = fft_smem(r, o, ty, a.py, a.Px, 1, pitch, true, false);
+  V* dst = ws + c * a.P3 + (int64_t)z * a.Py * a.Px;
+  for (int i = threadIdx.x; i < a.Py * a.Px; i += blockDim.x) {
+    const int y = i / a.Px, x = i - y * a.Px;
+    dst[i] = r[y * pitch + x];
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(512) k_plane_inv(const V* __restrict__ ws, V* __restrict__ phi,
+                                                   const V* __restrict__ twx, const V* __restrict__ twy,
+                                                   PlaneArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  V* tx = reinterpret_cast<V*>(smem_raw);
+  V* ty = tx + a.Px;
+  const int pitch = a.Px + 1;
+  V* A = ty + a.Py;
+  V* B = A + a.Py * pitch;
+  const int z = blockIdx.x, c = blockIdx.y;
+  for (int i = threadIdx.x; i < a.Px; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
+  const V* src = ws + c * a.P3 + (int64_t)z * a.Py * a.Px;
+  for (int i = threadIdx.x; i < a.Py * a.Px; i += blockDim.x) {
+    const int y = i / a.Px, x = i - y * a.Px;
+    A[y * pitch + x] = src[i];
+  }
+  __syncthreads();
+  V* r = fft_smem(A, B, ty, a.py, a.Px, 1, pitch, true, true);
+  V* o = (r == A) ? B : A;
+  r = fft_smem(r, o, tx, a.px, a.ny, pitch, 1, false, true);
+  V* dst = phi + c * a.ng + (int64_t)z * a.ny * a.nx;
+  for (int i = threadIdx.x; i < a.ny * a.nx; i += blockDim.x) {
+    const int y = i / a.nx, x = i - y * a.nx;
+    dst[i] = r[y * pitch + x];
+  }
+}
+
+// z pass: TL consecutive x of one y; forward FFT of the nz planes, times Ghat, inverse
+template <typename V>
+__global__ void __launch_bounds__(256) k_zfused(V* ws, const V* __restrict__ ghat,
+                                                const V* __restrict__ twz, PlaneArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  V* tz = reinterpret_cast<V*>(smem_raw);
+  const int pitch = a.Pz + 1;
+  V* A = tz + a.Pz;
+  V* B = A + a.TL * pitch;
+  const int x0 = blockIdx.x * a.TL, y = blockIdx.y, c = blockIdx.z;
+  const int nl = min(a.TL, a.Px - x0);
+  for (int i = threadIdx.x; i < a.Pz; i += blockDim.x) tz[i] = twz[i];
+  const int64_t plane = (int64_t)a.Py * a.Px;
+  V* base = ws + c * a.P3 + (int64_t)y * a.Px + x0;
+  for (int i = threadIdx.x; i < a.TL * a.Pz; i += blockDim.x) {
+    const int e = i / a.TL, l = i - e * a.TL;
+    V v = czero<V>();
+    if (l < nl && e < a.nz) v = base[e * plane + l];
+    A[l * pitch + e] = v;
+  }
+  __syncthreads();
+  V* r = fft_smem(A, B, tz, a.pz, a.TL, pitch, 1, false, false);
+  const int fy = min(y, a.Py - y);
+  for (int i = threadIdx.x; i < a.TL * a.Pz; i += blockDim.x) {
+    const int l = i / a.Pz, kz = i - l * a.Pz;
+    if (l >= nl) continue;
+    const int x = x0 + l;
+    const int fx = min(x, a.Px - x), fz = min(kz, a.Pz - kz);
+    r[l * pitch + kz] = cmul(r[l * pitch + kz], ghat[((int64_t)fz * a.gy + fy) * a.gx + fx]);
+  }
+  __syncthreads();
+  V* o = (r == A) ? B : A;
+  r = fft_smem(r, o, tz, a.pz, a.TL, pitch, 1, false, true);
+  for (int i = threadIdx.x; i < a.TL * a.nz; i += blockDim.x) {
+    const int e = i / a.TL, l = i - e * a.TL;
+    if (l < nl) base[e * plane + l] = r[l * pitch + e];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// generic batched 1-D pass (large planes, and the set-up FFT of the grid kernel)
+// ---------------------------------------------------------------------------------------
+struct LinePass {
+  int P, nin, nout;
+  int64_t ies, oes;
+  int n0, n1;
+  int64_t is0, is1, is2;
+  int64_t os0, os1, os2;
+  int fused;    // 1: forward, multiply by Ghat, inverse (z axis: line = (x = i0, y = i1))
+  int inverse;
+  int TL;
+  int gx, gy, Px, Py;
+  FftPlan plan;
+};
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_lines(const V* in, V* out, const V* __restrict__ twg,
+                                               const V* __restrict__ ghat, LinePass p) {
   extern __shared__ unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
+  const int pitch = p.P + 1;
   V* A = tw + p.P;
-  V* B = A + (int64_t)p.TL * p.P;
+  V* B = A + p.TL * pitch;
   const int i0base = blockIdx.x * p.TL;
   const int i1 = blockIdx.y, i2 = blockIdx.z;
   const int nl = min(p.TL, p.n0 - i0base);
   for (int i = threadIdx.x; i < p.P; i += blockDim.x) tw[i] = twg[i];
-  // load (zero padding beyond nin)
   const int64_t ib = i1 * p.is1 + i2 * p.is2;
-  if (p.ies == 1) {
-    for (int idx = threadIdx.x; idx < p.TL * p.P; idx += blockDim.x) {
-      const int l = idx / p.P, e = idx - l * p.P;
-      V v = czero<V>();
-      if (l < nl && e < p.nin) v = in[ib + (int64_t)(i0base + l) * p.is0 + e];
-      A[idx] = v;
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < p.TL * p.P; idx += blockDim.x) {
-      const int e = idx / p.TL, l = idx - e * p.TL;
-      V v = czero<V>();
-      if (l < nl && e < p.nin) v = in[ib + (int64_t)(i0base + l) * p.is0 + (int64_t)e * p.ies];
-      A[(int64_t)l * p.P + e] = v;
-    }
+  for (int idx = threadIdx.x; idx < p.TL * p.P; idx += blockDim.x) {
+    int l, e;
+    if (p.ies == 1) { l = idx / p.P; e = idx - l * p.P; }
+    else { e = idx / p.TL; l = idx - e * p.TL; }
+    V v = czero<V>();
+    if (l < nl && e < p.nin) v = in[ib + (int64_t)(i0base + l) * p.is0 + (int64_t)e * p.ies];
+    A[l * pitch + e] = v;
   }
   __syncthreads();
   V* res;
   if (!p.fused) {
-    res = run_stages(A, B, tw, p, p.inverse != 0);
+    res = fft_smem(A, B, tw, p.plan, p.TL, pitch, 1, false, p.inverse != 0);
   } else {
-    res = run_stages(A, B, tw, p, false);
-    // multiply by the octant of Ghat: line (x = i0, y = i1), element kz
+    res = fft_smem(A, B, tw, p.plan, p.TL, pitch, 1, false, false);
     for (int idx = threadIdx.x; idx < p.TL * p.P; idx += blockDim.x) {
       const int l = idx / p.P, kz = idx - l * p.P;
       if (l >= nl) continue;
       const int x = i0base + l, y = i1;
       const int fx = min(x, p.Px - x), fy = min(y, p.Py - y), fz = min(kz, p.P - kz);
-      res[idx] = cmul(res[idx], ghat[((int64_t)fz * p.gy + fy) * p.gx + fx]);
+      res[l * pitch + kz] = cmul(res[l * pitch + kz], ghat[((int64_t)fz * p.gy + fy) * p.gx + fx]);
     }
     __syncthreads();
     V* other = (res == A) ? B : A;
-    res = run_stages(res, other, tw, p, true);
+    res = fft_smem(res, other, tw, p.plan, p.TL, pitch, 1, false, true);
   }
-  // store the first nout outputs
   const int64_t ob = i1 * p.os1 + i2 * p.os2;
-  if (p.oes == 1) {
-    for (int idx = threadIdx.x; idx < p.TL * p.nout; idx += blockDim.x) {
-      const int l = idx / p.nout, e = idx - l * p.nout;
-      if (l < nl) out[ob + (int64_t)(i0base + l) * p.os0 + e] = res[(int64_t)l * p.P + e];
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < p.TL * p.nout; idx += blockDim.x) {
-      const int e = idx / p.TL, l = idx - e * p.TL;
-      if (l < nl) out[ob + (int64_t)(i0base + l) * p.os0 + (int64_t)e * p.oes] = res[(int64_t)l * p.P + e];
-    }
+  for (int idx = threadIdx.x; idx < p.TL * p.nout; idx += blockDim.x) {
+    int l, e;
+    if (p.oes == 1) { l = idx / p.nout; e = idx - l * p.nout; }
+    else { e = idx / p.TL; l = idx - e * p.TL; }
+    if (l < nl) out[ob + (int64_t)(i0base + l) * p.os0 + (int64_t)e * p.oes] = res[l * pitch + e];
   }
 }
 
+static constexpr size_t kSmemBudget = 200 * 1024;
+
 template <typename V>
-static int launch_pass(const V* in, V* out, const V* tw, const V* ghat, LinePass p, int n2,
-                       cudaStream_t s) {
-  const size_t avail = 96 * 1024 / sizeof(V);  // complex elements of shared memory
-  if (avail < 3 * (size_t)p.P) {
+static int launch_lines(const V* in, V* out, const V* tw, const V* ghat, LinePass p, int n2,
+                        cudaStream_t s) {
+  const size_t avail = 96 * 1024 / sizeof(V);
+  if (avail < 3 * (size_t)(p.P + 1)) {
     set_error("FFT length %d too large for shared memory", p.P);
     return BEM_EGRID;
   }
-  int TL = (int)std::min<size_t>(16, (avail - p.P) / (2 * (size_t)p.P));
-  if (TL < 1) {
-    set_error("FFT length %d too large for shared memory", p.P);
-    return BEM_EGRID;
-  }
-  TL = std::min(TL, p.n0);
+  int TL = (int)std::min<size_t>(16, (avail - p.P) / (2 * (size_t)(p.P + 1)));
+  TL = std::max(1, std::min(TL, p.n0));
   p.TL = TL;
-  size_t smem = ((size_t)p.P + 2 * (size_t)TL * p.P) * sizeof(V);
+  size_t smem = ((size_t)p.P + 2 * (size_t)TL * (p.P + 1)) * sizeof(V);
   dim3 grid((p.n0 + TL - 1) / TL, p.n1, n2);
-  static bool attr_set[2] = {false, false};
-  int which = sizeof(V) == 8 ? 0 : 1;
-  if (!attr_set[which]) {
-    BEM_CUDA(cudaFuncSetAttribute(k_fft_lines<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set[which] = true;
-  }
-  k_fft_lines<V><<<grid, 256, smem, s>>>(in, out, tw, ghat, p);
+  k_lines<V><<<grid, 256, smem, s>>>(in, out, tw, ghat, p);
   BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+template <typename V> static size_t plane_smem(int Px, int Py) {
+  return ((size_t)Px + Py + 2 * (size_t)Py * (Px + 1)) * sizeof(V);
+}
+
+int fft_init_attrs() {
+  const int lim = (int)kSmemBudget;
+  BEM_CUDA(cudaFuncSetAttribute(k_lines<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_lines<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_plane_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_plane_fwd<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_plane_inv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_plane_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_zfused<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_zfused<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return BEM_OK;
 }
 
@@ -227,48 +412,64 @@ template int make_twiddles<double>(aim_ctx*, PrecBuf<double>&);
 
 template <typename R>
 int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename C2<R>::T* phi,
-             int ncomp, cudaStream_t s) {
+             int ncomp, typename C2<R>::T* ws, cudaStream_t s) {
   typedef typename C2<R>::T V;
   const int nx = c->gn[0], ny = c->gn[1], nz = c->gn[2];
   const int Px = c->gp[0], Py = c->gp[1], Pz = c->gp[2];
   const int64_t P3 = (int64_t)Px * Py * Pz, ng = c->ng;
-  V* ws = b.ws;
+  const size_t psm = plane_smem<V>(Px, Py);
+  if (psm <= kSmemBudget) {
+    PlaneArgs a;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.Px = Px; a.Py = Py; a.Pz = Pz;
+    a.ng = ng; a.P3 = P3;
+    a.px = c->plan[0]; a.py = c->plan[1]; a.pz = c->plan[2];
+    a.gx = Px / 2 + 1; a.gy = Py / 2 + 1;
+    const size_t avail = 64 * 1024 / sizeof(V);
+    a.TL = (int)std::max<size_t>(1, std::min<size_t>(16, (avail - Pz) / (2 * (size_t)(Pz + 1))));
+    const size_t zsm = ((size_t)Pz + 2 * (size_t)a.TL * (Pz + 1)) * sizeof(V);
+    k_plane_fwd<V><<<dim3(nz, ncomp), 512, psm, s>>>(sigma, ws, b.tw[0], b.tw[1], a);
+    k_zfused<V><<<dim3((Px + a.TL - 1) / a.TL, Py, ncomp), 256, zsm, s>>>(ws, b.Ghat, b.tw[2], a);
+    k_plane_inv<V><<<dim3(nz, ncomp), 512, psm, s>>>(ws, phi, b.tw[0], b.tw[1], a);
+    BEM_CUDA(cudaGetLastError());
+    return BEM_OK;
+  }
   LinePass p{};
   // X forward
-  p = LinePass{};
   p.P = Px; p.nin = nx; p.nout = Px; p.ies = 1; p.oes = 1;
   p.n0 = ny; p.n1 = nz; p.is0 = nx; p.is1 = (int64_t)ny * nx; p.is2 = ng;
   p.os0 = Px; p.os1 = (int64_t)Py * Px; p.os2 = P3; p.plan = c->plan[0];
-  BEM_TRY(launch_pass<V>(sigma, ws, b.tw[0], nullptr, p, ncomp, s));
+  BEM_TRY(launch_lines<V>(sigma, ws, b.tw[0], nullptr, p, ncomp, s));
   // Y forward
   p = LinePass{};
   p.P = Py; p.nin = ny; p.nout = Py; p.ies = Px; p.oes = Px;
   p.n0 = Px; p.n1 = nz; p.is0 = 1; p.is1 = (int64_t)Py * Px; p.is2 = P3;
   p.os0 = 1; p.os1 = (int64_t)Py * Px; p.os2 = P3; p.plan = c->plan[1];
-  BEM_TRY(launch_pass<V>(ws, ws, b.tw[1], nullptr, p, ncomp, s));
+  BEM_TRY(launch_lines<V>(ws, ws, b.tw[1], nullptr, p, ncomp, s));
   // Z forward * Ghat * Z inverse
   p = LinePass{};
   p.P = Pz; p.nin = nz; p.nout = nz; p.ies = (int64_t)Py * Px; p.oes = (int64_t)Py * Px;
   p.n0 = Px; p.n1 = Py; p.is0 = 1; p.is1 = Px; p.is2 = P3;
   p.os0 = 1; p.os1 = Px; p.os2 = P3; p.fused = 1; p.plan = c->plan[2];
   p.gx = Px / 2 + 1; p.gy = Py / 2 + 1; p.Px = Px; p.Py = Py;
-  BEM_TRY(launch_pass<V>(ws, ws, b.tw[2], b.Ghat, p, ncomp, s));
+  BEM_TRY(launch_lines<V>(ws, ws, b.tw[2], b.Ghat, p, ncomp, s));
   // Y inverse
   p = LinePass{};
   p.P = Py; p.nin = Py; p.nout = ny; p.ies = Px; p.oes = Px; p.inverse = 1;
   p.n0 = Px; p.n1 = nz; p.is0 = 1; p.is1 = (int64_t)Py * Px; p.is2 = P3;
   p.os0 = 1; p.os1 = (int64_t)Py * Px; p.os2 = P3; p.plan = c->plan[1];
-  BEM_TRY(launch_pass<V>(ws, ws, b.tw[1], nullptr, p, ncomp, s));
+  BEM_TRY(launch_lines<V>(ws, ws, b.tw[1], nullptr, p, ncomp, s));
   // X inverse
   p = LinePass{};
   p.P = Px; p.nin = Px; p.nout = nx; p.ies = 1; p.oes = 1; p.inverse = 1;
   p.n0 = ny; p.n1 = nz; p.is0 = Px; p.is1 = (int64_t)Py * Px; p.is2 = P3;
   p.os0 = nx; p.os1 = (int64_t)ny * nx; p.os2 = ng; p.plan = c->plan[0];
-  BEM_TRY(launch_pass<V>(ws, phi, b.tw[0], nullptr, p, ncomp, s));
+  BEM_TRY(launch_lines<V>(ws, phi, b.tw[0], nullptr, p, ncomp, s));
   return BEM_OK;
 }
-template int fft_conv<float>(aim_ctx*, PrecBuf<float>&, const float2*, float2*, int, cudaStream_t);
-template int fft_conv<double>(aim_ctx*, PrecBuf<double>&, const double2*, double2*, int, cudaStream_t);
+template int fft_conv<float>(aim_ctx*, PrecBuf<float>&, const float2*, float2*, int, float2*,
+                              cudaStream_t);
+template int fft_conv<double>(aim_ctx*, PrecBuf<double>&, const double2*, double2*, int, double2*,
+                               cudaStream_t);
 
 // circulant grid kernel: offset d along an axis of padded length P lives at index d mod P
 __global__ void k_gcirc(double2* g, int Px, int Py, int Pz, int nx, int ny, int nz, double hx,
@@ -324,20 +525,20 @@ int make_ghat(aim_ctx* c) {
   p.P = Px; p.nin = Px; p.nout = Px; p.ies = 1; p.oes = 1;
   p.n0 = Py; p.n1 = Pz; p.is0 = Px; p.is1 = (int64_t)Py * Px; p.is2 = P3;
   p.os0 = Px; p.os1 = (int64_t)Py * Px; p.os2 = P3; p.plan = c->plan[0];
-  rc = launch_pass<double2>(G, G, c->f64.tw[0], nullptr, p, 1, 0);
+  rc = launch_lines<double2>(G, G, c->f64.tw[0], nullptr, p, 1, 0);
   if (rc == BEM_OK) {
     p = LinePass{};
     p.P = Py; p.nin = Py; p.nout = Py; p.ies = Px; p.oes = Px;
     p.n0 = Px; p.n1 = Pz; p.is0 = 1; p.is1 = (int64_t)Py * Px; p.is2 = P3;
     p.os0 = 1; p.os1 = (int64_t)Py * Px; p.os2 = P3; p.plan = c->plan[1];
-    rc = launch_pass<double2>(G, G, c->f64.tw[1], nullptr, p, 1, 0);
+    rc = launch_lines<double2>(G, G, c->f64.tw[1], nullptr, p, 1, 0);
   }
   if (rc == BEM_OK) {
     p = LinePass{};
     p.P = Pz; p.nin = Pz; p.nout = Pz; p.ies = (int64_t)Py * Px; p.oes = (int64_t)Py * Px;
     p.n0 = Px; p.n1 = Py; p.is0 = 1; p.is1 = Px; p.is2 = P3;
     p.os0 = 1; p.os1 = Px; p.os2 = P3; p.plan = c->plan[2];
-    rc = launch_pass<double2>(G, G, c->f64.tw[2], nullptr, p, 1, 0);
+    rc = launch_lines<double2>(G, G, c->f64.tw[2], nullptr, p, 1, 0);
   }
   const int64_t no = (int64_t)(Px / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1);
   if (rc == BEM_OK) rc = dalloc_t(c, &c->f64.Ghat, no);

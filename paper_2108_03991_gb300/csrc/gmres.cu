@@ -164,11 +164,17 @@ static int dot_into(const double2* V, int64_t ldv, int nv, const double2* w, int
 }
 
 // y = A x in FP64 (plain) or through the FP32 matvec
+// (both go through the context's fixed buffers so one captured graph serves every iteration)
 static int sys_apply(aim_ctx* c, int prec, const double2* x, double2* y, cudaStream_t s) {
   const int64_t n = (int64_t)c->ne + c->nt;
-  if (prec == BEM_C64) return matvec<double>(c, AIM_OP_SYSTEM, x, y, s);
+  if (prec == BEM_C64) {
+    BEM_CUDA(cudaMemcpyAsync(c->f64.xin, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    BEM_TRY(matvec_graph<double>(c, AIM_OP_SYSTEM, c->f64.xin, c->f64.yout, s));
+    BEM_CUDA(cudaMemcpyAsync(y, c->f64.yout, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    return BEM_OK;
+  }
   k_to32<<<kChunks, 256, 0, s>>>(x, c->f32.xin, n);
-  BEM_TRY(matvec<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s));
+  BEM_TRY(matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s));
   k_to64<<<kChunks, 256, 0, s>>>(c->f32.yout, y, n);
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
@@ -196,6 +202,12 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   BEM_TRY(W.alloc(&W.y, m + 1));
   BEM_TRY(W.alloc(&W.partial, (size_t)(m + 1) * kChunks));
   BEM_TRY(W.alloc(&W.dsc, 8));
+  // right preconditioning (flexible form: the preconditioned directions are kept)
+  double2* Zb = nullptr;
+  if (o->precond == 1) {
+    BEM_TRY(setup_precond(c));
+    BEM_TRY(W.alloc(&Zb, (size_t)m * n));
+  }
   BEM_CUDA(cudaMemsetAsync(W.H, 0, sizeof(double2) * ldh * m, s));
   // ||b||
   BEM_TRY(dot_into(b, n, 1, b, n, W, W.h, nullptr, s));
@@ -213,7 +225,7 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   }
   while (status != BEM_OK && iters < o->max_iter) {
     // r = b - A x (FP64 matvec), beta = ||r||
-    BEM_TRY(matvec<double>(c, AIM_OP_SYSTEM, x, W.w, s));
+    BEM_TRY(sys_apply(c, BEM_C64, x, W.w, s));
     k_sub<<<kChunks, 256, 0, s>>>(b, W.w, W.r, n);
     BEM_TRY(dot_into(W.r, n, 1, W.r, n, W, W.h, nullptr, s));
     k_normalize<<<kChunks, 256, 0, s>>>(W.r, W.h, W.V, W.dsc + 2, n);
@@ -228,6 +240,17 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
     int k = 0;
     for (; k < m && iters < o->max_iter; ++k) {
       const double2* vk = W.V + (int64_t)k * n;
+      if (Zb) {
+        double2* zk = Zb + (int64_t)k * n;
+        if (o->prec_mode == BEM_C64) {
+          BEM_TRY(precond_apply<double>(c, vk, zk, s));
+        } else {
+          k_to32<<<kChunks, 256, 0, s>>>(vk, c->f32.xin, n);
+          BEM_TRY(precond_apply<float>(c, c->f32.xin, c->f32.yout, s));
+          k_to64<<<kChunks, 256, 0, s>>>(c->f32.yout, zk, n);
+        }
+        vk = zk;
+      }
       BEM_TRY(sys_apply(c, o->prec_mode, vk, W.w, s));
       // CGS2: h = V^H w, w -= V h, twice; accumulate into column k of H
       double2* Hk = W.H + (int64_t)k * ldh;
@@ -250,12 +273,12 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
     }
     // x += V[:k] y, y = R^{-1} g
     k_backsolve<<<1, 1, 0, s>>>(W.H, ldh, k, W.g, W.y);
-    k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>(W.V, n, k, W.y, 1.0, x, n);
+    k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>(Zb ? Zb : W.V, n, k, W.y, 1.0, x, n);
     BEM_CUDA(cudaGetLastError());
     if (o->time_limit_s > 0 && std::chrono::duration<double>(clk::now() - t0).count() > o->time_limit_s) break;
   }
   // true residual with the FP64 matvec
-  BEM_TRY(matvec<double>(c, AIM_OP_SYSTEM, x, W.w, s));
+  BEM_TRY(sys_apply(c, BEM_C64, x, W.w, s));
   k_sub<<<kChunks, 256, 0, s>>>(b, W.w, W.r, n);
   BEM_TRY(dot_into(W.r, n, 1, W.r, n, W, W.h, nullptr, s));
   double2 rr;

@@ -19,6 +19,46 @@ template <typename R> struct Vec16;
 template <> struct Vec16<float> { typedef float4 T; static constexpr int kCplx = 2; };
 template <> struct Vec16<double> { typedef double2 T; static constexpr int kCplx = 1; };
 
+// One row of the product, one warp: acc[r] = sum_k A[row, k] x_r[k]. Rows are streamed with
+// 16-byte loads (two complex FP32 or one complex FP64 per load), evict-first so the streamed
+// matrix does not displace the vectors in L2; x is read through the read-only path (L1).
+template <typename R, int NRHS>
+__device__ __forceinline__ void row_dot(const typename C2<R>::T* __restrict__ arow_,
+                                        const typename C2<R>::T* __restrict__ xb, int n,
+                                        int64_t vstride, int lane, typename C2<R>::T* acc) {
+  typedef typename C2<R>::T V;
+  typedef typename Vec16<R>::T L16;
+  constexpr int CP = Vec16<R>::kCplx;
+  const L16* arow = reinterpret_cast<const L16*>(arow_);
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
+  const int nvec = (n + CP - 1) / CP;
+#pragma unroll 4
+  for (int v = lane; v < nvec; v += 32) {
+    L16 a = __ldcs(arow + v);
+    const int col = v * CP;
+    if constexpr (CP == 2) {
+      V a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) {
+        V x0 = __ldg(xb + r * vstride + col);
+        cfma(acc[r], a0, x0);
+        if (col + 1 < n) {
+          V x1 = __ldg(xb + r * vstride + col + 1);
+          cfma(acc[r], a1, x1);
+        }
+      }
+    } else {
+      V a0 = mk(a.x, a.y);
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) cfma(acc[r], a0, __ldg(xb + r * vstride + col));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r) acc[r] = warp_sum(acc[r]);
+}
+
+// Task-list form (one CTA per task of at most 16 rows).
 template <typename R, int NRHS>
 __global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks,
                                               const typename C2<R>::T* __restrict__ A,
@@ -26,49 +66,78 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks
                                               typename C2<R>::T* __restrict__ y, int64_t vstride,
                                               const typename C2<R>::T* __restrict__ hsub) {
   typedef typename C2<R>::T V;
-  typedef typename Vec16<R>::T L16;
-  constexpr int CP = Vec16<R>::kCplx;
   const GemvTask t = tasks[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const V* xb = x + t.xoff;
   for (int rr = warp; rr < t.nrows; rr += 8) {
     const int row = t.row0 + rr;
-    const L16* arow = reinterpret_cast<const L16*>(A + t.aoff + (int64_t)row * t.ld);
     V acc[NRHS];
-#pragma unroll
-    for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
-    const int nvec = (t.n + CP - 1) / CP;
-#pragma unroll 4
-    for (int v = lane; v < nvec; v += 32) {
-      L16 a = __ldg(arow + v);
-      const int col = v * CP;
-      if constexpr (CP == 2) {
-        V a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
-#pragma unroll
-        for (int r = 0; r < NRHS; ++r) {
-          V x0 = __ldg(xb + r * vstride + col);
-          cfma(acc[r], a0, x0);
-          if (col + 1 < t.n) {
-            V x1 = __ldg(xb + r * vstride + col + 1);
-            cfma(acc[r], a1, x1);
-          }
-        }
-      } else {
-        V a0 = mk(a.x, a.y);
-#pragma unroll
-        for (int r = 0; r < NRHS; ++r) cfma(acc[r], a0, __ldg(xb + r * vstride + col));
-      }
-    }
+    row_dot<R, NRHS>(A + t.aoff + (int64_t)row * t.ld, xb, t.n, vstride, lane, acc);
 #pragma unroll
     for (int r = 0; r < NRHS; ++r) {
-      V s = warp_sum(acc[r]);
       if (lane == 0) {
         int64_t o = r * vstride + t.xoff + row;
-        y[o] = hsub ? csub(hsub[o], s) : s;
+        y[o] = hsub ? csub(hsub[o], acc[r]) : acc[r];
       }
     }
   }
 }
+
+// Persistent form: CTA p streams the row panels of row p of the schedule (GemvPlan).
+template <typename R, int NRHS>
+__global__ void __launch_bounds__(kGemvThreads, kGemvCtasPerSm)
+    k_gemv_plan(const RowInfo* __restrict__ rows, const int2* __restrict__ segs,
+                const int32_t* __restrict__ cta_seg, const typename C2<R>::T* __restrict__ A,
+                const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
+                int64_t vstride, const typename C2<R>::T* __restrict__ hsub) {
+  typedef typename C2<R>::T V;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nw = kGemvThreads / 32;
+  const int s1 = cta_seg[blockIdx.x + 1];
+  for (int s = cta_seg[blockIdx.x]; s < s1; ++s) {
+    const int2 sg = segs[s];
+    for (int m = sg.x + warp; m < sg.y; m += nw) {
+      const RowInfo ri = rows[m];
+      V acc[NRHS];
+      row_dot<R, NRHS>(A + ri.aoff, x + ri.xoff, ri.n, vstride, lane, acc);
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) {
+          int64_t o = r * vstride + m;
+          y[o] = hsub ? csub(hsub[o], acc[r]) : acc[r];
+        }
+      }
+    }
+  }
+}
+
+template <typename R>
+int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
+                  typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
+                  cudaStream_t s) {
+  if (p.ncta == 0 || p.nrows == 0) return BEM_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += 4) {
+    const int nr = std::min(4, nrhs - r0);
+    const int64_t o = r0 * vstride;
+    const typename C2<R>::T* hs = hsub ? hsub + o : nullptr;
+#define BEM_GEMV_PLAN(NR)                                                                    \
+  k_gemv_plan<R, NR><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x + o, y + o, \
+                                                     vstride, hs)
+    switch (nr) {
+      case 1: BEM_GEMV_PLAN(1); break;
+      case 2: BEM_GEMV_PLAN(2); break;
+      case 3: BEM_GEMV_PLAN(3); break;
+      default: BEM_GEMV_PLAN(4); break;
+    }
+#undef BEM_GEMV_PLAN
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int run_gemv_plan<float>(const GemvPlan&, const float2*, const float2*, float2*, int,
+                                  int64_t, const float2*, cudaStream_t);
+template int run_gemv_plan<double>(const GemvPlan&, const double2*, const double2*, double2*, int,
+                                   int64_t, const double2*, cudaStream_t);
 
 template <typename R>
 int run_gemv(const GemvTask* d_tasks, int ntasks, const typename C2<R>::T* A,
@@ -101,6 +170,13 @@ __device__ __forceinline__ int node_offset(int k, int nx, int ny) {
   return ((k / 9 - 1) * ny + ((k / 3) % 3 - 1)) * nx + (k % 3 - 1);
 }
 
+// complex atomic add: one 8-byte vector atomic in FP32, two scalar atomics in FP64
+__device__ __forceinline__ void catomic_add(float2* o, float2 v) { atomicAdd(o, v); }
+__device__ __forceinline__ void catomic_add(double2* o, double2 v) {
+  atomicAdd(&o->x, v.x);
+  atomicAdd(&o->y, v.y);
+}
+
 template <typename R>
 __global__ void k_scatter_e(const R* __restrict__ WA, const int32_t* __restrict__ node,
                             const typename C2<R>::T* __restrict__ j, typename C2<R>::T* sigma,
@@ -113,9 +189,7 @@ __global__ void k_scatter_e(const R* __restrict__ WA, const int32_t* __restrict_
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const R w = WA[(int64_t)m * 81 + c * 27 + k];
-    R* o = reinterpret_cast<R*>(sigma + c * ng + nd);
-    atomicAdd(o, w * v.x);
-    atomicAdd(o + 1, w * v.y);
+    catomic_add(sigma + c * ng + nd, mk(w * v.x, w * v.y));
   }
 }
 
@@ -128,9 +202,53 @@ __global__ void k_scatter_t(const R* __restrict__ WP, const int32_t* __restrict_
   const int t = (int)(idx / 27), k = (int)(idx - (int64_t)t * 27);
   const typename C2<R>::T v = q[t];
   const R w = WP[(int64_t)t * 27 + k];
-  R* o = reinterpret_cast<R*>(sigma + node[t] + node_offset(k, nx, ny));
-  atomicAdd(o, w * v.x);
-  atomicAdd(o + 1, w * v.y);
+  catomic_add(sigma + node[t] + node_offset(k, nx, ny), mk(w * v.x, w * v.y));
+}
+
+// Gather form of the projection (no atomics, deterministic): one thread per grid node sums the
+// sources whose stencils touch it, from the node-major CSR of P^T. Every node is written, so
+// the grids need no clearing.
+template <typename R>
+__global__ void __launch_bounds__(256) k_project_e(const int32_t* __restrict__ prow,
+                                                   const int32_t* __restrict__ pcol,
+                                                   const R* __restrict__ WT,
+                                                   const typename C2<R>::T* __restrict__ j,
+                                                   typename C2<R>::T* __restrict__ sigma, int64_t ng) {
+  typedef typename C2<R>::T V;
+  const int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (nd >= ng) return;
+  V a0 = czero<V>(), a1 = czero<V>(), a2 = czero<V>();
+  const int e1 = prow[nd + 1];
+  for (int e = prow[nd]; e < e1; ++e) {
+    const V v = j[pcol[e]];
+    const R w0 = WT[3 * (int64_t)e], w1 = WT[3 * (int64_t)e + 1], w2 = WT[3 * (int64_t)e + 2];
+    a0.x += w0 * v.x; a0.y += w0 * v.y;
+    a1.x += w1 * v.x; a1.y += w1 * v.y;
+    a2.x += w2 * v.x; a2.y += w2 * v.y;
+  }
+  sigma[nd] = a0;
+  sigma[ng + nd] = a1;
+  sigma[2 * ng + nd] = a2;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_project_t(const int32_t* __restrict__ prow,
+                                                   const int32_t* __restrict__ pcol,
+                                                   const R* __restrict__ WT,
+                                                   const typename C2<R>::T* __restrict__ q,
+                                                   typename C2<R>::T* __restrict__ sigma, int64_t ng) {
+  typedef typename C2<R>::T V;
+  const int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (nd >= ng) return;
+  V a = czero<V>();
+  const int e1 = prow[nd + 1];
+  for (int e = prow[nd]; e < e1; ++e) {
+    const V v = q[pcol[e]];
+    const R w = WT[e];
+    a.x += w * v.x;
+    a.y += w * v.y;
+  }
+  sigma[nd] = a;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -139,15 +257,14 @@ __global__ void k_scatter_t(const R* __restrict__ WP, const int32_t* __restrict_
 template <typename V, typename R>
 __device__ __forceinline__ V jk0(V a, R k0) { return mk(-k0 * a.y, k0 * a.x); }
 
-// mode 0: y[t] = p_t (L^Phi alone); mode 1: p[t] = p_t and y2_t into y[ne + t]
+// p_t = (W_Phi phi)_t + (L^Phi_NR q)_t, written to out[t] (y for L^Phi alone, p in the system)
 template <typename R>
 __global__ void __launch_bounds__(256) k_rows_t(
     const R* __restrict__ WP, const int32_t* __restrict__ node,
     const typename C2<R>::T* __restrict__ phi, const int64_t* __restrict__ rowP,
     const int32_t* __restrict__ colP, const typename C2<R>::T* __restrict__ LP,
-    const typename C2<R>::T* __restrict__ q, const R* __restrict__ fdT,
-    const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ j, int nt, int ne,
-    int nx, int ny, R k0, int mode, typename C2<R>::T* __restrict__ p, typename C2<R>::T* __restrict__ y) {
+    const typename C2<R>::T* __restrict__ q, int nt, int nx, int ny,
+    typename C2<R>::T* __restrict__ out) {
   typedef typename C2<R>::T V;
   const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= nt) return;
@@ -159,25 +276,12 @@ __global__ void __launch_bounds__(256) k_rows_t(
   }
   for (int64_t i = rowP[t] + lane; i < rowP[t + 1]; i += 32) cfma(acc, LP[i], q[colP[i]]);
   acc = warp_sum(acc);
-  if (lane == 0) {
-    if (mode == 0) {
-      y[t] = acc;
-    } else {
-      p[t] = acc;
-      V s = jk0(q[t], k0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const V jj = j[tedge[3 * t + i]];
-        const R c = fdT[3 * t + i];
-        s.x += c * jj.x;
-        s.y += c * jj.y;
-      }
-      y[ne + t] = s;
-    }
-  }
+  if (lane == 0) out[t] = acc;
 }
 
-// mode 0: y[m] = a_m (L^A alone); mode 1: y1_m = j k0 a_m + (I_x e)_m - ((F D)^T p)_m
+// mode 0: y[m] = a_m (L^A alone).
+// mode 1 (system), rows m < ne:  y1_m = j k0 a_m + (I_x e)_m - ((F D)^T p)_m
+//                  rows ne + t:  y2_t = (F D j)_t + j k0 q_t
 template <typename R>
 __global__ void __launch_bounds__(256) k_rows_e(
     const R* __restrict__ WA, const int32_t* __restrict__ node,
@@ -187,9 +291,25 @@ __global__ void __launch_bounds__(256) k_rows_e(
     const int32_t* __restrict__ ixcol, const typename C2<R>::T* __restrict__ e,
     const R* __restrict__ fdE, const int32_t* __restrict__ et,
     const typename C2<R>::T* __restrict__ p, int ne, int nx, int ny, R k0, int mode,
-    typename C2<R>::T* __restrict__ y) {
+    typename C2<R>::T* __restrict__ y, int nt, const R* __restrict__ fdT,
+    const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ q) {
   typedef typename C2<R>::T V;
   const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (mode == 1 && m >= ne && m < ne + nt) {
+    if (lane == 0) {
+      const int t = m - ne;
+      V s = jk0(q[t], k0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V jj = j[tedge[3 * t + i]];
+        const R c = fdT[3 * t + i];
+        s.x += c * jj.x;
+        s.y += c * jj.y;
+      }
+      y[m] = s;
+    }
+    return;
+  }
   if (m >= ne) return;
   V acc = czero<V>();
   if (lane < 27) {
@@ -240,35 +360,40 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
   const int ne = c->ne, nt = c->nt, nx = c->gn[0], ny = c->gn[1];
   const int64_t ng = c->ng;
   const R k0 = (R)c->k0;
+  const int64_t P3 = (int64_t)c->gp[0] * c->gp[1] * c->gp[2];
   if (which == AIM_OP_LA) {
-    BEM_CUDA(cudaMemsetAsync(b.sigma, 0, 3 * ng * sizeof(V), s));
-    k_scatter_e<R><<<nb((int64_t)ne * 27, 256), 256, 0, s>>>(b.WA, c->d_nodeE, x, b.sigma, ne, nx, ny, ng);
-    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, s));
+    k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, x, b.sigma, ng);
+    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
                                           x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
-                                          nx, ny, k0, 0, y);
+                                          nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr);
   } else if (which == AIM_OP_LPHI) {
     V* sq = b.sigma + 3 * ng;
-    BEM_CUDA(cudaMemsetAsync(sq, 0, ng * sizeof(V), s));
-    k_scatter_t<R><<<nb((int64_t)nt * 27, 256), 256, 0, s>>>(b.WP, c->d_nodeT, x, sq, nt, nx, ny);
-    BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, s));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x,
-                                          b.fdT, c->d_tedge, nullptr, nt, ne, nx, ny, k0, 0, nullptr, y);
+    k_project_t<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowT, c->d_pcolT, b.WPT, x, sq, ng);
+    BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, s));
+    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x, nt,
+                                          nx, ny, y);
   } else if (which == AIM_OP_SYSTEM) {
+    // Two branches: the charge branch p = L^Phi q does not depend on the internal problem and
+    // runs on the side stream while the GEMVs stream Z and Y_eq.
     const V* h = x;
     const V* q = x + ne;
-    BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Z, h, b.e, 1, ne, nullptr, s));
-    BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Y, b.e, b.j, 1, ne, h, s));
-    BEM_CUDA(cudaMemsetAsync(b.sigma, 0, 4 * ng * sizeof(V), s));
-    k_scatter_e<R><<<nb((int64_t)ne * 27, 256), 256, 0, s>>>(b.WA, c->d_nodeE, b.j, b.sigma, ne, nx, ny, ng);
-    k_scatter_t<R><<<nb((int64_t)nt * 27, 256), 256, 0, s>>>(b.WP, c->d_nodeT, q, b.sigma + 3 * ng, nt, nx, ny);
-    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 4, s));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, b.sigma + 3 * ng, c->d_rowP, c->d_colP,
-                                          b.LP, q, b.fdT, c->d_tedge, b.j, nt, ne, nx, ny, k0, 1,
-                                          b.p, y);
-    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
-                                          b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p, ne, nx,
-                                          ny, k0, 1, y);
+    V* sq = b.sigma + 3 * ng;
+    BEM_CUDA(cudaEventRecord(c->ev_fork, s));
+    BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    k_project_t<R><<<nb(ng, 256), 256, 0, c->side>>>(c->d_prowT, c->d_pcolT, b.WPT, q, sq, ng);
+    BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
+    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
+                                                nt, nx, ny, b.p);
+    BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    BEM_TRY(run_gemv_plan<R>(c->gplan, b.Z, h, b.e, 1, ne, nullptr, s));
+    BEM_TRY(run_gemv_plan<R>(c->gplan, b.Y, b.e, b.j, 1, ne, h, s));
+    k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, b.j, b.sigma, ng);
+    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
+    BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+    k_rows_e<R><<<nb(ne + nt, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
+                                               b.LA, b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p,
+                                               ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q);
   } else {
     set_error("aim_matvec: unknown operator %d", which);
     return BEM_EINVAL;
@@ -279,12 +404,69 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
 template int matvec<float>(aim_ctx*, int, const void*, void*, cudaStream_t);
 template int matvec<double>(aim_ctx*, int, const void*, void*, cudaStream_t);
 
+int init_streams(aim_ctx* c) {
+  BEM_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  BEM_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  BEM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  BEM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  return BEM_OK;
+}
+
+void release_streams(aim_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  c->ev_fork = c->ev_join = nullptr;
+  c->side = c->cap = nullptr;
+}
+
+// The matvec is ~12 kernels; replaying it as one CUDA graph removes the per-launch host cost.
+// Graphs are captured on the context's private stream (the caller's stream may be the legacy
+// default stream, which cannot be captured) and keyed by operator, precision and buffers.
+template <typename R>
+int matvec_graph(aim_ctx* c, int which, const void* x, void* y, cudaStream_t s) {
+  if (!c->use_graphs) return matvec<R>(c, which, x, y, s);
+  aim_ctx::GKey key{which, (int)sizeof(R), x, y};
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    if (c->graphs.size() >= 64) {
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+      c->graphs.clear();
+    }
+    BEM_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = matvec<R>(c, which, x, y, c->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (rc != BEM_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (rc == BEM_OK) set_error("matvec capture: %s", cudaGetErrorString(e));
+      return rc != BEM_OK ? rc : BEM_ECUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      set_error("matvec graph instantiate: %s", cudaGetErrorString(e));
+      return BEM_ECUDA;
+    }
+    it = c->graphs.emplace(key, ex).first;
+  }
+  BEM_CUDA(cudaGraphLaunch(it->second, s));
+  return BEM_OK;
+}
+template int matvec_graph<float>(aim_ctx*, int, const void*, void*, cudaStream_t);
+template int matvec_graph<double>(aim_ctx*, int, const void*, void*, cudaStream_t);
+
 template <typename R>
 int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStream_t s) {
   typedef typename C2<R>::T V;
   PrecBuf<R>& b = buf<R>(c);
-  BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
-  if (heqv) BEM_TRY(run_gemv<R>(c->d_tasks, c->ntasks, b.Y, (const V*)ev, (V*)heqv, nrhs, c->ne, nullptr, s));
+  BEM_TRY(run_gemv_plan<R>(c->gplan, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
+  if (heqv) BEM_TRY(run_gemv_plan<R>(c->gplan, b.Y, (const V*)ev, (V*)heqv, nrhs, c->ne, nullptr, s));
   return BEM_OK;
 }
 template int internal<float>(aim_ctx*, const void*, void*, void*, int, cudaStream_t);
@@ -294,7 +476,7 @@ template <typename R>
 int conv(aim_ctx* c, const void* sigma, void* phi, int ncomp, cudaStream_t s) {
   typedef typename C2<R>::T V;
   PrecBuf<R>& b = buf<R>(c);
-  return fft_conv<R>(c, b, (const V*)sigma, (V*)phi, ncomp, s);
+  return fft_conv<R>(c, b, (const V*)sigma, (V*)phi, ncomp, b.ws, s);
 }
 template int conv<float>(aim_ctx*, const void*, void*, int, cudaStream_t);
 template int conv<double>(aim_ctx*, const void*, void*, int, cudaStream_t);

@@ -117,6 +117,60 @@ void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>&
   }
 }
 
+// The persistent GEMV plan. On the GPU a task (one object's block) is moldable at the
+// granularity of a single row, so the ideal schedule of Sec. III-C (total work spread evenly,
+// C_max = C_ideal up to one row) is reachable directly: the rows of all blocks, in order, are
+// cut into ncta contiguous ranges of equal matrix bytes, one per resident CTA. (Part_Schedule
+// as written stops at the first increment that does not shorten the schedule; with several
+// equal-size objects every single-task increment ties, so it would leave most blocks on one or
+// two processors.) ratio reports the longest CTA's bytes over the mean.
+void build_gemv_plan(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
+                     const std::vector<int32_t>& ld, int ncta, std::vector<RowInfo>* rows,
+                     std::vector<int2>* segs, std::vector<int32_t>* cta_seg, double* ratio) {
+  const int nb = (int)n.size();
+  std::vector<int32_t> xoff(nb);
+  int32_t tot = 0;
+  double bytes = 0;
+  for (int i = 0; i < nb; ++i) {
+    xoff[i] = tot;
+    tot += n[i];
+    bytes += (double)n[i] * n[i];
+  }
+  rows->resize(tot);
+  for (int i = 0; i < nb; ++i)
+    for (int r = 0; r < n[i]; ++r) {
+      RowInfo& ri = (*rows)[xoff[i] + r];
+      ri.aoff = off[i] + (int64_t)r * ld[i];
+      ri.n = n[i];
+      ri.xoff = xoff[i];
+    }
+  segs->clear();
+  cta_seg->assign(ncta + 1, 0);
+  const double per = bytes / ncta;
+  double acc = 0, worst = 0, cur = 0;
+  int r0 = 0, p = 0;
+  for (int m = 0; m < tot; ++m) {
+    const double w = (*rows)[m].n;
+    acc += w;
+    cur += w;
+    // close range p once the running total reaches its share (the last CTA takes the rest)
+    if (p < ncta - 1 && acc >= per * (p + 1)) {
+      segs->push_back(make_int2(r0, m + 1));
+      worst = std::max(worst, cur);
+      cur = 0;
+      r0 = m + 1;
+      ++p;
+      (*cta_seg)[p] = (int32_t)segs->size();
+    }
+  }
+  if (r0 < tot) {
+    segs->push_back(make_int2(r0, tot));
+    worst = std::max(worst, cur);
+  }
+  for (int q = p + 1; q <= ncta; ++q) (*cta_seg)[q] = (int32_t)segs->size();
+  *ratio = per > 0 ? worst / per : 1.0;
+}
+
 }  // namespace bem
 
 extern "C" double bem_part_schedule(int ntask, const double* W, int P, int p_cutoff, int32_t* Pi) {

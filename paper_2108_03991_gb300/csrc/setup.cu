@@ -1,5 +1,6 @@
 // Device set-up (FP64): projection stencils, the dense internal matrices Z_i and Y_i,eq, and
 // the precorrected near-region matrices L^A_NR and L^Phi_NR.
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -181,6 +182,20 @@ __global__ void k_weights_t(DGeo g, int ne, int nt, double* W64, float* W32) {
   }
   W64[(int64_t)t * 27 + k] = acc;
   W32[(int64_t)t * 27 + k] = (float)acc;
+}
+
+// weights in CSR order: WT[e][c] = W[src[e]][c][k[e]] (ncomp = 3 for RWG, 1 for pulses)
+__global__ void k_weights_csr(const int32_t* src, const int32_t* kk, const double* W, int64_t nent,
+                              int ncomp, double* T64, float* T32) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nent) return;
+  const int64_t m = src[e];
+  const int k = kk[e];
+  for (int cc = 0; cc < ncomp; ++cc) {
+    double w = W[m * 27 * ncomp + cc * 27 + k];
+    T64[e * ncomp + cc] = w;
+    T32[e * ncomp + cc] = (float)w;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -617,6 +632,41 @@ int setup_device(aim_ctx* c) {
     }
     BEM_TRY(upload(c, &c->d_nodeE, nodeE.data(), nodeE.size()));
     BEM_TRY(upload(c, &c->d_nodeT, nodeT.data(), nodeT.size()));
+    // P^T in grid-node-major CSR form (counting sort by node; sources ascending per node)
+    auto build = [&](const std::vector<int32_t>& node, int32_t** d_row, int32_t** d_col,
+                     int32_t** d_k) -> int {
+      const int ns = (int)node.size();
+      const int nx = c->gn[0], ny = c->gn[1];
+      std::vector<int32_t> row(c->ng + 1, 0), col(27 * (size_t)ns), kk(27 * (size_t)ns);
+      auto nd = [&](int m, int k) {
+        return node[m] + ((k / 9 - 1) * ny + ((k / 3) % 3 - 1)) * nx + (k % 3 - 1);
+      };
+      for (int m = 0; m < ns; ++m)
+        for (int k = 0; k < 27; ++k) row[nd(m, k) + 1]++;
+      for (int64_t i = 0; i < c->ng; ++i) row[i + 1] += row[i];
+      std::vector<int32_t> fill(row.begin(), row.end() - 1);
+      for (int m = 0; m < ns; ++m)
+        for (int k = 0; k < 27; ++k) {
+          int32_t p = fill[nd(m, k)]++;
+          col[p] = m;
+          kk[p] = k;
+        }
+      BEM_TRY(upload(c, d_row, row.data(), row.size()));
+      BEM_TRY(upload(c, d_col, col.data(), col.size()));
+      BEM_TRY(upload(c, d_k, kk.data(), kk.size()));
+      return BEM_OK;
+    };
+    int32_t *d_kE = nullptr, *d_kT = nullptr;
+    BEM_TRY(build(nodeE, &c->d_prowE, &c->d_pcolE, &d_kE));
+    BEM_TRY(build(nodeT, &c->d_prowT, &c->d_pcolT, &d_kT));
+    const int64_t nE = 27 * (int64_t)c->ne, nT = 27 * (int64_t)c->nt;
+    BEM_TRY(dalloc_t(c, &c->f64.WAT, 3 * nE));
+    BEM_TRY(dalloc_t(c, &c->f32.WAT, 3 * nE));
+    BEM_TRY(dalloc_t(c, &c->f64.WPT, nT));
+    BEM_TRY(dalloc_t(c, &c->f32.WPT, nT));
+    k_weights_csr<<<nblk(nE, 256), 256>>>(c->d_pcolE, d_kE, c->f64.WA, nE, 3, c->f64.WAT, c->f32.WAT);
+    k_weights_csr<<<nblk(nT, 256), 256>>>(c->d_pcolT, d_kT, c->f64.WP, nT, 1, c->f64.WPT, c->f32.WPT);
+    BEM_CUDA(cudaGetLastError());
   }
   // sparse tables
   std::vector<int32_t> ixcol;
@@ -641,6 +691,7 @@ int setup_device(aim_ctx* c) {
   // grid Green's function
   BEM_TRY(make_twiddles<float>(c, c->f32));
   BEM_TRY(make_twiddles<double>(c, c->f64));
+  BEM_TRY(fft_init_attrs());
   BEM_TRY(make_ghat(c));
   // GEMV work list
   {
@@ -652,6 +703,17 @@ int setup_device(aim_ctx* c) {
     build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, &c->tasks);
     c->ntasks = (int)c->tasks.size();
     BEM_TRY(upload(c, &c->d_tasks, c->tasks.data(), c->tasks.size()));
+    // persistent plan: one CTA per resident slot, rows of the Part_Schedule (Sec. III-C)
+    std::vector<RowInfo> rows;
+    std::vector<int2> segs;
+    std::vector<int32_t> cseg;
+    const int ncta = nsm * kGemvCtasPerSm;
+    build_gemv_plan(n, c->zoff, c->zld, ncta, &rows, &segs, &cseg, &c->gplan.cmax_over_ideal);
+    BEM_TRY(upload(c, &c->gplan.rows, rows.data(), rows.size()));
+    BEM_TRY(upload(c, &c->gplan.segs, segs.data(), segs.size()));
+    BEM_TRY(upload(c, &c->gplan.cta_seg, cseg.data(), cseg.size()));
+    c->gplan.ncta = ncta;
+    c->gplan.nrows = (int)rows.size();
   }
   // workspaces
   const size_t P = (size_t)c->gp[0] * c->gp[1] * c->gp[2];
@@ -670,10 +732,267 @@ int setup_device(aim_ctx* c) {
   BEM_TRY(dalloc_t(c, &c->f64.p, c->nt));
   BEM_TRY(dalloc_t(c, &c->f32.xin, ntot));
   BEM_TRY(dalloc_t(c, &c->f32.yout, ntot));
+  BEM_TRY(dalloc_t(c, &c->f64.xin, ntot));
+  BEM_TRY(dalloc_t(c, &c->f64.yout, ntot));
+  BEM_TRY(init_streams(c));
   BEM_CUDA(cudaDeviceSynchronize());
   c->geo_store = new DGeo(g);
   return BEM_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// block-diagonal preconditioner: A_ii, the system of Eq. (AEFIEoutJ) restricted to object i's
+// unknowns [h_i; q_i] with its exact dense L^A_ii and L^Phi_ii,
+//   A_ii = [[j k0 L^A + (-j k0 L^A Y + I_x) Z, -(F D)^T L^Phi], [(F D)(I - Y Z), j k0 I]],
+// inverted explicitly at set-up; the solve applies blockdiag(A_ii^{-1}) on the right.
+// ---------------------------------------------------------------------------------------
+__global__ void k_obj_A(DGeo g, int e0, int n, double k0, double2* LAc) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  int i = (int)(idx % n), j = (int)(idx / n);
+  double2 L;
+  rwg_pair(g, e0 + i, e0 + j, k0, 0.0, false, false, &L, nullptr);
+  LAc[idx] = L;
+}
+
+__global__ void k_obj_P(DGeo g, int t0, int m, double k0, double2* LPc) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * m) return;
+  int i = (int)(idx % m), j = (int)(idx / m);
+  Tri T, S;
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + i, &T);
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + j, &S);
+  Moments M;
+  pair_moments(T, S, k0, 0.0, false, false, true, &M);
+  LPc[idx] = M.M0;
+}
+
+// packed row-major (leading dimension ld) -> column-major n x n
+__global__ void k_unpack(const double2* P, int n, int ld, double2* C) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  int r = (int)(idx % n), col = (int)(idx / n);
+  C[idx] = P[(int64_t)r * ld + col];
+}
+
+// dense I_x restricted to the object (column-major), from the 4-per-row sparse table
+__global__ void k_dense_ix(const int32_t* ixcol, const double* ixval, int e0, int n, double2* C) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < 4; ++q) {
+    int col = ixcol[4 * (e0 + i) + q] - e0;
+    if (col >= 0 && col < n) C[i + (int64_t)col * n] = make_double2(ixval[4 * (e0 + i) + q], 0.0);
+  }
+}
+
+// dense F D restricted to the object (m x n, column-major)
+__global__ void k_dense_fd(const int32_t* tedge, const double* fdT, int t0, int m, int e0, int n,
+                           double2* C) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  for (int q = 0; q < 3; ++q) {
+    int col = tedge[3 * (t0 + t) + q] - e0;
+    if (col >= 0 && col < n) C[t + (int64_t)col * m] = make_double2(fdT[3 * (t0 + t) + q], 0.0);
+  }
+}
+
+// A_full (N = n + m, column-major) from A11 (n x n), A12 (n x m), A21 (m x n), A22 = j k0 I
+__global__ void k_bd_assemble(const double2* A11, const double2* A12, const double2* A21, int n,
+                              int m, double k0, double2* A) {
+  const int N = n + m;
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)N * N) return;
+  int r = (int)(idx % N), col = (int)(idx / N);
+  double2 v;
+  if (r < n && col < n) v = A11[r + (int64_t)col * n];
+  else if (r < n) v = A12[r + (int64_t)(col - n) * n];
+  else if (col < n) v = A21[(r - n) + (int64_t)col * m];
+  else v = make_double2(0.0, r == col ? k0 : 0.0);
+  A[idx] = v;
+}
+
+__global__ void k_identity(double2* A, int N) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)N * N) return;
+  A[idx] = make_double2((idx % N) == (idx / N) ? 1.0 : 0.0, 0.0);
+}
+
+struct BlasHandle {
+  cublasHandle_t h = nullptr;
+  ~BlasHandle() { if (h) cublasDestroy(h); }
+};
+
+static int zgemm(cublasHandle_t h, cublasOperation_t ta, int M, int N, int K, double2 alpha,
+                 const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C, int ldc) {
+  cuDoubleComplex al = make_cuDoubleComplex(alpha.x, alpha.y), be = make_cuDoubleComplex(beta.x, beta.y);
+  if (cublasZgemm(h, ta, CUBLAS_OP_N, M, N, K, &al, (const cuDoubleComplex*)A, lda,
+                  (const cuDoubleComplex*)B, ldb, &be, (cuDoubleComplex*)C, ldc) != CUBLAS_STATUS_SUCCESS) {
+    set_error("cublasZgemm failed");
+    return BEM_ECUDA;
+  }
+  return BEM_OK;
+}
+
+int setup_precond(aim_ctx* c) {
+  if (c->pc_ready) return BEM_OK;
+  const DGeo& g = *reinterpret_cast<const DGeo*>(c->geo_store);
+  const int nobj = c->nobj;
+  std::vector<int32_t> N(nobj), perm;
+  std::vector<int64_t> off(nobj);
+  std::vector<int32_t> ld(nobj);
+  int64_t o = 0;
+  int nmax = 0, mmax = 0, Nmax = 0;
+  for (int i = 0; i < nobj; ++i) {
+    const int n = c->e1[i] - c->e0[i], m = c->t1[i] - c->t0[i];
+    N[i] = n + m;
+    ld[i] = (int32_t)round_up(N[i], 4);
+    off[i] = o;
+    o += (int64_t)N[i] * ld[i];
+    nmax = std::max(nmax, n);
+    mmax = std::max(mmax, m);
+    Nmax = std::max(Nmax, N[i]);
+    for (int k = 0; k < n; ++k) perm.push_back(c->e0[i] + k);
+    for (int k = 0; k < m; ++k) perm.push_back(c->ne + c->t0[i] + k);
+  }
+  BEM_TRY(dalloc_t(c, &c->pc64, o));
+  BEM_TRY(dalloc_t(c, &c->pc32, o));
+  BEM_TRY(upload(c, &c->d_pcperm, perm.data(), perm.size()));
+  for (int k = 0; k < 2; ++k) {
+    BEM_TRY(dalloc_t(c, &c->pcw32[k], perm.size()));
+    BEM_TRY(dalloc_t(c, &c->pcw64[k], perm.size()));
+  }
+  // scratch (released at the end)
+  const size_t nn = (size_t)nmax * nmax, nm = (size_t)nmax * mmax, mm = (size_t)mmax * mmax,
+               NN = (size_t)Nmax * Nmax;
+  double2 *LA, *LP, *Zc, *Yc, *Ix, *FD, *T1, *T2, *A12, *A21, *Af, *X;
+  double2** bufs[] = {&LA, &LP, &Zc, &Yc, &Ix, &FD, &T1, &T2, &A12, &A21, &Af, &X};
+  size_t sizes[] = {nn, mm, nn, nn, nn, nm, nn, nn, nm, nm, NN, NN};
+  std::vector<void*> scratch;
+  int rc = BEM_OK;
+  for (int k = 0; k < 12 && rc == BEM_OK; ++k) {
+    cudaError_t e = cudaMalloc((void**)bufs[k], sizes[k] * sizeof(double2) + 16);
+    if (e != cudaSuccess) { set_error("preconditioner scratch: %s", cudaGetErrorString(e)); rc = BEM_ENOMEM; }
+    else scratch.push_back(*bufs[k]);
+  }
+  int64_t* ipiv = nullptr;
+  int* dinfo = nullptr;
+  if (rc == BEM_OK && (cudaMalloc(&ipiv, Nmax * sizeof(int64_t)) != cudaSuccess ||
+                       cudaMalloc(&dinfo, sizeof(int)) != cudaSuccess)) {
+    set_error("preconditioner scratch allocation failed");
+    rc = BEM_ENOMEM;
+  }
+  SolverScratch ss;
+  BlasHandle bh;
+  void* dwork = nullptr;
+  size_t dwsize = 0;
+  std::vector<char> hwork;
+  if (rc == BEM_OK && (cusolverDnCreate(&ss.h) != CUSOLVER_STATUS_SUCCESS ||
+                       cusolverDnCreateParams(&ss.p) != CUSOLVER_STATUS_SUCCESS ||
+                       cublasCreate(&bh.h) != CUBLAS_STATUS_SUCCESS)) {
+    set_error("cuSOLVER/cuBLAS handle creation failed");
+    rc = BEM_ECUDA;
+  }
+  const double k0 = c->k0;
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  for (int i = 0; i < nobj && rc == BEM_OK; ++i) {
+    const int e0 = c->e0[i], t0 = c->t0[i];
+    const int n = c->e1[i] - e0, m = c->t1[i] - t0, Nt = n + m;
+    k_obj_A<<<nblk((int64_t)n * n, 128), 128>>>(g, e0, n, k0, LA);
+    k_obj_P<<<nblk((int64_t)m * m, 128), 128>>>(g, t0, m, k0, LP);
+    k_unpack<<<nblk((int64_t)n * n, 256), 256>>>(c->f64.Z + c->zoff[i], n, c->zld[i], Zc);
+    k_unpack<<<nblk((int64_t)n * n, 256), 256>>>(c->f64.Y + c->zoff[i], n, c->zld[i], Yc);
+    cudaMemset(Ix, 0, (size_t)n * n * sizeof(double2));
+    cudaMemset(FD, 0, (size_t)m * n * sizeof(double2));
+    k_dense_ix<<<nblk(n, 128), 128>>>(c->d_ixcol, c->f64.ix, e0, n, Ix);
+    k_dense_fd<<<nblk(m, 128), 128>>>(c->d_tedge, c->f64.fdT, t0, m, e0, n, FD);
+    if (cudaGetLastError() != cudaSuccess) { set_error("preconditioner kernels failed"); rc = BEM_ECUDA; break; }
+    // T1 = L^A Y ; T2 = I_x - j k0 T1 ; T1 = T2 Z ; T1 += j k0 L^A  -> A11 in T1
+    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, one, LA, n, Yc, n, zero, T1, n);
+    if (rc) break;
+    BEM_CUDA(cudaMemcpy(T2, Ix, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice));
+    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, make_double2(0, -k0), LA, n, Yc, n, one, T2, n);
+    if (rc) break;
+    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, one, T2, n, Zc, n, zero, T1, n);
+    if (rc) break;
+    // T1 += j k0 L^A (as a GEMM with the identity would waste work; use axpy via cuBLAS)
+    {
+      cuDoubleComplex al = make_cuDoubleComplex(0, k0);
+      if (cublasZaxpy(bh.h, n * n, &al, (const cuDoubleComplex*)LA, 1, (cuDoubleComplex*)T1, 1) !=
+          CUBLAS_STATUS_SUCCESS) { set_error("cublasZaxpy failed"); rc = BEM_ECUDA; break; }
+    }
+    // A12 = -(F D)^T L^Phi   (n x m)
+    rc = zgemm(bh.h, CUBLAS_OP_T, n, m, m, make_double2(-1, 0), FD, m, LP, m, zero, A12, n);
+    if (rc) break;
+    // A21 = F D - F D (Y Z)  (m x n): T2 = Y Z ; A21 = FD ; A21 -= FD T2
+    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, one, Yc, n, Zc, n, zero, T2, n);
+    if (rc) break;
+    BEM_CUDA(cudaMemcpy(A21, FD, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToDevice));
+    rc = zgemm(bh.h, CUBLAS_OP_N, m, n, n, make_double2(-1, 0), FD, m, T2, n, one, A21, m);
+    if (rc) break;
+    k_bd_assemble<<<nblk((int64_t)Nt * Nt, 256), 256>>>(T1, A12, A21, n, m, k0, Af);
+    k_identity<<<nblk((int64_t)Nt * Nt, 256), 256>>>(X, Nt);
+    rc = lu_solve(ss, Af, X, Nt, ipiv, dinfo, &dwork, &dwsize, &hwork);
+    if (rc) break;
+    k_store_block<<<nblk((int64_t)Nt * ld[i], 256), 256>>>(X, Nt, ld[i], one, c->pc64 + off[i],
+                                                            c->pc32 + off[i]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("preconditioner store: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; }
+  }
+  cudaDeviceSynchronize();
+  for (void* p : scratch) cudaFree(p);
+  if (ipiv) cudaFree(ipiv);
+  if (dinfo) cudaFree(dinfo);
+  if (dwork) cudaFree(dwork);
+  if (rc != BEM_OK) return rc;
+  // persistent GEMV plan over the object-major blocks
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<RowInfo> rows;
+  std::vector<int2> segs;
+  std::vector<int32_t> cseg;
+  const int ncta = nsm * kGemvCtasPerSm;
+  build_gemv_plan(N, off, ld, ncta, &rows, &segs, &cseg, &c->pcplan.cmax_over_ideal);
+  BEM_TRY(upload(c, &c->pcplan.rows, rows.data(), rows.size()));
+  BEM_TRY(upload(c, &c->pcplan.segs, segs.data(), segs.size()));
+  BEM_TRY(upload(c, &c->pcplan.cta_seg, cseg.data(), cseg.size()));
+  c->pcplan.ncta = ncta;
+  c->pcplan.nrows = (int)rows.size();
+  c->pc_ready = true;
+  return BEM_OK;
+}
+
+template <typename V>
+__global__ void k_perm_gather(const int32_t* perm, const V* x, V* xp, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xp[i] = x[perm[i]];
+}
+template <typename V>
+__global__ void k_perm_scatter(const int32_t* perm, const V* yp, V* y, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[perm[i]] = yp[i];
+}
+
+// u = M_bd r (system ordering), in precision R
+template <typename R>
+int precond_apply(aim_ctx* c, const void* rv, void* uv, cudaStream_t s) {
+  typedef typename C2<R>::T V;
+  if (!c->pc_ready) {
+    set_error("block-diagonal preconditioner not built");
+    return BEM_EINVAL;
+  }
+  const int n = c->ne + c->nt;
+  V* w0 = sizeof(R) == 4 ? (V*)c->pcw32[0] : (V*)c->pcw64[0];
+  V* w1 = sizeof(R) == 4 ? (V*)c->pcw32[1] : (V*)c->pcw64[1];
+  const V* M = sizeof(R) == 4 ? (const V*)c->pc32 : (const V*)c->pc64;
+  k_perm_gather<V><<<nblk(n, 256), 256, 0, s>>>(c->d_pcperm, (const V*)rv, w0, n);
+  BEM_TRY(run_gemv_plan<R>(c->pcplan, M, w0, w1, 1, n, nullptr, s));
+  k_perm_scatter<V><<<nblk(n, 256), 256, 0, s>>>(c->d_pcperm, w1, (V*)uv, n);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int precond_apply<float>(aim_ctx*, const void*, void*, cudaStream_t);
+template int precond_apply<double>(aim_ctx*, const void*, void*, cudaStream_t);
 
 int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
                    cudaStream_t st) {
