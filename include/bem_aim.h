@@ -91,8 +91,9 @@ void aim_destroy(aim_ctx* ctx);
 const char* bem_last_error(void);
 
 /* Sizes: info[0]=N_E, [1]=N_T, [2]=nobj, [3..5]=grid n, [6..8]=padded FFT lengths,
- * [9]=nnz(L^A_NR), [10]=nnz(L^Phi_NR), [11]=bytes of Z and Y (C32), [12]=max n_i.
- * Writes min(n, 13) entries. */
+ * [9]=nnz(L^A_NR), [10]=nnz(L^Phi_NR), [11]=bytes of Z and Y (C32), [12]=max n_i,
+ * [13]=CTAs of the block GEMV launch, [14]=column parts per row (both chosen by the set-up
+ * autotuner). Writes min(n, 15) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)
@@ -156,7 +157,8 @@ typedef struct {
   int32_t restart;     /* Krylov subspace size before restart, 1..512 */
   int32_t max_iter;
   int32_t prec_mode;
-  int32_t precond;     /* 0 = none, 1 = block-diagonal (bem_precond_apply), on the right */
+  int32_t precond;     /* 0 = none, 1 = block-diagonal (bem_precond_apply), 2 = block-diagonal
+                          plus the learned correction (bem_net_apply); on the right */
   double time_limit_s; /* <= 0: none */
 } bem_solve_opts;
 
@@ -180,6 +182,31 @@ typedef struct {
  * reaches tol, BEM_ENOCONV (positive) when max_iter or the time limit stops it first. */
 int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
               bem_solve_info* info, void* stream);
+
+/* Learned correction of the preconditioner (an extension; not in the paper). A 4-layer 3-D
+ * convolutional net on the AIM grid (3x3x3 kernels, zero padding, no biases, ReLU between
+ * layers, channels 8-16-16-16-8; BF16 weights and activations, FP32 sums) maps the projected
+ * residual P r (Re/Im of the four grid components, scaled by their RMS) to a grid correction:
+ *   M(r) = M_bd r + W net(P r),  W = P^T (Sec. III-A item 1 operators).
+ * Weight layout: layer after layer, each [C_out][C_in][3][3][3] (dz, dy, dx), FP32; 20736 in all.
+ * bem_net_init: He-normal weights from a splitmix64 counter hash of seed.
+ * bem_net_weights: copy weights from (set = 1) or to (set = 0) the HOST array w of n floats;
+ *   with w = NULL returns the number of weights.
+ * bem_net_train: `steps` Adam steps of lr on batches of `batch` pairs r = A x (x complex normal
+ *   from the hash of seed), minimising |W net(P r) - (x - M_bd r)|^2 / |x - M_bd r|^2; losses
+ *   (HOST, may be NULL) receives the mean loss of each step. Builds M_bd on first use.
+ * bem_net_apply: z = M_bd r + W net(P r) for complex FP32 device vectors of N_E + N_T.
+ * bem_convnet_run: the network alone on an nx x ny x nz grid, for verification: x [8][ng] FP32
+ *   device input (rounded to BF16), w_host FP32 weights (rounded to BF16), out [8][ng] FP32
+ *   device output; when gout [8][ng] is given, the backward pass writes gw_host (FP32 host,
+ *   may be NULL) and gx [8][ng] (device, may be NULL). Synchronous on stream. */
+int bem_net_init(aim_ctx* ctx, uint64_t seed);
+int64_t bem_net_weights(aim_ctx* ctx, float* w, int64_t n, int set);
+int bem_net_train(aim_ctx* ctx, int steps, int batch, float lr, uint64_t seed, float* losses,
+                  void* stream);
+int bem_net_apply(aim_ctx* ctx, const void* r, void* z, void* stream);
+int bem_convnet_run(int nx, int ny, int nz, const float* w_host, const float* x, const float* gout,
+                    float* out, float* gw_host, float* gx, void* stream);
 
 /* Work lists for uneven block-diagonal products (Sec. III-C): LPT (Alg. 1) and the modified
  * Part_Schedule (Alg. 2). W: HOST task weights sorted in decreasing order (W_i = n_i^2);

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbem_aim.
 SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec",
            "internal_apply", "aim_conv", "bem_blockdiag_gemv", "aim_export",
            "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule", "bem_blockdiag_gemv_noalloc",
-           "bem_precond_apply"]
+           "bem_precond_apply", "bem_net_init", "bem_net_weights", "bem_net_train",
+           "bem_net_apply", "bem_convnet_run"]
 
 
 class BemError(RuntimeError):
@@ -81,6 +82,13 @@ def lib():
         L.bem_rhs_plane_wave.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.c_int, vp]
         L.bem_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
         L.bem_precond_apply.argtypes = [vp, vp, vp, C.c_int, vp]
+        fp = C.POINTER(C.c_float)
+        L.bem_net_init.argtypes = [vp, C.c_uint64]
+        L.bem_net_weights.argtypes = [vp, fp, i64, C.c_int]
+        L.bem_net_weights.restype = i64
+        L.bem_net_train.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.c_uint64, fp, vp]
+        L.bem_net_apply.argtypes = [vp, vp, vp, vp]
+        L.bem_convnet_run.argtypes = [C.c_int, C.c_int, C.c_int, fp, vp, vp, vp, fp, vp, vp]
         L.bem_part_schedule.argtypes = [C.c_int, C.POINTER(d), C.c_int, C.c_int, C.POINTER(i32)]
         L.bem_part_schedule.restype = d
         _LIB = L
@@ -140,6 +148,25 @@ def blockdiag_gemv_noalloc(sizes, A, x, y, nrhs=1, prec=BEM_C32):
     return y
 
 
+def convnet_run(w, x, gout=None):
+    """The learned-correction network alone (BF16 weights/activations, FP32 sums).
+    w: numpy float32 weights (all layers); x: CUDA float32 [8, nz, ny, nx]; gout: optional
+    CUDA float32 [8, nz, ny, nx]. Returns out (CUDA), gw (numpy or None), gx (CUDA or None)."""
+    import torch
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    _, nz, ny, nx = x.shape
+    out = torch.empty_like(x)
+    gw = np.zeros_like(w) if gout is not None else None
+    gx = torch.empty_like(x) if gout is not None else None
+    fp = C.POINTER(C.c_float)
+    _check(lib().bem_convnet_run(nx, ny, nz, w.ctypes.data_as(fp), _ptr(x, torch.float32),
+                                 _ptr(gout, torch.float32) if gout is not None else None,
+                                 _ptr(out, torch.float32),
+                                 gw.ctypes.data_as(fp) if gw is not None else None,
+                                 _ptr(gx, torch.float32) if gx is not None else None, _stream()))
+    return out, gw, gx
+
+
 def pack_blocks(blocks, dtype):
     """Row-major blocks with leading dimension n rounded up to 4, concatenated (numpy)."""
     out = []
@@ -171,8 +198,8 @@ class Context:
         h = C.c_void_p()
         _check(L.aim_setup(C.byref(m), C.byref(g), float(freq), C.byref(h)))
         self.h = h
-        info = (C.c_int64 * 13)()
-        _check(L.aim_info(h, info, 13))
+        info = (C.c_int64 * 15)()
+        _check(L.aim_info(h, info, 15))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -181,6 +208,7 @@ class Context:
         self.nnz_A, self.nnz_P = info[9], info[10]
         self.zy_bytes_c32 = info[11]
         self.ng = int(np.prod(self.grid_n))
+        self.gemv_ctas, self.gemv_split = info[13], info[14]
 
     def close(self):
         if self.h:
@@ -241,6 +269,37 @@ class Context:
         _check(lib().bem_precond_apply(self.h, _ptr(r, cdtype(prec)), _ptr(u, cdtype(prec)), prec,
                                        _stream()))
         return u
+
+    # ---- learned correction ---------------------------------------------------------
+    def net_init(self, seed=0):
+        _check(lib().bem_net_init(self.h, int(seed)))
+
+    def net_weights(self, w=None):
+        """Return the weights (numpy float32), or set them when w is given."""
+        L = lib()
+        n = _check(L.bem_net_weights(self.h, None, 0, 0))
+        fp = C.POINTER(C.c_float)
+        if w is None:
+            out = np.zeros(n, dtype=np.float32)
+            _check(L.bem_net_weights(self.h, out.ctypes.data_as(fp), n, 0))
+            return out
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(L.bem_net_weights(self.h, w.ctypes.data_as(fp), w.size, 1))
+        return w
+
+    def net_train(self, steps, batch=8, lr=1e-3, seed=0):
+        losses = np.zeros(steps, dtype=np.float32)
+        _check(lib().bem_net_train(self.h, int(steps), int(batch), float(lr), int(seed),
+                                   losses.ctypes.data_as(C.POINTER(C.c_float)), _stream()))
+        return losses
+
+    def net_apply(self, r, z=None):
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        _check(lib().bem_net_apply(self.h, _ptr(r, torch.complex64), _ptr(z, torch.complex64),
+                                   _stream()))
+        return z
 
     def solve(self, b, x=None, tol=1e-6, restart=100, max_iter=1000, prec_mode=BEM_C64,
               time_limit_s=0.0, precond=0):

@@ -82,6 +82,7 @@ void aim_destroy(aim_ctx* c) {
   cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
   release_streams(c);
+  free_net(c);
   free_geo_store(c);
   delete c;
 }
@@ -94,10 +95,10 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
   }
   int maxn = 0;
   for (int i = 0; i < c->nobj; ++i) maxn = std::max(maxn, c->e1[i] - c->e0[i]);
-  int64_t v[13] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
+  int64_t v[15] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
                    c->rowA.empty() ? 0 : c->rowA.back(), c->rowP.empty() ? 0 : c->rowP.back(),
-                   2 * c->zelems * 8, maxn};
-  for (int i = 0; i < n && i < 13; ++i) info[i] = v[i];
+                   2 * c->zelems * 8, maxn, c->gplan.ncta, c->gplan.split};
+  for (int i = 0; i < n && i < 15; ++i) info[i] = v[i];
   return BEM_OK;
 }
 
@@ -292,7 +293,7 @@ int bem_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_s
     return BEM_EINVAL;
   }
   if (!(o->tol > 0) || o->restart < 1 || o->restart > 512 || o->max_iter < 1 || o->precond < 0 ||
-      o->precond > 1) {
+      o->precond > 2) {
     set_error("bem_solve: bad options");
     return BEM_EINVAL;
   }

@@ -81,7 +81,13 @@ struct FftPlan {
   int P = 0;
   int nst = 0;
   int rad[kMaxStages] = {0};
+  // exact division by multiply-high: q = umulhi(n, mag) for n < 2^16 and divisors < 2^11
+  uint32_t mag_m[kMaxStages] = {0};   // divisor m_s = P / R_s
+  uint32_t mag_ns[kMaxStages] = {0};  // divisor Ns_s = R_0 ... R_{s-1} (0 when Ns_s = 1)
 };
+static inline uint32_t div_magic(uint32_t d) {
+  return d <= 1 ? 0u : (uint32_t)(((1ull << 32) + d - 1) / d);
+}
 bool make_fft_plan(int P, FftPlan* plan);
 int smooth_length(int need);  // smallest length >= need whose factors are 2, 3, 5, 7
 
@@ -138,6 +144,7 @@ struct GemvPlan {
   int32_t* cta_seg = nullptr;// device [ncta + 1]
   int ncta = 0;
   int nrows = 0;
+  int split = 2;               // column parts per row (1, 2 or 4), picked by the autotuner
   double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
 };
 void build_gemv_plan(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
@@ -222,6 +229,8 @@ struct aim_ctx {
   int32_t* d_pcperm = nullptr;  // object-major position -> system index
   float2* pcw32[2] = {nullptr, nullptr};
   double2* pcw64[2] = {nullptr, nullptr};
+  // learned correction network on the AIM grid (learned.cu)
+  void* net = nullptr;
 };
 
 namespace bem {
@@ -272,6 +281,13 @@ int make_ghat(aim_ctx* c);
 int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
                    cudaStream_t st);
 int setup_precond(aim_ctx* c);
+template <typename R>
+int project_all(aim_ctx* c, const typename C2<R>::T* r, typename C2<R>::T* sigma, cudaStream_t s);
+template <typename R>
+int interp_all(aim_ctx* c, const typename C2<R>::T* phi, typename C2<R>::T* u, cudaStream_t s);
+// learned correction (learned.cu): z = M_bd r + W net(P r) in FP32
+int net_apply(aim_ctx* c, const float2* r, float2* z, cudaStream_t s);
+void free_net(aim_ctx* c);
 template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cudaStream_t s);
 void free_geo_store(aim_ctx* c);
 double k0_of(double f);

@@ -13,8 +13,9 @@
 // Larger planes fall back to five batched 1-D passes (x, y, z-fused, y, x) with the same
 // pruning. Ghat is one octant (the circulant kernel is even along every axis) with the
 // 1/(Px Py Pz) normalisation folded in. Every transform is a Stockham autosort FFT in shared
-// memory with radix-8/4/2/3/5 butterflies and twiddles from a per-axis table; line pitches
-// are padded by one element to keep strided staging free of bank conflicts.
+// memory with radix-8/4/2/3/5 butterflies and twiddles from a per-axis table. Index divisions
+// use precomputed multiply-high constants, and element e of a line is stored at e + e/16 so
+// the strided stores of the early stages spread over the shared-memory banks.
 #include <algorithm>
 #include <cmath>
 
@@ -33,7 +34,14 @@ bool make_fft_plan(int P, FftPlan* plan) {
       plan->rad[plan->nst++] = r;
       n /= r;
     }
-  return n == 1 && P >= 1;
+  if (n != 1 || P < 1 || P >= 2048) return false;
+  int Ns = 1;
+  for (int s = 0; s < plan->nst; ++s) {
+    plan->mag_m[s] = div_magic(P / plan->rad[s]);
+    plan->mag_ns[s] = div_magic(Ns);
+    Ns *= plan->rad[s];
+  }
+  return true;
 }
 
 int smooth_length(int need) {
@@ -118,27 +126,39 @@ template <typename V> __device__ __forceinline__ void bfly8(V* v, bool inv) {
   v[7] = csub(e[3], w3);
 }
 
-// One Stockham stage over nlines lines held in shared memory. Element e of line l sits at
-// base[l * lstride + e * estride]. line_fast selects the thread mapping (consecutive threads
-// on consecutive lines, for lines that are adjacent in memory; otherwise on consecutive
-// butterflies of one line).
-template <typename V, int R>
+__device__ __forceinline__ int sw(int e) { return e + (e >> 4); }  // shared-memory swizzle
+__host__ __device__ __forceinline__ int sw_len(int n) { return n + (n >> 4) + 1; }
+__device__ __forceinline__ int udiv(int n, uint32_t mag) {  // exact n / d, mag = div_magic(d)
+  return mag ? (int)__umulhi((uint32_t)n, mag) : n;
+}
+
+// Line geometry in shared memory. SWL = false: element e of line l at l*ls + sw(e)*es (the
+// swizzle runs along the line); SWL = true: at sw(l)*ls + e*es (columns of a plane whose rows
+// are swizzled). line_fast maps consecutive threads to consecutive lines (lines adjacent in
+// memory), otherwise to consecutive butterflies of one line.
+struct Lines {
+  int nlines, ls, es;
+  uint32_t mag_nl;  // div_magic(nlines)
+  bool line_fast;
+};
+
+template <typename V, int R, bool SWL>
 __device__ __forceinline__ void stage_r(const V* src, V* dst, const V* tw, int P, int Ns,
-                                        int nlines, int lstride, int estride, bool line_fast,
-                                        bool inv) {
+                                        uint32_t mag_m, uint32_t mag_ns, const Lines& L, bool inv) {
   const int m = P / R;
   const int stw = P / (Ns * R);
-  const int total = nlines * m;
+  const int total = L.nlines * m;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int l, j;
-    if (line_fast) { j = idx / nlines; l = idx - j * nlines; }
-    else { l = idx / m; j = idx - l * m; }
-    const int k = j % Ns;
-    const V* s = src + l * lstride;
-    V* d = dst + l * lstride;
+    if (L.line_fast) { j = udiv(idx, L.mag_nl); l = idx - j * L.nlines; }
+    else { l = udiv(idx, mag_m); j = idx - l * m; }
+    const int k = j - udiv(j, mag_ns) * Ns;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[(j + r * m) * estride];
+    for (int r = 0; r < R; ++r) {
+      const int e = j + r * m;
+      v[r] = src[SWL ? sw(l) * L.ls + e * L.es : l * L.ls + sw(e) * L.es];
+    }
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -154,23 +174,26 @@ __device__ __forceinline__ void stage_r(const V* src, V* dst, const V* tw, int P
     else bfly8(v, inv);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) d[(base + r * Ns) * estride] = v[r];
+    for (int r = 0; r < R; ++r) {
+      const int e = base + r * Ns;
+      dst[SWL ? sw(l) * L.ls + e * L.es : l * L.ls + sw(e) * L.es] = v[r];
+    }
   }
 }
 
 // all stages of plan pl; returns the buffer holding the result (a or b)
-template <typename V>
-__device__ V* fft_smem(V* a, V* b, const V* tw, const FftPlan& pl, int nlines, int lstride,
-                       int estride, bool line_fast, bool inv) {
+template <typename V, bool SWL>
+__device__ V* fft_smem(V* a, V* b, const V* tw, const FftPlan& pl, const Lines& L, bool inv) {
   int Ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = pl.rad[st];
+    const uint32_t mm = pl.mag_m[st], mn = pl.mag_ns[st];
     switch (R) {
-      case 2: stage_r<V, 2>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
-      case 3: stage_r<V, 3>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
-      case 4: stage_r<V, 4>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
-      case 5: stage_r<V, 5>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
-      default: stage_r<V, 8>(a, b, tw, pl.P, Ns, nlines, lstride, estride, line_fast, inv); break;
+      case 2: stage_r<V, 2, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 3: stage_r<V, 3, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 4: stage_r<V, 4, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 5: stage_r<V, 5, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      default: stage_r<V, 8, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
     }
     __syncthreads();
     V* t = a;
@@ -188,10 +211,15 @@ struct PlaneArgs {
   int nx, ny, nz, Px, Py, Pz;
   int64_t ng, P3;
   FftPlan px, py, pz;
-  int gx, gy;  // octant dims of Ghat (Px/2+1, Py/2+1)
-  int TL;      // lines per CTA in the z pass
+  int gx, gy;        // octant dims of Ghat (Px/2+1, Py/2+1)
+  int TL;            // lines per CTA in the z pass
+  uint32_t mag_Px;   // div_magic(Px), div_magic(nx), div_magic(TL)
+  uint32_t mag_nx;
+  uint32_t mag_TL;
+  uint32_t mag_Pz;
 };
 
+// plane layout in shared memory: row y at y * pitch, element x at sw(x)
 template <typename V>
 __global__ void __launch_bounds__(512) k_plane_fwd(const V* __restrict__ sigma, V* __restrict__ ws,
                                                    const V* __restrict__ twx, const V* __restrict__ twy,
@@ -199,7 +227,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const V* __restrict__ sigma, 
   extern __shared__ unsigned char smem_raw[];
   V* tx = reinterpret_cast<V*>(smem_raw);
   V* ty = tx + a.Px;
-  const int pitch = a.Px + 1;
+  const int pitch = sw_len(a.Px);
   V* A = ty + a.Py;
   V* B = A + a.Py * pitch;
   const int z = blockIdx.x, c = blockIdx.y;
@@ -207,21 +235,23 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const V* __restrict__ sigma, 
   for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
   const V* src = sigma + c * a.ng + (int64_t)z * a.ny * a.nx;
   for (int i = threadIdx.x; i < a.Py * a.Px; i += blockDim.x) {
-    const int y = i / a.Px, x = i - y * a.Px;
+    const int y = udiv(i, a.mag_Px), x = i - y * a.Px;
     V v = czero<V>();
     if (y < a.ny && x < a.nx) v = src[y * a.nx + x];
-    A[y * pitch + x] = v;
-    B[y * pitch + x] = czero<V>();
+    A[y * pitch + sw(x)] = v;
+    B[y * pitch + sw(x)] = czero<V>();
   }
   __syncthreads();
   // rows (only the ny non-zero ones), then all columns
-  V* r = fft_smem(A, B, tx, a.px, a.ny, pitch, 1, false, false);
+  const Lines rows{a.ny, pitch, 1, 0, false};
+  V* r = fft_smem<V, false>(A, B, tx, a.px, rows, false);
   V* o = (r == A) ? B : A;
-  r = fft_smem(r, o, ty, a.py, a.Px, 1, pitch, true, false);
+  const Lines cols{a.Px, 1, pitch, a.mag_Px, true};
+  r = fft_smem<V, true>(r, o, ty, a.py, cols, false);
   V* dst = ws + c * a.P3 + (int64_t)z * a.Py * a.Px;
   for (int i = threadIdx.x; i < a.Py * a.Px; i += blockDim.x) {
-    const int y = i / a.Px, x = i - y * a.Px;
-    dst[i] = r[y * pitch + x];
+    const int y = udiv(i, a.mag_Px), x = i - y * a.Px;
+    dst[i] = r[y * pitch + sw(x)];
   }
 }
 
@@ -232,7 +262,7 @@ __global__ void __launch_bounds__(512) k_plane_inv(const V* __restrict__ ws, V* 
   extern __shared__ unsigned char smem_raw[];
   V* tx = reinterpret_cast<V*>(smem_raw);
   V* ty = tx + a.Px;
-  const int pitch = a.Px + 1;
+  const int pitch = sw_len(a.Px);
   V* A = ty + a.Py;
   V* B = A + a.Py * pitch;
   const int z = blockIdx.x, c = blockIdx.y;
@@ -240,17 +270,19 @@ __global__ void __launch_bounds__(512) k_plane_inv(const V* __restrict__ ws, V* 
   for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
   const V* src = ws + c * a.P3 + (int64_t)z * a.Py * a.Px;
   for (int i = threadIdx.x; i < a.Py * a.Px; i += blockDim.x) {
-    const int y = i / a.Px, x = i - y * a.Px;
-    A[y * pitch + x] = src[i];
+    const int y = udiv(i, a.mag_Px), x = i - y * a.Px;
+    A[y * pitch + sw(x)] = src[i];
   }
   __syncthreads();
-  V* r = fft_smem(A, B, ty, a.py, a.Px, 1, pitch, true, true);
+  const Lines cols{a.Px, 1, pitch, a.mag_Px, true};
+  V* r = fft_smem<V, true>(A, B, ty, a.py, cols, true);
   V* o = (r == A) ? B : A;
-  r = fft_smem(r, o, tx, a.px, a.ny, pitch, 1, false, true);
+  const Lines rows{a.ny, pitch, 1, 0, false};
+  r = fft_smem<V, false>(r, o, tx, a.px, rows, true);
   V* dst = phi + c * a.ng + (int64_t)z * a.ny * a.nx;
   for (int i = threadIdx.x; i < a.ny * a.nx; i += blockDim.x) {
-    const int y = i / a.nx, x = i - y * a.nx;
-    dst[i] = r[y * pitch + x];
+    const int y = udiv(i, a.mag_nx), x = i - y * a.nx;
+    dst[i] = r[y * pitch + sw(x)];
   }
 }
 
@@ -260,7 +292,7 @@ __global__ void __launch_bounds__(256) k_zfused(V* ws, const V* __restrict__ gha
                                                 const V* __restrict__ twz, PlaneArgs a) {
   extern __shared__ unsigned char smem_raw[];
   V* tz = reinterpret_cast<V*>(smem_raw);
-  const int pitch = a.Pz + 1;
+  const int pitch = sw_len(a.Pz);
   V* A = tz + a.Pz;
   V* B = A + a.TL * pitch;
   const int x0 = blockIdx.x * a.TL, y = blockIdx.y, c = blockIdx.z;
@@ -269,27 +301,29 @@ __global__ void __launch_bounds__(256) k_zfused(V* ws, const V* __restrict__ gha
   const int64_t plane = (int64_t)a.Py * a.Px;
   V* base = ws + c * a.P3 + (int64_t)y * a.Px + x0;
   for (int i = threadIdx.x; i < a.TL * a.Pz; i += blockDim.x) {
-    const int e = i / a.TL, l = i - e * a.TL;
+    const int e = udiv(i, a.mag_TL), l = i - e * a.TL;
     V v = czero<V>();
     if (l < nl && e < a.nz) v = base[e * plane + l];
-    A[l * pitch + e] = v;
+    A[l * pitch + sw(e)] = v;
   }
   __syncthreads();
-  V* r = fft_smem(A, B, tz, a.pz, a.TL, pitch, 1, false, false);
+  const Lines L{a.TL, pitch, 1, a.mag_TL, false};
+  V* r = fft_smem<V, false>(A, B, tz, a.pz, L, false);
   const int fy = min(y, a.Py - y);
   for (int i = threadIdx.x; i < a.TL * a.Pz; i += blockDim.x) {
-    const int l = i / a.Pz, kz = i - l * a.Pz;
+    const int l = udiv(i, a.mag_Pz), kz = i - l * a.Pz;
     if (l >= nl) continue;
     const int x = x0 + l;
     const int fx = min(x, a.Px - x), fz = min(kz, a.Pz - kz);
-    r[l * pitch + kz] = cmul(r[l * pitch + kz], ghat[((int64_t)fz * a.gy + fy) * a.gx + fx]);
+    const int o = l * pitch + sw(kz);
+    r[o] = cmul(r[o], ghat[((int64_t)fz * a.gy + fy) * a.gx + fx]);
   }
   __syncthreads();
   V* o = (r == A) ? B : A;
-  r = fft_smem(r, o, tz, a.pz, a.TL, pitch, 1, false, true);
+  r = fft_smem<V, false>(r, o, tz, a.pz, L, true);
   for (int i = threadIdx.x; i < a.TL * a.nz; i += blockDim.x) {
-    const int e = i / a.TL, l = i - e * a.TL;
-    if (l < nl) base[e * plane + l] = r[l * pitch + e];
+    const int e = udiv(i, a.mag_TL), l = i - e * a.TL;
+    if (l < nl) base[e * plane + l] = r[l * pitch + sw(e)];
   }
 }
 
@@ -306,6 +340,7 @@ struct LinePass {
   int inverse;
   int TL;
   int gx, gy, Px, Py;
+  uint32_t mag_P, mag_TL;
   FftPlan plan;
 };
 
@@ -314,7 +349,7 @@ __global__ void __launch_bounds__(256) k_lines(const V* in, V* out, const V* __r
                                                const V* __restrict__ ghat, LinePass p) {
   extern __shared__ unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);
-  const int pitch = p.P + 1;
+  const int pitch = sw_len(p.P);
   V* A = tw + p.P;
   V* B = A + p.TL * pitch;
   const int i0base = blockIdx.x * p.TL;
@@ -324,35 +359,37 @@ __global__ void __launch_bounds__(256) k_lines(const V* in, V* out, const V* __r
   const int64_t ib = i1 * p.is1 + i2 * p.is2;
   for (int idx = threadIdx.x; idx < p.TL * p.P; idx += blockDim.x) {
     int l, e;
-    if (p.ies == 1) { l = idx / p.P; e = idx - l * p.P; }
-    else { e = idx / p.TL; l = idx - e * p.TL; }
+    if (p.ies == 1) { l = udiv(idx, p.mag_P); e = idx - l * p.P; }
+    else { e = udiv(idx, p.mag_TL); l = idx - e * p.TL; }
     V v = czero<V>();
     if (l < nl && e < p.nin) v = in[ib + (int64_t)(i0base + l) * p.is0 + (int64_t)e * p.ies];
-    A[l * pitch + e] = v;
+    A[l * pitch + sw(e)] = v;
   }
   __syncthreads();
+  const Lines L{p.TL, pitch, 1, p.mag_TL, false};
   V* res;
   if (!p.fused) {
-    res = fft_smem(A, B, tw, p.plan, p.TL, pitch, 1, false, p.inverse != 0);
+    res = fft_smem<V, false>(A, B, tw, p.plan, L, p.inverse != 0);
   } else {
-    res = fft_smem(A, B, tw, p.plan, p.TL, pitch, 1, false, false);
+    res = fft_smem<V, false>(A, B, tw, p.plan, L, false);
     for (int idx = threadIdx.x; idx < p.TL * p.P; idx += blockDim.x) {
-      const int l = idx / p.P, kz = idx - l * p.P;
+      const int l = udiv(idx, p.mag_P), kz = idx - l * p.P;
       if (l >= nl) continue;
       const int x = i0base + l, y = i1;
       const int fx = min(x, p.Px - x), fy = min(y, p.Py - y), fz = min(kz, p.P - kz);
-      res[l * pitch + kz] = cmul(res[l * pitch + kz], ghat[((int64_t)fz * p.gy + fy) * p.gx + fx]);
+      const int o = l * pitch + sw(kz);
+      res[o] = cmul(res[o], ghat[((int64_t)fz * p.gy + fy) * p.gx + fx]);
     }
     __syncthreads();
     V* other = (res == A) ? B : A;
-    res = fft_smem(res, other, tw, p.plan, p.TL, pitch, 1, false, true);
+    res = fft_smem<V, false>(res, other, tw, p.plan, L, true);
   }
   const int64_t ob = i1 * p.os1 + i2 * p.os2;
   for (int idx = threadIdx.x; idx < p.TL * p.nout; idx += blockDim.x) {
     int l, e;
     if (p.oes == 1) { l = idx / p.nout; e = idx - l * p.nout; }
-    else { e = idx / p.TL; l = idx - e * p.TL; }
-    if (l < nl) out[ob + (int64_t)(i0base + l) * p.os0 + (int64_t)e * p.oes] = res[l * pitch + e];
+    else { e = udiv(idx, p.mag_TL); l = idx - e * p.TL; }
+    if (l < nl) out[ob + (int64_t)(i0base + l) * p.os0 + (int64_t)e * p.oes] = res[l * pitch + sw(e)];
   }
 }
 
@@ -362,14 +399,17 @@ template <typename V>
 static int launch_lines(const V* in, V* out, const V* tw, const V* ghat, LinePass p, int n2,
                         cudaStream_t s) {
   const size_t avail = 96 * 1024 / sizeof(V);
-  if (avail < 3 * (size_t)(p.P + 1)) {
+  const size_t pitch = sw_len(p.P);
+  if (avail < p.P + 2 * pitch) {
     set_error("FFT length %d too large for shared memory", p.P);
     return BEM_EGRID;
   }
-  int TL = (int)std::min<size_t>(16, (avail - p.P) / (2 * (size_t)(p.P + 1)));
+  int TL = (int)std::min<size_t>(16, (avail - p.P) / (2 * pitch));
   TL = std::max(1, std::min(TL, p.n0));
   p.TL = TL;
-  size_t smem = ((size_t)p.P + 2 * (size_t)TL * (p.P + 1)) * sizeof(V);
+  p.mag_P = div_magic(p.P);
+  p.mag_TL = div_magic(TL);
+  size_t smem = ((size_t)p.P + 2 * (size_t)TL * pitch) * sizeof(V);
   dim3 grid((p.n0 + TL - 1) / TL, p.n1, n2);
   k_lines<V><<<grid, 256, smem, s>>>(in, out, tw, ghat, p);
   BEM_CUDA(cudaGetLastError());
@@ -377,7 +417,7 @@ static int launch_lines(const V* in, V* out, const V* tw, const V* ghat, LinePas
 }
 
 template <typename V> static size_t plane_smem(int Px, int Py) {
-  return ((size_t)Px + Py + 2 * (size_t)Py * (Px + 1)) * sizeof(V);
+  return ((size_t)Px + Py + 2 * (size_t)Py * sw_len(Px)) * sizeof(V);
 }
 
 int fft_init_attrs() {
@@ -425,8 +465,13 @@ int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename
     a.px = c->plan[0]; a.py = c->plan[1]; a.pz = c->plan[2];
     a.gx = Px / 2 + 1; a.gy = Py / 2 + 1;
     const size_t avail = 64 * 1024 / sizeof(V);
-    a.TL = (int)std::max<size_t>(1, std::min<size_t>(16, (avail - Pz) / (2 * (size_t)(Pz + 1))));
-    const size_t zsm = ((size_t)Pz + 2 * (size_t)a.TL * (Pz + 1)) * sizeof(V);
+    const size_t zp = sw_len(Pz);
+    a.TL = (int)std::max<size_t>(1, std::min<size_t>(16, (avail - Pz) / (2 * zp)));
+    a.mag_Px = div_magic(Px);
+    a.mag_nx = div_magic(nx);
+    a.mag_TL = div_magic(a.TL);
+    a.mag_Pz = div_magic(Pz);
+    const size_t zsm = ((size_t)Pz + 2 * (size_t)a.TL * zp) * sizeof(V);
     k_plane_fwd<V><<<dim3(nz, ncomp), 512, psm, s>>>(sigma, ws, b.tw[0], b.tw[1], a);
     k_zfused<V><<<dim3((Px + a.TL - 1) / a.TL, Py, ncomp), 256, zsm, s>>>(ws, b.Ghat, b.tw[2], a);
     k_plane_inv<V><<<dim3(nz, ncomp), 512, psm, s>>>(ws, phi, b.tw[0], b.tw[1], a);

@@ -204,7 +204,7 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   BEM_TRY(W.alloc(&W.dsc, 8));
   // right preconditioning (flexible form: the preconditioned directions are kept)
   double2* Zb = nullptr;
-  if (o->precond == 1) {
+  if (o->precond == 1 || o->precond == 2) {
     BEM_TRY(setup_precond(c));
     BEM_TRY(W.alloc(&Zb, (size_t)m * n));
   }
@@ -242,7 +242,11 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
       const double2* vk = W.V + (int64_t)k * n;
       if (Zb) {
         double2* zk = Zb + (int64_t)k * n;
-        if (o->prec_mode == BEM_C64) {
+        if (o->precond == 2) {  // block-diagonal + learned correction (FP32)
+          k_to32<<<kChunks, 256, 0, s>>>(vk, c->f32.xin, n);
+          BEM_TRY(net_apply(c, c->f32.xin, c->f32.yout, s));
+          k_to64<<<kChunks, 256, 0, s>>>(c->f32.yout, zk, n);
+        } else if (o->prec_mode == BEM_C64) {
           BEM_TRY(precond_apply<double>(c, vk, zk, s));
         } else {
           k_to32<<<kChunks, 256, 0, s>>>(vk, c->f32.xin, n);

@@ -83,31 +83,86 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks
   }
 }
 
-// Persistent form: CTA p streams the row panels of row p of the schedule (GemvPlan).
-template <typename R, int NRHS>
+// Persistent form: CTA p streams the rows of its byte-balanced range (GemvPlan). Each row is
+// cut into S equal column parts; the S * rows work items of a chunk are dealt to the 8 warps
+// in turn (one warp reduction per part), partial sums meet in shared memory and the CTA adds
+// the S parts of each row at the end of the chunk. S = 1 is one warp per row; S = 2 or 4
+// evens out the work of the warps when a CTA holds only a few rows per warp.
+constexpr int kGemvChunk = 64;
+
+template <typename R, int NRHS, int S>
 __global__ void __launch_bounds__(kGemvThreads, kGemvCtasPerSm)
     k_gemv_plan(const RowInfo* __restrict__ rows, const int2* __restrict__ segs,
                 const int32_t* __restrict__ cta_seg, const typename C2<R>::T* __restrict__ A,
                 const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
                 int64_t vstride, const typename C2<R>::T* __restrict__ hsub) {
   typedef typename C2<R>::T V;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  typedef typename Vec16<R>::T L16;
+  constexpr int CP = Vec16<R>::kCplx;
   constexpr int nw = kGemvThreads / 32;
+  __shared__ V part[kGemvChunk][S][NRHS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s1 = cta_seg[blockIdx.x + 1];
   for (int s = cta_seg[blockIdx.x]; s < s1; ++s) {
     const int2 sg = segs[s];
-    for (int m = sg.x + warp; m < sg.y; m += nw) {
-      const RowInfo ri = rows[m];
-      V acc[NRHS];
-      row_dot<R, NRHS>(A + ri.aoff, x + ri.xoff, ri.n, vstride, lane, acc);
-      if (lane == 0) {
+    for (int c0 = sg.x; c0 < sg.y; c0 += kGemvChunk) {
+      const int c1 = min(sg.y, c0 + kGemvChunk);
+      for (int it = warp; it < (c1 - c0) * S; it += nw) {
+        const int rl = it / S, pp = it - rl * S;
+        const RowInfo ri = rows[c0 + rl];
+        const int nvec = (ri.n + CP - 1) / CP;
+        const int per = (nvec + S - 1) / S;
+        const int v0 = pp * per, v1 = min(nvec, v0 + per);
+        const L16* arow = reinterpret_cast<const L16*>(A + ri.aoff);
+        const V* xb = x + ri.xoff;
+        V acc[NRHS];
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
+#pragma unroll 4
+        for (int v = v0 + lane; v < v1; v += 32) {
+          const L16 a = __ldcs(arow + v);
+          const int col = v * CP;
+          if constexpr (CP == 2) {
+            const V a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
+#pragma unroll
+            for (int r = 0; r < NRHS; ++r) {
+              cfma(acc[r], a0, __ldg(xb + r * vstride + col));
+              if (col + 1 < ri.n) cfma(acc[r], a1, __ldg(xb + r * vstride + col + 1));
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride + col));
+          }
+        }
 #pragma unroll
         for (int r = 0; r < NRHS; ++r) {
-          int64_t o = r * vstride + m;
-          y[o] = hsub ? csub(hsub[o], acc[r]) : acc[r];
+          const V t = warp_sum(acc[r]);
+          if (lane == 0) part[rl][pp][r] = t;
         }
       }
+      __syncthreads();
+      for (int i = threadIdx.x; i < (c1 - c0) * NRHS; i += blockDim.x) {
+        const int rr = i / NRHS, r = i - rr * NRHS;
+        V t = part[rr][0][r];
+#pragma unroll
+        for (int q = 1; q < S; ++q) t = cadd(t, part[rr][q][r]);
+        const int64_t o = r * vstride + c0 + rr;
+        y[o] = hsub ? csub(hsub[o], t) : t;
+      }
+      __syncthreads();
     }
+  }
+}
+
+template <typename R, int S>
+static void launch_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A,
+                             const typename C2<R>::T* x, typename C2<R>::T* y, int nr,
+                             int64_t vstride, const typename C2<R>::T* hs, cudaStream_t s) {
+  switch (nr) {
+    case 1: k_gemv_plan<R, 1, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    case 2: k_gemv_plan<R, 2, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    case 3: k_gemv_plan<R, 3, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    default: k_gemv_plan<R, 4, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
   }
 }
 
@@ -120,16 +175,11 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
     const int nr = std::min(4, nrhs - r0);
     const int64_t o = r0 * vstride;
     const typename C2<R>::T* hs = hsub ? hsub + o : nullptr;
-#define BEM_GEMV_PLAN(NR)                                                                    \
-  k_gemv_plan<R, NR><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x + o, y + o, \
-                                                     vstride, hs)
-    switch (nr) {
-      case 1: BEM_GEMV_PLAN(1); break;
-      case 2: BEM_GEMV_PLAN(2); break;
-      case 3: BEM_GEMV_PLAN(3); break;
-      default: BEM_GEMV_PLAN(4); break;
+    switch (p.split) {
+      case 1: launch_gemv_plan<R, 1>(p, A, x + o, y + o, nr, vstride, hs, s); break;
+      case 4: launch_gemv_plan<R, 4>(p, A, x + o, y + o, nr, vstride, hs, s); break;
+      default: launch_gemv_plan<R, 2>(p, A, x + o, y + o, nr, vstride, hs, s); break;
     }
-#undef BEM_GEMV_PLAN
   }
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
@@ -460,6 +510,63 @@ int matvec_graph(aim_ctx* c, int which, const void* x, void* y, cudaStream_t s) 
 }
 template int matvec_graph<float>(aim_ctx*, int, const void*, void*, cudaStream_t);
 template int matvec_graph<double>(aim_ctx*, int, const void*, void*, cudaStream_t);
+
+// pure interpolation W (= P^T): u_m = sum_c sum_k WA[m][c][k] phi_c(node), u_{ne+t} likewise
+template <typename R>
+__global__ void __launch_bounds__(256) k_interp(const R* __restrict__ WA, const R* __restrict__ WP,
+                                                const int32_t* __restrict__ nodeE,
+                                                const int32_t* __restrict__ nodeT,
+                                                const typename C2<R>::T* __restrict__ phi, int64_t ng,
+                                                int ne, int nt, int nx, int ny,
+                                                typename C2<R>::T* __restrict__ u) {
+  typedef typename C2<R>::T V;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= ne + nt) return;
+  V acc = czero<V>();
+  if (lane < 27) {
+    if (row < ne) {
+      const int64_t nd = nodeE[row] + node_offset(lane, nx, ny);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R w = WA[(int64_t)row * 81 + c * 27 + lane];
+        const V f = phi[c * ng + nd];
+        acc.x += w * f.x;
+        acc.y += w * f.y;
+      }
+    } else {
+      const int t = row - ne;
+      const R w = WP[(int64_t)t * 27 + lane];
+      const V f = phi[3 * ng + nodeT[t] + node_offset(lane, nx, ny)];
+      acc = mk(w * f.x, w * f.y);
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) u[row] = acc;
+}
+
+// sigma = P r for a system vector r = [r_E; r_T]: comps 0..2 from r_E, comp 3 from r_T
+template <typename R>
+int project_all(aim_ctx* c, const typename C2<R>::T* r, typename C2<R>::T* sigma, cudaStream_t s) {
+  PrecBuf<R>& b = buf<R>(c);
+  const int64_t ng = c->ng;
+  k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, r, sigma, ng);
+  k_project_t<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowT, c->d_pcolT, b.WPT, r + c->ne, sigma + 3 * ng, ng);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int project_all<float>(aim_ctx*, const float2*, float2*, cudaStream_t);
+template int project_all<double>(aim_ctx*, const double2*, double2*, cudaStream_t);
+
+template <typename R>
+int interp_all(aim_ctx* c, const typename C2<R>::T* phi, typename C2<R>::T* u, cudaStream_t s) {
+  PrecBuf<R>& b = buf<R>(c);
+  k_interp<R><<<nb(c->ne + c->nt, 8), 256, 0, s>>>(b.WA, b.WP, c->d_nodeE, c->d_nodeT, phi, c->ng,
+                                                   c->ne, c->nt, c->gn[0], c->gn[1], u);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int interp_all<float>(aim_ctx*, const float2*, float2*, cudaStream_t);
+template int interp_all<double>(aim_ctx*, const double2*, double2*, cudaStream_t);
 
 template <typename R>
 int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStream_t s) {

@@ -400,6 +400,85 @@ __global__ void k_rhs_pw(DGeo g, int ne, int nt, double k0, double px, double py
 }
 
 // ---------------------------------------------------------------------------------------
+// GEMV autotuner: for the block layout (n, off, ld) of the FP32 matrix A, time the persistent
+// GEMV for {4, 6} CTAs per SM x {1, 2, 4} column parts per row with CUDA events on the real
+// data and keep the fastest plan (uploaded into the context).
+// ---------------------------------------------------------------------------------------
+static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::vector<int64_t>& off,
+                         const std::vector<int32_t>& ld, const float2* A, GemvPlan* out) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int64_t tot = 0;
+  for (int v : n) tot += v;
+  float2 *x = nullptr, *y = nullptr;
+  BEM_CUDA(cudaMalloc(&x, tot * sizeof(float2)));
+  BEM_CUDA(cudaMalloc(&y, tot * sizeof(float2)));
+  BEM_CUDA(cudaMemset(x, 0, tot * sizeof(float2)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_cps = kGemvCtasPerSm, best_split = 2;
+  int rc = BEM_OK;
+  for (int cps : {4, 6}) {
+    std::vector<RowInfo> rows;
+    std::vector<int2> segs;
+    std::vector<int32_t> cseg;
+    double ratio = 0;
+    build_gemv_plan(n, off, ld, nsm * cps, &rows, &segs, &cseg, &ratio);
+    GemvPlan p;
+    p.ncta = nsm * cps;
+    p.nrows = (int)rows.size();
+    void *d0 = nullptr, *d1 = nullptr, *d2 = nullptr;
+    if (cudaMalloc(&d0, rows.size() * sizeof(RowInfo)) != cudaSuccess ||
+        cudaMalloc(&d1, segs.size() * sizeof(int2) + 8) != cudaSuccess ||
+        cudaMalloc(&d2, cseg.size() * sizeof(int32_t)) != cudaSuccess) {
+      set_error("autotune: allocation failed");
+      rc = BEM_ENOMEM;
+      break;
+    }
+    cudaMemcpy(d0, rows.data(), rows.size() * sizeof(RowInfo), cudaMemcpyHostToDevice);
+    cudaMemcpy(d1, segs.data(), segs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    cudaMemcpy(d2, cseg.data(), cseg.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    p.rows = (RowInfo*)d0;
+    p.segs = (int2*)d1;
+    p.cta_seg = (int32_t*)d2;
+    for (int split : {1, 2, 4}) {
+      p.split = split;
+      for (int w = 0; w < 2; ++w) run_gemv_plan<float>(p, A, x, y, 1, tot, nullptr, 0);
+      cudaEventRecord(e0, 0);
+      for (int r = 0; r < 5; ++r) run_gemv_plan<float>(p, A, x, y, 1, tot, nullptr, 0);
+      cudaEventRecord(e1, 0);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_cps = cps; best_split = split; }
+    }
+    cudaFree(d0);
+    cudaFree(d1);
+    cudaFree(d2);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (rc != BEM_OK) return rc;
+  BEM_CUDA(cudaGetLastError());
+  std::vector<RowInfo> rows;
+  std::vector<int2> segs;
+  std::vector<int32_t> cseg;
+  build_gemv_plan(n, off, ld, nsm * best_cps, &rows, &segs, &cseg, &out->cmax_over_ideal);
+  BEM_TRY(upload(c, &out->rows, rows.data(), rows.size()));
+  BEM_TRY(upload(c, &out->segs, segs.data(), segs.size()));
+  BEM_TRY(upload(c, &out->cta_seg, cseg.data(), cseg.size()));
+  out->ncta = nsm * best_cps;
+  out->nrows = (int)rows.size();
+  out->split = best_split;
+  return BEM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------------------
 struct DevGeoStore {
@@ -703,17 +782,8 @@ int setup_device(aim_ctx* c) {
     build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, &c->tasks);
     c->ntasks = (int)c->tasks.size();
     BEM_TRY(upload(c, &c->d_tasks, c->tasks.data(), c->tasks.size()));
-    // persistent plan: one CTA per resident slot, rows of the Part_Schedule (Sec. III-C)
-    std::vector<RowInfo> rows;
-    std::vector<int2> segs;
-    std::vector<int32_t> cseg;
-    const int ncta = nsm * kGemvCtasPerSm;
-    build_gemv_plan(n, c->zoff, c->zld, ncta, &rows, &segs, &cseg, &c->gplan.cmax_over_ideal);
-    BEM_TRY(upload(c, &c->gplan.rows, rows.data(), rows.size()));
-    BEM_TRY(upload(c, &c->gplan.segs, segs.data(), segs.size()));
-    BEM_TRY(upload(c, &c->gplan.cta_seg, cseg.data(), cseg.size()));
-    c->gplan.ncta = ncta;
-    c->gplan.nrows = (int)rows.size();
+    // persistent, byte-balanced plan with the autotuned launch shape
+    BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan));
   }
   // workspaces
   const size_t P = (size_t)c->gp[0] * c->gp[1] * c->gp[2];
@@ -944,20 +1014,8 @@ int setup_precond(aim_ctx* c) {
   if (dinfo) cudaFree(dinfo);
   if (dwork) cudaFree(dwork);
   if (rc != BEM_OK) return rc;
-  // persistent GEMV plan over the object-major blocks
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  std::vector<RowInfo> rows;
-  std::vector<int2> segs;
-  std::vector<int32_t> cseg;
-  const int ncta = nsm * kGemvCtasPerSm;
-  build_gemv_plan(N, off, ld, ncta, &rows, &segs, &cseg, &c->pcplan.cmax_over_ideal);
-  BEM_TRY(upload(c, &c->pcplan.rows, rows.data(), rows.size()));
-  BEM_TRY(upload(c, &c->pcplan.segs, segs.data(), segs.size()));
-  BEM_TRY(upload(c, &c->pcplan.cta_seg, cseg.data(), cseg.size()));
-  c->pcplan.ncta = ncta;
-  c->pcplan.nrows = (int)rows.size();
+  // persistent GEMV plan over the object-major blocks (autotuned launch shape)
+  BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan));
   c->pc_ready = true;
   return BEM_OK;
 }
