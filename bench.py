@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim"])
+    ap.add_argument("--train-steps", type=int, default=300)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -288,8 +289,24 @@ def main():
         ctx.precond(torch.zeros(ctx.n, dtype=torch.complex64, device=dev), prec=api.BEM_C32)
         torch.cuda.synchronize()
         solve["precond_setup_s"] = time.perf_counter() - t1
+        # learned correction: trained on another seed of the same family (the benchmark
+        # structure is unseen), weights carried over
+        t1 = time.perf_counter()
+        tmesh, tgrid, _ = synth.bar_array_config(100, 10e9)
+        tctx = api.Context(tmesh, tgrid, 10e9)
+        tctx.net_init(1)
+        losses = tctx.net_train(steps=args.train_steps, batch=4, lr=2e-3, seed=2)
+        w = tctx.net_weights()
+        tctx.close()
+        ctx.net_weights(w)
+        torch.cuda.synchronize()
+        solve["learned_training"] = {
+            "structure": "4x4 Cu bar array, seed 100", "steps": args.train_steps, "batch": 4,
+            "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
+            "seconds_incl_setup": time.perf_counter() - t1}
         for name, mode, pc in (("plain_fp64", api.BEM_C64, 0), ("block_fp64", api.BEM_C64, 1),
-                               ("chosen_fp32_block", api.BEM_C32, 1)):
+                               ("chosen_fp32_block", api.BEM_C32, 1),
+                               ("chosen_fp32_block_learned", api.BEM_C32, 2)):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             xs, info = ctx.solve(b, tol=1e-6, restart=200, max_iter=3000, prec_mode=mode,

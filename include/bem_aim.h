@@ -195,7 +195,8 @@ int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
  * bem_net_train: `steps` Adam steps of lr on batches of `batch` pairs r = A x (x complex normal
  *   from the hash of seed), minimising |W net(P r) - (x - M_bd r)|^2 / |x - M_bd r|^2; losses
  *   (HOST, may be NULL) receives the mean loss of each step. Builds M_bd on first use.
- * bem_net_apply: z = M_bd r + W net(P r) for complex FP32 device vectors of N_E + N_T.
+ * bem_net_apply: z = M_bd r + W net(P r) for complex FP32 device vectors of N_E + N_T
+ *   (z = W net(P r) alone when correction_only is non-zero).
  * bem_convnet_run: the network alone on an nx x ny x nz grid, for verification: x [8][ng] FP32
  *   device input (rounded to BF16), w_host FP32 weights (rounded to BF16), out [8][ng] FP32
  *   device output; when gout [8][ng] is given, the backward pass writes gw_host (FP32 host,
@@ -204,7 +205,7 @@ int bem_net_init(aim_ctx* ctx, uint64_t seed);
 int64_t bem_net_weights(aim_ctx* ctx, float* w, int64_t n, int set);
 int bem_net_train(aim_ctx* ctx, int steps, int batch, float lr, uint64_t seed, float* losses,
                   void* stream);
-int bem_net_apply(aim_ctx* ctx, const void* r, void* z, void* stream);
+int bem_net_apply(aim_ctx* ctx, const void* r, void* z, int correction_only, void* stream);
 int bem_convnet_run(int nx, int ny, int nz, const float* w_host, const float* x, const float* gout,
                     float* out, float* gw_host, float* gx, void* stream);
 

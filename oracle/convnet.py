@@ -62,14 +62,18 @@ def conv3d_grad_weight(x, g):
     return gw
 
 
-def forward(x, ws):
-    """Returns the list of activations [x, h1, h2, h3, out]."""
+def forward(x, ws, store=None):
+    """Returns the list of activations [x, h1, h2, h3, out]. `store`, if given, is applied to
+    each hidden activation after the ReLU (the storage format of the activations, e.g. BF16
+    rounding), so that the ReLU masks and the next layer see what the kernels keep."""
     acts = [x]
     h = x
     for l, w in enumerate(ws):
         h = conv3d(h, w)
         if l < len(ws) - 1:
             h = np.maximum(h, 0.0)
+            if store is not None:
+                h = store(h)
         acts.append(h)
     return acts
 

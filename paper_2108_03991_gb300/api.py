@@ -87,7 +87,7 @@ def lib():
         L.bem_net_weights.argtypes = [vp, fp, i64, C.c_int]
         L.bem_net_weights.restype = i64
         L.bem_net_train.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.c_uint64, fp, vp]
-        L.bem_net_apply.argtypes = [vp, vp, vp, vp]
+        L.bem_net_apply.argtypes = [vp, vp, vp, C.c_int, vp]
         L.bem_convnet_run.argtypes = [C.c_int, C.c_int, C.c_int, fp, vp, vp, vp, fp, vp, vp]
         L.bem_part_schedule.argtypes = [C.c_int, C.POINTER(d), C.c_int, C.c_int, C.POINTER(i32)]
         L.bem_part_schedule.restype = d
@@ -293,12 +293,13 @@ class Context:
                                    losses.ctypes.data_as(C.POINTER(C.c_float)), _stream()))
         return losses
 
-    def net_apply(self, r, z=None):
+    def net_apply(self, r, z=None, correction_only=False):
+        """z = M_bd r + W net(P r) (or W net(P r) alone), complex64 device vectors."""
         import torch
         if z is None:
             z = torch.empty_like(r)
         _check(lib().bem_net_apply(self.h, _ptr(r, torch.complex64), _ptr(z, torch.complex64),
-                                   _stream()))
+                                   int(bool(correction_only)), _stream()))
         return z
 
     def solve(self, b, x=None, tol=1e-6, restart=100, max_iter=1000, prec_mode=BEM_C64,

@@ -97,7 +97,7 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
   for (int i = 0; i < c->nobj; ++i) maxn = std::max(maxn, c->e1[i] - c->e0[i]);
   int64_t v[15] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
                    c->rowA.empty() ? 0 : c->rowA.back(), c->rowP.empty() ? 0 : c->rowP.back(),
-                   2 * c->zelems * 8, maxn, c->gplan.ncta, c->gplan.split};
+                   2 * c->zelems * 8, maxn, c->gplan.ncta, c->gplan.tma ? -c->gplan.nstage : c->gplan.split};
   for (int i = 0; i < n && i < 15; ++i) info[i] = v[i];
   return BEM_OK;
 }

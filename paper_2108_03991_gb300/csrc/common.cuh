@@ -135,9 +135,16 @@ struct RowInfo {   // one row of the block-diagonal matrix (global row = output 
   int32_t xoff;    // first unknown of the block
 };
 
-// Persistent launch of a block-diagonal product built from a schedule C (Sec. III-C): one CTA
-// per processor p executes the row panels listed in row p of C, segments
-// [seg[cta_seg[p]], ..., seg[cta_seg[p+1]-1]], each a range [r0, r1) of global rows.
+struct TmaStage {  // whole rows [r0, r1) streamed as one bulk copy of nel complex elements
+  int32_t r0, r1;
+  int64_t e0;      // element offset of the first row
+  int32_t nel;
+  int32_t pad;
+};
+
+// Persistent launch of a block-diagonal product: CTA p streams the rows of its segments
+// [seg[cta_seg[p]], ..., seg[cta_seg[p+1]-1]], each a range [r0, r1) of global rows. With
+// tma set, the rows are fed through shared-memory stages by bulk copies (gemv_tma.cu).
 struct GemvPlan {
   RowInfo* rows = nullptr;   // device [nrows]
   int2* segs = nullptr;      // device [nseg]
@@ -146,7 +153,24 @@ struct GemvPlan {
   int nrows = 0;
   int split = 2;               // column parts per row (1, 2 or 4), picked by the autotuner
   double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
+  // bulk-copy staging
+  int tma = 0;
+  TmaStage* stages = nullptr;  // device
+  int32_t* cta_stage = nullptr;// device [ncta + 1]
+  int32_t* soff = nullptr;     // device [nrows] element offset of a row inside its stage
+  int nstage = 4;              // buffers in the ring
+  int stage_bytes = 0;
+  int* err = nullptr;          // device: non-zero after a bounded wait timed out
 };
+bool build_tma_stages(const std::vector<RowInfo>& rows, const std::vector<int2>& segs,
+                      const std::vector<int32_t>& cta_seg, int64_t stage_elems,
+                      std::vector<TmaStage>* stages, std::vector<int32_t>* cta_stage,
+                      std::vector<int32_t>* soff);
+int tma_init_attrs();
+template <typename R>
+int run_gemv_tma(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
+                 typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
+                 cudaStream_t s);
 void build_gemv_plan(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
                      const std::vector<int32_t>& ld, int ncta, std::vector<RowInfo>* rows,
                      std::vector<int2>* segs, std::vector<int32_t>* cta_seg, double* ratio);
@@ -181,7 +205,8 @@ struct aim_ctx {
   std::vector<int32_t> zld;
   int64_t zelems = 0;
   std::vector<bem::GemvTask> tasks;
-  bem::GemvPlan gplan;
+  bem::GemvPlan gplan;    // FP32 products (autotuned; may use bulk-copy staging)
+  bem::GemvPlan gplan64;  // FP64 products
   bem::FftPlan plan[3];
   // device: integer tables
   int32_t* d_nodeE = nullptr;  // [ne] linear index of the anchor node
@@ -224,6 +249,7 @@ struct aim_ctx {
   // row-major in object-major unknown order ([h_i; q_i] per object), built on first use
   bool pc_ready = false;
   bem::GemvPlan pcplan;
+  bem::GemvPlan pcplan64;
   float2* pc32 = nullptr;
   double2* pc64 = nullptr;
   int32_t* d_pcperm = nullptr;  // object-major position -> system index

@@ -171,6 +171,7 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
                   typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
                   cudaStream_t s) {
   if (p.ncta == 0 || p.nrows == 0) return BEM_OK;
+  if (p.tma) return run_gemv_tma<R>(p, A, x, y, nrhs, vstride, hsub, s);
   for (int r0 = 0; r0 < nrhs; r0 += 4) {
     const int nr = std::min(4, nrhs - r0);
     const int64_t o = r0 * vstride;
@@ -436,8 +437,9 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
                                                 nt, nx, ny, b.p);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
-    BEM_TRY(run_gemv_plan<R>(c->gplan, b.Z, h, b.e, 1, ne, nullptr, s));
-    BEM_TRY(run_gemv_plan<R>(c->gplan, b.Y, b.e, b.j, 1, ne, h, s));
+    const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
+    BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
+    BEM_TRY(run_gemv_plan<R>(gp, b.Y, b.e, b.j, 1, ne, h, s));
     k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, b.j, b.sigma, ng);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -572,8 +574,9 @@ template <typename R>
 int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStream_t s) {
   typedef typename C2<R>::T V;
   PrecBuf<R>& b = buf<R>(c);
-  BEM_TRY(run_gemv_plan<R>(c->gplan, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
-  if (heqv) BEM_TRY(run_gemv_plan<R>(c->gplan, b.Y, (const V*)ev, (V*)heqv, nrhs, c->ne, nullptr, s));
+  const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
+  BEM_TRY(run_gemv_plan<R>(gp, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
+  if (heqv) BEM_TRY(run_gemv_plan<R>(gp, b.Y, (const V*)ev, (V*)heqv, nrhs, c->ne, nullptr, s));
   return BEM_OK;
 }
 template int internal<float>(aim_ctx*, const void*, void*, void*, int, cudaStream_t);

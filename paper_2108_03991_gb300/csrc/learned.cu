@@ -410,7 +410,17 @@ static int net_train_step(aim_ctx* c, Net& n, int batch, float lr, uint64_t seed
   BEM_CUDA(cudaMemsetAsync(n.g, 0, n.nw * sizeof(float), s));
   double lsum = 0;
   for (int b = 0; b < batch; ++b) {
-    k_randn_c<<<(N + 255) / 256, 256, 0, s>>>(splitmix64(seed * 7919ull + b), N, n.x);
+    if (b % 2 == 0) {
+      // white x
+      k_randn_c<<<(N + 255) / 256, 256, 0, s>>>(splitmix64(seed * 7919ull + b), N, n.x);
+    } else {
+      // smooth x: grid potentials of random grid sources, interpolated to the unknowns
+      const int64_t n4 = 4 * c->ng;
+      k_randn_c<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(splitmix64(seed * 7919ull + b), (int)n4,
+                                                             n.sig);
+      BEM_TRY(fft_conv<float>(c, c->f32, n.sig, n.phi, 4, c->f32.ws, s));
+      BEM_TRY(interp_all<float>(c, n.phi, n.x, s));
+    }
     BEM_TRY(matvec_graph<float>(c, AIM_OP_SYSTEM, n.x, n.r, s));          // r = A x
     BEM_TRY(precond_apply<float>(c, n.r, n.t, s));                        // t = M_bd r
     k_axpy_c<<<(N + 255) / 256, 256, 0, s>>>(n.x, n.t, -1.f, N, n.t);     // t = x - M_bd r
@@ -502,12 +512,16 @@ int bem_net_train(aim_ctx* c, int steps, int batch, float lr, uint64_t seed, flo
   return BEM_OK;
 }
 
-int bem_net_apply(aim_ctx* c, const void* r, void* z, void* stream) {
+int bem_net_apply(aim_ctx* c, const void* r, void* z, int correction_only, void* stream) {
   if (!c || !r || !z || r == z) {
     set_error("bem_net_apply: bad arguments");
     return BEM_EINVAL;
   }
-  return net_apply(c, (const float2*)r, (float2*)z, (cudaStream_t)stream);
+  if (!correction_only) return net_apply(c, (const float2*)r, (float2*)z, (cudaStream_t)stream);
+  int rc = BEM_OK;
+  Net* n = get_net(c, &rc);
+  if (!n) return rc;
+  return net_correction(c, *n, (const float2*)r, (float2*)z, (cudaStream_t)stream);
 }
 
 // Standalone network pass for verification: x [8][ng] FP32 (rounded to BF16 on entry), weights

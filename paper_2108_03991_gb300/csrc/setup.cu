@@ -404,22 +404,70 @@ __global__ void k_rhs_pw(DGeo g, int ne, int nt, double k0, double px, double py
 // GEMV for {4, 6} CTAs per SM x {1, 2, 4} column parts per row with CUDA events on the real
 // data and keep the fastest plan (uploaded into the context).
 // ---------------------------------------------------------------------------------------
+static int upload_plan(aim_ctx* c, const std::vector<RowInfo>& rows, const std::vector<int2>& segs,
+                       const std::vector<int32_t>& cseg, GemvPlan* p) {
+  BEM_TRY(upload(c, &p->rows, rows.data(), rows.size()));
+  BEM_TRY(upload(c, &p->segs, segs.data(), segs.size()));
+  BEM_TRY(upload(c, &p->cta_seg, cseg.data(), cseg.size()));
+  p->ncta = (int)cseg.size() - 1;
+  p->nrows = (int)rows.size();
+  return BEM_OK;
+}
+
+struct TunePlan {  // a candidate plan held in temporary device memory
+  GemvPlan p;
+  std::vector<void*> mem;
+  ~TunePlan() { for (void* q : mem) cudaFree(q); }
+  template <typename T> int put(T** d, const std::vector<T>& h) {
+    if (cudaMalloc((void**)d, h.size() * sizeof(T) + 16) != cudaSuccess) {
+      set_error("autotune: allocation failed");
+      return BEM_ENOMEM;
+    }
+    mem.push_back(*d);
+    if (!h.empty() && cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("autotune: copy failed");
+      return BEM_ECUDA;
+    }
+    return BEM_OK;
+  }
+};
+
+// GEMV autotuner: for the block layout (n, off, ld) of the FP32 matrix A, time the candidate
+// launches with CUDA events on the real data and keep the fastest: the plain persistent kernel
+// with {4, 6} CTAs per SM x {1, 2, 4} column parts per row, and the bulk-copy-staged kernel
+// with {1, 2} CTAs per SM (when every row fits a stage). out32 receives the winner; out64 (the
+// FP64 products) the best plain candidate.
 static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::vector<int64_t>& off,
-                         const std::vector<int32_t>& ld, const float2* A, GemvPlan* out) {
+                         const std::vector<int32_t>& ld, const float2* A, GemvPlan* out32,
+                         GemvPlan* out64) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t tot = 0;
   for (int v : n) tot += v;
   float2 *x = nullptr, *y = nullptr;
+  int* derr = nullptr;
   BEM_CUDA(cudaMalloc(&x, tot * sizeof(float2)));
   BEM_CUDA(cudaMalloc(&y, tot * sizeof(float2)));
   BEM_CUDA(cudaMemset(x, 0, tot * sizeof(float2)));
+  BEM_TRY(dalloc_t(c, &derr, 1));
+  BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_cps = kGemvCtasPerSm, best_split = 2;
+  auto timeit = [&](const GemvPlan& p) -> float {
+    for (int w = 0; w < 2; ++w) run_gemv_plan<float>(p, A, x, y, 1, tot, nullptr, 0);
+    cudaEventRecord(e0, 0);
+    for (int r = 0; r < 5; ++r) run_gemv_plan<float>(p, A, x, y, 1, tot, nullptr, 0);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  float best = 1e30f, best_plain = 1e30f;
+  int best_kind = 0, best_cps = kGemvCtasPerSm, best_split = 2;  // kind 0 plain, 1 staged
+  int plain_cps = kGemvCtasPerSm, plain_split = 2;
   int rc = BEM_OK;
   for (int cps : {4, 6}) {
     std::vector<RowInfo> rows;
@@ -427,37 +475,42 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
     std::vector<int32_t> cseg;
     double ratio = 0;
     build_gemv_plan(n, off, ld, nsm * cps, &rows, &segs, &cseg, &ratio);
-    GemvPlan p;
-    p.ncta = nsm * cps;
-    p.nrows = (int)rows.size();
-    void *d0 = nullptr, *d1 = nullptr, *d2 = nullptr;
-    if (cudaMalloc(&d0, rows.size() * sizeof(RowInfo)) != cudaSuccess ||
-        cudaMalloc(&d1, segs.size() * sizeof(int2) + 8) != cudaSuccess ||
-        cudaMalloc(&d2, cseg.size() * sizeof(int32_t)) != cudaSuccess) {
-      set_error("autotune: allocation failed");
-      rc = BEM_ENOMEM;
-      break;
-    }
-    cudaMemcpy(d0, rows.data(), rows.size() * sizeof(RowInfo), cudaMemcpyHostToDevice);
-    cudaMemcpy(d1, segs.data(), segs.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    cudaMemcpy(d2, cseg.data(), cseg.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-    p.rows = (RowInfo*)d0;
-    p.segs = (int2*)d1;
-    p.cta_seg = (int32_t*)d2;
+    TunePlan t;
+    if ((rc = t.put(&t.p.rows, rows)) || (rc = t.put(&t.p.segs, segs)) || (rc = t.put(&t.p.cta_seg, cseg))) break;
+    t.p.ncta = nsm * cps;
+    t.p.nrows = (int)rows.size();
     for (int split : {1, 2, 4}) {
-      p.split = split;
-      for (int w = 0; w < 2; ++w) run_gemv_plan<float>(p, A, x, y, 1, tot, nullptr, 0);
-      cudaEventRecord(e0, 0);
-      for (int r = 0; r < 5; ++r) run_gemv_plan<float>(p, A, x, y, 1, tot, nullptr, 0);
-      cudaEventRecord(e1, 0);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_cps = cps; best_split = split; }
+      t.p.split = split;
+      const float ms = timeit(t.p);
+      if (ms < best_plain) { best_plain = ms; plain_cps = cps; plain_split = split; }
+      if (ms < best) { best = ms; best_kind = 0; best_cps = cps; best_split = split; }
     }
-    cudaFree(d0);
-    cudaFree(d1);
-    cudaFree(d2);
+  }
+  const int stage_bytes = 32 * 1024;
+  for (int cps : {1, 2}) {
+    if (rc != BEM_OK) break;
+    std::vector<RowInfo> rows;
+    std::vector<int2> segs;
+    std::vector<int32_t> cseg, cst, soff;
+    std::vector<TmaStage> st;
+    double ratio = 0;
+    build_gemv_plan(n, off, ld, nsm * cps, &rows, &segs, &cseg, &ratio);
+    if (!build_tma_stages(rows, segs, cseg, stage_bytes / (int)sizeof(float2), &st, &cst, &soff)) break;
+    TunePlan t;
+    if ((rc = t.put(&t.p.rows, rows)) || (rc = t.put(&t.p.stages, st)) ||
+        (rc = t.put(&t.p.cta_stage, cst)) || (rc = t.put(&t.p.soff, soff)))
+      break;
+    t.p.ncta = nsm * cps;
+    t.p.nrows = (int)rows.size();
+    t.p.tma = 1;
+    t.p.nstage = cps == 1 ? 4 : 3;
+    t.p.stage_bytes = stage_bytes;
+    t.p.err = derr;
+    const float ms = timeit(t.p);
+    int herr = 0;
+    cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (herr == 0 && ms < best) { best = ms; best_kind = 1; best_cps = cps; }
+    cudaMemset(derr, 0, sizeof(int));
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -465,16 +518,32 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
   cudaFree(y);
   if (rc != BEM_OK) return rc;
   BEM_CUDA(cudaGetLastError());
+  {  // FP64 plan: the best plain candidate
+    std::vector<RowInfo> rows;
+    std::vector<int2> segs;
+    std::vector<int32_t> cseg;
+    build_gemv_plan(n, off, ld, nsm * plain_cps, &rows, &segs, &cseg, &out64->cmax_over_ideal);
+    BEM_TRY(upload_plan(c, rows, segs, cseg, out64));
+    out64->split = plain_split;
+  }
   std::vector<RowInfo> rows;
   std::vector<int2> segs;
   std::vector<int32_t> cseg;
-  build_gemv_plan(n, off, ld, nsm * best_cps, &rows, &segs, &cseg, &out->cmax_over_ideal);
-  BEM_TRY(upload(c, &out->rows, rows.data(), rows.size()));
-  BEM_TRY(upload(c, &out->segs, segs.data(), segs.size()));
-  BEM_TRY(upload(c, &out->cta_seg, cseg.data(), cseg.size()));
-  out->ncta = nsm * best_cps;
-  out->nrows = (int)rows.size();
-  out->split = best_split;
+  build_gemv_plan(n, off, ld, nsm * best_cps, &rows, &segs, &cseg, &out32->cmax_over_ideal);
+  BEM_TRY(upload_plan(c, rows, segs, cseg, out32));
+  out32->split = best_split;
+  if (best_kind == 1) {
+    std::vector<int32_t> cst, soff;
+    std::vector<TmaStage> st;
+    build_tma_stages(rows, segs, cseg, stage_bytes / (int)sizeof(float2), &st, &cst, &soff);
+    BEM_TRY(upload(c, &out32->stages, st.data(), st.size()));
+    BEM_TRY(upload(c, &out32->cta_stage, cst.data(), cst.size()));
+    BEM_TRY(upload(c, &out32->soff, soff.data(), soff.size()));
+    out32->tma = 1;
+    out32->nstage = best_cps == 1 ? 4 : 3;
+    out32->stage_bytes = stage_bytes;
+    out32->err = derr;
+  }
   return BEM_OK;
 }
 
@@ -783,7 +852,8 @@ int setup_device(aim_ctx* c) {
     c->ntasks = (int)c->tasks.size();
     BEM_TRY(upload(c, &c->d_tasks, c->tasks.data(), c->tasks.size()));
     // persistent, byte-balanced plan with the autotuned launch shape
-    BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan));
+    BEM_TRY(tma_init_attrs());
+    BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan, &c->gplan64));
   }
   // workspaces
   const size_t P = (size_t)c->gp[0] * c->gp[1] * c->gp[2];
@@ -1015,7 +1085,7 @@ int setup_precond(aim_ctx* c) {
   if (dwork) cudaFree(dwork);
   if (rc != BEM_OK) return rc;
   // persistent GEMV plan over the object-major blocks (autotuned launch shape)
-  BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan));
+  BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan, &c->pcplan64));
   c->pc_ready = true;
   return BEM_OK;
 }
@@ -1044,7 +1114,7 @@ int precond_apply(aim_ctx* c, const void* rv, void* uv, cudaStream_t s) {
   V* w1 = sizeof(R) == 4 ? (V*)c->pcw32[1] : (V*)c->pcw64[1];
   const V* M = sizeof(R) == 4 ? (const V*)c->pc32 : (const V*)c->pc64;
   k_perm_gather<V><<<nblk(n, 256), 256, 0, s>>>(c->d_pcperm, (const V*)rv, w0, n);
-  BEM_TRY(run_gemv_plan<R>(c->pcplan, M, w0, w1, 1, n, nullptr, s));
+  BEM_TRY(run_gemv_plan<R>(sizeof(R) == 4 ? c->pcplan : c->pcplan64, M, w0, w1, 1, n, nullptr, s));
   k_perm_scatter<V><<<nblk(n, 256), 256, 0, s>>>(c->d_pcperm, w1, (V*)uv, n);
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;

@@ -43,12 +43,12 @@ def test_convnet_forward_backward_vs_oracle(dev, shape):
     g = rng.standard_normal((8, nz, ny, nx)).astype(np.float32)
     out, gw, gx = api.convnet_run(wflat, torch.from_numpy(x).to(dev), torch.from_numpy(g).to(dev))
     wsb = convnet.unflatten(bf16(wflat))
-    acts = convnet.forward(bf16(x), wsb)
+    acts = convnet.forward(bf16(x), wsb, store=bf16)
     gws, gxo = convnet.backward(acts, wsb, g.astype(np.float64))
-    assert rel(out.cpu().numpy(), acts[-1]) < 2e-2
-    assert rel(gx.cpu().numpy(), gxo) < 2e-2
+    assert rel(out.cpu().numpy(), acts[-1]) < 1e-2
+    assert rel(gx.cpu().numpy(), gxo) < 1e-2
     for l, gwl in enumerate(convnet.unflatten(gw)):
-        assert rel(gwl, gws[l]) < 2e-2, l
+        assert rel(gwl, gws[l]) < 1e-2, l
 
 
 @pytest.fixture(scope="module")
@@ -68,8 +68,7 @@ def test_net_correction_vs_oracle(small):
     w = ctx.net_weights()
     r = synth.rand_cvec(ctx.n, 4).astype(np.complex64)
     rd = torch.from_numpy(r).cuda()
-    z = ctx.net_apply(rd).cpu().numpy().astype(np.complex128)
-    zb = ctx.precond(rd, prec=api.BEM_C32).cpu().numpy().astype(np.complex128)
+    corr_g = ctx.net_apply(rd, correction_only=True).cpu().numpy().astype(np.complex128)
     mesh = synth.small_bars(2, 2.0)
     grid = synth.grid_box(mesh, 0.5)
     rw = from_mesh(mesh)
@@ -79,10 +78,10 @@ def test_net_correction_vs_oracle(small):
     sig = np.stack([A.PA[c].T @ r[:ne] for c in range(3)] + [A.PP.T @ r[ne:]])
     rms = np.sqrt(np.sum(np.abs(sig) ** 2) / (8 * sig.shape[1]))
     xin = np.concatenate([[s.real, s.imag] for s in sig]).reshape(8, nz, ny, nx) / rms
-    out = convnet.forward(bf16(xin), convnet.unflatten(bf16(w)))[-1] * rms
+    out = convnet.forward(bf16(xin), convnet.unflatten(bf16(w)), store=bf16)[-1] * rms
     phi = (out[0::2] + 1j * out[1::2]).reshape(4, -1)
     corr = np.concatenate([sum(A.PA[c] @ phi[c] for c in range(3)), A.PP @ phi[3]])
-    assert rel(z - zb, corr) < 2e-2
+    assert rel(corr_g, corr) < 2e-2
 
 
 def test_training_lowers_loss_and_solve_converges(small):
