@@ -193,7 +193,8 @@ int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
  * bem_net_weights: copy weights from (set = 1) or to (set = 0) the HOST array w of n floats;
  *   with w = NULL returns the number of weights.
  * bem_net_train: `steps` Adam steps of lr on batches of `batch` pairs r = A x (x complex normal
- *   from the hash of seed), minimising |W net(P r) - (x - M_bd r)|^2 / |x - M_bd r|^2; losses
+ *   from the hash of seed, half of them smoothed on the grid), minimising the grid-projected
+ *   error |P (W net(P r) - t)|^2 / |P t|^2 with t = x - M_bd r; losses
  *   (HOST, may be NULL) receives the mean loss of each step. Builds M_bd on first use.
  * bem_net_apply: z = M_bd r + W net(P r) for complex FP32 device vectors of N_E + N_T
  *   (z = W net(P r) alone when correction_only is non-zero).

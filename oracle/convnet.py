@@ -7,8 +7,9 @@ zero padding, no biases (so net(a x) = a net(x) for a > 0), ReLU between layers,
 grid components (x, y, z RWG components and the charge), scaled by the RMS of the grid; the
 output, scaled back, is interpolated with W = P^T to a correction in unknown space:
   M(r) = M_bd r + W net(P r).
-Training minimises the relative error |W net(P r) - (A^{-1} r - M_bd r)|^2 / |A^{-1} r - M_bd r|^2
-over pairs r = A x.
+Training minimises the grid-projected relative error |P (W net(P r) - t)|^2 / |P t|^2 with
+t = A^{-1} r - M_bd r over pairs r = A x (reading: the block-diagonal part leaves mesh-scale
+error modes no grid field can represent; the network acts as a grid-level correction).
 
 Layouts: activations [C, nz, ny, nx]; weights [C_out, C_in, 3, 3, 3] indexed (dz, dy, dx).
 """

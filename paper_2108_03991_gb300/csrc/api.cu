@@ -160,7 +160,8 @@ int bem_blockdiag_gemv(int nblk, const int32_t* n, const void* A, const void* x,
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // the same persistent, Part_Schedule-built launch as the context's internal products
+  // the persistent byte-balanced launch of the context's plain internal products (4-6 CTAs per
+  // SM, rows of all blocks cut into equal-byte ranges), with the default shape (no autotuning)
   std::vector<RowInfo> rows;
   std::vector<int2> segs;
   std::vector<int32_t> cseg;

@@ -5,8 +5,11 @@
 // scaled by their RMS) to a grid correction that W = P^T interpolates back:
 //   M(r) = M_bd r + W net(P r),
 // used on the right in flexible GMRES. Weights and activations are BF16, every sum is FP32;
-// gradients are FP32. Training minimises |W net(P r) - (x - M_bd r)|^2 / |x - M_bd r|^2 over
-// pairs r = A x with x drawn on the device (splitmix64 counter hash, Box-Muller), with Adam.
+// gradients are FP32. Training minimises |P (W net(P r) - t)|^2 / |P t|^2, t = x - M_bd r, over
+// pairs r = A x with x drawn on the device (splitmix64 counter hash, Box-Muller; half of them
+// smoothed as grid potentials of random grid sources), with Adam. The error is measured on the
+// grid: the block-diagonal part leaves mesh-scale error modes that no grid field represents, and
+// the network is meant as a coarse (grid-level) correction beside it.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -211,18 +214,6 @@ __global__ void k_pack_grad(const float2* gphi, const float* sumsq, const float*
   g[2 * c * ng + p] = sc * gphi[i].x;
   g[(2 * c + 1) * ng + p] = sc * gphi[i].y;
 }
-// e = u - t, and |e|^2, |t|^2 accumulated into acc[0], acc[1]
-__global__ void k_resid(const float2* u, const float2* t, int n, float2* e, float* acc) {
-  float a = 0.f, b = 0.f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float2 d = make_float2(u[i].x - t[i].x, u[i].y - t[i].y);
-    e[i] = d;
-    a += d.x * d.x + d.y * d.y;
-    b += t[i].x * t[i].x + t[i].y * t[i].y;
-  }
-  float2 s = warp_sum(make_float2(a, b));
-  if ((threadIdx.x & 31) == 0) { atomicAdd(acc, s.x); atomicAdd(acc + 1, s.y); }
-}
 __global__ void k_axpy_c(const float2* a, const float2* b, float sb, int n, float2* o) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) o[i] = make_float2(a[i].x + sb * b[i].x, a[i].y + sb * b[i].y);
@@ -238,7 +229,7 @@ struct Net {
   float* out = nullptr;      // [8][ng]
   float* gbuf[2] = {nullptr, nullptr};  // [16][ng] gradients
   float* scal = nullptr;     // [0] sumsq of the input grid, [1..2] |e|^2, |t|^2
-  float2 *sig = nullptr, *phi = nullptr;  // [4][ng]
+  float2 *sig = nullptr, *phi = nullptr, *g2 = nullptr;  // [4][ng]
   float2 *x = nullptr, *r = nullptr, *t = nullptr, *u = nullptr, *e = nullptr;  // [N]
   int adam_t = 0;
   std::vector<void*> mem;
@@ -360,6 +351,7 @@ static Net* get_net(aim_ctx* c, int* rc) {
   if (*rc == BEM_OK) *rc = n->alloc(&n->scal, 8);
   if (*rc == BEM_OK) *rc = n->alloc(&n->sig, 4 * (size_t)c->ng);
   if (*rc == BEM_OK) *rc = n->alloc(&n->phi, 4 * (size_t)c->ng);
+  if (*rc == BEM_OK) *rc = n->alloc(&n->g2, 4 * (size_t)c->ng);
   for (float2** p : {&n->x, &n->r, &n->t, &n->u, &n->e})
     if (*rc == BEM_OK) *rc = n->alloc(p, N);
   if (*rc != BEM_OK) {
@@ -425,9 +417,16 @@ static int net_train_step(aim_ctx* c, Net& n, int batch, float lr, uint64_t seed
     BEM_TRY(precond_apply<float>(c, n.r, n.t, s));                        // t = M_bd r
     k_axpy_c<<<(N + 255) / 256, 256, 0, s>>>(n.x, n.t, -1.f, N, n.t);     // t = x - M_bd r
     BEM_TRY(net_correction(c, n, n.r, n.u, s));                           // u = W net(P r)
+    // loss |P e|^2 / |P t|^2 with e = u - t: the error measured on the grid, where the
+    // correction lives; gradient w.r.t. the output grid = 2 P W P e / |P t|^2
     BEM_CUDA(cudaMemsetAsync(n.scal + 1, 0, 2 * sizeof(float), s));
-    k_resid<<<304, 256, 0, s>>>(n.u, n.t, N, n.e, n.scal + 1);            // e = u - t
+    k_axpy_c<<<(N + 255) / 256, 256, 0, s>>>(n.u, n.t, -1.f, N, n.e);     // e = u - t
     BEM_TRY(project_all<float>(c, n.e, n.phi, s));                         // P e
+    BEM_TRY(project_all<float>(c, n.t, n.g2, s));                          // P t
+    k_sumsq<<<304, 256, 0, s>>>(n.phi, 4 * c->ng, n.scal + 1);
+    k_sumsq<<<304, 256, 0, s>>>(n.g2, 4 * c->ng, n.scal + 2);
+    BEM_TRY(interp_all<float>(c, n.phi, n.e, s));                          // W P e
+    BEM_TRY(project_all<float>(c, n.e, n.phi, s));                         // P W P e
     k_pack_grad<<<(unsigned)((4 * c->ng + 255) / 256), 256, 0, s>>>(n.phi, n.scal, n.scal + 2,
                                                                         c->ng, n.gbuf[0]);
     BEM_TRY(net_backward(n, d, nullptr, s));
