@@ -156,7 +156,9 @@ def ncu_case(args):
     gemv: the block-diagonal GEMV alone on random blocks with the workload's block sizes (one of
           Z or Y_eq: ~200 MB in FP32, larger than L2);
     aim:  the grid convolution (4 components) on the workload's AIM grid, set up on two small
-          boxes at opposite corners of the array's bounding box (same grid, tiny set-up)."""
+          boxes at opposite corners of the array's bounding box (same grid, tiny set-up);
+    internal: the workload's own internal products (e = Z h, h_eq = Y e) with the launch the
+          set-up autotuner chose, inside the profiler range "internal_steps"."""
     import numpy as np
     import torch
 
@@ -176,6 +178,20 @@ def ncu_case(args):
             ctx.conv(s, phi, ncomp=4, prec=api.BEM_C32)
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": "aim", "grid": list(ctx.grid_n), "fft": list(ctx.padded)}))
+        return
+    if args.ncu_case == "internal":
+        mesh, grid, freq = synth.bar_array_config(0, 10e9)
+        ctx = api.Context(mesh, grid, freq)
+        h = torch.from_numpy(synth.rand_cvec(ctx.ne, 4).astype(np.complex64)).cuda()
+        e, heq = torch.empty_like(h), torch.empty_like(h)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("internal_steps")
+        for _ in range(args.steps):
+            ctx.internal(h, e, heq, prec=api.BEM_C32)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "internal", "ctas": ctx.gemv_ctas, "split": ctx.gemv_split,
+                          "loads_in_flight": ctx.gemv_unroll, "tune_ns": ctx.gemv_tune_ns}))
         return
     mesh = synth.bar_array(0)
     sizes = [int(np.sum(mesh.obj == i)) * 3 // 2 for i in range(mesh.nobj)]
@@ -198,7 +214,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim"])
+    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal"])
     ap.add_argument("--train-steps", type=int, default=300)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -237,8 +253,10 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(s)
+        torch.cuda.nvtx.range_push("matvec_steps")  # profiler range of the timed steps
         for _ in range(args.steps):
             ctx.matvec(x, y, prec=api.BEM_C32)
+        torch.cuda.nvtx.range_pop()
         ev1.record(s)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
@@ -304,6 +322,11 @@ def main():
             "structure": "4x4 Cu bar array, seed 100", "steps": args.train_steps, "batch": 4,
             "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
             "seconds_incl_setup": time.perf_counter() - t1}
+        # untimed warm-up: allocates the context's Krylov workspace and captures the FP64 and
+        # FP32 matvec graphs, as a long-lived solver context has them before its next solve
+        for mode in (api.BEM_C64, api.BEM_C32):
+            ctx.solve(b, tol=1e-6, restart=200, max_iter=2, prec_mode=mode, precond=1)
+        solve["warm"] = "workspace and matvec graphs from an untimed 2-iteration solve"
         for name, mode, pc in (("plain_fp64", api.BEM_C64, 0), ("block_fp64", api.BEM_C64, 1),
                                ("chosen_fp32_block", api.BEM_C32, 1),
                                ("chosen_fp32_block_learned", api.BEM_C32, 2)):
@@ -324,7 +347,7 @@ def main():
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
         value = world * 1e3 / ms
-        # per system matvec: 2 GEMV, 2 scatter, 2 x 3 FFT passes, 2 row kernels (+2 memsets)
+        # per system matvec: 2 GEMV, 2 projections, 2 x 3 FFT passes, 2 row kernels
         launches_per_step = 12
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -339,7 +362,11 @@ def main():
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": src, "traffic": None,
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
-                         "launch": {"ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split}},
+                         "launch": {"ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split,
+                                    "loads_in_flight": ctx.gemv_unroll,
+                                    "autotune_ns_per_launch": ctx.gemv_tune_ns,
+                                    "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
+                                                       for r in ctx.gemv_tune_table()]}},
             "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * ctx.n,
                     "d2h_bytes_per_step": 8 * ctx.n},
             "gpu_launches": launches_per_step * args.steps,

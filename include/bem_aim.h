@@ -92,9 +92,22 @@ const char* bem_last_error(void);
 
 /* Sizes: info[0]=N_E, [1]=N_T, [2]=nobj, [3..5]=grid n, [6..8]=padded FFT lengths,
  * [9]=nnz(L^A_NR), [10]=nnz(L^Phi_NR), [11]=bytes of Z and Y (C32), [12]=max n_i,
- * [13]=CTAs of the block GEMV launch, [14]=column parts per row (both chosen by the set-up
- * autotuner). Writes min(n, 15) entries. */
+ * [13]=CTAs of the block GEMV launch, [14]=column parts per row, or minus the number of
+ * shared-memory stages when the bulk-copy-staged kernel was chosen, [15]=16-byte loads in flight
+ * per lane (0 for the staged kernel) (all chosen by the set-up autotuner), [16]=ns per launch of
+ * the best plain candidate, [17]=ns per launch of the best staged candidate (-1 if none ran
+ * correctly), [18]=autotuner candidates rejected (product differed from the first candidate's
+ * beyond FP32 rounding, or a bounded wait timed out; set-up products include the preconditioner
+ * blocks once they are built). Writes min(n, 19) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
+
+/* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the
+ * GPU counterpart of the paper's choice of schedule for the internal products, Sec. III-C):
+ * kind 0 = the set-up autotuner's choice (default), 1 = the fastest persistent register-path
+ * candidate, 2 = the fastest bulk-copy-staged candidate. Waits for the device to be idle and
+ * drops the captured matvec graphs. BEM_EINVAL if kind is out of range or no candidate of that
+ * kind ran correctly at set-up (aim_info entries 16-17). FP64 products always use kind 1. */
+int aim_gemv_select(aim_ctx* ctx, int kind);
 
 /* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)
  * or AIM_OP_SYSTEM (the SLIM system of Eq. AEFIEoutJ, vectors of N_E + N_T):
@@ -142,6 +155,9 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *   what 5: pulse projection weights, double [N_T][27]
  *   what 6: stencil anchors, int32 [N_E + N_T][3]
  *   what 7: edge table, int32 [N_E][6] = (a, b, T+, T-, v+, v-)
+ *   what 8: the set-up GEMV autotuner's table, float [candidates][5] = (kind: 0 row plan,
+ *           1 flat, 2 bulk-copy staged; CTAs per SM; column parts per row; loads in flight
+ *           per lane; ns per launch, or -1 when the candidate was rejected or not applicable)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
 
@@ -178,8 +194,12 @@ typedef struct {
 } bem_solve_info;
 
 /* Solve A x = b (Eq. AEFIEoutJ) with restarted GMRES on the device (Sec. III-E). b and x
- * are complex double device vectors of N_E + N_T. Returns BEM_OK when the true residual
- * reaches tol, BEM_ENOCONV (positive) when max_iter or the time limit stops it first. */
+ * are complex double device vectors of N_E + N_T; x holds the initial guess on entry (all
+ * zeros: none, and the first residual needs no matvec) and the solution on exit. The Krylov
+ * workspace ((m+1) + m vectors of N_E + N_T complex doubles with a preconditioner, m + 1
+ * without; m = restart) is allocated by the first solve that needs it and kept by the context
+ * for later solves (freed by aim_destroy). Returns BEM_OK when the true residual reaches tol,
+ * BEM_ENOCONV (positive) when max_iter or the time limit stops it first. */
 int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
               bem_solve_info* info, void* stream);
 

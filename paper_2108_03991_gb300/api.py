@@ -72,6 +72,7 @@ def lib():
         L.bem_last_error.restype = C.c_char_p
         L.aim_info.argtypes = [vp, C.POINTER(i64), C.c_int]
         L.aim_matvec.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
+        L.aim_gemv_select.argtypes = [vp, C.c_int]
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int, C.c_int, vp]
@@ -198,8 +199,8 @@ class Context:
         h = C.c_void_p()
         _check(L.aim_setup(C.byref(m), C.byref(g), float(freq), C.byref(h)))
         self.h = h
-        info = (C.c_int64 * 15)()
-        _check(L.aim_info(h, info, 15))
+        info = (C.c_int64 * 19)()
+        _check(L.aim_info(h, info, 19))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -209,6 +210,13 @@ class Context:
         self.zy_bytes_c32 = info[11]
         self.ng = int(np.prod(self.grid_n))
         self.gemv_ctas, self.gemv_split = info[13], info[14]
+        self.gemv_unroll = info[15]
+        self.gemv_tune_ns = {"plain": info[16], "staged": info[17]}
+        self.gemv_tune_rejected = info[18]
+
+    def gemv_select(self, kind):
+        """FP32 block-GEMV launch: 0 autotuned choice, 1 best plain, 2 best bulk-copy staged."""
+        _check(lib().aim_gemv_select(self.h, int(kind)))
 
     def close(self):
         if self.h:
@@ -322,6 +330,11 @@ class Context:
         buf = np.empty(need, dtype=np.uint8)
         _check(L.aim_export(self.h, what, index, buf.ctypes.data_as(C.c_void_p), need))
         return buf
+
+    def gemv_tune_table(self):
+        """The set-up GEMV autotuner's candidates: rows (kind 0 row plan / 1 flat / 2 staged,
+        CTAs per SM, column parts per row, loads in flight per lane, ns per launch or -1)."""
+        return self._export(8).view(np.float32).reshape(-1, 5)
 
     def Z(self, i):
         b = self._export(0, i).view(np.complex128)

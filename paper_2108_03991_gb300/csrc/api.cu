@@ -84,6 +84,7 @@ void aim_destroy(aim_ctx* c) {
   release_streams(c);
   free_net(c);
   free_geo_store(c);
+  if (c->gm_ws) cudaFree(c->gm_ws);
   delete c;
 }
 
@@ -95,10 +96,32 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
   }
   int maxn = 0;
   for (int i = 0; i < c->nobj; ++i) maxn = std::max(maxn, c->e1[i] - c->e0[i]);
-  int64_t v[15] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
+  auto ns = [](float ms5) -> int64_t { return ms5 < 1e29f ? (int64_t)(ms5 * 1e6f / 5.f) : -1; };
+  int64_t v[19] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
                    c->rowA.empty() ? 0 : c->rowA.back(), c->rowP.empty() ? 0 : c->rowP.back(),
-                   2 * c->zelems * 8, maxn, c->gplan.ncta, c->gplan.tma ? -c->gplan.nstage : c->gplan.split};
-  for (int i = 0; i < n && i < 15; ++i) info[i] = v[i];
+                   2 * c->zelems * 8, maxn, c->gplan.ncta, c->gplan.tma ? -c->gplan.nstage : c->gplan.split,
+                   c->gplan.tma ? 0 : c->gplan.unroll, ns(c->tune_ms[0]), ns(c->tune_ms[1]),
+                   c->tune_rejected};
+  for (int i = 0; i < n && i < 19; ++i) info[i] = v[i];
+  return BEM_OK;
+}
+
+int aim_gemv_select(aim_ctx* c, int kind) {
+  BEM_TRY(check_ctx(c, "aim_gemv_select"));
+  if (kind < 0 || kind > 2) {
+    set_error("aim_gemv_select: kind must be 0 (autotuned), 1 (plain) or 2 (staged)");
+    return BEM_EINVAL;
+  }
+  const bem::GemvPlan& p = kind == 0 ? c->gplan_auto : c->gplan_alt[kind - 1];
+  if (p.ncta == 0) {
+    set_error("aim_gemv_select: no %s plan (no candidate of that kind ran correctly at set-up)",
+              kind == 2 ? "staged" : "plain");
+    return BEM_EINVAL;
+  }
+  BEM_CUDA(cudaDeviceSynchronize());
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old launches
+  c->graphs.clear();
+  c->gplan = p;
   return BEM_OK;
 }
 
@@ -257,6 +280,13 @@ int64_t aim_export(const aim_ctx* c, int what, int index, void* out, int64_t cap
       o[6 * n + 2] = c->et[2 * n]; o[6 * n + 3] = c->et[2 * n + 1];
       o[6 * n + 4] = c->eopp[2 * n]; o[6 * n + 5] = c->eopp[2 * n + 1];
     }
+    return need;
+  }
+  if (what == 8) {
+    int64_t need = (int64_t)c->tune_table.size() * 4;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    memcpy(out, c->tune_table.data(), need);
     return need;
   }
   set_error("aim_export: unknown item %d", what);

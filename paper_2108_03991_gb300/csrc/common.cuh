@@ -141,10 +141,21 @@ struct TmaStage {  // whole rows [r0, r1) streamed as one bulk copy of nel compl
   int32_t nel;
   int32_t pad;
 };
+// Row table of one stage, bulk-copied into shared memory beside the stage's matrix bytes so
+// the consumers never wait on global memory for it.
+constexpr int kTmaMaxRows = 64;  // rows per stage
+struct TmaDesc {
+  int32_t r0, nr, nel, pad;        // first global row, rows, complex elements in the stage
+  int32_t soff[kTmaMaxRows + 4];   // element offset of row k inside the stage; soff[nr] = nel
+  int32_t n[kTmaMaxRows];          // row length (block size)
+  int32_t xoff[kTmaMaxRows];       // offset of the block's slice of x
+};
+static_assert(sizeof(TmaDesc) % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 // Persistent launch of a block-diagonal product: CTA p streams the rows of its segments
 // [seg[cta_seg[p]], ..., seg[cta_seg[p+1]-1]], each a range [r0, r1) of global rows. With
-// tma set, the rows are fed through shared-memory stages by bulk copies (gemv_tma.cu).
+// tma set, the rows are fed through shared-memory stages by bulk copies (gemv_tma.cu); with
+// flat set, a CTA's rows are read as chunks of whole rows described like the stages.
 struct GemvPlan {
   RowInfo* rows = nullptr;   // device [nrows]
   int2* segs = nullptr;      // device [nseg]
@@ -152,12 +163,14 @@ struct GemvPlan {
   int ncta = 0;
   int nrows = 0;
   int split = 2;               // column parts per row (1, 2 or 4), picked by the autotuner
+  int unroll = 4;              // 16-byte loads in flight per lane (4 or 8), likewise
+  int flat = 0;                // flat form: rows in chunks (stages, descs, cta_stage as chunks)
   double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
   // bulk-copy staging
   int tma = 0;
   TmaStage* stages = nullptr;  // device
   int32_t* cta_stage = nullptr;// device [ncta + 1]
-  int32_t* soff = nullptr;     // device [nrows] element offset of a row inside its stage
+  TmaDesc* descs = nullptr;    // device [stages] row tables
   int nstage = 4;              // buffers in the ring
   int stage_bytes = 0;
   int* err = nullptr;          // device: non-zero after a bounded wait timed out
@@ -165,7 +178,7 @@ struct GemvPlan {
 bool build_tma_stages(const std::vector<RowInfo>& rows, const std::vector<int2>& segs,
                       const std::vector<int32_t>& cta_seg, int64_t stage_elems,
                       std::vector<TmaStage>* stages, std::vector<int32_t>* cta_stage,
-                      std::vector<int32_t>* soff);
+                      std::vector<TmaDesc>* descs);
 int tma_init_attrs();
 template <typename R>
 int run_gemv_tma(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
@@ -207,6 +220,11 @@ struct aim_ctx {
   std::vector<bem::GemvTask> tasks;
   bem::GemvPlan gplan;    // FP32 products (autotuned; may use bulk-copy staging)
   bem::GemvPlan gplan64;  // FP64 products
+  bem::GemvPlan gplan_auto;    // the autotuner's FP32 choice
+  bem::GemvPlan gplan_alt[2];  // best plain and best staged FP32 plans (ncta = 0: none)
+  float tune_ms[2] = {0, 0};  // autotuner: best plain, best staged candidate (5 launches, ms)
+  int tune_rejected = 0;      // autotuner candidates rejected (wrong product or timed out)
+  std::vector<float> tune_table;  // autotuner: (kind, cps, split, unroll, ns) per candidate
   bem::FftPlan plan[3];
   // device: integer tables
   int32_t* d_nodeE = nullptr;  // [ne] linear index of the anchor node
@@ -216,6 +234,11 @@ struct aim_ctx {
   int32_t* d_pcolE = nullptr;  // [27 ne] source (RWG) index
   int32_t* d_prowT = nullptr;  // [ng + 1]
   int32_t* d_pcolT = nullptr;  // [27 nt] source (triangle) index
+  // grid nodes with at least one entry in P (work list of the projection) and the others
+  // (zero-filled by the same launch); [0, nwE) then [nwE, ng) for RWG, likewise for pulses
+  int32_t* d_pnodeE = nullptr;  // [ng]
+  int32_t* d_pnodeT = nullptr;  // [ng]
+  int32_t nwE = 0, nwT = 0;
   int64_t* d_rowA = nullptr;
   int32_t* d_colA = nullptr;
   int64_t* d_rowP = nullptr;
@@ -255,6 +278,9 @@ struct aim_ctx {
   int32_t* d_pcperm = nullptr;  // object-major position -> system index
   float2* pcw32[2] = {nullptr, nullptr};
   double2* pcw64[2] = {nullptr, nullptr};
+  // GMRES workspace kept between solves (gmres.cu)
+  void* gm_ws = nullptr;
+  size_t gm_bytes = 0;
   // learned correction network on the AIM grid (learned.cu)
   void* net = nullptr;
 };

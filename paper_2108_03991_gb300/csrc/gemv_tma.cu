@@ -3,21 +3,23 @@
 //
 // Each persistent CTA owns a byte-balanced, contiguous range of matrix rows (rows of consecutive
 // blocks are adjacent in memory), cut on the host into stages of whole rows. A producer warp
-// streams the stages into a ring of shared-memory buffers with cp.async.bulk; an mbarrier's
-// transaction count signals arrival. Eight consumer warps treat a stage as one flat array of
-// 16-byte vectors split evenly between them whatever the row lengths; every lane accumulates the
-// dot product of its current row and adds it into a per-row partial in shared memory when its row
-// changes. The partials are written out (optionally as hsub - A x) when the stage is done and the
-// buffer goes back to the producer. Every wait is bounded: on a timeout the kernel records an
-// error code in *err and all warps leave together (the result is then invalid, the context
-// stays usable).
+// streams the stages into a ring of shared-memory slots with cp.async.bulk: the stage's matrix
+// bytes and its row table (TmaDesc) land in the slot and an mbarrier's transaction count
+// signals arrival. Sixteen consumer warps split a stage's 16-byte vectors evenly between them
+// whatever the row lengths; a warp walks the rows its share touches, lanes strided within a
+// row with 4 vectors in flight each (2 when two CTAs share an SM), and adds each row's warp sum
+// into a per-row partial in shared memory. The consumer warps do not meet at a barrier: a
+// per-slot counter elects the last warp done with a stage, which writes the stage's rows out
+// (optionally as hsub - A x) and clears the partials; every warp then releases the slot to the
+// producer.
+// Every wait is bounded: on a timeout the kernel records an error code in *err and the warps
+// leave (the result is then invalid, the context stays usable).
 #include "common.cuh"
 
 namespace bem {
 
-constexpr int kTmaConsumerWarps = 8;
+constexpr int kTmaConsumerWarps = 16;
 constexpr int kTmaThreads = (kTmaConsumerWarps + 1) * 32;
-constexpr int kTmaMaxRows = 64;          // rows per stage
 constexpr uint32_t kTmaSpin = 1u << 24;  // bounded mbarrier polls
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -53,20 +55,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// barrier of the consumer warps only (named barrier 1); returns true when any thread passed fail
-__device__ __forceinline__ bool consumers_any(bool fail) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)fail), "n"(kTmaConsumerWarps * 32)
-      : "memory");
-  return r != 0;
-}
-__device__ __forceinline__ void consumers_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kTmaConsumerWarps * 32) : "memory");
-}
 
 __device__ __forceinline__ void sadd(float2* p, float2 v) {
   atomicAdd(&p->x, v.x);
@@ -81,35 +69,55 @@ template <typename R> struct Vec16T;
 template <> struct Vec16T<float> { typedef float4 T; static constexpr int kCplx = 2; };
 template <> struct Vec16T<double> { typedef double2 T; static constexpr int kCplx = 1; };
 
+// shared-memory layout of one CTA (byte offsets), shared by the kernel and its launcher
+struct TmaSmem {
+  size_t desc, full, empty, done, part, total;
+  __host__ __device__ TmaSmem(int nst, int stage_bytes, int part_bytes) {
+    desc = (size_t)nst * stage_bytes;
+    full = desc + (size_t)nst * sizeof(TmaDesc);
+    empty = full + 8 * (size_t)nst;
+    done = empty + 8 * (size_t)nst;
+    part = (done + 4 * (size_t)nst + 15) & ~(size_t)15;
+    total = part + (size_t)nst * part_bytes;
+  }
+};
+
 template <typename R, int NRHS, int NST>
-__global__ void __launch_bounds__(kTmaThreads, 1)
-    k_gemv_tma(const RowInfo* __restrict__ rows, const int32_t* __restrict__ soff,
-               const TmaStage* __restrict__ stages, const int32_t* __restrict__ cta_stage,
-               const typename C2<R>::T* __restrict__ A, const typename C2<R>::T* __restrict__ x,
-               typename C2<R>::T* __restrict__ y, int64_t vstride,
-               const typename C2<R>::T* __restrict__ hsub, int stage_bytes, int* err) {
+__global__ void __launch_bounds__(kTmaThreads, NST == 3 ? 2 : 1)
+    k_gemv_tma(const TmaStage* __restrict__ stages, const TmaDesc* __restrict__ descs,
+               const int32_t* __restrict__ cta_stage, const typename C2<R>::T* __restrict__ A,
+               const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
+               int64_t vstride, const typename C2<R>::T* __restrict__ hsub, int stage_bytes,
+               int* err) {
   typedef typename C2<R>::T V;
   typedef typename Vec16T<R>::T L16;
   constexpr int CP = Vec16T<R>::kCplx;
+  constexpr int CW = kTmaConsumerWarps;
+  constexpr int kPart = kTmaMaxRows * NRHS;  // partials per slot
+  constexpr int kTmaU = NST == 3 ? 2 : 4;    // 16-byte vectors in flight per consumer lane
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* bufs = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)NST * stage_bytes);
-  uint64_t* empty = full + NST;
-  V* part = reinterpret_cast<V*>(empty + NST);  // [kTmaMaxRows][NRHS]
+  const TmaSmem L(NST, stage_bytes, kPart * (int)sizeof(V));
+  TmaDesc* desc = reinterpret_cast<TmaDesc*>(smem + L.desc);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.full);
+  uint64_t* empty = reinterpret_cast<uint64_t*>(smem + L.empty);
+  int* done = reinterpret_cast<int*>(smem + L.done);
+  V* part = reinterpret_cast<V*>(smem + L.part);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int st0 = cta_stage[blockIdx.x], nst = cta_stage[blockIdx.x + 1] - st0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kTmaConsumerWarps);
+      mbar_init(&empty[s], CW);
+      done[s] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < kTmaMaxRows * NRHS; i += blockDim.x) part[i] = czero<V>();
+  for (int i = threadIdx.x; i < NST * kPart; i += blockDim.x) part[i] = czero<V>();
   __syncthreads();
-  if (warp == kTmaConsumerWarps) {
+  if (warp == CW) {
     // ---------------- producer ----------------
     if (lane == 0) {
+      int issued = 0;
       for (int i = 0; i < nst; ++i) {
         const int s = i % NST;
         if (!mbar_wait(&empty[s], ((i / NST) & 1) ^ 1)) {
@@ -118,9 +126,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         }
         const TmaStage st = stages[st0 + i];
         const uint32_t bytes = (uint32_t)st.nel * (uint32_t)sizeof(V);
-        mbar_arrive_tx(&full[s], bytes);
-        bulk_g2s(bufs + (size_t)s * stage_bytes, A + st.e0, bytes, &full[s]);
+        mbar_arrive_tx(&full[s], bytes + (uint32_t)sizeof(TmaDesc));
+        bulk_g2s(smem + (size_t)s * stage_bytes, A + st.e0, bytes, &full[s]);
+        bulk_g2s(&desc[s], descs + st0 + i, (uint32_t)sizeof(TmaDesc), &full[s]);
+        issued = i + 1;
       }
+      // no copy may still be landing in shared memory when the CTA ends: wait (bounded) for
+      // the last copy into each slot (later waits on the same phase return at once)
+      for (int i = max(0, issued - NST); i < issued; ++i)
+        if (!mbar_wait(&full[i % NST], (i / NST) & 1)) atomicExch(err, 3);
     }
     return;
   }
@@ -128,67 +142,78 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
   for (int i = 0; i < nst; ++i) {
     const int s = i % NST;
     const bool ok = mbar_wait(&full[s], (i / NST) & 1);
-    if (consumers_any(!ok)) {
-      if (threadIdx.x == 0) atomicExch(err, 2);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicExch(err, 2);
       break;
     }
-    const TmaStage st = stages[st0 + i];
-    const int nr = st.r1 - st.r0;
-    const L16* sb = reinterpret_cast<const L16*>(bufs + (size_t)s * stage_bytes);
-    const int nvec = st.nel / CP;
-    const int per = (nvec + kTmaConsumerWarps - 1) / kTmaConsumerWarps;
-    const int v0 = warp * per, v1 = min(nvec, v0 + per);
-    if (v0 + lane < v1) {
-      int k = 0;
-      int e = (v0 + lane) * CP;
-      while (k < nr - 1 && e >= soff[st.r0 + k + 1]) ++k;
-      int rend = (k < nr - 1) ? soff[st.r0 + k + 1] : st.nel;
-      RowInfo ri = rows[st.r0 + k];
-      int rbeg = soff[st.r0 + k];
+    const TmaDesc& d = desc[s];
+    const int nr = d.nr;
+    const L16* sb = reinterpret_cast<const L16*>(smem + (size_t)s * stage_bytes);
+    V* ps = part + s * kPart;
+    // the warp's piece of the stage: an equal share of the 16-byte vectors, walked row by row
+    // (warp-uniform), lanes strided within a row; one warp reduction and one shared-memory
+    // add per (warp, row) pair
+    const int nvec = d.nel / CP;
+    const int per = (nvec + CW - 1) / CW;
+    const int v0 = min(nvec, warp * per), v1 = min(nvec, v0 + per);
+    int k = 0;
+    while (k + 1 < nr && d.soff[k + 1] <= v0 * CP) ++k;
+    for (int vs = v0; vs < v1; ++k) {
+      const int ve = min(v1, d.soff[k + 1] / CP);
+      const int nn = d.n[k], c0 = d.soff[k];
+      const V* xb = x + d.xoff[k] - c0;  // element e of the stage is column e - c0 of row k
       V acc[NRHS];
 #pragma unroll
       for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
-      for (int v = v0 + lane; v < v1; v += 32) {
-        e = v * CP;
-        if (e >= rend) {
-#pragma unroll
-          for (int r = 0; r < NRHS; ++r) { sadd(&part[k * NRHS + r], acc[r]); acc[r] = czero<V>(); }
-          while (k < nr - 1 && e >= soff[st.r0 + k + 1]) ++k;
-          rend = (k < nr - 1) ? soff[st.r0 + k + 1] : st.nel;
-          rbeg = soff[st.r0 + k];
-          ri = rows[st.r0 + k];
-        }
-        const int col = e - rbeg;
-        const L16 a = sb[v];
-        const V* xb = x + ri.xoff + col;
+      auto use = [&](const L16& a, int e) {
+        const int col = e - c0;
         if constexpr (CP == 2) {
-          if (col < ri.n) {
 #pragma unroll
-            for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride));
-          }
-          if (col + 1 < ri.n) {
-#pragma unroll
-            for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.z, a.w), __ldg(xb + r * vstride + 1));
+          for (int r = 0; r < NRHS; ++r) {
+            if (col < nn) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride + e));
+            if (col + 1 < nn) cfma(acc[r], mk(a.z, a.w), __ldg(xb + r * vstride + e + 1));
           }
         } else {
-          if (col < ri.n) {
 #pragma unroll
-            for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride));
-          }
+          for (int r = 0; r < NRHS; ++r)
+            if (col < nn) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride + e));
         }
-      }
+      };
+      int v = vs + lane;
+      for (; v + (kTmaU - 1) * 32 < ve; v += 32 * kTmaU) {
+        L16 a[kTmaU];
 #pragma unroll
-      for (int r = 0; r < NRHS; ++r) sadd(&part[k * NRHS + r], acc[r]);
+        for (int u = 0; u < kTmaU; ++u) a[u] = sb[v + 32 * u];
+#pragma unroll
+        for (int u = 0; u < kTmaU; ++u) use(a[u], (v + 32 * u) * CP);
+      }
+      for (; v < ve; v += 32) use(sb[v], v * CP);
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) {
+        const V t = warp_sum(acc[r]);
+        if (lane == 0) sadd(&ps[k * NRHS + r], t);
+      }
+      vs = ve;
     }
-    consumers_sync();
-    for (int t = threadIdx.x; t < nr * NRHS; t += kTmaConsumerWarps * 32) {
-      const int rr = t / NRHS, r = t - rr * NRHS;
-      const int64_t o = r * vstride + st.r0 + rr;
-      const V val = part[t];
-      y[o] = hsub ? csub(hsub[o], val) : val;
-      part[t] = czero<V>();
+    // the last consumer warp done with this stage writes its rows and clears the partials
+    __syncwarp();
+    __threadfence_block();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&done[s], 1) == CW - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence_block();
+      for (int t = lane; t < nr * NRHS; t += 32) {
+        const int rr = t / NRHS, r = t - rr * NRHS;
+        const int64_t o = r * vstride + d.r0 + rr;
+        const V val = ps[t];
+        y[o] = hsub ? csub(hsub[o], val) : val;
+        ps[t] = czero<V>();
+      }
+      if (lane == 0) done[s] = 0;
+      __syncwarp();
+      __threadfence_block();
     }
-    consumers_sync();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
@@ -198,12 +223,12 @@ static void launch_tma(const GemvPlan& p, const typename C2<R>::T* A, const type
                        typename C2<R>::T* y, int nr, int64_t vstride, const typename C2<R>::T* hs,
                        cudaStream_t s) {
   typedef typename C2<R>::T V;
-  const size_t sm = (size_t)NST * p.stage_bytes + 2 * NST * 8 + (size_t)kTmaMaxRows * 4 * sizeof(V);
-#define BEM_TMA(NR)                                                                               \
-  do {                                                                                           \
-    k_gemv_tma<R, NR, NST><<<p.ncta, kTmaThreads, sm, s>>>(p.rows, p.soff, p.stages, p.cta_stage, \
-                                                           A, x, y, vstride, hs, p.stage_bytes,   \
-                                                           p.err);                                \
+#define BEM_TMA(NR)                                                                                \
+  do {                                                                                            \
+    const TmaSmem L(NST, p.stage_bytes, kTmaMaxRows * NR * (int)sizeof(V));                       \
+    k_gemv_tma<R, NR, NST><<<p.ncta, kTmaThreads, L.total, s>>>(p.stages, p.descs, p.cta_stage, A, \
+                                                                x, y, vstride, hs, p.stage_bytes,  \
+                                                                p.err);                            \
   } while (0)
   switch (nr) {
     case 1: BEM_TMA(1); break;
@@ -233,7 +258,8 @@ template int run_gemv_tma<float>(const GemvPlan&, const float2*, const float2*, 
 template int run_gemv_tma<double>(const GemvPlan&, const double2*, const double2*, double2*, int,
                                   int64_t, const double2*, cudaStream_t);
 
-// Allow the ring of stages (up to 4 x 48 KB) in dynamic shared memory; called at set-up.
+// Allow the ring of slots (4 x 40 KB or 3 x 24 KB plus row tables and partials) in dynamic
+// shared memory; called at set-up.
 int tma_init_attrs() {
   const int lim = 200 * 1024;
 #define BEM_ATTR(RR, NR, NST) \
@@ -247,31 +273,39 @@ int tma_init_attrs() {
 }
 
 // Cut the rows of each CTA's byte-balanced range into stages of whole rows: at most stage_elems
-// complex elements (row storage ld = n rounded up to 4) and kTmaMaxRows rows. soff[row] is the
-// row's element offset inside its stage. False when one row does not fit a stage.
+// complex elements (row storage ld = n rounded up to 4) and kTmaMaxRows rows, each with its row
+// table. False when one row does not fit a stage.
 bool build_tma_stages(const std::vector<RowInfo>& rows, const std::vector<int2>& segs,
                       const std::vector<int32_t>& cta_seg, int64_t stage_elems,
                       std::vector<TmaStage>* stages, std::vector<int32_t>* cta_stage,
-                      std::vector<int32_t>* soff) {
+                      std::vector<TmaDesc>* descs) {
   const int ncta = (int)cta_seg.size() - 1;
   stages->clear();
+  descs->clear();
   cta_stage->assign(ncta + 1, 0);
-  soff->assign(rows.size(), 0);
   for (int c = 0; c < ncta; ++c) {
     for (int q = cta_seg[c]; q < cta_seg[c + 1]; ++q) {
       int cur = segs[q].x;
       const int end = segs[q].y;
       while (cur < end) {
         const int start = cur;
+        TmaDesc d{};
         int64_t el = 0;
         while (cur < end && cur - start < kTmaMaxRows) {
           const int64_t ld = (rows[cur].n + 3) & ~3;
-          if (el + ld > stage_elems) break;
-          (*soff)[cur] = (int32_t)el;
+          // rows of one stage must be adjacent in memory (one bulk copy)
+          if (el + ld > stage_elems || (cur > start && rows[cur].aoff != rows[start].aoff + el)) break;
+          d.soff[cur - start] = (int32_t)el;
+          d.n[cur - start] = rows[cur].n;
+          d.xoff[cur - start] = rows[cur].xoff;
           el += ld;
           ++cur;
         }
         if (cur == start) return false;
+        d.r0 = start;
+        d.nr = cur - start;
+        d.nel = (int32_t)el;
+        d.soff[d.nr] = (int32_t)el;
         TmaStage st;
         st.r0 = start;
         st.r1 = cur;
@@ -279,6 +313,7 @@ bool build_tma_stages(const std::vector<RowInfo>& rows, const std::vector<int2>&
         st.nel = (int32_t)el;
         st.pad = 0;
         stages->push_back(st);
+        descs->push_back(d);
       }
     }
     (*cta_stage)[c + 1] = (int32_t)stages->size();

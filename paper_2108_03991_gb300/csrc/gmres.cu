@@ -141,19 +141,45 @@ __global__ void k_set_g0(double2* g, int m1, const double* beta) {
   for (int i = threadIdx.x; i < m1; i += blockDim.x) g[i] = make_double2(i == 0 ? *beta : 0.0, 0.0);
 }
 
+// Krylov workspace, carved from one device buffer that the context keeps between solves
 struct GmWork {
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr,
-          *g = nullptr, *h = nullptr, *hacc = nullptr, *partial = nullptr, *y = nullptr;
+          *g = nullptr, *h = nullptr, *hacc = nullptr, *partial = nullptr, *y = nullptr, *Zb = nullptr;
   double* dsc = nullptr;  // [0] = subdiagonal, [1] = residual estimate, [2] = beta
-  std::vector<void*> mem;
-  ~GmWork() { for (void* p : mem) cudaFree(p); }
-  template <typename T> int alloc(T** p, size_t n) {
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
-    if (e != cudaSuccess) { set_error("gmres workspace: %s", cudaGetErrorString(e)); return BEM_ENOMEM; }
-    mem.push_back(*p);
-    return BEM_OK;
-  }
 };
+
+static int gm_workspace(aim_ctx* c, int64_t n, int m, bool flexible, GmWork* W) {
+  const int ldh = m + 1;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t z = sizeof(double2);
+  const size_t sizes[13] = {al((size_t)(m + 1) * n * z), al(n * z), al(n * z), al((size_t)ldh * m * z),
+                            al(m * z), al(m * z), al((m + 1) * z), al((m + 1) * z), al((m + 1) * z),
+                            al((size_t)(m + 1) * kChunks * z), al((m + 1) * z),
+                            flexible ? al((size_t)m * n * z) : 0, al(8 * sizeof(double))};
+  size_t total = 0;
+  for (size_t v : sizes) total += v;
+  if (c->gm_bytes < total) {
+    if (c->gm_ws) cudaFree(c->gm_ws);
+    c->gm_ws = nullptr;
+    c->gm_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->gm_ws, total);
+    if (e != cudaSuccess) {
+      set_error("gmres workspace (%zu bytes): %s", total, cudaGetErrorString(e));
+      c->gm_ws = nullptr;
+      return BEM_ENOMEM;
+    }
+    c->gm_bytes = total;
+  }
+  char* p = static_cast<char*>(c->gm_ws);
+  double2** dst[12] = {&W->V, &W->w, &W->r, &W->H, &W->cs, &W->sn, &W->g, &W->h, &W->hacc,
+                       &W->partial, &W->y, &W->Zb};
+  for (int i = 0; i < 12; ++i) {
+    *dst[i] = sizes[i] ? reinterpret_cast<double2*>(p) : nullptr;
+    p += sizes[i];
+  }
+  W->dsc = reinterpret_cast<double*>(p);
+  return BEM_OK;
+}
 
 static int dot_into(const double2* V, int64_t ldv, int nv, const double2* w, int64_t n, GmWork& W,
                     double2* h, double2* acc, cudaStream_t s) {
@@ -189,32 +215,21 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   const int64_t n = (int64_t)c->ne + c->nt;
   const int m = o->restart;
   const int ldh = m + 1;
+  // right preconditioning (flexible form: the preconditioned directions Zb are kept)
+  const bool flexible = o->precond == 1 || o->precond == 2;
+  if (flexible) BEM_TRY(setup_precond(c));
   GmWork W;
-  BEM_TRY(W.alloc(&W.V, (size_t)(m + 1) * n));
-  BEM_TRY(W.alloc(&W.w, n));
-  BEM_TRY(W.alloc(&W.r, n));
-  BEM_TRY(W.alloc(&W.H, (size_t)ldh * m));
-  BEM_TRY(W.alloc(&W.cs, m));
-  BEM_TRY(W.alloc(&W.sn, m));
-  BEM_TRY(W.alloc(&W.g, m + 1));
-  BEM_TRY(W.alloc(&W.h, m + 1));
-  BEM_TRY(W.alloc(&W.hacc, m + 1));
-  BEM_TRY(W.alloc(&W.y, m + 1));
-  BEM_TRY(W.alloc(&W.partial, (size_t)(m + 1) * kChunks));
-  BEM_TRY(W.alloc(&W.dsc, 8));
-  // right preconditioning (flexible form: the preconditioned directions are kept)
-  double2* Zb = nullptr;
-  if (o->precond == 1 || o->precond == 2) {
-    BEM_TRY(setup_precond(c));
-    BEM_TRY(W.alloc(&Zb, (size_t)m * n));
-  }
+  BEM_TRY(gm_workspace(c, n, m, flexible, &W));
+  double2* Zb = W.Zb;
   BEM_CUDA(cudaMemsetAsync(W.H, 0, sizeof(double2) * ldh * m, s));
-  // ||b||
+  // ||b|| and ||x0|| (a zero initial guess needs no first matvec: r = b)
   BEM_TRY(dot_into(b, n, 1, b, n, W, W.h, nullptr, s));
-  double2 bb;
-  BEM_CUDA(cudaMemcpyAsync(&bb, W.h, sizeof(double2), cudaMemcpyDeviceToHost, s));
+  BEM_TRY(dot_into(x, n, 1, x, n, W, W.h + 1, nullptr, s));
+  double2 bb[2];
+  BEM_CUDA(cudaMemcpyAsync(bb, W.h, 2 * sizeof(double2), cudaMemcpyDeviceToHost, s));
   BEM_CUDA(cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(std::max(bb.x, 0.0));
+  const double bnorm = std::sqrt(std::max(bb[0].x, 0.0));
+  bool x_zero = bb[1].x == 0.0;
   int iters = 0;
   double est = 1.0, truer = 1.0;
   int status = BEM_ENOCONV;
@@ -225,10 +240,15 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   }
   while (status != BEM_OK && iters < o->max_iter) {
     // r = b - A x (FP64 matvec), beta = ||r||
-    BEM_TRY(sys_apply(c, BEM_C64, x, W.w, s));
-    k_sub<<<kChunks, 256, 0, s>>>(b, W.w, W.r, n);
-    BEM_TRY(dot_into(W.r, n, 1, W.r, n, W, W.h, nullptr, s));
-    k_normalize<<<kChunks, 256, 0, s>>>(W.r, W.h, W.V, W.dsc + 2, n);
+    const double2* r = b;
+    if (!x_zero) {
+      BEM_TRY(sys_apply(c, BEM_C64, x, W.w, s));
+      k_sub<<<kChunks, 256, 0, s>>>(b, W.w, W.r, n);
+      r = W.r;
+    }
+    x_zero = false;
+    BEM_TRY(dot_into(r, n, 1, r, n, W, W.h, nullptr, s));
+    k_normalize<<<kChunks, 256, 0, s>>>(r, W.h, W.V, W.dsc + 2, n);
     double beta;
     BEM_CUDA(cudaMemcpyAsync(&beta, W.dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaStreamSynchronize(s));

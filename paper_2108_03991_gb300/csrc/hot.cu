@@ -19,41 +19,51 @@ template <typename R> struct Vec16;
 template <> struct Vec16<float> { typedef float4 T; static constexpr int kCplx = 2; };
 template <> struct Vec16<double> { typedef double2 T; static constexpr int kCplx = 1; };
 
+// acc[r] += sum over the 16-byte vectors [v0, v1) of one row of A (lane-strided) times x_r.
+// U vectors per lane are loaded before any is used, so each lane keeps U loads in flight.
+template <typename R, int NRHS, int U>
+__device__ __forceinline__ void dot_range(const typename Vec16<R>::T* __restrict__ arow,
+                                          const typename C2<R>::T* __restrict__ xb, int n, int v0,
+                                          int v1, int64_t vstride, int lane,
+                                          typename C2<R>::T* acc) {
+  typedef typename Vec16<R>::T L16;
+  constexpr int CP = Vec16<R>::kCplx;
+  auto use = [&](const L16& a, int col) {
+    if constexpr (CP == 2) {
+      const auto a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) {
+        cfma(acc[r], a0, __ldg(xb + r * vstride + col));
+        if (col + 1 < n) cfma(acc[r], a1, __ldg(xb + r * vstride + col + 1));
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride + col));
+    }
+  };
+  int v = v0 + lane;
+  for (; v + (U - 1) * 32 < v1; v += U * 32) {
+    L16 a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = __ldcs(arow + v + 32 * u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) use(a[u], (v + 32 * u) * CP);
+  }
+  for (; v < v1; v += 32) use(__ldcs(arow + v), v * CP);
+}
+
 // One row of the product, one warp: acc[r] = sum_k A[row, k] x_r[k]. Rows are streamed with
 // 16-byte loads (two complex FP32 or one complex FP64 per load), evict-first so the streamed
 // matrix does not displace the vectors in L2; x is read through the read-only path (L1).
 template <typename R, int NRHS>
-__device__ __forceinline__ void row_dot(const typename C2<R>::T* __restrict__ arow_,
+__device__ __forceinline__ void row_dot(const typename C2<R>::T* __restrict__ arow,
                                         const typename C2<R>::T* __restrict__ xb, int n,
                                         int64_t vstride, int lane, typename C2<R>::T* acc) {
-  typedef typename C2<R>::T V;
-  typedef typename Vec16<R>::T L16;
   constexpr int CP = Vec16<R>::kCplx;
-  const L16* arow = reinterpret_cast<const L16*>(arow_);
 #pragma unroll
-  for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
-  const int nvec = (n + CP - 1) / CP;
-#pragma unroll 4
-  for (int v = lane; v < nvec; v += 32) {
-    L16 a = __ldcs(arow + v);
-    const int col = v * CP;
-    if constexpr (CP == 2) {
-      V a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
-#pragma unroll
-      for (int r = 0; r < NRHS; ++r) {
-        V x0 = __ldg(xb + r * vstride + col);
-        cfma(acc[r], a0, x0);
-        if (col + 1 < n) {
-          V x1 = __ldg(xb + r * vstride + col + 1);
-          cfma(acc[r], a1, x1);
-        }
-      }
-    } else {
-      V a0 = mk(a.x, a.y);
-#pragma unroll
-      for (int r = 0; r < NRHS; ++r) cfma(acc[r], a0, __ldg(xb + r * vstride + col));
-    }
-  }
+  for (int r = 0; r < NRHS; ++r) acc[r] = czero<typename C2<R>::T>();
+  dot_range<R, NRHS, 4>(reinterpret_cast<const typename Vec16<R>::T*>(arow), xb, n, 0,
+                        (n + CP - 1) / CP, vstride, lane, acc);
 #pragma unroll
   for (int r = 0; r < NRHS; ++r) acc[r] = warp_sum(acc[r]);
 }
@@ -87,11 +97,12 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks
 // cut into S equal column parts; the S * rows work items of a chunk are dealt to the 8 warps
 // in turn (one warp reduction per part), partial sums meet in shared memory and the CTA adds
 // the S parts of each row at the end of the chunk. S = 1 is one warp per row; S = 2 or 4
-// evens out the work of the warps when a CTA holds only a few rows per warp.
+// evens out the work of the warps when a CTA holds only a few rows per warp. U = loads in
+// flight per lane (U = 8 needs more registers: 4 CTAs per SM instead of 6).
 constexpr int kGemvChunk = 64;
 
-template <typename R, int NRHS, int S>
-__global__ void __launch_bounds__(kGemvThreads, kGemvCtasPerSm)
+template <typename R, int NRHS, int S, int U>
+__global__ void __launch_bounds__(kGemvThreads, U >= 8 ? 4 : kGemvCtasPerSm)
     k_gemv_plan(const RowInfo* __restrict__ rows, const int2* __restrict__ segs,
                 const int32_t* __restrict__ cta_seg, const typename C2<R>::T* __restrict__ A,
                 const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
@@ -113,27 +124,11 @@ __global__ void __launch_bounds__(kGemvThreads, kGemvCtasPerSm)
         const int nvec = (ri.n + CP - 1) / CP;
         const int per = (nvec + S - 1) / S;
         const int v0 = pp * per, v1 = min(nvec, v0 + per);
-        const L16* arow = reinterpret_cast<const L16*>(A + ri.aoff);
-        const V* xb = x + ri.xoff;
         V acc[NRHS];
 #pragma unroll
         for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
-#pragma unroll 4
-        for (int v = v0 + lane; v < v1; v += 32) {
-          const L16 a = __ldcs(arow + v);
-          const int col = v * CP;
-          if constexpr (CP == 2) {
-            const V a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
-#pragma unroll
-            for (int r = 0; r < NRHS; ++r) {
-              cfma(acc[r], a0, __ldg(xb + r * vstride + col));
-              if (col + 1 < ri.n) cfma(acc[r], a1, __ldg(xb + r * vstride + col + 1));
-            }
-          } else {
-#pragma unroll
-            for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride + col));
-          }
-        }
+        dot_range<R, NRHS, U>(reinterpret_cast<const L16*>(A + ri.aoff), x + ri.xoff, ri.n, v0, v1,
+                              vstride, lane, acc);
 #pragma unroll
         for (int r = 0; r < NRHS; ++r) {
           const V t = warp_sum(acc[r]);
@@ -154,15 +149,102 @@ __global__ void __launch_bounds__(kGemvThreads, kGemvCtasPerSm)
   }
 }
 
-template <typename R, int S>
+template <typename R, int S, int U>
 static void launch_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A,
                              const typename C2<R>::T* x, typename C2<R>::T* y, int nr,
                              int64_t vstride, const typename C2<R>::T* hs, cudaStream_t s) {
   switch (nr) {
-    case 1: k_gemv_plan<R, 1, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
-    case 2: k_gemv_plan<R, 2, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
-    case 3: k_gemv_plan<R, 3, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
-    default: k_gemv_plan<R, 4, S><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    case 1: k_gemv_plan<R, 1, S, U><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    case 2: k_gemv_plan<R, 2, S, U><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    case 3: k_gemv_plan<R, 3, S, U><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+    default: k_gemv_plan<R, 4, S, U><<<p.ncta, kGemvThreads, 0, s>>>(p.rows, p.segs, p.cta_seg, A, x, y, vstride, hs); break;
+  }
+}
+
+template <typename R, int U>
+static void launch_gemv_plan_u(const GemvPlan& p, const typename C2<R>::T* A,
+                               const typename C2<R>::T* x, typename C2<R>::T* y, int nr,
+                               int64_t vstride, const typename C2<R>::T* hs, cudaStream_t s) {
+  switch (p.split) {
+    case 1: launch_gemv_plan<R, 1, U>(p, A, x, y, nr, vstride, hs, s); break;
+    case 4: launch_gemv_plan<R, 4, U>(p, A, x, y, nr, vstride, hs, s); break;
+    default: launch_gemv_plan<R, 2, U>(p, A, x, y, nr, vstride, hs, s); break;
+  }
+}
+
+// Flat form: a CTA's rows are adjacent in memory, so its range is one contiguous run of matrix
+// bytes. It is taken in chunks of at most kTmaMaxRows whole rows (the row tables of the staged
+// form); the 8 warps split a chunk's 16-byte vectors evenly whatever the row lengths, walk the
+// rows their share touches (lanes strided within a row, U loads in flight per lane) and add each
+// row's warp sum into a per-row partial in shared memory. No warp waits on another's rows, and
+// every warp of every CTA streams the same number of bytes (to one vector).
+template <typename R, int NRHS, int U>
+__global__ void __launch_bounds__(kGemvThreads, U >= 8 ? 4 : kGemvCtasPerSm)
+    k_gemv_flat(const TmaStage* __restrict__ chunks, const TmaDesc* __restrict__ descs,
+                const int32_t* __restrict__ cta_chunk, const typename C2<R>::T* __restrict__ A,
+                const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
+                int64_t vstride, const typename C2<R>::T* __restrict__ hsub) {
+  typedef typename C2<R>::T V;
+  typedef typename Vec16<R>::T L16;
+  constexpr int CP = Vec16<R>::kCplx;
+  constexpr int nw = kGemvThreads / 32;
+  __shared__ __align__(16) TmaDesc d;
+  __shared__ V part[kTmaMaxRows * NRHS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ch1 = cta_chunk[blockIdx.x + 1];
+  for (int ch = cta_chunk[blockIdx.x]; ch < ch1; ++ch) {
+    {
+      const int4* src = reinterpret_cast<const int4*>(descs + ch);
+      int4* dst = reinterpret_cast<int4*>(&d);
+      for (int i = threadIdx.x; i < (int)(sizeof(TmaDesc) / 16); i += blockDim.x) dst[i] = src[i];
+      for (int i = threadIdx.x; i < kTmaMaxRows * NRHS; i += blockDim.x) part[i] = czero<V>();
+    }
+    const L16* a16 = reinterpret_cast<const L16*>(A + chunks[ch].e0);
+    __syncthreads();
+    const int nr = d.nr;
+    const int nvec = d.nel / CP;
+    const int per = (nvec + nw - 1) / nw;
+    const int v0 = min(nvec, warp * per), v1 = min(nvec, v0 + per);
+    int k = 0;
+    while (k + 1 < nr && d.soff[k + 1] <= v0 * CP) ++k;
+    for (int vs = v0; vs < v1; ++k) {
+      const int ve = min(v1, d.soff[k + 1] / CP);
+      const int c0 = d.soff[k];
+      V acc[NRHS];
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
+      // element e of the chunk is column e - c0 of row k: shift the row's x slice by c0 and
+      // let dot_range count columns from the chunk start (its bound n becomes c0 + n)
+      dot_range<R, NRHS, U>(a16, x + d.xoff[k] - c0, c0 + d.n[k], vs, ve, vstride, lane, acc);
+#pragma unroll
+      for (int r = 0; r < NRHS; ++r) {
+        const V t = warp_sum(acc[r]);
+        if (lane == 0) {
+          atomicAdd(&part[k * NRHS + r].x, t.x);
+          atomicAdd(&part[k * NRHS + r].y, t.y);
+        }
+      }
+      vs = ve;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * NRHS; t += blockDim.x) {
+      const int rr = t / NRHS, r = t - rr * NRHS;
+      const int64_t o = r * vstride + d.r0 + rr;
+      y[o] = hsub ? csub(hsub[o], part[t]) : part[t];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R, int U>
+static void launch_gemv_flat(const GemvPlan& p, const typename C2<R>::T* A,
+                             const typename C2<R>::T* x, typename C2<R>::T* y, int nr,
+                             int64_t vstride, const typename C2<R>::T* hs, cudaStream_t s) {
+  switch (nr) {
+    case 1: k_gemv_flat<R, 1, U><<<p.ncta, kGemvThreads, 0, s>>>(p.stages, p.descs, p.cta_stage, A, x, y, vstride, hs); break;
+    case 2: k_gemv_flat<R, 2, U><<<p.ncta, kGemvThreads, 0, s>>>(p.stages, p.descs, p.cta_stage, A, x, y, vstride, hs); break;
+    case 3: k_gemv_flat<R, 3, U><<<p.ncta, kGemvThreads, 0, s>>>(p.stages, p.descs, p.cta_stage, A, x, y, vstride, hs); break;
+    default: k_gemv_flat<R, 4, U><<<p.ncta, kGemvThreads, 0, s>>>(p.stages, p.descs, p.cta_stage, A, x, y, vstride, hs); break;
   }
 }
 
@@ -176,10 +258,13 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
     const int nr = std::min(4, nrhs - r0);
     const int64_t o = r0 * vstride;
     const typename C2<R>::T* hs = hsub ? hsub + o : nullptr;
-    switch (p.split) {
-      case 1: launch_gemv_plan<R, 1>(p, A, x + o, y + o, nr, vstride, hs, s); break;
-      case 4: launch_gemv_plan<R, 4>(p, A, x + o, y + o, nr, vstride, hs, s); break;
-      default: launch_gemv_plan<R, 2>(p, A, x + o, y + o, nr, vstride, hs, s); break;
+    if (p.flat) {
+      if (p.unroll >= 8) launch_gemv_flat<R, 8>(p, A, x + o, y + o, nr, vstride, hs, s);
+      else launch_gemv_flat<R, 4>(p, A, x + o, y + o, nr, vstride, hs, s);
+    } else if (p.unroll >= 8) {
+      launch_gemv_plan_u<R, 8>(p, A, x + o, y + o, nr, vstride, hs, s);
+    } else {
+      launch_gemv_plan_u<R, 4>(p, A, x + o, y + o, nr, vstride, hs, s);
     }
   }
   BEM_CUDA(cudaGetLastError());
@@ -215,91 +300,89 @@ template int run_gemv<double>(const GemvTask*, int, const double2*, const double
                               int64_t, const double2*, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------
-// projection P: scatter with atomics, one thread per (source, stencil node)
+// projection P (Sec. III-A item 1): gather form, no atomics, deterministic
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int node_offset(int k, int nx, int ny) {
   return ((k / 9 - 1) * ny + ((k / 3) % 3 - 1)) * nx + (k % 3 - 1);
 }
 
-// complex atomic add: one 8-byte vector atomic in FP32, two scalar atomics in FP64
-__device__ __forceinline__ void catomic_add(float2* o, float2 v) { atomicAdd(o, v); }
-__device__ __forceinline__ void catomic_add(double2* o, double2 v) {
-  atomicAdd(&o->x, v.x);
-  atomicAdd(&o->y, v.y);
-}
+// sigma_c(node) = sum over the CSR entries e of the node of WT[e][c] * src[col[e]], for the NC
+// components of one source kind. A group of G lanes shares one node of the work list (the nodes
+// some stencil touches): the lanes take every G-th entry, so a node's entries are fetched in
+// parallel, and meet in a shuffle reduction. Blocks past nb_work write the zeros of the nodes
+// no stencil touches (the rest of the work list), so every node is written each time.
+constexpr int kProjG = 8;
 
-template <typename R>
-__global__ void k_scatter_e(const R* __restrict__ WA, const int32_t* __restrict__ node,
-                            const typename C2<R>::T* __restrict__ j, typename C2<R>::T* sigma,
-                            int ne, int nx, int ny, int64_t ng) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)ne * 27) return;
-  const int m = (int)(idx / 27), k = (int)(idx - (int64_t)m * 27);
-  const typename C2<R>::T v = j[m];
-  const int64_t nd = node[m] + node_offset(k, nx, ny);
+template <typename R, int NC>
+__global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ work, int nwork,
+                                                 int64_t ng, int nb_work,
+                                                 const int32_t* __restrict__ prow,
+                                                 const int32_t* __restrict__ pcol,
+                                                 const R* __restrict__ WT,
+                                                 const typename C2<R>::T* __restrict__ src,
+                                                 typename C2<R>::T* __restrict__ sigma) {
+  typedef typename C2<R>::T V;
+  if ((int)blockIdx.x >= nb_work) {
+    const int64_t i = nwork + (int64_t)(blockIdx.x - nb_work) * blockDim.x + threadIdx.x;
+    if (i < ng) {
+      const int nd = work[i];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R w = WA[(int64_t)m * 81 + c * 27 + k];
-    catomic_add(sigma + c * ng + nd, mk(w * v.x, w * v.y));
+      for (int c = 0; c < NC; ++c) sigma[c * ng + nd] = czero<V>();
+    }
+    return;
+  }
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kProjG;
+  const int l = threadIdx.x & (kProjG - 1);
+  V acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = czero<V>();
+  int nd = 0;
+  if (g < nwork) {
+    nd = work[g];
+    const int e1 = prow[nd + 1];
+#pragma unroll 4
+    for (int e = prow[nd] + l; e < e1; e += kProjG) {
+      const V v = src[pcol[e]];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const R w = WT[(int64_t)NC * e + c];
+        acc[c].x += w * v.x;
+        acc[c].y += w * v.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = kProjG / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+    }
+  if (l == 0 && g < nwork) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sigma[c * ng + nd] = acc[c];
   }
 }
 
-template <typename R>
-__global__ void k_scatter_t(const R* __restrict__ WP, const int32_t* __restrict__ node,
-                            const typename C2<R>::T* __restrict__ q, typename C2<R>::T* sigma,
-                            int nt, int nx, int ny) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nt * 27) return;
-  const int t = (int)(idx / 27), k = (int)(idx - (int64_t)t * 27);
-  const typename C2<R>::T v = q[t];
-  const R w = WP[(int64_t)t * 27 + k];
-  catomic_add(sigma + node[t] + node_offset(k, nx, ny), mk(w * v.x, w * v.y));
-}
+static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Gather form of the projection (no atomics, deterministic): one thread per grid node sums the
-// sources whose stencils touch it, from the node-major CSR of P^T. Every node is written, so
-// the grids need no clearing.
+// sigma_{x,y,z} = P_c j (RWG sources, 3 components)
 template <typename R>
-__global__ void __launch_bounds__(256) k_project_e(const int32_t* __restrict__ prow,
-                                                   const int32_t* __restrict__ pcol,
-                                                   const R* __restrict__ WT,
-                                                   const typename C2<R>::T* __restrict__ j,
-                                                   typename C2<R>::T* __restrict__ sigma, int64_t ng) {
-  typedef typename C2<R>::T V;
-  const int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (nd >= ng) return;
-  V a0 = czero<V>(), a1 = czero<V>(), a2 = czero<V>();
-  const int e1 = prow[nd + 1];
-  for (int e = prow[nd]; e < e1; ++e) {
-    const V v = j[pcol[e]];
-    const R w0 = WT[3 * (int64_t)e], w1 = WT[3 * (int64_t)e + 1], w2 = WT[3 * (int64_t)e + 2];
-    a0.x += w0 * v.x; a0.y += w0 * v.y;
-    a1.x += w1 * v.x; a1.y += w1 * v.y;
-    a2.x += w2 * v.x; a2.y += w2 * v.y;
-  }
-  sigma[nd] = a0;
-  sigma[ng + nd] = a1;
-  sigma[2 * ng + nd] = a2;
+static void project_e(const aim_ctx* c, const R* WT, const typename C2<R>::T* j,
+                      typename C2<R>::T* sigma, cudaStream_t s) {
+  const int nbw = (int)nb((int64_t)c->nwE * kProjG, 256);
+  const int nbz = (int)nb(c->ng - c->nwE, 256);
+  k_project<R, 3><<<nbw + nbz, 256, 0, s>>>(c->d_pnodeE, c->nwE, c->ng, nbw, c->d_prowE,
+                                            c->d_pcolE, WT, j, sigma);
 }
-
+// sigma_q = P_Phi q (pulse sources, 1 component)
 template <typename R>
-__global__ void __launch_bounds__(256) k_project_t(const int32_t* __restrict__ prow,
-                                                   const int32_t* __restrict__ pcol,
-                                                   const R* __restrict__ WT,
-                                                   const typename C2<R>::T* __restrict__ q,
-                                                   typename C2<R>::T* __restrict__ sigma, int64_t ng) {
-  typedef typename C2<R>::T V;
-  const int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (nd >= ng) return;
-  V a = czero<V>();
-  const int e1 = prow[nd + 1];
-  for (int e = prow[nd]; e < e1; ++e) {
-    const V v = q[pcol[e]];
-    const R w = WT[e];
-    a.x += w * v.x;
-    a.y += w * v.y;
-  }
-  sigma[nd] = a;
+static void project_t(const aim_ctx* c, const R* WT, const typename C2<R>::T* q,
+                      typename C2<R>::T* sigma, cudaStream_t s) {
+  const int nbw = (int)nb((int64_t)c->nwT * kProjG, 256);
+  const int nbz = (int)nb(c->ng - c->nwT, 256);
+  k_project<R, 1><<<nbw + nbz, 256, 0, s>>>(c->d_pnodeT, c->nwT, c->ng, nbw, c->d_prowT,
+                                            c->d_pcolT, WT, q, sigma);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -307,6 +390,26 @@ __global__ void __launch_bounds__(256) k_project_t(const int32_t* __restrict__ p
 // ---------------------------------------------------------------------------------------
 template <typename V, typename R>
 __device__ __forceinline__ V jk0(V a, R k0) { return mk(-k0 * a.y, k0 * a.x); }
+
+// acc += sum over the CSR row [i0, i1) of val[i] * x[col[i]], one warp; four independent
+// entries per lane are in flight at a time (the column load and the gather it feeds are a
+// dependent pair, so a plain loop would wait on both for every entry)
+template <typename V>
+__device__ __forceinline__ void near_row(const V* __restrict__ val, const int32_t* __restrict__ col,
+                                         const V* __restrict__ x, int64_t i0, int64_t i1, int lane,
+                                         V& acc) {
+  int64_t i = i0 + lane;
+  for (; i + 96 < i1; i += 128) {
+    const int c0 = col[i], c1 = col[i + 32], c2 = col[i + 64], c3 = col[i + 96];
+    const V a0 = val[i], a1 = val[i + 32], a2 = val[i + 64], a3 = val[i + 96];
+    const V x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    cfma(acc, a0, x0);
+    cfma(acc, a1, x1);
+    cfma(acc, a2, x2);
+    cfma(acc, a3, x3);
+  }
+  for (; i < i1; i += 32) cfma(acc, val[i], x[col[i]]);
+}
 
 // p_t = (W_Phi phi)_t + (L^Phi_NR q)_t, written to out[t] (y for L^Phi alone, p in the system)
 template <typename R>
@@ -325,7 +428,7 @@ __global__ void __launch_bounds__(256) k_rows_t(
     const V f = phi[node[t] + node_offset(lane, nx, ny)];
     acc = mk(w * f.x, w * f.y);
   }
-  for (int64_t i = rowP[t] + lane; i < rowP[t + 1]; i += 32) cfma(acc, LP[i], q[colP[i]]);
+  near_row(LP, colP, q, rowP[t], rowP[t + 1], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) out[t] = acc;
 }
@@ -373,7 +476,7 @@ __global__ void __launch_bounds__(256) k_rows_e(
       acc.y += w * f.y;
     }
   }
-  for (int64_t i = rowA[m] + lane; i < rowA[m + 1]; i += 32) cfma(acc, LA[i], j[colA[i]]);
+  near_row(LA, colA, j, rowA[m], rowA[m + 1], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) {
     if (mode == 0) {
@@ -396,8 +499,6 @@ __global__ void __launch_bounds__(256) k_rows_e(
   }
 }
 
-static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
 template <typename R> PrecBuf<R>& buf(aim_ctx* c);
 template <> PrecBuf<float>& buf<float>(aim_ctx* c) { return c->f32; }
 template <> PrecBuf<double>& buf<double>(aim_ctx* c) { return c->f64; }
@@ -413,14 +514,14 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
   const R k0 = (R)c->k0;
   const int64_t P3 = (int64_t)c->gp[0] * c->gp[1] * c->gp[2];
   if (which == AIM_OP_LA) {
-    k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, x, b.sigma, ng);
+    project_e<R>(c, b.WAT, x, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
                                           x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
                                           nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr);
   } else if (which == AIM_OP_LPHI) {
     V* sq = b.sigma + 3 * ng;
-    k_project_t<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowT, c->d_pcolT, b.WPT, x, sq, ng);
+    project_t<R>(c, b.WPT, x, sq, s);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, s));
     k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x, nt,
                                           nx, ny, y);
@@ -432,7 +533,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     V* sq = b.sigma + 3 * ng;
     BEM_CUDA(cudaEventRecord(c->ev_fork, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    k_project_t<R><<<nb(ng, 256), 256, 0, c->side>>>(c->d_prowT, c->d_pcolT, b.WPT, q, sq, ng);
+    project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
                                                 nt, nx, ny, b.p);
@@ -440,7 +541,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
     BEM_TRY(run_gemv_plan<R>(gp, b.Y, b.e, b.j, 1, ne, h, s));
-    k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, b.j, b.sigma, ng);
+    project_e<R>(c, b.WAT, b.j, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     k_rows_e<R><<<nb(ne + nt, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
@@ -551,8 +652,8 @@ template <typename R>
 int project_all(aim_ctx* c, const typename C2<R>::T* r, typename C2<R>::T* sigma, cudaStream_t s) {
   PrecBuf<R>& b = buf<R>(c);
   const int64_t ng = c->ng;
-  k_project_e<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowE, c->d_pcolE, b.WAT, r, sigma, ng);
-  k_project_t<R><<<nb(ng, 256), 256, 0, s>>>(c->d_prowT, c->d_pcolT, b.WPT, r + c->ne, sigma + 3 * ng, ng);
+  project_e<R>(c, b.WAT, r, sigma, s);
+  project_t<R>(c, b.WPT, r + c->ne, sigma + 3 * ng, s);
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }

@@ -400,9 +400,7 @@ __global__ void k_rhs_pw(DGeo g, int ne, int nt, double k0, double px, double py
 }
 
 // ---------------------------------------------------------------------------------------
-// GEMV autotuner: for the block layout (n, off, ld) of the FP32 matrix A, time the persistent
-// GEMV for {4, 6} CTAs per SM x {1, 2, 4} column parts per row with CUDA events on the real
-// data and keep the fastest plan (uploaded into the context).
+// Persistent GEMV plans: upload a byte-balanced row plan into the context.
 // ---------------------------------------------------------------------------------------
 static int upload_plan(aim_ctx* c, const std::vector<RowInfo>& rows, const std::vector<int2>& segs,
                        const std::vector<int32_t>& cseg, GemvPlan* p) {
@@ -433,25 +431,106 @@ struct TunePlan {  // a candidate plan held in temporary device memory
 };
 
 // GEMV autotuner: for the block layout (n, off, ld) of the FP32 matrix A, time the candidate
-// launches with CUDA events on the real data and keep the fastest: the plain persistent kernel
-// with {4, 6} CTAs per SM x {1, 2, 4} column parts per row, and the bulk-copy-staged kernel
-// with {1, 2} CTAs per SM (when every row fits a stage). out32 receives the winner; out64 (the
-// FP64 products) the best plain candidate.
+// launches with CUDA events on the real data and keep the fastest. Candidates: the row-plan
+// kernel with (CTAs per SM, loads in flight per lane) in {(6, 4), (4, 4), (4, 8)} x {1, 2, 4}
+// column parts per row; the flat kernel with (6, 4) and (4, 8); the bulk-copy-staged kernel
+// with 1 CTA per SM (4 stages of 40 KB) and 2 (3 of 24 KB), when every row fits a stage.
+// Every candidate's product of a fixed x is checked against the first candidate's; a launch
+// that disagrees beyond FP32 rounding, or whose bounded waits timed out, is rejected and counted
+// in tune_rejected. out32 receives the winner, out64 (the FP64 products) the best register-path
+// candidate, alt (if not null) the best register-path and the best staged FP32 plan. tune_ms
+// receives the time of 5 launches of those two.
+namespace {
+struct GemvCand {
+  int kind;   // 0 row plan, 1 flat, 2 staged
+  int cps;    // CTAs per SM
+  int split;  // column parts per row (row plan)
+  int unroll; // loads in flight per lane (row plan, flat)
+};
+}  // namespace
+
+// Build and upload the plan of candidate g (into context memory when c_owned, else into t).
+static int make_gemv_plan(aim_ctx* c, TunePlan* t, const GemvCand& g, int nsm,
+                          const std::vector<int32_t>& n, const std::vector<int64_t>& off,
+                          const std::vector<int32_t>& ld, int* derr, GemvPlan* out) {
+  std::vector<RowInfo> rows;
+  std::vector<int2> segs;
+  std::vector<int32_t> cseg, cst;
+  std::vector<TmaStage> st;
+  std::vector<TmaDesc> dsc;
+  GemvPlan p;
+  build_gemv_plan(n, off, ld, nsm * g.cps, &rows, &segs, &cseg, &p.cmax_over_ideal);
+  const int stage_bytes = g.cps == 1 ? 40 * 1024 : 24 * 1024;
+  if (g.kind != 0) {
+    const int64_t lim = g.kind == 2 ? stage_bytes / (int)sizeof(float2) : ((int64_t)1 << 40);
+    if (!build_tma_stages(rows, segs, cseg, lim, &st, &cst, &dsc)) return 1;  // not applicable
+  }
+  auto put = [&](auto** d, const auto& h) -> int {
+    if (t) return t->put(d, h);
+    return upload(c, d, h.data(), h.size());
+  };
+  BEM_TRY(put(&p.rows, rows));
+  BEM_TRY(put(&p.segs, segs));
+  BEM_TRY(put(&p.cta_seg, cseg));
+  p.ncta = nsm * g.cps;
+  p.nrows = (int)rows.size();
+  p.split = g.split;
+  p.unroll = g.unroll;
+  if (g.kind != 0) {
+    BEM_TRY(put(&p.stages, st));
+    BEM_TRY(put(&p.cta_stage, cst));
+    BEM_TRY(put(&p.descs, dsc));
+    p.flat = g.kind == 1;
+    p.tma = g.kind == 2;
+    p.nstage = g.cps == 1 ? 4 : 3;
+    p.stage_bytes = stage_bytes;
+    p.err = derr;
+  }
+  *out = p;
+  return BEM_OK;
+}
+
 static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::vector<int64_t>& off,
                          const std::vector<int32_t>& ld, const float2* A, GemvPlan* out32,
-                         GemvPlan* out64) {
+                         GemvPlan* out64, float* tune_ms, GemvPlan* alt) {
+  tune_ms[0] = tune_ms[1] = 1e30f;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t tot = 0;
   for (int v : n) tot += v;
-  float2 *x = nullptr, *y = nullptr;
+  std::vector<GemvCand> cands;
+  for (int cu : {0, 1, 2}) {
+    const int cps = cu == 0 ? 6 : 4, u = cu == 2 ? 8 : 4;
+    for (int split : {1, 2, 4}) cands.push_back({0, cps, split, u});
+  }
+  cands.push_back({1, 6, 1, 4});
+  cands.push_back({1, 4, 1, 8});
+  cands.push_back({2, 1, 1, 4});
+  cands.push_back({2, 2, 1, 2});
   int* derr = nullptr;
-  BEM_CUDA(cudaMalloc(&x, tot * sizeof(float2)));
-  BEM_CUDA(cudaMalloc(&y, tot * sizeof(float2)));
-  BEM_CUDA(cudaMemset(x, 0, tot * sizeof(float2)));
   BEM_TRY(dalloc_t(c, &derr, 1));
   BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
+  TunePlan io;  // x, y of the trial launches
+  std::vector<float2> xh(tot), yh(tot), yref;
+  for (int64_t i = 0; i < tot; ++i) xh[i] = make_float2((float)std::sin(0.37 * i), (float)std::cos(0.11 * i));
+  float2 *x = nullptr, *y = nullptr;
+  BEM_TRY(io.put(&x, xh));
+  BEM_TRY(io.put(&y, yh));
+  // the product of candidate 0 is the reference of the others (same sums in another order)
+  auto agrees = [&]() -> bool {
+    if (cudaMemcpy(yh.data(), y, tot * sizeof(float2), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    if (yref.empty()) {
+      yref = yh;
+      return true;
+    }
+    double num = 0, den = 0;
+    for (int64_t i = 0; i < tot; ++i) {
+      num = std::max(num, (double)std::hypot(yh[i].x - yref[i].x, yh[i].y - yref[i].y));
+      den = std::max(den, (double)std::hypot(yref[i].x, yref[i].y));
+    }
+    return num <= 1e-4 * den;
+  };
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -465,84 +544,53 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
     cudaEventElapsedTime(&ms, e0, e1);
     return ms;
   };
-  float best = 1e30f, best_plain = 1e30f;
-  int best_kind = 0, best_cps = kGemvCtasPerSm, best_split = 2;  // kind 0 plain, 1 staged
-  int plain_cps = kGemvCtasPerSm, plain_split = 2;
+  int best = -1, best_reg = -1, best_staged = -1;
+  float tbest = 1e30f;
   int rc = BEM_OK;
-  for (int cps : {4, 6}) {
-    std::vector<RowInfo> rows;
-    std::vector<int2> segs;
-    std::vector<int32_t> cseg;
-    double ratio = 0;
-    build_gemv_plan(n, off, ld, nsm * cps, &rows, &segs, &cseg, &ratio);
+  for (int i = 0; i < (int)cands.size(); ++i) {
     TunePlan t;
-    if ((rc = t.put(&t.p.rows, rows)) || (rc = t.put(&t.p.segs, segs)) || (rc = t.put(&t.p.cta_seg, cseg))) break;
-    t.p.ncta = nsm * cps;
-    t.p.nrows = (int)rows.size();
-    for (int split : {1, 2, 4}) {
-      t.p.split = split;
-      const float ms = timeit(t.p);
-      if (ms < best_plain) { best_plain = ms; plain_cps = cps; plain_split = split; }
-      if (ms < best) { best = ms; best_kind = 0; best_cps = cps; best_split = split; }
+    GemvPlan p;
+    const int r = make_gemv_plan(c, &t, cands[i], nsm, n, off, ld, derr, &p);
+    float* row = nullptr;
+    if (alt) {  // the context's own products: record the table
+      c->tune_table.insert(c->tune_table.end(), {(float)cands[i].kind, (float)cands[i].cps,
+                                                 (float)cands[i].split, (float)cands[i].unroll, -1.f});
+      row = &c->tune_table.back();
     }
-  }
-  const int stage_bytes = 32 * 1024;
-  for (int cps : {1, 2}) {
-    if (rc != BEM_OK) break;
-    std::vector<RowInfo> rows;
-    std::vector<int2> segs;
-    std::vector<int32_t> cseg, cst, soff;
-    std::vector<TmaStage> st;
-    double ratio = 0;
-    build_gemv_plan(n, off, ld, nsm * cps, &rows, &segs, &cseg, &ratio);
-    if (!build_tma_stages(rows, segs, cseg, stage_bytes / (int)sizeof(float2), &st, &cst, &soff)) break;
-    TunePlan t;
-    if ((rc = t.put(&t.p.rows, rows)) || (rc = t.put(&t.p.stages, st)) ||
-        (rc = t.put(&t.p.cta_stage, cst)) || (rc = t.put(&t.p.soff, soff)))
-      break;
-    t.p.ncta = nsm * cps;
-    t.p.nrows = (int)rows.size();
-    t.p.tma = 1;
-    t.p.nstage = cps == 1 ? 4 : 3;
-    t.p.stage_bytes = stage_bytes;
-    t.p.err = derr;
-    const float ms = timeit(t.p);
+    if (r == 1) continue;  // rows do not fit a stage
+    if (r != BEM_OK) { rc = r; break; }
+    const float ms = timeit(p);
     int herr = 0;
     cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
-    if (herr == 0 && ms < best) { best = ms; best_kind = 1; best_cps = cps; }
     cudaMemset(derr, 0, sizeof(int));
+    if (cudaGetLastError() != cudaSuccess || herr != 0 || !agrees()) {
+      ++c->tune_rejected;
+      continue;
+    }
+    if (row) *row = ms * 1e6f / 5.f;
+    if (ms < tbest) { tbest = ms; best = i; }
+    if (cands[i].kind == 2) {
+      if (ms < tune_ms[1]) { tune_ms[1] = ms; best_staged = i; }
+    } else if (ms < tune_ms[0]) {
+      tune_ms[0] = ms;
+      best_reg = i;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(x);
-  cudaFree(y);
   if (rc != BEM_OK) return rc;
   BEM_CUDA(cudaGetLastError());
-  {  // FP64 plan: the best plain candidate
-    std::vector<RowInfo> rows;
-    std::vector<int2> segs;
-    std::vector<int32_t> cseg;
-    build_gemv_plan(n, off, ld, nsm * plain_cps, &rows, &segs, &cseg, &out64->cmax_over_ideal);
-    BEM_TRY(upload_plan(c, rows, segs, cseg, out64));
-    out64->split = plain_split;
+  if (best_reg < 0) {
+    set_error("GEMV autotuner: no register-path candidate gave the reference product");
+    return BEM_ECUDA;
   }
-  std::vector<RowInfo> rows;
-  std::vector<int2> segs;
-  std::vector<int32_t> cseg;
-  build_gemv_plan(n, off, ld, nsm * best_cps, &rows, &segs, &cseg, &out32->cmax_over_ideal);
-  BEM_TRY(upload_plan(c, rows, segs, cseg, out32));
-  out32->split = best_split;
-  if (best_kind == 1) {
-    std::vector<int32_t> cst, soff;
-    std::vector<TmaStage> st;
-    build_tma_stages(rows, segs, cseg, stage_bytes / (int)sizeof(float2), &st, &cst, &soff);
-    BEM_TRY(upload(c, &out32->stages, st.data(), st.size()));
-    BEM_TRY(upload(c, &out32->cta_stage, cst.data(), cst.size()));
-    BEM_TRY(upload(c, &out32->soff, soff.data(), soff.size()));
-    out32->tma = 1;
-    out32->nstage = best_cps == 1 ? 4 : 3;
-    out32->stage_bytes = stage_bytes;
-    out32->err = derr;
+  BEM_TRY(make_gemv_plan(c, nullptr, cands[best_reg], nsm, n, off, ld, derr, out64));
+  GemvPlan staged;  // ncta = 0: no staged candidate ran correctly
+  if (best_staged >= 0) BEM_TRY(make_gemv_plan(c, nullptr, cands[best_staged], nsm, n, off, ld, derr, &staged));
+  *out32 = best == best_staged ? staged : *out64;
+  if (alt) {
+    alt[0] = *out64;
+    alt[1] = staged;
   }
   return BEM_OK;
 }
@@ -782,7 +830,7 @@ int setup_device(aim_ctx* c) {
     BEM_TRY(upload(c, &c->d_nodeT, nodeT.data(), nodeT.size()));
     // P^T in grid-node-major CSR form (counting sort by node; sources ascending per node)
     auto build = [&](const std::vector<int32_t>& node, int32_t** d_row, int32_t** d_col,
-                     int32_t** d_k) -> int {
+                     int32_t** d_k, int32_t** d_work, int32_t* nwork) -> int {
       const int ns = (int)node.size();
       const int nx = c->gn[0], ny = c->gn[1];
       std::vector<int32_t> row(c->ng + 1, 0), col(27 * (size_t)ns), kk(27 * (size_t)ns);
@@ -799,14 +847,23 @@ int setup_device(aim_ctx* c) {
           col[p] = m;
           kk[p] = k;
         }
+      // node work list: nodes with entries (ascending), then the empty ones
+      std::vector<int32_t> work;
+      work.reserve(c->ng);
+      for (int64_t i = 0; i < c->ng; ++i)
+        if (row[i + 1] > row[i]) work.push_back((int32_t)i);
+      *nwork = (int32_t)work.size();
+      for (int64_t i = 0; i < c->ng; ++i)
+        if (row[i + 1] == row[i]) work.push_back((int32_t)i);
       BEM_TRY(upload(c, d_row, row.data(), row.size()));
       BEM_TRY(upload(c, d_col, col.data(), col.size()));
       BEM_TRY(upload(c, d_k, kk.data(), kk.size()));
+      BEM_TRY(upload(c, d_work, work.data(), work.size()));
       return BEM_OK;
     };
     int32_t *d_kE = nullptr, *d_kT = nullptr;
-    BEM_TRY(build(nodeE, &c->d_prowE, &c->d_pcolE, &d_kE));
-    BEM_TRY(build(nodeT, &c->d_prowT, &c->d_pcolT, &d_kT));
+    BEM_TRY(build(nodeE, &c->d_prowE, &c->d_pcolE, &d_kE, &c->d_pnodeE, &c->nwE));
+    BEM_TRY(build(nodeT, &c->d_prowT, &c->d_pcolT, &d_kT, &c->d_pnodeT, &c->nwT));
     const int64_t nE = 27 * (int64_t)c->ne, nT = 27 * (int64_t)c->nt;
     BEM_TRY(dalloc_t(c, &c->f64.WAT, 3 * nE));
     BEM_TRY(dalloc_t(c, &c->f32.WAT, 3 * nE));
@@ -853,7 +910,9 @@ int setup_device(aim_ctx* c) {
     BEM_TRY(upload(c, &c->d_tasks, c->tasks.data(), c->tasks.size()));
     // persistent, byte-balanced plan with the autotuned launch shape
     BEM_TRY(tma_init_attrs());
-    BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan, &c->gplan64));
+    BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan, &c->gplan64, c->tune_ms,
+                          c->gplan_alt));
+    c->gplan_auto = c->gplan;
   }
   // workspaces
   const size_t P = (size_t)c->gp[0] * c->gp[1] * c->gp[2];
@@ -1085,7 +1144,10 @@ int setup_precond(aim_ctx* c) {
   if (dwork) cudaFree(dwork);
   if (rc != BEM_OK) return rc;
   // persistent GEMV plan over the object-major blocks (autotuned launch shape)
-  BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan, &c->pcplan64));
+  {
+    float pc_ms[2];
+    BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan, &c->pcplan64, pc_ms, nullptr));
+  }
   c->pc_ready = true;
   return BEM_OK;
 }

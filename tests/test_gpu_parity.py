@@ -157,6 +157,39 @@ def test_internal_apply_nrhs(prob):
         assert rel(heq[r], blockops.block_gemv(S.Ys, [a for a, _ in S.ranges], e[r])) < 1e-6
 
 
+def test_gemv_autotuner_candidates(prob):
+    """Every GEMV candidate the set-up autotuner timed agreed with the first one, and both the
+    plain and the bulk-copy-staged kernels produced a plan."""
+    ctx = prob["ctx"]
+    assert ctx.gemv_tune_rejected == 0
+    assert ctx.gemv_tune_ns["plain"] > 0 and ctx.gemv_tune_ns["staged"] > 0
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_gemv_kinds_match_oracle(prob, kind):
+    """The plain and the staged FP32 GEMV, forced in turn, against the FP64 oracle: internal
+    products with 3 right-hand sides (the staged kernel's multi-RHS and h - Y e forms) and the
+    system matvec."""
+    ctx, S = prob["ctx"], prob["S"]
+    ctx.gemv_select(kind)
+    try:
+        h = np.stack([synth.rand_cvec(ctx.ne, 60 + r) for r in range(3)])
+        e, heq = ctx.internal(torch.from_numpy(h.ravel().astype(np.complex64)).cuda(), nrhs=3,
+                              prec=api.BEM_C32)
+        e = e.cpu().numpy().reshape(3, -1)
+        heq = heq.cpu().numpy().reshape(3, -1)
+        for r in range(3):
+            eo = blockops.block_gemv(S.Zs, [a for a, _ in S.ranges], h[r])
+            assert rel(e[r], eo) < 1e-5
+            ho = blockops.block_gemv(S.Ys, [a for a, _ in S.ranges], e[r].astype(np.complex128))
+            assert rel(heq[r], ho) < 1e-5
+        x = synth.rand_cvec(ctx.n, 7)
+        y = ctx.matvec(torch.from_numpy(x.astype(np.complex64)).cuda(), prec=api.BEM_C32)
+        assert rel(y.cpu().numpy(), S.matvec(x)) < 1e-5
+    finally:
+        ctx.gemv_select(0)
+
+
 def test_plane_wave_rhs(prob):
     ctx, rw, k0 = prob["ctx"], prob["rw"], prob["k0"]
     b = ctx.rhs_plane_wave(prec=api.BEM_C64).cpu().numpy()
