@@ -151,6 +151,18 @@ def run_reference(args, rank, world):
                                     "d2h_bytes_per_step": 0}}))
 
 
+# DRAM bytes (read + write) per launch of the block GEMV from the ncu capture summarised in
+# profiles/gemv_internal_bar_array.md; valid only for the launch shape captured there
+PROFILED_GEMV = {"kind": 0, "ctas": 912, "split": 1, "unroll": 4, "bytes": 205.4e6}
+
+
+def gemv_traffic(ctx):
+    p = PROFILED_GEMV
+    same = (ctx.gemv_kind == p["kind"] and ctx.gemv_ctas == p["ctas"]
+            and ctx.gemv_split == p["split"] and ctx.gemv_unroll == p["unroll"])
+    return int(p["bytes"]) if same else None
+
+
 def ncu_case(args):
     """Small cases for profiler captures.
     gemv: the block-diagonal GEMV alone on random blocks with the workload's block sizes (one of
@@ -206,6 +218,73 @@ def ncu_case(args):
                       "bytes": int(A.numel() * 8)}))
 
 
+def precision_study(args):
+    """FP32-bulk against FP64 on the 4x4 bar array over 1-100 GHz: for each frequency the
+    relative error of the complex-FP32 system matvec, and of every solve output of the chosen
+    FP32-bulk FGMRES (block-diagonal preconditioner, 1e-6) against an FP64 FGMRES solve to 1e-10
+    of the same system: h, j = h - Y Z h, q, the radiation vector in three directions, and the
+    2x2 admittance of two delta-gap ports on bar 0 (1 um from its ends)."""
+    import numpy as np
+    import torch
+
+    from paper_2108_03991_gb300 import api, build, synth
+    build.build()
+    out = []
+    rh = np.array([[0.0, 0.0, -1.0], [1.0, 0.0, 0.0], [0.0, 0.6, 0.8]])
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    for f_ghz in (1, 10, 30, 60, 100):
+        mesh, grid, freq = synth.bar_array_config(0, f_ghz * 1e9)
+        t0 = time.perf_counter()
+        ctx = api.Context(mesh, grid, freq)
+        zs = mesh.verts[np.unique(mesh.tris[mesh.obj == 0])][:, 2]
+        rings = [ctx.port_ring(0, 2, z) for z in (zs.min() + 1.0, zs.max() - 1.0)]
+        xr = synth.rand_cvec(ctx.n, 9)
+        y32 = ctx.matvec(torch.from_numpy(xr.astype(np.complex64)).cuda(), prec=api.BEM_C32)
+        y64 = ctx.matvec(torch.from_numpy(xr).cuda(), prec=api.BEM_C64)
+        row = {"GHz": f_ghz, "matvec_fp32": rel(y32.cpu().numpy(), y64.cpu().numpy())}
+        rhs = [("plane_wave", ctx.rhs_plane_wave(prec=api.BEM_C64))]
+        rhs += [(f"port{q}", ctx.rhs_port(e, sgn, v_gap=1.0)) for q, (e, sgn) in enumerate(rings)]
+        sol = {}
+        for mode, tol in ((api.BEM_C64, 1e-10), (api.BEM_C32, 1e-6)):
+            for name, b in rhs:
+                x, info = ctx.solve(b, tol=tol, restart=200, max_iter=2000, prec_mode=mode,
+                                    time_limit_s=60.0, precond=1)
+                sol[(mode, name)] = (x, info)
+        x64, i64 = sol[(api.BEM_C64, "plane_wave")]
+        x32, i32 = sol[(api.BEM_C32, "plane_wave")]
+
+        def parts(x):
+            h = x[:ctx.ne].contiguous()
+            _, heq = ctx.internal(h, prec=api.BEM_C64)
+            return (h.cpu().numpy(), (h - heq).cpu().numpy(), x[ctx.ne:].cpu().numpy(),
+                    ctx.farfield(x, rh, prec=api.BEM_C64))
+        h64, j64, q64, n64 = parts(x64)
+        h32, j32, q32, n32 = parts(x32)
+        Y = {}
+        for mode in (api.BEM_C64, api.BEM_C32):
+            M = np.zeros((2, 2), complex)
+            for qi in range(2):
+                xq = sol[(mode, f"port{qi}")][0]
+                for p, (e, sgn) in enumerate(rings):
+                    M[p, qi] = ctx.port_current(xq, e, sgn, prec=api.BEM_C64)
+            Y[mode] = M
+        row.update({"h": rel(h32, h64), "j": rel(j32, j64), "q": rel(q32, q64),
+                    "far_field": rel(n32, n64),
+                    "port_Y": float(np.max(np.abs(Y[api.BEM_C32] - Y[api.BEM_C64]))
+                                    / np.max(np.abs(Y[api.BEM_C64]))),
+                    "Y11_S": [Y[api.BEM_C64][0, 0].real, Y[api.BEM_C64][0, 0].imag],
+                    "iters_fp64_1e-10": i64["iters"], "iters_fp32_1e-6": i32["iters"],
+                    "resid_true_fp32": i32["resid_true"],
+                    "seconds_with_setup": time.perf_counter() - t0})
+        out.append(row)
+        ctx.close()
+        print(json.dumps(row), file=sys.stderr)
+    print(json.dumps({"precision_study": out, "workload": WORKLOAD.replace("10 GHz", "1-100 GHz")}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,11 +295,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal"])
     ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--precision-study", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.ncu_case:
         return ncu_case(args)
+    if args.precision_study:
+        return precision_study(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -347,8 +429,9 @@ def main():
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
         value = world * 1e3 / ms
-        # per system matvec: 2 GEMV, 2 projections, 2 x 3 FFT passes, 2 row kernels
-        launches_per_step = 12
+        # per system matvec: 2 GEMV (each with a y-initialising launch in the stream form),
+        # 2 projections, 2 x 3 FFT passes, 2 row kernels
+        launches_per_step = 10 + 2 * (2 if ctx.gemv_kind == 3 else 1)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -360,7 +443,8 @@ def main():
                        "setup_s": setup_s},
             "roofline": {"kernel": "k_gemv (block-diagonal Z / Y_eq)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_source": src, "traffic": None,
+                         "frac": achieved / hbm, "peak_source": src, "traffic": gemv_traffic(ctx),
+                         "traffic_unit": "DRAM bytes per launch (ncu, profiles/gemv_internal_bar_array.md)",
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
                          "launch": {"ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split,
                                     "loads_in_flight": ctx.gemv_unroll,

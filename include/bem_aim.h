@@ -92,13 +92,15 @@ const char* bem_last_error(void);
 
 /* Sizes: info[0]=N_E, [1]=N_T, [2]=nobj, [3..5]=grid n, [6..8]=padded FFT lengths,
  * [9]=nnz(L^A_NR), [10]=nnz(L^Phi_NR), [11]=bytes of Z and Y (C32), [12]=max n_i,
- * [13]=CTAs of the block GEMV launch, [14]=column parts per row, or minus the number of
- * shared-memory stages when the bulk-copy-staged kernel was chosen, [15]=16-byte loads in flight
+ * [13]=CTAs of the block GEMV launch, [14]=column parts per row of the row-plan kernel, 0 for
+ * the flat and stream kernels, or minus the number of shared-memory stages when the bulk-copy-staged kernel
+ * was chosen, [15]=16-byte loads in flight
  * per lane (0 for the staged kernel) (all chosen by the set-up autotuner), [16]=ns per launch of
  * the best plain candidate, [17]=ns per launch of the best staged candidate (-1 if none ran
  * correctly), [18]=autotuner candidates rejected (product differed from the first candidate's
  * beyond FP32 rounding, or a bounded wait timed out; set-up products include the preconditioner
- * blocks once they are built). Writes min(n, 19) entries. */
+ * blocks once they are built), [19]=kind of the chosen FP32 launch (0 row plan, 1 flat, 2
+ * bulk-copy staged, 3 stream). Writes min(n, 20) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the
@@ -156,7 +158,7 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *   what 6: stencil anchors, int32 [N_E + N_T][3]
  *   what 7: edge table, int32 [N_E][6] = (a, b, T+, T-, v+, v-)
  *   what 8: the set-up GEMV autotuner's table, float [candidates][5] = (kind: 0 row plan,
- *           1 flat, 2 bulk-copy staged; CTAs per SM; column parts per row; loads in flight
+ *           1 flat, 2 bulk-copy staged, 3 stream; CTAs per SM; column parts per row; loads in flight
  *           per lane; ns per launch, or -1 when the candidate was rejected or not applicable)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
@@ -165,6 +167,41 @@ int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t c
  * Sec. II-A right-hand side. pol and khat are host arrays of 3 doubles. */
 int bem_rhs_plane_wave(aim_ctx* ctx, const double* pol, const double* khat, void* b, int prec,
                        void* stream);
+
+/* Lumped ports. The paper excites structures through lumped ports (Sec. II, after Wang 2004)
+ * without giving the model; reading: a delta gap on a closed ring of mesh edges around a
+ * conductor's cross-section. bem_port_ring lists the edges of object obj whose two vertices lie
+ * within tol of the plane x_axis = coord (micrometres), with s_m = +1 when the RWG function
+ * f_m crosses the plane towards +axis, -1 otherwise. edges and signs are HOST arrays receiving
+ * the first min(count, cap) entries (NULL: count only). Returns the count or BEM_EINVAL. */
+int bem_port_ring(aim_ctx* ctx, int obj, int axis, double coord, double tol, int32_t* edges,
+                  double* signs, int cap);
+
+/* b = [s_m l_m V / eta0 on the ring edges, 0 on the other edges; 0 on the triangles]: the
+ * delta-gap excitation <f_m, E_inc> / eta0 of a gap voltage V (volts), in the scaling of
+ * bem_rhs_plane_wave, so that the solution's h is H in A/m. edges, signs: HOST arrays of n
+ * entries (from bem_port_ring). b: device vector of N_E + N_T in prec. Synchronises the stream.
+ * Errors: BEM_EINVAL for an empty port or an edge out of range. */
+int bem_rhs_port(aim_ctx* ctx, int n, const int32_t* edges, const double* signs, double v_gap,
+                 void* b, int prec, void* stream);
+
+/* Port current I = sum_m s_m l_m h_m of the solution x = [h; q] (device, prec): the
+ * circulation of H around the ring (Ampere's law), in amperes (h in A/m, lengths converted to
+ * metres). The port admittance is Y_pq = I_p / V_q. current: HOST, 2 doubles (re, im).
+ * Synchronises the stream. */
+int bem_port_current(aim_ctx* ctx, int n, const int32_t* edges, const double* signs,
+                     const void* x, int prec, double* current, void* stream);
+
+/* Radiation vector N(rhat) = int J_Delta(r') exp(j k0 rhat . r') dS' of the solution x = [h; q]
+ * (device, prec), with J_Delta = sum_n j_n f_n and j = h - Y_eq Z h: in the equivalent problem
+ * only J_Delta radiates into the background (Sec. II). The far field is
+ * E(r) = -j k0 eta0 exp(-j k0 r) / (4 pi r) (I - rhat rhat) N, so the monostatic RCS of a unit
+ * plane wave is sigma = k0^2 eta0^2 |(I - rhat rhat) N|^2 / (4 pi) (um^2, k0 in 1/um).
+ * The integral uses the 7-point rule per triangle, accumulated in FP64. rhat: HOST [ndir][3]
+ * unit vectors; nvec: HOST [ndir][3] complex doubles (re, im interleaved), in (A/m) um^2. Uses
+ * the context's internal work vectors (as aim_matvec does); synchronises the stream. */
+int bem_farfield(aim_ctx* ctx, const void* x, int prec, int ndir, const double* rhat,
+                 double* nvec, void* stream);
 
 /* Options of bem_solve. prec_mode: BEM_C64 (plain: FP64 everywhere) or BEM_C32 (system
  * matvec in complex FP32, Arnoldi and Givens in FP64). */

@@ -73,6 +73,11 @@ def lib():
         L.aim_info.argtypes = [vp, C.POINTER(i64), C.c_int]
         L.aim_matvec.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
         L.aim_gemv_select.argtypes = [vp, C.c_int]
+        L.bem_port_ring.argtypes = [vp, C.c_int, C.c_int, d, d, C.POINTER(i32), C.POINTER(d), C.c_int]
+        L.bem_rhs_port.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), d, vp, C.c_int, vp]
+        L.bem_port_current.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), vp, C.c_int,
+                                       C.POINTER(d), vp]
+        L.bem_farfield.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(d), C.POINTER(d), vp]
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int, C.c_int, vp]
@@ -199,8 +204,8 @@ class Context:
         h = C.c_void_p()
         _check(L.aim_setup(C.byref(m), C.byref(g), float(freq), C.byref(h)))
         self.h = h
-        info = (C.c_int64 * 19)()
-        _check(L.aim_info(h, info, 19))
+        info = (C.c_int64 * 20)()
+        _check(L.aim_info(h, info, 20))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -213,6 +218,50 @@ class Context:
         self.gemv_unroll = info[15]
         self.gemv_tune_ns = {"plain": info[16], "staged": info[17]}
         self.gemv_tune_rejected = info[18]
+        self.gemv_kind = info[19]  # 0 row plan, 1 flat, 2 bulk-copy staged, 3 stream
+
+    # ---- ports and far field ---------------------------------------------------------
+    def port_ring(self, obj, axis, coord, tol=1e-6):
+        """Edges (library order) and crossing signs of a delta-gap ring of object `obj` in the
+        plane x_axis = coord (um)."""
+        L = lib()
+        n = _check(L.bem_port_ring(self.h, int(obj), int(axis), float(coord), float(tol), None,
+                                   None, 0))
+        e = np.zeros(n, dtype=np.int32)
+        s = np.zeros(n, dtype=np.float64)
+        _check(L.bem_port_ring(self.h, int(obj), int(axis), float(coord), float(tol),
+                               e.ctypes.data_as(C.POINTER(C.c_int32)),
+                               s.ctypes.data_as(C.POINTER(C.c_double)), n))
+        return e, s
+
+    def rhs_port(self, edges, signs, v_gap=1.0, prec=BEM_C64, device="cuda"):
+        import torch
+        e = np.ascontiguousarray(edges, dtype=np.int32)
+        s = np.ascontiguousarray(signs, dtype=np.float64)
+        b = torch.empty(self.n, dtype=cdtype(prec), device=device)
+        _check(lib().bem_rhs_port(self.h, len(e), e.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  s.ctypes.data_as(C.POINTER(C.c_double)), float(v_gap),
+                                  _ptr(b), prec, _stream()))
+        return b
+
+    def port_current(self, x, edges, signs, prec=BEM_C64):
+        """Port current in amperes (complex) of the solution x = [h; q]."""
+        e = np.ascontiguousarray(edges, dtype=np.int32)
+        s = np.ascontiguousarray(signs, dtype=np.float64)
+        out = (C.c_double * 2)()
+        _check(lib().bem_port_current(self.h, len(e), e.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      s.ctypes.data_as(C.POINTER(C.c_double)), _ptr(x, cdtype(prec)),
+                                      prec, out, _stream()))
+        return complex(out[0], out[1])
+
+    def farfield(self, x, rhat, prec=BEM_C64):
+        """Radiation vector N(rhat) [ndir, 3] (complex) of the solution x = [h; q]."""
+        r = np.ascontiguousarray(np.atleast_2d(rhat), dtype=np.float64)
+        out = np.zeros((r.shape[0], 6))
+        _check(lib().bem_farfield(self.h, _ptr(x, cdtype(prec)), prec, r.shape[0],
+                                  r.ctypes.data_as(C.POINTER(C.c_double)),
+                                  out.ctypes.data_as(C.POINTER(C.c_double)), _stream()))
+        return out[:, 0::2] + 1j * out[:, 1::2]
 
     def gemv_select(self, kind):
         """FP32 block-GEMV launch: 0 autotuned choice, 1 best plain, 2 best bulk-copy staged."""

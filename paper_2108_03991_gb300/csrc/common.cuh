@@ -165,6 +165,9 @@ struct GemvPlan {
   int split = 2;               // column parts per row (1, 2 or 4), picked by the autotuner
   int unroll = 4;              // 16-byte loads in flight per lane (4 or 8), likewise
   int flat = 0;                // flat form: rows in chunks (stages, descs, cta_stage as chunks)
+  int stream = 0;              // stream form: equal vector shares per warp, atomic row sums
+  int32_t* wrow = nullptr;     // device [warps]: row holding each warp's first vector
+  int64_t nquad = 0;           // whole block storage in units of 4 complex elements
   double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
   // bulk-copy staging
   int tma = 0;
@@ -187,6 +190,14 @@ int run_gemv_tma(const GemvPlan& p, const typename C2<R>::T* A, const typename C
 void build_gemv_plan(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
                      const std::vector<int32_t>& ld, int ncta, std::vector<RowInfo>* rows,
                      std::vector<int2>* segs, std::vector<int32_t>* cta_seg, double* ratio);
+// physical constants (SI) and the length unit of the library (micrometre)
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
+constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+constexpr double kEta0 = kMu0 * kC0;
+constexpr double kEll = 1e-6;
+// Radon's 7-point degree-5 rule on the triangle: (l1, l2, l3, w) x 7, weights summing to one
+void radon7_host(double* out);
 constexpr int kGemvThreads = 256;
 constexpr int kGemvCtasPerSm = 6;
 
@@ -281,6 +292,8 @@ struct aim_ctx {
   // GMRES workspace kept between solves (gmres.cu)
   void* gm_ws = nullptr;
   size_t gm_bytes = 0;
+  // far-field geometry (post.cu), built on first use
+  void* far_geo = nullptr;
   // learned correction network on the AIM grid (learned.cu)
   void* net = nullptr;
 };
@@ -342,6 +355,7 @@ int net_apply(aim_ctx* c, const float2* r, float2* z, cudaStream_t s);
 void free_net(aim_ctx* c);
 template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cudaStream_t s);
 void free_geo_store(aim_ctx* c);
+void free_far_geo(aim_ctx* c);
 double k0_of(double f);
 // solver (gmres.cu)
 int gmres_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,

@@ -15,6 +15,13 @@ namespace bem {
 // ---------------------------------------------------------------------------------------
 // block-diagonal GEMV: one warp per row, 16-byte vector loads, x read through the L1 cache
 // ---------------------------------------------------------------------------------------
+// complex atomic add: one 8-byte vector atomic in FP32, two scalar atomics in FP64
+__device__ __forceinline__ void catomic_add(float2* o, float2 v) { atomicAdd(o, v); }
+__device__ __forceinline__ void catomic_add(double2* o, double2 v) {
+  atomicAdd(&o->x, v.x);
+  atomicAdd(&o->y, v.y);
+}
+
 template <typename R> struct Vec16;
 template <> struct Vec16<float> { typedef float4 T; static constexpr int kCplx = 2; };
 template <> struct Vec16<double> { typedef double2 T; static constexpr int kCplx = 1; };
@@ -28,28 +35,41 @@ __device__ __forceinline__ void dot_range(const typename Vec16<R>::T* __restrict
                                           typename C2<R>::T* acc) {
   typedef typename Vec16<R>::T L16;
   constexpr int CP = Vec16<R>::kCplx;
+  // x_r read as one 16-byte load per vector when its slice is 16-byte aligned (col is even)
+  bool x16[NRHS];
+#pragma unroll
+  for (int r = 0; r < NRHS; ++r)
+    x16[r] = CP == 2 && ((reinterpret_cast<uintptr_t>(xb + r * vstride) & 15) == 0);
   auto use = [&](const L16& a, int col) {
     if constexpr (CP == 2) {
       const auto a0 = mk(a.x, a.y), a1 = mk(a.z, a.w);
 #pragma unroll
       for (int r = 0; r < NRHS; ++r) {
-        cfma(acc[r], a0, __ldg(xb + r * vstride + col));
-        if (col + 1 < n) cfma(acc[r], a1, __ldg(xb + r * vstride + col + 1));
+        if (x16[r] && col + 1 < n) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(xb + r * vstride + col));
+          cfma(acc[r], a0, mk(q.x, q.y));
+          cfma(acc[r], a1, mk(q.z, q.w));
+        } else {
+          cfma(acc[r], a0, __ldg(xb + r * vstride + col));
+          if (col + 1 < n) cfma(acc[r], a1, __ldg(xb + r * vstride + col + 1));
+        }
       }
     } else {
 #pragma unroll
       for (int r = 0; r < NRHS; ++r) cfma(acc[r], mk(a.x, a.y), __ldg(xb + r * vstride + col));
     }
   };
-  int v = v0 + lane;
-  for (; v + (U - 1) * 32 < v1; v += U * 32) {
+  // every batch, the last one included, has its U loads issued before any is used (a plain
+  // remainder loop would wait for one load at a time at the end of every row)
+  for (int v = v0 + lane; v < v1; v += U * 32) {
     L16 a[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) a[u] = __ldcs(arow + v + 32 * u);
+    for (int u = 0; u < U; ++u)
+      if (v + 32 * u < v1) a[u] = __ldcs(arow + v + 32 * u);
 #pragma unroll
-    for (int u = 0; u < U; ++u) use(a[u], (v + 32 * u) * CP);
+    for (int u = 0; u < U; ++u)
+      if (v + 32 * u < v1) use(a[u], (v + 32 * u) * CP);
   }
-  for (; v < v1; v += 32) use(__ldcs(arow + v), v * CP);
 }
 
 // One row of the product, one warp: acc[r] = sum_k A[row, k] x_r[k]. Rows are streamed with
@@ -248,12 +268,92 @@ static void launch_gemv_flat(const GemvPlan& p, const typename C2<R>::T* A,
   }
 }
 
+// Stream form: the blocks' storage (rows back to back, no gaps) is one run of 16-byte vectors,
+// cut into equal shares, one per warp of the grid (to 32 bytes), so every warp streams the
+// same bytes and starts at once. A warp walks the rows its share touches (the next row's
+// descriptor is fetched while the current row streams) and adds each row's warp sum atomically
+// into y, which k_gemv_init first set to 0, or to hsub with the sums subtracted.
+template <typename R, int NRHS, int U>
+__global__ void __launch_bounds__(kGemvThreads, U >= 8 ? 4 : kGemvCtasPerSm)
+    k_gemv_stream(const int32_t* __restrict__ wrow, const RowInfo* __restrict__ rows,
+                  int64_t nquad, const typename C2<R>::T* __restrict__ A,
+                  const typename C2<R>::T* __restrict__ x, typename C2<R>::T* __restrict__ y,
+                  int64_t vstride, R sign) {
+  typedef typename C2<R>::T V;
+  typedef typename Vec16<R>::T L16;
+  constexpr int CP = Vec16<R>::kCplx;
+  constexpr int nw = kGemvThreads / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t W = (int64_t)gridDim.x * nw;
+  const int64_t w = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5);
+  // shares in units of 4 complex elements (one row of ld is a whole number of them), so the
+  // per-warp first rows are the same for FP32 and FP64
+  const int64_t v0 = 4 * (nquad * w / W) / CP;
+  const int len = (int)(4 * (nquad * (w + 1) / W) / CP - v0);
+  if (len <= 0) return;
+  const L16* a16 = reinterpret_cast<const L16*>(A) + v0;  // the warp's share
+  int k = wrow[w];
+  RowInfo ri = rows[k];
+  for (int pos = 0; pos < len; ++k) {
+    const int rs = (int)(ri.aoff / CP - v0);  // row start relative to the share (may be < 0)
+    const int ve = min(len, rs + ((ri.n + 3) & ~3) / CP);
+    RowInfo nxt = ri;
+    if (ve < len) nxt = rows[k + 1];
+    V acc[NRHS];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) acc[r] = czero<V>();
+    dot_range<R, NRHS, U>(a16 + rs, x + ri.xoff, ri.n, pos - rs, ve - rs, vstride, lane, acc);
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) {
+      const V t = warp_sum(acc[r]);
+      if (lane == 0) catomic_add(y + r * vstride + k, mk(sign * t.x, sign * t.y));
+    }
+    ri = nxt;
+    pos = ve;
+  }
+}
+
+// y_r = 0, or y_r = hsub_r, for the rows [0, nrows) of nrhs vectors
+template <typename V>
+__global__ void k_gemv_init(V* __restrict__ y, const V* __restrict__ hsub, int64_t nrows, int nrhs,
+                            int64_t vstride) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nrows * nrhs) return;
+  const int64_t r = i / nrows, m = i - r * nrows;
+  y[r * vstride + m] = hsub ? hsub[r * vstride + m] : czero<V>();
+}
+
+template <typename R, int U>
+static void launch_gemv_stream(const GemvPlan& p, const typename C2<R>::T* A,
+                               const typename C2<R>::T* x, typename C2<R>::T* y, int nr,
+                               int64_t vstride, R sign, cudaStream_t s) {
+  switch (nr) {
+    case 1: k_gemv_stream<R, 1, U><<<p.ncta, kGemvThreads, 0, s>>>(p.wrow, p.rows, p.nquad, A, x, y, vstride, sign); break;
+    case 2: k_gemv_stream<R, 2, U><<<p.ncta, kGemvThreads, 0, s>>>(p.wrow, p.rows, p.nquad, A, x, y, vstride, sign); break;
+    case 3: k_gemv_stream<R, 3, U><<<p.ncta, kGemvThreads, 0, s>>>(p.wrow, p.rows, p.nquad, A, x, y, vstride, sign); break;
+    default: k_gemv_stream<R, 4, U><<<p.ncta, kGemvThreads, 0, s>>>(p.wrow, p.rows, p.nquad, A, x, y, vstride, sign); break;
+  }
+}
+
 template <typename R>
 int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
                   typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
                   cudaStream_t s) {
   if (p.ncta == 0 || p.nrows == 0) return BEM_OK;
   if (p.tma) return run_gemv_tma<R>(p, A, x, y, nrhs, vstride, hsub, s);
+  if (p.stream) {
+    k_gemv_init<<<(unsigned)((p.nrows * (int64_t)nrhs + 255) / 256), 256, 0, s>>>(y, hsub, (int64_t)p.nrows,
+                                                                               nrhs, vstride);
+    const R sign = hsub ? R(-1) : R(1);
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+      const int nr = std::min(4, nrhs - r0);
+      const int64_t o = r0 * vstride;
+      if (p.unroll >= 8) launch_gemv_stream<R, 8>(p, A, x + o, y + o, nr, vstride, sign, s);
+      else launch_gemv_stream<R, 4>(p, A, x + o, y + o, nr, vstride, sign, s);
+    }
+    BEM_CUDA(cudaGetLastError());
+    return BEM_OK;
+  }
   for (int r0 = 0; r0 < nrhs; r0 += 4) {
     const int nr = std::min(4, nrhs - r0);
     const int64_t o = r0 * vstride;

@@ -18,7 +18,7 @@ void build_ix_fd(const aim_ctx* c, std::vector<int32_t>* ixcol, std::vector<doub
 // ---------------------------------------------------------------------------------------
 // rules (host)
 // ---------------------------------------------------------------------------------------
-static void radon7_host(double* out) {  // (l1, l2, l3, w) x 7, weights sum to one
+void radon7_host(double* out) {  // (l1, l2, l3, w) x 7, weights sum to one
   const double s = std::sqrt(15.0);
   const double a1 = (6.0 - s) / 21.0, a2 = (6.0 + s) / 21.0;
   const double w1 = (155.0 - s) / 1200.0, w2 = (155.0 + s) / 1200.0;
@@ -442,7 +442,7 @@ struct TunePlan {  // a candidate plan held in temporary device memory
 // receives the time of 5 launches of those two.
 namespace {
 struct GemvCand {
-  int kind;   // 0 row plan, 1 flat, 2 staged
+  int kind;   // 0 row plan, 1 flat, 2 staged, 3 stream
   int cps;    // CTAs per SM
   int split;  // column parts per row (row plan)
   int unroll; // loads in flight per lane (row plan, flat)
@@ -461,9 +461,29 @@ static int make_gemv_plan(aim_ctx* c, TunePlan* t, const GemvCand& g, int nsm,
   GemvPlan p;
   build_gemv_plan(n, off, ld, nsm * g.cps, &rows, &segs, &cseg, &p.cmax_over_ideal);
   const int stage_bytes = g.cps == 1 ? 40 * 1024 : 24 * 1024;
-  if (g.kind != 0) {
+  if (g.kind == 1 || g.kind == 2) {
     const int64_t lim = g.kind == 2 ? stage_bytes / (int)sizeof(float2) : ((int64_t)1 << 40);
     if (!build_tma_stages(rows, segs, cseg, lim, &st, &cst, &dsc)) return 1;  // not applicable
+  }
+  std::vector<int32_t> wrow;
+  int64_t nquad = 0;
+  if (g.kind == 3) {
+    // the storage must be gapless: row m + 1 starts where row m (length ld) ends
+    int64_t end = rows.empty() ? 0 : rows[0].aoff;
+    if (end != 0) return 1;
+    for (const RowInfo& r : rows) {
+      if (r.aoff != end) return 1;
+      end += (r.n + 3) & ~3;
+    }
+    nquad = end / 4;
+    const int64_t W = (int64_t)nsm * g.cps * (kGemvThreads / 32);
+    wrow.resize(W);
+    size_t m = 0;
+    for (int64_t w = 0; w < W; ++w) {
+      const int64_t e0 = 4 * (nquad * w / W);  // first element of warp w's share
+      while (m + 1 < rows.size() && rows[m + 1].aoff <= e0) ++m;
+      wrow[w] = (int32_t)m;
+    }
   }
   auto put = [&](auto** d, const auto& h) -> int {
     if (t) return t->put(d, h);
@@ -476,7 +496,12 @@ static int make_gemv_plan(aim_ctx* c, TunePlan* t, const GemvCand& g, int nsm,
   p.nrows = (int)rows.size();
   p.split = g.split;
   p.unroll = g.unroll;
-  if (g.kind != 0) {
+  if (g.kind == 3) {
+    BEM_TRY(put(&p.wrow, wrow));
+    p.stream = 1;
+    p.nquad = nquad;
+  }
+  if (g.kind == 1 || g.kind == 2) {
     BEM_TRY(put(&p.stages, st));
     BEM_TRY(put(&p.cta_stage, cst));
     BEM_TRY(put(&p.descs, dsc));
@@ -506,6 +531,8 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
   }
   cands.push_back({1, 6, 1, 4});
   cands.push_back({1, 4, 1, 8});
+  cands.push_back({3, 6, 1, 4});
+  cands.push_back({3, 4, 1, 8});
   cands.push_back({2, 1, 1, 4});
   cands.push_back({2, 2, 1, 2});
   int* derr = nullptr;
@@ -625,10 +652,6 @@ static int geo_upload(aim_ctx* c, DevGeoStore* s) {
   return BEM_OK;
 }
 
-static const double kC0 = 299792458.0;
-static const double kMu0 = 4e-7 * 3.14159265358979323846;
-static const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
-static const double kEll = 1e-6;
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
