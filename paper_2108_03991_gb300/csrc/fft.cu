@@ -327,6 +327,122 @@ __global__ void __launch_bounds__(256) k_zfused(V* ws, const V* __restrict__ gha
   }
 }
 
+// z pass in registers, for Pz = L * M with L in {8, 16, 32} lanes and M in {2, 3, 4, 5, 8}:
+// a group of L lanes holds one z line, element z = l + L n1 in lane l, register n1. Forward:
+// the M-point DFT over n1 in registers, the twiddles W_Pz^(l k1), then for every k1 an L-point
+// DFT across the lanes by radix-2 decimation in frequency with xor shuffles, which leaves
+// X[k1 + M bitrev(l)] in lane l. The product with Ghat is taken in that order, and the inverse
+// undoes the steps in reverse (the butterflies of every shuffle stage inverted, then the
+// conjugate twiddles, then the inverse M-point DFT), so the output is back in natural order
+// with no shared memory and no barrier. A CTA of 8 warps takes 8 * 32 / L adjacent x of one y.
+template <typename V, int M>
+__device__ __forceinline__ void dft_small(V* v, bool inv) {
+  if (M == 2) bfly2(v);
+  else if (M == 3) bfly3(v, inv);
+  else if (M == 4) bfly4(v, inv);
+  else if (M == 5) bfly5(v, inv);
+  else bfly8(v, inv);
+}
+
+template <typename V> __device__ __forceinline__ V shfl_x(V v, int s) {
+  return mk(__shfl_xor_sync(0xffffffffu, v.x, s), __shfl_xor_sync(0xffffffffu, v.y, s));
+}
+
+template <typename V, int L, int M>
+__global__ void __launch_bounds__(256) k_zreg(V* ws, const V* __restrict__ ghat,
+                                              const V* __restrict__ twz, PlaneArgs a) {
+  constexpr int G = 32 / L;  // lines per warp
+  constexpr int LOG_L = L == 8 ? 3 : (L == 16 ? 4 : 5);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lg = lane & (L - 1), grp = lane / L;
+  const int x = blockIdx.x * (8 * G) + warp * G + grp, y = blockIdx.y, c = blockIdx.z;
+  const bool live = x < a.Px;
+  const int P = a.Pz;
+  const int64_t plane = (int64_t)a.Py * a.Px;
+  V* base = ws + c * a.P3 + (int64_t)y * a.Px + (live ? x : 0);
+  V v[M];
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    const int z = lg + L * n1;
+    v[n1] = (live && z < a.nz) ? base[z * plane] : czero<V>();
+  }
+  // twiddles of this lane: W_P^(lg k1) and W_(2s)^(lg mod s) = W_P^((lg mod s) P / (2s))
+  V tk[M], ts[LOG_L];
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) tk[k1] = twz[(lg * k1) % P];
+#pragma unroll
+  for (int st = 0; st < LOG_L; ++st) {
+    const int sp = L >> (st + 1);  // pair distance of stage st: L/2, L/4, ..., 1
+    ts[st] = twz[(lg & (sp - 1)) * (P / (2 * sp))];
+  }
+  // forward
+  dft_small<V, M>(v, false);
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], tk[k1]);
+#pragma unroll
+  for (int st = 0; st < LOG_L; ++st) {
+    const int sp = L >> (st + 1);
+    const bool top = (lg & sp) == 0;
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const V p = shfl_x(v[k1], sp);
+      v[k1] = top ? cadd(v[k1], p) : cmul(csub(p, v[k1]), ts[st]);
+    }
+  }
+  // times Ghat at k = k1 + M bitrev(lg)
+  const int fy = min(y, a.Py - y), fx = min(x, a.Px - x);
+  const int k2 = (int)(__brev((unsigned)lg) >> (32 - LOG_L));
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) {
+    const int k = k1 + M * k2, fz = min(k, P - k);
+    if (live) v[k1] = cmul(v[k1], ghat[((int64_t)fz * a.gy + fy) * a.gx + fx]);
+  }
+  // inverse: shuffle stages in reverse order, each butterfly inverted (unnormalised)
+#pragma unroll
+  for (int st = LOG_L - 1; st >= 0; --st) {
+    const int sp = L >> (st + 1);
+    const bool top = (lg & sp) == 0;
+    const V w = mk(ts[st].x, -ts[st].y);
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const V own = top ? v[k1] : cmul(v[k1], w);
+      const V p = shfl_x(own, sp);
+      v[k1] = top ? cadd(own, p) : csub(p, own);
+    }
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], mk(tk[k1].x, -tk[k1].y));
+  dft_small<V, M>(v, true);
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    const int z = lg + L * n1;
+    if (live && z < a.nz) base[z * plane] = v[n1];
+  }
+}
+
+// (L, M) of the register z pass for Pz, or false
+static bool zreg_shape(int P, int* L, int* M) {
+  for (int l : {32, 16, 8})
+    for (int m : {2, 3, 4, 5, 8})
+      if (l * m == P) {
+        *L = l;
+        *M = m;
+        return true;
+      }
+  return false;
+}
+
+template <typename V>
+static void launch_zreg(int L, int M, dim3 grid, cudaStream_t s, V* ws, const V* ghat,
+                        const V* tw, const PlaneArgs& a) {
+#define BEM_Z(LL, MM) \
+  if (L == LL && M == MM) { k_zreg<V, LL, MM><<<grid, 256, 0, s>>>(ws, ghat, tw, a); return; }
+  BEM_Z(32, 2) BEM_Z(32, 3) BEM_Z(32, 4) BEM_Z(32, 5) BEM_Z(32, 8)
+  BEM_Z(16, 2) BEM_Z(16, 3) BEM_Z(16, 4) BEM_Z(16, 5) BEM_Z(16, 8)
+  BEM_Z(8, 2) BEM_Z(8, 3) BEM_Z(8, 4) BEM_Z(8, 5) BEM_Z(8, 8)
+#undef BEM_Z
+}
+
 // ---------------------------------------------------------------------------------------
 // generic batched 1-D pass (large planes, and the set-up FFT of the grid kernel)
 // ---------------------------------------------------------------------------------------
@@ -473,7 +589,13 @@ int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename
     a.mag_Pz = div_magic(Pz);
     const size_t zsm = ((size_t)Pz + 2 * (size_t)a.TL * zp) * sizeof(V);
     k_plane_fwd<V><<<dim3(nz, ncomp), 512, psm, s>>>(sigma, ws, b.tw[0], b.tw[1], a);
-    k_zfused<V><<<dim3((Px + a.TL - 1) / a.TL, Py, ncomp), 256, zsm, s>>>(ws, b.Ghat, b.tw[2], a);
+    int zl = 0, zm = 0;
+    if (zreg_shape(Pz, &zl, &zm)) {
+      const int per = 8 * (32 / zl);  // x lines per CTA
+      launch_zreg<V>(zl, zm, dim3((Px + per - 1) / per, Py, ncomp), s, ws, b.Ghat, b.tw[2], a);
+    } else {
+      k_zfused<V><<<dim3((Px + a.TL - 1) / a.TL, Py, ncomp), 256, zsm, s>>>(ws, b.Ghat, b.tw[2], a);
+    }
     k_plane_inv<V><<<dim3(nz, ncomp), 512, psm, s>>>(ws, phi, b.tw[0], b.tw[1], a);
     BEM_CUDA(cudaGetLastError());
     return BEM_OK;
