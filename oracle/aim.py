@@ -199,16 +199,24 @@ class Aim:
             out[idx] = np.einsum("ia,ab,ib->i", W_m[idx], gl[kk], W_n[idx])
         return out
 
-    def build_near(self, LA_exact=None, LP_exact=None):
+    def build_near(self, LA_exact=None, LP_exact=None, rows_e=None, rows_t=None):
         """Precorrected near-region matrices. Exact entries are computed for the near pairs
-        unless dense exact matrices are supplied."""
+        unless dense exact matrices are supplied. rows_e / rows_t, if given, restrict the
+        entries to those testing functions (the other rows stay empty): rows of L^A and L^Phi
+        sampled one by one on structures too large for every near pair."""
         rw = self.rw
         M, N = self.near_e
+        if rows_e is not None:
+            keep = np.isin(M, np.asarray(rows_e))
+            M, N = M[keep], N[keep]
         la = LA_exact[M, N] if LA_exact is not None else rwg_entries(rw, self.k0, M, N, "A")
         pre = sum(self.precorrection(self.WA[M, c, :], self.WA[N, c, :], self.anc_e[M],
                                      self.anc_e[N]) for c in range(3))
         self.LNR_A = sp.csr_matrix((la - pre, (M, N)), shape=(rw.ne, rw.ne))
         T, S = self.near_t
+        if rows_t is not None:
+            keep = np.isin(T, np.asarray(rows_t))
+            T, S = T[keep], S[keep]
         lp = LP_exact[T, S] if LP_exact is not None else pulse_entries(rw, self.k0, T, S)
         pre = self.precorrection(self.WP[T], self.WP[S], self.anc_t[T], self.anc_t[S])
         self.LNR_P = sp.csr_matrix((lp - pre, (T, S)), shape=(rw.nt, rw.nt))

@@ -287,12 +287,17 @@ def plane_wave_rhs(rw: RWG, k0, pol=(1.0, 0.0, 0.0), khat=(0.0, 0.0, 1.0)):
 # -------------------------------------------------------------------------------------
 # internal problem (Sec. II-B) and the system (Sec. II-C)
 # -------------------------------------------------------------------------------------
-def internal_blocks(rw: RWG, freq, sigma, ix=None):
-    """Per-object Zhat_i and Yhat_i (dense), background vacuum (mu_rl = 1)."""
+def internal_blocks(rw: RWG, freq, sigma, ix=None, objects=None):
+    """Per-object Zhat_i and Yhat_i (dense), background vacuum (mu_rl = 1). With `objects`,
+    only those objects' blocks are formed (None in the other places)."""
     k0 = k0_of(freq)
     ix = ix_matrix(rw) if ix is None else ix
     Zs, Ys = [], []
     for i, (e0, e1) in enumerate(rw.obj_edge_ranges()):
+        if objects is not None and i not in objects:
+            Zs.append(None)
+            Ys.append(None)
+            continue
         ixi = ix[e0:e1, e0:e1].toarray()
         epsc = eps_rc(sigma[i], freq)
         ki = k_medium(k0, epsc)
