@@ -194,6 +194,8 @@ def ncu_case(args):
     if args.ncu_case == "internal":
         mesh, grid, freq = synth.bar_array_config(0, 10e9)
         ctx = api.Context(mesh, grid, freq)
+        if args.gemv_shape:  # the launch the timed run chose (the autotuner's timing under a
+            ctx.gemv_plan(*[int(v) for v in args.gemv_shape.split(",")])  # profiler differs)
         h = torch.from_numpy(synth.rand_cvec(ctx.ne, 4).astype(np.complex64)).cuda()
         e, heq = torch.empty_like(h), torch.empty_like(h)
         torch.cuda.synchronize()
@@ -202,7 +204,8 @@ def ncu_case(args):
             ctx.internal(h, e, heq, prec=api.BEM_C32)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        print(json.dumps({"ncu_case": "internal", "ctas": ctx.gemv_ctas, "split": ctx.gemv_split,
+        print(json.dumps({"ncu_case": "internal", "kind": ctx.gemv_kind, "ctas": ctx.gemv_ctas,
+                          "split": ctx.gemv_split,
                           "loads_in_flight": ctx.gemv_unroll, "tune_ns": ctx.gemv_tune_ns}))
         return
     mesh = synth.bar_array(0)
@@ -216,6 +219,40 @@ def ncu_case(args):
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": "gemv", "blocks": len(sizes), "rows": N,
                       "bytes": int(A.numel() * 8)}))
+
+
+def copper_bar_numbers(api, synth, torch):
+    """The single 2x2x20 um copper bar at 10 GHz (2016 RWG + 1344 pulse unknowns): microseconds
+    per graph-replayed system matvec in FP64 and FP32, and the time to a true FP64 residual of
+    1e-6 for the plane wave, plain FP64 GMRES against the chosen FP32-bulk FGMRES with the
+    block-diagonal preconditioner (after an untimed warm-up solve of each)."""
+    mesh, grid, freq = synth.copper_bar()
+    ctx = api.Context(mesh, grid, freq)
+    out = {"structure": "Cu bar 2x2x20 um, 10 GHz", "ne": ctx.ne, "nt": ctx.nt}
+    for prec, name in ((api.BEM_C64, "matvec_us_fp64"), (api.BEM_C32, "matvec_us_fp32")):
+        x = torch.from_numpy(synth.rand_cvec(ctx.n, 2)).to(api.cdtype(prec)).cuda()
+        y = torch.empty_like(x)
+        for _ in range(10):
+            ctx.matvec(x, y, prec=prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(100):
+            ctx.matvec(x, y, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) * 10.0  # 100 launches, ms -> us each
+    b = ctx.rhs_plane_wave(prec=api.BEM_C64)
+    for name, mode, pc in (("plain_fp64", api.BEM_C64, 0), ("chosen_fp32_block", api.BEM_C32, 1)):
+        ctx.solve(b, tol=1e-6, restart=200, max_iter=2, prec_mode=mode, precond=pc)  # warm-up
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, info = ctx.solve(b, tol=1e-6, restart=200, max_iter=3000, prec_mode=mode,
+                            time_limit_s=60.0, precond=pc)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t1, "iters": info["iters"],
+                     "resid_true": info["resid_true"], "status": info["status"]}
+    ctx.close()
+    return out
 
 
 def precision_study(args):
@@ -296,6 +333,8 @@ def main():
     ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal"])
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--precision-study", action="store_true")
+    ap.add_argument("--gemv-shape", default=None,
+                    help="kind,ctas_per_sm,split,unroll of the GEMV launch in --ncu-case internal")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -414,11 +453,16 @@ def main():
                                ("chosen_fp32_block_learned", api.BEM_C32, 2)):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
+            torch.cuda.nvtx.range_push("solve_" + name)  # profiler range of this solve
             xs, info = ctx.solve(b, tol=1e-6, restart=200, max_iter=3000, prec_mode=mode,
                                  time_limit_s=120.0, precond=pc)
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             solve[name] = {"seconds": time.perf_counter() - t1, "iters": info["iters"],
                            "resid_true": info["resid_true"], "status": info["status"]}
+
+    if not args.no_solve and rank == 0:
+        solve["copper_bar"] = copper_bar_numbers(api, synth, torch)
 
     if rank == 0:
         hbm, src = peaks()

@@ -111,6 +111,16 @@ int aim_info(const aim_ctx* ctx, int64_t* info, int n);
  * kind ran correctly at set-up (aim_info entries 16-17). FP64 products always use kind 1. */
 int aim_gemv_select(aim_ctx* ctx, int kind);
 
+/* Set the FP32 block-GEMV launch explicitly (reproducible timing or profiling; the autotuner's
+ * choice otherwise): kind 0 row plan (ctas_per_sm 4 or 6, split 1, 2 or 4 column parts per
+ * row, unroll 4, or 8 with 4 CTAs/SM), 1 flat or 3 stream ((6, unroll 4) or (4, unroll 8);
+ * split ignored), 2 bulk-copy staged (ctas_per_sm 1 or 2; split, unroll ignored). The launch's
+ * product of a fixed vector is checked against the reference launch before it is used. Waits
+ * for the device to be idle and drops the captured matvec graphs. Errors: BEM_EINVAL for an
+ * unsupported shape, BEM_ECUDA if the check fails. aim_gemv_select(ctx, 0) restores the
+ * autotuner's choice. */
+int aim_gemv_plan(aim_ctx* ctx, int kind, int ctas_per_sm, int split, int unroll);
+
 /* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)
  * or AIM_OP_SYSTEM (the SLIM system of Eq. AEFIEoutJ, vectors of N_E + N_T):
  *   e = Z h, h_eq = Y e, j = h - h_eq,

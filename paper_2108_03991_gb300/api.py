@@ -73,6 +73,7 @@ def lib():
         L.aim_info.argtypes = [vp, C.POINTER(i64), C.c_int]
         L.aim_matvec.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
         L.aim_gemv_select.argtypes = [vp, C.c_int]
+        L.aim_gemv_plan.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.bem_port_ring.argtypes = [vp, C.c_int, C.c_int, d, d, C.POINTER(i32), C.POINTER(d), C.c_int]
         L.bem_rhs_port.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), d, vp, C.c_int, vp]
         L.bem_port_current.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), vp, C.c_int,
@@ -204,8 +205,11 @@ class Context:
         h = C.c_void_p()
         _check(L.aim_setup(C.byref(m), C.byref(g), float(freq), C.byref(h)))
         self.h = h
+        self._read_info()
+
+    def _read_info(self):
         info = (C.c_int64 * 20)()
-        _check(L.aim_info(h, info, 20))
+        _check(lib().aim_info(self.h, info, 20))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -263,9 +267,15 @@ class Context:
                                   out.ctypes.data_as(C.POINTER(C.c_double)), _stream()))
         return out[:, 0::2] + 1j * out[:, 1::2]
 
+    def gemv_plan(self, kind, ctas_per_sm, split=1, unroll=4):
+        """Set the FP32 block-GEMV launch explicitly (see aim_gemv_plan)."""
+        _check(lib().aim_gemv_plan(self.h, int(kind), int(ctas_per_sm), int(split), int(unroll)))
+        self._read_info()
+
     def gemv_select(self, kind):
         """FP32 block-GEMV launch: 0 autotuned choice, 1 best plain, 2 best bulk-copy staged."""
         _check(lib().aim_gemv_select(self.h, int(kind)))
+        self._read_info()
 
     def close(self):
         if self.h:

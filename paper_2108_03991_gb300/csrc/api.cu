@@ -128,6 +128,15 @@ int aim_gemv_select(aim_ctx* c, int kind) {
   return BEM_OK;
 }
 
+int aim_gemv_plan(aim_ctx* c, int kind, int ctas_per_sm, int split, int unroll) {
+  BEM_TRY(check_ctx(c, "aim_gemv_plan"));
+  BEM_CUDA(cudaDeviceSynchronize());
+  BEM_TRY(set_gemv_shape(c, kind, ctas_per_sm, split, unroll));
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old launches
+  c->graphs.clear();
+  return BEM_OK;
+}
+
 int aim_matvec(aim_ctx* c, int which, const void* x, void* y, int prec, void* stream) {
   BEM_TRY(check_ctx(c, "aim_matvec"));
   BEM_TRY(check_prec(prec, "aim_matvec"));

@@ -356,6 +356,7 @@ void free_net(aim_ctx* c);
 template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cudaStream_t s);
 void free_geo_store(aim_ctx* c);
 void free_far_geo(aim_ctx* c);
+int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);
 double k0_of(double f);
 // solver (gmres.cu)
 int gmres_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,

@@ -622,6 +622,63 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
   return BEM_OK;
 }
 
+// A caller-chosen FP32 launch for the context's internal products (kind 0 row plan, 1 flat,
+// 2 staged, 3 stream), checked against the autotuner's reference product before use.
+int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
+  const bool ok_shape =
+      (kind == 0 && (cps == 4 || cps == 6) && (split == 1 || split == 2 || split == 4) &&
+       (unroll == 4 || (unroll == 8 && cps == 4))) ||
+      ((kind == 1 || kind == 3) && ((cps == 6 && unroll == 4) || (cps == 4 && unroll == 8))) ||
+      (kind == 2 && (cps == 1 || cps == 2));
+  if (!ok_shape) {
+    set_error("aim_gemv_plan: unsupported shape (kind %d, %d CTAs/SM, split %d, unroll %d)", kind,
+              cps, split, unroll);
+    return BEM_EINVAL;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<int32_t> n(c->nobj);
+  for (int i = 0; i < c->nobj; ++i) n[i] = c->e1[i] - c->e0[i];
+  int* derr = nullptr;
+  BEM_TRY(dalloc_t(c, &derr, 1));
+  BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
+  GemvPlan p;
+  const GemvCand g{kind, cps, kind == 0 ? split : 1, kind == 2 ? (cps == 1 ? 4 : 2) : unroll};
+  const int r = make_gemv_plan(c, nullptr, g, nsm, n, c->zoff, c->zld, derr, &p);
+  if (r == 1) {
+    set_error("aim_gemv_plan: a row does not fit a shared-memory stage");
+    return BEM_EINVAL;
+  }
+  BEM_TRY(r);
+  // the product of a fixed x must match the first autotuner candidate's (row plan, 6 CTAs/SM)
+  int64_t tot = 0;
+  for (int v : n) tot += v;
+  std::vector<float2> xh(tot), y0(tot), y1(tot);
+  for (int64_t i = 0; i < tot; ++i) xh[i] = make_float2((float)std::sin(0.37 * i), (float)std::cos(0.11 * i));
+  TunePlan io;
+  float2 *x = nullptr, *y = nullptr;
+  BEM_TRY(io.put(&x, xh));
+  BEM_TRY(io.put(&y, y0));
+  BEM_TRY(run_gemv_plan<float>(c->gplan_alt[0], c->f32.Z, x, y, 1, tot, nullptr, 0));
+  BEM_CUDA(cudaMemcpy(y0.data(), y, tot * sizeof(float2), cudaMemcpyDeviceToHost));
+  BEM_TRY(run_gemv_plan<float>(p, c->f32.Z, x, y, 1, tot, nullptr, 0));
+  BEM_CUDA(cudaMemcpy(y1.data(), y, tot * sizeof(float2), cudaMemcpyDeviceToHost));
+  int herr = 0;
+  BEM_CUDA(cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost));
+  double num = 0, den = 0;
+  for (int64_t i = 0; i < tot; ++i) {
+    num = std::max(num, (double)std::hypot(y1[i].x - y0[i].x, y1[i].y - y0[i].y));
+    den = std::max(den, (double)std::hypot(y0[i].x, y0[i].y));
+  }
+  if (herr != 0 || !(num <= 1e-4 * den)) {
+    set_error("aim_gemv_plan: the launch's product differs from the reference (%g)", num / den);
+    return BEM_ECUDA;
+  }
+  c->gplan = p;
+  return BEM_OK;
+}
+
 // ---------------------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------------------

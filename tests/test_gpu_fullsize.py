@@ -1,0 +1,99 @@
+"""GPU parity at the benchmark's full size, in the launch configuration bench.py times: the 4x4
+Cu bar array (seed 0), 17,832 RWG + 11,888 pulse unknowns, 10 GHz, AIM grid 35 x 35 x 78, set up
+exactly as bench.py does (the set-up autotuner picks the GEMV launch). The oracle cannot form
+every near pair and every internal block at this size in a test's time, so it computes sampled
+outputs one by one: 64 seeded rows of L^A and of L^Phi (far part by the full FFT convolution,
+near part from the exact entries of those rows), the rows of the smallest object for the
+internal products, and sampled rows of the whole system matvec for an x whose h is non-zero on
+that object only (so j needs only that object's Z and Y_eq)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import aim as oaim, operators as op  # noqa: E402
+from oracle.rwg import from_mesh  # noqa: E402
+from paper_2108_03991_gb300 import api, synth  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_03991_gb300 import build
+    build.build()
+    mesh, grid, freq = synth.bar_array_config(0, 10e9)
+    ctx = api.Context(mesh, grid, freq)
+    rw = from_mesh(mesh)
+    k0 = op.k0_of(freq)
+    rng = np.random.default_rng(12)
+    rows_e = np.sort(rng.choice(rw.ne, 64, replace=False))
+    rows_t = np.sort(rng.choice(rw.nt, 64, replace=False))
+    A = oaim.Aim(rw, grid.origin, grid.h, grid.n, k0)
+    # L^Phi rows: the sampled triangles and the two triangles of every sampled edge
+    tri = np.unique(np.concatenate([rows_t, rw.et[rows_e].ravel()]))
+    A.build_near(rows_e=rows_e, rows_t=tri)
+    ranges = rw.obj_edge_ranges()
+    obj = int(np.argmin([b - a for a, b in ranges]))
+    Zs, Ys = op.internal_blocks(rw, freq, mesh.sigma, objects=[obj])
+    return dict(ctx=ctx, rw=rw, k0=k0, A=A, rows_e=rows_e, rows_t=rows_t, obj=obj,
+                rng=ranges[obj], Z=Zs[obj], Y=Ys[obj], ix=op.ix_matrix(rw), fd=op.fd_matrix(rw))
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-11)])
+def test_fullsize_LA_LPhi_rows(full, prec, tol):
+    ctx, A, re, rt = full["ctx"], full["A"], full["rows_e"], full["rows_t"]
+    j = synth.rand_cvec(ctx.ne, 21)
+    q = synth.rand_cvec(ctx.nt, 22)
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    ya = ctx.matvec(torch.from_numpy(j.astype(npdt)).cuda(), which=api.AIM_OP_LA, prec=prec)
+    yp = ctx.matvec(torch.from_numpy(q.astype(npdt)).cuda(), which=api.AIM_OP_LPHI, prec=prec)
+    ref_a = (A.far_A(j) + A.LNR_A @ j)[re]
+    ref_p = (A.far_P(q) + A.LNR_P @ q)[rt]
+    assert rel(ya.cpu().numpy()[re], ref_a) < tol
+    assert rel(yp.cpu().numpy()[rt], ref_p) < tol
+
+
+@pytest.mark.parametrize("prec,tol_z,tol_y", [(api.BEM_C32, 1e-5, 1e-5), (api.BEM_C64, 1e-9, 1e-6)])
+def test_fullsize_internal_rows(full, prec, tol_z, tol_y):
+    """e = Z h and h_eq = Y_eq e on the rows of the smallest object, with the launch the
+    autotuner chose for all 16 objects (the other objects' rows are computed in the same
+    launch). FP64 bounds as in the small-problem tests (two independent LU solves)."""
+    ctx = full["ctx"]
+    a, b = full["rng"]
+    h = synth.rand_cvec(ctx.ne, 23)
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    e, heq = ctx.internal(torch.from_numpy(h.astype(npdt)).cuda(), prec=prec)
+    eo = full["Z"] @ h[a:b]
+    assert rel(e.cpu().numpy()[a:b], eo) < tol_z
+    assert rel(heq.cpu().numpy()[a:b], full["Y"] @ eo) < tol_y
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-7)])
+def test_fullsize_system_rows(full, prec, tol):
+    """Sampled rows of the system matvec of Eq. AEFIEoutJ (both block rows) for x = [h; q]
+    with h non-zero on the smallest object only and q everywhere."""
+    ctx, A, rw, k0 = full["ctx"], full["A"], full["rw"], full["k0"]
+    re, rt = full["rows_e"], full["rows_t"]
+    a, b = full["rng"]
+    h = np.zeros(ctx.ne, complex)
+    h[a:b] = synth.rand_cvec(b - a, 24)
+    q = synth.rand_cvec(ctx.nt, 25)
+    x = np.concatenate([h, q])
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    y = ctx.matvec(torch.from_numpy(x.astype(npdt)).cuda(), prec=prec).cpu().numpy()
+    e = np.zeros(ctx.ne, complex)
+    e[a:b] = full["Z"] @ h[a:b]
+    j = h.copy()
+    j[a:b] -= full["Y"] @ e[a:b]
+    lphi_q = A.far_P(q) + A.LNR_P @ q  # exact on the triangles of the sampled edges
+    y1 = 1j * k0 * (A.far_A(j) + A.LNR_A @ j) + full["ix"] @ e - full["fd"].T @ lphi_q
+    y2 = full["fd"] @ j + 1j * k0 * q
+    got = np.concatenate([y[re], y[ctx.ne + rt]])
+    ref = np.concatenate([y1[re], y2[rt]])
+    assert rel(got, ref) < tol

@@ -165,13 +165,18 @@ def test_gemv_autotuner_candidates(prob):
     assert ctx.gemv_tune_ns["plain"] > 0 and ctx.gemv_tune_ns["staged"] > 0
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, (0, 6, 2, 4), (0, 4, 4, 8), (1, 4, 1, 8), (3, 6, 1, 4),
+                                  (3, 4, 1, 8), (2, 2, 1, 4)])
 def test_gemv_kinds_match_oracle(prob, kind):
-    """The plain and the staged FP32 GEMV, forced in turn, against the FP64 oracle: internal
-    products with 3 right-hand sides (the staged kernel's multi-RHS and h - Y e forms) and the
-    system matvec."""
+    """Every FP32 GEMV form, forced in turn (the autotuner's best plain and best staged, then
+    explicit row-plan, flat, stream and staged launches), against the FP64 oracle: internal
+    products with 3 right-hand sides (the multi-RHS and h - Y e forms) and the system matvec."""
     ctx, S = prob["ctx"], prob["S"]
-    ctx.gemv_select(kind)
+    if isinstance(kind, tuple):
+        ctx.gemv_plan(*kind)
+        assert ctx.gemv_kind == kind[0]
+    else:
+        ctx.gemv_select(kind)
     try:
         h = np.stack([synth.rand_cvec(ctx.ne, 60 + r) for r in range(3)])
         e, heq = ctx.internal(torch.from_numpy(h.ravel().astype(np.complex64)).cuda(), nrhs=3,
