@@ -6,6 +6,10 @@ axial position z_p; a gap voltage V drives E_inc = V delta(z - z_p) zhat, so
   <f_m, E_inc> = s_m V l_m   for the ring edges (s_m = +1 if f_m crosses the edge along +z),
 and the port current is the circulation of H around the ring (Ampere),
   I = sum_m s_m l_m h_m.
+Units: with lengths in micrometres the first block row of the system is the SI row divided by
+ell^2 (ell = 1e-6 m), so port_rhs(V = 1) is the excitation of a gap voltage eta0 * ell volts
+(the RHS carries the 1/eta0 of the E_inc/eta0 row), port_current is the current in amperes
+divided by ell, and the input impedance is Z = eta0 / port_current(V = 1) ohms.
 """
 from __future__ import annotations
 
