@@ -187,9 +187,10 @@ int bem_rhs_plane_wave(aim_ctx* ctx, const double* pol, const double* khat, void
 int bem_port_ring(aim_ctx* ctx, int obj, int axis, double coord, double tol, int32_t* edges,
                   double* signs, int cap);
 
-/* b = [s_m l_m V / eta0 on the ring edges, 0 on the other edges; 0 on the triangles]: the
- * delta-gap excitation <f_m, E_inc> / eta0 of a gap voltage V (volts), in the scaling of
- * bem_rhs_plane_wave, so that the solution's h is H in A/m. edges, signs: HOST arrays of n
+/* b = [s_m l_m V / (eta0 ell) on the ring edges (l_m in micrometres, ell = 1e-6 m), 0 on the
+ * other edges; 0 on the triangles]: the delta-gap excitation <f_m, E_inc> / eta0 of a gap
+ * voltage V (volts) in the micrometre scaling of bem_rhs_plane_wave (the first block row is the
+ * SI row divided by ell^2), so that the solution's h is H in A/m. edges, signs: HOST arrays of n
  * entries (from bem_port_ring). b: device vector of N_E + N_T in prec. Synchronises the stream.
  * Errors: BEM_EINVAL for an empty port or an edge out of range. */
 int bem_rhs_port(aim_ctx* ctx, int n, const int32_t* edges, const double* signs, double v_gap,

@@ -327,32 +327,136 @@ __global__ void __launch_bounds__(256) k_zfused(V* ws, const V* __restrict__ gha
   }
 }
 
-// z pass in registers, for Pz = L * M with L in {8, 16, 32} lanes and M in {2, 3, 4, 5, 8}:
-// a group of L lanes holds one z line, element z = l + L n1 in lane l, register n1. Forward:
-// the M-point DFT over n1 in registers, the twiddles W_Pz^(l k1), then for every k1 an L-point
-// DFT across the lanes by radix-2 decimation in frequency with xor shuffles, which leaves
-// X[k1 + M bitrev(l)] in lane l. The product with Ghat is taken in that order, and the inverse
-// undoes the steps in reverse (the butterflies of every shuffle stage inverted, then the
-// conjugate twiddles, then the inverse M-point DFT), so the output is back in natural order
-// with no shared memory and no barrier. A CTA of 8 warps takes 8 * 32 / L adjacent x of one y.
-template <typename V, int M>
-__device__ __forceinline__ void dft_small(V* v, bool inv) {
-  if (M == 2) bfly2(v);
-  else if (M == 3) bfly3(v, inv);
-  else if (M == 4) bfly4(v, inv);
-  else if (M == 5) bfly5(v, inv);
+// ---------------------------------------------------------------------------------------
+// transforms in registers: a line of P = L * M points held by a group of L lanes (L = 8, 16 or
+// 32), element n = l + L n1 in lane l, register n1. Forward: the M-point DFT over n1 in
+// registers, the twiddles W_P^(l k1), then for every k1 an L-point DFT across the lanes by
+// radix-2 decimation in frequency with xor shuffles, which leaves X[k1 + M bitrev(l)] in lane l,
+// register k1. The inverse undoes the steps in reverse (every shuffle butterfly inverted, the
+// conjugate twiddles, the inverse M-point DFT) and takes its input in that bit-reversed order,
+// so a forward and an inverse transform need no reordering and no shared memory between them.
+// Both are unnormalised. The M-point DFT is one butterfly for M in {2, 3, 4, 5, 8} and two
+// levels A x B (A-point DFTs of stride B, twiddles W_M^(b ka), B-point DFTs) for M in
+// {6, 9, 10, 12, 15, 16}; twiddles come from the line's table W_P^j (P divisible by M).
+// ---------------------------------------------------------------------------------------
+template <typename V, int R>
+__device__ __forceinline__ void bfly_r(V* v, bool inv) {
+  if (R == 2) bfly2(v);
+  else if (R == 3) bfly3(v, inv);
+  else if (R == 4) bfly4(v, inv);
+  else if (R == 5) bfly5(v, inv);
   else bfly8(v, inv);
+}
+
+template <int M> struct Split { static constexpr int A = 1, B = 1; };
+template <> struct Split<6> { static constexpr int A = 2, B = 3; };
+template <> struct Split<9> { static constexpr int A = 3, B = 3; };
+template <> struct Split<10> { static constexpr int A = 2, B = 5; };
+template <> struct Split<12> { static constexpr int A = 4, B = 3; };
+template <> struct Split<15> { static constexpr int A = 3, B = 5; };
+template <> struct Split<16> { static constexpr int A = 4, B = 4; };
+
+// natural-order M-point DFT of v in registers (tw: W_P^j, P = M * tstride)
+template <typename V, int M>
+__device__ __forceinline__ void dft_reg(V* v, const V* tw, int tstride, bool inv) {
+  if constexpr (M == 2 || M == 3 || M == 4 || M == 5 || M == 8) {
+    bfly_r<V, M>(v, inv);
+  } else {
+    constexpr int A = Split<M>::A, B = Split<M>::B;
+    V u[B][A];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+      for (int a = 0; a < A; ++a) u[b][a] = v[b + B * a];
+      bfly_r<V, A>(u[b], inv);
+#pragma unroll
+      for (int ka = 1; ka < A; ++ka)
+        if (b > 0) {
+          V w = tw[(b * ka) * tstride];
+          if (inv) w.y = -w.y;
+          u[b][ka] = cmul(u[b][ka], w);
+        }
+    }
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) {
+      V t[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) t[b] = u[b][ka];
+      bfly_r<V, B>(t, inv);
+#pragma unroll
+      for (int kb = 0; kb < B; ++kb) v[ka + A * kb] = t[kb];
+    }
+  }
 }
 
 template <typename V> __device__ __forceinline__ V shfl_x(V v, int s) {
   return mk(__shfl_xor_sync(0xffffffffu, v.x, s), __shfl_xor_sync(0xffffffffu, v.y, s));
 }
 
+template <int L> struct Log2 { static constexpr int v = L == 8 ? 3 : (L == 16 ? 4 : 5); };
+
+// twiddles of lane lg for a line of P = L M: tk[k1] = W_P^(lg k1), ts[st] = W_(2s)^(lg mod s)
+// for the shuffle stage of pair distance s = L >> (st + 1)
+template <typename V, int L, int M>
+__device__ __forceinline__ void reg_twiddles(const V* tw, int P, int lg, V* tk, V* ts) {
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) tk[k1] = tw[(lg * k1) % P];
+#pragma unroll
+  for (int st = 0; st < Log2<L>::v; ++st) {
+    const int sp = L >> (st + 1);
+    ts[st] = tw[(lg & (sp - 1)) * (P / (2 * sp))];
+  }
+}
+
+template <typename V, int L, int M>
+__device__ __forceinline__ void reg_fft_fwd(V* v, const V* tw, int P, int lg, const V* tk,
+                                            const V* ts) {
+  dft_reg<V, M>(v, tw, P / M, false);
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], tk[k1]);
+#pragma unroll
+  for (int st = 0; st < Log2<L>::v; ++st) {
+    const int sp = L >> (st + 1);
+    const bool top = (lg & sp) == 0;
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const V p = shfl_x(v[k1], sp);
+      v[k1] = top ? cadd(v[k1], p) : cmul(csub(p, v[k1]), ts[st]);
+    }
+  }
+}
+
+template <typename V, int L, int M>
+__device__ __forceinline__ void reg_fft_inv(V* v, const V* tw, int P, int lg, const V* tk,
+                                            const V* ts) {
+#pragma unroll
+  for (int st = Log2<L>::v - 1; st >= 0; --st) {
+    const int sp = L >> (st + 1);
+    const bool top = (lg & sp) == 0;
+    const V w = mk(ts[st].x, -ts[st].y);
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const V own = top ? v[k1] : cmul(v[k1], w);
+      const V p = shfl_x(own, sp);
+      v[k1] = top ? cadd(own, p) : csub(p, own);
+    }
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], mk(tk[k1].x, -tk[k1].y));
+  dft_reg<V, M>(v, tw, P / M, true);
+}
+
+template <int L> __device__ __forceinline__ int brev_l(int l) {
+  return (int)(__brev((unsigned)l) >> (32 - Log2<L>::v));
+}
+
+// z pass: a CTA of 8 warps takes 8 * 32 / L adjacent x of one y; forward transform along z of
+// the nz planes that hold data, times Ghat (in the transform's bit-reversed order), inverse,
+// and the first nz outputs stored back
 template <typename V, int L, int M>
 __global__ void __launch_bounds__(256) k_zreg(V* ws, const V* __restrict__ ghat,
                                               const V* __restrict__ twz, PlaneArgs a) {
   constexpr int G = 32 / L;  // lines per warp
-  constexpr int LOG_L = L == 8 ? 3 : (L == 16 ? 4 : 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lg = lane & (L - 1), grp = lane / L;
   const int x = blockIdx.x * (8 * G) + warp * G + grp, y = blockIdx.y, c = blockIdx.z;
@@ -366,53 +470,17 @@ __global__ void __launch_bounds__(256) k_zreg(V* ws, const V* __restrict__ ghat,
     const int z = lg + L * n1;
     v[n1] = (live && z < a.nz) ? base[z * plane] : czero<V>();
   }
-  // twiddles of this lane: W_P^(lg k1) and W_(2s)^(lg mod s) = W_P^((lg mod s) P / (2s))
-  V tk[M], ts[LOG_L];
-#pragma unroll
-  for (int k1 = 0; k1 < M; ++k1) tk[k1] = twz[(lg * k1) % P];
-#pragma unroll
-  for (int st = 0; st < LOG_L; ++st) {
-    const int sp = L >> (st + 1);  // pair distance of stage st: L/2, L/4, ..., 1
-    ts[st] = twz[(lg & (sp - 1)) * (P / (2 * sp))];
-  }
-  // forward
-  dft_small<V, M>(v, false);
-#pragma unroll
-  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], tk[k1]);
-#pragma unroll
-  for (int st = 0; st < LOG_L; ++st) {
-    const int sp = L >> (st + 1);
-    const bool top = (lg & sp) == 0;
-#pragma unroll
-    for (int k1 = 0; k1 < M; ++k1) {
-      const V p = shfl_x(v[k1], sp);
-      v[k1] = top ? cadd(v[k1], p) : cmul(csub(p, v[k1]), ts[st]);
-    }
-  }
-  // times Ghat at k = k1 + M bitrev(lg)
+  V tk[M], ts[Log2<L>::v];
+  reg_twiddles<V, L, M>(twz, P, lg, tk, ts);
+  reg_fft_fwd<V, L, M>(v, twz, P, lg, tk, ts);
   const int fy = min(y, a.Py - y), fx = min(x, a.Px - x);
-  const int k2 = (int)(__brev((unsigned)lg) >> (32 - LOG_L));
+  const int k2 = brev_l<L>(lg);
 #pragma unroll
   for (int k1 = 0; k1 < M; ++k1) {
     const int k = k1 + M * k2, fz = min(k, P - k);
     if (live) v[k1] = cmul(v[k1], ghat[((int64_t)fz * a.gy + fy) * a.gx + fx]);
   }
-  // inverse: shuffle stages in reverse order, each butterfly inverted (unnormalised)
-#pragma unroll
-  for (int st = LOG_L - 1; st >= 0; --st) {
-    const int sp = L >> (st + 1);
-    const bool top = (lg & sp) == 0;
-    const V w = mk(ts[st].x, -ts[st].y);
-#pragma unroll
-    for (int k1 = 0; k1 < M; ++k1) {
-      const V own = top ? v[k1] : cmul(v[k1], w);
-      const V p = shfl_x(own, sp);
-      v[k1] = top ? cadd(own, p) : csub(p, own);
-    }
-  }
-#pragma unroll
-  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], mk(tk[k1].x, -tk[k1].y));
-  dft_small<V, M>(v, true);
+  reg_fft_inv<V, L, M>(v, twz, P, lg, tk, ts);
 #pragma unroll
   for (int n1 = 0; n1 < M; ++n1) {
     const int z = lg + L * n1;
@@ -420,15 +488,142 @@ __global__ void __launch_bounds__(256) k_zreg(V* ws, const V* __restrict__ ghat,
   }
 }
 
-// (L, M) of the register z pass for Pz, or false
-static bool zreg_shape(int P, int* L, int* M) {
-  for (int l : {32, 16, 8})
-    for (int m : {2, 3, 4, 5, 8})
-      if (l * m == P) {
-        *L = l;
-        *M = m;
-        return true;
+// plane passes in registers (one padded x-y plane per CTA of 256 threads, the x spectra of the
+// rows in shared memory at pitch Px + 1 between the two directions). Forward: the ny rows that
+// hold data along x (groups of LX lanes, one row each) into shared memory, then every column
+// along y, stored straight to the workspace (for one register the groups of a warp write
+// adjacent x of one row). Inverse: every column along y read straight from the workspace,
+// keeping the ny rows that are read back, into shared memory, then those rows along x, storing
+// the nx x ny window.
+template <typename V, int LX, int MX, int LY, int MY>
+__global__ void __launch_bounds__(256) k_plane_fwd_reg(const V* __restrict__ sigma, V* __restrict__ ws,
+                                                       const V* __restrict__ twx,
+                                                       const V* __restrict__ twy, PlaneArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  V* tx = reinterpret_cast<V*>(smem_raw);
+  V* ty = tx + a.Px;
+  V* S = ty + a.Py;
+  const int pitch = a.Px + 1;
+  const int z = blockIdx.x, c = blockIdx.y;
+  for (int i = threadIdx.x; i < a.Px; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
+  __syncthreads();
+  const V* src = sigma + c * a.ng + (int64_t)z * a.ny * a.nx;
+  {
+    const int lg = threadIdx.x & (LX - 1), grp = threadIdx.x / LX, ngrp = blockDim.x / LX;
+    V tk[MX], ts[Log2<LX>::v];
+    reg_twiddles<V, LX, MX>(tx, a.Px, lg, tk, ts);
+    const int k2 = brev_l<LX>(lg);
+    // every group runs the same number of rounds (the shuffles need whole warps)
+    for (int y0 = 0; y0 < a.ny; y0 += ngrp) {
+      const int y = y0 + grp;
+      V v[MX];
+#pragma unroll
+      for (int n1 = 0; n1 < MX; ++n1) {
+        const int x = lg + LX * n1;
+        v[n1] = (y < a.ny && x < a.nx) ? src[y * a.nx + x] : czero<V>();
       }
+      reg_fft_fwd<V, LX, MX>(v, tx, a.Px, lg, tk, ts);
+      if (y < a.ny) {
+#pragma unroll
+        for (int k1 = 0; k1 < MX; ++k1) S[y * pitch + k1 + MX * k2] = v[k1];
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int lg = threadIdx.x & (LY - 1), grp = threadIdx.x / LY, ngrp = blockDim.x / LY;
+    V tk[MY], ts[Log2<LY>::v];
+    reg_twiddles<V, LY, MY>(ty, a.Py, lg, tk, ts);
+    const int k2 = brev_l<LY>(lg);
+    V* dst = ws + c * a.P3 + (int64_t)z * a.Py * a.Px;
+    for (int x0 = 0; x0 < a.Px; x0 += ngrp) {
+      const int kx = x0 + grp;
+      V v[MY];
+#pragma unroll
+      for (int n1 = 0; n1 < MY; ++n1) {
+        const int y = lg + LY * n1;
+        v[n1] = (kx < a.Px && y < a.ny) ? S[y * pitch + kx] : czero<V>();
+      }
+      reg_fft_fwd<V, LY, MY>(v, ty, a.Py, lg, tk, ts);
+      if (kx < a.Px) {
+#pragma unroll
+        for (int k1 = 0; k1 < MY; ++k1) dst[(k1 + MY * k2) * a.Px + kx] = v[k1];
+      }
+    }
+  }
+}
+
+template <typename V, int LX, int MX, int LY, int MY>
+__global__ void __launch_bounds__(256) k_plane_inv_reg(const V* __restrict__ ws, V* __restrict__ phi,
+                                                       const V* __restrict__ twx,
+                                                       const V* __restrict__ twy, PlaneArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  V* tx = reinterpret_cast<V*>(smem_raw);
+  V* ty = tx + a.Px;
+  V* S = ty + a.Py;
+  const int pitch = a.Px + 1;
+  const int z = blockIdx.x, c = blockIdx.y;
+  for (int i = threadIdx.x; i < a.Px; i += blockDim.x) tx[i] = twx[i];
+  for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
+  const V* src = ws + c * a.P3 + (int64_t)z * a.Py * a.Px;
+  __syncthreads();
+  {
+    const int lg = threadIdx.x & (LY - 1), grp = threadIdx.x / LY, ngrp = blockDim.x / LY;
+    V tk[MY], ts[Log2<LY>::v];
+    reg_twiddles<V, LY, MY>(ty, a.Py, lg, tk, ts);
+    const int k2 = brev_l<LY>(lg);
+    for (int x0 = 0; x0 < a.Px; x0 += ngrp) {
+      const int kx = x0 + grp;
+      V v[MY];
+#pragma unroll
+      for (int k1 = 0; k1 < MY; ++k1)
+        v[k1] = kx < a.Px ? src[(k1 + MY * k2) * a.Px + kx] : czero<V>();
+      reg_fft_inv<V, LY, MY>(v, ty, a.Py, lg, tk, ts);
+      if (kx < a.Px) {
+#pragma unroll
+        for (int n1 = 0; n1 < MY; ++n1) {
+          const int y = lg + LY * n1;
+          if (y < a.ny) S[y * pitch + kx] = v[n1];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int lg = threadIdx.x & (LX - 1), grp = threadIdx.x / LX, ngrp = blockDim.x / LX;
+    V tk[MX], ts[Log2<LX>::v];
+    reg_twiddles<V, LX, MX>(tx, a.Px, lg, tk, ts);
+    const int k2 = brev_l<LX>(lg);
+    V* dst = phi + c * a.ng + (int64_t)z * a.ny * a.nx;
+    for (int y0 = 0; y0 < a.ny; y0 += ngrp) {
+      const int y = y0 + grp;
+      V v[MX];
+#pragma unroll
+      for (int k1 = 0; k1 < MX; ++k1) v[k1] = y < a.ny ? S[y * pitch + k1 + MX * k2] : czero<V>();
+      reg_fft_inv<V, LX, MX>(v, tx, a.Px, lg, tk, ts);
+      if (y < a.ny) {
+#pragma unroll
+        for (int n1 = 0; n1 < MX; ++n1) {
+          const int x = lg + LX * n1;
+          if (x < a.nx) dst[y * a.nx + x] = v[n1];
+        }
+      }
+    }
+  }
+}
+
+// the register shapes (L lanes, M registers) built, one per length P = L M, the most lanes first
+#define BEM_REG_SHAPES(X)                                                                         \
+  X(32, 2) X(32, 3) X(32, 4) X(32, 5) X(32, 6) X(32, 8) X(32, 9) X(32, 10) X(32, 12) X(32, 15)    \
+  X(32, 16) X(16, 3) X(16, 5) X(16, 9) X(16, 15) X(8, 3) X(8, 5) X(8, 9) X(8, 15)
+
+// (L, M) of a register transform of length P, or false
+static bool reg_shape(int P, int* L, int* M) {
+#define BEM_S(LL, MM) \
+  if (P == LL * MM) { *L = LL; *M = MM; return true; }
+  BEM_REG_SHAPES(BEM_S)
+#undef BEM_S
   return false;
 }
 
@@ -437,10 +632,24 @@ static void launch_zreg(int L, int M, dim3 grid, cudaStream_t s, V* ws, const V*
                         const V* tw, const PlaneArgs& a) {
 #define BEM_Z(LL, MM) \
   if (L == LL && M == MM) { k_zreg<V, LL, MM><<<grid, 256, 0, s>>>(ws, ghat, tw, a); return; }
-  BEM_Z(32, 2) BEM_Z(32, 3) BEM_Z(32, 4) BEM_Z(32, 5) BEM_Z(32, 8)
-  BEM_Z(16, 2) BEM_Z(16, 3) BEM_Z(16, 4) BEM_Z(16, 5) BEM_Z(16, 8)
-  BEM_Z(8, 2) BEM_Z(8, 3) BEM_Z(8, 4) BEM_Z(8, 5) BEM_Z(8, 8)
+  BEM_REG_SHAPES(BEM_Z)
 #undef BEM_Z
+}
+
+// the plane passes in registers exist for equal x and y shapes (square padded planes)
+template <typename V>
+static bool launch_plane_reg(bool inverse, int L, int M, dim3 grid, size_t smem, cudaStream_t s,
+                             const V* in, V* out, const V* twx, const V* twy, const PlaneArgs& a) {
+  const int nt = 256;
+#define BEM_P(LL, MM)                                                                                  \
+  if (L == LL && M == MM) {                                                                           \
+    if (inverse) k_plane_inv_reg<V, LL, MM, LL, MM><<<grid, nt, smem, s>>>(in, out, twx, twy, a);       \
+    else k_plane_fwd_reg<V, LL, MM, LL, MM><<<grid, nt, smem, s>>>(in, out, twx, twy, a);               \
+    return true;                                                                                      \
+  }
+  BEM_REG_SHAPES(BEM_P)
+#undef BEM_P
+  return false;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -588,15 +797,34 @@ int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename
     a.mag_TL = div_magic(a.TL);
     a.mag_Pz = div_magic(Pz);
     const size_t zsm = ((size_t)Pz + 2 * (size_t)a.TL * zp) * sizeof(V);
-    k_plane_fwd<V><<<dim3(nz, ncomp), 512, psm, s>>>(sigma, ws, b.tw[0], b.tw[1], a);
-    int zl = 0, zm = 0;
-    if (zreg_shape(Pz, &zl, &zm)) {
-      const int per = 8 * (32 / zl);  // x lines per CTA
-      launch_zreg<V>(zl, zm, dim3((Px + per - 1) / per, Py, ncomp), s, ws, b.Ghat, b.tw[2], a);
-    } else {
-      k_zfused<V><<<dim3((Px + a.TL - 1) / a.TL, Py, ncomp), 256, zsm, s>>>(ws, b.Ghat, b.tw[2], a);
+    // the register forms for FP32 (FP64 runs at a small fraction of the FP32 rate on this GPU
+    // and needs twice the registers: it keeps the shared-memory passes)
+    int xl = 0, xm = 0, zl = 0, zm = 0;
+    const size_t rsm = ((size_t)Px + Py + (size_t)ny * (Px + 1)) * sizeof(V);
+    bool fwd_done = false, z_done = false, inv_done = false;
+    if constexpr (sizeof(V) == sizeof(float2)) {
+      if (Px == Py && reg_shape(Px, &xl, &xm) && rsm <= 48 * 1024) {
+        fwd_done = launch_plane_reg<V>(false, xl, xm, dim3(nz, ncomp), rsm, s, sigma, ws, b.tw[0],
+                                       b.tw[1], a);
+        inv_done = true;  // launched below, after the z pass
+      }
+      if (reg_shape(Pz, &zl, &zm)) z_done = true;
     }
-    k_plane_inv<V><<<dim3(nz, ncomp), 512, psm, s>>>(ws, phi, b.tw[0], b.tw[1], a);
+    if (!fwd_done) k_plane_fwd<V><<<dim3(nz, ncomp), 512, psm, s>>>(sigma, ws, b.tw[0], b.tw[1], a);
+    if constexpr (sizeof(V) == sizeof(float2)) {
+      if (z_done) {
+        const int per = 8 * (32 / zl);  // x lines per CTA
+        launch_zreg<V>(zl, zm, dim3((Px + per - 1) / per, Py, ncomp), s, ws, b.Ghat, b.tw[2], a);
+      }
+    }
+    if (!z_done)
+      k_zfused<V><<<dim3((Px + a.TL - 1) / a.TL, Py, ncomp), 256, zsm, s>>>(ws, b.Ghat, b.tw[2], a);
+    if constexpr (sizeof(V) == sizeof(float2)) {
+      if (inv_done)
+        inv_done = launch_plane_reg<V>(true, xl, xm, dim3(nz, ncomp), rsm, s, ws, phi, b.tw[0],
+                                       b.tw[1], a);
+    }
+    if (!inv_done) k_plane_inv<V><<<dim3(nz, ncomp), 512, psm, s>>>(ws, phi, b.tw[0], b.tw[1], a);
     BEM_CUDA(cudaGetLastError());
     return BEM_OK;
   }

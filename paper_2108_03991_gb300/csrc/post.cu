@@ -189,7 +189,9 @@ int bem_rhs_port(aim_ctx* c, int n, const int32_t* edges, const double* signs, d
   const int64_t N = (int64_t)c->ne + c->nt;
   const size_t es = prec == BEM_C32 ? sizeof(float2) : sizeof(double2);
   std::vector<double> val(n);
-  for (int i = 0; i < n; ++i) val[i] = signs[i] * c->elen[edges[i]] * v_gap / kEta0;
+  // <f_m, E_inc> / eta0 = s_m l_m V / eta0 in SI units; the first block row of the system in
+  // micrometre units is the SI row divided by ell^2, and l_m is in micrometres here
+  for (int i = 0; i < n; ++i) val[i] = signs[i] * c->elen[edges[i]] * v_gap / (kEta0 * kEll);
   int32_t* de = nullptr;
   double* dv = nullptr;
   BEM_CUDA(cudaMallocAsync((void**)&de, n * sizeof(int32_t), s));

@@ -94,6 +94,52 @@ def box(lo, size, div):
     return np.array(verts, dtype=np.float64), np.array(tris, dtype=np.int32)
 
 
+def voxel_surface(solid, a, lo=(0.0, 0.0, 0.0)):
+    """Closed surface of a union of cubes of side a: solid[i, j, k] marks the cube
+    lo + a [i, i+1] x [j, j+1] x [k, k+1]. Every face between a solid and an empty cube is one
+    quad split into two triangles, counter-clockwise seen from the empty side (outward).
+    Vertices are shared through their lattice coordinates. Cubes that touch along an edge only
+    would make the surface non-manifold; the caller's shapes avoid them."""
+    solid = np.asarray(solid, dtype=bool)
+    lo = np.asarray(lo, dtype=np.float64)
+    pad = np.pad(solid, 1)
+    vid: dict[tuple[int, int, int], int] = {}
+    verts: list[np.ndarray] = []
+
+    def vertex(ijk):
+        key = tuple(int(v) for v in ijk)
+        i = vid.get(key)
+        if i is None:
+            i = len(verts)
+            vid[key] = i
+            verts.append(lo + a * np.array(key, dtype=np.float64))
+        return i
+
+    tris = []
+    for ax in range(3):
+        b, c = (ax + 1) % 3, (ax + 2) % 3
+        for sgn in (1, -1):
+            step = [0, 0, 0]
+            step[ax] = sgn
+            nb = np.roll(pad, -sgn, axis=ax)  # the neighbour on the +/- ax side
+            for cell in np.argwhere(pad & ~nb):
+                i0 = cell - 1  # back to unpadded indices
+                base = i0.copy()
+                if sgn > 0:
+                    base[ax] += 1
+                u, v = (b, c) if sgn > 0 else (c, b)  # e_u x e_v = sgn e_ax (outward)
+
+                def p(du, dv):
+                    ijk = base.copy()
+                    ijk[u] += du
+                    ijk[v] += dv
+                    return vertex(ijk)
+                p00, p10, p11, p01 = p(0, 0), p(1, 0), p(1, 1), p(0, 1)
+                tris.append((p00, p10, p11))
+                tris.append((p00, p11, p01))
+    return np.array(verts, dtype=np.float64), np.array(tris, dtype=np.int32)
+
+
 def icosphere(radius, subdiv, center=(0.0, 0.0, 0.0)):
     """Sphere surface: an icosahedron refined subdiv times by midpoint splitting."""
     t = (1.0 + math.sqrt(5.0)) / 2.0
@@ -170,6 +216,18 @@ def bar_mesh(w, t, length, a, sigma=SIGMA_CU, lo=(0.0, 0.0, 0.0)) -> Mesh:
     """One rectangular bar w x t x length (um), structured squares of side a split in two."""
     div = (round(w / a), round(t / a), round(length / a))
     V, F = box(lo, (w, t, length), div)
+    return merge([(V, F)], [sigma])
+
+
+def square_loop(side, w, t, a, sigma=SIGMA_CU) -> Mesh:
+    """A closed square loop (picture frame) of a conductor with cross-section w x t: outer side
+    `side`, in the plane z in [0, t], meshed with squares of side a (a divides side, w, t).
+    Its centreline is a square of side side - w."""
+    n, m, h = round(side / a), round(w / a), round(t / a)
+    solid = np.zeros((n, n, h), dtype=bool)
+    solid[:, :, :] = True
+    solid[m:n - m, m:n - m, :] = False
+    V, F = voxel_surface(solid, a)
     return merge([(V, F)], [sigma])
 
 

@@ -1,8 +1,9 @@
 """GPU parity of the excitation and post-processing calls (bem_port_ring, bem_rhs_port,
 bem_port_current, bem_farfield) against the FP64 oracle on a 1 x 1 x 4 um copper bar with two
 delta-gap ports, 10 GHz. The oracle's port right-hand side s l V with V = 1 is the library's
-with a gap voltage of eta0 volts; its port current sum s l h is the library's current times
-1e6 (edge lengths in micrometres there, metres here)."""
+for a gap voltage of eta0 * 1e-6 volts (micrometre scaling of the first block row); its port
+current sum s l h is the library's current (amperes) times 1e6 (edge lengths in micrometres
+there, metres here)."""
 import numpy as np
 import pytest
 
@@ -52,7 +53,7 @@ def test_port_rings_match_oracle(bar):
 def test_port_rhs_matches_oracle(bar):
     ctx, rw = bar["ctx"], bar["rw"]
     for eo, so in bar["rings"]:
-        b = ctx.rhs_port(eo, so, v_gap=op.ETA0, prec=api.BEM_C64).cpu().numpy()
+        b = ctx.rhs_port(eo, so, v_gap=op.ETA0 * op.ELL, prec=api.BEM_C64).cpu().numpy()
         ref = np.concatenate([ports.port_rhs(rw, eo, so), np.zeros(rw.nt)])
         assert rel(b, ref) < 1e-14
 
@@ -76,7 +77,7 @@ def test_two_port_admittance(bar, mode, tol, rtol):
     Yo = _oracle_admittance(bar)
     Yd = np.zeros((2, 2), complex)
     for q, (eq, sq) in enumerate(bar["rings"]):
-        b = ctx.rhs_port(eq, sq, v_gap=op.ETA0, prec=api.BEM_C64)
+        b = ctx.rhs_port(eq, sq, v_gap=op.ETA0 * op.ELL, prec=api.BEM_C64)
         x, info = ctx.solve(b, tol=tol, restart=100, max_iter=500, prec_mode=mode, precond=1)
         assert info["status"] == 0
         for p, (ep, sp) in enumerate(bar["rings"]):

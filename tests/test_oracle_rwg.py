@@ -68,3 +68,18 @@ def test_outward_orientation():
     # divergence theorem: sum A n . x = 3 V
     vol = np.sum(rw.area * np.einsum("ij,ij->i", rw.normal, rw.centroid)) / 3.0
     assert abs(vol - 6.0) < 1e-12
+
+
+def test_voxel_surface_and_loop_topology():
+    """The voxel-surface mesher reproduces the structured box (same vertices and triangles up to
+    order) and meshes the square loop as one closed, consistently oriented surface of genus 1
+    (V - E + F = 0)."""
+    V, F = synth.voxel_surface(np.ones((2, 2, 4), dtype=bool), 0.5)
+    Vb, Fb = synth.box((0.0, 0.0, 0.0), (1.0, 1.0, 2.0), (2, 2, 4))
+    assert V.shape == Vb.shape and F.shape == Fb.shape
+    assert np.allclose(np.sort(V, axis=0), np.sort(Vb, axis=0))
+    rw = from_mesh(synth.merge([(V, F)], [1.0]))
+    assert rw.ne == 3 * rw.nt // 2
+    loop = synth.square_loop(10.0, 2.0, 2.0, 1.0)
+    rl = from_mesh(loop)
+    assert loop.verts.shape[0] - rl.ne + rl.nt == 0
