@@ -94,54 +94,89 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(values, device="cpu"):
+    """The element-wise maximum over all ranks of a few per-rank timings (the job is as slow
+    as its slowest replica); the values themselves on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def replicas_value(ms_per_step, world):
+    """Whole-job matvecs/s of `world` independent replicas, each step taking ms_per_step (the
+    maximum over ranks)."""
+    return world * 1e3 / ms_per_step
+
+
+class OracleMatvec:
+    """The FP64 oracle's O-AIM system matvec (Eq. AEFIEoutJ as a sequence, NumPy/SciPy) on the
+    full workload: the 4x4 bar array, 17,832 RWG + 11,888 pulse unknowns, its AIM grid and
+    near-region pattern. The dense internal blocks and the near-region values are seeded random
+    numbers of the right sizes and sparsity: the matvec's cost does not depend on the values,
+    and forming the true ones takes the oracle tens of minutes."""
+
+    def __init__(self):
+        import numpy as np
+        import scipy.sparse as sp
+
+        from oracle import aim as oaim, operators as op
+        from oracle.rwg import from_mesh
+        from paper_2108_03991_gb300 import synth
+
+        mesh, grid, freq = synth.bar_array_config(0, 10e9)
+        rw = from_mesh(mesh)
+        A = oaim.Aim(rw, grid.origin, grid.h, grid.n, op.k0_of(freq))
+        rng = np.random.default_rng(7)
+        M, N = A.near_e
+        A.LNR_A = sp.csr_matrix((rng.standard_normal(M.size) + 0j, (M, N)), shape=(rw.ne, rw.ne))
+        T, S_ = A.near_t
+        A.LNR_P = sp.csr_matrix((rng.standard_normal(T.size) + 0j, (T, S_)), shape=(rw.nt, rw.nt))
+        sizes = [b - a for a, b in rw.obj_edge_ranges()]
+        blocks = synth.rand_blocks(sizes, 8)
+        self.S = op.SlimSystem(rw, freq, blocks, blocks, A.LA, A.LPhi)
+        self.x = synth.rand_cvec(self.S.n, 1)
+        self.desc = (f"the full workload ({rw.ne} RWG + {rw.nt} pulse unknowns, 16 objects); "
+                     "internal blocks and near-region values seeded random of the true sizes")
+
+    def run(self, seconds=0.0):
+        """Matvecs for at least `seconds` (at least one); returns seconds per matvec."""
+        n, t0 = 0, time.perf_counter()
+        while True:
+            self.S.matvec(self.x)
+            n += 1
+            if time.perf_counter() - t0 >= seconds:
+                return (time.perf_counter() - t0) / n
+
+
 def oracle_baseline(seconds=15.0):
-    """The FP64 oracle (O-AIM system matvec) on one bar of the workload, timed on the host
-    cores and scaled to the full workload by the ratio of dense internal-block elements
-    (the dominant cost of both)."""
-    import numpy as np
-
-    from oracle import aim as oaim, operators as op
-    from oracle.rwg import from_mesh
-    from paper_2108_03991_gb300 import synth
-
-    full = synth.bar_array(0)
-    Ls = synth.bar_array_lengths(0)
-    i = int(np.argmin(Ls))
-    L = float(Ls[i])
-    sample = synth.bar_mesh(1.0, 1.0, L, 0.5)
-    grid = synth.grid_box(sample, 0.5)
-    freq = 10e9
-    rw = from_mesh(sample)
-    A = oaim.Aim(rw, grid.origin, grid.h, grid.n, op.k0_of(freq)).build_near()
-    Zs, Ys = op.internal_blocks(rw, freq, sample.sigma)
-    S = op.SlimSystem(rw, freq, Zs, Ys, A.LA, A.LPhi)
-    x = synth.rand_cvec(S.n, 1)
-    S.matvec(x)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        S.matvec(x)
-        n += 1
-    dt = (time.perf_counter() - t0) / n
-    rwf = from_mesh(full)
-    full_cost = sum((b - a) ** 2 for a, b in rwf.obj_edge_ranges())
-    samp_cost = rw.ne ** 2
-    rate = 1.0 / dt * samp_cost / full_cost
+    """The oracle timed on the host cores on the full workload (about `seconds` of work)."""
+    om = OracleMatvec()
+    om.run()
+    dt = om.run(seconds)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one {L:g} um bar of the array ({rw.ne} edges): {1.0 / dt:.2f} matvecs/s, "
-                      f"scaled by the internal-block elements ({samp_cost} of {full_cost})"}
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{om.desc}: {dt:.3f} s per matvec over {seconds:g} s"}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: W untimed matvecs, then K timed steps of the same
+    workload within about a minute in all (one matvec per step at least)."""
     if rank != 0:
         return
-    steps = []
-    cb = None
-    for _ in range(max(1, args.steps)):
-        cb = oracle_baseline(seconds=max(5.0, 40.0 / max(1, args.steps)))
-        steps.append(cb["value"])
-    v = sum(steps) / len(steps)
-    cb["value"] = v
+    om = OracleMatvec()
+    for _ in range(max(0, args.warmup)):
+        om.run()
+    per_step = 60.0 / max(1, args.steps)
+    t0 = time.perf_counter()
+    dts = [om.run(per_step) for _ in range(max(1, args.steps))]
+    v = 1.0 / (sum(dts) / len(dts))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"{om.desc}; {len(dts)} steps in {time.perf_counter() - t0:.1f} s"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
@@ -153,7 +188,7 @@ def run_reference(args, rank, world):
 
 # DRAM bytes (read + write) per launch of the block GEMV from the ncu capture summarised in
 # profiles/gemv_internal_bar_array.md; valid only for the launch shape captured there
-PROFILED_GEMV = {"kind": 0, "ctas": 912, "split": 1, "unroll": 4, "bytes": 205.4e6}
+PROFILED_GEMV = {"kind": 1, "ctas": 912, "split": 0, "unroll": 4, "bytes": 207.9e6}
 
 
 def gemv_traffic(ctx):
@@ -411,10 +446,7 @@ def main():
         ev1.record(s)
         torch.cuda.synchronize()
         e2e_ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms, e2e_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
 
     solve = None
     if not args.no_solve and rank == 0:
@@ -466,13 +498,14 @@ def main():
 
     if rank == 0:
         hbm, src = peaks()
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         ZY = ctx.zy_bytes_c32 // 2  # bytes of Z (or Y) in FP32, one GEMV launch
         gemv_bytes = ZY + 2 * 8 * ctx.ne
         achieved = gemv_bytes / (gemv_ms * 1e-3) / 1e9
         cpu = None
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
-        value = world * 1e3 / ms
+        value = replicas_value(ms, world)
         # per system matvec: 2 GEMV (each with a y-initialising launch in the stream form),
         # 2 projections, 2 x 3 FFT passes, 2 row kernels
         launches_per_step = 10 + 2 * (2 if ctx.gemv_kind == 3 else 1)
@@ -490,13 +523,16 @@ def main():
                          "frac": achieved / hbm, "peak_source": src, "traffic": gemv_traffic(ctx),
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/gemv_internal_bar_array.md)",
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
-                         "launch": {"ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split,
+                         "launch": {"kind": ["row plan", "flat", "staged", "stream"][ctx.gemv_kind],
+                                    "shape": [ctx.gemv_kind, ctx.gemv_ctas // nsm,
+                                              max(ctx.gemv_split, 1), ctx.gemv_unroll],
+                                    "ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split,
                                     "loads_in_flight": ctx.gemv_unroll,
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
                                     "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
                                                        for r in ctx.gemv_tune_table()]}},
-            "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * ctx.n,
-                    "d2h_bytes_per_step": 8 * ctx.n},
+            "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "solve": solve,

@@ -238,10 +238,6 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
     status = BEM_OK;
     est = truer = 0;
   }
-  // With FP32 matvecs the Arnoldi estimate drifts from the true FP64 residual by the FP32
-  // rounding of the products; stopping the inner iteration at half the tolerance makes the
-  // true residual check after the cycle pass more often, saving a cycle and an FP64 matvec.
-  const double inner_tol = o->prec_mode == BEM_C32 ? 0.5 * o->tol : o->tol;
   bool fresh = bnorm == 0;
   while (status != BEM_OK && iters < o->max_iter) {
     // r = b - A x (FP64 matvec), beta = ||r||
@@ -298,7 +294,7 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
       BEM_CUDA(cudaStreamSynchronize(s));
       ++iters;
       est = res / bnorm;
-      if (est <= inner_tol) { ++k; break; }
+      if (est <= o->tol) { ++k; break; }
       if (o->time_limit_s > 0 && std::chrono::duration<double>(clk::now() - t0).count() > o->time_limit_s) { ++k; break; }
     }
     // x += V[:k] y, y = R^{-1} g
