@@ -97,7 +97,8 @@ int smooth_length(int need);  // smallest length >= need whose factors are 2, 3,
 template <typename R> struct PrecBuf {
   typedef typename C2<R>::T V;
   V* Z = nullptr;      // packed row-major blocks (ld_i = round_up(n_i, 4))
-  V* Y = nullptr;
+  V* Y = nullptr;      // Y_eq blocks, FP64 only (export and preconditioner set-up)
+  V* C = nullptr;      // C_i = Y_i Z_i (Eq. EFIEeqYZ: h_eq = Y_eq Z h), same layout as Z
   R* WA = nullptr;     // [ne][3][27] projection weights of RWG functions
   R* WP = nullptr;     // [nt][27] projection weights of pulses
   R* WAT = nullptr;    // [nnzPe][3] the same weights in grid-node-major (CSR) order
@@ -231,6 +232,7 @@ struct aim_ctx {
   std::vector<bem::GemvTask> tasks;
   bem::GemvPlan gplan;    // FP32 products (autotuned; may use bulk-copy staging)
   bem::GemvPlan gplan64;  // FP64 products
+  bem::GemvPlan gbg32, gbg64;  // e = Z h beside the AIM chain in the system matvec (few CTAs)
   bem::GemvPlan gplan_auto;    // the autotuner's FP32 choice
   bem::GemvPlan gplan_alt[2];  // best plain and best staged FP32 plans (ncta = 0: none)
   float tune_ms[2] = {0, 0};  // autotuner: best plain, best staged candidate (5 launches, ms)
@@ -264,8 +266,8 @@ struct aim_ctx {
   std::vector<void*> allocs;   // every device allocation, freed by aim_destroy
   void* geo_store = nullptr;   // device geometry descriptor (set-up kernels, right-hand sides)
   // streams for the two-branch matvec and its CUDA-graph capture
-  cudaStream_t cap = nullptr, side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr, zside = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr;
   struct GKey {
     int which, prec;
     const void* x;

@@ -626,24 +626,30 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x, nt,
                                           nx, ny, y);
   } else if (which == AIM_OP_SYSTEM) {
-    // Two branches: the charge branch p = L^Phi q does not depend on the internal problem and
-    // runs on the side stream while the GEMVs stream Z and Y_eq.
+    // Three branches. With C = Y_eq Z formed at set-up (Eq. EFIEeqYZ), j = h - C h and e = Z h
+    // are independent: the main stream runs j and its AIM chain (projection, convolution,
+    // rows); e = Z h streams beside it with few CTAs (it is needed only by the last kernel,
+    // for I_x e); the charge branch p = L^Phi q runs on the side stream.
     const V* h = x;
     const V* q = x + ne;
     V* sq = b.sigma + 3 * ng;
     BEM_CUDA(cudaEventRecord(c->ev_fork, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
                                                 nt, nx, ny, b.p);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
-    BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
-    BEM_TRY(run_gemv_plan<R>(gp, b.Y, b.e, b.j, 1, ne, h, s));
+    const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
+    BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
+    BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
+    BEM_CUDA(cudaEventRecord(c->ev_z, c->zside));
     project_e<R>(c, b.WAT, b.j, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+    BEM_CUDA(cudaStreamWaitEvent(s, c->ev_z, 0));
     k_rows_e<R><<<nb(ne + nt, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
                                                b.LA, b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p,
                                                ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q);
@@ -660,8 +666,10 @@ template int matvec<double>(aim_ctx*, int, const void*, void*, cudaStream_t);
 int init_streams(aim_ctx* c) {
   BEM_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   BEM_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  BEM_CUDA(cudaStreamCreateWithFlags(&c->zside, cudaStreamNonBlocking));
   BEM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   BEM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  BEM_CUDA(cudaEventCreateWithFlags(&c->ev_z, cudaEventDisableTiming));
   return BEM_OK;
 }
 
@@ -670,7 +678,9 @@ void release_streams(aim_ctx* c) {
   c->graphs.clear();
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_z) cudaEventDestroy(c->ev_z);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->zside) cudaStreamDestroy(c->zside);
   if (c->cap) cudaStreamDestroy(c->cap);
   c->ev_fork = c->ev_join = nullptr;
   c->side = c->cap = nullptr;
@@ -777,7 +787,7 @@ int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStr
   PrecBuf<R>& b = buf<R>(c);
   const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
   BEM_TRY(run_gemv_plan<R>(gp, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
-  if (heqv) BEM_TRY(run_gemv_plan<R>(gp, b.Y, (const V*)ev, (V*)heqv, nrhs, c->ne, nullptr, s));
+  if (heqv) BEM_TRY(run_gemv_plan<R>(gp, b.C, (const V*)hv, (V*)heqv, nrhs, c->ne, nullptr, s));
   return BEM_OK;
 }
 template int internal<float>(aim_ctx*, const void*, void*, void*, int, cudaStream_t);

@@ -282,7 +282,12 @@ __global__ void k_store_block(const double2* X, int n, int ld, double2 alpha, do
   double2 v = make_double2(0, 0);
   if (col < n) v = cmul(alpha, X[r + (int64_t)col * n]);
   Z64[idx] = v;
-  Z32[idx] = make_float2((float)v.x, (float)v.y);
+  if (Z32) Z32[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void k_round32(const double2* __restrict__ a, float2* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
 // Near region of L^A: exact entry minus the grid's own contribution
@@ -772,8 +777,10 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
   c->zelems = off;
   BEM_TRY(dalloc_t(c, &c->f64.Z, off));
   BEM_TRY(dalloc_t(c, &c->f64.Y, off));
+  BEM_TRY(dalloc_t(c, &c->f64.C, off));
   BEM_TRY(dalloc_t(c, &c->f32.Z, off));
-  BEM_TRY(dalloc_t(c, &c->f32.Y, off));
+  BEM_TRY(dalloc_t(c, &c->f32.C, off));
+  BEM_CUDA(cudaMemset(c->f64.C, 0, off * sizeof(double2)));
   double2 *L = nullptr, *B = nullptr;
   int64_t* ipiv = nullptr;
   int* dinfo = nullptr;
@@ -814,9 +821,35 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
       double2 al = make_double2(alpha.real(), alpha.imag());
       k_store_block<<<nblk((int64_t)n * c->zld[i], 256), 256>>>(
           B, n, c->zld[i], al, (pass == 0 ? c->f64.Z : c->f64.Y) + c->zoff[i],
-          (pass == 0 ? c->f32.Z : c->f32.Y) + c->zoff[i]);
+          pass == 0 ? c->f32.Z + c->zoff[i] : nullptr);
       e = cudaGetLastError();
       if (e != cudaSuccess) { set_error("k_store_block: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; }
+    }
+  }
+  // C_i = Y_i Z_i (row-major blocks of leading dimension ld: in cuBLAS's column-major view
+  // they are the transposes, so C^T = Z^T Y^T is one plain product), in FP64, then rounded
+  if (rc == BEM_OK) {
+    cublasHandle_t bh = nullptr;
+    if (cublasCreate(&bh) != CUBLAS_STATUS_SUCCESS) {
+      set_error("cublasCreate failed");
+      rc = BEM_ECUDA;
+    }
+    const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+    for (int i = 0; i < nobj && rc == BEM_OK; ++i) {
+      const int n = c->e1[i] - c->e0[i], ld = c->zld[i];
+      const int64_t o = c->zoff[i];
+      if (cublasZgemm(bh, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one,
+                      (const cuDoubleComplex*)(c->f64.Z + o), ld, (const cuDoubleComplex*)(c->f64.Y + o),
+                      ld, &zero, (cuDoubleComplex*)(c->f64.C + o), ld) != CUBLAS_STATUS_SUCCESS) {
+        set_error("cublasZgemm (Y Z) failed");
+        rc = BEM_ECUDA;
+      }
+    }
+    if (bh) cublasDestroy(bh);
+    if (rc == BEM_OK) {
+      k_round32<<<1216, 256>>>(c->f64.C, c->f32.C, c->zelems);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) { set_error("k_round32: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; }
     }
   }
   cudaDeviceSynchronize();
@@ -993,6 +1026,13 @@ int setup_device(aim_ctx* c) {
     BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan, &c->gplan64, c->tune_ms,
                           c->gplan_alt));
     c->gplan_auto = c->gplan;
+    // e = Z h runs beside the AIM chain of j in the system matvec: a launch of few CTAs (2 per
+    // SM, 8 loads in flight per lane) that leaves most of every SM to the chain's kernels
+    int* derr = nullptr;
+    BEM_TRY(dalloc_t(c, &derr, 1));
+    BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
+    BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{1, 2, 1, 8}, nsm, n, c->zoff, c->zld, derr, &c->gbg32));
+    c->gbg64 = c->gbg32;  // a row plan holds no precision
   }
   // workspaces
   const size_t P = (size_t)c->gp[0] * c->gp[1] * c->gp[2];
