@@ -530,7 +530,9 @@ def main():
                                     "loads_in_flight": ctx.gemv_unroll,
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
                                     "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
-                                                       for r in ctx.gemv_tune_table()]}},
+                                                       for r in ctx.gemv_tune_table() if r[0] < 4],
+                                    "matvec_schedules": [[int(v) for v in r[1:3]] + [float(r[4])]
+                                                         for r in ctx.gemv_tune_table() if r[0] == 4]}},
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n},
             "gpu_launches": launches_per_step * args.steps,

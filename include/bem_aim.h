@@ -167,9 +167,11 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *   what 5: pulse projection weights, double [N_T][27]
  *   what 6: stencil anchors, int32 [N_E + N_T][3]
  *   what 7: edge table, int32 [N_E][6] = (a, b, T+, T-, v+, v-)
- *   what 8: the set-up GEMV autotuner's table, float [candidates][5] = (kind: 0 row plan,
+ *   what 8: the set-up autotuners' table, float [candidates][5] = (kind: 0 row plan,
  *           1 flat, 2 bulk-copy staged, 3 stream; CTAs per SM; column parts per row; loads in flight
- *           per lane; ns per launch, or -1 when the candidate was rejected or not applicable)
+ *           per lane; ns per launch, or -1 when the candidate was rejected or not applicable),
+ *           then the system-matvec schedules (kind 4; CTAs per SM of the e = Z h launch that runs
+ *           beside the AIM chain; 0 = it starts with j's GEMV, 1 = after it; 8; ns per matvec)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
 

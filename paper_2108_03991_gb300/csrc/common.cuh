@@ -267,7 +267,8 @@ struct aim_ctx {
   void* geo_store = nullptr;   // device geometry descriptor (set-up kernels, right-hand sides)
   // streams for the two-branch matvec and its CUDA-graph capture
   cudaStream_t cap = nullptr, side = nullptr, zside = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr, ev_c = nullptr;
+  bool z_after = false;  // e = Z h starts when j = h - C h is out (else with it)
   struct GKey {
     int which, prec;
     const void* x;
@@ -359,6 +360,7 @@ template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cuda
 void free_geo_store(aim_ctx* c);
 void free_far_geo(aim_ctx* c);
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);
+int tune_matvec_schedule(aim_ctx* c);
 double k0_of(double f);
 // solver (gmres.cu)
 int gmres_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,

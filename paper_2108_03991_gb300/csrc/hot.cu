@@ -644,6 +644,10 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
     BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
+    if (c->z_after) {  // e = Z h once j is out, beside the AIM chain only
+      BEM_CUDA(cudaEventRecord(c->ev_c, s));
+      BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_c, 0));
+    }
     BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
     BEM_CUDA(cudaEventRecord(c->ev_z, c->zside));
     project_e<R>(c, b.WAT, b.j, b.sigma, s);
@@ -670,6 +674,7 @@ int init_streams(aim_ctx* c) {
   BEM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   BEM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   BEM_CUDA(cudaEventCreateWithFlags(&c->ev_z, cudaEventDisableTiming));
+  BEM_CUDA(cudaEventCreateWithFlags(&c->ev_c, cudaEventDisableTiming));
   return BEM_OK;
 }
 
@@ -679,6 +684,7 @@ void release_streams(aim_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_z) cudaEventDestroy(c->ev_z);
+  if (c->ev_c) cudaEventDestroy(c->ev_c);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->zside) cudaStreamDestroy(c->zside);
   if (c->cap) cudaStreamDestroy(c->cap);

@@ -684,6 +684,66 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
   return BEM_OK;
 }
 
+// Schedule autotuner of the system matvec: e = Z h runs beside the AIM chain of j with a
+// launch of few CTAs. Time the captured FP32 graph for each (CTAs per SM of that launch,
+// start with j's GEMV or after it) with CUDA events and keep the fastest; the FP64 matvec
+// uses the same choice. tune_table gains rows (kind 4, CTAs per SM, start, 8, ns per matvec).
+int tune_matvec_schedule(aim_ctx* c) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<int32_t> n(c->nobj);
+  for (int i = 0; i < c->nobj; ++i) n[i] = c->e1[i] - c->e0[i];
+  int* derr = nullptr;
+  BEM_TRY(dalloc_t(c, &derr, 1));
+  BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
+  const int64_t N = (int64_t)c->ne + c->nt;
+  std::vector<float2> xh(N);
+  for (int64_t i = 0; i < N; ++i) xh[i] = make_float2((float)std::sin(0.7 * i), (float)std::cos(0.3 * i));
+  BEM_CUDA(cudaMemcpy(c->f32.xin, xh.data(), N * sizeof(float2), cudaMemcpyHostToDevice));
+  cudaStream_t s = nullptr;
+  BEM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_cps = 2;
+  bool best_after = false;
+  int rc = BEM_OK;
+  for (int cps : {1, 2, 3}) {
+    GemvPlan p;
+    if ((rc = make_gemv_plan(c, nullptr, GemvCand{1, cps, 1, 8}, nsm, n, c->zoff, c->zld, derr, &p)) != BEM_OK) break;
+    for (bool after : {false, true}) {
+      c->gbg32 = c->gbg64 = p;
+      c->z_after = after;
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+      c->graphs.clear();
+      for (int w = 0; w < 3 && rc == BEM_OK; ++w) rc = matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s);
+      if (rc != BEM_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 20 && rc == BEM_OK; ++r) rc = matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->tune_table.insert(c->tune_table.end(), {4.f, (float)cps, after ? 1.f : 0.f, 8.f, ms * 1e6f / 20.f});
+      if (ms < best) { best = ms; best_cps = cps; best_after = after; }
+    }
+    if (rc != BEM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  if (rc != BEM_OK) return rc;
+  BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{1, best_cps, 1, 8}, nsm, n, c->zoff, c->zld, derr, &c->gbg32));
+  c->gbg64 = c->gbg32;
+  c->z_after = best_after;
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
 // ---------------------------------------------------------------------------------------
 // orchestration
 // ---------------------------------------------------------------------------------------
@@ -1056,6 +1116,7 @@ int setup_device(aim_ctx* c) {
   BEM_TRY(init_streams(c));
   BEM_CUDA(cudaDeviceSynchronize());
   c->geo_store = new DGeo(g);
+  BEM_TRY(tune_matvec_schedule(c));
   return BEM_OK;
 }
 
