@@ -523,14 +523,15 @@ def main():
                          "frac": achieved / hbm, "peak_source": src, "traffic": gemv_traffic(ctx),
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/gemv_internal_bar_array.md)",
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
-                         "launch": {"kind": ["row plan", "flat", "staged", "stream"][ctx.gemv_kind],
+                         "launch": {"kind": {0: "row plan", 1: "flat", 2: "staged", 3: "stream",
+                                             5: "Part_Schedule task list"}[ctx.gemv_kind],
                                     "shape": [ctx.gemv_kind, ctx.gemv_ctas // nsm,
                                               max(ctx.gemv_split, 1), ctx.gemv_unroll],
                                     "ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split,
                                     "loads_in_flight": ctx.gemv_unroll,
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
                                     "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
-                                                       for r in ctx.gemv_tune_table() if r[0] < 4],
+                                                       for r in ctx.gemv_tune_table() if r[0] != 4],
                                     "matvec_schedules": [[int(v) for v in r[1:3]] + [float(r[4])]
                                                          for r in ctx.gemv_tune_table() if r[0] == 4]}},
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,

@@ -100,7 +100,8 @@ const char* bem_last_error(void);
  * correctly), [18]=autotuner candidates rejected (product differed from the first candidate's
  * beyond FP32 rounding, or a bounded wait timed out; set-up products include the preconditioner
  * blocks once they are built), [19]=kind of the chosen FP32 launch (0 row plan, 1 flat, 2
- * bulk-copy staged, 3 stream). Writes min(n, 20) entries. */
+ * bulk-copy staged, 3 stream, 5 the modified Part_Schedule's task list). Writes min(n, 20)
+ * entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the
@@ -114,7 +115,9 @@ int aim_gemv_select(aim_ctx* ctx, int kind);
 /* Set the FP32 block-GEMV launch explicitly (reproducible timing or profiling; the autotuner's
  * choice otherwise): kind 0 row plan (ctas_per_sm 4 or 6, split 1, 2 or 4 column parts per
  * row, unroll 4, or 8 with 4 CTAs/SM), 1 flat or 3 stream ((6, unroll 4) or (4, unroll 8);
- * split ignored), 2 bulk-copy staged (ctas_per_sm 1 or 2; split, unroll ignored). The launch's
+ * split ignored), 2 bulk-copy staged (ctas_per_sm 1 or 2; split, unroll ignored), 5 the task
+ * list of the modified Part_Schedule (Alg. 2) over 4 CTA slots per SM, one CTA per task of at
+ * most 16 rows (other arguments ignored). The launch's
  * product of a fixed vector is checked against the reference launch before it is used. Waits
  * for the device to be idle and drops the captured matvec graphs. Errors: BEM_EINVAL for an
  * unsupported shape, BEM_ECUDA if the check fails. aim_gemv_select(ctx, 0) restores the
@@ -168,7 +171,7 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *   what 6: stencil anchors, int32 [N_E + N_T][3]
  *   what 7: edge table, int32 [N_E][6] = (a, b, T+, T-, v+, v-)
  *   what 8: the set-up autotuners' table, float [candidates][5] = (kind: 0 row plan,
- *           1 flat, 2 bulk-copy staged, 3 stream; CTAs per SM; column parts per row; loads in flight
+ *           1 flat, 2 bulk-copy staged, 3 stream, 5 Part_Schedule task list; CTAs per SM; column parts per row; loads in flight
  *           per lane; ns per launch, or -1 when the candidate was rejected or not applicable),
  *           then the system-matvec schedules (kind 4; CTAs per SM of the e = Z h launch that runs
  *           beside the AIM chain; 0 = it starts with j's GEMV, 1 = after it; 8; ns per matvec)

@@ -167,6 +167,8 @@ struct GemvPlan {
   int unroll = 4;              // 16-byte loads in flight per lane (4 or 8), likewise
   int flat = 0;                // flat form: rows in chunks (stages, descs, cta_stage as chunks)
   int stream = 0;              // stream form: equal vector shares per warp, atomic row sums
+  GemvTask* tasks = nullptr;   // task-list form: the modified Part_Schedule's row panels
+  int ntasks = 0;              //   (one CTA per task of <= 16 rows), when non-zero
   int32_t* wrow = nullptr;     // device [warps]: row holding each warp's first vector
   int64_t nquad = 0;           // whole block storage in units of 4 complex elements
   double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
@@ -229,7 +231,6 @@ struct aim_ctx {
   std::vector<int64_t> zoff;                       // element offset of block i
   std::vector<int32_t> zld;
   int64_t zelems = 0;
-  std::vector<bem::GemvTask> tasks;
   bem::GemvPlan gplan;    // FP32 products (autotuned; may use bulk-copy staging)
   bem::GemvPlan gplan64;  // FP64 products
   bem::GemvPlan gbg32, gbg64;  // e = Z h beside the AIM chain in the system matvec (few CTAs)
@@ -259,8 +260,6 @@ struct aim_ctx {
   int32_t* d_ixcol = nullptr;  // [ne][4]
   int32_t* d_et = nullptr;     // [ne][2]
   int32_t* d_tedge = nullptr;  // [nt][3]
-  bem::GemvTask* d_tasks = nullptr;
-  int ntasks = 0;
   bem::PrecBuf<float> f32;
   bem::PrecBuf<double> f64;
   std::vector<void*> allocs;   // every device allocation, freed by aim_destroy

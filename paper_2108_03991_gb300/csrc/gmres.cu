@@ -12,46 +12,26 @@ namespace bem {
 
 static constexpr int kChunks = 304;  // 2 x 152 SMs
 
-// partial[j][block] = sum over the block's slice of conj(V_j) w, for nv vectors taken eight at
-// a time (w read once per group, one block reduction per group)
-constexpr int kDotGroup = 8;
-
-__global__ void __launch_bounds__(256) k_dots(const double2* __restrict__ V, int64_t ldv, int nv,
-                                              const double2* __restrict__ w, int64_t n,
-                                              double2* __restrict__ partial) {
-  __shared__ double2 red[8][kDotGroup];
+__global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int nv,
+                       const double2* __restrict__ w, int64_t n, double2* __restrict__ partial) {
+  __shared__ double2 red[8];
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j0 = 0; j0 < nv; j0 += kDotGroup) {
-    const int g = min(kDotGroup, nv - j0);
-    double2 acc[kDotGroup];
-#pragma unroll
-    for (int q = 0; q < kDotGroup; ++q) acc[q] = make_double2(0, 0);
+  for (int j = 0; j < nv; ++j) {
+    double2 acc = make_double2(0, 0);
+    const double2* v = V + j * ldv;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const double2 b = w[i];
-#pragma unroll
-      for (int q = 0; q < kDotGroup; ++q) {
-        if (q < g) {
-          const double2 a = V[(int64_t)(j0 + q) * ldv + i];
-          acc[q].x += a.x * b.x + a.y * b.y;  // conj(a) b
-          acc[q].y += a.x * b.y - a.y * b.x;
-        }
-      }
+      double2 a = v[i], b = w[i];
+      acc.x += a.x * b.x + a.y * b.y;  // conj(a) b
+      acc.y += a.x * b.y - a.y * b.x;
     }
-#pragma unroll
-    for (int q = 0; q < kDotGroup; ++q) {
-      const double2 t = warp_sum(acc[q]);
-      if (lane == 0) red[warp][q] = t;
-    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x < g) {
+    if (threadIdx.x == 0) {
       double2 s = make_double2(0, 0);
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        s.x += red[k][threadIdx.x].x;
-        s.y += red[k][threadIdx.x].y;
-      }
-      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { s.x += red[k].x; s.y += red[k].y; }
+      partial[(int64_t)j * gridDim.x + blockIdx.x] = s;
     }
     __syncthreads();
   }

@@ -341,6 +341,7 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
                   cudaStream_t s) {
   if (p.ncta == 0 || p.nrows == 0) return BEM_OK;
   if (p.tma) return run_gemv_tma<R>(p, A, x, y, nrhs, vstride, hsub, s);
+  if (p.ntasks > 0) return run_gemv<R>(p.tasks, p.ntasks, A, x, y, nrhs, vstride, hsub, s);
   if (p.stream) {
     k_gemv_init<<<(unsigned)((p.nrows * (int64_t)nrhs + 255) / 256), 256, 0, s>>>(y, hsub, (int64_t)p.nrows,
                                                                                nrhs, vstride);

@@ -447,7 +447,7 @@ struct TunePlan {  // a candidate plan held in temporary device memory
 // receives the time of 5 launches of those two.
 namespace {
 struct GemvCand {
-  int kind;   // 0 row plan, 1 flat, 2 staged, 3 stream
+  int kind;   // 0 row plan, 1 flat, 2 staged, 3 stream, 5 Part_Schedule task list
   int cps;    // CTAs per SM
   int split;  // column parts per row (row plan)
   int unroll; // loads in flight per lane (row plan, flat)
@@ -464,6 +464,22 @@ static int make_gemv_plan(aim_ctx* c, TunePlan* t, const GemvCand& g, int nsm,
   std::vector<TmaStage> st;
   std::vector<TmaDesc> dsc;
   GemvPlan p;
+  if (g.kind == 5) {
+    // the paper's schedule: each block cut into the modified Part_Schedule's P_i row panels
+    // (P = 4 CTA slots per SM, Alg. 2), the panels into tasks of <= 16 rows, one CTA each
+    std::vector<int32_t> xo(n.size());
+    for (size_t i = 0, acc = 0; i < n.size(); acc += n[i], ++i) xo[i] = (int32_t)acc;
+    std::vector<GemvTask> tasks;
+    build_gemv_tasks(n, off, xo, ld, nsm, &tasks);
+    if (t) BEM_TRY(t->put(&p.tasks, tasks));
+    else BEM_TRY(upload(c, &p.tasks, tasks.data(), tasks.size()));
+    p.ntasks = (int)tasks.size();
+    p.ncta = p.ntasks;
+    p.nrows = 0;
+    for (int v : n) p.nrows += v;
+    *out = p;
+    return BEM_OK;
+  }
   build_gemv_plan(n, off, ld, nsm * g.cps, &rows, &segs, &cseg, &p.cmax_over_ideal);
   const int stage_bytes = g.cps == 1 ? 40 * 1024 : 24 * 1024;
   if (g.kind == 1 || g.kind == 2) {
@@ -538,6 +554,7 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
   cands.push_back({1, 4, 1, 8});
   cands.push_back({3, 6, 1, 4});
   cands.push_back({3, 4, 1, 8});
+  cands.push_back({5, 4, 1, 4});
   cands.push_back({2, 1, 1, 4});
   cands.push_back({2, 2, 1, 2});
   int* derr = nullptr;
@@ -634,7 +651,7 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
       (kind == 0 && (cps == 4 || cps == 6) && (split == 1 || split == 2 || split == 4) &&
        (unroll == 4 || (unroll == 8 && cps == 4))) ||
       ((kind == 1 || kind == 3) && ((cps == 6 && unroll == 4) || (cps == 4 && unroll == 8))) ||
-      (kind == 2 && (cps == 1 || cps == 2));
+      (kind == 2 && (cps == 1 || cps == 2)) || kind == 5;
   if (!ok_shape) {
     set_error("aim_gemv_plan: unsupported shape (kind %d, %d CTAs/SM, split %d, unroll %d)", kind,
               cps, split, unroll);
@@ -649,7 +666,8 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
   BEM_TRY(dalloc_t(c, &derr, 1));
   BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
   GemvPlan p;
-  const GemvCand g{kind, cps, kind == 0 ? split : 1, kind == 2 ? (cps == 1 ? 4 : 2) : unroll};
+  const GemvCand g{kind, kind == 5 ? 4 : cps, kind == 0 ? split : 1,
+                   kind == 2 ? (cps == 1 ? 4 : 2) : unroll};
   const int r = make_gemv_plan(c, nullptr, g, nsm, n, c->zoff, c->zld, derr, &p);
   if (r == 1) {
     set_error("aim_gemv_plan: a row does not fit a shared-memory stage");
@@ -1076,11 +1094,8 @@ int setup_device(aim_ctx* c) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    std::vector<int32_t> n(c->nobj), xo(c->nobj);
-    for (int i = 0; i < c->nobj; ++i) { n[i] = c->e1[i] - c->e0[i]; xo[i] = c->e0[i]; }
-    build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, &c->tasks);
-    c->ntasks = (int)c->tasks.size();
-    BEM_TRY(upload(c, &c->d_tasks, c->tasks.data(), c->tasks.size()));
+    std::vector<int32_t> n(c->nobj);
+    for (int i = 0; i < c->nobj; ++i) n[i] = c->e1[i] - c->e0[i];
     // persistent, byte-balanced plan with the autotuned launch shape
     BEM_TRY(tma_init_attrs());
     BEM_TRY(autotune_gemv(c, n, c->zoff, c->zld, c->f32.Z, &c->gplan, &c->gplan64, c->tune_ms,

@@ -166,10 +166,11 @@ def test_gemv_autotuner_candidates(prob):
 
 
 @pytest.mark.parametrize("kind", [1, 2, (0, 6, 2, 4), (0, 4, 4, 8), (1, 4, 1, 8), (3, 6, 1, 4),
-                                  (3, 4, 1, 8), (2, 2, 1, 4)])
+                                  (3, 4, 1, 8), (2, 2, 1, 4), (5, 4, 1, 4)])
 def test_gemv_kinds_match_oracle(prob, kind):
     """Every FP32 GEMV form, forced in turn (the autotuner's best plain and best staged, then
-    explicit row-plan, flat, stream and staged launches), against the FP64 oracle: internal
+    explicit row-plan, flat, stream, staged and Part_Schedule task-list launches), against the
+    FP64 oracle: internal
     products with 3 right-hand sides (the multi-RHS and h - Y e forms) and the system matvec."""
     ctx, S = prob["ctx"], prob["S"]
     if isinstance(kind, tuple):
