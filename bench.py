@@ -188,14 +188,14 @@ def run_reference(args, rank, world):
 
 # DRAM bytes (read + write) per launch of the block GEMV from the ncu capture summarised in
 # profiles/gemv_internal_bar_array.md; valid only for the launch shape captured there
-PROFILED_GEMV = {"kind": 1, "ctas": 912, "split": 0, "unroll": 4, "bytes": 207.9e6}
+# DRAM bytes per launch (read + write) of the GEMV shapes captured with ncu on this workload,
+# keyed by (kind, CTAs per SM, split, loads in flight) as aim_info reports them
+PROFILED_GEMV = {(1, 6, 0, 4): 207.9e6, (5, 4, 2, 4): 204.9e6, (5, 16, 1, 4): 208.3e6}
 
 
 def gemv_traffic(ctx):
-    p = PROFILED_GEMV
-    same = (ctx.gemv_kind == p["kind"] and ctx.gemv_ctas == p["ctas"]
-            and ctx.gemv_split == p["split"] and ctx.gemv_unroll == p["unroll"])
-    return int(p["bytes"]) if same else None
+    b = PROFILED_GEMV.get((ctx.gemv_kind, ctx.gemv_cps, ctx.gemv_split, ctx.gemv_unroll))
+    return int(b) if b else None
 
 
 def ncu_case(args):
@@ -506,9 +506,9 @@ def main():
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
         value = replicas_value(ms, world)
-        # per system matvec: 2 GEMV (each with a y-initialising launch in the stream form),
-        # 2 projections, 2 x 3 FFT passes, 2 row kernels
-        launches_per_step = 10 + 2 * (2 if ctx.gemv_kind == 3 else 1)
+        # per system matvec: the GEMV of j (with a y-initialising launch in the stream form),
+        # the GEMV of e, 2 projections, 2 x 3 FFT passes, the near region of j, 2 row kernels
+        launches_per_step = 11 + (2 if ctx.gemv_kind == 3 else 1) + 1
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -524,15 +524,19 @@ def main():
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/gemv_internal_bar_array.md)",
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
                          "launch": {"kind": {0: "row plan", 1: "flat", 2: "staged", 3: "stream",
-                                             5: "Part_Schedule task list"}[ctx.gemv_kind],
-                                    "shape": [ctx.gemv_kind, ctx.gemv_ctas // nsm,
+                                             5: "Part_Schedule task list",
+                                             6: "Part_Schedule tasks, persistent CTAs"}[ctx.gemv_kind],
+                                    "shape": [ctx.gemv_kind, ctx.gemv_cps,
                                               max(ctx.gemv_split, 1), ctx.gemv_unroll],
-                                    "ctas": ctx.gemv_ctas, "parts_per_row": ctx.gemv_split,
+                                    "ctas": ctx.gemv_ctas,
+                                    "parts_per_row": 0 if ctx.gemv_kind >= 5 else ctx.gemv_split,
+                                    "rows_per_task": ((4 if ctx.gemv_cps == 16 else 8) * ctx.gemv_split
+                                                      if ctx.gemv_kind >= 5 else None),
                                     "loads_in_flight": ctx.gemv_unroll,
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
                                     "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
                                                        for r in ctx.gemv_tune_table() if r[0] != 4],
-                                    "matvec_schedules": [[int(v) for v in r[1:3]] + [float(r[4])]
+                                    "matvec_schedules": [[int(v) for v in r[1:4]] + [float(r[4])]
                                                          for r in ctx.gemv_tune_table() if r[0] == 4]}},
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n},

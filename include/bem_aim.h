@@ -92,16 +92,17 @@ const char* bem_last_error(void);
 
 /* Sizes: info[0]=N_E, [1]=N_T, [2]=nobj, [3..5]=grid n, [6..8]=padded FFT lengths,
  * [9]=nnz(L^A_NR), [10]=nnz(L^Phi_NR), [11]=bytes of Z and Y (C32), [12]=max n_i,
- * [13]=CTAs of the block GEMV launch, [14]=column parts per row of the row-plan kernel, 0 for
- * the flat and stream kernels, or minus the number of shared-memory stages when the bulk-copy-staged kernel
- * was chosen, [15]=16-byte loads in flight
+ * [13]=CTAs of the block GEMV launch, [14]=column parts per row of the row-plan kernel, rows
+ * per task / 8 of the task list, 0 for the flat and stream kernels, or minus the number of
+ * shared-memory stages when the bulk-copy-staged kernel was chosen, [15]=16-byte loads in flight
  * per lane (0 for the staged kernel) (all chosen by the set-up autotuner), [16]=ns per launch of
  * the best plain candidate, [17]=ns per launch of the best staged candidate (-1 if none ran
  * correctly), [18]=autotuner candidates rejected (product differed from the first candidate's
  * beyond FP32 rounding, or a bounded wait timed out; set-up products include the preconditioner
  * blocks once they are built), [19]=kind of the chosen FP32 launch (0 row plan, 1 flat, 2
- * bulk-copy staged, 3 stream, 5 the modified Part_Schedule's task list). Writes min(n, 20)
- * entries. */
+ * bulk-copy staged, 3 stream, 5 the modified Part_Schedule's task list, 6 the same tasks taken
+ * in turn by persistent CTAs), [20]=CTAs per SM of that launch's shape (for the task list:
+ * 4, 8 or 16, the variant). Writes min(n, 21) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the
@@ -117,7 +118,8 @@ int aim_gemv_select(aim_ctx* ctx, int kind);
  * row, unroll 4, or 8 with 4 CTAs/SM), 1 flat or 3 stream ((6, unroll 4) or (4, unroll 8);
  * split ignored), 2 bulk-copy staged (ctas_per_sm 1 or 2; split, unroll ignored), 5 the task
  * list of the modified Part_Schedule (Alg. 2) over 4 CTA slots per SM, one CTA per task of at
- * most 16 rows (other arguments ignored). The launch's
+ * most 8 * split rows (split 1, 2 or 4; unroll 4 or 8; ctas_per_sm ignored), 6 the same tasks
+ * taken in turn from a counter by ctas_per_sm (1-8) persistent CTAs per SM. The launch's
  * product of a fixed vector is checked against the reference launch before it is used. Waits
  * for the device to be idle and drops the captured matvec graphs. Errors: BEM_EINVAL for an
  * unsupported shape, BEM_ECUDA if the check fails. aim_gemv_select(ctx, 0) restores the
@@ -171,10 +173,13 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *   what 6: stencil anchors, int32 [N_E + N_T][3]
  *   what 7: edge table, int32 [N_E][6] = (a, b, T+, T-, v+, v-)
  *   what 8: the set-up autotuners' table, float [candidates][5] = (kind: 0 row plan,
- *           1 flat, 2 bulk-copy staged, 3 stream, 5 Part_Schedule task list; CTAs per SM; column parts per row; loads in flight
- *           per lane; ns per launch, or -1 when the candidate was rejected or not applicable),
- *           then the system-matvec schedules (kind 4; CTAs per SM of the e = Z h launch that runs
- *           beside the AIM chain; 0 = it starts with j's GEMV, 1 = after it; 8; ns per matvec)
+ *           1 flat, 2 bulk-copy staged, 3 stream, 5 Part_Schedule task list (one CTA per
+ *           task), 6 the same tasks taken in turn by persistent CTAs; CTAs per SM; column parts
+ *           per row, or rows per task / 8 for kinds 5 and 6; loads in flight per lane; ns per
+ *           launch, or -1 when the candidate was rejected or not applicable), then the
+ *           system-matvec schedules (4; CTAs per SM of the e = Z h launch that runs beside the
+ *           AIM chain; 0 = it starts with j's GEMV, 1 = after it; kind of that launch, 1 or 6;
+ *           ns per matvec)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
 

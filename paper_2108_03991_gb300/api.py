@@ -208,8 +208,8 @@ class Context:
         self._read_info()
 
     def _read_info(self):
-        info = (C.c_int64 * 20)()
-        _check(lib().aim_info(self.h, info, 20))
+        info = (C.c_int64 * 21)()
+        _check(lib().aim_info(self.h, info, 21))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -222,7 +222,8 @@ class Context:
         self.gemv_unroll = info[15]
         self.gemv_tune_ns = {"plain": info[16], "staged": info[17]}
         self.gemv_tune_rejected = info[18]
-        self.gemv_kind = info[19]  # 0 row plan, 1 flat, 2 bulk-copy staged, 3 stream
+        self.gemv_kind = info[19]  # 0 row plan, 1 flat, 2 staged, 3 stream, 5 and 6 task lists
+        self.gemv_cps = info[20]
 
     # ---- ports and far field ---------------------------------------------------------
     def port_ring(self, obj, axis, coord, tol=1e-6):

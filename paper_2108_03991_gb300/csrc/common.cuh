@@ -117,6 +117,7 @@ template <typename R> struct PrecBuf {
   V* heq = nullptr;    // [ne]
   V* j = nullptr;      // [ne]
   V* p = nullptr;      // [nt]
+  V* anear = nullptr;  // [ne] near-region part L^A_NR j of the system matvec
   V* xin = nullptr;    // [ne + nt] conversion buffer for mixed precision
   V* yout = nullptr;
 };
@@ -163,12 +164,18 @@ struct GemvPlan {
   int32_t* cta_seg = nullptr;// device [ncta + 1]
   int ncta = 0;
   int nrows = 0;
+  int cps = 0;                 // the shape's CTAs per SM (as asked of make_gemv_plan)
   int split = 2;               // column parts per row (1, 2 or 4), picked by the autotuner
   int unroll = 4;              // 16-byte loads in flight per lane (4 or 8), likewise
   int flat = 0;                // flat form: rows in chunks (stages, descs, cta_stage as chunks)
   int stream = 0;              // stream form: equal vector shares per warp, atomic row sums
   GemvTask* tasks = nullptr;   // task-list form: the modified Part_Schedule's row panels
-  int ntasks = 0;              //   (one CTA per task of <= 16 rows), when non-zero
+  int ntasks = 0;              //   (one CTA per task of <= 8 * split rows), when non-zero
+  int task_form = 0;           // task list, one right-hand side: 0 = 8 warps per CTA, 1 = 8
+                               //   warps and 8 resident CTAs per SM (32 registers), 2 = 4 warps,
+                               //   16 resident CTAs per SM, tasks of <= 4 * split rows
+  int* ctr = nullptr;          // dynamic task list: device [2] = next task, CTAs finished; the
+                               //   ncta persistent CTAs take tasks in turn (zero between launches)
   int32_t* wrow = nullptr;     // device [warps]: row holding each warp's first vector
   int64_t nquad = 0;           // whole block storage in units of 4 complex elements
   double cmax_over_ideal = 0;  // schedule length / (total work / ncta)
@@ -316,7 +323,7 @@ int build_geometry(aim_ctx* c, const bem_mesh* m, const aim_grid* g);
 // scheduling (host, sched.cpp)
 void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
                       const std::vector<int32_t>& xoff, const std::vector<int32_t>& ld,
-                      int nsm, std::vector<GemvTask>* tasks);
+                      int nsm, int rows_per_task, std::vector<GemvTask>* tasks);
 // setup (setup.cu)
 int setup_device(aim_ctx* c);
 // hot path (hot.cu)

@@ -454,8 +454,8 @@ template <int L> __device__ __forceinline__ int brev_l(int l) {
 // the nz planes that hold data, times Ghat (in the transform's bit-reversed order), inverse,
 // and the first nz outputs stored back
 template <typename V, int L, int M>
-__global__ void __launch_bounds__(256) k_zreg(V* ws, const V* __restrict__ ghat,
-                                              const V* __restrict__ twz, PlaneArgs a) {
+__global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg(V* ws, const V* __restrict__ ghat,
+                                                 const V* __restrict__ twz, PlaneArgs a) {
   constexpr int G = 32 / L;  // lines per warp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lg = lane & (L - 1), grp = lane / L;
@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(256) k_zreg(V* ws, const V* __restrict__ ghat,
 // keeping the ny rows that are read back, into shared memory, then those rows along x, storing
 // the nx x ny window.
 template <typename V, int LX, int MX, int LY, int MY>
-__global__ void __launch_bounds__(256) k_plane_fwd_reg(const V* __restrict__ sigma, V* __restrict__ ws,
+__global__ void __launch_bounds__(384) k_plane_fwd_reg(const V* __restrict__ sigma, V* __restrict__ ws,
                                                        const V* __restrict__ twx,
                                                        const V* __restrict__ twy, PlaneArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(256) k_plane_fwd_reg(const V* __restrict__ sig
 }
 
 template <typename V, int LX, int MX, int LY, int MY>
-__global__ void __launch_bounds__(256) k_plane_inv_reg(const V* __restrict__ ws, V* __restrict__ phi,
+__global__ void __launch_bounds__(384) k_plane_inv_reg(const V* __restrict__ ws, V* __restrict__ phi,
                                                        const V* __restrict__ twx,
                                                        const V* __restrict__ twy, PlaneArgs a) {
   extern __shared__ unsigned char smem_raw[];
@@ -640,7 +640,13 @@ static void launch_zreg(int L, int M, dim3 grid, cudaStream_t s, V* ws, const V*
 template <typename V>
 static bool launch_plane_reg(bool inverse, int L, int M, dim3 grid, size_t smem, cudaStream_t s,
                              const V* in, V* out, const V* twx, const V* twy, const PlaneArgs& a) {
-  const int nt = 256;
+  // threads: L lanes x G groups, G picked (up to 384 threads) for the fewest rounds of the
+  // two directions (ny rows along x, then Px columns along y; the same counts inverted)
+  int nt = 256, rounds = 1 << 30;
+  for (int t = 128; t <= 384; t += 32) {
+    const int G = t / L, r = (a.ny + G - 1) / G + (a.Px + G - 1) / G;
+    if (r < rounds) { rounds = r; nt = t; }
+  }
 #define BEM_P(LL, MM)                                                                                  \
   if (L == LL && M == MM) {                                                                           \
     if (inverse) k_plane_inv_reg<V, LL, MM, LL, MM><<<grid, nt, smem, s>>>(in, out, twx, twy, a);       \

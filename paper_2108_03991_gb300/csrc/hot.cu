@@ -75,22 +75,24 @@ __device__ __forceinline__ void dot_range(const typename Vec16<R>::T* __restrict
 // One row of the product, one warp: acc[r] = sum_k A[row, k] x_r[k]. Rows are streamed with
 // 16-byte loads (two complex FP32 or one complex FP64 per load), evict-first so the streamed
 // matrix does not displace the vectors in L2; x is read through the read-only path (L1).
-template <typename R, int NRHS>
+template <typename R, int NRHS, int U = 4>
 __device__ __forceinline__ void row_dot(const typename C2<R>::T* __restrict__ arow,
                                         const typename C2<R>::T* __restrict__ xb, int n,
                                         int64_t vstride, int lane, typename C2<R>::T* acc) {
   constexpr int CP = Vec16<R>::kCplx;
 #pragma unroll
   for (int r = 0; r < NRHS; ++r) acc[r] = czero<typename C2<R>::T>();
-  dot_range<R, NRHS, 4>(reinterpret_cast<const typename Vec16<R>::T*>(arow), xb, n, 0,
+  dot_range<R, NRHS, U>(reinterpret_cast<const typename Vec16<R>::T*>(arow), xb, n, 0,
                         (n + CP - 1) / CP, vstride, lane, acc);
 #pragma unroll
   for (int r = 0; r < NRHS; ++r) acc[r] = warp_sum(acc[r]);
 }
 
-// Task-list form (one CTA per task of at most 16 rows).
-template <typename R, int NRHS>
-__global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks,
+// Task-list form: one CTA per task (a run of rows of one block), NW warps taking the rows in
+// turn; U = 16-byte loads in flight per lane; MINB resident CTAs per SM asked of the compiler
+// (0: no request).
+template <typename R, int NRHS, int U = 4, int NW = 8, int MINB = 0>
+__global__ void __launch_bounds__(NW * 32, MINB) k_gemv(const GemvTask* __restrict__ tasks,
                                               const typename C2<R>::T* __restrict__ A,
                                               const typename C2<R>::T* __restrict__ x,
                                               typename C2<R>::T* __restrict__ y, int64_t vstride,
@@ -99,10 +101,10 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks
   const GemvTask t = tasks[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const V* xb = x + t.xoff;
-  for (int rr = warp; rr < t.nrows; rr += 8) {
+  for (int rr = warp; rr < t.nrows; rr += NW) {
     const int row = t.row0 + rr;
     V acc[NRHS];
-    row_dot<R, NRHS>(A + t.aoff + (int64_t)row * t.ld, xb, t.n, vstride, lane, acc);
+    row_dot<R, NRHS, U>(A + t.aoff + (int64_t)row * t.ld, xb, t.n, vstride, lane, acc);
 #pragma unroll
     for (int r = 0; r < NRHS; ++r) {
       if (lane == 0) {
@@ -110,6 +112,45 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvTask* __restrict__ tasks
         y[o] = hsub ? csub(hsub[o], acc[r]) : acc[r];
       }
     }
+  }
+}
+
+// Dynamic task list: ncta persistent CTAs take the tasks in list order from a counter (the
+// largest blocks first, as in LPT), so a launch of few CTAs per SM still balances like the
+// one-CTA-per-task form. The CTA that finishes last sets the counters back to zero for the
+// next launch of the plan (a plan never runs concurrently with itself). Every CTA leaves the
+// loop after at most ntasks + gridDim.x fetches in all; nothing waits.
+template <typename R, int U>
+__global__ void __launch_bounds__(256) k_gemv_dyn(const GemvTask* __restrict__ tasks, int ntasks,
+                                                  int* __restrict__ ctr,
+                                                  const typename C2<R>::T* __restrict__ A,
+                                                  const typename C2<R>::T* __restrict__ x,
+                                                  typename C2<R>::T* __restrict__ y,
+                                                  const typename C2<R>::T* __restrict__ hsub) {
+  typedef typename C2<R>::T V;
+  __shared__ int s_task;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(&ctr[0], 1);
+    __syncthreads();
+    const int ti = s_task;
+    __syncthreads();  // all have read s_task before the next fetch overwrites it
+    if (ti >= ntasks) break;
+    const GemvTask t = tasks[ti];
+    const V* xb = x + t.xoff;
+    for (int rr = warp; rr < t.nrows; rr += 8) {
+      const int row = t.row0 + rr;
+      V acc[1];
+      row_dot<R, 1, U>(A + t.aoff + (int64_t)row * t.ld, xb, t.n, 0, lane, acc);
+      if (lane == 0) {
+        const int64_t o = t.xoff + row;
+        y[o] = hsub ? csub(hsub[o], acc[0]) : acc[0];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
+    atomicExch(&ctr[0], 0);
+    atomicExch(&ctr[1], 0);
   }
 }
 
@@ -341,7 +382,27 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
                   cudaStream_t s) {
   if (p.ncta == 0 || p.nrows == 0) return BEM_OK;
   if (p.tma) return run_gemv_tma<R>(p, A, x, y, nrhs, vstride, hsub, s);
-  if (p.ntasks > 0) return run_gemv<R>(p.tasks, p.ntasks, A, x, y, nrhs, vstride, hsub, s);
+  if (p.ntasks > 0) {
+    if (p.ctr && nrhs == 1) {
+      if (p.unroll >= 8)
+        k_gemv_dyn<R, 8><<<p.ncta, 256, 0, s>>>(p.tasks, p.ntasks, p.ctr, A, x, y, hsub);
+      else
+        k_gemv_dyn<R, 4><<<p.ncta, 256, 0, s>>>(p.tasks, p.ntasks, p.ctr, A, x, y, hsub);
+      BEM_CUDA(cudaGetLastError());
+      return BEM_OK;
+    }
+    if (nrhs == 1 && (p.unroll == 8 || p.task_form != 0)) {
+      if (p.unroll == 8)
+        k_gemv<R, 1, 8><<<p.ntasks, 256, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
+      else if (p.task_form == 1)
+        k_gemv<R, 1, 4, 8, 8><<<p.ntasks, 256, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
+      else
+        k_gemv<R, 1, 4, 4, 16><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
+      BEM_CUDA(cudaGetLastError());
+      return BEM_OK;
+    }
+    return run_gemv<R>(p.tasks, p.ntasks, A, x, y, nrhs, vstride, hsub, s);
+  }
   if (p.stream) {
     k_gemv_init<<<(unsigned)((p.nrows * (int64_t)nrhs + 255) / 256), 256, 0, s>>>(y, hsub, (int64_t)p.nrows,
                                                                                nrhs, vstride);
@@ -547,7 +608,8 @@ __global__ void __launch_bounds__(256) k_rows_e(
     const R* __restrict__ fdE, const int32_t* __restrict__ et,
     const typename C2<R>::T* __restrict__ p, int ne, int nx, int ny, R k0, int mode,
     typename C2<R>::T* __restrict__ y, int nt, const R* __restrict__ fdT,
-    const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ q) {
+    const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ q,
+    const typename C2<R>::T* __restrict__ anear) {
   typedef typename C2<R>::T V;
   const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (mode == 1 && m >= ne && m < ne + nt) {
@@ -577,9 +639,14 @@ __global__ void __launch_bounds__(256) k_rows_e(
       acc.y += w * f.y;
     }
   }
-  near_row(LA, colA, j, rowA[m], rowA[m + 1], lane, acc);
+  if (!anear) near_row(LA, colA, j, rowA[m], rowA[m + 1], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) {
+    if (anear) {
+      const V an = anear[m];
+      acc.x += an.x;
+      acc.y += an.y;
+    }
     if (mode == 0) {
       y[m] = acc;
     } else {
@@ -598,6 +665,23 @@ __global__ void __launch_bounds__(256) k_rows_e(
       y[m] = s;
     }
   }
+}
+
+// a = L^A_NR j (the near region of the RWG rows), one warp per row: the part of the system
+// matvec's first row that needs only j, run beside the convolution
+template <typename R>
+__global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA,
+                                                const int32_t* __restrict__ colA,
+                                                const typename C2<R>::T* __restrict__ LA,
+                                                const typename C2<R>::T* __restrict__ j, int ne,
+                                                typename C2<R>::T* __restrict__ a) {
+  typedef typename C2<R>::T V;
+  const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (m >= ne) return;
+  V acc = czero<V>();
+  near_row(LA, colA, j, rowA[m], rowA[m + 1], lane, acc);
+  acc = warp_sum(acc);
+  if (lane == 0) a[m] = acc;
 }
 
 template <typename R> PrecBuf<R>& buf(aim_ctx* c);
@@ -619,7 +703,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
                                           x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
-                                          nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr);
+                                          nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr, nullptr);
   } else if (which == AIM_OP_LPHI) {
     V* sq = b.sigma + 3 * ng;
     project_t<R>(c, b.WPT, x, sq, s);
@@ -630,7 +714,9 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     // Three branches. With C = Y_eq Z formed at set-up (Eq. EFIEeqYZ), j = h - C h and e = Z h
     // are independent: the main stream runs j and its AIM chain (projection, convolution,
     // rows); e = Z h streams beside it with few CTAs (it is needed only by the last kernel,
-    // for I_x e); the charge branch p = L^Phi q runs on the side stream.
+    // for I_x e); the charge branch p = L^Phi q runs on the side stream, followed there by
+    // the near region L^A_NR j once j is out, so that only the interpolation and the
+    // combination follow the convolution.
     const V* h = x;
     const V* q = x + ne;
     V* sq = b.sigma + 3 * ng;
@@ -641,14 +727,15 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
                                                 nt, nx, ny, b.p);
-    BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
     BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
-    if (c->z_after) {  // e = Z h once j is out, beside the AIM chain only
-      BEM_CUDA(cudaEventRecord(c->ev_c, s));
+    BEM_CUDA(cudaEventRecord(c->ev_c, s));
+    BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
+    k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.j, ne, b.anear);
+    BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    if (c->z_after)  // e = Z h once j is out, beside the AIM chain only
       BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_c, 0));
-    }
     BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
     BEM_CUDA(cudaEventRecord(c->ev_z, c->zside));
     project_e<R>(c, b.WAT, b.j, b.sigma, s);
@@ -657,7 +744,8 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_z, 0));
     k_rows_e<R><<<nb(ne + nt, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
                                                b.LA, b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p,
-                                               ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q);
+                                               ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q,
+                                               b.anear);
   } else {
     set_error("aim_matvec: unknown operator %d", which);
     return BEM_EINVAL;

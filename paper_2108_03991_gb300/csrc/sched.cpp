@@ -86,7 +86,7 @@ double part_schedule(int ntask, const double* W, int P, int p_cutoff, int32_t* P
 // kRowsPerTask rows so one CTA (8 warps) processes one task.
 void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
                       const std::vector<int32_t>& xoff, const std::vector<int32_t>& ld, int nsm,
-                      std::vector<GemvTask>* tasks) {
+                      int rows_per_task, std::vector<GemvTask>* tasks) {
   const int nb = (int)n.size();
   std::vector<int> order(nb);
   std::iota(order.begin(), order.end(), 0);
@@ -97,7 +97,7 @@ void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>&
   const int P = std::max(1, 4 * nsm);
   part_schedule(nb, W.data(), P, 20, Pi.data());
   tasks->clear();
-  const int kRowsPerTask = 16;
+  const int kRowsPerTask = std::max(1, rows_per_task);
   for (int r = 0; r < nb; ++r) {
     int i = order[r];
     int panels = std::max(1, std::min<int>(Pi[r], n[i]));

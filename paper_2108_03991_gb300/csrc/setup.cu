@@ -447,10 +447,11 @@ struct TunePlan {  // a candidate plan held in temporary device memory
 // receives the time of 5 launches of those two.
 namespace {
 struct GemvCand {
-  int kind;   // 0 row plan, 1 flat, 2 staged, 3 stream, 5 Part_Schedule task list
+  int kind;   // 0 row plan, 1 flat, 2 staged, 3 stream, 5 Part_Schedule task list,
+              // 6 the same tasks taken in turn by cps persistent CTAs per SM
   int cps;    // CTAs per SM
-  int split;  // column parts per row (row plan)
-  int unroll; // loads in flight per lane (row plan, flat)
+  int split;  // column parts per row (row plan); rows per task / 8 (task list)
+  int unroll; // loads in flight per lane (row plan, flat, task list)
 };
 }  // namespace
 
@@ -464,17 +465,28 @@ static int make_gemv_plan(aim_ctx* c, TunePlan* t, const GemvCand& g, int nsm,
   std::vector<TmaStage> st;
   std::vector<TmaDesc> dsc;
   GemvPlan p;
-  if (g.kind == 5) {
+  if (g.kind == 5 || g.kind == 6) {
     // the paper's schedule: each block cut into the modified Part_Schedule's P_i row panels
-    // (P = 4 CTA slots per SM, Alg. 2), the panels into tasks of <= 16 rows, one CTA each
+    // (P = 4 CTA slots per SM, Alg. 2), the panels into tasks of <= 8 * split rows, one CTA each
     std::vector<int32_t> xo(n.size());
     for (size_t i = 0, acc = 0; i < n.size(); acc += n[i], ++i) xo[i] = (int32_t)acc;
     std::vector<GemvTask> tasks;
-    build_gemv_tasks(n, off, xo, ld, nsm, &tasks);
+    const int form = g.kind == 5 && g.cps == 8 ? 1 : g.kind == 5 && g.cps == 16 ? 2 : 0;
+    build_gemv_tasks(n, off, xo, ld, nsm, (form == 2 ? 4 : 8) * g.split, &tasks);
     if (t) BEM_TRY(t->put(&p.tasks, tasks));
     else BEM_TRY(upload(c, &p.tasks, tasks.data(), tasks.size()));
     p.ntasks = (int)tasks.size();
     p.ncta = p.ntasks;
+    p.split = g.split;
+    p.unroll = g.unroll;
+    p.task_form = form;
+    p.cps = g.cps;
+    if (g.kind == 6) {
+      const std::vector<int> zero(2, 0);
+      if (t) BEM_TRY(t->put(&p.ctr, zero));
+      else BEM_TRY(upload(c, &p.ctr, zero.data(), zero.size()));
+      p.ncta = nsm * g.cps;
+    }
     p.nrows = 0;
     for (int v : n) p.nrows += v;
     *out = p;
@@ -514,6 +526,7 @@ static int make_gemv_plan(aim_ctx* c, TunePlan* t, const GemvCand& g, int nsm,
   BEM_TRY(put(&p.segs, segs));
   BEM_TRY(put(&p.cta_seg, cseg));
   p.ncta = nsm * g.cps;
+  p.cps = g.cps;
   p.nrows = (int)rows.size();
   p.split = g.split;
   p.unroll = g.unroll;
@@ -554,7 +567,13 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
   cands.push_back({1, 4, 1, 8});
   cands.push_back({3, 6, 1, 4});
   cands.push_back({3, 4, 1, 8});
-  cands.push_back({5, 4, 1, 4});
+  for (int split : {1, 2}) cands.push_back({5, 4, split, 4});
+  cands.push_back({5, 8, 1, 4});
+  cands.push_back({5, 16, 1, 4});
+  cands.push_back({5, 16, 2, 4});
+  cands.push_back({5, 4, 1, 8});
+  cands.push_back({6, 5, 2, 4});
+  cands.push_back({6, 4, 2, 8});
   cands.push_back({2, 1, 1, 4});
   cands.push_back({2, 2, 1, 2});
   int* derr = nullptr;
@@ -651,7 +670,11 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
       (kind == 0 && (cps == 4 || cps == 6) && (split == 1 || split == 2 || split == 4) &&
        (unroll == 4 || (unroll == 8 && cps == 4))) ||
       ((kind == 1 || kind == 3) && ((cps == 6 && unroll == 4) || (cps == 4 && unroll == 8))) ||
-      (kind == 2 && (cps == 1 || cps == 2)) || kind == 5;
+      (kind == 2 && (cps == 1 || cps == 2)) ||
+      (kind == 5 && (split == 1 || split == 2 || split == 4) &&
+       ((cps == 4 && (unroll == 4 || unroll == 8)) || ((cps == 8 || cps == 16) && unroll == 4))) ||
+      (kind == 6 && (split == 1 || split == 2 || split == 4) && (unroll == 4 || unroll == 8) &&
+       cps >= 1 && cps <= 8);
   if (!ok_shape) {
     set_error("aim_gemv_plan: unsupported shape (kind %d, %d CTAs/SM, split %d, unroll %d)", kind,
               cps, split, unroll);
@@ -666,7 +689,7 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
   BEM_TRY(dalloc_t(c, &derr, 1));
   BEM_CUDA(cudaMemset(derr, 0, sizeof(int)));
   GemvPlan p;
-  const GemvCand g{kind, kind == 5 ? 4 : cps, kind == 0 ? split : 1,
+  const GemvCand g{kind, cps, kind == 0 || kind >= 5 ? split : 1,
                    kind == 2 ? (cps == 1 ? 4 : 2) : unroll};
   const int r = make_gemv_plan(c, nullptr, g, nsm, n, c->zoff, c->zld, derr, &p);
   if (r == 1) {
@@ -703,9 +726,10 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
 }
 
 // Schedule autotuner of the system matvec: e = Z h runs beside the AIM chain of j with a
-// launch of few CTAs. Time the captured FP32 graph for each (CTAs per SM of that launch,
-// start with j's GEMV or after it) with CUDA events and keep the fastest; the FP64 matvec
-// uses the same choice. tune_table gains rows (kind 4, CTAs per SM, start, 8, ns per matvec).
+// launch of few CTAs. Time the captured FP32 graph for each (launch of e: the flat form or the
+// dynamic task list, and its CTAs per SM; start with j's GEMV or after it) with CUDA events and
+// keep the fastest; the FP64 matvec uses the same choice. tune_table gains rows (4, CTAs per
+// SM, start, kind of the e launch, ns per matvec).
 int tune_matvec_schedule(aim_ctx* c) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -725,12 +749,13 @@ int tune_matvec_schedule(aim_ctx* c) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int best_cps = 2;
+  GemvCand best_g{1, 2, 1, 8};
   bool best_after = false;
   int rc = BEM_OK;
-  for (int cps : {1, 2, 3}) {
+  const GemvCand zc[] = {{1, 1, 1, 8}, {1, 2, 1, 8}, {1, 3, 1, 8}, {6, 2, 2, 4}, {6, 3, 2, 4}, {6, 4, 2, 4}};
+  for (const GemvCand& g : zc) {
     GemvPlan p;
-    if ((rc = make_gemv_plan(c, nullptr, GemvCand{1, cps, 1, 8}, nsm, n, c->zoff, c->zld, derr, &p)) != BEM_OK) break;
+    if ((rc = make_gemv_plan(c, nullptr, g, nsm, n, c->zoff, c->zld, derr, &p)) != BEM_OK) break;
     for (bool after : {false, true}) {
       c->gbg32 = c->gbg64 = p;
       c->z_after = after;
@@ -744,8 +769,8 @@ int tune_matvec_schedule(aim_ctx* c) {
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      c->tune_table.insert(c->tune_table.end(), {4.f, (float)cps, after ? 1.f : 0.f, 8.f, ms * 1e6f / 20.f});
-      if (ms < best) { best = ms; best_cps = cps; best_after = after; }
+      c->tune_table.insert(c->tune_table.end(), {4.f, (float)g.cps, after ? 1.f : 0.f, (float)g.kind, ms * 1e6f / 20.f});
+      if (ms < best) { best = ms; best_g = g; best_after = after; }
     }
     if (rc != BEM_OK) break;
   }
@@ -755,7 +780,7 @@ int tune_matvec_schedule(aim_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   if (rc != BEM_OK) return rc;
-  BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{1, best_cps, 1, 8}, nsm, n, c->zoff, c->zld, derr, &c->gbg32));
+  BEM_TRY(make_gemv_plan(c, nullptr, best_g, nsm, n, c->zoff, c->zld, derr, &c->gbg32));
   c->gbg64 = c->gbg32;
   c->z_after = best_after;
   BEM_CUDA(cudaGetLastError());
@@ -1120,6 +1145,8 @@ int setup_device(aim_ctx* c) {
   BEM_TRY(dalloc_t(c, &c->f64.e, c->ne));
   BEM_TRY(dalloc_t(c, &c->f32.heq, c->ne));
   BEM_TRY(dalloc_t(c, &c->f64.heq, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f32.anear, c->ne));
+  BEM_TRY(dalloc_t(c, &c->f64.anear, c->ne));
   BEM_TRY(dalloc_t(c, &c->f32.j, c->ne));
   BEM_TRY(dalloc_t(c, &c->f64.j, c->ne));
   BEM_TRY(dalloc_t(c, &c->f32.p, c->nt));

@@ -166,7 +166,9 @@ def test_gemv_autotuner_candidates(prob):
 
 
 @pytest.mark.parametrize("kind", [1, 2, (0, 6, 2, 4), (0, 4, 4, 8), (1, 4, 1, 8), (3, 6, 1, 4),
-                                  (3, 4, 1, 8), (2, 2, 1, 4), (5, 4, 1, 4)])
+                                  (3, 4, 1, 8), (2, 2, 1, 4), (5, 4, 1, 4),
+                                  (5, 4, 4, 4), (5, 4, 2, 8), (5, 8, 1, 4), (5, 16, 2, 4),
+                                  (6, 3, 2, 4), (6, 4, 1, 8)])
 def test_gemv_kinds_match_oracle(prob, kind):
     """Every FP32 GEMV form, forced in turn (the autotuner's best plain and best staged, then
     explicit row-plan, flat, stream, staged and Part_Schedule task-list launches), against the
