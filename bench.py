@@ -190,7 +190,8 @@ def run_reference(args, rank, world):
 # profiles/gemv_internal_bar_array.md; valid only for the launch shape captured there
 # DRAM bytes per launch (read + write) of the GEMV shapes captured with ncu on this workload,
 # keyed by (kind, CTAs per SM, split, loads in flight) as aim_info reports them
-PROFILED_GEMV = {(1, 6, 0, 4): 207.9e6, (5, 4, 2, 4): 204.9e6, (5, 16, 1, 4): 208.3e6}
+PROFILED_GEMV = {(1, 6, 0, 4): 207.9e6, (5, 4, 2, 4): 204.9e6, (5, 16, 1, 4): 208.3e6,
+                 (5, 8, 1, 4): 207.6e6}
 
 
 def gemv_traffic(ctx):
