@@ -394,6 +394,11 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
     if (nrhs == 1 && (p.unroll == 8 || p.task_form != 0)) {
       if (p.unroll == 8)
         k_gemv<R, 1, 8><<<p.ntasks, 256, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
+      else if constexpr (sizeof(R) == 8)  // FP64 needs more than 32 registers: no occupancy request
+        if (p.task_form == 1)
+          k_gemv<R, 1, 4, 8, 0><<<p.ntasks, 256, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
+        else
+          k_gemv<R, 1, 4, 4, 0><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
       else if (p.task_form == 1)
         k_gemv<R, 1, 4, 8, 8><<<p.ntasks, 256, 0, s>>>(p.tasks, A, x, y, vstride, hsub);
       else
