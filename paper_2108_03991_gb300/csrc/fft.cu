@@ -414,14 +414,19 @@ __device__ __forceinline__ void reg_fft_fwd(V* v, const V* tw, int P, int lg, co
   dft_reg<V, M>(v, tw, P / M, false);
 #pragma unroll
   for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], tk[k1]);
+  typedef decltype(v[0].x) R;
 #pragma unroll
   for (int st = 0; st < Log2<L>::v; ++st) {
+    // lower lane of a pair: v + p; upper lane: (p - v) W. As one branch-free form:
+    // (p + sg v) we with sg = +-1 (exact products) and we = 1 on the lower lane
     const int sp = L >> (st + 1);
     const bool top = (lg & sp) == 0;
+    const R sg = top ? R(1) : R(-1);
+    const V we = top ? mk(R(1), R(0)) : ts[st];
 #pragma unroll
     for (int k1 = 0; k1 < M; ++k1) {
       const V p = shfl_x(v[k1], sp);
-      v[k1] = top ? cadd(v[k1], p) : cmul(csub(p, v[k1]), ts[st]);
+      v[k1] = cmul(mk(sg * v[k1].x + p.x, sg * v[k1].y + p.y), we);
     }
   }
 }
@@ -429,16 +434,19 @@ __device__ __forceinline__ void reg_fft_fwd(V* v, const V* tw, int P, int lg, co
 template <typename V, int L, int M>
 __device__ __forceinline__ void reg_fft_inv(V* v, const V* tw, int P, int lg, const V* tk,
                                             const V* ts) {
+  typedef decltype(v[0].x) R;
 #pragma unroll
   for (int st = Log2<L>::v - 1; st >= 0; --st) {
+    // the upper lane first takes conj(W); then lower: own + p, upper: p - own (= p + sg own)
     const int sp = L >> (st + 1);
     const bool top = (lg & sp) == 0;
-    const V w = mk(ts[st].x, -ts[st].y);
+    const R sg = top ? R(1) : R(-1);
+    const V we = top ? mk(R(1), R(0)) : mk(ts[st].x, -ts[st].y);
 #pragma unroll
     for (int k1 = 0; k1 < M; ++k1) {
-      const V own = top ? v[k1] : cmul(v[k1], w);
+      const V own = cmul(v[k1], we);
       const V p = shfl_x(own, sp);
-      v[k1] = top ? cadd(own, p) : csub(p, own);
+      v[k1] = mk(sg * own.x + p.x, sg * own.y + p.y);
     }
   }
 #pragma unroll
