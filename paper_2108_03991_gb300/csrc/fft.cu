@@ -396,15 +396,17 @@ template <typename V> __device__ __forceinline__ V shfl_x(V v, int s) {
 template <int L> struct Log2 { static constexpr int v = L == 8 ? 3 : (L == 16 ? 4 : 5); };
 
 // twiddles of lane lg for a line of P = L M: tk[k1] = W_P^(lg k1), ts[st] = W_(2s)^(lg mod s)
-// for the shuffle stage of pair distance s = L >> (st + 1)
+// for the shuffle stage of pair distance s = L >> (st + 1). The table holds W_P^j, so the
+// indices are lg k1 (< P, no reduction needed) and (lg mod s) P / (2 s) = (lg mod s) M 2^st.
 template <typename V, int L, int M>
 __device__ __forceinline__ void reg_twiddles(const V* tw, int P, int lg, V* tk, V* ts) {
+  (void)P;
 #pragma unroll
-  for (int k1 = 0; k1 < M; ++k1) tk[k1] = tw[(lg * k1) % P];
+  for (int k1 = 0; k1 < M; ++k1) tk[k1] = tw[lg * k1];
 #pragma unroll
   for (int st = 0; st < Log2<L>::v; ++st) {
     const int sp = L >> (st + 1);
-    ts[st] = tw[(lg & (sp - 1)) * (P / (2 * sp))];
+    ts[st] = tw[(lg & (sp - 1)) * (M << st)];
   }
 }
 
@@ -493,6 +495,62 @@ __global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg(V* ws, const V* __
   for (int n1 = 0; n1 < M; ++n1) {
     const int z = lg + L * n1;
     if (live && z < a.nz) base[z * plane] = v[n1];
+  }
+}
+
+// z pass with the CTA's lines staged through shared memory: the nz data planes and the Ghat
+// column of the CTA's 8 * 32 / L adjacent x are read and written as contiguous runs of x
+// (one warp per line would touch 32 planes per load, a quarter of each sector), then each
+// line is transformed in registers as in k_zreg. Dynamic shared memory: NL (nz + 1) + NL (Pz + 1)
+// elements.
+template <typename V, int L, int M>
+__global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg_st(V* ws, const V* __restrict__ ghat,
+                                                            const V* __restrict__ twz, PlaneArgs a) {
+  constexpr int G = 32 / L, NL = 8 * G;  // lines per warp, per CTA
+  extern __shared__ unsigned char smem_raw[];
+  const int sp = a.nz + 1, gp = a.Pz + 1;
+  V* S = reinterpret_cast<V*>(smem_raw);  // [NL][sp]: the line's data along z
+  V* Gs = S + NL * sp;                    // [NL][gp]: Ghat along the line's k
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lg = lane & (L - 1), xi = warp * G + lane / L;
+  const int x0 = blockIdx.x * NL, y = blockIdx.y, c = blockIdx.z;
+  const int P = a.Pz, nlive = min(NL, a.Px - x0);
+  const int64_t plane = (int64_t)a.Py * a.Px;
+  V* base = ws + c * a.P3 + (int64_t)y * a.Px + x0;
+  for (int i = threadIdx.x; i < a.nz * NL; i += blockDim.x) {
+    const int z = i / NL, l = i - z * NL;
+    S[l * sp + z] = l < nlive ? base[z * plane + l] : czero<V>();
+  }
+  const int fy = min(y, a.Py - y);
+  for (int i = threadIdx.x; i < P * NL; i += blockDim.x) {
+    const int k = i / NL, l = i - k * NL, x = x0 + l;
+    Gs[l * gp + k] = l < nlive ? ghat[((int64_t)min(k, P - k) * a.gy + fy) * a.gx + min(x, a.Px - x)]
+                               : czero<V>();
+  }
+  __syncthreads();
+  V v[M];
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    const int z = lg + L * n1;
+    v[n1] = z < a.nz ? S[xi * sp + z] : czero<V>();
+  }
+  V tk[M], ts[Log2<L>::v];
+  reg_twiddles<V, L, M>(twz, P, lg, tk, ts);
+  reg_fft_fwd<V, L, M>(v, twz, P, lg, tk, ts);
+  const int k2 = brev_l<L>(lg);
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) v[k1] = cmul(v[k1], Gs[xi * gp + k1 + M * k2]);
+  reg_fft_inv<V, L, M>(v, twz, P, lg, tk, ts);
+  // each lane rewrites only the entries it read: no barrier before the write-back
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    const int z = lg + L * n1;
+    if (z < a.nz) S[xi * sp + z] = v[n1];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.nz * NL; i += blockDim.x) {
+    const int z = i / NL, l = i - z * NL;
+    if (l < nlive) base[z * plane + l] = S[l * sp + z];
   }
 }
 
@@ -638,8 +696,15 @@ static bool reg_shape(int P, int* L, int* M) {
 template <typename V>
 static void launch_zreg(int L, int M, dim3 grid, cudaStream_t s, V* ws, const V* ghat,
                         const V* tw, const PlaneArgs& a) {
-#define BEM_Z(LL, MM) \
-  if (L == LL && M == MM) { k_zreg<V, LL, MM><<<grid, 256, 0, s>>>(ws, ghat, tw, a); return; }
+  const int NL = 8 * (32 / L);
+  const size_t smem = (size_t)NL * ((a.nz + 1) + (a.Pz + 1)) * sizeof(V);
+  const bool staged = smem <= 48 * 1024;
+#define BEM_Z(LL, MM)                                                          \
+  if (L == LL && M == MM) {                                                    \
+    if (staged) k_zreg_st<V, LL, MM><<<grid, 256, smem, s>>>(ws, ghat, tw, a); \
+    else k_zreg<V, LL, MM><<<grid, 256, 0, s>>>(ws, ghat, tw, a);              \
+    return;                                                                    \
+  }
   BEM_REG_SHAPES(BEM_Z)
 #undef BEM_Z
 }

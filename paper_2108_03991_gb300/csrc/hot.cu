@@ -616,10 +616,10 @@ __global__ void __launch_bounds__(256) k_rows_e(
     const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ q,
     const typename C2<R>::T* __restrict__ anear) {
   typedef typename C2<R>::T V;
-  const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (mode == 1 && m >= ne && m < ne + nt) {
-    if (lane == 0) {
-      const int t = m - ne;
+  const int nbE = (ne + 7) >> 3;  // blocks of the RWG rows (one warp per row); then the pulse
+  if ((int)blockIdx.x >= nbE) {   // rows of mode 1, one thread per row
+    const int t = (blockIdx.x - nbE) * blockDim.x + threadIdx.x;
+    if (mode == 1 && t < nt) {
       V s = jk0(q[t], k0);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -628,10 +628,11 @@ __global__ void __launch_bounds__(256) k_rows_e(
         s.x += c * jj.x;
         s.y += c * jj.y;
       }
-      y[m] = s;
+      y[ne + t] = s;
     }
     return;
   }
+  const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (m >= ne) return;
   V acc = czero<V>();
   if (lane < 27) {
@@ -747,7 +748,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_z, 0));
-    k_rows_e<R><<<nb(ne + nt, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
+    k_rows_e<R><<<nb(ne, 8) + nb(nt, 256), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
                                                b.LA, b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p,
                                                ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q,
                                                b.anear);
