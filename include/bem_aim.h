@@ -178,8 +178,9 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *           per row, or rows per task / 8 for kinds 5 and 6; loads in flight per lane; ns per
  *           launch, or -1 when the candidate was rejected or not applicable), then the
  *           system-matvec schedules (4; CTAs per SM of the e = Z h launch that runs beside the
- *           AIM chain; 0 = it starts with j's GEMV, 1 = after it; kind of that launch, 1 or 6;
- *           ns per matvec)
+ *           AIM chain, 0 when it runs on the main stream; 0 = it starts with j's GEMV, 1 = after
+ *           it beside the chain, 2 = after it on the main stream with j's launch shape; kind of
+ *           that launch; ns per matvec)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
 

@@ -274,7 +274,8 @@ struct aim_ctx {
   // streams for the two-branch matvec and its CUDA-graph capture
   cudaStream_t cap = nullptr, side = nullptr, zside = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr, ev_c = nullptr;
-  bool z_after = false;  // e = Z h starts when j = h - C h is out (else with it)
+  int z_after = 0;  // e = Z h: 0 beside j's GEMV, 1 beside the AIM chain once j = h - C h is
+                    // out, 2 on the main stream after j's GEMV with the whole GPU
   struct GKey {
     int which, prec;
     const void* x;

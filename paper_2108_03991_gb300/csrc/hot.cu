@@ -728,7 +728,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     V* sq = b.sigma + 3 * ng;
     BEM_CUDA(cudaEventRecord(c->ev_fork, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
+    if (c->z_after != 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
@@ -740,10 +740,14 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
     k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.j, ne, b.anear);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
-    if (c->z_after)  // e = Z h once j is out, beside the AIM chain only
-      BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_c, 0));
-    BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
-    BEM_CUDA(cudaEventRecord(c->ev_z, c->zside));
+    if (c->z_after == 2) {  // e = Z h right after j's GEMV on the main stream, whole GPU
+      BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
+    } else {
+      if (c->z_after)  // e = Z h once j is out, beside the AIM chain only
+        BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_c, 0));
+      BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
+    }
+    BEM_CUDA(cudaEventRecord(c->ev_z, c->z_after == 2 ? s : c->zside));
     project_e<R>(c, b.WAT, b.j, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));

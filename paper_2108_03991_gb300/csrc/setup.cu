@@ -726,10 +726,12 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
 }
 
 // Schedule autotuner of the system matvec: e = Z h runs beside the AIM chain of j with a
-// launch of few CTAs. Time the captured FP32 graph for each (launch of e: the flat form or the
-// dynamic task list, and its CTAs per SM; start with j's GEMV or after it) with CUDA events and
-// keep the fastest; the FP64 matvec uses the same choice. tune_table gains rows (4, CTAs per
-// SM, start, kind of the e launch, ns per matvec).
+// launch of few CTAs, or after j's GEMV on the main stream with the whole GPU. Time the
+// captured FP32 graph for each (launch of e: the flat form or the dynamic task list, and its
+// CTAs per SM; start with j's GEMV, after it beside the chain, or after it on the main stream)
+// with CUDA events and keep the fastest; the FP64 matvec uses the same choice. tune_table gains
+// rows (4, CTAs per SM or 0 for the main-stream launch, start 0/1/2, kind of the e launch, ns
+// per matvec).
 int tune_matvec_schedule(aim_ctx* c) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -750,13 +752,18 @@ int tune_matvec_schedule(aim_ctx* c) {
   cudaEventCreate(&e1);
   float best = 1e30f;
   GemvCand best_g{1, 2, 1, 8};
-  bool best_after = false;
+  int best_after = 0;
   int rc = BEM_OK;
-  const GemvCand zc[] = {{1, 1, 1, 8}, {1, 2, 1, 8}, {1, 3, 1, 8}, {6, 2, 2, 4}, {6, 3, 2, 4}, {6, 4, 2, 4}};
-  for (const GemvCand& g : zc) {
+  // the last entry stands for the serial schedule (e = Z h after j's GEMV, with its launch)
+  const GemvCand zc[] = {{1, 1, 1, 8}, {1, 2, 1, 8}, {1, 3, 1, 8}, {6, 2, 2, 4}, {6, 3, 2, 4}, {6, 4, 2, 4},
+                         {1, 2, 1, 8}};
+  const int nzc = (int)(sizeof(zc) / sizeof(zc[0]));
+  for (int gi = 0; gi < nzc; ++gi) {
+    const GemvCand& g = zc[gi];
     GemvPlan p;
     if ((rc = make_gemv_plan(c, nullptr, g, nsm, n, c->zoff, c->zld, derr, &p)) != BEM_OK) break;
-    for (bool after : {false, true}) {
+    for (int after : {0, 1, 2}) {
+      if ((after == 2) != (gi == nzc - 1)) continue;
       c->gbg32 = c->gbg64 = p;
       c->z_after = after;
       for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -769,7 +776,9 @@ int tune_matvec_schedule(aim_ctx* c) {
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      c->tune_table.insert(c->tune_table.end(), {4.f, (float)g.cps, after ? 1.f : 0.f, (float)g.kind, ms * 1e6f / 20.f});
+      c->tune_table.insert(c->tune_table.end(), {4.f, after == 2 ? 0.f : (float)g.cps, (float)after,
+                                                 after == 2 ? (float)(c->gplan.ctr ? 6 : c->gplan.ntasks ? 5 : 1) : (float)g.kind,
+                                                 ms * 1e6f / 20.f});
       if (ms < best) { best = ms; best_g = g; best_after = after; }
     }
     if (rc != BEM_OK) break;

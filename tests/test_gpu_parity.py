@@ -198,6 +198,30 @@ def test_gemv_kinds_match_oracle(prob, kind):
         ctx.gemv_select(0)
 
 
+@pytest.mark.parametrize("shape", [(6, 2, 1, 4), (6, 3, 2, 8)])
+def test_dynamic_task_list_relaunch(prob, shape):
+    """The dynamic task list (persistent CTAs taking tasks from a counter that the last CTA sets
+    back to zero): repeated one-vector launches give the same product every time and match the
+    oracle, so no launch starts from a stale counter."""
+    ctx, S = prob["ctx"], prob["S"]
+    ctx.gemv_plan(*shape)
+    try:
+        assert ctx.gemv_kind == 6
+        h = synth.rand_cvec(ctx.ne, 70)
+        ht = torch.from_numpy(h.astype(np.complex64)).cuda()
+        eo = blockops.block_gemv(S.Zs, [a for a, _ in S.ranges], h)
+        first = None
+        for _ in range(5):
+            e, _ = ctx.internal(ht, prec=api.BEM_C32, want_heq=False)
+            e = e.cpu().numpy()
+            assert rel(e, eo) < 1e-5
+            if first is None:
+                first = e
+            assert np.array_equal(e, first)
+    finally:
+        ctx.gemv_select(0)
+
+
 def test_plane_wave_rhs(prob):
     ctx, rw, k0 = prob["ctx"], prob["rw"], prob["k0"]
     b = ctx.rhs_plane_wave(prec=api.BEM_C64).cpu().numpy()
