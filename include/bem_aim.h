@@ -126,6 +126,16 @@ int aim_gemv_select(aim_ctx* ctx, int kind);
  * autotuner's choice. */
 int aim_gemv_plan(aim_ctx* ctx, int kind, int ctas_per_sm, int split, int unroll);
 
+/* Schedule of the two internal products in the system matvec (e = Z h and j = h - C h, C =
+ * Y_eq Z; the GPU counterpart of the paper's placement of the internal workload beside the
+ * external one, Sec. III-C): mode 0 = e beside j's GEMV with the tuned few-CTA launch, 1 = e
+ * beside the AIM chain of j once j is out, 2 = e on the main stream right after j's GEMV with
+ * j's launch, 3 = both in one paired task-list launch (in j's launch shape when that is a
+ * task list, else 8-row tasks on 8 warps), -1 = the set-up schedule tuner's choice. Drops the
+ * captured matvec graphs; BEM_EINVAL for a mode out of range (or 3 when the set-up built no
+ * paired plan). aim_info does not report it; aim_export item 8 holds the tuner's timings. */
+int aim_matvec_schedule(aim_ctx* ctx, int mode);
+
 /* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)
  * or AIM_OP_SYSTEM (the SLIM system of Eq. AEFIEoutJ, vectors of N_E + N_T):
  *   e = Z h, h_eq = Y e, j = h - h_eq,

@@ -74,6 +74,7 @@ def lib():
         L.aim_matvec.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
         L.aim_gemv_select.argtypes = [vp, C.c_int]
         L.aim_gemv_plan.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.aim_matvec_schedule.argtypes = [vp, C.c_int]
         L.bem_port_ring.argtypes = [vp, C.c_int, C.c_int, d, d, C.POINTER(i32), C.POINTER(d), C.c_int]
         L.bem_rhs_port.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), d, vp, C.c_int, vp]
         L.bem_port_current.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), vp, C.c_int,
@@ -272,6 +273,10 @@ class Context:
         """Set the FP32 block-GEMV launch explicitly (see aim_gemv_plan)."""
         _check(lib().aim_gemv_plan(self.h, int(kind), int(ctas_per_sm), int(split), int(unroll)))
         self._read_info()
+
+    def matvec_schedule(self, mode=-1):
+        """Schedule of e = Z h in the system matvec (see aim_matvec_schedule; -1 = tuned)."""
+        _check(lib().aim_matvec_schedule(self.h, int(mode)))
 
     def gemv_select(self, kind):
         """FP32 block-GEMV launch: 0 autotuned choice, 1 best plain, 2 best bulk-copy staged."""

@@ -125,6 +125,8 @@ int aim_gemv_select(aim_ctx* c, int kind) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old launches
   c->graphs.clear();
   c->gplan = p;
+  // the paired launch holds the autotuned shape: another choice runs e = Z h after j's GEMV
+  c->z_after = kind != 0 && c->z_tuned == 3 ? 2 : c->z_tuned;
   return BEM_OK;
 }
 
@@ -134,6 +136,20 @@ int aim_gemv_plan(aim_ctx* c, int kind, int ctas_per_sm, int split, int unroll) 
   BEM_TRY(set_gemv_shape(c, kind, ctas_per_sm, split, unroll));
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old launches
   c->graphs.clear();
+  if (c->z_tuned == 3) c->z_after = 2;  // the paired launch holds the autotuned shape
+  return BEM_OK;
+}
+
+int aim_matvec_schedule(aim_ctx* c, int mode) {
+  BEM_TRY(check_ctx(c, "aim_matvec_schedule"));
+  if (mode < -1 || mode > 3 || (mode == 3 && c->gpair.ntasks == 0)) {
+    set_error("aim_matvec_schedule: mode must be -1..3 (3 needs the paired plan of the set-up)");
+    return BEM_EINVAL;
+  }
+  BEM_CUDA(cudaDeviceSynchronize());
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old schedule
+  c->graphs.clear();
+  c->z_after = mode < 0 ? c->z_tuned : mode;
   return BEM_OK;
 }
 

@@ -129,6 +129,7 @@ struct GemvTask {  // a run of rows of one block
   int32_t ld;
   int32_t row0;
   int32_t nrows;
+  int32_t sel;     // paired launch: 0 = first matrix (y0, minus from hsub), 1 = second (y1)
 };
 
 struct RowInfo {   // one row of the block-diagonal matrix (global row = output index)
@@ -241,6 +242,7 @@ struct aim_ctx {
   bem::GemvPlan gplan;    // FP32 products (autotuned; may use bulk-copy staging)
   bem::GemvPlan gplan64;  // FP64 products
   bem::GemvPlan gbg32, gbg64;  // e = Z h beside the AIM chain in the system matvec (few CTAs)
+  bem::GemvPlan gpair;         // j = h - C h and e = Z h as one task list (both precisions)
   bem::GemvPlan gplan_auto;    // the autotuner's FP32 choice
   bem::GemvPlan gplan_alt[2];  // best plain and best staged FP32 plans (ncta = 0: none)
   float tune_ms[2] = {0, 0};  // autotuner: best plain, best staged candidate (5 launches, ms)
@@ -275,7 +277,9 @@ struct aim_ctx {
   cudaStream_t cap = nullptr, side = nullptr, zside = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr, ev_c = nullptr;
   int z_after = 0;  // e = Z h: 0 beside j's GEMV, 1 beside the AIM chain once j = h - C h is
-                    // out, 2 on the main stream after j's GEMV with the whole GPU
+                    // out, 2 on the main stream after j's GEMV with the whole GPU, 3 in one
+                    // launch with j's GEMV (gpair)
+  int z_tuned = 0;  // the schedule tuner's choice of z_after
   struct GKey {
     int which, prec;
     const void* x;
@@ -332,6 +336,10 @@ template <typename R>
 int run_gemv(const GemvTask* d_tasks, int ntasks, const typename C2<R>::T* A,
              const typename C2<R>::T* x, typename C2<R>::T* y, int nrhs, int64_t vstride,
              const typename C2<R>::T* hsub, cudaStream_t s);
+template <typename R>
+int run_gemv_pair(const GemvPlan& p, const typename C2<R>::T* A0, const typename C2<R>::T* A1,
+                  const typename C2<R>::T* x, typename C2<R>::T* y0, typename C2<R>::T* y1,
+                  const typename C2<R>::T* hsub, cudaStream_t s);
 template <typename R>
 int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
                   typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,

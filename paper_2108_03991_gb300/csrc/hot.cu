@@ -115,6 +115,63 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_gemv(const GemvTask* __restri
   }
 }
 
+// Paired task list: two block-diagonal matrices of the same layout applied to one x in one
+// launch; a task with sel = 0 computes y0 = hsub - A0 x (or A0 x) on its rows, sel = 1
+// computes y1 = A1 x. One right-hand side.
+template <typename R, int U, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_gemv_pair(const GemvTask* __restrict__ tasks,
+                                                           const typename C2<R>::T* __restrict__ A0,
+                                                           const typename C2<R>::T* __restrict__ A1,
+                                                           const typename C2<R>::T* __restrict__ x,
+                                                           typename C2<R>::T* __restrict__ y0,
+                                                           typename C2<R>::T* __restrict__ y1,
+                                                           const typename C2<R>::T* __restrict__ hsub) {
+  typedef typename C2<R>::T V;
+  const GemvTask t = tasks[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const V* A = t.sel ? A1 : A0;
+  V* y = t.sel ? y1 : y0;
+  const V* hs = t.sel ? nullptr : hsub;
+  const V* xb = x + t.xoff;
+  for (int rr = warp; rr < t.nrows; rr += NW) {
+    const int row = t.row0 + rr;
+    V acc[1];
+    row_dot<R, 1, U>(A + t.aoff + (int64_t)row * t.ld, xb, t.n, 0, lane, acc);
+    if (lane == 0) {
+      const int64_t o = t.xoff + row;
+      y[o] = hs ? csub(hs[o], acc[0]) : acc[0];
+    }
+  }
+}
+
+template <typename R>
+int run_gemv_pair(const GemvPlan& p, const typename C2<R>::T* A0, const typename C2<R>::T* A1,
+                  const typename C2<R>::T* x, typename C2<R>::T* y0, typename C2<R>::T* y1,
+                  const typename C2<R>::T* hsub, cudaStream_t s) {
+  if (p.ntasks == 0) return BEM_OK;
+  if (p.unroll == 8) {
+    k_gemv_pair<R, 8, 8, 0><<<p.ntasks, 256, 0, s>>>(p.tasks, A0, A1, x, y0, y1, hsub);
+  } else if constexpr (sizeof(R) == 8) {  // FP64 needs more than 32 registers
+    if (p.task_form == 2)
+      k_gemv_pair<R, 4, 4, 0><<<p.ntasks, 128, 0, s>>>(p.tasks, A0, A1, x, y0, y1, hsub);
+    else
+      k_gemv_pair<R, 4, 8, 0><<<p.ntasks, 256, 0, s>>>(p.tasks, A0, A1, x, y0, y1, hsub);
+  } else {
+    if (p.task_form == 0)
+      k_gemv_pair<R, 4, 8, 0><<<p.ntasks, 256, 0, s>>>(p.tasks, A0, A1, x, y0, y1, hsub);
+    else if (p.task_form == 1)
+      k_gemv_pair<R, 4, 8, 8><<<p.ntasks, 256, 0, s>>>(p.tasks, A0, A1, x, y0, y1, hsub);
+    else
+      k_gemv_pair<R, 4, 4, 16><<<p.ntasks, 128, 0, s>>>(p.tasks, A0, A1, x, y0, y1, hsub);
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int run_gemv_pair<float>(const GemvPlan&, const float2*, const float2*, const float2*,
+                                  float2*, float2*, const float2*, cudaStream_t);
+template int run_gemv_pair<double>(const GemvPlan&, const double2*, const double2*, const double2*,
+                                   double2*, double2*, const double2*, cudaStream_t);
+
 // Dynamic task list: ncta persistent CTAs take the tasks in list order from a counter (the
 // largest blocks first, as in LPT), so a launch of few CTAs per SM still balances like the
 // one-CTA-per-task form. The CTA that finishes last sets the counters back to zero for the
@@ -717,37 +774,41 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x, nt,
                                           nx, ny, y);
   } else if (which == AIM_OP_SYSTEM) {
-    // Three branches. With C = Y_eq Z formed at set-up (Eq. EFIEeqYZ), j = h - C h and e = Z h
-    // are independent: the main stream runs j and its AIM chain (projection, convolution,
-    // rows); e = Z h streams beside it with few CTAs (it is needed only by the last kernel,
-    // for I_x e); the charge branch p = L^Phi q runs on the side stream, followed there by
-    // the near region L^A_NR j once j is out, so that only the interpolation and the
-    // combination follow the convolution.
+    // With C = Y_eq Z formed at set-up (Eq. EFIEeqYZ), j = h - C h and e = Z h are
+    // independent. The main stream runs j and its AIM chain (projection, convolution, rows);
+    // e = Z h (needed only by the last kernel, for I_x e) runs, as the set-up schedule tuner
+    // chose, beside j's GEMV or beside the chain with few CTAs (z_after 0 or 1), after j's
+    // GEMV on the main stream (2), or in one launch with j's GEMV (3). The charge branch
+    // p = L^Phi q runs on the side stream, followed there by the near region L^A_NR j once j is
+    // out, so that only the interpolation and the combination follow the convolution.
     const V* h = x;
     const V* q = x + ne;
     V* sq = b.sigma + 3 * ng;
     BEM_CUDA(cudaEventRecord(c->ev_fork, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    if (c->z_after != 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
+    if (c->z_after < 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
                                                 nt, nx, ny, b.p);
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
-    BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
+    if (c->z_after == 3)  // j = h - C h and e = Z h in one launch
+      BEM_TRY(run_gemv_pair<R>(c->gpair, b.C, b.Z, h, b.j, b.e, h, s));
+    else
+      BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
     BEM_CUDA(cudaEventRecord(c->ev_c, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
     k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.j, ne, b.anear);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     if (c->z_after == 2) {  // e = Z h right after j's GEMV on the main stream, whole GPU
       BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
-    } else {
+    } else if (c->z_after != 3) {
       if (c->z_after)  // e = Z h once j is out, beside the AIM chain only
         BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_c, 0));
       BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
     }
-    BEM_CUDA(cudaEventRecord(c->ev_z, c->z_after == 2 ? s : c->zside));
+    BEM_CUDA(cudaEventRecord(c->ev_z, c->z_after >= 2 ? s : c->zside));
     project_e<R>(c, b.WAT, b.j, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));

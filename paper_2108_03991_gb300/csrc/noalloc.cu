@@ -93,6 +93,7 @@ extern "C" int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void
       t.ld = ld;
       t.row0 = r0;
       t.nrows = std::min(kNoAllocRows, n[i] - r0);
+      t.sel = 0;
     }
     off += (int64_t)n[i] * ld;
     xoff += n[i];

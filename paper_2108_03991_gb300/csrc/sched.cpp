@@ -111,6 +111,7 @@ void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>&
         t.ld = ld[i];
         t.row0 = r0;
         t.nrows = std::min(kRowsPerTask, b - r0);
+        t.sel = 0;
         tasks->push_back(t);
       }
     }

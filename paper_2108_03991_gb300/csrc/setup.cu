@@ -754,16 +754,37 @@ int tune_matvec_schedule(aim_ctx* c) {
   GemvCand best_g{1, 2, 1, 8};
   int best_after = 0;
   int rc = BEM_OK;
-  // the last entry stands for the serial schedule (e = Z h after j's GEMV, with its launch)
+  // the paired task list (C tasks, then Z tasks) in j's launch shape when that is a task list,
+  // else in the 8-row, 8-warp shape
+  c->gpair = GemvPlan();
+  {
+    const bool tl = c->gplan.ntasks > 0 && !c->gplan.ctr;
+    GemvPlan p;
+    if (tl) p = c->gplan;
+    else BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 8, 1, 4}, nsm, n, c->zoff, c->zld, derr, &p));
+    std::vector<int32_t> xo(n.size());
+    for (size_t i = 0, acc = 0; i < n.size(); acc += n[i], ++i) xo[i] = (int32_t)acc;
+    std::vector<GemvTask> t1;
+    build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, (p.task_form == 2 ? 4 : 8) * p.split, &t1);
+    std::vector<GemvTask> t2 = t1;
+    for (GemvTask& t : t2) t.sel = 1;
+    t1.insert(t1.end(), t2.begin(), t2.end());
+    BEM_TRY(upload(c, &p.tasks, t1.data(), t1.size()));
+    p.ntasks = p.ncta = (int)t1.size();
+    c->gpair = p;
+  }
+  // the last two entries stand for the serial schedules (e = Z h after j's GEMV with its
+  // launch shape; both in one paired launch)
   const GemvCand zc[] = {{1, 1, 1, 8}, {1, 2, 1, 8}, {1, 3, 1, 8}, {6, 2, 2, 4}, {6, 3, 2, 4}, {6, 4, 2, 4},
-                         {1, 2, 1, 8}};
+                         {1, 2, 1, 8}, {1, 2, 1, 8}};
   const int nzc = (int)(sizeof(zc) / sizeof(zc[0]));
   for (int gi = 0; gi < nzc; ++gi) {
     const GemvCand& g = zc[gi];
     GemvPlan p;
     if ((rc = make_gemv_plan(c, nullptr, g, nsm, n, c->zoff, c->zld, derr, &p)) != BEM_OK) break;
-    for (int after : {0, 1, 2}) {
-      if ((after == 2) != (gi == nzc - 1)) continue;
+    for (int after : {0, 1, 2, 3}) {
+      const int want = gi == nzc - 1 ? 3 : gi == nzc - 2 ? 2 : -1;
+      if (want >= 0 ? after != want : after >= 2) continue;
       c->gbg32 = c->gbg64 = p;
       c->z_after = after;
       for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -776,8 +797,8 @@ int tune_matvec_schedule(aim_ctx* c) {
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
-      c->tune_table.insert(c->tune_table.end(), {4.f, after == 2 ? 0.f : (float)g.cps, (float)after,
-                                                 after == 2 ? (float)(c->gplan.ctr ? 6 : c->gplan.ntasks ? 5 : 1) : (float)g.kind,
+      c->tune_table.insert(c->tune_table.end(), {4.f, after >= 2 ? 0.f : (float)g.cps, (float)after,
+                                                 after >= 2 ? (float)(c->gplan.ctr ? 6 : c->gplan.ntasks ? 5 : 1) : (float)g.kind,
                                                  ms * 1e6f / 20.f});
       if (ms < best) { best = ms; best_g = g; best_after = after; }
     }
@@ -791,7 +812,7 @@ int tune_matvec_schedule(aim_ctx* c) {
   if (rc != BEM_OK) return rc;
   BEM_TRY(make_gemv_plan(c, nullptr, best_g, nsm, n, c->zoff, c->zld, derr, &c->gbg32));
   c->gbg64 = c->gbg32;
-  c->z_after = best_after;
+  c->z_after = c->z_tuned = best_after;
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }

@@ -198,6 +198,22 @@ def test_gemv_kinds_match_oracle(prob, kind):
         ctx.gemv_select(0)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_matvec_schedules_match_oracle(prob, mode):
+    """Every schedule of the two internal products in the system matvec (e beside j's GEMV,
+    beside the AIM chain, after j's GEMV, one paired launch; the last with the task-list GEMV)
+    gives the oracle's product, in both precisions."""
+    ctx, S = prob["ctx"], prob["S"]
+    try:
+        ctx.matvec_schedule(mode)
+        x = synth.rand_cvec(ctx.n, 71)
+        for prec, dt, tol in [(api.BEM_C32, np.complex64, 1e-5), (api.BEM_C64, np.complex128, 1e-7)]:
+            y = ctx.matvec(torch.from_numpy(x.astype(dt)).cuda(), prec=prec)
+            assert rel(y.cpu().numpy(), S.matvec(x)) < tol
+    finally:
+        ctx.matvec_schedule(-1)
+
+
 @pytest.mark.parametrize("shape", [(6, 2, 1, 4), (6, 3, 2, 8)])
 def test_dynamic_task_list_relaunch(prob, shape):
     """The dynamic task list (persistent CTAs taking tasks from a counter that the last CTA sets
