@@ -272,6 +272,20 @@ typedef struct {
 int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
               bem_solve_info* info, void* stream);
 
+/* Port admittance matrix: for each port q, the solve (bem_solve with opts) of a unit gap
+ * voltage on q with the other ports shorted, then the currents of every port p:
+ * Y[p][q] = I_p / V_q in siemens (the paper's port excitation, Sec. II; its S-parameter and
+ * impedance outputs follow from Y). Ports are given as rings (bem_port_ring): ring_n[p] edges
+ * each, edges and signs HOST arrays holding the rings one after another. Y: HOST
+ * [nport][nport] complex doubles (re, im interleaved); infos: HOST [nport] (or NULL), the
+ * solve information of each column. Allocates two device vectors of N_E + N_T complex doubles
+ * for the call; synchronises the stream. Returns BEM_OK, BEM_ENOCONV when a solve stopped
+ * before tol (Y is still filled), or a negative error (BEM_EINVAL for an empty port or an edge
+ * out of range). */
+int bem_port_matrix(aim_ctx* ctx, int nport, const int32_t* ring_n, const int32_t* edges,
+                    const double* signs, const bem_solve_opts* opts, double* Y,
+                    bem_solve_info* infos, void* stream);
+
 /* Learned correction of the preconditioner (an extension; not in the paper). A 4-layer 3-D
  * convolutional net on the AIM grid (3x3x3 kernels, zero padding, no biases, ReLU between
  * layers, channels 8-16-16-16-8; BF16 weights and activations, FP32 sums) maps the projected

@@ -89,6 +89,8 @@ def lib():
         L.aim_export.restype = i64
         L.bem_rhs_plane_wave.argtypes = [vp, C.POINTER(d), C.POINTER(d), vp, C.c_int, vp]
         L.bem_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+        L.bem_port_matrix.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(i32), C.POINTER(d),
+                                      C.POINTER(SolveOpts), C.POINTER(d), C.POINTER(SolveInfo), vp]
         L.bem_precond_apply.argtypes = [vp, vp, vp, C.c_int, vp]
         fp = C.POINTER(C.c_float)
         L.bem_net_init.argtypes = [vp, C.c_uint64]
@@ -259,6 +261,23 @@ class Context:
                                       s.ctypes.data_as(C.POINTER(C.c_double)), _ptr(x, cdtype(prec)),
                                       prec, out, _stream()))
         return complex(out[0], out[1])
+
+    def port_matrix(self, rings, tol=1e-6, restart=100, max_iter=1000, prec_mode=BEM_C64,
+                    precond=1, time_limit_s=0.0):
+        """Port admittance matrix Y [nport, nport] (siemens) from one solve per port (unit gap
+        voltage, the others shorted; see bem_port_matrix). rings: [(edges, signs), ...] from
+        port_ring. Returns (Y, status, [iterations per column])."""
+        n = np.array([len(e) for e, _ in rings], dtype=np.int32)
+        e = np.ascontiguousarray(np.concatenate([np.asarray(e) for e, _ in rings]), dtype=np.int32)
+        s = np.ascontiguousarray(np.concatenate([np.asarray(s) for _, s in rings]), dtype=np.float64)
+        o = SolveOpts(tol, restart, max_iter, prec_mode, int(precond), time_limit_s)
+        infos = (SolveInfo * len(n))()
+        Y = np.zeros((len(n), len(n), 2))
+        rc = _check(lib().bem_port_matrix(self.h, len(n), n.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          e.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          s.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o),
+                                          Y.ctypes.data_as(C.POINTER(C.c_double)), infos, _stream()))
+        return Y[..., 0] + 1j * Y[..., 1], rc, [inf.iters for inf in infos]
 
     def farfield(self, x, rhat, prec=BEM_C64):
         """Radiation vector N(rhat) [ndir, 3] (complex) of the solution x = [h; q]."""

@@ -241,6 +241,61 @@ int bem_port_current(aim_ctx* c, int n, const int32_t* edges, const double* sign
   return BEM_OK;
 }
 
+int bem_port_matrix(aim_ctx* c, int nport, const int32_t* ring_n, const int32_t* edges,
+                    const double* signs, const bem_solve_opts* opts, double* Y,
+                    bem_solve_info* infos, void* stream) {
+  if (!c || nport < 1 || !ring_n || !edges || !signs || !opts || !Y) {
+    set_error("bem_port_matrix: bad arguments");
+    return BEM_EINVAL;
+  }
+  std::vector<int64_t> off(nport + 1, 0);
+  for (int p = 0; p < nport; ++p) {
+    if (ring_n[p] < 1) {
+      set_error("bem_port_matrix: port %d has no edges", p);
+      return BEM_EINVAL;
+    }
+    off[p + 1] = off[p] + ring_n[p];
+  }
+  for (int p = 0; p < nport; ++p)
+    BEM_TRY(check_edges(c, ring_n[p], edges + off[p], signs + off[p], "bem_port_matrix"));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = (int64_t)c->ne + c->nt;
+  double2 *b = nullptr, *x = nullptr;
+  BEM_CUDA(cudaMalloc((void**)&b, N * sizeof(double2)));
+  if (cudaMalloc((void**)&x, N * sizeof(double2)) != cudaSuccess) {
+    cudaFree(b);
+    set_error("bem_port_matrix: out of device memory");
+    return BEM_ENOMEM;
+  }
+  int worst = BEM_OK;
+  for (int q = 0; q < nport && worst >= 0; ++q) {
+    // unit gap voltage on port q, the others shorted; Y_pq = I_p / V_q
+    int rc = bem_rhs_port(c, ring_n[q], edges + off[q], signs + off[q], 1.0, b, BEM_C64, stream);
+    if (rc == BEM_OK && cudaMemsetAsync(x, 0, N * sizeof(double2), s) != cudaSuccess) rc = BEM_ECUDA;
+    bem_solve_info info{};
+    if (rc == BEM_OK) rc = bem_solve(c, b, x, opts, &info, stream);
+    if (rc < 0) {
+      worst = rc;
+      break;
+    }
+    worst = std::max(worst, rc);
+    if (infos) infos[q] = info;
+    for (int p = 0; p < nport && worst >= 0; ++p) {
+      double cur[2];
+      const int r2 = bem_port_current(c, ring_n[p], edges + off[p], signs + off[p], x, BEM_C64, cur, stream);
+      if (r2 != BEM_OK) {
+        worst = r2;
+        break;
+      }
+      Y[2 * (p * nport + q)] = cur[0];
+      Y[2 * (p * nport + q) + 1] = cur[1];
+    }
+  }
+  cudaFree(b);
+  cudaFree(x);
+  return worst;
+}
+
 int bem_farfield(aim_ctx* c, const void* x, int prec, int ndir, const double* rhat, double* nvec,
                  void* stream) {
   if (!c || !x || !rhat || !nvec || ndir < 1 || ndir > 65535 || (prec != BEM_C32 && prec != BEM_C64)) {

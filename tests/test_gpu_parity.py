@@ -332,3 +332,38 @@ def test_errors_are_reported(dev):
     with pytest.raises(api.BemError) as ei:
         api.Context(bad, synth.grid_box(bad, 0.5), 10e9)
     assert ei.value.code == -2
+
+
+# ---------------------------------------------------------------------------------------
+# degenerate cases: one conductor, a zero right-hand side, a solve that starts converged
+# ---------------------------------------------------------------------------------------
+def test_single_object_matvec_and_zero_rhs(dev):
+    """One conductor (one internal block, no inter-object coupling in the preconditioner): the
+    system matvec matches the oracle in both precisions; a zero right-hand side returns x = 0
+    with status OK and no iteration; a solve started from the converged x returns at once with
+    its true residual."""
+    mesh = synth.small_bars(1, 2.0)
+    grid = synth.grid_box(mesh, 0.5)
+    freq = 10e9
+    ctx = api.Context(mesh, grid, freq)
+    rw = from_mesh(mesh)
+    A = oaim.Aim(rw, grid.origin, grid.h, grid.n, op.k0_of(freq)).build_near()
+    Zs, Ys = op.internal_blocks(rw, freq, mesh.sigma)
+    S = op.SlimSystem(rw, freq, Zs, Ys, A.LA, A.LPhi)
+    assert ctx.nobj == 1
+    x = synth.rand_cvec(ctx.n, 80)
+    for prec, dt, tol in [(api.BEM_C32, np.complex64, 1e-5), (api.BEM_C64, np.complex128, 1e-7)]:
+        y = ctx.matvec(torch.from_numpy(x.astype(dt)).cuda(), prec=prec)
+        assert rel(y.cpu().numpy(), S.matvec(x)) < tol
+    zero = torch.zeros(ctx.n, dtype=torch.complex128, device=dev)
+    x0, info = ctx.solve(zero, tol=1e-6, restart=20, max_iter=50, prec_mode=api.BEM_C32, precond=1)
+    assert info["status"] == api.BEM_OK and info["iters"] == 0
+    assert torch.count_nonzero(x0).item() == 0
+    b = ctx.rhs_plane_wave(prec=api.BEM_C64)
+    xs, info = ctx.solve(b, tol=1e-6, restart=50, max_iter=200, prec_mode=api.BEM_C32, precond=1)
+    assert info["status"] == api.BEM_OK and info["resid_true"] <= 1e-6
+    xs2, info2 = ctx.solve(b, x=xs.clone(), tol=1e-6, restart=50, max_iter=200,
+                           prec_mode=api.BEM_C32, precond=1)
+    assert info2["status"] == api.BEM_OK and info2["iters"] == 0
+    assert info2["resid_true"] <= 1e-6
+    ctx.close()

@@ -87,6 +87,21 @@ def test_two_port_admittance(bar, mode, tol, rtol):
     assert abs(Yd[0, 1] - Yd[1, 0]) <= 2e-3 * abs(Yd[0, 1])
 
 
+@pytest.mark.parametrize("mode,tol,rtol", [(api.BEM_C64, 1e-10, 1e-5), (api.BEM_C32, 1e-6, 1e-4)])
+def test_port_matrix_matches_oracle(bar, mode, tol, rtol):
+    """bem_port_matrix (one device solve per port, currents of every port) against the oracle's
+    dense solves: Y in siemens is the oracle's admittance (gap voltage eta0 * 1e-6 volts, current
+    in amperes / 1e-6) divided by eta0."""
+    ctx = bar["ctx"]
+    Yo = _oracle_admittance(bar) / op.ETA0
+    Y, rc, iters = ctx.port_matrix([(e, s) for e, s in bar["rings"]], tol=tol, restart=100,
+                                   max_iter=500, prec_mode=mode, precond=1)
+    assert rc == api.BEM_OK and len(iters) == 2 and min(iters) > 0
+    assert np.max(np.abs(Y - Yo)) / np.max(np.abs(Yo)) < rtol
+    with pytest.raises(api.BemError):
+        ctx.port_matrix([(np.array([ctx.ne], dtype=np.int32), np.array([1.0]))])
+
+
 @pytest.mark.parametrize("prec,tol", [(api.BEM_C64, 1e-6), (api.BEM_C32, 1e-5)])
 def test_farfield_matches_oracle(bar, prec, tol):
     """Radiation vector of J_Delta for a random x = [h; q], several directions. The FP64 bound
