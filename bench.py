@@ -507,9 +507,12 @@ def main():
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
         value = replicas_value(ms, world)
-        # per system matvec: the GEMV of j (with a y-initialising launch in the stream form),
-        # the GEMV of e, 2 projections, 2 x 3 FFT passes, the near region of j, 2 row kernels
-        launches_per_step = 11 + (2 if ctx.gemv_kind == 3 else 1) + 1
+        # per system matvec: 2 projections, 2 x 3 FFT passes, the near region of j, 2 row
+        # kernels, and the internal GEMVs: one paired launch (schedule 3), else the GEMV of j
+        # and that of e (with a y-initialising launch each in the stream form, schedule 2)
+        stream_init = 1 if ctx.gemv_kind == 3 else 0
+        launches_per_step = 11 + (1 if ctx.matvec_mode == 3 else
+                                  2 + stream_init * (2 if ctx.matvec_mode == 2 else 1))
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -537,6 +540,7 @@ def main():
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
                                     "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
                                                        for r in ctx.gemv_tune_table() if r[0] != 4],
+                                    "matvec_schedule": ctx.matvec_mode,
                                     "matvec_schedules": [[int(v) for v in r[1:4]] + [float(r[4])]
                                                          for r in ctx.gemv_tune_table() if r[0] == 4]}},
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,

@@ -102,7 +102,8 @@ const char* bem_last_error(void);
  * blocks once they are built), [19]=kind of the chosen FP32 launch (0 row plan, 1 flat, 2
  * bulk-copy staged, 3 stream, 5 the modified Part_Schedule's task list, 6 the same tasks taken
  * in turn by persistent CTAs), [20]=CTAs per SM of that launch's shape (for the task list:
- * 4, 8 or 16, the variant). Writes min(n, 21) entries. */
+ * 4, 8 or 16, the variant), [21]=schedule of the internal products in the system matvec
+ * (aim_matvec_schedule modes 0-3). Writes min(n, 22) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the
@@ -133,7 +134,7 @@ int aim_gemv_plan(aim_ctx* ctx, int kind, int ctas_per_sm, int split, int unroll
  * j's launch, 3 = both in one paired task-list launch (in j's launch shape when that is a
  * task list, else 8-row tasks on 8 warps), -1 = the set-up schedule tuner's choice. Drops the
  * captured matvec graphs; BEM_EINVAL for a mode out of range (or 3 when the set-up built no
- * paired plan). aim_info does not report it; aim_export item 8 holds the tuner's timings. */
+ * paired plan). aim_info entry 21 reports it; aim_export item 8 holds the tuner's timings. */
 int aim_matvec_schedule(aim_ctx* ctx, int mode);
 
 /* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)

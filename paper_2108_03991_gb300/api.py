@@ -211,8 +211,8 @@ class Context:
         self._read_info()
 
     def _read_info(self):
-        info = (C.c_int64 * 21)()
-        _check(lib().aim_info(self.h, info, 21))
+        info = (C.c_int64 * 22)()
+        _check(lib().aim_info(self.h, info, 22))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -227,6 +227,7 @@ class Context:
         self.gemv_tune_rejected = info[18]
         self.gemv_kind = info[19]  # 0 row plan, 1 flat, 2 staged, 3 stream, 5 and 6 task lists
         self.gemv_cps = info[20]
+        self.matvec_mode = info[21]  # schedule of e = Z h (aim_matvec_schedule)
 
     # ---- ports and far field ---------------------------------------------------------
     def port_ring(self, obj, axis, coord, tol=1e-6):
@@ -296,6 +297,7 @@ class Context:
     def matvec_schedule(self, mode=-1):
         """Schedule of e = Z h in the system matvec (see aim_matvec_schedule; -1 = tuned)."""
         _check(lib().aim_matvec_schedule(self.h, int(mode)))
+        self._read_info()
 
     def gemv_select(self, kind):
         """FP32 block-GEMV launch: 0 autotuned choice, 1 best plain, 2 best bulk-copy staged."""

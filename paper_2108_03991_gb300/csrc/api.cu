@@ -99,13 +99,13 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
   for (int i = 0; i < c->nobj; ++i) maxn = std::max(maxn, c->e1[i] - c->e0[i]);
   auto ns = [](float ms5) -> int64_t { return ms5 < 1e29f ? (int64_t)(ms5 * 1e6f / 5.f) : -1; };
   const int kind = c->gplan.tma ? 2 : c->gplan.stream ? 3 : c->gplan.flat ? 1 : c->gplan.ctr ? 6 : c->gplan.ntasks ? 5 : 0;
-  int64_t v[21] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
+  int64_t v[22] = {c->ne, c->nt, c->nobj, c->gn[0], c->gn[1], c->gn[2], c->gp[0], c->gp[1], c->gp[2],
                    c->rowA.empty() ? 0 : c->rowA.back(), c->rowP.empty() ? 0 : c->rowP.back(),
                    2 * c->zelems * 8, maxn, c->gplan.ncta,
                    c->gplan.tma ? -c->gplan.nstage : kind != 0 && kind < 5 ? 0 : c->gplan.split,
                    c->gplan.tma ? 0 : c->gplan.unroll, ns(c->tune_ms[0]), ns(c->tune_ms[1]),
-                   c->tune_rejected, kind, c->gplan.cps};
-  for (int i = 0; i < n && i < 21; ++i) info[i] = v[i];
+                   c->tune_rejected, kind, c->gplan.cps, c->z_after};
+  for (int i = 0; i < n && i < 22; ++i) info[i] = v[i];
   return BEM_OK;
 }
 
