@@ -231,6 +231,46 @@ def square_loop(side, w, t, a, sigma=SIGMA_CU) -> Mesh:
     return merge([(V, F)], [sigma])
 
 
+def trace_batch(seed=0, ntrace=256, widths=(1.0, 4.0), lengths=(10.0, 200.0), gap=3.0, a=0.5,
+                sigma=SIGMA_CU):
+    """Independent copper interconnects in one structure (the batched workload): seeded straight
+    and L-shaped traces of square cross-section w x w, w uniform in `widths` rounded to the mesh
+    step a, centreline length lognormal clipped to `lengths` (rounded to a), laid side by side
+    along y with `gap` um between their bounding boxes, meshed with a x a squares (voxel_surface).
+    Each trace has two lumped ports, rings 1 um (or a quarter of the arm) in from its free ends.
+    Returns the mesh and, per trace, [(axis, coord), (axis, coord)] of its port planes."""
+    rng = np.random.default_rng(seed)
+    parts, ports = [], []
+    y0 = 0.0
+    for _ in range(ntrace):
+        w = max(a, round(rng.uniform(*widths) / a) * a)
+        L = float(np.clip(np.exp(rng.uniform(np.log(lengths[0]), np.log(lengths[1]))), *lengths))
+        L = max(4 * w, round(L / a) * a)
+        lshape = bool(rng.integers(2))
+        m, n = round(w / a), round(L / a)
+        if lshape:  # arm 1 along x, arm 2 along +y from its far end, each about L / 2 long
+            n1 = max(2 * m, n // 2)
+            n2 = max(2 * m, n - n1)
+            solid = np.zeros((n1, n2, m), dtype=bool)
+            solid[:, :m, :] = True
+            solid[n1 - m:, :, :] = True
+        else:
+            solid = np.ones((n, m, m), dtype=bool)
+        lo = (0.0, y0, 0.0)
+        V, F = voxel_surface(solid, a, lo)
+        parts.append((V, F))
+        inset1 = max(a, min(1.0, round(solid.shape[0] * a / 4 / a) * a))
+        p1 = (0, inset1)
+        if lshape:
+            inset2 = max(a, min(1.0, round(solid.shape[1] * a / 4 / a) * a))
+            p2 = (1, y0 + solid.shape[1] * a - inset2)
+        else:
+            p2 = (0, solid.shape[0] * a - inset1)
+        ports.append([p1, p2])
+        y0 += solid.shape[1] * a + gap
+    return merge(parts, [sigma] * ntrace), ports
+
+
 def copper_bar() -> tuple[Mesh, Grid, float]:
     """Copper bar 2x2x20 um, 0.5 um squares (1344 triangles, 2016 edges), 10 GHz,
     AIM grid spacing 0.5 um."""
