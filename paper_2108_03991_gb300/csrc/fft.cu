@@ -498,19 +498,19 @@ __global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg(V* ws, const V* __
   }
 }
 
-// z pass with the CTA's lines staged through shared memory: the nz data planes and the Ghat
-// column of the CTA's 8 * 32 / L adjacent x are read and written as contiguous runs of x
-// (one warp per line would touch 32 planes per load, a quarter of each sector), then each
-// line is transformed in registers as in k_zreg. Dynamic shared memory: NL (nz + 1) + NL (Pz + 1)
-// elements.
+// z pass with the CTA's lines staged through shared memory: the nz data planes of the CTA's
+// 8 * 32 / L adjacent x are read and written as contiguous runs of x (one warp per line would
+// touch 32 planes per load, a quarter of each sector), then each line is transformed in
+// registers as in k_zreg. Ghat comes from gz, the line's values already in the lanes' order
+// (lane l, register k1: frequency k1 + M brev(l)), so a warp reads it in whole sectors.
+// Dynamic shared memory: NL (nz + 1) elements.
 template <typename V, int L, int M>
-__global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg_st(V* ws, const V* __restrict__ ghat,
+__global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg_st(V* ws, const V* __restrict__ gz,
                                                             const V* __restrict__ twz, PlaneArgs a) {
   constexpr int G = 32 / L, NL = 8 * G;  // lines per warp, per CTA
   extern __shared__ unsigned char smem_raw[];
-  const int sp = a.nz + 1, gp = a.Pz + 1;
+  const int sp = a.nz + 1;
   V* S = reinterpret_cast<V*>(smem_raw);  // [NL][sp]: the line's data along z
-  V* Gs = S + NL * sp;                    // [NL][gp]: Ghat along the line's k
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lg = lane & (L - 1), xi = warp * G + lane / L;
   const int x0 = blockIdx.x * NL, y = blockIdx.y, c = blockIdx.z;
@@ -520,12 +520,6 @@ __global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg_st(V* ws, const V*
   for (int i = threadIdx.x; i < a.nz * NL; i += blockDim.x) {
     const int z = i / NL, l = i - z * NL;
     S[l * sp + z] = l < nlive ? base[z * plane + l] : czero<V>();
-  }
-  const int fy = min(y, a.Py - y);
-  for (int i = threadIdx.x; i < P * NL; i += blockDim.x) {
-    const int k = i / NL, l = i - k * NL, x = x0 + l;
-    Gs[l * gp + k] = l < nlive ? ghat[((int64_t)min(k, P - k) * a.gy + fy) * a.gx + min(x, a.Px - x)]
-                               : czero<V>();
   }
   __syncthreads();
   V v[M];
@@ -537,9 +531,11 @@ __global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg_st(V* ws, const V*
   V tk[M], ts[Log2<L>::v];
   reg_twiddles<V, L, M>(twz, P, lg, tk, ts);
   reg_fft_fwd<V, L, M>(v, twz, P, lg, tk, ts);
-  const int k2 = brev_l<L>(lg);
+  if (xi < nlive) {
+    const V* g = gz + ((int64_t)y * a.Px + x0 + xi) * P + lg;
 #pragma unroll
-  for (int k1 = 0; k1 < M; ++k1) v[k1] = cmul(v[k1], Gs[xi * gp + k1 + M * k2]);
+    for (int k1 = 0; k1 < M; ++k1) v[k1] = cmul(v[k1], g[k1 * L]);
+  }
   reg_fft_inv<V, L, M>(v, twz, P, lg, tk, ts);
   // each lane rewrites only the entries it read: no barrier before the write-back
 #pragma unroll
@@ -552,6 +548,20 @@ __global__ void __launch_bounds__(256, M <= 6 ? 4 : 1) k_zreg_st(V* ws, const V*
     const int z = i / NL, l = i - z * NL;
     if (l < nlive) base[z * plane + l] = S[l * sp + z];
   }
+}
+
+// gz[(y Px + x) Pz + k1 L + l] = Ghat(fz, fy, fx) at frequency k = k1 + M brev(l) of line (x, y)
+template <typename V, int L>
+__global__ void k_ghat_lines(const V* __restrict__ oct, int M, int Px, int Py, int Pz, V* gz) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)Px * Py * Pz) return;
+  const int r = (int)(idx % Pz);
+  const int64_t line = idx / Pz;
+  const int x = (int)(line % Px), y = (int)(line / Px);
+  const int l = r % L, k1 = r / L;
+  const int k = k1 + M * brev_l<L>(l);
+  const int fz = min(k, Pz - k), fy = min(y, Py - y), fx = min(x, Px - x);
+  gz[idx] = oct[((int64_t)fz * (Py / 2 + 1) + fy) * (Px / 2 + 1) + fx];
 }
 
 // plane passes in registers (one padded x-y plane per CTA of 256 threads, the x spectra of the
@@ -695,15 +705,15 @@ static bool reg_shape(int P, int* L, int* M) {
 
 template <typename V>
 static void launch_zreg(int L, int M, dim3 grid, cudaStream_t s, V* ws, const V* ghat,
-                        const V* tw, const PlaneArgs& a) {
+                        const V* gz, const V* tw, const PlaneArgs& a) {
   const int NL = 8 * (32 / L);
-  const size_t smem = (size_t)NL * ((a.nz + 1) + (a.Pz + 1)) * sizeof(V);
-  const bool staged = smem <= 48 * 1024;
-#define BEM_Z(LL, MM)                                                          \
-  if (L == LL && M == MM) {                                                    \
-    if (staged) k_zreg_st<V, LL, MM><<<grid, 256, smem, s>>>(ws, ghat, tw, a); \
-    else k_zreg<V, LL, MM><<<grid, 256, 0, s>>>(ws, ghat, tw, a);              \
-    return;                                                                    \
+  const size_t smem = (size_t)NL * (a.nz + 1) * sizeof(V);
+  const bool staged = gz && smem <= 48 * 1024;
+#define BEM_Z(LL, MM)                                                        \
+  if (L == LL && M == MM) {                                                  \
+    if (staged) k_zreg_st<V, LL, MM><<<grid, 256, smem, s>>>(ws, gz, tw, a); \
+    else k_zreg<V, LL, MM><<<grid, 256, 0, s>>>(ws, ghat, tw, a);            \
+    return;                                                                  \
   }
   BEM_REG_SHAPES(BEM_Z)
 #undef BEM_Z
@@ -893,7 +903,7 @@ int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename
     if constexpr (sizeof(V) == sizeof(float2)) {
       if (z_done) {
         const int per = 8 * (32 / zl);  // x lines per CTA
-        launch_zreg<V>(zl, zm, dim3((Px + per - 1) / per, Py, ncomp), s, ws, b.Ghat, b.tw[2], a);
+        launch_zreg<V>(zl, zm, dim3((Px + per - 1) / per, Py, ncomp), s, ws, b.Ghat, b.Gz, b.tw[2], a);
       }
     }
     if (!z_done)
@@ -1017,9 +1027,17 @@ int make_ghat(aim_ctx* c) {
   const int64_t no = (int64_t)(Px / 2 + 1) * (Py / 2 + 1) * (Pz / 2 + 1);
   if (rc == BEM_OK) rc = dalloc_t(c, &c->f64.Ghat, no);
   if (rc == BEM_OK) rc = dalloc_t(c, &c->f32.Ghat, no);
+  int zl = 0, zm = 0;
+  if (rc == BEM_OK && reg_shape(Pz, &zl, &zm)) rc = dalloc_t(c, &c->f32.Gz, P3);
   if (rc == BEM_OK) {
     k_ghat_oct<<<(unsigned)((no + 255) / 256), 256>>>(G, Px, Py, Pz, 1.0 / (double)P3, c->f64.Ghat,
                                                       c->f32.Ghat);
+    if (c->f32.Gz) {  // the register z pass's lane order of each line
+      const unsigned nb = (unsigned)((P3 + 255) / 256);
+      if (zl == 32) k_ghat_lines<float2, 32><<<nb, 256>>>(c->f32.Ghat, zm, Px, Py, Pz, c->f32.Gz);
+      else if (zl == 16) k_ghat_lines<float2, 16><<<nb, 256>>>(c->f32.Ghat, zm, Px, Py, Pz, c->f32.Gz);
+      else k_ghat_lines<float2, 8><<<nb, 256>>>(c->f32.Ghat, zm, Px, Py, Pz, c->f32.Gz);
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       set_error("make_ghat: %s", cudaGetErrorString(e));
