@@ -144,6 +144,16 @@ int aim_matvec_schedule(aim_ctx* ctx, int mode);
  * x and y must not alias. prec selects the arithmetic (BEM_C32 or BEM_C64). */
 int aim_matvec(aim_ctx* ctx, int which, const void* x, void* y, int prec, void* stream);
 
+/* y_i = A x_i for nvec vectors in HOST memory (x, y: nvec vectors of the operator's length,
+ * one after another; page-locked memory lets the copies run asynchronously): the products of
+ * aim_matvec, with the host-to-device copy of x_{i+1} and the device-to-host copy of y_{i-1}
+ * overlapping the product of x_i (two device buffer pairs kept by the context, two copy
+ * streams). Ordered after the work already on `stream`; the work on `stream` after the call
+ * waits for the last copy to the host, so synchronising `stream` makes y readable. x and y must
+ * not alias. Errors: BEM_EINVAL (bad pointers, nvec < 1, unknown operator), BEM_ENOMEM. */
+int aim_matvec_host(aim_ctx* ctx, int which, const void* x, void* y, int nvec, int prec,
+                    void* stream);
+
 /* The internal problem (Sec. II-B, Eqs. MFIEinZin, EFIEeqYeq): e = Z h, h_eq = Y e, for
  * nrhs right-hand sides stored one after another (each N_E long). heq may be NULL. */
 int internal_apply(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, int prec,

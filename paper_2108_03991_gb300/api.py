@@ -22,7 +22,9 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "internal_apply", "aim_conv", "bem_blockdiag_gemv", "aim_export",
            "bem_rhs_plane_wave", "bem_solve", "bem_part_schedule", "bem_blockdiag_gemv_noalloc",
            "bem_precond_apply", "bem_net_init", "bem_net_weights", "bem_net_train",
-           "bem_net_apply", "bem_convnet_run"]
+           "bem_net_apply", "bem_convnet_run", "aim_gemv_select", "aim_gemv_plan",
+           "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
+           "bem_port_current", "bem_port_matrix", "bem_farfield"]
 
 
 class BemError(RuntimeError):
@@ -75,6 +77,7 @@ def lib():
         L.aim_gemv_select.argtypes = [vp, C.c_int]
         L.aim_gemv_plan.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.aim_matvec_schedule.argtypes = [vp, C.c_int]
+        L.aim_matvec_host.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, vp]
         L.bem_port_ring.argtypes = [vp, C.c_int, C.c_int, d, d, C.POINTER(i32), C.POINTER(d), C.c_int]
         L.bem_rhs_port.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), d, vp, C.c_int, vp]
         L.bem_port_current.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), vp, C.c_int,
@@ -325,6 +328,24 @@ class Context:
             raise ValueError("vector length mismatch")
         _check(lib().aim_matvec(self.h, which, _ptr(x, cdtype(prec)), _ptr(y, cdtype(prec)), prec,
                                 _stream()))
+        return y
+
+    def matvec_host(self, x, y=None, which=AIM_OP_SYSTEM, prec=BEM_C32):
+        """y_i = A x_i for the rows of the host (CPU) tensor x [nvec, n], copies overlapped
+        with the products (aim_matvec_host); pin x and y for asynchronous copies. Ordered on the
+        current stream; synchronise it before reading y."""
+        import torch
+        n = {AIM_OP_LA: self.ne, AIM_OP_LPHI: self.nt, AIM_OP_SYSTEM: self.n}[which]
+        if x.device.type != "cpu" or x.dtype != cdtype(prec) or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CPU tensor of the precision's complex type")
+        if x.numel() % n:
+            raise ValueError("vector length mismatch")
+        if y is None:
+            y = torch.empty(x.shape, dtype=x.dtype, pin_memory=x.is_pinned())
+        if y.shape != x.shape or y.dtype != x.dtype or y.device.type != "cpu" or not y.is_contiguous():
+            raise ValueError("y must match x")
+        _check(lib().aim_matvec_host(self.h, which, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                     x.numel() // n, prec, _stream()))
         return y
 
     def internal(self, h, e=None, heq=None, nrhs=1, prec=BEM_C32, want_heq=True):

@@ -140,6 +140,76 @@ int aim_gemv_plan(aim_ctx* c, int kind, int ctas_per_sm, int split, int unroll) 
   return BEM_OK;
 }
 
+int aim_matvec_host(aim_ctx* c, int which, const void* x, void* y, int nvec, int prec, void* stream) {
+  BEM_TRY(check_ctx(c, "aim_matvec_host"));
+  BEM_TRY(check_prec(prec, "aim_matvec_host"));
+  if (!x || !y || x == y || nvec < 1) {
+    set_error("aim_matvec_host: x and y must be distinct host pointers and nvec >= 1");
+    return BEM_EINVAL;
+  }
+  const int64_t n = which == AIM_OP_LA ? c->ne : which == AIM_OP_LPHI ? c->nt
+                    : which == AIM_OP_SYSTEM ? (int64_t)c->ne + c->nt : -1;
+  if (n < 0) {
+    set_error("aim_matvec_host: unknown operator %d", which);
+    return BEM_EINVAL;
+  }
+  const size_t bytes = (size_t)n * (prec == BEM_C32 ? sizeof(float2) : sizeof(double2));
+  if (!c->h2d) {
+    BEM_CUDA(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking));
+    BEM_CUDA(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      BEM_CUDA(cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
+      BEM_CUDA(cudaEventCreateWithFlags(&c->ev_comp[b], cudaEventDisableTiming));
+      BEM_CUDA(cudaEventCreateWithFlags(&c->ev_out[b], cudaEventDisableTiming));
+    }
+  }
+  if (c->hbuf_bytes < bytes) {  // the largest operator length in FP64 serves every call
+    const size_t big = ((size_t)c->ne + c->nt) * sizeof(double2);
+    BEM_CUDA(cudaDeviceSynchronize());
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // keyed by the old buffers
+    c->graphs.clear();
+    for (auto& pr : c->hbuf)
+      for (void*& p : pr) {
+        if (p) cudaFree(p);
+        p = nullptr;
+      }
+    c->hbuf_bytes = 0;
+    for (auto& pr : c->hbuf)
+      for (void*& p : pr)
+        if (cudaMalloc(&p, big) != cudaSuccess) {
+          set_error("aim_matvec_host: out of device memory");
+          return BEM_ENOMEM;
+        }
+    c->hbuf_bytes = big;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // the copies start after the work already on the caller's stream
+  BEM_CUDA(cudaEventRecord(c->ev_in[0], s));
+  BEM_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_in[0], 0));
+  BEM_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_in[0], 0));
+  const char* xh = static_cast<const char*>(x);
+  char* yh = static_cast<char*>(y);
+  for (int i = 0; i < nvec; ++i) {
+    const int b = i & 1;
+    void* xd = c->hbuf[b][0];
+    void* yd = c->hbuf[b][1];
+    // x_i may overwrite buffer b once product i - 2 has read it
+    if (i >= 2) BEM_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_comp[b], 0));
+    BEM_CUDA(cudaMemcpyAsync(xd, xh + (size_t)i * bytes, bytes, cudaMemcpyHostToDevice, c->h2d));
+    BEM_CUDA(cudaEventRecord(c->ev_in[b], c->h2d));
+    BEM_CUDA(cudaStreamWaitEvent(s, c->ev_in[b], 0));
+    // y_i may overwrite buffer b once y_{i-2} has gone to the host
+    if (i >= 2) BEM_CUDA(cudaStreamWaitEvent(s, c->ev_out[b], 0));
+    BEM_TRY(prec == BEM_C32 ? matvec_graph<float>(c, which, xd, yd, s) : matvec_graph<double>(c, which, xd, yd, s));
+    BEM_CUDA(cudaEventRecord(c->ev_comp[b], s));
+    BEM_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_comp[b], 0));
+    BEM_CUDA(cudaMemcpyAsync(yh + (size_t)i * bytes, yd, bytes, cudaMemcpyDeviceToHost, c->d2h));
+    BEM_CUDA(cudaEventRecord(c->ev_out[b], c->d2h));
+  }
+  BEM_CUDA(cudaStreamWaitEvent(s, c->ev_out[(nvec - 1) & 1], 0));
+  return BEM_OK;
+}
+
 int aim_matvec_schedule(aim_ctx* c, int mode) {
   BEM_TRY(check_ctx(c, "aim_matvec_schedule"));
   if (mode < -1 || mode > 3 || (mode == 3 && c->gpair.ntasks == 0)) {

@@ -277,6 +277,12 @@ struct aim_ctx {
   // streams for the two-branch matvec and its CUDA-graph capture
   cudaStream_t cap = nullptr, side = nullptr, zside = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr, ev_c = nullptr;
+  // host-buffer matvecs: two device buffer pairs, copy streams and their events (lazily made)
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr};
+  void* hbuf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [buffer][x, y]
+  size_t hbuf_bytes = 0;
   int z_after = 0;  // e = Z h: 0 beside j's GEMV, 1 beside the AIM chain once j = h - C h is
                     // out, 2 on the main stream after j's GEMV with the whole GPU, 3 in one
                     // launch with j's GEMV (gpair)

@@ -850,6 +850,15 @@ void release_streams(aim_ctx* c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   c->ev_fork = c->ev_join = nullptr;
   c->side = c->cap = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    for (cudaEvent_t* e : {&c->ev_in[b], &c->ev_comp[b], &c->ev_out[b]})
+      if (*e) cudaEventDestroy(*e), *e = nullptr;
+    for (void*& p : c->hbuf[b])
+      if (p) cudaFree(p), p = nullptr;
+  }
+  if (c->h2d) cudaStreamDestroy(c->h2d);
+  if (c->d2h) cudaStreamDestroy(c->d2h);
+  c->h2d = c->d2h = nullptr;
 }
 
 // The matvec is ~12 kernels; replaying it as one CUDA graph removes the per-launch host cost.

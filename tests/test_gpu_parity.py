@@ -214,6 +214,32 @@ def test_matvec_schedules_match_oracle(prob, mode):
         ctx.matvec_schedule(-1)
 
 
+@pytest.mark.parametrize("prec", [api.BEM_C32, api.BEM_C64])
+def test_matvec_host_pipeline(prob, prec):
+    """aim_matvec_host (host vectors, copies overlapped with the products through two device
+    buffer pairs) gives each vector the device matvec's product, for 1, 2 and 5 vectors and for
+    the three operators; pageable host memory works too."""
+    ctx = prob["ctx"]
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    for which, n in [(api.AIM_OP_SYSTEM, ctx.n), (api.AIM_OP_LA, ctx.ne), (api.AIM_OP_LPHI, ctx.nt)]:
+        for nvec, pin in [(1, True), (2, False), (5, True)]:
+            xs = np.stack([synth.rand_cvec(n, 100 + i) for i in range(nvec)]).astype(npdt)
+            xh = torch.from_numpy(xs)
+            if pin:
+                xh = xh.pin_memory()
+            yh = ctx.matvec_host(xh, which=which, prec=prec)
+            torch.cuda.synchronize()
+            for i in range(nvec):
+                yd = ctx.matvec(torch.from_numpy(xs[i]).cuda(), which=which, prec=prec).cpu().numpy()
+                assert rel(yh[i].numpy(), yd) < 1e-6
+    xz = torch.zeros((1, ctx.n), dtype=torch.complex64)
+    yz = torch.zeros_like(xz)
+    L = api.lib()
+    assert L.aim_matvec_host(ctx.h, 7, xz.data_ptr(), yz.data_ptr(), 1, api.BEM_C32, None) == -1
+    assert L.aim_matvec_host(ctx.h, api.AIM_OP_SYSTEM, xz.data_ptr(), yz.data_ptr(), 0, api.BEM_C32,
+                             None) == -1
+
+
 @pytest.mark.parametrize("shape", [(6, 2, 1, 4), (6, 3, 2, 8)])
 def test_dynamic_task_list_relaunch(prob, shape):
     """The dynamic task list (persistent CTAs taking tasks from a counter that the last CTA sets
