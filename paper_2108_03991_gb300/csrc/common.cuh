@@ -379,6 +379,7 @@ int interp_all(aim_ctx* c, const typename C2<R>::T* phi, typename C2<R>::T* u, c
 int net_apply(aim_ctx* c, const float2* r, float2* z, cudaStream_t s);
 void free_net(aim_ctx* c);
 template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cudaStream_t s);
+int precond_apply_mixed(aim_ctx* c, const double2* r, float2* u32, double2* u64, cudaStream_t s);
 void free_geo_store(aim_ctx* c);
 void free_far_geo(aim_ctx* c);
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);

@@ -12,6 +12,8 @@ namespace bem {
 
 static constexpr int kChunks = 304;  // 2 x 152 SMs
 
+// Dot products h[j] = V_j^H w of nv basis vectors with w: per-block partial sums (k_dots),
+// then one block per vector adds them (k_reduce); for a long basis.
 __global__ void k_dots(const double2* __restrict__ V, int64_t ldv, int nv,
                        const double2* __restrict__ w, int64_t n, double2* __restrict__ partial) {
   __shared__ double2 red[8];
@@ -59,6 +61,58 @@ __global__ void k_reduce(const double2* __restrict__ partial, int nchunks, int n
   }
 }
 
+// The same and their reduction in one launch, for a short basis: every block writes its
+// partial sums, and the block that finishes last (a counter it sets back to zero) adds the partials:
+// h[j] = sum of partials; if acc != nullptr: acc[j] += h[j]. No block waits for another.
+__global__ void __launch_bounds__(256) k_dots_red(const double2* __restrict__ V, int64_t ldv, int nv,
+                                                  const double2* __restrict__ w, int64_t n,
+                                                  double2* __restrict__ partial, unsigned* ctr,
+                                                  double2* __restrict__ h, double2* acc) {
+  __shared__ double2 red[8];
+  __shared__ bool last;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+  for (int j = 0; j < nv; ++j) {
+    double2 a2 = make_double2(0, 0);
+    const double2* v = V + j * ldv;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      double2 a = v[i], b = w[i];
+      a2.x += a.x * b.x + a.y * b.y;  // conj(a) b
+      a2.y += a.x * b.y - a.y * b.x;
+    }
+    a2 = warp_sum(a2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 t = make_double2(0, 0);
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { t.x += red[k].x; t.y += red[k].y; }
+      partial[(int64_t)j * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partials are visible before it is counted
+    last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = warp; j < nv; j += (int)(blockDim.x >> 5)) {
+    double2 t = make_double2(0, 0);
+    for (int i = lane; i < (int)gridDim.x; i += 32) {
+      const double2 q = __ldcg(&partial[(int64_t)j * gridDim.x + i]);
+      t.x += q.x;
+      t.y += q.y;
+    }
+    t = warp_sum(t);
+    if (lane == 0) {
+      h[j] = t;
+      if (acc) { acc[j].x += t.x; acc[j].y += t.y; }
+    }
+  }
+  if (threadIdx.x == 0) *ctr = 0u;
+}
+
 // w += sign * sum_j h[j] V[j]
 __global__ void k_axpy_basis(const double2* __restrict__ V, int64_t ldv, int nv,
                              const double2* __restrict__ h, double sign, double2* w, int64_t n) {
@@ -102,10 +156,10 @@ __global__ void k_to64(const float2* a, double2* o, int64_t n) {
 
 // Givens step for column k of H (leading dimension ldh = m + 1), one thread.
 // Rotation (c, s) acts as (x, y) -> (conj(c) x + conj(s) y, -s x + c y).
-__global__ void k_givens(double2* H, int ldh, int k, const double* hsub, double2* cs, double2* sn,
-                         double2* g, double* resid) {
+__device__ void givens_step(double2* H, int ldh, int k, double hsub, double2* cs, double2* sn,
+                            double2* g, double* resid) {
   double2* col = H + (int64_t)k * ldh;
-  col[k + 1] = make_double2(*hsub, 0.0);
+  col[k + 1] = make_double2(hsub, 0.0);
   for (int i = 0; i < k; ++i) {
     double2 a = col[i], b = col[i + 1], c = cs[i], s = sn[i];
     double2 t = cadd(cmul(cconj(c), a), cmul(cconj(s), b));
@@ -124,6 +178,18 @@ __global__ void k_givens(double2* H, int ldh, int k, const double* hsub, double2
   g[k + 1] = mk(-(s.x * gk.x - s.y * gk.y), -(s.x * gk.y + s.y * gk.x));
   g[k] = cmul(cconj(c), gk);
   *resid = sqrt(g[k + 1].x * g[k + 1].x + g[k + 1].y * g[k + 1].y);
+}
+
+// v_{k+1} = w / |w| and, in block 0's first thread, the Givens step of column k with the
+// subdiagonal |w| (the Arnoldi step's last two operations in one launch)
+__global__ void k_normalize_givens(const double2* __restrict__ in, const double2* nrm2, double2* out,
+                                   int64_t n, double2* H, int ldh, int k, double2* cs, double2* sn,
+                                   double2* g, double* resid) {
+  const double nr = sqrt(fmax(nrm2->x, 0.0));
+  const double s = nr > 0 ? 1.0 / nr : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_double2(in[i].x * s, in[i].y * s);
+  if (blockIdx.x == 0 && threadIdx.x == 0) givens_step(H, ldh, k, nr, cs, sn, g, resid);
 }
 
 // y = R^{-1} g for the leading k x k upper-triangular block, one thread
@@ -145,7 +211,8 @@ __global__ void k_set_g0(double2* g, int m1, const double* beta) {
 struct GmWork {
   double2 *V = nullptr, *w = nullptr, *r = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr,
           *g = nullptr, *h = nullptr, *hacc = nullptr, *partial = nullptr, *y = nullptr, *Zb = nullptr;
-  double* dsc = nullptr;  // [0] = subdiagonal, [1] = residual estimate, [2] = beta
+  double* dsc = nullptr;  // [0] = subdiagonal, [1] = residual estimate, [2] = beta,
+                          // [4] = block counter of k_dots_red (zero between launches)
 };
 
 static int gm_workspace(aim_ctx* c, int64_t n, int m, bool flexible, GmWork* W) {
@@ -183,8 +250,13 @@ static int gm_workspace(aim_ctx* c, int64_t n, int m, bool flexible, GmWork* W) 
 
 static int dot_into(const double2* V, int64_t ldv, int nv, const double2* w, int64_t n, GmWork& W,
                     double2* h, double2* acc, cudaStream_t s) {
-  k_dots<<<kChunks, 256, 0, s>>>(V, ldv, nv, w, n, W.partial);
-  k_reduce<<<nv, 256, 0, s>>>(W.partial, kChunks, nv, h, acc);
+  if (nv <= 16) {  // one launch; the last block's reduction is short
+    k_dots_red<<<kChunks, 256, 0, s>>>(V, ldv, nv, w, n, W.partial,
+                                       reinterpret_cast<unsigned*>(W.dsc + 4), h, acc);
+  } else {
+    k_dots<<<kChunks, 256, 0, s>>>(V, ldv, nv, w, n, W.partial);
+    k_reduce<<<nv, 256, 0, s>>>(W.partial, kChunks, nv, h, acc);
+  }
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }
@@ -220,6 +292,7 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   if (flexible) BEM_TRY(setup_precond(c));
   GmWork W;
   BEM_TRY(gm_workspace(c, n, m, flexible, &W));
+  BEM_CUDA(cudaMemsetAsync(W.dsc + 4, 0, sizeof(double), s));
   double2* Zb = W.Zb;
   BEM_CUDA(cudaMemsetAsync(W.H, 0, sizeof(double2) * ldh * m, s));
   // ||b|| and ||x0|| (a zero initial guess needs no first matvec: r = b)
@@ -271,13 +344,18 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
         } else if (o->prec_mode == BEM_C64) {
           BEM_TRY(precond_apply<double>(c, vk, zk, s));
         } else {
-          k_to32<<<kChunks, 256, 0, s>>>(vk, c->f32.xin, n);
-          BEM_TRY(precond_apply<float>(c, c->f32.xin, c->f32.yout, s));
-          k_to64<<<kChunks, 256, 0, s>>>(c->f32.yout, zk, n);
+          // the preconditioned vector lands in the FP32 matvec's input buffer (and in zk), so
+          // the FP32 product below starts from it without converting zk back
+          BEM_TRY(precond_apply_mixed(c, vk, c->f32.xin, zk, s));
         }
         vk = zk;
       }
-      BEM_TRY(sys_apply(c, o->prec_mode, vk, W.w, s));
+      if (Zb && o->precond == 1 && o->prec_mode == BEM_C32) {
+        BEM_TRY(matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s));
+        k_to64<<<kChunks, 256, 0, s>>>(c->f32.yout, W.w, n);
+      } else {
+        BEM_TRY(sys_apply(c, o->prec_mode, vk, W.w, s));
+      }
       // CGS2: h = V^H w, w -= V h, twice; accumulate into column k of H
       double2* Hk = W.H + (int64_t)k * ldh;
       BEM_CUDA(cudaMemsetAsync(Hk, 0, sizeof(double2) * (k + 1), s));
@@ -286,8 +364,8 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
         k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>(W.V, n, k + 1, W.h, -1.0, W.w, n);
       }
       BEM_TRY(dot_into(W.w, n, 1, W.w, n, W, W.h, nullptr, s));
-      k_normalize<<<kChunks, 256, 0, s>>>(W.w, W.h, W.V + (int64_t)(k + 1) * n, W.dsc, n);
-      k_givens<<<1, 1, 0, s>>>(W.H, ldh, k, W.dsc, W.cs, W.sn, W.g, W.dsc + 1);
+      k_normalize_givens<<<kChunks, 256, 0, s>>>(W.w, W.h, W.V + (int64_t)(k + 1) * n, n, W.H, ldh, k,
+                                                 W.cs, W.sn, W.g, W.dsc + 1);
       BEM_CUDA(cudaGetLastError());
       double res;
       BEM_CUDA(cudaMemcpyAsync(&res, W.dsc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));

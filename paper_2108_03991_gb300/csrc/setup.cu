@@ -1437,6 +1437,41 @@ int precond_apply(aim_ctx* c, const void* rv, void* uv, cudaStream_t s) {
 template int precond_apply<float>(aim_ctx*, const void*, void*, cudaStream_t);
 template int precond_apply<double>(aim_ctx*, const void*, void*, cudaStream_t);
 
+__global__ void k_perm_gather32(const int32_t* perm, const double2* x, float2* xp, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = x[perm[i]];
+    xp[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void k_perm_scatter2(const int32_t* perm, const float2* yp, float2* y32, double2* y64,
+                                int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 v = yp[i];
+    y32[perm[i]] = v;
+    y64[perm[i]] = make_double2(v.x, v.y);
+  }
+}
+
+// The FP32 preconditioner of an FP64 Krylov vector: u = M_bd (float) r, returned both in FP32
+// (u32, the next FP32 product's input) and in FP64 (u64, the flexible basis); the conversions
+// ride on the permutation launches.
+int precond_apply_mixed(aim_ctx* c, const double2* r, float2* u32, double2* u64, cudaStream_t s) {
+  if (!c->pc_ready) {
+    set_error("block-diagonal preconditioner not built");
+    return BEM_EINVAL;
+  }
+  const int n = c->ne + c->nt;
+  float2* w0 = (float2*)c->pcw32[0];
+  float2* w1 = (float2*)c->pcw32[1];
+  k_perm_gather32<<<nblk(n, 256), 256, 0, s>>>(c->d_pcperm, r, w0, n);
+  BEM_TRY(run_gemv_plan<float>(c->pcplan, (const float2*)c->pc32, w0, w1, 1, n, nullptr, s));
+  k_perm_scatter2<<<nblk(n, 256), 256, 0, s>>>(c->d_pcperm, w1, u32, u64, n);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
 int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
                    cudaStream_t st) {
   const DGeo& g = *reinterpret_cast<const DGeo*>(c->geo_store);
