@@ -430,6 +430,19 @@ def main():
         ev1.record(s)
         torch.cuda.synchronize()
         gemv_ms = ev0.elapsed_time(ev1) / (2 * args.steps)
+        # the batched system matvec: 4 right-hand sides per graph launch
+        xb = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.n, 500 + r) for r in range(4)])
+                              .astype(np.complex64)).to(dev)
+        yb = torch.empty_like(xb)
+        for _ in range(3):
+            ctx.matvec_batch(xb, yb, prec=api.BEM_C32)
+        torch.cuda.synchronize()
+        ev0.record(s)
+        for _ in range(args.steps):
+            ctx.matvec_batch(xb, yb, prec=api.BEM_C32)
+        ev1.record(s)
+        torch.cuda.synchronize()
+        batch_ms = ev0.elapsed_time(ev1) / args.steps
         # end to end through the host-buffer call: K distinct pinned host inputs, each copied
         # to the device, multiplied and copied back (the copies of neighbouring steps overlap
         # the products)
@@ -443,7 +456,7 @@ def main():
         ev1.record(s)
         torch.cuda.synchronize()
         e2e_ms = ev0.elapsed_time(ev1) / args.steps
-    ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
+    ms, e2e_ms, batch_ms = max_over_ranks([ms, e2e_ms, batch_ms], dev)
 
     solve = None
     if not args.no_solve and rank == 0:
@@ -542,6 +555,9 @@ def main():
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n,
                     "call": "aim_matvec_host (pinned host vectors, copies overlapped)"},
+            "batched": {"nrhs": 4, "value": replicas_value(batch_ms / 4, world), "unit": UNIT,
+                        "ms_per_launch": batch_ms,
+                        "note": "aim_matvec_batch: 4 right-hand sides per graph, matvecs/s counted per right-hand side"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "solve": solve,

@@ -144,6 +144,15 @@ int aim_matvec_schedule(aim_ctx* ctx, int mode);
  * x and y must not alias. prec selects the arithmetic (BEM_C32 or BEM_C64). */
 int aim_matvec(aim_ctx* ctx, int which, const void* x, void* y, int prec, void* stream);
 
+/* The system matvec of aim_matvec (AIM_OP_SYSTEM) for nrhs (1..4) right-hand sides at once:
+ * x, y: device vectors of nrhs (N_E + N_T) entries, one right-hand side after another. Each
+ * internal block matrix is read once for all of them and the grid convolution transforms all
+ * their grids per launch, so a batch costs much less than nrhs separate products (the
+ * many-right-hand-side use of the internal blocks, Sec. III-C). x and y must not alias.
+ * The first call per precision allocates the batch buffers (about 130 MB in FP32 at the
+ * 4x4 bar array); later calls allocate nothing. BEM_EINVAL for nrhs out of range. */
+int aim_matvec_batch(aim_ctx* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
+
 /* y_i = A x_i for nvec vectors in HOST memory (x, y: nvec vectors of the operator's length,
  * one after another; page-locked memory lets the copies run asynchronously): the products of
  * aim_matvec, with the host-to-device copy of x_{i+1} and the device-to-host copy of y_{i-1}

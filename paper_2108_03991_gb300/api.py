@@ -24,7 +24,7 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "bem_precond_apply", "bem_net_init", "bem_net_weights", "bem_net_train",
            "bem_net_apply", "bem_convnet_run", "aim_gemv_select", "aim_gemv_plan",
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
-           "bem_port_current", "bem_port_matrix", "bem_farfield"]
+           "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch"]
 
 
 class BemError(RuntimeError):
@@ -78,6 +78,7 @@ def lib():
         L.aim_gemv_plan.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
         L.aim_matvec_schedule.argtypes = [vp, C.c_int]
         L.aim_matvec_host.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, vp]
+        L.aim_matvec_batch.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_port_ring.argtypes = [vp, C.c_int, C.c_int, d, d, C.POINTER(i32), C.POINTER(d), C.c_int]
         L.bem_rhs_port.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), d, vp, C.c_int, vp]
         L.bem_port_current.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), vp, C.c_int,
@@ -328,6 +329,18 @@ class Context:
             raise ValueError("vector length mismatch")
         _check(lib().aim_matvec(self.h, which, _ptr(x, cdtype(prec)), _ptr(y, cdtype(prec)), prec,
                                 _stream()))
+        return y
+
+    def matvec_batch(self, x, y=None, prec=BEM_C32):
+        """System matvec of nrhs = x.numel() / N right-hand sides at once (aim_matvec_batch);
+        x, y: device tensors of nrhs * N entries (or [nrhs, N])."""
+        import torch
+        if x.numel() % self.n:
+            raise ValueError("vector length mismatch")
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().aim_matvec_batch(self.h, _ptr(x, cdtype(prec)), _ptr(y, cdtype(prec)),
+                                      x.numel() // self.n, prec, _stream()))
         return y
 
     def matvec_host(self, x, y=None, which=AIM_OP_SYSTEM, prec=BEM_C32):

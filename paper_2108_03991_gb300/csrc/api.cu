@@ -140,6 +140,22 @@ int aim_gemv_plan(aim_ctx* c, int kind, int ctas_per_sm, int split, int unroll) 
   return BEM_OK;
 }
 
+int aim_matvec_batch(aim_ctx* c, const void* x, void* y, int nrhs, int prec, void* stream) {
+  BEM_TRY(check_ctx(c, "aim_matvec_batch"));
+  BEM_TRY(check_prec(prec, "aim_matvec_batch"));
+  if (!x || !y || x == y || nrhs < 1 || nrhs > kMaxBatch) {
+    set_error("aim_matvec_batch: distinct x and y and 1 <= nrhs <= %d required", kMaxBatch);
+    return BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (prec == BEM_C32) {
+    BEM_TRY(batch_buffers<float>(c));
+    return matvec_graph<float>(c, kBatchOp + nrhs, x, y, s);
+  }
+  BEM_TRY(batch_buffers<double>(c));
+  return matvec_graph<double>(c, kBatchOp + nrhs, x, y, s);
+}
+
 int aim_matvec_host(aim_ctx* c, int which, const void* x, void* y, int nvec, int prec, void* stream) {
   BEM_TRY(check_ctx(c, "aim_matvec_host"));
   BEM_TRY(check_prec(prec, "aim_matvec_host"));

@@ -119,6 +119,11 @@ template <typename R> struct PrecBuf {
   V* j = nullptr;      // [ne]
   V* p = nullptr;      // [nt]
   V* anear = nullptr;  // [ne] near-region part L^A_NR j of the system matvec
+  // batched system matvec (up to kMaxBatch right-hand sides; made on first use): j and e with
+  // the input's stride N_E + N_T, L^A_NR j [r][ne], p [r][nt], grids [r][3][ng] and [r][ng],
+  // FFT workspaces [3 r][P3] and [r][P3]
+  V *bj = nullptr, *be = nullptr, *ban = nullptr, *bp = nullptr, *bsE = nullptr, *bsT = nullptr,
+    *bwsE = nullptr, *bwsT = nullptr;
   V* xin = nullptr;    // [ne + nt] conversion buffer for mixed precision
   V* yout = nullptr;
 };
@@ -352,6 +357,9 @@ int run_gemv_plan(const GemvPlan& p, const typename C2<R>::T* A, const typename 
                   typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
                   cudaStream_t s);
 template <typename R> int matvec(aim_ctx* c, int which, const void* x, void* y, cudaStream_t s);
+// the system matvec of nrhs right-hand sides in one graph: which = kBatchOp + nrhs
+constexpr int kBatchOp = 16, kMaxBatch = 4;
+template <typename R> int batch_buffers(aim_ctx* c);
 // matvec through a cached CUDA graph (captured on first use for these buffers)
 template <typename R> int matvec_graph(aim_ctx* c, int which, const void* x, void* y,
                                        cudaStream_t s);

@@ -544,8 +544,11 @@ __global__ void __launch_bounds__(256) k_project(const int32_t* __restrict__ wor
                                                  const int32_t* __restrict__ pcol,
                                                  const R* __restrict__ WT,
                                                  const typename C2<R>::T* __restrict__ src,
-                                                 typename C2<R>::T* __restrict__ sigma) {
+                                                 typename C2<R>::T* __restrict__ sigma,
+                                                 int64_t src_rs, int64_t sig_rs) {
   typedef typename C2<R>::T V;
+  src += blockIdx.y * src_rs;  // right-hand side blockIdx.y of a batch
+  sigma += blockIdx.y * sig_rs;
   if ((int)blockIdx.x >= nb_work) {
     const int64_t i = nwork + (int64_t)(blockIdx.x - nb_work) * blockDim.x + threadIdx.x;
     if (i < ng) {
@@ -593,20 +596,20 @@ static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b)
 // sigma_{x,y,z} = P_c j (RWG sources, 3 components)
 template <typename R>
 static void project_e(const aim_ctx* c, const R* WT, const typename C2<R>::T* j,
-                      typename C2<R>::T* sigma, cudaStream_t s) {
+                      typename C2<R>::T* sigma, cudaStream_t s, int nrhs = 1, int64_t j_rs = 0) {
   const int nbw = (int)nb((int64_t)c->nwE * kProjG, 256);
   const int nbz = (int)nb(c->ng - c->nwE, 256);
-  k_project<R, 3><<<nbw + nbz, 256, 0, s>>>(c->d_pnodeE, c->nwE, c->ng, nbw, c->d_prowE,
-                                            c->d_pcolE, WT, j, sigma);
+  k_project<R, 3><<<dim3(nbw + nbz, nrhs), 256, 0, s>>>(c->d_pnodeE, c->nwE, c->ng, nbw, c->d_prowE,
+                                                        c->d_pcolE, WT, j, sigma, j_rs, 3 * c->ng);
 }
 // sigma_q = P_Phi q (pulse sources, 1 component)
 template <typename R>
 static void project_t(const aim_ctx* c, const R* WT, const typename C2<R>::T* q,
-                      typename C2<R>::T* sigma, cudaStream_t s) {
+                      typename C2<R>::T* sigma, cudaStream_t s, int nrhs = 1, int64_t q_rs = 0) {
   const int nbw = (int)nb((int64_t)c->nwT * kProjG, 256);
   const int nbz = (int)nb(c->ng - c->nwT, 256);
-  k_project<R, 1><<<nbw + nbz, 256, 0, s>>>(c->d_pnodeT, c->nwT, c->ng, nbw, c->d_prowT,
-                                            c->d_pcolT, WT, q, sigma);
+  k_project<R, 1><<<dim3(nbw + nbz, nrhs), 256, 0, s>>>(c->d_pnodeT, c->nwT, c->ng, nbw, c->d_prowT,
+                                                        c->d_pcolT, WT, q, sigma, q_rs, c->ng);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -642,8 +645,11 @@ __global__ void __launch_bounds__(256) k_rows_t(
     const typename C2<R>::T* __restrict__ phi, const int64_t* __restrict__ rowP,
     const int32_t* __restrict__ colP, const typename C2<R>::T* __restrict__ LP,
     const typename C2<R>::T* __restrict__ q, int nt, int nx, int ny,
-    typename C2<R>::T* __restrict__ out) {
+    typename C2<R>::T* __restrict__ out, int64_t phi_rs = 0, int64_t q_rs = 0, int64_t out_rs = 0) {
   typedef typename C2<R>::T V;
+  phi += blockIdx.y * phi_rs;  // right-hand side blockIdx.y of a batch
+  q += blockIdx.y * q_rs;
+  out += blockIdx.y * out_rs;
   const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= nt) return;
   V acc = czero<V>();
@@ -656,6 +662,11 @@ __global__ void __launch_bounds__(256) k_rows_t(
   acc = warp_sum(acc);
   if (lane == 0) out[t] = acc;
 }
+
+// offsets of right-hand side blockIdx.y in a batch (0: one right-hand side)
+struct RowsStride {
+  int64_t phi = 0, j = 0, e = 0, p = 0, q = 0, an = 0, y = 0;
+};
 
 // mode 0: y[m] = a_m (L^A alone).
 // mode 1 (system), rows m < ne:  y1_m = j k0 a_m + (I_x e)_m - ((F D)^T p)_m
@@ -671,8 +682,18 @@ __global__ void __launch_bounds__(256) k_rows_e(
     const typename C2<R>::T* __restrict__ p, int ne, int nx, int ny, R k0, int mode,
     typename C2<R>::T* __restrict__ y, int nt, const R* __restrict__ fdT,
     const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ q,
-    const typename C2<R>::T* __restrict__ anear) {
+    const typename C2<R>::T* __restrict__ anear, RowsStride rs = RowsStride()) {
   typedef typename C2<R>::T V;
+  {
+    const int64_t r = blockIdx.y;
+    phi += r * rs.phi;
+    j += r * rs.j;
+    if (e) e += r * rs.e;
+    if (p) p += r * rs.p;
+    if (q) q += r * rs.q;
+    if (anear) anear += r * rs.an;
+    y += r * rs.y;
+  }
   const int nbE = (ne + 7) >> 3;  // blocks of the RWG rows (one warp per row); then the pulse
   if ((int)blockIdx.x >= nbE) {   // rows of mode 1, one thread per row
     const int t = (blockIdx.x - nbE) * blockDim.x + threadIdx.x;
@@ -737,8 +758,11 @@ __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA
                                                 const int32_t* __restrict__ colA,
                                                 const typename C2<R>::T* __restrict__ LA,
                                                 const typename C2<R>::T* __restrict__ j, int ne,
-                                                typename C2<R>::T* __restrict__ a) {
+                                                typename C2<R>::T* __restrict__ a, int64_t j_rs = 0,
+                                                int64_t a_rs = 0) {
   typedef typename C2<R>::T V;
+  j += blockIdx.y * j_rs;  // right-hand side blockIdx.y of a batch
+  a += blockIdx.y * a_rs;
   const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (m >= ne) return;
   V acc = czero<V>();
@@ -751,9 +775,79 @@ template <typename R> PrecBuf<R>& buf(aim_ctx* c);
 template <> PrecBuf<float>& buf<float>(aim_ctx* c) { return c->f32; }
 template <> PrecBuf<double>& buf<double>(aim_ctx* c) { return c->f64; }
 
+// The system matvec of Eq. AEFIEoutJ for nrhs right-hand sides x_r = [h_r; q_r] (stride
+// N_E + N_T) at once: each block matrix is read once for all of them (the GEMV takes the
+// right-hand sides together), the convolution transforms 3 nrhs and nrhs grids per launch, and
+// the projection, near-region and row kernels take the right-hand side from blockIdx.y. The
+// internal products run on the main stream one after the other, the charge branch and the near
+// region of j on the side stream (the serial schedule of the one-vector matvec).
+template <typename R>
+int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s) {
+  typedef typename C2<R>::T V;
+  PrecBuf<R>& b = buf<R>(c);
+  if (!b.bwsT) {
+    set_error("batched matvec: buffers not made");
+    return BEM_EINVAL;
+  }
+  const V* x = static_cast<const V*>(xv);
+  V* y = static_cast<V*>(yv);
+  const int ne = c->ne, nt = c->nt, nx = c->gn[0], ny = c->gn[1];
+  const int64_t ng = c->ng, N = (int64_t)ne + nt;
+  const R k0 = (R)c->k0;
+  const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
+  BEM_CUDA(cudaEventRecord(c->ev_fork, s));
+  BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+  project_t<R>(c, b.WPT, x + ne, b.bsT, c->side, nrhs, N);
+  BEM_TRY(fft_conv<R>(c, b, b.bsT, b.bsT, nrhs, b.bwsT, c->side));
+  k_rows_t<R><<<dim3(nb(nt, 8), nrhs), 256, 0, c->side>>>(b.WP, c->d_nodeT, b.bsT, c->d_rowP, c->d_colP,
+                                                           b.LP, x + ne, nt, nx, ny, b.bp, ng, N, nt);
+  BEM_TRY(run_gemv_plan<R>(gp, b.C, x, b.bj, nrhs, N, x, s));  // j_r = h_r - C h_r
+  BEM_CUDA(cudaEventRecord(c->ev_c, s));
+  BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
+  k_near_e<R><<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.bj, ne, b.ban,
+                                                           N, ne);
+  BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
+  BEM_TRY(run_gemv_plan<R>(gp, b.Z, x, b.be, nrhs, N, nullptr, s));  // e_r = Z h_r
+  project_e<R>(c, b.WAT, b.bj, b.bsE, s, nrhs, N);
+  BEM_TRY(fft_conv<R>(c, b, b.bsE, b.bsE, 3 * nrhs, b.bwsE, s));
+  BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+  RowsStride rs;
+  rs.phi = 3 * ng;
+  rs.j = N;
+  rs.e = N;
+  rs.p = nt;
+  rs.q = N;
+  rs.an = ne;
+  rs.y = N;
+  k_rows_e<R><<<dim3(nb(ne, 8) + nb(nt, 256), nrhs), 256, 0, s>>>(
+      b.WA, c->d_nodeE, b.bsE, ng, c->d_rowA, c->d_colA, b.LA, b.bj, b.ix, c->d_ixcol, b.be, b.fdE,
+      c->d_et, b.bp, ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, x + ne, b.ban, rs);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+template <typename R>
+int batch_buffers(aim_ctx* c) {
+  PrecBuf<R>& b = buf<R>(c);
+  if (b.bwsT) return BEM_OK;
+  const int64_t N = (int64_t)c->ne + c->nt, P3 = (int64_t)c->gp[0] * c->gp[1] * c->gp[2];
+  BEM_TRY(dalloc_t(c, &b.bj, kMaxBatch * N));
+  BEM_TRY(dalloc_t(c, &b.be, kMaxBatch * N));
+  BEM_TRY(dalloc_t(c, &b.ban, kMaxBatch * (int64_t)c->ne));
+  BEM_TRY(dalloc_t(c, &b.bp, kMaxBatch * (int64_t)c->nt));
+  BEM_TRY(dalloc_t(c, &b.bsE, 3 * kMaxBatch * c->ng));
+  BEM_TRY(dalloc_t(c, &b.bsT, kMaxBatch * c->ng));
+  BEM_TRY(dalloc_t(c, &b.bwsE, 3 * kMaxBatch * P3));
+  BEM_TRY(dalloc_t(c, &b.bwsT, kMaxBatch * P3));
+  return BEM_OK;
+}
+template int batch_buffers<float>(aim_ctx*);
+template int batch_buffers<double>(aim_ctx*);
+
 template <typename R>
 int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
   typedef typename C2<R>::T V;
+  if (which > kBatchOp) return matvec_batch<R>(c, xv, yv, which - kBatchOp, s);
   PrecBuf<R>& b = buf<R>(c);
   const V* x = static_cast<const V*>(xv);
   V* y = static_cast<V*>(yv);

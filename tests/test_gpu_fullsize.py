@@ -97,3 +97,16 @@ def test_fullsize_system_rows(full, prec, tol):
     got = np.concatenate([y[re], y[ctx.ne + rt]])
     ref = np.concatenate([y1[re], y2[rt]])
     assert rel(got, ref) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-6), (api.BEM_C64, 1e-12)])
+def test_fullsize_batch_matches_single(full, prec, tol):
+    """The batched system matvec of 4 right-hand sides at full size against the one-vector
+    matvec (itself checked against the oracle above) for each right-hand side."""
+    ctx = full["ctx"]
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    xs = np.stack([synth.rand_cvec(ctx.n, 300 + r) for r in range(4)]).astype(npdt)
+    y = ctx.matvec_batch(torch.from_numpy(xs.ravel()).cuda(), prec=prec).cpu().numpy().reshape(4, -1)
+    for r in range(4):
+        y1 = ctx.matvec(torch.from_numpy(xs[r]).cuda(), prec=prec).cpu().numpy()
+        assert rel(y[r], y1) < tol

@@ -214,6 +214,24 @@ def test_matvec_schedules_match_oracle(prob, mode):
         ctx.matvec_schedule(-1)
 
 
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-7)])
+def test_matvec_batch_matches_oracle(prob, prec, tol):
+    """The batched system matvec (1-4 right-hand sides in one graph) against the oracle for every
+    right-hand side, and against the one-vector device matvec; nrhs outside 1..4 is refused."""
+    ctx, S = prob["ctx"], prob["S"]
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    for nrhs in (1, 2, 3, 4):
+        xs = np.stack([synth.rand_cvec(ctx.n, 200 + 10 * nrhs + r) for r in range(nrhs)])
+        xd = torch.from_numpy(xs.astype(npdt).ravel()).cuda()
+        y = ctx.matvec_batch(xd, prec=prec).cpu().numpy().reshape(nrhs, ctx.n)
+        for r in range(nrhs):
+            assert rel(y[r], S.matvec(xs[r])) < tol
+            y1 = ctx.matvec(torch.from_numpy(xs[r].astype(npdt)).cuda(), prec=prec).cpu().numpy()
+            assert rel(y[r], y1) < 1e-6
+    with pytest.raises(api.BemError):
+        ctx.matvec_batch(torch.zeros(5 * ctx.n, dtype=api.cdtype(prec), device="cuda"), prec=prec)
+
+
 @pytest.mark.parametrize("prec", [api.BEM_C32, api.BEM_C64])
 def test_matvec_host_pipeline(prob, prec):
     """aim_matvec_host (host vectors, copies overlapped with the products through two device
