@@ -249,6 +249,7 @@ struct aim_ctx {
   bem::GemvPlan gplan64;  // FP64 products
   bem::GemvPlan gbg32, gbg64;  // e = Z h beside the AIM chain in the system matvec (few CTAs)
   bem::GemvPlan gpair;         // j = h - C h and e = Z h as one task list (both precisions)
+  bem::GemvPlan gmr;           // several right-hand sides: task list of 16-row tasks (k_gemv_mr)
   bem::GemvPlan gplan_auto;    // the autotuner's FP32 choice
   bem::GemvPlan gplan_alt[2];  // best plain and best staged FP32 plans (ncta = 0: none)
   float tune_ms[2] = {0, 0};  // autotuner: best plain, best staged candidate (5 launches, ms)
@@ -348,6 +349,10 @@ template <typename R>
 int run_gemv(const GemvTask* d_tasks, int ntasks, const typename C2<R>::T* A,
              const typename C2<R>::T* x, typename C2<R>::T* y, int nrhs, int64_t vstride,
              const typename C2<R>::T* hsub, cudaStream_t s);
+template <typename R>
+int run_gemv_mr(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
+                typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
+                cudaStream_t s);
 template <typename R>
 int run_gemv_pair(const GemvPlan& p, const typename C2<R>::T* A0, const typename C2<R>::T* A1,
                   const typename C2<R>::T* x, typename C2<R>::T* y0, typename C2<R>::T* y1,

@@ -115,6 +115,110 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_gemv(const GemvTask* __restri
   }
 }
 
+// Several right-hand sides at once: each warp takes RB = 4 rows of its task and NR right-hand
+// sides, so every 16-byte load of the matrix (two complex entries of one row) meets NR vectors
+// and every load of x serves RB rows (a register tile of RB x NR accumulators). One CTA of NW
+// warps per task of at most 4 NW rows; y_r = A x_r, or hsub_r - A x_r. x is read as 8-byte
+// complex pairs (its slices need not be 16-byte aligned); an odd row length masks the last
+// pair's second entry.
+template <typename R, int NR, int NW>
+__global__ void __launch_bounds__(NW * 32) k_gemv_mr(const GemvTask* __restrict__ tasks,
+                                                     const typename C2<R>::T* __restrict__ A,
+                                                     const typename C2<R>::T* __restrict__ x,
+                                                     typename C2<R>::T* __restrict__ y, int64_t vstride,
+                                                     const typename C2<R>::T* __restrict__ hsub) {
+  typedef typename C2<R>::T V;
+  typedef typename Vec16<R>::T L16;  // 16 bytes: two complex FP32 or one complex FP64
+  constexpr int CP = Vec16<R>::kCplx;
+  constexpr int RB = 4;
+  const GemvTask t = tasks[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = t.row0 + warp * RB;
+  const int nr = min(RB, t.row0 + t.nrows - r0);
+  if (nr <= 0) return;
+  const V* xb = x + t.xoff;
+  const L16* arow[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k)
+    arow[k] = reinterpret_cast<const L16*>(A + t.aoff + (int64_t)(r0 + min(k, nr - 1)) * t.ld);
+  V acc[RB][NR];
+#pragma unroll
+  for (int k = 0; k < RB; ++k)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[k][r] = czero<V>();
+  constexpr int U = 2;                 // 16-byte loads in flight per row and lane
+  const int nv = (t.n + CP - 1) / CP;  // 16-byte vectors per row
+  for (int v = lane; v < nv; v += 32 * U) {
+    L16 a[U][RB];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < RB; ++k)
+        if (v + 32 * u < nv) a[u][k] = __ldcs(arow[k] + v + 32 * u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (v + 32 * u >= nv) break;
+#pragma unroll
+      for (int q = 0; q < CP; ++q) {
+        const int col = (v + 32 * u) * CP + q;
+        if (col >= t.n) break;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const V xv = __ldg(xb + r * vstride + col);
+#pragma unroll
+          for (int k = 0; k < RB; ++k) {
+            V av;
+            if constexpr (CP == 2) av = q == 0 ? mk(a[u][k].x, a[u][k].y) : mk(a[u][k].z, a[u][k].w);
+            else av = mk(a[u][k].x, a[u][k].y);
+            cfma(acc[k][r], av, xv);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RB; ++k)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[k][r] = warp_sum(acc[k][r]);
+  if (lane < RB * NR) {
+    const int k = lane / NR, r = lane % NR;
+    V out = czero<V>();
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk)
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr)
+        if (kk == k && rr == r) out = acc[kk][rr];
+    if (k < nr) {
+      const int64_t o = r * vstride + t.xoff + r0 + k;
+      y[o] = hsub ? csub(hsub[o], out) : out;
+    }
+  }
+}
+
+template <typename R>
+int run_gemv_mr(const GemvPlan& p, const typename C2<R>::T* A, const typename C2<R>::T* x,
+                typename C2<R>::T* y, int nrhs, int64_t vstride, const typename C2<R>::T* hsub,
+                cudaStream_t s) {
+  if (p.ntasks == 0) return BEM_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += 4) {
+    const int nr = std::min(4, nrhs - r0);
+    const int64_t o = r0 * vstride;
+    const typename C2<R>::T* hs = hsub ? hsub + o : nullptr;
+    switch (nr) {
+      case 1: k_gemv_mr<R, 1, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
+      case 2: k_gemv_mr<R, 2, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
+      case 3: k_gemv_mr<R, 3, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
+      default: k_gemv_mr<R, 4, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
+    }
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+template int run_gemv_mr<float>(const GemvPlan&, const float2*, const float2*, float2*, int, int64_t,
+                                const float2*, cudaStream_t);
+template int run_gemv_mr<double>(const GemvPlan&, const double2*, const double2*, double2*, int,
+                                 int64_t, const double2*, cudaStream_t);
+
 // Paired task list: two block-diagonal matrices of the same layout applied to one x in one
 // launch; a task with sel = 0 computes y0 = hsub - A0 x (or A0 x) on its rows, sel = 1
 // computes y1 = A1 x. One right-hand side.
@@ -801,13 +905,17 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   BEM_TRY(fft_conv<R>(c, b, b.bsT, b.bsT, nrhs, b.bwsT, c->side));
   k_rows_t<R><<<dim3(nb(nt, 8), nrhs), 256, 0, c->side>>>(b.WP, c->d_nodeT, b.bsT, c->d_rowP, c->d_colP,
                                                            b.LP, x + ne, nt, nx, ny, b.bp, ng, N, nt);
-  BEM_TRY(run_gemv_plan<R>(gp, b.C, x, b.bj, nrhs, N, x, s));  // j_r = h_r - C h_r
+  auto gemv = [&](const V* A, V* out, const V* hs) -> int {
+    return c->gmr.ntasks > 0 ? run_gemv_mr<R>(c->gmr, A, x, out, nrhs, N, hs, s)
+                             : run_gemv_plan<R>(gp, A, x, out, nrhs, N, hs, s);
+  };
+  BEM_TRY(gemv(b.C, b.bj, x));  // j_r = h_r - C h_r
   BEM_CUDA(cudaEventRecord(c->ev_c, s));
   BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
   k_near_e<R><<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.bj, ne, b.ban,
                                                            N, ne);
   BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
-  BEM_TRY(run_gemv_plan<R>(gp, b.Z, x, b.be, nrhs, N, nullptr, s));  // e_r = Z h_r
+  BEM_TRY(gemv(b.Z, b.be, nullptr));  // e_r = Z h_r
   project_e<R>(c, b.WAT, b.bj, b.bsE, s, nrhs, N);
   BEM_TRY(fft_conv<R>(c, b, b.bsE, b.bsE, 3 * nrhs, b.bwsE, s));
   BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));

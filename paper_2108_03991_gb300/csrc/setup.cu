@@ -773,6 +773,8 @@ int tune_matvec_schedule(aim_ctx* c) {
     p.ntasks = p.ncta = (int)t1.size();
     c->gpair = p;
   }
+  // the multi-right-hand-side launch (4 warps of 4 rows per task) of the batched matvec
+  BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 16, 4, 4}, nsm, n, c->zoff, c->zld, derr, &c->gmr));
   // the last two entries stand for the serial schedules (e = Z h after j's GEMV with its
   // launch shape; both in one paired launch)
   const GemvCand zc[] = {{1, 1, 1, 8}, {1, 2, 1, 8}, {1, 3, 1, 8}, {6, 2, 2, 4}, {6, 3, 2, 4}, {6, 4, 2, 4},
