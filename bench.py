@@ -502,6 +502,30 @@ def main():
             torch.cuda.nvtx.range_pop()
             solve[name] = {"seconds": time.perf_counter() - t1, "iters": info["iters"],
                            "resid_true": info["resid_true"], "status": info["status"]}
+        # four plane waves (polarisation x, y along +z; z, y along +x): solved one after
+        # another with the chosen form, and together with the batched FGMRES
+        waves = [((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)), ((0.0, 1.0, 0.0), (0.0, 0.0, 1.0)),
+                 ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0)), ((0.0, 1.0, 0.0), (1.0, 0.0, 0.0))]
+        bw = torch.cat([ctx.rhs_plane_wave(pol, kh, prec=api.BEM_C64) for pol, kh in waves])
+        ctx.solve_batch(bw, tol=1e-6, restart=200, max_iter=2, prec_mode=api.BEM_C32, precond=1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        its = []
+        for r in range(4):
+            _, info = ctx.solve(bw[r * ctx.n:(r + 1) * ctx.n].contiguous(), tol=1e-6, restart=200,
+                                max_iter=3000, prec_mode=api.BEM_C32, precond=1)
+            its.append(info["iters"])
+        torch.cuda.synchronize()
+        solve["chosen_4_waves_one_by_one"] = {"seconds": time.perf_counter() - t1, "iters": its}
+        t1 = time.perf_counter()
+        torch.cuda.nvtx.range_push("solve_batch4")
+        _, rc, infos = ctx.solve_batch(bw, tol=1e-6, restart=200, max_iter=3000,
+                                       prec_mode=api.BEM_C32, precond=1, time_limit_s=120.0)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        solve["chosen_4_waves_batched"] = {
+            "seconds": time.perf_counter() - t1, "iters": infos[0]["iters"], "status": rc,
+            "resid_true": [i["resid_true"] for i in infos]}
 
     if not args.no_solve and rank == 0:
         solve["copper_bar"] = copper_bar_numbers(api, synth, torch)

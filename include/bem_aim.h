@@ -292,6 +292,18 @@ typedef struct {
 int bem_solve(aim_ctx* ctx, const void* b, void* x, const bem_solve_opts* opts,
               bem_solve_info* info, void* stream);
 
+/* bem_solve for nrhs (1..4) right-hand sides at once: b and x hold nrhs complex double device
+ * vectors of N_E + N_T, one after another (x: initial guesses in, solutions out). The systems
+ * run in lockstep, each with its own Krylov basis: every iteration applies the preconditioner
+ * and the system matrix to all of them together (aim_matvec_batch; the block matrices are read
+ * once per iteration for all right-hand sides), and a cycle ends when every residual estimate is
+ * below tol. opts as for bem_solve with precond 0 or 1 (the learned correction is not batched).
+ * infos: HOST [nrhs] (or NULL), iterations and residuals per right-hand side. The batched
+ * workspace ((2m + 4) nrhs vectors) is kept by the context. Returns BEM_OK when every true
+ * residual reaches tol, BEM_ENOCONV otherwise. */
+int bem_solve_batch(aim_ctx* ctx, const void* b, void* x, int nrhs, const bem_solve_opts* opts,
+                    bem_solve_info* infos, void* stream);
+
 /* Port admittance matrix: for each port q, the solve (bem_solve with opts) of a unit gap
  * voltage on q with the other ports shorted, then the currents of every port p:
  * Y[p][q] = I_p / V_q in siemens (the paper's port excitation, Sec. II; its S-parameter and

@@ -24,7 +24,8 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "bem_precond_apply", "bem_net_init", "bem_net_weights", "bem_net_train",
            "bem_net_apply", "bem_convnet_run", "aim_gemv_select", "aim_gemv_plan",
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
-           "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch"]
+           "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
+           "bem_solve_batch"]
 
 
 class BemError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
         L.aim_matvec_schedule.argtypes = [vp, C.c_int]
         L.aim_matvec_host.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.c_int, vp]
         L.aim_matvec_batch.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
+        L.bem_solve_batch.argtypes = [vp, vp, vp, C.c_int, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
         L.bem_port_ring.argtypes = [vp, C.c_int, C.c_int, d, d, C.POINTER(i32), C.POINTER(d), C.c_int]
         L.bem_rhs_port.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), d, vp, C.c_int, vp]
         L.bem_port_current.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(d), vp, C.c_int,
@@ -441,6 +443,22 @@ class Context:
                                     C.byref(o), C.byref(inf), _stream()))
         return x, {"status": rc, "iters": inf.iters, "resid_est": inf.resid_est,
                    "resid_true": inf.resid_true, "seconds": inf.seconds}
+
+    def solve_batch(self, b, x=None, tol=1e-6, restart=100, max_iter=1000, prec_mode=BEM_C64,
+                    time_limit_s=0.0, precond=0):
+        """bem_solve_batch: b [nrhs * N] complex128 device vectors solved in lockstep."""
+        import torch
+        if b.numel() % self.n:
+            raise ValueError("vector length mismatch")
+        nrhs = b.numel() // self.n
+        if x is None:
+            x = torch.zeros_like(b)
+        o = SolveOpts(tol, restart, max_iter, prec_mode, int(precond), time_limit_s)
+        infos = (SolveInfo * nrhs)()
+        rc = _check(lib().bem_solve_batch(self.h, _ptr(b, torch.complex128), _ptr(x, torch.complex128),
+                                          nrhs, C.byref(o), infos, _stream()))
+        return x, rc, [{"iters": i.iters, "resid_est": i.resid_est, "resid_true": i.resid_true,
+                        "seconds": i.seconds} for i in infos]
 
     # ---- set-up products (host copies) ----------------------------------------------
     def _export(self, what, index=0):

@@ -86,6 +86,7 @@ void aim_destroy(aim_ctx* c) {
   free_geo_store(c);
   free_far_geo(c);
   if (c->gm_ws) cudaFree(c->gm_ws);
+  if (c->gmb_ws) cudaFree(c->gmb_ws);
   delete c;
 }
 
@@ -444,6 +445,22 @@ int bem_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_s
   }
   BEM_TRY(check_prec(o->prec_mode, "bem_solve"));
   return gmres_solve(c, b, x, o, info, (cudaStream_t)stream);
+}
+
+int bem_solve_batch(aim_ctx* c, const void* b, void* x, int nrhs, const bem_solve_opts* o,
+                    bem_solve_info* infos, void* stream) {
+  BEM_TRY(check_ctx(c, "bem_solve_batch"));
+  if (!b || !x || !o || b == x || nrhs < 1 || nrhs > kMaxBatch) {
+    set_error("bem_solve_batch: bad pointers or nrhs outside 1..%d", kMaxBatch);
+    return BEM_EINVAL;
+  }
+  if (!(o->tol > 0) || o->restart < 1 || o->restart > 512 || o->max_iter < 1 || o->precond < 0 ||
+      o->precond > 1) {
+    set_error("bem_solve_batch: bad options (precond 0 or 1)");
+    return BEM_EINVAL;
+  }
+  BEM_TRY(check_prec(o->prec_mode, "bem_solve_batch"));
+  return gmres_solve_batch(c, b, x, nrhs, o, infos, (cudaStream_t)stream);
 }
 
 }  // extern "C"

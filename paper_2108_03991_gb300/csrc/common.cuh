@@ -316,6 +316,11 @@ struct aim_ctx {
   int32_t* d_pcperm = nullptr;  // object-major position -> system index
   float2* pcw32[2] = {nullptr, nullptr};
   double2* pcw64[2] = {nullptr, nullptr};
+  bem::GemvPlan pcmr;                        // several right-hand sides (k_gemv_mr)
+  float2* pcb32[2] = {nullptr, nullptr};     // [kMaxBatch][N] work vectors of the batched apply
+  // batched FGMRES: workspace kept between solves, batched FP32 / FP64 vectors [kMaxBatch][N]
+  void* gmb_ws = nullptr;
+  size_t gmb_bytes = 0;
   // GMRES workspace kept between solves (gmres.cu)
   void* gm_ws = nullptr;
   size_t gm_bytes = 0;
@@ -393,12 +398,16 @@ int net_apply(aim_ctx* c, const float2* r, float2* z, cudaStream_t s);
 void free_net(aim_ctx* c);
 template <typename R> int precond_apply(aim_ctx* c, const void* r, void* u, cudaStream_t s);
 int precond_apply_mixed(aim_ctx* c, const double2* r, float2* u32, double2* u64, cudaStream_t s);
+int precond_apply_batch(aim_ctx* c, const double2* r, int nrhs, float2* u32, double2* u64,
+                        cudaStream_t s);
 void free_geo_store(aim_ctx* c);
 void free_far_geo(aim_ctx* c);
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);
 int tune_matvec_schedule(aim_ctx* c);
 double k0_of(double f);
 // solver (gmres.cu)
+int gmres_solve_batch(aim_ctx* c, const void* b, void* x, int nrhs, const bem_solve_opts* o,
+                      bem_solve_info* infos, cudaStream_t s);
 int gmres_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,
                 cudaStream_t s);
 }  // namespace bem

@@ -403,4 +403,216 @@ int gmres_solve(aim_ctx* c, const void* bv, void* xv, const bem_solve_opts* o, b
   return status;
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched FGMRES: nrhs (<= kMaxBatch) systems A x_r = b_r solved in lockstep. Each right-hand
+// side has its own Krylov basis, Hessenberg matrix and rotations; every iteration applies the
+// preconditioner and the system matrix to all of them at once (aim_matvec_batch and the
+// batched preconditioner read each block matrix once for all), the Gram-Schmidt and Givens
+// steps run per right-hand side. Basis vectors of one step are stored side by side
+// (V[k][r][N]) so the batched products read them as one block. A cycle ends when every
+// right-hand side's residual estimate is below tol (or after m steps); the true FP64 residuals
+// are then taken with one batched FP64 product.
+// ---------------------------------------------------------------------------------------
+struct GmBatch {
+  double2 *V = nullptr, *Zb = nullptr, *w = nullptr, *rr = nullptr, *ax = nullptr;
+  float2 *x32 = nullptr, *y32 = nullptr;
+  double2 *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h = nullptr,
+          *partial = nullptr;
+  double* dsc = nullptr;  // [r][8]: [1] residual estimate, [2] beta; [kMaxBatch * 8] counter
+};
+
+static int gm_batch_workspace(aim_ctx* c, int64_t n, int m, int B, bool flexible, GmBatch* W) {
+  const int ldh = m + 1;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t z = sizeof(double2), f = sizeof(float2);
+  const size_t sizes[14] = {al((size_t)(m + 1) * B * n * z), flexible ? al((size_t)m * B * n * z) : 0,
+                            al(B * n * z), al(B * n * z), al(B * n * z), al(B * n * f), al(B * n * f),
+                            al((size_t)B * ldh * m * z), al((size_t)B * m * z), al((size_t)B * m * z),
+                            al((size_t)B * (m + 1) * z), al((size_t)B * (m + 1) * z),
+                            al((size_t)B * (m + 1) * z), al((size_t)(m + 1) * kChunks * z)};
+  size_t total = al((size_t)(kMaxBatch * 8 + 8) * sizeof(double));
+  for (size_t v : sizes) total += v;
+  if (c->gmb_bytes < total) {
+    if (c->gmb_ws) cudaFree(c->gmb_ws);
+    c->gmb_ws = nullptr;
+    c->gmb_bytes = 0;
+    if (cudaMalloc(&c->gmb_ws, total) != cudaSuccess) {
+      set_error("batched gmres workspace (%zu bytes): out of device memory", total);
+      return BEM_ENOMEM;
+    }
+    c->gmb_bytes = total;
+  }
+  char* p = static_cast<char*>(c->gmb_ws);
+  void** dst[14] = {(void**)&W->V, (void**)&W->Zb, (void**)&W->w, (void**)&W->rr, (void**)&W->ax,
+                    (void**)&W->x32, (void**)&W->y32, (void**)&W->H, (void**)&W->cs, (void**)&W->sn,
+                    (void**)&W->g, (void**)&W->y, (void**)&W->h, (void**)&W->partial};
+  for (int i = 0; i < 14; ++i) {
+    *dst[i] = sizes[i] ? static_cast<void*>(p) : nullptr;
+    p += sizes[i];
+  }
+  W->dsc = reinterpret_cast<double*>(p);
+  return BEM_OK;
+}
+
+static int dots_b(const double2* V, int64_t ldv, int nv, const double2* w, int64_t n, GmBatch& W,
+                  double2* h, double2* acc, cudaStream_t s) {
+  if (nv <= 16) {
+    k_dots_red<<<kChunks, 256, 0, s>>>(V, ldv, nv, w, n, W.partial,
+                                       reinterpret_cast<unsigned*>(W.dsc + kMaxBatch * 8), h, acc);
+  } else {
+    k_dots<<<kChunks, 256, 0, s>>>(V, ldv, nv, w, n, W.partial);
+    k_reduce<<<nv, 256, 0, s>>>(W.partial, kChunks, nv, h, acc);
+  }
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+// y (FP64, B vectors of N) = A x for the batch: FP64 batched product, or FP32 from x32
+static int batch_apply64(aim_ctx* c, const double2* x, double2* y, int B, cudaStream_t s) {
+  BEM_TRY(batch_buffers<double>(c));
+  return matvec_graph<double>(c, kBatchOp + B, x, y, s);
+}
+
+int gmres_solve_batch(aim_ctx* c, const void* bv, void* xv, int B, const bem_solve_opts* o,
+                      bem_solve_info* infos, cudaStream_t s) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const double2* b = (const double2*)bv;
+  double2* x = (double2*)xv;
+  const int64_t n = (int64_t)c->ne + c->nt, Bn = B * n;
+  const int m = o->restart, ldh = m + 1, m1 = m + 1;
+  const bool flexible = o->precond == 1;
+  const bool fp32 = o->prec_mode == BEM_C32;
+  if (flexible) BEM_TRY(setup_precond(c));
+  if (fp32) BEM_TRY(batch_buffers<float>(c));
+  BEM_TRY(batch_buffers<double>(c));
+  GmBatch W;
+  BEM_TRY(gm_batch_workspace(c, n, m, B, flexible, &W));
+  BEM_CUDA(cudaMemsetAsync(W.dsc + kMaxBatch * 8, 0, sizeof(double), s));
+  BEM_CUDA(cudaMemsetAsync(W.H, 0, sizeof(double2) * B * ldh * m, s));
+  std::vector<double2> hh((size_t)B * m1);
+  std::vector<double> dh((size_t)B * 8);
+  for (int r = 0; r < B; ++r) {
+    BEM_TRY(dots_b(b + r * n, n, 1, b + r * n, n, W, W.h + r * m1, nullptr, s));
+    BEM_TRY(dots_b(x + r * n, n, 1, x + r * n, n, W, W.h + r * m1 + 1, nullptr, s));
+  }
+  BEM_CUDA(cudaMemcpyAsync(hh.data(), W.h, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+  BEM_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> bnorm(B), est(B, 1.0), truer(B, 1.0);
+  bool x_zero = true;
+  for (int r = 0; r < B; ++r) {
+    bnorm[r] = std::sqrt(std::max(hh[(size_t)r * m1].x, 0.0));
+    if (bnorm[r] == 0) {  // a zero right-hand side has the zero solution
+      BEM_CUDA(cudaMemsetAsync(x + r * n, 0, n * sizeof(double2), s));
+    } else if (hh[(size_t)r * m1 + 1].x != 0.0) {
+      x_zero = false;
+    }
+  }
+  auto rel = [&](double v, int r) { return bnorm[r] > 0 ? v / bnorm[r] : 0.0; };
+  auto all_below = [&](const std::vector<double>& v) {
+    for (int r = 0; r < B; ++r)
+      if (!(v[r] <= o->tol)) return false;
+    return true;
+  };
+  auto out_of_time = [&]() {
+    return o->time_limit_s > 0 && std::chrono::duration<double>(clk::now() - t0).count() > o->time_limit_s;
+  };
+  int iters = 0;
+  bool fresh = false, converged = false;
+  while (iters < o->max_iter) {
+    // r = b - A x with the batched FP64 product (none for a zero initial guess)
+    if (!x_zero) {
+      BEM_TRY(batch_apply64(c, x, W.ax, B, s));
+      k_sub<<<kChunks, 256, 0, s>>>(b, W.ax, W.rr, Bn);
+    } else {
+      BEM_CUDA(cudaMemcpyAsync(W.rr, b, Bn * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    }
+    x_zero = false;
+    for (int r = 0; r < B; ++r) {
+      BEM_TRY(dots_b(W.rr + r * n, n, 1, W.rr + r * n, n, W, W.h + r * m1, nullptr, s));
+      k_normalize<<<kChunks, 256, 0, s>>>(W.rr + r * n, W.h + r * m1, W.V + r * n, W.dsc + r * 8 + 2, n);
+    }
+    BEM_CUDA(cudaMemcpyAsync(dh.data(), W.dsc, dh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < B; ++r) est[r] = truer[r] = rel(dh[(size_t)r * 8 + 2], r);
+    fresh = true;
+    if (all_below(truer)) { converged = true; break; }
+    if (out_of_time()) break;
+    for (int r = 0; r < B; ++r) k_set_g0<<<1, 256, 0, s>>>(W.g + r * m1, m1, W.dsc + r * 8 + 2);
+    int k = 0;
+    for (; k < m && iters < o->max_iter; ++k) {
+      const double2* Vk = W.V + (int64_t)k * Bn;
+      const double2* in64 = Vk;
+      if (flexible) {
+        double2* Zk = W.Zb + (int64_t)k * Bn;
+        if (fp32) {
+          BEM_TRY(precond_apply_batch(c, Vk, B, W.x32, Zk, s));  // FP32 copy lands in x32
+        } else {
+          for (int r = 0; r < B; ++r) BEM_TRY(precond_apply<double>(c, Vk + r * n, Zk + r * n, s));
+        }
+        in64 = Zk;
+      }
+      if (fp32) {
+        if (!flexible) k_to32<<<kChunks, 256, 0, s>>>(in64, W.x32, Bn);
+        BEM_TRY(matvec_graph<float>(c, kBatchOp + B, W.x32, W.y32, s));
+        k_to64<<<kChunks, 256, 0, s>>>(W.y32, W.w, Bn);
+      } else {
+        // through a fixed input buffer, so that one captured graph serves every step
+        BEM_CUDA(cudaMemcpyAsync(W.rr, in64, Bn * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        BEM_TRY(batch_apply64(c, W.rr, W.w, B, s));
+      }
+      for (int r = 0; r < B; ++r) {
+        const double2* Vr = W.V + r * n;
+        double2* wr = W.w + r * n;
+        double2* hr = W.h + r * m1;
+        double2* Hr = W.H + (int64_t)r * ldh * m;
+        double2* Hk = Hr + (int64_t)k * ldh;
+        BEM_CUDA(cudaMemsetAsync(Hk, 0, sizeof(double2) * (k + 1), s));
+        for (int pass = 0; pass < 2; ++pass) {
+          BEM_TRY(dots_b(Vr, Bn, k + 1, wr, n, W, hr, Hk, s));
+          k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>(Vr, Bn, k + 1, hr, -1.0, wr, n);
+        }
+        BEM_TRY(dots_b(wr, n, 1, wr, n, W, hr, nullptr, s));
+        k_normalize_givens<<<kChunks, 256, 0, s>>>(wr, hr, W.V + (int64_t)(k + 1) * Bn + r * n, n, Hr, ldh,
+                                                   k, W.cs + r * m, W.sn + r * m, W.g + r * m1,
+                                                   W.dsc + r * 8 + 1);
+      }
+      BEM_CUDA(cudaGetLastError());
+      BEM_CUDA(cudaMemcpyAsync(dh.data(), W.dsc, dh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      BEM_CUDA(cudaStreamSynchronize(s));
+      ++iters;
+      for (int r = 0; r < B; ++r) est[r] = rel(dh[(size_t)r * 8 + 1], r);
+      if (all_below(est)) { ++k; break; }
+      if (out_of_time()) { ++k; break; }
+    }
+    // x_r += Z_r y_r (or V_r y_r), y_r = R_r^{-1} g_r
+    for (int r = 0; r < B; ++r) {
+      k_backsolve<<<1, 1, 0, s>>>(W.H + (int64_t)r * ldh * m, ldh, k, W.g + r * m1, W.y + r * m1);
+      k_axpy_basis<<<kChunks, 256, (k + 1) * sizeof(double2), s>>>((flexible ? W.Zb : W.V) + r * n, Bn, k,
+                                                                 W.y + r * m1, 1.0, x + r * n, n);
+    }
+    fresh = false;
+    BEM_CUDA(cudaGetLastError());
+    if (out_of_time()) break;
+  }
+  if (!fresh && !converged) {  // the true residuals of the last update
+    BEM_TRY(batch_apply64(c, x, W.ax, B, s));
+    k_sub<<<kChunks, 256, 0, s>>>(b, W.ax, W.rr, Bn);
+    for (int r = 0; r < B; ++r)
+      BEM_TRY(dots_b(W.rr + r * n, n, 1, W.rr + r * n, n, W, W.h + r * m1, nullptr, s));
+    BEM_CUDA(cudaMemcpyAsync(hh.data(), W.h, hh.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < B; ++r) truer[r] = rel(std::sqrt(std::max(hh[(size_t)r * m1].x, 0.0)), r);
+  }
+  const double secs = std::chrono::duration<double>(clk::now() - t0).count();
+  if (infos)
+    for (int r = 0; r < B; ++r) {
+      infos[r].iters = iters;
+      infos[r].resid_est = est[r];
+      infos[r].resid_true = truer[r];
+      infos[r].seconds = secs;
+    }
+  return all_below(truer) ? BEM_OK : BEM_ENOCONV;
+}
+
 }  // namespace bem

@@ -1402,6 +1402,12 @@ int setup_precond(aim_ctx* c) {
   {
     float pc_ms[2];
     BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan, &c->pcplan64, pc_ms, nullptr));
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int* derr = nullptr;
+    BEM_TRY(dalloc_t(c, &derr, 1));
+    BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 16, 4, 4}, nsm, N, off, ld, derr, &c->pcmr));
   }
   c->pc_ready = true;
   return BEM_OK;
@@ -1454,6 +1460,49 @@ __global__ void k_perm_scatter2(const int32_t* perm, const float2* yp, float2* y
     y32[perm[i]] = v;
     y64[perm[i]] = make_double2(v.x, v.y);
   }
+}
+
+__global__ void k_perm_gather32b(const int32_t* perm, const double2* x, int64_t xs, float2* xp,
+                                 int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double2 v = x[blockIdx.y * xs + perm[i]];
+    xp[(int64_t)blockIdx.y * n + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void k_perm_scatter2b(const int32_t* perm, const float2* yp, float2* y32, double2* y64,
+                                 int64_t ys, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 v = yp[(int64_t)blockIdx.y * n + i];
+    y32[blockIdx.y * ys + perm[i]] = v;
+    y64[blockIdx.y * ys + perm[i]] = make_double2(v.x, v.y);
+  }
+}
+
+// The FP32 preconditioner of nrhs FP64 Krylov vectors r (stride ys = N_E + N_T) at once, the
+// block matrices read once for all of them: u32 (FP32, the batched product's input) and u64
+// (FP64), both with stride ys.
+int precond_apply_batch(aim_ctx* c, const double2* r, int nrhs, float2* u32, double2* u64,
+                        cudaStream_t s) {
+  if (!c->pc_ready || nrhs < 1 || nrhs > kMaxBatch) {
+    set_error("batched preconditioner: not built or nrhs out of range");
+    return BEM_EINVAL;
+  }
+  const int n = c->ne + c->nt;
+  if (!c->pcb32[0])
+    for (int k = 0; k < 2; ++k) BEM_TRY(dalloc_t(c, &c->pcb32[k], (size_t)kMaxBatch * n));
+  const dim3 g(nblk(n, 256), nrhs);
+  k_perm_gather32b<<<g, 256, 0, s>>>(c->d_pcperm, r, n, c->pcb32[0], n);
+  if (c->pcmr.ntasks > 0)
+    BEM_TRY(run_gemv_mr<float>(c->pcmr, (const float2*)c->pc32, c->pcb32[0], c->pcb32[1], nrhs, n,
+                               nullptr, s));
+  else
+    BEM_TRY(run_gemv_plan<float>(c->pcplan, (const float2*)c->pc32, c->pcb32[0], c->pcb32[1], nrhs,
+                                 n, nullptr, s));
+  k_perm_scatter2b<<<g, 256, 0, s>>>(c->d_pcperm, c->pcb32[1], u32, u64, n, n);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
 }
 
 // The FP32 preconditioner of an FP64 Krylov vector: u = M_bd (float) r, returned both in FP32
