@@ -310,8 +310,9 @@ int bem_solve_batch(aim_ctx* ctx, const void* b, void* x, int nrhs, const bem_so
  * impedance outputs follow from Y). Ports are given as rings (bem_port_ring): ring_n[p] edges
  * each, edges and signs HOST arrays holding the rings one after another. Y: HOST
  * [nport][nport] complex doubles (re, im interleaved); infos: HOST [nport] (or NULL), the
- * solve information of each column. Allocates two device vectors of N_E + N_T complex doubles
- * for the call; synchronises the stream. Returns BEM_OK, BEM_ENOCONV when a solve stopped
+ * solve information of each column. With precond 0 or 1 the ports are solved up to four at a
+ * time (bem_solve_batch). Allocates device vectors for the group's right-hand sides and
+ * solutions for the call; synchronises the stream. Returns BEM_OK, BEM_ENOCONV when a solve stopped
  * before tol (Y is still filled), or a negative error (BEM_EINVAL for an empty port or an edge
  * out of range). */
 int bem_port_matrix(aim_ctx* ctx, int nport, const int32_t* ring_n, const int32_t* edges,

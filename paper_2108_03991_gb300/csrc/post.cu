@@ -260,35 +260,47 @@ int bem_port_matrix(aim_ctx* c, int nport, const int32_t* ring_n, const int32_t*
     BEM_TRY(check_edges(c, ring_n[p], edges + off[p], signs + off[p], "bem_port_matrix"));
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = (int64_t)c->ne + c->nt;
+  // ports in groups of up to kMaxBatch solved together (bem_solve_batch) when the options allow
+  const int G = opts->precond <= 1 ? std::min(nport, (int)kMaxBatch) : 1;
   double2 *b = nullptr, *x = nullptr;
-  BEM_CUDA(cudaMalloc((void**)&b, N * sizeof(double2)));
-  if (cudaMalloc((void**)&x, N * sizeof(double2)) != cudaSuccess) {
+  BEM_CUDA(cudaMalloc((void**)&b, G * N * sizeof(double2)));
+  if (cudaMalloc((void**)&x, G * N * sizeof(double2)) != cudaSuccess) {
     cudaFree(b);
     set_error("bem_port_matrix: out of device memory");
     return BEM_ENOMEM;
   }
   int worst = BEM_OK;
-  for (int q = 0; q < nport && worst >= 0; ++q) {
+  std::vector<bem_solve_info> inf(G);
+  for (int q0 = 0; q0 < nport && worst >= 0; q0 += G) {
+    const int g = std::min(G, nport - q0);
     // unit gap voltage on port q, the others shorted; Y_pq = I_p / V_q
-    int rc = bem_rhs_port(c, ring_n[q], edges + off[q], signs + off[q], 1.0, b, BEM_C64, stream);
-    if (rc == BEM_OK && cudaMemsetAsync(x, 0, N * sizeof(double2), s) != cudaSuccess) rc = BEM_ECUDA;
-    bem_solve_info info{};
-    if (rc == BEM_OK) rc = bem_solve(c, b, x, opts, &info, stream);
+    int rc = BEM_OK;
+    for (int i = 0; i < g && rc == BEM_OK; ++i)
+      rc = bem_rhs_port(c, ring_n[q0 + i], edges + off[q0 + i], signs + off[q0 + i], 1.0, b + i * N,
+                        BEM_C64, stream);
+    if (rc == BEM_OK && cudaMemsetAsync(x, 0, g * N * sizeof(double2), s) != cudaSuccess) rc = BEM_ECUDA;
+    if (rc == BEM_OK)
+      rc = g > 1 ? bem_solve_batch(c, b, x, g, opts, inf.data(), stream)
+                 : bem_solve(c, b, x, opts, inf.data(), stream);
     if (rc < 0) {
       worst = rc;
       break;
     }
     worst = std::max(worst, rc);
-    if (infos) infos[q] = info;
-    for (int p = 0; p < nport && worst >= 0; ++p) {
-      double cur[2];
-      const int r2 = bem_port_current(c, ring_n[p], edges + off[p], signs + off[p], x, BEM_C64, cur, stream);
-      if (r2 != BEM_OK) {
-        worst = r2;
-        break;
+    for (int i = 0; i < g && worst >= 0; ++i) {
+      const int q = q0 + i;
+      if (infos) infos[q] = inf[i];
+      for (int p = 0; p < nport; ++p) {
+        double cur[2];
+        const int r2 = bem_port_current(c, ring_n[p], edges + off[p], signs + off[p], x + i * N,
+                                        BEM_C64, cur, stream);
+        if (r2 != BEM_OK) {
+          worst = r2;
+          break;
+        }
+        Y[2 * (p * nport + q)] = cur[0];
+        Y[2 * (p * nport + q) + 1] = cur[1];
       }
-      Y[2 * (p * nport + q)] = cur[0];
-      Y[2 * (p * nport + q) + 1] = cur[1];
     }
   }
   cudaFree(b);
