@@ -61,15 +61,31 @@ __global__ void k_reduce(const double2* __restrict__ partial, int nchunks, int n
   }
 }
 
+// Offsets of right-hand side blockIdx.y when a kernel serves a batch of systems (batched
+// FGMRES); all zero for one system.
+struct KOff {
+  int64_t V = 0, w = 0, h = 0, acc = 0, part = 0, out = 0, H = 0, cs = 0, g = 0, res = 0;
+};
+
 // The same and their reduction in one launch, for a short basis: every block writes its
 // partial sums, and the block that finishes last (a counter it sets back to zero) adds the partials:
 // h[j] = sum of partials; if acc != nullptr: acc[j] += h[j]. No block waits for another.
 __global__ void __launch_bounds__(256) k_dots_red(const double2* __restrict__ V, int64_t ldv, int nv,
                                                   const double2* __restrict__ w, int64_t n,
                                                   double2* __restrict__ partial, unsigned* ctr,
-                                                  double2* __restrict__ h, double2* acc) {
+                                                  double2* __restrict__ h, double2* acc,
+                                                  KOff o = KOff()) {
   __shared__ double2 red[8];
   __shared__ bool last;
+  {
+    const int64_t y = blockIdx.y;  // the counter of system y is ctr[y]
+    V += y * o.V;
+    w += y * o.w;
+    partial += y * o.part;
+    ctr += y;
+    h += y * o.h;
+    if (acc) acc += y * o.acc;
+  }
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
   for (int j = 0; j < nv; ++j) {
@@ -115,8 +131,12 @@ __global__ void __launch_bounds__(256) k_dots_red(const double2* __restrict__ V,
 
 // w += sign * sum_j h[j] V[j]
 __global__ void k_axpy_basis(const double2* __restrict__ V, int64_t ldv, int nv,
-                             const double2* __restrict__ h, double sign, double2* w, int64_t n) {
+                             const double2* __restrict__ h, double sign, double2* w, int64_t n,
+                             KOff o = KOff()) {
   extern __shared__ double2 hs[];
+  V += blockIdx.y * o.V;
+  h += blockIdx.y * o.h;
+  w += blockIdx.y * o.w;
   for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = h[j];
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -184,7 +204,18 @@ __device__ void givens_step(double2* H, int ldh, int k, double hsub, double2* cs
 // subdiagonal |w| (the Arnoldi step's last two operations in one launch)
 __global__ void k_normalize_givens(const double2* __restrict__ in, const double2* nrm2, double2* out,
                                    int64_t n, double2* H, int ldh, int k, double2* cs, double2* sn,
-                                   double2* g, double* resid) {
+                                   double2* g, double* resid, KOff o = KOff()) {
+  {
+    const int64_t y = blockIdx.y;
+    in += y * o.w;
+    nrm2 += y * o.h;
+    out += y * o.out;
+    H += y * o.H;
+    cs += y * o.cs;
+    sn += y * o.cs;
+    g += y * o.g;
+    resid += y * o.res;
+  }
   const double nr = sqrt(fmax(nrm2->x, 0.0));
   const double s = nr > 0 ? 1.0 / nr : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -429,7 +460,7 @@ static int gm_batch_workspace(aim_ctx* c, int64_t n, int m, int B, bool flexible
                             al(B * n * z), al(B * n * z), al(B * n * z), al(B * n * f), al(B * n * f),
                             al((size_t)B * ldh * m * z), al((size_t)B * m * z), al((size_t)B * m * z),
                             al((size_t)B * (m + 1) * z), al((size_t)B * (m + 1) * z),
-                            al((size_t)B * (m + 1) * z), al((size_t)(m + 1) * kChunks * z)};
+                            al((size_t)B * (m + 1) * z), al((size_t)B * (m + 1) * kChunks * z)};
   size_t total = al((size_t)(kMaxBatch * 8 + 8) * sizeof(double));
   for (size_t v : sizes) total += v;
   if (c->gmb_bytes < total) {
@@ -488,7 +519,7 @@ int gmres_solve_batch(aim_ctx* c, const void* bv, void* xv, int B, const bem_sol
   BEM_TRY(batch_buffers<double>(c));
   GmBatch W;
   BEM_TRY(gm_batch_workspace(c, n, m, B, flexible, &W));
-  BEM_CUDA(cudaMemsetAsync(W.dsc + kMaxBatch * 8, 0, sizeof(double), s));
+  BEM_CUDA(cudaMemsetAsync(W.dsc + kMaxBatch * 8, 0, 8 * sizeof(double), s));  // counters
   BEM_CUDA(cudaMemsetAsync(W.H, 0, sizeof(double2) * B * ldh * m, s));
   std::vector<double2> hh((size_t)B * m1);
   std::vector<double> dh((size_t)B * 8);
@@ -561,7 +592,41 @@ int gmres_solve_batch(aim_ctx* c, const void* bv, void* xv, int B, const bem_sol
         BEM_CUDA(cudaMemcpyAsync(W.rr, in64, Bn * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         BEM_TRY(batch_apply64(c, W.rr, W.w, B, s));
       }
-      for (int r = 0; r < B; ++r) {
+      if (k + 1 <= 16) {  // every system's Gram-Schmidt and Givens steps in the same launches
+        for (int r = 0; r < B; ++r)
+          BEM_CUDA(cudaMemsetAsync(W.H + (int64_t)r * ldh * m + (int64_t)k * ldh, 0,
+                                   sizeof(double2) * (k + 1), s));
+        unsigned* ctr = reinterpret_cast<unsigned*>(W.dsc + kMaxBatch * 8);
+        KOff o;
+        o.V = n;
+        o.w = n;
+        o.h = m1;
+        o.acc = (int64_t)ldh * m;
+        o.part = (int64_t)m1 * kChunks;
+        const dim3 gb(kChunks, B);
+        for (int pass = 0; pass < 2; ++pass) {
+          k_dots_red<<<gb, 256, 0, s>>>(W.V, Bn, k + 1, W.w, n, W.partial, ctr, W.h,
+                                        W.H + (int64_t)k * ldh, o);
+          k_axpy_basis<<<gb, 256, (k + 1) * sizeof(double2), s>>>(W.V, Bn, k + 1, W.h, -1.0, W.w, n, o);
+        }
+        KOff on;
+        on.V = n;
+        on.w = n;
+        on.h = m1;
+        on.part = (int64_t)m1 * kChunks;
+        k_dots_red<<<gb, 256, 0, s>>>(W.w, n, 1, W.w, n, W.partial, ctr, W.h, nullptr, on);
+        KOff og;
+        og.w = n;
+        og.h = m1;
+        og.out = n;
+        og.H = (int64_t)ldh * m;
+        og.cs = m;
+        og.g = m1;
+        og.res = 8;
+        k_normalize_givens<<<gb, 256, 0, s>>>(W.w, W.h, W.V + (int64_t)(k + 1) * Bn, n, W.H, ldh, k,
+                                              W.cs, W.sn, W.g, W.dsc + 1, og);
+      }
+      for (int r = 0; r < B && k + 1 > 16; ++r) {
         const double2* Vr = W.V + r * n;
         double2* wr = W.w + r * n;
         double2* hr = W.h + r * m1;
