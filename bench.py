@@ -206,7 +206,9 @@ def ncu_case(args):
     aim:  the grid convolution (4 components) on the workload's AIM grid, set up on two small
           boxes at opposite corners of the array's bounding box (same grid, tiny set-up);
     internal: the workload's own internal products (e = Z h, h_eq = Y e) with the launch the
-          set-up autotuner chose, inside the profiler range "internal_steps"."""
+          set-up autotuner chose, inside the profiler range "internal_steps".
+    batch: the workload's batched system matvec of 4 right-hand sides, inside the profiler
+          range "batch_steps"."""
     import numpy as np
     import torch
 
@@ -226,6 +228,21 @@ def ncu_case(args):
             ctx.conv(s, phi, ncomp=4, prec=api.BEM_C32)
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": "aim", "grid": list(ctx.grid_n), "fft": list(ctx.padded)}))
+        return
+    if args.ncu_case == "batch":
+        mesh, grid, freq = synth.bar_array_config(0, 10e9)
+        ctx = api.Context(mesh, grid, freq)
+        xb = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.n, 500 + r) for r in range(4)])
+                              .astype(np.complex64)).cuda()
+        yb = torch.empty_like(xb)
+        ctx.matvec_batch(xb, yb)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("batch_steps")
+        for _ in range(args.steps):
+            ctx.matvec_batch(xb, yb)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "batch", "nrhs": 4}))
         return
     if args.ncu_case == "internal":
         mesh, grid, freq = synth.bar_array_config(0, 10e9)
@@ -366,7 +383,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal"])
+    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal", "batch"])
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--precision-study", action="store_true")
     ap.add_argument("--gemv-shape", default=None,
