@@ -589,7 +589,7 @@ def main():
                                     "loads_in_flight": ctx.gemv_unroll,
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
                                     "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
-                                                       for r in ctx.gemv_tune_table() if r[0] != 4],
+                                                       for r in ctx.gemv_tune_table() if r[0] not in (4, 7)],
                                     "matvec_schedule": ctx.matvec_mode,
                                     "matvec_schedules": [[int(v) for v in r[1:4]] + [float(r[4])]
                                                          for r in ctx.gemv_tune_table() if r[0] == 4]}},
@@ -598,6 +598,8 @@ def main():
                     "call": "aim_matvec_host (pinned host vectors, copies overlapped)"},
             "batched": {"nrhs": 4, "value": replicas_value(batch_ms / 4, world), "unit": UNIT,
                         "ms_per_launch": batch_ms,
+                        "gemv_shapes_ns": [[int(r[2]), float(r[4])] for r in ctx.gemv_tune_table()
+                                           if r[0] == 7],
                         "note": "aim_matvec_batch: 4 right-hand sides per graph, matvecs/s counted per right-hand side"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),

@@ -209,8 +209,10 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *           launch, or -1 when the candidate was rejected or not applicable), then the
  *           system-matvec schedules (4; CTAs per SM of the e = Z h launch that runs beside the
  *           AIM chain, 0 when it runs on the main stream; 0 = it starts with j's GEMV, 1 = after
- *           it beside the chain, 2 = after it on the main stream with j's launch shape; kind of
- *           that launch; ns per matvec)
+ *           it beside the chain, 2 = after it on the main stream with j's launch shape, 3 = both
+ *           in one paired launch; kind of that launch; ns per matvec), then the
+ *           multi-right-hand-side GEMV shapes of the batched matvec (7; 16; rows per warp; 4;
+ *           ns per launch of 4 right-hand sides)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
 

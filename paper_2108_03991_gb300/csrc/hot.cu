@@ -115,13 +115,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_gemv(const GemvTask* __restri
   }
 }
 
-// Several right-hand sides at once: each warp takes RB = 4 rows of its task and NR right-hand
+// Several right-hand sides at once: each warp takes RB (2 or 4) rows of its task and NR right-hand
 // sides, so every 16-byte load of the matrix (two complex entries of one row) meets NR vectors
 // and every load of x serves RB rows (a register tile of RB x NR accumulators). One CTA of NW
-// warps per task of at most 4 NW rows; y_r = A x_r, or hsub_r - A x_r. x is read as 8-byte
+// warps per task of at most RB NW rows; y_r = A x_r, or hsub_r - A x_r. x is read as 8-byte
 // complex pairs (its slices need not be 16-byte aligned); an odd row length masks the last
 // pair's second entry.
-template <typename R, int NR, int NW>
+template <typename R, int NR, int NW, int RB>
 __global__ void __launch_bounds__(NW * 32) k_gemv_mr(const GemvTask* __restrict__ tasks,
                                                      const typename C2<R>::T* __restrict__ A,
                                                      const typename C2<R>::T* __restrict__ x,
@@ -130,7 +130,6 @@ __global__ void __launch_bounds__(NW * 32) k_gemv_mr(const GemvTask* __restrict_
   typedef typename C2<R>::T V;
   typedef typename Vec16<R>::T L16;  // 16 bytes: two complex FP32 or one complex FP64
   constexpr int CP = Vec16<R>::kCplx;
-  constexpr int RB = 4;
   const GemvTask t = tasks[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = t.row0 + warp * RB;
@@ -204,12 +203,24 @@ int run_gemv_mr(const GemvPlan& p, const typename C2<R>::T* A, const typename C2
     const int nr = std::min(4, nrhs - r0);
     const int64_t o = r0 * vstride;
     const typename C2<R>::T* hs = hsub ? hsub + o : nullptr;
-    switch (nr) {
-      case 1: k_gemv_mr<R, 1, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
-      case 2: k_gemv_mr<R, 2, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
-      case 3: k_gemv_mr<R, 3, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
-      default: k_gemv_mr<R, 4, 4><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs); break;
+    // RB = rows per warp = the plan's rows per task / 4 warps (its split)
+#define BEM_MR(NRV, RBV) k_gemv_mr<R, NRV, 4, RBV><<<p.ntasks, 128, 0, s>>>(p.tasks, A, x + o, y + o, vstride, hs)
+    if (p.split == 2) {
+      switch (nr) {
+        case 1: BEM_MR(1, 2); break;
+        case 2: BEM_MR(2, 2); break;
+        case 3: BEM_MR(3, 2); break;
+        default: BEM_MR(4, 2); break;
+      }
+    } else {
+      switch (nr) {
+        case 1: BEM_MR(1, 4); break;
+        case 2: BEM_MR(2, 4); break;
+        case 3: BEM_MR(3, 4); break;
+        default: BEM_MR(4, 4); break;
+      }
     }
+#undef BEM_MR
   }
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;

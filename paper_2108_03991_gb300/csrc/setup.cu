@@ -773,8 +773,41 @@ int tune_matvec_schedule(aim_ctx* c) {
     p.ntasks = p.ncta = (int)t1.size();
     c->gpair = p;
   }
-  // the multi-right-hand-side launch (4 warps of 4 rows per task) of the batched matvec
-  BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 16, 4, 4}, nsm, n, c->zoff, c->zld, derr, &c->gmr));
+  // the multi-right-hand-side launch of the batched matvec: 4 warps of 4 or of 2 rows per task,
+  // the faster on 4 right-hand sides of Z (CUDA events, 5 launches each)
+  {
+    GemvPlan cand[2];
+    BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 16, 4, 4}, nsm, n, c->zoff, c->zld, derr, &cand[0]));
+    BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 16, 2, 4}, nsm, n, c->zoff, c->zld, derr, &cand[1]));
+    const int64_t ne = c->ne;
+    float2 *xx = nullptr, *yy = nullptr;
+    BEM_CUDA(cudaMalloc(&xx, 4 * ne * sizeof(float2)));
+    if (cudaMalloc(&yy, 4 * ne * sizeof(float2)) != cudaSuccess) {
+      cudaFree(xx);
+      set_error("schedule tuner: out of device memory");
+      return BEM_ENOMEM;
+    }
+    cudaMemset(xx, 0, 4 * ne * sizeof(float2));
+    cudaEvent_t a0, a1;
+    cudaEventCreate(&a0);
+    cudaEventCreate(&a1);
+    float tm[2] = {0, 0};
+    for (int i = 0; i < 2; ++i) {
+      run_gemv_mr<float>(cand[i], c->f32.Z, xx, yy, 4, ne, nullptr, 0);
+      cudaEventRecord(a0, 0);
+      for (int r = 0; r < 5; ++r) run_gemv_mr<float>(cand[i], c->f32.Z, xx, yy, 4, ne, nullptr, 0);
+      cudaEventRecord(a1, 0);
+      cudaEventSynchronize(a1);
+      cudaEventElapsedTime(&tm[i], a0, a1);
+      c->tune_table.insert(c->tune_table.end(), {7.f, 16.f, (float)cand[i].split, 4.f, tm[i] * 1e6f / 5.f});
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    cudaFree(xx);
+    cudaFree(yy);
+    BEM_CUDA(cudaGetLastError());
+    c->gmr = tm[1] < tm[0] ? cand[1] : cand[0];
+  }
   // the last two entries stand for the serial schedules (e = Z h after j's GEMV with its
   // launch shape; both in one paired launch)
   const GemvCand zc[] = {{1, 1, 1, 8}, {1, 2, 1, 8}, {1, 3, 1, 8}, {6, 2, 2, 4}, {6, 3, 2, 4}, {6, 4, 2, 4},
