@@ -827,15 +827,18 @@ int tune_matvec_schedule(aim_ctx* c) {
       for (int w = 0; w < 3 && rc == BEM_OK; ++w) rc = matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s);
       if (rc != BEM_OK) break;
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 20 && rc == BEM_OK; ++r) rc = matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s);
+      for (int r = 0; r < 40 && rc == BEM_OK; ++r) rc = matvec_graph<float>(c, AIM_OP_SYSTEM, c->f32.xin, c->f32.yout, s);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       c->tune_table.insert(c->tune_table.end(), {4.f, after >= 2 ? 0.f : (float)g.cps, (float)after,
                                                  after >= 2 ? (float)(c->gplan.ctr ? 6 : c->gplan.ntasks ? 5 : 1) : (float)g.kind,
-                                                 ms * 1e6f / 20.f});
-      if (ms < best) { best = ms; best_g = g; best_after = after; }
+                                                 ms * 1e6f / 40.f});
+      // a schedule with e beside other work must win by 2%: its time depends on how the
+      // concurrent kernels interleave and varies more from run to run than the serial ones
+      const float eff = after < 2 ? ms * 1.02f : ms;
+      if (eff < best) { best = eff; best_g = g; best_after = after; }
     }
     if (rc != BEM_OK) break;
   }
