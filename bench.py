@@ -189,13 +189,15 @@ def run_reference(args, rank, world):
 # DRAM bytes (read + write) per launch of the block GEMV from the ncu capture summarised in
 # profiles/gemv_internal_bar_array.md; valid only for the launch shape captured there
 # DRAM bytes per launch (read + write) of the GEMV shapes captured with ncu on this workload,
-# keyed by (kind, CTAs per SM, split, loads in flight) as aim_info reports them
+# keyed by (kind, CTAs per SM, split, loads in flight) as aim_info reports them ("pair" first:
+# the paired launch of that shape)
 PROFILED_GEMV = {(1, 6, 0, 4): 207.9e6, (5, 4, 2, 4): 204.9e6, (5, 16, 1, 4): 208.3e6,
-                 (5, 8, 1, 4): 207.6e6}
+                 (5, 8, 1, 4): 207.6e6, ("pair", 5, 16, 1, 4): 409.7e6}
 
 
-def gemv_traffic(ctx):
-    b = PROFILED_GEMV.get((ctx.gemv_kind, ctx.gemv_cps, ctx.gemv_split, ctx.gemv_unroll))
+def gemv_traffic(ctx, paired=False):
+    key = (ctx.gemv_kind, ctx.gemv_cps, ctx.gemv_split, ctx.gemv_unroll)
+    b = PROFILED_GEMV.get(("pair",) + key if paired else key)
     return int(b) if b else None
 
 
@@ -249,6 +251,8 @@ def ncu_case(args):
         ctx = api.Context(mesh, grid, freq)
         if args.gemv_shape:  # the launch the timed run chose (the autotuner's timing under a
             ctx.gemv_plan(*[int(v) for v in args.gemv_shape.split(",")])  # profiler differs)
+        if args.schedule is not None:  # 3: both products in the paired launch
+            ctx.matvec_schedule(args.schedule)
         h = torch.from_numpy(synth.rand_cvec(ctx.ne, 4).astype(np.complex64)).cuda()
         e, heq = torch.empty_like(h), torch.empty_like(h)
         torch.cuda.synchronize()
@@ -386,6 +390,8 @@ def main():
     ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal", "batch"])
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--precision-study", action="store_true")
+    ap.add_argument("--schedule", type=int, default=None,
+                    help="matvec schedule (aim_matvec_schedule) in --ncu-case internal")
     ap.add_argument("--gemv-shape", default=None,
                     help="kind,ctas_per_sm,split,unroll of the GEMV launch in --ncu-case internal")
     args = ap.parse_args()
@@ -434,7 +440,8 @@ def main():
         ev1.record(s)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
-        # dominant kernel: the block-diagonal GEMV (two launches per internal_apply)
+        # dominant kernel: the block-diagonal GEMV, as the matvec launches it: one paired launch
+        # of C and Z per internal_apply under the paired schedule, else two launches
         e = torch.empty(ctx.ne, dtype=torch.complex64, device=dev)
         heq = torch.empty_like(e)
         h = x[:ctx.ne].contiguous()
@@ -446,7 +453,8 @@ def main():
             ctx.internal(h, e, heq, prec=api.BEM_C32)
         ev1.record(s)
         torch.cuda.synchronize()
-        gemv_ms = ev0.elapsed_time(ev1) / (2 * args.steps)
+        paired = ctx.matvec_mode == 3
+        gemv_ms = ev0.elapsed_time(ev1) / ((1 if paired else 2) * args.steps)
         # the batched system matvec: 4 right-hand sides per graph launch
         xb = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.n, 500 + r) for r in range(4)])
                               .astype(np.complex64)).to(dev)
@@ -550,8 +558,10 @@ def main():
     if rank == 0:
         hbm, src = peaks()
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        ZY = ctx.zy_bytes_c32 // 2  # bytes of Z (or Y) in FP32, one GEMV launch
-        gemv_bytes = ZY + 2 * 8 * ctx.ne
+        ZY = ctx.zy_bytes_c32 // 2  # bytes of Z (or C) in FP32
+        # algorithmic bytes of one launch: the matrix (both under the paired schedule), x read,
+        # the output(s) written
+        gemv_bytes = 2 * ZY + 3 * 8 * ctx.ne if paired else ZY + 2 * 8 * ctx.ne
         achieved = gemv_bytes / (gemv_ms * 1e-3) / 1e9
         cpu = None
         if not args.no_cpu:
@@ -572,9 +582,11 @@ def main():
                        "nnz_near": [ctx.nnz_A, ctx.nnz_P], "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (Z, Y ~%.0f MB)" % (ctx.zy_bytes_c32 / 1e6),
                        "setup_s": setup_s},
-            "roofline": {"kernel": "k_gemv (block-diagonal Z / Y_eq)", "bound": "hbm",
+            "roofline": {"kernel": ("k_gemv_pair (C = Y_eq Z and Z in one launch)" if paired
+                                    else "k_gemv (block-diagonal Z / C)"), "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_source": src, "traffic": gemv_traffic(ctx),
+                         "frac": achieved / hbm, "peak_source": src,
+                         "traffic": gemv_traffic(ctx, paired),
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/gemv_internal_bar_array.md)",
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
                          "launch": {"kind": {0: "row plan", 1: "flat", 2: "staged", 3: "stream",

@@ -164,7 +164,9 @@ int aim_matvec_host(aim_ctx* ctx, int which, const void* x, void* y, int nvec, i
                     void* stream);
 
 /* The internal problem (Sec. II-B, Eqs. MFIEinZin, EFIEeqYeq): e = Z h, h_eq = Y e, for
- * nrhs right-hand sides stored one after another (each N_E long). heq may be NULL. */
+ * nrhs right-hand sides stored one after another (each N_E long). heq may be NULL. With one
+ * right-hand side, both outputs and the paired matvec schedule (aim_matvec_schedule mode 3),
+ * the two products are one launch, as in the system matvec. */
 int internal_apply(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, int prec,
                    void* stream);
 

@@ -1174,6 +1174,8 @@ int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStr
   typedef typename C2<R>::T V;
   PrecBuf<R>& b = buf<R>(c);
   const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
+  if (nrhs == 1 && heqv && c->z_after == 3 && c->gpair.ntasks > 0)  // the matvec's paired launch
+    return run_gemv_pair<R>(c->gpair, b.C, b.Z, (const V*)hv, (V*)heqv, (V*)ev, nullptr, s);
   BEM_TRY(run_gemv_plan<R>(gp, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
   if (heqv) BEM_TRY(run_gemv_plan<R>(gp, b.C, (const V*)hv, (V*)heqv, nrhs, c->ne, nullptr, s));
   return BEM_OK;

@@ -665,6 +665,8 @@ static int autotune_gemv(aim_ctx* c, const std::vector<int32_t>& n, const std::v
 
 // A caller-chosen FP32 launch for the context's internal products (kind 0 row plan, 1 flat,
 // 2 staged, 3 stream), checked against the autotuner's reference product before use.
+static int make_pair_plan(aim_ctx* c, const GemvPlan& base, int nsm, GemvPlan* out);
+
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
   const bool ok_shape =
       (kind == 0 && (cps == 4 || cps == 6) && (split == 1 || split == 2 || split == 4) &&
@@ -722,6 +724,26 @@ int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll) {
     return BEM_ECUDA;
   }
   c->gplan = p;
+  if (kind == 5) BEM_TRY(make_pair_plan(c, p, nsm, &c->gpair));  // the paired launch follows the shape
+  return BEM_OK;
+}
+
+// The paired task list of a task-list launch shape: its tasks over C (sel 0), then over Z (sel 1)
+static int make_pair_plan(aim_ctx* c, const GemvPlan& base, int nsm, GemvPlan* out) {
+  std::vector<int32_t> n(c->nobj), xo(c->nobj);
+  for (int i = 0, acc = 0; i < c->nobj; acc += n[i], ++i) {
+    n[i] = c->e1[i] - c->e0[i];
+    xo[i] = acc;
+  }
+  std::vector<GemvTask> t1;
+  build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, (base.task_form == 2 ? 4 : 8) * base.split, &t1);
+  std::vector<GemvTask> t2 = t1;
+  for (GemvTask& t : t2) t.sel = 1;
+  t1.insert(t1.end(), t2.begin(), t2.end());
+  GemvPlan p = base;
+  BEM_TRY(upload(c, &p.tasks, t1.data(), t1.size()));
+  p.ntasks = p.ncta = (int)t1.size();
+  *out = p;
   return BEM_OK;
 }
 
@@ -758,20 +780,10 @@ int tune_matvec_schedule(aim_ctx* c) {
   // else in the 8-row, 8-warp shape
   c->gpair = GemvPlan();
   {
-    const bool tl = c->gplan.ntasks > 0 && !c->gplan.ctr;
     GemvPlan p;
-    if (tl) p = c->gplan;
+    if (c->gplan.ntasks > 0 && !c->gplan.ctr) p = c->gplan;
     else BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 8, 1, 4}, nsm, n, c->zoff, c->zld, derr, &p));
-    std::vector<int32_t> xo(n.size());
-    for (size_t i = 0, acc = 0; i < n.size(); acc += n[i], ++i) xo[i] = (int32_t)acc;
-    std::vector<GemvTask> t1;
-    build_gemv_tasks(n, c->zoff, xo, c->zld, nsm, (p.task_form == 2 ? 4 : 8) * p.split, &t1);
-    std::vector<GemvTask> t2 = t1;
-    for (GemvTask& t : t2) t.sel = 1;
-    t1.insert(t1.end(), t2.begin(), t2.end());
-    BEM_TRY(upload(c, &p.tasks, t1.data(), t1.size()));
-    p.ntasks = p.ncta = (int)t1.size();
-    c->gpair = p;
+    BEM_TRY(make_pair_plan(c, p, nsm, &c->gpair));
   }
   // the multi-right-hand-side launch of the batched matvec: 4 warps of 4 or of 2 rows per task,
   // the faster on 4 right-hand sides of Z (CUDA events, 5 launches each)
