@@ -280,7 +280,7 @@ struct aim_ctx {
   bem::PrecBuf<double> f64;
   std::vector<void*> allocs;   // every device allocation, freed by aim_destroy
   void* geo_store = nullptr;   // device geometry descriptor (set-up kernels, right-hand sides)
-  // streams for the two-branch matvec and its CUDA-graph capture
+  // streams of the system matvec (main, charge side, e = Z h side) and its CUDA-graph capture
   cudaStream_t cap = nullptr, side = nullptr, zside = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_z = nullptr, ev_c = nullptr;
   // host-buffer matvecs: two device buffer pairs, copy streams and their events (lazily made)

@@ -747,13 +747,14 @@ static int make_pair_plan(aim_ctx* c, const GemvPlan& base, int nsm, GemvPlan* o
   return BEM_OK;
 }
 
-// Schedule autotuner of the system matvec: e = Z h runs beside the AIM chain of j with a
-// launch of few CTAs, or after j's GEMV on the main stream with the whole GPU. Time the
-// captured FP32 graph for each (launch of e: the flat form or the dynamic task list, and its
-// CTAs per SM; start with j's GEMV, after it beside the chain, or after it on the main stream)
-// with CUDA events and keep the fastest; the FP64 matvec uses the same choice. tune_table gains
-// rows (4, CTAs per SM or 0 for the main-stream launch, start 0/1/2, kind of the e launch, ns
-// per matvec).
+// Schedule autotuner of the system matvec: e = Z h runs beside j's GEMV or beside the AIM
+// chain of j with a launch of few CTAs, after j's GEMV on the main stream with the whole GPU,
+// or with j's GEMV in one paired task list. Time the captured FP32 graph for each (launch of
+// e: the flat form or the dynamic task list, and its CTAs per SM; schedule 0-3) with CUDA
+// events and keep the fastest, a concurrent schedule having to win by 2%; the FP64 matvec uses
+// the same choice. tune_table gains rows (4, CTAs per SM or 0 for the main-stream launches,
+// schedule, kind of the e launch, ns per matvec). It also times the two shapes of the
+// multi-right-hand-side GEMV of the batched matvec (rows 7, 16, rows per warp, 4, ns).
 int tune_matvec_schedule(aim_ctx* c) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
