@@ -608,7 +608,8 @@ def main():
                                                          for r in ctx.gemv_tune_table() if r[0] == 4]}},
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n,
-                    "call": "aim_matvec_host (pinned host vectors, copies overlapped)"},
+                    "call": "aim_matvec_host: 200 distinct pinned host vectors, taken 4 at a "
+                            "time by the batched product, copies overlapped with the products"},
             "batched": {"nrhs": 4, "value": replicas_value(batch_ms / 4, world), "unit": UNIT,
                         "ms_per_launch": batch_ms,
                         "gemv_shapes_ns": [[int(r[2]), float(r[4])] for r in ctx.gemv_tune_table()

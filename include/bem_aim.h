@@ -155,8 +155,9 @@ int aim_matvec_batch(aim_ctx* ctx, const void* x, void* y, int nrhs, int prec, v
 
 /* y_i = A x_i for nvec vectors in HOST memory (x, y: nvec vectors of the operator's length,
  * one after another; page-locked memory lets the copies run asynchronously): the products of
- * aim_matvec, with the host-to-device copy of x_{i+1} and the device-to-host copy of y_{i-1}
- * overlapping the product of x_i (two device buffer pairs kept by the context, two copy
+ * aim_matvec (the system operator takes the vectors four at a time through aim_matvec_batch),
+ * with the host-to-device copy of the next vectors and the device-to-host copy of the previous
+ * ones overlapping the current product (two device buffer pairs kept by the context, two copy
  * streams). Ordered after the work already on `stream`; the work on `stream` after the call
  * waits for the last copy to the host, so synchronising `stream` makes y readable. x and y must
  * not alias. Errors: BEM_EINVAL (bad pointers, nvec < 1, unknown operator), BEM_ENOMEM. */

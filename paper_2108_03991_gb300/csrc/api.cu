@@ -180,8 +180,14 @@ int aim_matvec_host(aim_ctx* c, int which, const void* x, void* y, int nvec, int
       BEM_CUDA(cudaEventCreateWithFlags(&c->ev_out[b], cudaEventDisableTiming));
     }
   }
-  if (c->hbuf_bytes < bytes) {  // the largest operator length in FP64 serves every call
-    const size_t big = ((size_t)c->ne + c->nt) * sizeof(double2);
+  // the system operator takes the vectors kMaxBatch at a time through the batched product
+  const int G = which == AIM_OP_SYSTEM ? kMaxBatch : 1;
+  if (G > 1) {
+    if (prec == BEM_C32) BEM_TRY(batch_buffers<float>(c));
+    else BEM_TRY(batch_buffers<double>(c));
+  }
+  if (c->hbuf_bytes < (size_t)G * bytes) {  // kMaxBatch system vectors in FP64 serve every call
+    const size_t big = (size_t)kMaxBatch * ((size_t)c->ne + c->nt) * sizeof(double2);
     BEM_CUDA(cudaDeviceSynchronize());
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // keyed by the old buffers
     c->graphs.clear();
@@ -206,24 +212,28 @@ int aim_matvec_host(aim_ctx* c, int which, const void* x, void* y, int nvec, int
   BEM_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_in[0], 0));
   const char* xh = static_cast<const char*>(x);
   char* yh = static_cast<char*>(y);
-  for (int i = 0; i < nvec; ++i) {
-    const int b = i & 1;
+  const int ngroup = (nvec + G - 1) / G;
+  for (int i = 0; i < ngroup; ++i) {
+    const int b = i & 1, v0 = i * G, g = std::min(G, nvec - v0);
     void* xd = c->hbuf[b][0];
     void* yd = c->hbuf[b][1];
-    // x_i may overwrite buffer b once product i - 2 has read it
+    // group i may overwrite buffer b once product i - 2 has read it
     if (i >= 2) BEM_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_comp[b], 0));
-    BEM_CUDA(cudaMemcpyAsync(xd, xh + (size_t)i * bytes, bytes, cudaMemcpyHostToDevice, c->h2d));
+    BEM_CUDA(cudaMemcpyAsync(xd, xh + (size_t)v0 * bytes, (size_t)g * bytes, cudaMemcpyHostToDevice,
+                             c->h2d));
     BEM_CUDA(cudaEventRecord(c->ev_in[b], c->h2d));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_in[b], 0));
-    // y_i may overwrite buffer b once y_{i-2} has gone to the host
+    // y of group i may overwrite buffer b once group i - 2 has gone to the host
     if (i >= 2) BEM_CUDA(cudaStreamWaitEvent(s, c->ev_out[b], 0));
-    BEM_TRY(prec == BEM_C32 ? matvec_graph<float>(c, which, xd, yd, s) : matvec_graph<double>(c, which, xd, yd, s));
+    const int op = G > 1 ? kBatchOp + g : which;
+    BEM_TRY(prec == BEM_C32 ? matvec_graph<float>(c, op, xd, yd, s) : matvec_graph<double>(c, op, xd, yd, s));
     BEM_CUDA(cudaEventRecord(c->ev_comp[b], s));
     BEM_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_comp[b], 0));
-    BEM_CUDA(cudaMemcpyAsync(yh + (size_t)i * bytes, yd, bytes, cudaMemcpyDeviceToHost, c->d2h));
+    BEM_CUDA(cudaMemcpyAsync(yh + (size_t)v0 * bytes, yd, (size_t)g * bytes, cudaMemcpyDeviceToHost,
+                             c->d2h));
     BEM_CUDA(cudaEventRecord(c->ev_out[b], c->d2h));
   }
-  BEM_CUDA(cudaStreamWaitEvent(s, c->ev_out[(nvec - 1) & 1], 0));
+  BEM_CUDA(cudaStreamWaitEvent(s, c->ev_out[(ngroup - 1) & 1], 0));
   return BEM_OK;
 }
 
