@@ -10,7 +10,11 @@
 
 Readings of Alg. 2 (the listing is terse): "P_i < P_cutoff" takes d = 1; otherwise d is the
 distance to the next approximate square above P_i; ties in tau or in F_p go to the lowest
-index; the comparison "C_max != h" is exact on identical floating-point arithmetic.
+index; the comparison "C_max != h" is exact on identical floating-point arithmetic. An
+increment is undone, and the algorithm ends, when the new schedule is longer than the current
+one (the termination rule stated in Sec. III-C); the listing's "not shorter" test would stop
+at the first tie, whereas Sec. IV-B reports two processes per conductor for its buses of
+identical conductors with P = 2 per conductor, which only the strict test gives.
 """
 from __future__ import annotations
 
@@ -87,7 +91,7 @@ def part_schedule(W, P, p_cutoff=None):
             break
         Pi[i] += d
         rows2, F2 = lpt_moldable(W, Pi, P)
-        if F2.max() >= cmax:
+        if F2.max() > cmax:
             Pi[i] -= d
             break
         rows, F, cmax = rows2, F2, F2.max()

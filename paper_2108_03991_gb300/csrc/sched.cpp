@@ -6,7 +6,9 @@
 // number of CTAs that split block i into row panels. Parallel tasks (P_i > 1) start together on
 // dedicated slots; sequential tasks follow by LPT. Readings of Alg. 2: "P_i < P_cutoff" takes
 // d = 1, otherwise d is the distance to the next approximate square (Q^2 or Q(Q+1)) above P_i;
-// ties in tau or finish time go to the lowest index.
+// ties in tau or finish time go to the lowest index; an increment is undone, and the search
+// ends, only when the new schedule is longer (the termination rule of Sec. III-C, which gives
+// the two processes per conductor that Sec. IV-B reports for identical conductors).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -72,7 +74,7 @@ double part_schedule(int ntask, const double* W, int P, int p_cutoff, int32_t* P
     if (cmax != h || a < 0) break;
     Pi[im] += (int32_t)d;
     double c2 = lpt_moldable(ntask, W, Pi, P, nullptr, &F);
-    if (c2 >= cmax) {
+    if (c2 > cmax) {  // a longer schedule ends the algorithm (Sec. III-C); a tie goes on
       Pi[im] -= (int32_t)d;
       break;
     }
@@ -121,10 +123,8 @@ void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>&
 // The persistent GEMV plan. On the GPU a task (one object's block) is moldable at the
 // granularity of a single row, so the ideal schedule of Sec. III-C (total work spread evenly,
 // C_max = C_ideal up to one row) is reachable directly: the rows of all blocks, in order, are
-// cut into ncta contiguous ranges of equal matrix bytes, one per resident CTA. (Part_Schedule
-// as written stops at the first increment that does not shorten the schedule; with several
-// equal-size objects every single-task increment ties, so it would leave most blocks on one or
-// two processors.) ratio reports the longest CTA's bytes over the mean.
+// cut into ncta contiguous ranges of equal matrix bytes, one per resident CTA, with no search
+// over P_i. ratio reports the longest CTA's bytes over the mean.
 void build_gemv_plan(const std::vector<int32_t>& n, const std::vector<int64_t>& off,
                      const std::vector<int32_t>& ld, int ncta, std::vector<RowInfo>* rows,
                      std::vector<int2>* segs, std::vector<int32_t>* cta_seg, double* ratio) {

@@ -41,6 +41,19 @@ def test_part_schedule_matches_oracle(L, cut):
         assert cm == co
 
 
+def test_part_schedule_bus_matches_oracle(L):
+    """The library's Part_Schedule on the identical-conductor buses of Sec. IV-B: two processes
+    per conductor, as the oracle."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "bus_processes_per_conductor.txt")
+    rows = [tuple(int(v) for v in ln.split()) for ln in open(path) if ln.strip() and ln[0] != "#"]
+    assert len(rows) == 7
+    for pairs, P, ne in rows:
+        nc = 2 * pairs
+        W = np.full(nc, float(ne // nc) ** 2)
+        Pi, cm = api.part_schedule(W, P, 20)
+        assert np.all(Pi == 2) and cm == W[0] / 2
+
+
 def test_part_schedule_rejects_unsorted(L):
     with pytest.raises(api.BemError):
         api.part_schedule(np.array([1.0, 2.0]), 4)

@@ -1,4 +1,6 @@
 """Pins of the schedulers (Sec. III-C, Algs. 1 and 2, Eqs. R_LPT and R_part)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -63,3 +65,31 @@ def test_modified_vs_original_on_interposer_shape():
         assert Pm[Pm > 1].sum() <= P
         worst = max(worst, cm / co - 1)
     assert worst < 0.15
+
+
+def bus_rows():
+    """The high-speed bus structures of Sec. IV-B (tests/golden/bus_processes_per_conductor.txt):
+    (conductors, P, N_E) per row."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "bus_processes_per_conductor.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            pairs, P, ne = (int(v) for v in line.split())
+            rows.append((2 * pairs, P, ne))
+    return rows
+
+
+def test_bus_two_processes_per_conductor():
+    """Sec. IV-B: on the buses of identical conductors, the modified Part_Schedule (P_cutoff =
+    20, Sec. III-C-2) with the printed P assigns two processes to every conductor. The table's
+    N_E is the same per conductor in every row (identical conductors: W_i = N_E,i^2 equal)."""
+    rows = bus_rows()
+    assert len(rows) == 7
+    per = {ne // nc for nc, _, ne in rows}
+    assert per == {7026} and all(ne % nc == 0 for nc, _, ne in rows)
+    for nc, P, ne in rows:
+        W = np.full(nc, float(ne // nc) ** 2)
+        Pi, sched_rows, cmax = sched.part_schedule(W, P, p_cutoff=20)
+        assert np.all(Pi == 2), (nc, P)
+        assert cmax == W[0] / 2
+        assert all(len(r) == 1 for r in sched_rows)  # one conductor per process
