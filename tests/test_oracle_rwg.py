@@ -1,4 +1,6 @@
 """Pins of the mesh generator and the RWG / pulse data (Sec. II)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -83,3 +85,16 @@ def test_voxel_surface_and_loop_topology():
     loop = synth.square_loop(10.0, 2.0, 2.0, 1.0)
     rl = from_mesh(loop)
     assert loop.verts.shape[0] - rl.ne + rl.nt == 0
+
+
+def test_sphere_mesh_counts_of_the_paper():
+    """Sec. IV-A meshes its sphere with 1,956 triangles and 2,934 edges
+    (tests/golden/sphere_mesh_counts.txt). Any closed genus-0 triangle mesh of that many
+    triangles must give the same number of RWG functions: here the structured box of 1 x 9 x 48
+    intervals (4 (1*9 + 9*48 + 48*1) = 1,956 triangles), with V - E + F = 2 (980 vertices)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "sphere_mesh_counts.txt")
+    nt, ne = (int(v) for v in next(ln for ln in open(path) if ln.strip() and ln[0] != "#").split())
+    mesh = synth.merge([synth.box((0.0, 0.0, 0.0), (0.5, 4.5, 24.0), (1, 9, 48))], [synth.SIGMA_CU])
+    rw = from_mesh(mesh)
+    assert rw.nt == nt and rw.ne == ne
+    assert mesh.nv - rw.ne + rw.nt == 2 and mesh.nv == 980
