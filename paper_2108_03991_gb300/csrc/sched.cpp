@@ -103,8 +103,15 @@ void build_gemv_tasks(const std::vector<int32_t>& n, const std::vector<int64_t>&
   for (int r = 0; r < nb; ++r) {
     int i = order[r];
     int panels = std::max(1, std::min<int>(Pi[r], n[i]));
+    // panel p spans rows [bnd(p), bnd(p + 1)): the even split snapped to a whole number of
+    // tasks, so only a block's last task can be short (a panel may come out empty)
+    auto bnd = [&](int p) {
+      if (p >= panels) return (int)n[i];
+      const int64_t e = (int64_t)n[i] * p / panels;
+      return (int)std::min<int64_t>(n[i], (e + kRowsPerTask / 2) / kRowsPerTask * kRowsPerTask);
+    };
     for (int p = 0; p < panels; ++p) {
-      int a = (int)((int64_t)n[i] * p / panels), b = (int)((int64_t)n[i] * (p + 1) / panels);
+      const int a = bnd(p), b = bnd(p + 1);
       for (int r0 = a; r0 < b; r0 += kRowsPerTask) {
         GemvTask t;
         t.aoff = off[i];
