@@ -189,9 +189,12 @@ int bem_blockdiag_gemv(int nblk, const int32_t* n, const void* A, const void* x,
  * into the library, which every GPU that loads the library holds until exit. It takes the
  * same arguments and gives the same result. Limit: at most 32768 panels of 16 rows, i.e. the
  * sum over blocks of ceil(n_i / 16) <= 32768 (up to 524,288 rows); larger inputs return
- * BEM_EINVAL with a message. The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture. All calls share
- * the one array: calls whose GPU work overlaps (other streams, other threads) race on it. */
+ * BEM_EINVAL with a message. Every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress) and copies its work list there from a static host array. The
+ * call cannot be captured into a CUDA graph (a replay would re-read that host array after other
+ * calls rewrote it): while `stream` is capturing it returns BEM_EINVAL and does nothing. All
+ * calls share the one array: calls whose GPU work overlaps (other streams, other threads) race
+ * on it. */
 int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const void* x, void* y,
                                int nrhs, int prec, void* stream);
 
@@ -216,6 +219,11 @@ int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void* A, const 
  *           in one paired launch; kind of that launch; ns per matvec), then the
  *           multi-right-hand-side GEMV shapes of the batched matvec (7; 16; rows per warp; 4;
  *           ns per launch of 4 right-hand sides)
+ *   what 9: the dense L_k of object index / 2 (Sec. II-B: the EFIE operator of the object's
+ *           interior, k = k_i, when index is even; of the background, k = k0, when odd), as the
+ *           set-up forms it before the LU solve of Eqs. MFIEinZin / EFIEeqYeq: complex double,
+ *           row-major n_i x n_i. Recomputed on the device for the call (FP64 integrals).
+ *   what 10: K_k + I_x/2 of the same object and wavenumber (same layout)
  * Returns the number of bytes needed when out is NULL. */
 int64_t aim_export(const aim_ctx* ctx, int what, int index, void* out, int64_t cap);
 

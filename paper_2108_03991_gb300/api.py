@@ -484,6 +484,15 @@ class Context:
         n = int(round(np.sqrt(b.size)))
         return b.reshape(n, n)
 
+    def LK(self, i, background=False):
+        """L_k and K_k + I_x/2 of object i as the set-up forms them before its LU solve
+        (k = k_i, or k0 with background=True)."""
+        idx = 2 * i + (1 if background else 0)
+        Lb = self._export(9, idx).view(np.complex128)
+        Kb = self._export(10, idx).view(np.complex128)
+        n = int(round(np.sqrt(Lb.size)))
+        return Lb.reshape(n, n), Kb.reshape(n, n)
+
     def near(self, which):
         b = self._export(2 if which == "A" else 3)
         nr = (self.ne if which == "A" else self.nt) + 1

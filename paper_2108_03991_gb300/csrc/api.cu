@@ -414,6 +414,22 @@ int64_t aim_export(const aim_ctx* c, int what, int index, void* out, int64_t cap
     memcpy(out, c->tune_table.data(), need);
     return need;
   }
+  if (what == 9 || what == 10) {
+    const int obj = index >> 1, pass = index & 1;
+    if (index < 0 || obj >= c->nobj) {
+      set_error("aim_export: object index out of range");
+      return BEM_EINVAL;
+    }
+    const int n = c->e1[obj] - c->e0[obj];
+    int64_t need = (int64_t)n * n * 16;
+    if (!out) return need;
+    if (cap < need) { set_error("aim_export: buffer too small"); return BEM_EINVAL; }
+    std::vector<double2> other((size_t)n * n);
+    double2* o = (double2*)out;
+    BEM_TRY(what == 9 ? export_LK(const_cast<aim_ctx*>(c), obj, pass, o, other.data())
+                      : export_LK(const_cast<aim_ctx*>(c), obj, pass, other.data(), o));
+    return need;
+  }
   set_error("aim_export: unknown item %d", what);
   return BEM_EINVAL;
 }

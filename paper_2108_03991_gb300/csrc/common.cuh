@@ -401,6 +401,9 @@ int precond_apply_mixed(aim_ctx* c, const double2* r, float2* u32, double2* u64,
 int precond_apply_batch(aim_ctx* c, const double2* r, int nrhs, float2* u32, double2* u64,
                         cudaStream_t s);
 void free_geo_store(aim_ctx* c);
+// the dense L_k and K_k + I_x/2 of one object as the set-up forms them before its LU solve
+// (pass 0: k = k_i, pass 1: k = k0), row-major n_i x n_i complex doubles on the host
+int export_LK(aim_ctx* c, int obj, int pass, double2* L_out, double2* K_out);
 void free_far_geo(aim_ctx* c);
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);
 int tune_matvec_schedule(aim_ctx* c);

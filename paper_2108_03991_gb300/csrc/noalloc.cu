@@ -10,11 +10,17 @@
 //
 // The scratch: kNoAllocMaxTasks tasks (32 bytes each, 1 MiB) in a file-scope __device__ array.
 // Every GPU that loads the library holds it until the process exits. In host code the array's
-// name is only a host-side stand-in, so the host looks up its device address once per device
-// with cudaGetSymbolAddress (done by the first call on each device, with that device current)
-// and passes that address to the kernel. Every call overwrites the entries it uses; nothing has
-// to start at zero. All calls share the one array: calls whose GPU work overlaps (different
-// streams, or different host threads) race on it and must be ordered by the caller.
+// name is only a host-side stand-in, so every call looks up its device address on the current
+// device with cudaGetSymbolAddress (cheap next to the copy; nothing is cached, so a device reset
+// that reloads the module leaves no stale address) and passes that address to the kernel. Every
+// call overwrites the entries it uses; nothing has to start at zero. All calls share the one
+// array: calls whose GPU work overlaps (different streams, or different host threads) race on it
+// and must be ordered by the caller.
+//
+// The work list reaches the array by a copy from a static host array. A CUDA graph captured
+// around the call would record that copy and read the host array again at every replay, after
+// later calls may have rewritten it, and then run another call's list against this call's
+// matrices. So the call refuses to run while its stream is being captured.
 #include <mutex>
 
 #include "common.cuh"
@@ -23,28 +29,17 @@ namespace bem {
 
 constexpr int kNoAllocMaxTasks = 32768;
 constexpr int kNoAllocRows = 16;  // rows per task
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) GemvTask g_noalloc_tasks[kNoAllocMaxTasks];
 
 static std::mutex g_noalloc_mu;
 static GemvTask g_noalloc_host[kNoAllocMaxTasks];  // host staging (static storage, no heap)
-static GemvTask* g_noalloc_dev[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device (looked up on every call).
 static int noalloc_scratch(GemvTask** out) {
-  int dev = 0;
-  BEM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("bem_blockdiag_gemv_noalloc: device index %d out of range", dev);
-    return BEM_EINVAL;
-  }
-  if (!g_noalloc_dev[dev]) {
-    void* p = nullptr;
-    BEM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_tasks));
-    g_noalloc_dev[dev] = static_cast<GemvTask*>(p);
-  }
-  *out = g_noalloc_dev[dev];
+  void* p = nullptr;
+  BEM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_tasks));
+  *out = static_cast<GemvTask*>(p);
   return BEM_OK;
 }
 
@@ -77,6 +72,15 @@ extern "C" int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void
               kNoAllocMaxTasks * kNoAllocRows);
     return BEM_EINVAL;
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+  if (ce != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    if (ce != cudaSuccess) cudaGetLastError();
+    set_error("bem_blockdiag_gemv_noalloc: the stream is being captured into a CUDA graph; this "
+              "call cannot be captured (its work list is copied from a shared host array)");
+    return BEM_EINVAL;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   GemvTask* d_tasks = nullptr;
   BEM_TRY(noalloc_scratch(&d_tasks));
@@ -98,7 +102,6 @@ extern "C" int bem_blockdiag_gemv_noalloc(int nblk, const int32_t* n, const void
     off += (int64_t)n[i] * ld;
     xoff += n[i];
   }
-  cudaStream_t s = (cudaStream_t)stream;
   // From pageable host memory the copy returns once the source has been staged, so the host
   // buffer may be reused as soon as the lock is released.
   BEM_CUDA(cudaMemcpyAsync(d_tasks, g_noalloc_host, (size_t)k * sizeof(GemvTask),

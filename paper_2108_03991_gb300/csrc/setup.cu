@@ -1587,6 +1587,48 @@ int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int
   return BEM_OK;
 }
 
+int export_LK(aim_ctx* c, int obj, int pass, double2* L_out, double2* K_out) {
+  const DGeo& g = *reinterpret_cast<const DGeo*>(c->geo_store);
+  const int n = c->e1[obj] - c->e0[obj];
+  const bem_material& mt = c->mat[obj];
+  const double w = 2.0 * kPi * c->freq;
+  std::complex<double> k(c->k0, 0.0);
+  if (pass == 0) {
+    std::complex<double> epsc(mt.eps_r, -mt.sigma / (w * kEps0));
+    k = c->k0 * std::sqrt(epsc * mt.mu_r);
+    if (k.imag() > 0) k = -k;
+  }
+  const size_t nn = (size_t)n * n;
+  double2 *L = nullptr, *B = nullptr;
+  BEM_CUDA(cudaMalloc(&L, nn * sizeof(double2)));
+  cudaError_t e = cudaMalloc(&B, nn * sizeof(double2));
+  if (e == cudaSuccess) {
+    k_obj_LK<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[obj], n, k.real(), k.imag(), c->d_ixcol,
+                                                 c->f64.ix, L, B);
+    e = cudaGetLastError();
+  }
+  std::vector<double2> tl, tb;
+  if (e == cudaSuccess) {
+    tl.resize(nn);
+    tb.resize(nn);
+    e = cudaMemcpy(tl.data(), L, nn * sizeof(double2), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(tb.data(), B, nn * sizeof(double2), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(L);
+  if (B) cudaFree(B);
+  if (e != cudaSuccess) {
+    set_error("export_LK: %s", cudaGetErrorString(e));
+    return BEM_ECUDA;
+  }
+  // the set-up kernel writes column-major; the export is row-major
+  for (int r = 0; r < n; ++r)
+    for (int col = 0; col < n; ++col) {
+      L_out[(size_t)r * n + col] = tl[r + (size_t)col * n];
+      K_out[(size_t)r * n + col] = tb[r + (size_t)col * n];
+    }
+  return BEM_OK;
+}
+
 void free_geo_store(aim_ctx* c) {
   delete reinterpret_cast<DGeo*>(c->geo_store);
   c->geo_store = nullptr;

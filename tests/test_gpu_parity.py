@@ -12,10 +12,7 @@ pytestmark = pytest.mark.gpu
 from oracle import aim as oaim, blockops, gmres as ogmres, operators as op  # noqa: E402
 from oracle.rwg import from_mesh  # noqa: E402
 from paper_2108_03991_gb300 import api, synth  # noqa: E402
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+from syscheck import check_system, max_rel, rel  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -126,14 +123,82 @@ def test_matvec_LA_LPhi(prob, prec, tol):
     assert rel(yp, A.LPhi(q)) < tol
 
 
+def _system_input(ctx, case, seed):
+    """x = [h; q] with both parts random, with q = 0 (row 1 is then j k0 L^A j + I_x e, two terms
+    of the same order, and row 2 is F D j), or with h = 0 (row 1 is -(F D)^T L^Phi q, row 2 j k0 q)."""
+    x = synth.rand_cvec(ctx.n, seed)
+    if case == "q0":
+        x[ctx.ne:] = 0
+    elif case == "h0":
+        x[:ctx.ne] = 0
+    return x
+
+
+@pytest.mark.parametrize("case", ["both", "q0", "h0"])
 @pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-7)])
-def test_system_matvec(prob, prec, tol):
-    """The full SLIM matvec (Eq. AEFIEoutJ). The FP64 bound reflects the Y_eq set-up
-    discrepancy (ill-conditioned L_l), not the matvec arithmetic."""
+def test_system_matvec(prob, prec, tol, case):
+    """The full SLIM matvec (Eq. AEFIEoutJ), each block row against its own norm and element by
+    element. The FP64 bound reflects the Y_eq set-up discrepancy (ill-conditioned L_l), not the
+    matvec arithmetic."""
     ctx, S = prob["ctx"], prob["S"]
-    x = synth.rand_cvec(ctx.n, 5)
+    x = _system_input(ctx, case, 5)
     y = ctx.matvec(torch.from_numpy(x).to(api.cdtype(prec)).cuda(), prec=prec).cpu().numpy()
-    assert rel(y, S.matvec(x)) < tol
+    check_system(y, S.matvec(x), ctx.ne, tol)
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-4), (api.BEM_C64, 1e-6)])
+def test_system_matvec_inductive_term(prob, prec, tol):
+    """The j k0 L^A j term of row 1 on its own: with q = 0, y1 - I_x e (e from the oracle) must be
+    the oracle's j k0 L^A j. In the system matvec the near region of L^A j is a separate kernel on
+    a side stream whose result joins the interpolation (a path the L^A-only operator does not
+    take), so this isolates it. Bound: the relative set-up discrepancy of Y_eq (1e-6, see
+    test_internal_blocks) times |Y e| / |j|, about 0.5 here, in FP64; FP32 rounding of the
+    products relative to this term's size in FP32."""
+    ctx, S, A, k0 = prob["ctx"], prob["S"], prob["aim"], prob["k0"]
+    x = _system_input(ctx, "q0", 15)
+    ne = ctx.ne
+    y = ctx.matvec(torch.from_numpy(x).to(api.cdtype(prec)).cuda(), prec=prec).cpu().numpy()
+    h, q, e, heq, j = S.parts(x)
+    term = 1j * k0 * A.LA(j)
+    got = y[:ne] - S.ix @ e
+    assert rel(got, term) < tol
+    assert max_rel(got, term) < 3 * tol
+    # the near part alone is about half of L^A j here: dropping it would be an O(1) error
+    assert np.linalg.norm(A.LNR_A @ j) > 0.2 * np.linalg.norm(A.LA(j))
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-7)])
+def test_system_matvec_buffer_reuse(prob, prec, tol):
+    """The matvec graph captured for a buffer pair, replayed with new contents written into the
+    same input buffer: each product is the oracle's for its own input (nothing stale from the
+    previous replay, such as the side stream's near-region result)."""
+    ctx, S = prob["ctx"], prob["S"]
+    dt = api.cdtype(prec)
+    xd = torch.empty(ctx.n, dtype=dt, device="cuda")
+    yd = torch.empty(ctx.n, dtype=dt, device="cuda")
+    for seed, case in ((31, "both"), (32, "q0"), (33, "h0"), (34, "q0")):
+        x = _system_input(ctx, case, seed)
+        xd.copy_(torch.from_numpy(x).to(dt))
+        ctx.matvec(xd, yd, prec=prec)
+        check_system(yd.cpu().numpy(), S.matvec(x), ctx.ne, tol)
+
+
+def test_setup_internal_matrices(prob):
+    """The dense L_k and K_k + I_x/2 of every object, for k = k_i and k = k0, as the set-up forms
+    them before the LU solves of Eqs. MFIEinZin and EFIEeqYeq, against the oracle's Galerkin
+    matrices: the same integration rules on both sides, so they agree to FP64 rounding (1e-12),
+    which the LU then amplifies by cond(L) (the Z and Y bounds above)."""
+    ctx, rw, freq, mesh = prob["ctx"], prob["rw"], prob["freq"], prob["mesh"]
+    ix = op.ix_matrix(rw)
+    k0 = op.k0_of(freq)
+    for i, (a, b) in enumerate(rw.obj_edge_ranges()):
+        ki = op.k_medium(k0, op.eps_rc(mesh.sigma[i], freq))
+        for bg, k in ((False, ki), (True, k0)):
+            Lg, Kg = ctx.LK(i, background=bg)
+            Lo = op.dense_rwg(rw, k, "L", a, b)
+            Ko = op.dense_rwg(rw, k, "K", a, b) + 0.5 * ix[a:b, a:b].toarray()
+            assert max_rel(Lg, Lo) < 1e-12
+            assert max_rel(Kg, Ko) < 1e-12
 
 
 def test_system_matvec_c32_vs_gpu_c64(prob):
@@ -142,7 +207,7 @@ def test_system_matvec_c32_vs_gpu_c64(prob):
     x = synth.rand_cvec(ctx.n, 6)
     y32 = ctx.matvec(torch.from_numpy(x).to(torch.complex64).cuda(), prec=api.BEM_C32).cpu().numpy()
     y64 = ctx.matvec(torch.from_numpy(x).cuda(), prec=api.BEM_C64).cpu().numpy()
-    assert rel(y32, y64) < 1e-5
+    check_system(y32, y64, ctx.ne, 1e-5)
 
 
 def test_internal_apply_nrhs(prob):
@@ -191,9 +256,10 @@ def test_gemv_kinds_match_oracle(prob, kind):
             assert rel(e[r], eo) < 1e-5
             ho = blockops.block_gemv(S.Ys, [a for a, _ in S.ranges], e[r].astype(np.complex128))
             assert rel(heq[r], ho) < 1e-5
-        x = synth.rand_cvec(ctx.n, 7)
-        y = ctx.matvec(torch.from_numpy(x.astype(np.complex64)).cuda(), prec=api.BEM_C32)
-        assert rel(y.cpu().numpy(), S.matvec(x)) < 1e-5
+        for case, seed in (("both", 7), ("q0", 8)):
+            x = _system_input(ctx, case, seed)
+            y = ctx.matvec(torch.from_numpy(x.astype(np.complex64)).cuda(), prec=api.BEM_C32)
+            check_system(y.cpu().numpy(), S.matvec(x), ctx.ne, 1e-5)
     finally:
         ctx.gemv_select(0)
 
@@ -206,10 +272,11 @@ def test_matvec_schedules_match_oracle(prob, mode):
     ctx, S = prob["ctx"], prob["S"]
     try:
         ctx.matvec_schedule(mode)
-        x = synth.rand_cvec(ctx.n, 71)
-        for prec, dt, tol in [(api.BEM_C32, np.complex64, 1e-5), (api.BEM_C64, np.complex128, 1e-7)]:
-            y = ctx.matvec(torch.from_numpy(x.astype(dt)).cuda(), prec=prec)
-            assert rel(y.cpu().numpy(), S.matvec(x)) < tol
+        for case, seed in (("both", 71), ("q0", 72)):
+            x = _system_input(ctx, case, seed)
+            for prec, dt, tol in [(api.BEM_C32, np.complex64, 1e-5), (api.BEM_C64, np.complex128, 1e-7)]:
+                y = ctx.matvec(torch.from_numpy(x.astype(dt)).cuda(), prec=prec)
+                check_system(y.cpu().numpy(), S.matvec(x), ctx.ne, tol)
     finally:
         ctx.matvec_schedule(-1)
 
@@ -220,12 +287,13 @@ def test_matvec_batch_matches_oracle(prob, prec, tol):
     right-hand side, and against the one-vector device matvec; nrhs outside 1..4 is refused."""
     ctx, S = prob["ctx"], prob["S"]
     npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    cases = ("both", "q0", "h0", "q0")
     for nrhs in (1, 2, 3, 4):
-        xs = np.stack([synth.rand_cvec(ctx.n, 200 + 10 * nrhs + r) for r in range(nrhs)])
+        xs = np.stack([_system_input(ctx, cases[r], 200 + 10 * nrhs + r) for r in range(nrhs)])
         xd = torch.from_numpy(xs.astype(npdt).ravel()).cuda()
         y = ctx.matvec_batch(xd, prec=prec).cpu().numpy().reshape(nrhs, ctx.n)
         for r in range(nrhs):
-            assert rel(y[r], S.matvec(xs[r])) < tol
+            check_system(y[r], S.matvec(xs[r]), ctx.ne, tol)
             y1 = ctx.matvec(torch.from_numpy(xs[r].astype(npdt)).cuda(), prec=prec).cpu().numpy()
             assert rel(y[r], y1) < 1e-6
     with pytest.raises(api.BemError):
@@ -395,10 +463,11 @@ def test_single_object_matvec_and_zero_rhs(dev):
     Zs, Ys = op.internal_blocks(rw, freq, mesh.sigma)
     S = op.SlimSystem(rw, freq, Zs, Ys, A.LA, A.LPhi)
     assert ctx.nobj == 1
-    x = synth.rand_cvec(ctx.n, 80)
-    for prec, dt, tol in [(api.BEM_C32, np.complex64, 1e-5), (api.BEM_C64, np.complex128, 1e-7)]:
-        y = ctx.matvec(torch.from_numpy(x.astype(dt)).cuda(), prec=prec)
-        assert rel(y.cpu().numpy(), S.matvec(x)) < tol
+    for case, seed in (("both", 80), ("q0", 81)):
+        x = _system_input(ctx, case, seed)
+        for prec, dt, tol in [(api.BEM_C32, np.complex64, 1e-5), (api.BEM_C64, np.complex128, 1e-7)]:
+            y = ctx.matvec(torch.from_numpy(x.astype(dt)).cuda(), prec=prec)
+            check_system(y.cpu().numpy(), S.matvec(x), ctx.ne, tol)
     zero = torch.zeros(ctx.n, dtype=torch.complex128, device=dev)
     x0, info = ctx.solve(zero, tol=1e-6, restart=20, max_iter=50, prec_mode=api.BEM_C32, precond=1)
     assert info["status"] == api.BEM_OK and info["iters"] == 0
