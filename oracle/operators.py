@@ -26,6 +26,7 @@ import math
 import numpy as np
 import scipy.sparse as sp
 
+from . import highk
 from .quad import NEAR_FACTOR, radon7, subdivide4, rule_points, static_potentials
 from .rwg import RWG
 
@@ -90,8 +91,23 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
     dc = rw.centroid[T] - rw.centroid[S]
     dmax = np.maximum(rw.diam[T], rw.diam[S])
     near = np.einsum("ij,ij->i", dc, dc) < (NEAR_FACTOR * dmax) ** 2
+    # near pairs at large |k| (Sec. II-B, high conductivity): the edge-integral scheme of
+    # oracle/highk.py, or the regular rule beyond the decay range
+    hk = near & (abs(k) * dmax > highk.HIGHK)
+    if np.any(hk):
+        rad = np.max(np.linalg.norm(X - rw.centroid[:, None, :], axis=2), axis=1)
+        if complex(k).imag != 0.0:
+            sep = np.linalg.norm(dc, axis=1) - rad[T] - rad[S] > highk.DECAY / abs(complex(k).imag)
+            near &= ~(hk & sep)
+            hk &= ~sep
+        ih = np.nonzero(hk)[0]
+        if ih.size:
+            m = highk.pair_moments_batch(X[T[ih]], X[S[ih]], rw.normal[S[ih]], rw.diam[S[ih]], k,
+                                         want_K)
+            for key, v in m.items():
+                out[key][ih] = v
     for sel_near in (False, True):
-        idx_all = np.nonzero(near == sel_near)[0]
+        idx_all = np.nonzero((near == sel_near) & ~hk)[0]
         bi, wi = (bn, wn) if sel_near else (bo, wo)
         bp_, wp_ = bo, wo
         nqo = wp_.size

@@ -99,6 +99,13 @@ static int upload_rules() {
   BEM_CUDA(cudaMemcpyToSymbol(c_r7, r7, sizeof(r7)));
   BEM_CUDA(cudaMemcpyToSymbol(c_r28, r28, sizeof(r28)));
   BEM_CUDA(cudaMemcpyToSymbol(c_gl, gl, sizeof(gl)));
+  double x8[8], w8[8], g8[16];
+  gauss_legendre(8, x8, w8);
+  for (int i = 0; i < 8; ++i) {
+    g8[i] = 0.5 * (x8[i] + 1.0);
+    g8[8 + i] = 0.5 * w8[i];
+  }
+  BEM_CUDA(cudaMemcpyToSymbol(c_gl8, g8, sizeof(g8)));
   return BEM_OK;
 }
 
@@ -258,17 +265,90 @@ __device__ void rwg_pair(const DGeo& g, int m, int n, double kr, double ki, bool
   if (Kval) *Kval = K;
 }
 
-// Dense internal matrices of one object (column-major, n x n): Lc = L_k, Bc = K_k + I_x/2.
-__global__ void k_obj_LK(DGeo g, int e0, int n, double kr, double ki, const int32_t* ixcol,
-                         const double* ixval, double2* Lc, double2* Bc) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// Dense internal matrices of one object, in three passes over its triangle pairs (m triangles
+// from t0, local pair index it * m + is): the moments of every regular and small-|k| near pair
+// (one thread each), the large-|k| near pairs listed for the second pass; those by one warp each
+// (the edge-integral scheme of quad.cuh); then every RWG entry from the four pair moments of its
+// two triangles.
+__global__ void k_obj_moments(DGeo g, int t0, int m, double kr, double ki, bool wantK,
+                              Moments* mom, int* hk_list, int* hk_count) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * m) return;
+  const int it = (int)(idx / m), is = (int)(idx % m);
+  Tri T, S;
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + it, &T);
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + is, &S);
+  const int kind = pair_kind(T, S, kr, ki);
+  if (kind == 2) {
+    const int p = atomicAdd(hk_count, 1);
+    hk_list[p] = (int)idx;  // at most m * m entries: the list holds them all
+    return;
+  }
+  Moments M;
+  pair_moments(T, S, kr, ki, true, wantK, false, &M, kind);
+  mom[idx] = M;
+}
+
+__global__ void k_obj_moments_hk(DGeo g, int t0, int m, double kr, double ki, bool wantK,
+                                 Moments* mom, const int* hk_list, int count) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (w >= count) return;  // warp-uniform
+  const int idx = hk_list[w];
+  const int it = idx / m, is = idx % m;
+  Tri T, S;
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + it, &T);
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + is, &S);
+  Moments M;
+  hk_pair_moments_warp(T, S, kr, ki, wantK, &M);
+  if ((threadIdx.x & 31) == 0) mom[idx] = M;
+}
+
+// Lc = L_k, Bc = K_k + I_x/2 (column-major n x n) from the pair moments
+__global__ void k_obj_assemble(DGeo g, int e0, int n, int t0, int m, double kr, double ki,
+                               const Moments* __restrict__ mom, const int32_t* ixcol,
+                               const double* ixval, double2* Lc, double2* Bc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
-  int i = (int)(idx % n), j = (int)(idx / n);  // column-major: consecutive threads walk a column
-  int m = e0 + i, nn = e0 + j;
-  double2 L, K;
-  rwg_pair(g, m, nn, kr, ki, true, true, &L, &K);
+  const int i = (int)(idx % n), j = (int)(idx / n);  // column-major: consecutive threads walk a column
+  const int mm = e0 + i, nn = e0 + j;
+  const double den = kr * kr + ki * ki;
+  const double2 ik2 = make_double2((kr * kr - ki * ki) / (den * den), -2.0 * kr * ki / (den * den));
+  double2 L = {0, 0}, K = {0, 0};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int t = g.et[2 * mm + a], sidx = g.et[2 * nn + b];
+      const Moments& M = mom[(int64_t)(t - t0) * m + (sidx - t0)];
+      double sm, sn;
+      const double *va, *vb;
+      half_rwg(g, mm, t, &sm, &va);
+      half_rwg(g, nn, sidx, &sn, &vb);
+      const double cf = sm * sn * g.elen[mm] * g.elen[nn] / (4.0 * g.area[t] * g.area[sidx]);
+      double2 v = M.M2;
+      for (int q = 0; q < 3; ++q) {
+        v.x += -M.M1[q].x * vb[q] - va[q] * M.M1p[q].x;
+        v.y += -M.M1[q].y * vb[q] - va[q] * M.M1p[q].y;
+      }
+      const double vv = d_dot(va, vb);
+      v.x += vv * M.M0.x;
+      v.y += vv * M.M0.y;
+      L.x += cf * v.x;
+      L.y += cf * v.y;
+      const double dv = sm * sn * g.elen[mm] * g.elen[nn] / (g.area[t] * g.area[sidx]);
+      const double2 t2 = cmul(M.M0, ik2);
+      L.x -= dv * t2.x;
+      L.y -= dv * t2.y;
+      double bxa[3];
+      d_cross(vb, va, bxa);
+      double2 kv = {0, 0};
+      for (int q = 0; q < 3; ++q) {
+        kv.x += M.U[q].x * (vb[q] - va[q]) + M.Vs[q].x * bxa[q];
+        kv.y += M.U[q].y * (vb[q] - va[q]) + M.Vs[q].y * bxa[q];
+      }
+      K.x += cf * kv.x;
+      K.y += cf * kv.y;
+    }
   for (int q = 0; q < 4; ++q)
-    if (ixcol[4 * m + q] == nn) K.x += 0.5 * ixval[4 * m + q];
+    if (ixcol[4 * mm + q] == nn) K.x += 0.5 * ixval[4 * mm + q];
   Lc[idx] = L;
   Bc[idx] = K;
 }
@@ -945,6 +1025,55 @@ static int lu_solve(SolverScratch& ss, double2* L, double2* B, int n, int64_t* i
   return BEM_OK;
 }
 
+// scratch of the pair-moment passes, sized for the object with the most triangles
+struct MomentScratch {
+  Moments* mom = nullptr;
+  int* list = nullptr;
+  int* count = nullptr;
+  int64_t cap = 0;
+  ~MomentScratch() {
+    if (mom) cudaFree(mom);
+    if (list) cudaFree(list);
+    if (count) cudaFree(count);
+  }
+  int reserve(int64_t pairs) {
+    if (pairs <= cap) return BEM_OK;
+    if (mom) cudaFree(mom);
+    if (list) cudaFree(list);
+    mom = nullptr;
+    list = nullptr;
+    BEM_CUDA(cudaMalloc(&mom, pairs * sizeof(Moments)));
+    BEM_CUDA(cudaMalloc(&list, pairs * sizeof(int)));
+    if (!count) BEM_CUDA(cudaMalloc(&count, sizeof(int)));
+    cap = pairs;
+    return BEM_OK;
+  }
+};
+
+// L_k (into L) and K_k + I_x/2 (into B), column-major n x n, for object obj and wavenumber k
+static int object_LK(aim_ctx* c, const DGeo& g, int obj, std::complex<double> k, MomentScratch* ms,
+                     double2* L, double2* B) {
+  const int n = c->e1[obj] - c->e0[obj];
+  const int t0 = c->t0[obj], m = c->t1[obj] - c->t0[obj];
+  const int64_t pairs = (int64_t)m * m;
+  BEM_TRY(ms->reserve(pairs));
+  BEM_CUDA(cudaMemset(ms->count, 0, sizeof(int)));
+  k_obj_moments<<<nblk(pairs, 128), 128>>>(g, t0, m, k.real(), k.imag(), true, ms->mom, ms->list,
+                                           ms->count);
+  BEM_CUDA(cudaGetLastError());
+  int nhk = 0;
+  BEM_CUDA(cudaMemcpy(&nhk, ms->count, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nhk > 0) {
+    k_obj_moments_hk<<<nblk((int64_t)nhk * 32, 128), 128>>>(g, t0, m, k.real(), k.imag(), true,
+                                                             ms->mom, ms->list, nhk);
+    BEM_CUDA(cudaGetLastError());
+  }
+  k_obj_assemble<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[obj], n, t0, m, k.real(), k.imag(),
+                                                     ms->mom, c->d_ixcol, c->f64.ix, L, B);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
 static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, const double* d_ixval) {
   const int nobj = c->nobj;
   c->zoff.assign(nobj, 0);
@@ -974,6 +1103,7 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
   BEM_CUDA(cudaMalloc(&ipiv, nmax * sizeof(int64_t)));
   BEM_CUDA(cudaMalloc(&dinfo, sizeof(int)));
   SolverScratch ss;
+  MomentScratch ms;
   void* dwork = nullptr;
   size_t dwsize = 0;
   std::vector<char> hwork;
@@ -994,10 +1124,8 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
       // pass 0: Z = -(1/(j k0 eps_rc)) L_{k_i}^{-1}(K_{k_i} + I_x/2)
       // pass 1: Y = (1/(j k0 mu_rl)) L_{k0}^{-1}(K_{k0} + I_x/2), background vacuum
       std::complex<double> k = pass == 0 ? ki : std::complex<double>(c->k0, 0.0);
-      k_obj_LK<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[i], n, k.real(), k.imag(), d_ixcol,
-                                                   d_ixval, L, B);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) { set_error("k_obj_LK: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; break; }
+      rc = object_LK(c, g, i, k, &ms, L, B);
+      if (rc != BEM_OK) break;
       rc = lu_solve(ss, L, B, n, ipiv, dinfo, &dwork, &dwsize, &hwork);
       if (rc != BEM_OK) break;
       std::complex<double> jk0(0.0, c->k0);
@@ -1006,7 +1134,7 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
       k_store_block<<<nblk((int64_t)n * c->zld[i], 256), 256>>>(
           B, n, c->zld[i], al, (pass == 0 ? c->f64.Z : c->f64.Y) + c->zoff[i],
           pass == 0 ? c->f32.Z + c->zoff[i] : nullptr);
-      e = cudaGetLastError();
+      cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) { set_error("k_store_block: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; }
     }
   }
@@ -1103,6 +1231,17 @@ static int setup_near(aim_ctx* c, const DGeo& g) {
 }
 
 int setup_device(aim_ctx* c) {
+  {
+    // the background-medium integrals (near region, preconditioner blocks, Y_eq) use the
+    // small-|k| near rule, valid while k0 times the element size stays at or below kHighK
+    double dmx = 0.0;
+    for (double v : c->diam) dmx = std::max(dmx, v);
+    if (c->k0 * dmx > kHighK) {
+      set_error("aim_setup: k0 times the largest element (%.3g) exceeds %.2g; refine the mesh",
+                c->k0 * dmx, kHighK);
+      return BEM_EINVAL;
+    }
+  }
   BEM_TRY(upload_rules());
   DevGeoStore s;
   BEM_TRY(geo_upload(c, &s));
@@ -1603,9 +1742,9 @@ int export_LK(aim_ctx* c, int obj, int pass, double2* L_out, double2* K_out) {
   BEM_CUDA(cudaMalloc(&L, nn * sizeof(double2)));
   cudaError_t e = cudaMalloc(&B, nn * sizeof(double2));
   if (e == cudaSuccess) {
-    k_obj_LK<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[obj], n, k.real(), k.imag(), c->d_ixcol,
-                                                 c->f64.ix, L, B);
-    e = cudaGetLastError();
+    MomentScratch ms;
+    if (object_LK(c, g, obj, k, &ms, L, B) != BEM_OK) e = cudaErrorUnknown;
+    else e = cudaDeviceSynchronize();
   }
   std::vector<double2> tl, tb;
   if (e == cudaSuccess) {

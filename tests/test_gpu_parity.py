@@ -100,6 +100,36 @@ def test_internal_blocks(prob):
         assert rel(ctx.Y(i), S.Ys[i]) < 1e-6
 
 
+@pytest.fixture(scope="module")
+def gold_box(dev):
+    """A gold box 1 x 1 x 1.5 um with 0.5 um elements at 1 THz: |k_i| times the element
+    diameter is 12.7, so every near pair of the internal operator takes the large-|k| rule
+    (edge integrals, the testing triangle subdivided three levels toward the source)."""
+    mesh = synth.bar_mesh(1.0, 1.0, 1.5, 0.5, sigma=synth.SIGMA_AU)
+    grid = synth.grid_box(mesh, 0.5)
+    freq = 1e12
+    ctx = api.Context(mesh, grid, freq)
+    rw = from_mesh(mesh)
+    return dict(ctx=ctx, rw=rw, mesh=mesh, freq=freq)
+
+
+def test_setup_internal_matrices_high_k(gold_box):
+    """L_{k_i} and K_{k_i} + I_x/2 of the gold box at 1 THz against the oracle's (the same
+    large-|k| rule written independently on both sides): 1e-12 of the largest entry."""
+    ctx, rw, mesh, freq = gold_box["ctx"], gold_box["rw"], gold_box["mesh"], gold_box["freq"]
+    k0 = op.k0_of(freq)
+    ki = op.k_medium(k0, op.eps_rc(mesh.sigma[0], freq))
+    assert abs(ki) * rw.diam.max() > 10
+    ix = op.ix_matrix(rw).toarray()
+    Lg, Kg = ctx.LK(0)
+    Lo = op.dense_rwg(rw, ki, "L")
+    Ko = op.dense_rwg(rw, ki, "K") + 0.5 * ix
+    assert max_rel(Lg, Lo) < 1e-12
+    assert max_rel(Kg, Ko) < 1e-12
+    Zo = -np.linalg.solve(Lo, Ko) / (1j * k0 * op.eps_rc(mesh.sigma[0], freq))
+    assert max_rel(ctx.Z(0), Zo) < 1e-10
+
+
 @pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 2e-6), (api.BEM_C64, 1e-12)])
 def test_grid_convolution(prob, prec, tol):
     ctx, A = prob["ctx"], prob["aim"]
