@@ -103,7 +103,10 @@ const char* bem_last_error(void);
  * bulk-copy staged, 3 stream, 5 the modified Part_Schedule's task list, 6 the same tasks taken
  * in turn by persistent CTAs), [20]=CTAs per SM of that launch's shape (for the task list:
  * 4, 8 or 16, the variant), [21]=schedule of the internal products in the system matvec
- * (aim_matvec_schedule modes 0-3). Writes min(n, 22) entries. */
+ * (aim_matvec_schedule modes 0-3), [22..31]=wall time in microseconds of the set-up stages:
+ * host geometry, projection stencils, internal integrals at k_i (all objects), internal
+ * integrals at k0, LU solves, C = Y Z, near region, FFT of the grid kernel, GEMV autotuner,
+ * matvec schedule tuner. Writes min(n, 32) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the

@@ -21,23 +21,27 @@ the plane angle that S subtends at rho (2 pi inside, 0 outside). On S's own plan
 term is the principal value (dropped, as in the small-|k| rule). An edge whose line passes
 through rho (|P| <= 1e-12 diam) has J1 = J4 = 0 and no angle: the limits from both sides agree.
 
-The edge integrals use a graded Gauss-Legendre rule (8 points per interval) in |t|, the
+The edge integrals use a graded Gauss-Legendre rule (6 points per interval) in |t|, the
 integrands being even in t: breakpoints at h0 2^j up to the first one above 2 dmax, then steps
 of dmax, with h0 = min(|P| (w if P = 0), 1/|k|)/2, dmax = 2/|k| and w = sqrt(P^2 + a^2); the
-rule stops where |Im k| (R - w) exceeds 36 (exp(-36) ~ 2e-16 of the peak) and skips an edge
-whose |Im k| (w - a) exceeds 36.
+rule stops where |Im k| (R - w) exceeds 18 (exp(-18) ~ 2e-8 of the peak) and skips an edge
+whose |Im k| (w - a) exceeds 18. The edge integrals are then accurate to a few 1e-9, far below
+the outer rule's own error (about 1e-3 at |k| diam = 36, see the refinement study).
 
 Outer (testing) integrals: T is split into four midpoint sub-triangles, recursively, wherever
-a sub-triangle lies within its own size of where the inner integrals vary fast, down to
-depth D = min(6, ceil(log2(|k| diam_T))) (so that |k| diam <= 1 there); every leaf takes
-Radon's 7-point rule. "Where they vary fast" is the boundary of S when T lies in S's plane,
-and S itself otherwise. The split test: distance from the sub-triangle's centroid to that set
-below its circumradius (about the centroid) plus its diameter.
+a sub-triangle lies close to where the inner integrals vary fast, down to depth
+D = min(3, ceil(log2(|k| diam_T))); every leaf takes Radon's 7-point rule. "Where they vary
+fast" is the boundary of S when T lies in S's plane, and S itself otherwise. The split test,
+with c the sub-triangle's centroid, rad its circumradius about c and dm its diameter: the
+distance from c to that set is below rad + dm/4, and (for a lossy medium) the sub-triangle's
+nearest point lies within 12/|Im k| of it (farther on, the integrand is below exp(-12) of its
+peak and the leaf's 7 points take it as it is).
 
 Pairs use this scheme when they are near (the small-|k| criterion: centroid distance below
-2.1 times the larger diameter) and |k| max(diam_t, diam_s) > 0.5; near pairs separated by more
-than 36/|Im k| (centroid distance minus both circumradii) take the regular 7 x 7 rule, their
-values being below exp(-36) of the touching pairs'.
+2.1 times the larger diameter) and |k| max(diam_t, diam_s) > 0.5; a near pair whose testing
+triangle lies wholly farther than 18/|Im k| from the source (T's centroid distance to S minus
+T's circumradius) takes the regular 7 x 7 rule, its values being below exp(-18) of the
+touching pairs'.
 """
 from __future__ import annotations
 
@@ -48,14 +52,15 @@ import numpy as np
 from .quad import radon7
 
 HIGHK = 0.5
-DECAY = 36.0
-NGL = 8
+DECAY = 18.0
+NGL = 6
 DEPTH_MAX = 3
 P_ZERO = 1e-12
 # refinement controls for the convergence study (0 = the rule above): extra subdivision levels
 # and extra Gauss-Legendre points per interval
 REFINE_DEPTH = 0
 SPLIT_MARGIN = 0.25
+SPLIT_DECAY = 12.0
 DMAX_FACTOR = 6.0
 
 
@@ -240,13 +245,16 @@ def leaves(T, S, nS, diamS, k):
             return min(_seg_dist(c, S[i], S[(i + 1) % 3]) for i in range(3))
         return _tri_dist(c, S, nS)
 
+    kim = abs(complex(k).imag)
+
     def rec(t, lev):
         c = t.mean(axis=0)
         if lev < D:
             rad = max(np.linalg.norm(t[j] - c) for j in range(3))
             dm = max(np.linalg.norm(t[1] - t[0]), np.linalg.norm(t[2] - t[1]),
                      np.linalg.norm(t[0] - t[2]))
-            if dist(c) < rad + SPLIT_MARGIN * dm:
+            dc = dist(c)
+            if dc < rad + SPLIT_MARGIN * dm and (kim == 0.0 or kim * (dc - rad) < SPLIT_DECAY):
                 for ch in _sub4(t):
                     rec(ch, lev + 1)
                 return
@@ -304,9 +312,12 @@ def pair_moments_batch(Ts, Ss, nSs, diamSs, k, want_K=True, chunk=20000):
     return out
 
 
-def separated(cT, cS, radT, radS, k):
-    """True when the pair is beyond the decay range (regular rule)."""
+def separated(T, S, nS, k):
+    """True when the pair is beyond the decay range (regular rule): every point of T lies farther
+    than DECAY / |Im k| from S (distance of T's centroid to S minus T's circumradius)."""
     kim = abs(complex(k).imag)
     if kim == 0.0:
         return False
-    return float(np.linalg.norm(cT - cS)) - radT - radS > DECAY / kim
+    c = T.mean(axis=0)
+    rad = max(np.linalg.norm(T[j] - c) for j in range(3))
+    return kim * (_tri_dist(c, S, nS) - rad) > DECAY

@@ -95,9 +95,10 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
     # oracle/highk.py, or the regular rule beyond the decay range
     hk = near & (abs(k) * dmax > highk.HIGHK)
     if np.any(hk):
-        rad = np.max(np.linalg.norm(X - rw.centroid[:, None, :], axis=2), axis=1)
         if complex(k).imag != 0.0:
-            sep = np.linalg.norm(dc, axis=1) - rad[T] - rad[S] > highk.DECAY / abs(complex(k).imag)
+            sep = np.zeros(T.size, dtype=bool)
+            for i in np.nonzero(hk)[0]:
+                sep[i] = highk.separated(X[T[i]], X[S[i]], rw.normal[S[i]], k)
             near &= ~(hk & sep)
             hk &= ~sep
         ih = np.nonzero(hk)[0]

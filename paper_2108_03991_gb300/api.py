@@ -217,8 +217,8 @@ class Context:
         self._read_info()
 
     def _read_info(self):
-        info = (C.c_int64 * 22)()
-        _check(lib().aim_info(self.h, info, 22))
+        info = (C.c_int64 * 32)()
+        _check(lib().aim_info(self.h, info, 32))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -234,6 +234,9 @@ class Context:
         self.gemv_kind = info[19]  # 0 row plan, 1 flat, 2 staged, 3 stream, 5 and 6 task lists
         self.gemv_cps = info[20]
         self.matvec_mode = info[21]  # schedule of e = Z h (aim_matvec_schedule)
+        self.setup_stage_s = dict(zip(
+            ("geometry", "stencils", "internal_ki", "internal_k0", "lu", "yz", "near", "ghat",
+             "gemv_tune", "schedule_tune"), (v * 1e-6 for v in info[22:32])))
 
     # ---- ports and far field ---------------------------------------------------------
     def port_ring(self, obj, axis, coord, tol=1e-6):

@@ -67,7 +67,9 @@ int aim_setup(const bem_mesh* mesh, const aim_grid* grid, double freq_hz, aim_ct
   cudaGetDevice(&c->device);
   c->freq = freq_hz;
   c->k0 = k0_of(freq_hz);
+  const double t0 = wall_ms();
   int rc = build_geometry(c, mesh, grid);
+  c->setup_ms[0] = wall_ms() - t0;
   if (rc == BEM_OK) rc = setup_device(c);
   if (rc != BEM_OK) {
     aim_destroy(c);
@@ -107,6 +109,7 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
                    c->gplan.tma ? 0 : c->gplan.unroll, ns(c->tune_ms[0]), ns(c->tune_ms[1]),
                    c->tune_rejected, kind, c->gplan.cps, c->z_after};
   for (int i = 0; i < n && i < 22; ++i) info[i] = v[i];
+  for (int i = 22; i < n && i < 32; ++i) info[i] = (int64_t)(c->setup_ms[i - 22] * 1e3);
   return BEM_OK;
 }
 

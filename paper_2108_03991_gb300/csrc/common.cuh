@@ -252,6 +252,10 @@ struct aim_ctx {
   bem::GemvPlan gmr;           // several right-hand sides: task list of 16-row tasks (k_gemv_mr)
   bem::GemvPlan gplan_auto;    // the autotuner's FP32 choice
   bem::GemvPlan gplan_alt[2];  // best plain and best staged FP32 plans (ncta = 0: none)
+  // wall time of the set-up stages in ms (aim_info entries 22-31): host geometry, stencils,
+  // internal integrals at k_i, internal integrals at k0, LU solves, C = Y Z, near region,
+  // FFT of the grid kernel, GEMV autotuner, matvec schedule tuner
+  double setup_ms[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   float tune_ms[2] = {0, 0};  // autotuner: best plain, best staged candidate (5 launches, ms)
   int tune_rejected = 0;      // autotuner candidates rejected (wrong product or timed out)
   std::vector<float> tune_table;  // autotuner: (kind, cps, split, unroll, ns) per candidate
@@ -401,6 +405,7 @@ int precond_apply_mixed(aim_ctx* c, const double2* r, float2* u32, double2* u64,
 int precond_apply_batch(aim_ctx* c, const double2* r, int nrhs, float2* u32, double2* u64,
                         cudaStream_t s);
 void free_geo_store(aim_ctx* c);
+double wall_ms();  // host wall clock in milliseconds
 // the dense L_k and K_k + I_x/2 of one object as the set-up forms them before its LU solve
 // (pass 0: k = k_i, pass 1: k = k0), row-major n_i x n_i complex doubles on the host
 int export_LK(aim_ctx* c, int obj, int pass, double2* L_out, double2* K_out);

@@ -245,25 +245,29 @@ __device__ inline void pair_moments(const Tri& T, const Tri& S, double kr, doubl
 //      int_S grad_r G  = -[sum_e u_e J3_e + n (sgn(d) Omega e^{-jka} - d sum_e J4_e)] / (4 pi)
 //    J1 = int P e^{-jkR}/(P^2+t^2), J2 = int e^{-jkR}, J3 = int e^{-jkR}/R,
 //    J4 = int P e^{-jkR}/((P^2+t^2) R) over [l-, l+]; Omega the plane angle S subtends at rho;
-//    each J by 8-point Gauss-Legendre on a graded partition of |t| (the integrands are even):
+//    each J by 6-point Gauss-Legendre on a graded partition of |t| (the integrands are even):
 //    breakpoints h0 2^j (h0 = min(|P|, 1/|k|)/2; w instead of |P| when P = 0) up to the first
 //    above 2 dmax, then steps dmax = kDmaxFactor/|k|, cut where |Im k| (R - w) > kDecay; edges
 //    with |Im k| (w - a) > kDecay skipped (w = sqrt(P^2 + a^2));
 //  * outer integral: T split into four midpoint children, recursively, where a sub-triangle's
-//    centroid is closer to the set where the inner integrals vary fast (the edges of S when T
-//    lies in S's plane, S itself otherwise) than its circumradius plus kSplitMargin times its
-//    diameter, down to depth min(kDepthMax, ceil(log2(|k| diam_T))); Radon's 7 points per leaf;
-//  * near pairs farther apart than kDecay/|Im k| (centroid distance minus both circumradii) take
-//    the regular 7 x 7 rule.
+//    centroid c is closer to the set where the inner integrals vary fast (the edges of S when T
+//    lies in S's plane, S itself otherwise) than its circumradius rad plus kSplitMargin times its
+//    diameter and, for a lossy medium, |Im k| (dist - rad) < kSplitDecay, down to depth
+//    min(kDepthMax, ceil(log2(|k| diam_T))); Radon's 7 points per leaf;
+//  * near pairs whose testing triangle lies wholly beyond kDecay/|Im k| of the source (T's
+//    centroid distance to S minus its circumradius) take the regular 7 x 7 rule.
+// The set-up evaluates one outer rule point per thread (k_hk_points in setup.cu).
 constexpr double kHighK = 0.5;
-constexpr double kDecay = 36.0;
+constexpr double kDecay = 18.0;
 constexpr double kPZero = 1e-12;
 constexpr double kSplitMargin = 0.25;
+constexpr double kSplitDecay = 12.0;
 constexpr double kDmaxFactor = 6.0;
 constexpr int kDepthMax = 3;
 
-// 8-point Gauss-Legendre on [0, 1]: c_gl8[i] = node, c_gl8[8 + i] = weight
-__constant__ double c_gl8[16];
+// Gauss-Legendre on [0, 1] with kNgl points: c_glx[i] = node, c_glx[kNgl + i] = weight
+constexpr int kNgl = 6;
+__constant__ double c_glx[2 * kNgl];
 
 struct EdgeJ {
   double2 J1, J2, J3, J4;
@@ -278,9 +282,9 @@ __device__ inline void hk_piece(double P, double w2, double kr, double ki, doubl
   auto seg = [&](double hi) {
     const double L = hi - lo;
     if (L > 0) {
-      for (int q = 0; q < 8; ++q) {
-        const double t = lo + L * c_gl8[q];
-        const double wt = L * c_gl8[8 + q];
+      for (int q = 0; q < kNgl; ++q) {
+        const double t = lo + L * c_glx[q];
+        const double wt = L * c_glx[kNgl + q];
         const double R = sqrt(w2 + t * t);
         double sn, cs;
         sincos(kr * R, &sn, &cs);
@@ -450,7 +454,7 @@ __device__ inline double sub_diam(const Sub& t) {
 }
 
 // does the reading split this sub-triangle (given it is above the depth limit)?
-__device__ inline bool hk_split(const Sub& t, const Tri& S, bool coplanar) {
+__device__ inline bool hk_split(const Sub& t, const Tri& S, bool coplanar, double kim) {
   const double c[3] = {(t.v[0][0] + t.v[1][0] + t.v[2][0]) / 3.0,
                        (t.v[0][1] + t.v[1][1] + t.v[2][1]) / 3.0,
                        (t.v[0][2] + t.v[1][2] + t.v[2][2]) / 3.0};
@@ -469,7 +473,7 @@ __device__ inline bool hk_split(const Sub& t, const Tri& S, bool coplanar) {
   } else {
     dist = tri_dist(c, S);
   }
-  return dist < rad + kSplitMargin * dm;
+  return dist < rad + kSplitMargin * dm && (kim == 0.0 || kim * (dist - rad) < kSplitDecay);
 }
 
 __device__ inline int hk_depth(double kabs, double diamT) {
@@ -492,6 +496,85 @@ __device__ inline bool hk_coplanar(const Tri& T, const Tri& S) {
   return fabs(d_dot(nT, S.n)) / nn >= 1.0 - 1e-12 && fabs(d_dot(q, S.n)) <= 1e-10 * S.diam;
 }
 
+// one outer rule point r (weight wp): add its contributions to the 28 moment sums
+// (M0, M2, M1[3], M1p[3], Vs[3], U[3] as re, im)
+__device__ inline void hk_point(const double* r, double wp, const Tri& S, double kr, double ki,
+                                bool wantK, double* acc) {
+  double2 S0, S1[3], V[3];
+  hk_inner(r, S, kr, ki, wantK, &S0, S1, V);
+  acc[0] += wp * S0.x; acc[1] += wp * S0.y;
+  for (int a = 0; a < 3; ++a) {
+    acc[2] += wp * r[a] * S1[a].x; acc[3] += wp * r[a] * S1[a].y;
+    acc[4 + 2 * a] += wp * r[a] * S0.x; acc[5 + 2 * a] += wp * r[a] * S0.y;
+    acc[10 + 2 * a] += wp * S1[a].x; acc[11 + 2 * a] += wp * S1[a].y;
+  }
+  if (wantK) {
+    const double2 vx[3] = {
+        make_double2(V[1].x * r[2] - V[2].x * r[1], V[1].y * r[2] - V[2].y * r[1]),
+        make_double2(V[2].x * r[0] - V[0].x * r[2], V[2].y * r[0] - V[0].y * r[2]),
+        make_double2(V[0].x * r[1] - V[1].x * r[0], V[0].y * r[1] - V[1].y * r[0])};
+    for (int a = 0; a < 3; ++a) {
+      acc[16 + 2 * a] += wp * V[a].x; acc[17 + 2 * a] += wp * V[a].y;
+      acc[22 + 2 * a] += wp * vx[a].x; acc[23 + 2 * a] += wp * vx[a].y;
+    }
+  }
+}
+
+__device__ inline void acc_to_moments(const double* acc, Moments* out) {
+  out->M0 = make_double2(acc[0], acc[1]);
+  out->M2 = make_double2(acc[2], acc[3]);
+  for (int a = 0; a < 3; ++a) {
+    out->M1[a] = make_double2(acc[4 + 2 * a], acc[5 + 2 * a]);
+    out->M1p[a] = make_double2(acc[10 + 2 * a], acc[11 + 2 * a]);
+    out->Vs[a] = make_double2(acc[16 + 2 * a], acc[17 + 2 * a]);
+    out->U[a] = make_double2(acc[22 + 2 * a], acc[23 + 2 * a]);
+  }
+}
+
+// a large-|k| pair whose testing triangle is not subdivided: Radon's 7 points of T, one thread
+__device__ inline void hk_pair_moments_leaf(const Tri& T, const Tri& S, double kr, double ki,
+                                            bool wantK, Moments* out) {
+  double acc[28];
+  for (int i = 0; i < 28; ++i) acc[i] = 0.0;
+  for (int q = 0; q < 7; ++q) {
+    double r[3];
+    rule_point(T, c_r7, q, r);
+    double e1[3], e2[3], cr[3];
+    d_sub(T.v[1], T.v[0], e1);
+    d_sub(T.v[2], T.v[0], e2);
+    d_cross(e1, e2, cr);
+    hk_point(r, c_r7[4 * q + 3] * (0.5 * sqrt(d_dot(cr, cr))), S, kr, ki, wantK, acc);
+  }
+  acc_to_moments(acc, out);
+}
+
+// The outer rule points of a large-|k| pair as a flat list: a point is (finest sub-triangle index
+// idx below the leaf that owns it, rule point q). hk_leaf walks from T to the leaf containing
+// finest index idx and reports whether idx owns it (the first finest index below the leaf).
+__device__ inline bool hk_leaf(const Tri& T, const Tri& S, int D, bool cop, double kim, int idx,
+                               Sub* leaf) {
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) leaf->v[k][a] = T.v[k][a];
+  for (int lev = 0; lev < D; ++lev) {
+    if (!hk_split(*leaf, S, cop, kim)) return (idx & ((1 << (2 * (D - lev))) - 1)) == 0;
+    Sub ch;
+    sub_child(*leaf, (idx >> (2 * (D - 1 - lev))) & 3, &ch);
+    *leaf = ch;
+  }
+  return true;
+}
+
+// number of outer rule points of the pair (7 per leaf)
+__device__ inline int hk_count_points(const Tri& T, const Tri& S, double kr, double ki) {
+  const int D = hk_depth(sqrt(kr * kr + ki * ki), T.diam);
+  const bool cop = hk_coplanar(T, S);
+  int n = 0;
+  Sub leaf;
+  for (int idx = 0; idx < (1 << (2 * D)); ++idx)
+    if (hk_leaf(T, S, D, cop, fabs(ki), idx, &leaf)) n += 7;
+  return n;
+}
+
 // Moments of one high-|k| pair by one warp: the lanes take the depth-D sub-triangle indices and
 // their 7 rule points; a leaf is owned by the first finest index below it. Lane 0 of the result
 // holds the sums.
@@ -499,6 +582,7 @@ __device__ inline void hk_pair_moments_warp(const Tri& T, const Tri& S, double k
                                             bool wantK, Moments* out) {
   const int lane = threadIdx.x & 31;
   const double kabs = sqrt(kr * kr + ki * ki);
+  const double kim = fabs(ki);
   const int D = hk_depth(kabs, T.diam);
   const bool cop = hk_coplanar(T, S);
   const int nfine = 1 << (2 * D);
@@ -511,7 +595,7 @@ __device__ inline void hk_pair_moments_warp(const Tri& T, const Tri& S, double k
       for (int a = 0; a < 3; ++a) t.v[k][a] = T.v[k][a];
     bool own = true;
     for (int lev = 0; lev < D; ++lev) {
-      if (!hk_split(t, S, cop)) {
+      if (!hk_split(t, S, cop, kim)) {
         // a leaf at this level: owned by the finest index whose lower digits are all zero
         const int low = idx & ((1 << (2 * (D - lev))) - 1);
         own = low == 0;
@@ -532,44 +616,18 @@ __device__ inline void hk_pair_moments_warp(const Tri& T, const Tri& S, double k
     const double r[3] = {l1 * t.v[0][0] + l2 * t.v[1][0] + l3 * t.v[2][0],
                          l1 * t.v[0][1] + l2 * t.v[1][1] + l3 * t.v[2][1],
                          l1 * t.v[0][2] + l2 * t.v[1][2] + l3 * t.v[2][2]};
-    const double wp = c_r7[4 * q + 3] * area;
-    double2 S0, S1[3], V[3];
-    hk_inner(r, S, kr, ki, wantK, &S0, S1, V);
-    // M0, M2, M1[3], M1p[3], Vs[3], U[3] (re, im) in acc
-    acc[0] += wp * S0.x; acc[1] += wp * S0.y;
-    for (int a = 0; a < 3; ++a) {
-      acc[2] += wp * r[a] * S1[a].x; acc[3] += wp * r[a] * S1[a].y;
-      acc[4 + 2 * a] += wp * r[a] * S0.x; acc[5 + 2 * a] += wp * r[a] * S0.y;
-      acc[10 + 2 * a] += wp * S1[a].x; acc[11 + 2 * a] += wp * S1[a].y;
-    }
-    if (wantK) {
-      const double2 vx[3] = {
-          make_double2(V[1].x * r[2] - V[2].x * r[1], V[1].y * r[2] - V[2].y * r[1]),
-          make_double2(V[2].x * r[0] - V[0].x * r[2], V[2].y * r[0] - V[0].y * r[2]),
-          make_double2(V[0].x * r[1] - V[1].x * r[0], V[0].y * r[1] - V[1].y * r[0])};
-      for (int a = 0; a < 3; ++a) {
-        acc[16 + 2 * a] += wp * V[a].x; acc[17 + 2 * a] += wp * V[a].y;
-        acc[22 + 2 * a] += wp * vx[a].x; acc[23 + 2 * a] += wp * vx[a].y;
-      }
-    }
+    hk_point(r, c_r7[4 * q + 3] * area, S, kr, ki, wantK, acc);
   }
   for (int i = 0; i < 28; ++i) {
     double v = acc[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     acc[i] = v;
   }
-  out->M0 = make_double2(acc[0], acc[1]);
-  out->M2 = make_double2(acc[2], acc[3]);
-  for (int a = 0; a < 3; ++a) {
-    out->M1[a] = make_double2(acc[4 + 2 * a], acc[5 + 2 * a]);
-    out->M1p[a] = make_double2(acc[10 + 2 * a], acc[11 + 2 * a]);
-    out->Vs[a] = make_double2(acc[16 + 2 * a], acc[17 + 2 * a]);
-    out->U[a] = make_double2(acc[22 + 2 * a], acc[23 + 2 * a]);
-  }
+  acc_to_moments(acc, out);
 }
 
 // classification of a pair for the reading: 0 regular 7 x 7, 1 near (small-|k| subtraction),
-// 2 near at large |k| (the edge-integral scheme above)
+// 2 near at large |k| with T subdivided, 3 near at large |k| with T a single leaf
 __device__ inline int pair_kind(const Tri& T, const Tri& S, double kr, double ki) {
   double dc[3];
   d_sub(T.c, S.c, dc);
@@ -578,18 +636,23 @@ __device__ inline int pair_kind(const Tri& T, const Tri& S, double kr, double ki
   if (!near) return 0;
   const double kabs = sqrt(kr * kr + ki * ki);
   if (!(kabs * dm > kHighK)) return 1;
+  Sub t;
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) t.v[k][a] = T.v[k][a];
+  const double c[3] = {(t.v[0][0] + t.v[1][0] + t.v[2][0]) / 3.0,
+                       (t.v[0][1] + t.v[1][1] + t.v[2][1]) / 3.0,
+                       (t.v[0][2] + t.v[1][2] + t.v[2][2]) / 3.0};
   if (ki != 0.0) {
-    double radT = 0, radS = 0;
+    double rad = 0;
     for (int j = 0; j < 3; ++j) {
       double e[3];
-      d_sub(T.v[j], T.c, e);
-      radT = fmax(radT, sqrt(d_dot(e, e)));
-      d_sub(S.v[j], S.c, e);
-      radS = fmax(radS, sqrt(d_dot(e, e)));
+      d_sub(t.v[j], c, e);
+      rad = fmax(rad, sqrt(d_dot(e, e)));
     }
-    if (sqrt(d_dot(dc, dc)) - radT - radS > kDecay / fabs(ki)) return 0;
+    if (fabs(ki) * (tri_dist(c, S) - rad) > kDecay) return 0;
   }
-  return 2;
+  if (hk_depth(kabs, T.diam) > 0 && hk_split(t, S, hk_coplanar(T, S), fabs(ki))) return 2;
+  return 3;
 }
 
 }  // namespace bem

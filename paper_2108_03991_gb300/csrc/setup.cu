@@ -4,6 +4,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 
@@ -11,6 +12,11 @@
 #include "quad.cuh"
 
 namespace bem {
+
+double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 void build_ix_fd(const aim_ctx* c, std::vector<int32_t>* ixcol, std::vector<double>* ixval,
                  std::vector<double>* fdE, std::vector<double>* fdT);
@@ -99,13 +105,13 @@ static int upload_rules() {
   BEM_CUDA(cudaMemcpyToSymbol(c_r7, r7, sizeof(r7)));
   BEM_CUDA(cudaMemcpyToSymbol(c_r28, r28, sizeof(r28)));
   BEM_CUDA(cudaMemcpyToSymbol(c_gl, gl, sizeof(gl)));
-  double x8[8], w8[8], g8[16];
-  gauss_legendre(8, x8, w8);
-  for (int i = 0; i < 8; ++i) {
-    g8[i] = 0.5 * (x8[i] + 1.0);
-    g8[8 + i] = 0.5 * w8[i];
+  double xg[kNgl], wg[kNgl], gx[2 * kNgl];
+  gauss_legendre(kNgl, xg, wg);
+  for (int i = 0; i < kNgl; ++i) {
+    gx[i] = 0.5 * (xg[i] + 1.0);
+    gx[kNgl + i] = 0.5 * wg[i];
   }
-  BEM_CUDA(cudaMemcpyToSymbol(c_gl8, g8, sizeof(g8)));
+  BEM_CUDA(cudaMemcpyToSymbol(c_glx, gx, sizeof(gx)));
   return BEM_OK;
 }
 
@@ -279,9 +285,10 @@ __global__ void k_obj_moments(DGeo g, int t0, int m, double kr, double ki, bool 
   load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + it, &T);
   load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + is, &S);
   const int kind = pair_kind(T, S, kr, ki);
-  if (kind == 2) {
+  if (kind >= 2) {
     const int p = atomicAdd(hk_count, 1);
     hk_list[p] = (int)idx;  // at most m * m entries: the list holds them all
+    mom[idx] = Moments{};   // the point kernel adds into it
     return;
   }
   Moments M;
@@ -289,18 +296,87 @@ __global__ void k_obj_moments(DGeo g, int t0, int m, double kr, double ki, bool 
   mom[idx] = M;
 }
 
-__global__ void k_obj_moments_hk(DGeo g, int t0, int m, double kr, double ki, bool wantK,
-                                 Moments* mom, const int* hk_list, int count) {
-  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  if (w >= count) return;  // warp-uniform
-  const int idx = hk_list[w];
-  const int it = idx / m, is = idx % m;
+// outer rule points per large-|k| pair (one thread per pair)
+__global__ void k_hk_count(DGeo g, int t0, int m, double kr, double ki, const int* hk_list,
+                           int count, int* npts) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const int idx = hk_list[p];
   Tri T, S;
-  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + it, &T);
-  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + is, &S);
-  Moments M;
-  hk_pair_moments_warp(T, S, kr, ki, wantK, &M);
-  if ((threadIdx.x & 31) == 0) mom[idx] = M;
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx / m, &T);
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx % m, &S);
+  npts[p] = hk_count_points(T, S, kr, ki);
+}
+
+// the flat point list: item = pair * 512 + finest index * 8 + rule point, pairs in list order
+__global__ void k_hk_items(DGeo g, int t0, int m, double kr, double ki, const int* hk_list,
+                           int count, const int64_t* off, int32_t* items) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const int idx = hk_list[p];
+  Tri T, S;
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx / m, &T);
+  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx % m, &S);
+  const int D = hk_depth(sqrt(kr * kr + ki * ki), T.diam);
+  const bool cop = hk_coplanar(T, S);
+  int64_t o = off[p];
+  Sub leaf;
+  for (int f = 0; f < (1 << (2 * D)); ++f)
+    if (hk_leaf(T, S, D, cop, fabs(ki), f, &leaf))
+      for (int q = 0; q < 7; ++q) items[o++] = p * 512 + f * 8 + q;
+}
+
+// one outer rule point per thread: its inner integrals, added into its pair's moments (a
+// segmented sum over the warp's consecutive items of one pair, then one atomic add per pair
+// and warp)
+__global__ void __launch_bounds__(128) k_hk_points(DGeo g, int t0, int m, double kr, double ki,
+                                                   bool wantK, const int* hk_list,
+                                                   const int32_t* items, int64_t nitems,
+                                                   Moments* mom) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  double acc[28];
+  for (int a = 0; a < 28; ++a) acc[a] = 0.0;
+  int p = -1;
+  if (i < nitems) {
+    const int32_t code = items[i];
+    p = code >> 9;
+    const int f = (code >> 3) & 63, q = code & 7;
+    const int idx = hk_list[p];
+    Tri T, S;
+    load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx / m, &T);
+    load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx % m, &S);
+    const int D = hk_depth(sqrt(kr * kr + ki * ki), T.diam);
+    Sub leaf;
+    hk_leaf(T, S, D, hk_coplanar(T, S), fabs(ki), f, &leaf);
+    double e1[3], e2[3], cr[3];
+    d_sub(leaf.v[1], leaf.v[0], e1);
+    d_sub(leaf.v[2], leaf.v[0], e2);
+    d_cross(e1, e2, cr);
+    const double area = 0.5 * sqrt(d_dot(cr, cr));
+    const double l1 = c_r7[4 * q], l2 = c_r7[4 * q + 1], l3 = c_r7[4 * q + 2];
+    const double r[3] = {l1 * leaf.v[0][0] + l2 * leaf.v[1][0] + l3 * leaf.v[2][0],
+                         l1 * leaf.v[0][1] + l2 * leaf.v[1][1] + l3 * leaf.v[2][1],
+                         l1 * leaf.v[0][2] + l2 * leaf.v[1][2] + l3 * leaf.v[2][2]};
+    hk_point(r, c_r7[4 * q + 3] * area, S, kr, ki, wantK, acc);
+  }
+  // suffix sums within runs of equal p (items of a pair are consecutive)
+  for (int o = 1; o < 32; o <<= 1) {
+    const int po = __shfl_down_sync(0xffffffffu, p, o);
+    const bool take = lane + o < 32 && po == p;
+    for (int a = 0; a < 28; ++a) {
+      const double v = __shfl_down_sync(0xffffffffu, acc[a], o);
+      if (take) acc[a] += v;
+    }
+  }
+  const int pu = __shfl_up_sync(0xffffffffu, p, 1);
+  if (p >= 0 && (lane == 0 || pu != p)) {
+    double* dst = reinterpret_cast<double*>(&mom[hk_list[p]]);
+    // Moments layout: M0, M2, M1[3], M1p[3], U[3], Vs[3] (double2 each)
+    const int map[28] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15,
+                         22, 23, 24, 25, 26, 27, 16, 17, 18, 19, 20, 21};
+    for (int a = 0; a < 28; ++a) atomicAdd(dst + map[a], acc[a]);
+  }
 }
 
 // Lc = L_k, Bc = K_k + I_x/2 (column-major n x n) from the pair moments
@@ -1031,10 +1107,35 @@ struct MomentScratch {
   int* list = nullptr;
   int* count = nullptr;
   int64_t cap = 0;
+  int* npts = nullptr;        // points per large-|k| pair
+  int64_t* off = nullptr;     // their offsets in the point list
+  int32_t* items = nullptr;   // the point list
+  int64_t pcap = 0, icap = 0;
   ~MomentScratch() {
     if (mom) cudaFree(mom);
     if (list) cudaFree(list);
     if (count) cudaFree(count);
+    if (npts) cudaFree(npts);
+    if (off) cudaFree(off);
+    if (items) cudaFree(items);
+  }
+  int reserve_pts(int64_t pairs, int64_t points) {
+    if (pairs > pcap) {
+      if (npts) cudaFree(npts);
+      if (off) cudaFree(off);
+      npts = nullptr;
+      off = nullptr;
+      BEM_CUDA(cudaMalloc(&npts, pairs * sizeof(int)));
+      BEM_CUDA(cudaMalloc(&off, pairs * sizeof(int64_t)));
+      pcap = pairs;
+    }
+    if (points > icap) {
+      if (items) cudaFree(items);
+      items = nullptr;
+      BEM_CUDA(cudaMalloc(&items, points * sizeof(int32_t)));
+      icap = points;
+    }
+    return BEM_OK;
   }
   int reserve(int64_t pairs) {
     if (pairs <= cap) return BEM_OK;
@@ -1063,9 +1164,27 @@ static int object_LK(aim_ctx* c, const DGeo& g, int obj, std::complex<double> k,
   BEM_CUDA(cudaGetLastError());
   int nhk = 0;
   BEM_CUDA(cudaMemcpy(&nhk, ms->count, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nhk >= (1 << 22)) {
+    set_error("aim_setup: object %d has %d large-|k| near pairs (at most %d)", obj, nhk, (1 << 22) - 1);
+    return BEM_EINVAL;
+  }
   if (nhk > 0) {
-    k_obj_moments_hk<<<nblk((int64_t)nhk * 32, 128), 128>>>(g, t0, m, k.real(), k.imag(), true,
-                                                             ms->mom, ms->list, nhk);
+    // count the outer rule points of every large-|k| pair, lay them out, integrate per point
+    BEM_TRY(ms->reserve_pts(nhk, 0));
+    k_hk_count<<<nblk(nhk, 128), 128>>>(g, t0, m, k.real(), k.imag(), ms->list, nhk, ms->npts);
+    BEM_CUDA(cudaGetLastError());
+    std::vector<int> cnt(nhk);
+    std::vector<int64_t> off(nhk);
+    BEM_CUDA(cudaMemcpy(cnt.data(), ms->npts, nhk * sizeof(int), cudaMemcpyDeviceToHost));
+    int64_t tot = 0;
+    for (int p = 0; p < nhk; ++p) { off[p] = tot; tot += cnt[p]; }
+    BEM_TRY(ms->reserve_pts(nhk, tot));
+    BEM_CUDA(cudaMemcpy(ms->off, off.data(), nhk * sizeof(int64_t), cudaMemcpyHostToDevice));
+    k_hk_items<<<nblk(nhk, 128), 128>>>(g, t0, m, k.real(), k.imag(), ms->list, nhk, ms->off,
+                                         ms->items);
+    BEM_CUDA(cudaGetLastError());
+    k_hk_points<<<nblk(tot, 128), 128>>>(g, t0, m, k.real(), k.imag(), true, ms->list, ms->items,
+                                          tot, ms->mom);
     BEM_CUDA(cudaGetLastError());
   }
   k_obj_assemble<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[obj], n, t0, m, k.real(), k.imag(),
@@ -1124,10 +1243,16 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
       // pass 0: Z = -(1/(j k0 eps_rc)) L_{k_i}^{-1}(K_{k_i} + I_x/2)
       // pass 1: Y = (1/(j k0 mu_rl)) L_{k0}^{-1}(K_{k0} + I_x/2), background vacuum
       std::complex<double> k = pass == 0 ? ki : std::complex<double>(c->k0, 0.0);
+      double t0 = wall_ms();
       rc = object_LK(c, g, i, k, &ms, L, B);
       if (rc != BEM_OK) break;
+      cudaDeviceSynchronize();
+      double t1 = wall_ms();
+      c->setup_ms[2 + pass] += t1 - t0;
       rc = lu_solve(ss, L, B, n, ipiv, dinfo, &dwork, &dwsize, &hwork);
       if (rc != BEM_OK) break;
+      cudaDeviceSynchronize();
+      c->setup_ms[4] += wall_ms() - t1;
       std::complex<double> jk0(0.0, c->k0);
       std::complex<double> alpha = pass == 0 ? -1.0 / (jk0 * epsc) : 1.0 / jk0;
       double2 al = make_double2(alpha.real(), alpha.imag());
@@ -1140,6 +1265,7 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
   }
   // C_i = Y_i Z_i (row-major blocks of leading dimension ld: in cuBLAS's column-major view
   // they are the transposes, so C^T = Z^T Y^T is one plain product), in FP64, then rounded
+  const double tyz = wall_ms();
   if (rc == BEM_OK) {
     cublasHandle_t bh = nullptr;
     if (cublasCreate(&bh) != CUBLAS_STATUS_SUCCESS) {
@@ -1165,6 +1291,7 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
     }
   }
   cudaDeviceSynchronize();
+  c->setup_ms[5] = wall_ms() - tyz;
   cudaFree(L);
   cudaFree(B);
   cudaFree(ipiv);
@@ -1242,6 +1369,7 @@ int setup_device(aim_ctx* c) {
       return BEM_EINVAL;
     }
   }
+  double tst = wall_ms();
   BEM_TRY(upload_rules());
   DevGeoStore s;
   BEM_TRY(geo_upload(c, &s));
@@ -1325,15 +1453,23 @@ int setup_device(aim_ctx* c) {
   }
   BEM_TRY(upload(c, &c->d_et, c->et.data(), c->et.size()));
   BEM_TRY(upload(c, &c->d_tedge, c->t_edges.data(), c->t_edges.size()));
+  BEM_CUDA(cudaDeviceSynchronize());
+  c->setup_ms[1] = wall_ms() - tst;
   // internal problem
   BEM_TRY(setup_internal(c, g, c->d_ixcol, c->f64.ix));
   // near region
+  tst = wall_ms();
   BEM_TRY(setup_near(c, g));
+  c->setup_ms[6] = wall_ms() - tst;
   // grid Green's function
+  tst = wall_ms();
   BEM_TRY(make_twiddles<float>(c, c->f32));
   BEM_TRY(make_twiddles<double>(c, c->f64));
   BEM_TRY(fft_init_attrs());
   BEM_TRY(make_ghat(c));
+  BEM_CUDA(cudaDeviceSynchronize());
+  c->setup_ms[7] = wall_ms() - tst;
+  tst = wall_ms();
   // GEMV work list
   {
     int dev = 0, nsm = 0;
@@ -1377,8 +1513,11 @@ int setup_device(aim_ctx* c) {
   BEM_TRY(dalloc_t(c, &c->f64.yout, ntot));
   BEM_TRY(init_streams(c));
   BEM_CUDA(cudaDeviceSynchronize());
+  c->setup_ms[8] = wall_ms() - tst;
   c->geo_store = new DGeo(g);
+  tst = wall_ms();
   BEM_TRY(tune_matvec_schedule(c));
+  c->setup_ms[9] = wall_ms() - tst;
   return BEM_OK;
 }
 

@@ -271,6 +271,100 @@ def trace_batch(seed=0, ntrace=256, widths=(1.0, 4.0), lengths=(10.0, 200.0), ga
     return merge(parts, [sigma] * ntrace), ports
 
 
+def split_ring(cx, cy, r_out=20.0, width=4.0, thick=1.0, gap=4.0, n_theta=50, n_r=2, n_z=1):
+    """Closed surface of a split ring resonator: the annulus r_out - width <= r <= r_out in the
+    plane z in [0, thick], centred at (cx, cy), with a gap of chord length `gap` (at the mean
+    radius) centred on the +x direction. The ring's arc is cut into n_theta equal angular steps,
+    its width into n_r and its thickness into n_z: top, bottom, outer and inner walls are quads
+    of the swept cross-section and the two end faces quads of the cross-section itself, each
+    split into two triangles, outward and counter-clockwise seen from outside
+    (2 (2 n_theta n_r + 2 n_theta n_z + 2 n_r n_z) triangles: 608 for 50, 2, 1)."""
+    r_in = r_out - width
+    r_mid = r_out - 0.5 * width
+    tg = 2.0 * math.asin(gap / (2.0 * r_mid))
+    th = np.linspace(0.5 * tg, 2.0 * math.pi - 0.5 * tg, n_theta + 1)
+    rr = np.linspace(r_in, r_out, n_r + 1)
+    zz = np.linspace(0.0, thick, n_z + 1)
+    vid: dict = {}
+    verts: list = []
+
+    def vertex(j, a, b):
+        key = (j, a, b)
+        i = vid.get(key)
+        if i is None:
+            i = len(verts)
+            vid[key] = i
+            verts.append((cx + rr[a] * math.cos(th[j]), cy + rr[a] * math.sin(th[j]), zz[b]))
+        return i
+
+    tris = []
+
+    def quad(p00, p10, p11, p01, out):
+        """Two triangles of the quad, ordered so that their normal points along `out`."""
+        P = [np.array(verts[i]) for i in (p00, p10, p11)]
+        nrm = np.cross(P[1] - P[0], P[2] - P[0])
+        if np.dot(nrm, out) < 0:
+            p10, p01 = p01, p10
+        tris.append((p00, p10, p11))
+        tris.append((p00, p11, p01))
+
+    for j in range(n_theta):
+        tm = 0.5 * (th[j] + th[j + 1])
+        er = np.array([math.cos(tm), math.sin(tm), 0.0])
+        for a in range(n_r):
+            quad(vertex(j, a, n_z), vertex(j + 1, a, n_z), vertex(j + 1, a + 1, n_z),
+                 vertex(j, a + 1, n_z), np.array([0.0, 0.0, 1.0]))
+            quad(vertex(j, a, 0), vertex(j + 1, a, 0), vertex(j + 1, a + 1, 0), vertex(j, a + 1, 0),
+                 np.array([0.0, 0.0, -1.0]))
+        for b in range(n_z):
+            quad(vertex(j, n_r, b), vertex(j + 1, n_r, b), vertex(j + 1, n_r, b + 1),
+                 vertex(j, n_r, b + 1), er)
+            quad(vertex(j, 0, b), vertex(j + 1, 0, b), vertex(j + 1, 0, b + 1), vertex(j, 0, b + 1),
+                 -er)
+    for j, sgn in ((0, -1.0), (n_theta, 1.0)):
+        et = sgn * np.array([-math.sin(th[j]), math.cos(th[j]), 0.0])  # into the gap
+        for a in range(n_r):
+            for b in range(n_z):
+                quad(vertex(j, a, b), vertex(j, a + 1, b), vertex(j, a + 1, b + 1),
+                     vertex(j, a, b + 1), et)
+    return np.array(verts, dtype=np.float64), np.array(tris, dtype=np.int32)
+
+
+def srr_array(seed=2, nx=32, ny=32, pitch=50.0, jitter=0.05, sigma=SIGMA_AU, **ring) -> Mesh:
+    """nx x ny gold split rings (the large metasurface workload): ring (i, j) centred at
+    (pitch (i + 1/2), pitch (j + 1/2)), its in-plane sizes (outer radius 20 um, width 4 um, gap
+    4 um) scaled by a seeded factor uniform in [1 - jitter, 1 + jitter]; thickness 1 um."""
+    rng = np.random.default_rng(seed)
+    scale = rng.uniform(1.0 - jitter, 1.0 + jitter, nx * ny)
+    parts = []
+    for i in range(nx):
+        for j in range(ny):
+            f = float(scale[i * ny + j])
+            parts.append(split_ring(pitch * (i + 0.5), pitch * (j + 0.5), r_out=20.0 * f,
+                                    width=4.0 * f, gap=4.0 * f, **ring))
+    return merge(parts, [sigma] * len(parts))
+
+
+def srr_array_config(seed=2, n=32, freq=1e12, pitch=50.0) -> tuple[Mesh, Grid, float]:
+    """n x n gold split-ring array at 1 THz with its AIM grid (srr_grid)."""
+    m = srr_array(seed, n, n, pitch)
+    return m, srr_grid(n, pitch), freq
+
+
+def srr_grid(n=32, pitch=50.0) -> Grid:
+    """AIM grid of the n x n split-ring array: 16 n nodes along x and y (512 for 32 x 32), the
+    array's n pitch spread over all but the two margin nodes (3.137 um spacing at 50 um pitch),
+    8 nodes of 0.5 um along z around the 1 um thick layer; the origin is a twelfth of a cell off
+    the symmetric position so that no source centre falls half-way between two nodes."""
+    nxy = 16 * n
+    hxy = pitch * n / (nxy - 2)
+    h = np.array([hxy, hxy, 0.5])
+    nn = np.array([nxy, nxy, 8], dtype=np.int64)
+    centre = np.array([0.5 * pitch * n, 0.5 * pitch * n, 0.5])
+    origin = centre - 0.5 * (nn - 1) * h + h / 12.0
+    return Grid(origin, h, nn)
+
+
 def copper_bar() -> tuple[Mesh, Grid, float]:
     """Copper bar 2x2x20 um, 0.5 um squares (1344 triangles, 2016 edges), 10 GHz,
     AIM grid spacing 0.5 um."""

@@ -65,14 +65,14 @@ def test_inner_off_plane_matches_subdivision(kd):
     S0, S1, V = highk.inner(pts, TRI, NRM, DIAM, k)
     for i, r in enumerate(pts):
         b0, b1, bv = _subdivided(r, k)
-        # the subdivided remainder converges as the square of the sub-triangle size (2/256
-        # here); far from S at large |k| the values are exponentially small and both sides
-        # carry rounding of the O(0.1) static parts (1e-14 absolute)
-        assert abs(S0[i] - b0) <= 3e-10 * abs(b0) + 1e-14
-        assert np.linalg.norm(S1[i] - b1) <= 3e-10 * np.linalg.norm(b1) + 1e-14
+        # the edge rule is accurate to a few 1e-9 of the largest values; far from S at large
+        # |k| the values are exponentially small and the rule's cut-off (exp(-18) of the peak)
+        # and the O(0.1) static parts' rounding set an absolute floor
+        assert abs(S0[i] - b0) <= 1e-8 * abs(b0) + 1e-10
+        assert np.linalg.norm(S1[i] - b1) <= 1e-8 * np.linalg.norm(b1) + 1e-10
         # V's remainder keeps an R^-3 part where |k| R >> 1 (the static subtraction no longer
         # cancels it), so the subdivision is the less accurate side there
-        assert np.linalg.norm(V[i] - bv) <= 3e-8 * np.linalg.norm(bv) + 1e-14
+        assert np.linalg.norm(V[i] - bv) <= 3e-8 * np.linalg.norm(bv) + 1e-10
 
 
 def _polar(rho, k, nseg=64, ng=16):
@@ -119,8 +119,8 @@ def test_inner_in_plane_matches_polar(kd):
     S0, S1, _ = highk.inner(pts, TRI, NRM, DIAM, k)
     for i, r in enumerate(pts):
         b0, b1 = _polar(r, k)
-        assert abs(S0[i] - b0) <= 1e-10 * abs(b0)
-        assert np.linalg.norm(S1[i] - b1) <= 1e-10 * np.linalg.norm(b1)
+        assert abs(S0[i] - b0) <= 1e-8 * abs(b0)
+        assert np.linalg.norm(S1[i] - b1) <= 1e-8 * np.linalg.norm(b1)
 
 
 def test_outer_rule_partitions_the_triangle():
