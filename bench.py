@@ -1,16 +1,18 @@
 """Benchmark: SLIM system matvecs per second on one GB300 (and N independent replicas).
 
-Workload: the precision-study structure — a 4 x 4 array of copper bars (1 x 1 um cross-section,
-5 um pitch, seeded lengths uniform in 5-40 um, 0.5 um mesh: 11,888 triangles, 17,832 RWG
-edges, 16 objects), 10 GHz, AIM grid spacing 0.5 um, order-2 stencils, near radius 2 cells.
-A step is one system matrix-vector product of Eq. (AEFIEoutJ) in complex FP32 (internal blocks
-Z and Y_eq, AIM projection, FFT convolution, interpolation, near region, sparse terms).
-Inputs (Z and Y alone are ~320 MB) exceed the 129 MB L2, so no flush is needed between steps.
+Workload (the largest configuration): a 32 x 32 array of gold split-ring resonators at 1 THz
+(seed 2; outer radius 20 um, width 4 um, gap 4 um with +-5% seeded size jitter, thickness 1 um,
+pitch 50 um; 608 triangles per ring: 622,592 triangles, 933,888 RWG edges, 1,024 objects), AIM
+grid 512 x 512 x 8 (3.137 x 3.137 x 0.5 um), order-2 stencils, near radius 2 cells. A step is
+one system matrix-vector product of Eq. (AEFIEoutJ) in complex FP32 (internal blocks Z and
+C = Y_eq Z, AIM projection, FFT convolution, interpolation, near region, sparse terms). Inputs
+(Z and C alone are 13.6 GB) exceed the 129 MB L2, so no flush is needed between steps.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--bar-array]
 
 `--impl reference` times the FP64 CPU oracle on the host cores (a bounded sample of the same
-workload, scaled to the full workload's matvec cost).
+workload, scaled to the full workload's matvec cost). `--bar-array` adds the 4 x 4 copper bar
+array's numbers (solves with the learned correction, batched solves, the copper bar).
 """
 from __future__ import annotations
 
@@ -28,7 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "matvecs/s (HBM roofline %) and time to 1e-6 residual, chosen vs plain, 1 GB300"
 UNIT = "matvecs/s"
-WORKLOAD = "4x4 Cu bar array (seed 0), 17832 RWG + 11888 pulse unknowns, 10 GHz, AIM 0.5 um grid"
+WORKLOAD = ("32x32 Au split-ring array (seed 2), 933888 RWG + 622592 pulse unknowns, 1 THz, "
+            "AIM grid 512x512x8")
+BAR_WORKLOAD = "4x4 Cu bar array (seed 0), 17832 RWG + 11888 pulse unknowns, 10 GHz, AIM 0.5 um grid"
+SUB = 8  # the oracle's sample: the 8 x 8 sub-array (64 of the 1,024 rings)
 
 
 def peaks():
@@ -113,13 +118,15 @@ def replicas_value(ms_per_step, world):
 
 
 class OracleMatvec:
-    """The FP64 oracle's O-AIM system matvec (Eq. AEFIEoutJ as a sequence, NumPy/SciPy) on the
-    full workload: the 4x4 bar array, 17,832 RWG + 11,888 pulse unknowns, its AIM grid and
-    near-region pattern. The dense internal blocks and the near-region values are seeded random
-    numbers of the right sizes and sparsity: the matvec's cost does not depend on the values,
-    and forming the true ones takes the oracle tens of minutes."""
+    """The FP64 oracle's O-AIM system matvec (Eq. AEFIEoutJ as a sequence, NumPy/SciPy) on a
+    bounded sample of the workload: the SUB x SUB sub-array of the split-ring array (same ring
+    geometry, grid spacing and near-region rule), its matvec time scaled to the full array by
+    the number of rings (every part of the product grows with it). The dense internal blocks
+    and the near-region values are seeded random numbers of the true sizes and sparsity: the
+    matvec's cost does not depend on the values, and forming the true ones takes the oracle
+    tens of minutes."""
 
-    def __init__(self):
+    def __init__(self, sub=SUB, nfull=32):
         import numpy as np
         import scipy.sparse as sp
 
@@ -127,7 +134,7 @@ class OracleMatvec:
         from oracle.rwg import from_mesh
         from paper_2108_03991_gb300 import synth
 
-        mesh, grid, freq = synth.bar_array_config(0, 10e9)
+        mesh, grid, freq = synth.srr_array_config(2, sub)
         rw = from_mesh(mesh)
         A = oaim.Aim(rw, grid.origin, grid.h, grid.n, op.k0_of(freq))
         rng = np.random.default_rng(7)
@@ -139,32 +146,37 @@ class OracleMatvec:
         blocks = synth.rand_blocks(sizes, 8)
         self.S = op.SlimSystem(rw, freq, blocks, blocks, A.LA, A.LPhi)
         self.x = synth.rand_cvec(self.S.n, 1)
-        self.desc = (f"the full workload ({rw.ne} RWG + {rw.nt} pulse unknowns, 16 objects); "
-                     "internal blocks and near-region values seeded random of the true sizes")
+        self.scale = (nfull * nfull) / (sub * sub)
+        self.desc = (f"the {sub}x{sub} sub-array ({rw.ne} RWG + {rw.nt} pulse unknowns, {mesh.nobj} "
+                     f"rings, grid {'x'.join(str(int(v)) for v in grid.n)}), time scaled by the "
+                     f"ring count ({self.scale:g}x) to the {nfull}x{nfull} array; internal blocks "
+                     "and near-region values seeded random of the true sizes")
 
     def run(self, seconds=0.0):
-        """Matvecs for at least `seconds` (at least one); returns seconds per matvec."""
+        """Sample matvecs for at least `seconds` (at least one); returns seconds per matvec of
+        the full workload (the sample's time times the scale)."""
         n, t0 = 0, time.perf_counter()
         while True:
             self.S.matvec(self.x)
             n += 1
             if time.perf_counter() - t0 >= seconds:
-                return (time.perf_counter() - t0) / n
+                return self.scale * (time.perf_counter() - t0) / n
 
 
 def oracle_baseline(seconds=15.0):
-    """The oracle timed on the host cores on the full workload (about `seconds` of work)."""
+    """The oracle timed on the host cores on a bounded sample of the workload (about
+    `seconds` of work)."""
     om = OracleMatvec()
     om.run()
     dt = om.run(seconds)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{om.desc}: {dt:.3f} s per matvec over {seconds:g} s"}
+            "sample": f"{om.desc}: {dt / om.scale:.3f} s per sample matvec over {seconds:g} s"}
 
 
 def run_reference(args, rank, world):
     """The oracle as the reference arm: W untimed matvecs, then K timed steps of the same
-    workload within about a minute in all (one matvec per step at least)."""
+    workload within about a minute in all (one sample matvec per step at least)."""
     if rank != 0:
         return
     om = OracleMatvec()
@@ -186,19 +198,16 @@ def run_reference(args, rank, world):
                                     "d2h_bytes_per_step": 0}}))
 
 
-# DRAM bytes (read + write) per launch of the block GEMV from the ncu capture summarised in
-# profiles/gemv_internal_bar_array.md; valid only for the launch shape captured there
-# DRAM bytes per launch (read + write) of the GEMV shapes captured with ncu on this workload,
-# keyed by (kind, CTAs per SM, split, loads in flight) as aim_info reports them ("pair" first:
-# the paired launch of that shape)
-PROFILED_GEMV = {(1, 6, 0, 4): 207.9e6, (5, 4, 2, 4): 204.9e6, (5, 16, 1, 4): 208.3e6,
-                 (5, 8, 1, 4): 207.6e6, ("pair", 5, 16, 1, 4): 409.7e6,
-                 ("pair", 5, 8, 1, 4): 409.5e6}
+# DRAM bytes (read + write) per launch of the GEMV shapes captured with ncu on the split-ring
+# array, keyed by (rings per side, "pair" for the paired launch of C and Z, kind, CTAs per SM,
+# split, loads in flight) as aim_info reports them; a launch of another shape reports none
+PROFILED_GEMV: dict = {}
 
 
-def gemv_traffic(ctx, paired=False):
-    key = (ctx.gemv_kind, ctx.gemv_cps, ctx.gemv_split, ctx.gemv_unroll)
-    b = PROFILED_GEMV.get(("pair",) + key if paired else key)
+def gemv_traffic(ctx, rings, paired=False):
+    key = (rings, "pair" if paired else "one", ctx.gemv_kind, ctx.gemv_cps, ctx.gemv_split,
+           ctx.gemv_unroll)
+    b = PROFILED_GEMV.get(key)
     return int(b) if b else None
 
 
@@ -208,8 +217,9 @@ def ncu_case(args):
           Z or Y_eq: ~200 MB in FP32, larger than L2);
     aim:  the grid convolution (4 components) on the workload's AIM grid, set up on two small
           boxes at opposite corners of the array's bounding box (same grid, tiny set-up);
-    internal: the workload's own internal products (e = Z h, h_eq = Y e) with the launch the
-          set-up autotuner chose, inside the profiler range "internal_steps".
+    internal: the split-ring array's internal products (e = Z h, h_eq = Y e; --rings per side,
+          8 for a capture that fits the profiler) with the launch the set-up autotuner chose,
+          inside the profiler range "internal_steps".
     batch: the workload's batched system matvec of 4 right-hand sides, inside the profiler
           range "batch_steps"."""
     import numpy as np
@@ -248,7 +258,7 @@ def ncu_case(args):
         print(json.dumps({"ncu_case": "batch", "nrhs": 4}))
         return
     if args.ncu_case == "internal":
-        mesh, grid, freq = synth.bar_array_config(0, 10e9)
+        mesh, grid, freq = synth.srr_array_config(2, args.rings)
         ctx = api.Context(mesh, grid, freq)
         if args.gemv_shape:  # the launch the timed run chose (the autotuner's timing under a
             ctx.gemv_plan(*[int(v) for v in args.gemv_shape.split(",")])  # profiler differs)
@@ -380,6 +390,96 @@ def precision_study(args):
     print(json.dumps({"precision_study": out, "workload": WORKLOAD.replace("10 GHz", "1-100 GHz")}))
 
 
+def bar_array_section(args, api, synth, torch, np, dev):
+    """The 4 x 4 copper bar array (10 GHz): the time to a true FP64 relative residual of 1e-6
+    for the plane wave, plain FP64 GMRES (no preconditioner) against FP64 FGMRES and the chosen
+    FP32-bulk FGMRES (FP64 Arnoldi) with the block-diagonal preconditioner, with and without
+    the learned correction; four plane waves one by one and batched; the copper bar."""
+    mesh, grid, freq = synth.bar_array_config(0, 10e9)
+    t0 = time.perf_counter()
+    ctx = api.Context(mesh, grid, freq)
+    torch.cuda.synchronize()
+    out = {"workload": BAR_WORKLOAD, "setup_s": time.perf_counter() - t0}
+    solve = {}
+    b = ctx.rhs_plane_wave(prec=api.BEM_C64)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ctx.precond(torch.zeros(ctx.n, dtype=torch.complex64, device=dev), prec=api.BEM_C32)
+    torch.cuda.synchronize()
+    solve["precond_setup_s"] = time.perf_counter() - t1
+    # learned correction: trained on another seed of the same family (the benchmark
+    # structure is unseen), weights carried over
+    t1 = time.perf_counter()
+    tmesh, tgrid, _ = synth.bar_array_config(100, 10e9)
+    tctx = api.Context(tmesh, tgrid, 10e9)
+    tctx.net_init(1)
+    losses = tctx.net_train(steps=args.train_steps, batch=4, lr=2e-3, seed=2)
+    w = tctx.net_weights()
+    tctx.close()
+    ctx.net_weights(w)
+    torch.cuda.synchronize()
+    solve["learned_training"] = {
+        "structure": "4x4 Cu bar array, seed 100", "steps": args.train_steps, "batch": 4,
+        "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
+        "seconds_incl_setup": time.perf_counter() - t1}
+    # untimed warm-up: allocates the context's Krylov workspace and captures the FP64 and
+    # FP32 matvec graphs, as a long-lived solver context has them before its next solve
+    for mode in (api.BEM_C64, api.BEM_C32):
+        ctx.solve(b, tol=1e-6, restart=200, max_iter=2, prec_mode=mode, precond=1)
+    solve["warm"] = "workspace and matvec graphs from an untimed 2-iteration solve"
+    for name, mode, pc in (("plain_fp64", api.BEM_C64, 0), ("block_fp64", api.BEM_C64, 1),
+                           ("chosen_fp32_block", api.BEM_C32, 1),
+                           ("chosen_fp32_block_learned", api.BEM_C32, 2)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        torch.cuda.nvtx.range_push("solve_" + name)  # profiler range of this solve
+        xs, info = ctx.solve(b, tol=1e-6, restart=200, max_iter=3000, prec_mode=mode,
+                             time_limit_s=120.0, precond=pc)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    solve[name] = {"seconds": time.perf_counter() - t1, "iters": info["iters"],
+                       "resid_true": info["resid_true"], "status": info["status"]}
+    # four plane waves (polarisation x, y along +z; z, y along +x): solved one after
+    # another with the chosen form, and together with the batched FGMRES
+    waves = [((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)), ((0.0, 1.0, 0.0), (0.0, 0.0, 1.0)),
+             ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0)), ((0.0, 1.0, 0.0), (1.0, 0.0, 0.0))]
+    bw = torch.cat([ctx.rhs_plane_wave(pol, kh, prec=api.BEM_C64) for pol, kh in waves])
+    ctx.solve_batch(bw, tol=1e-6, restart=200, max_iter=2, prec_mode=api.BEM_C32, precond=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    its = []
+    for r in range(4):
+        _, info = ctx.solve(bw[r * ctx.n:(r + 1) * ctx.n].contiguous(), tol=1e-6, restart=200,
+                            max_iter=3000, prec_mode=api.BEM_C32, precond=1)
+        its.append(info["iters"])
+    torch.cuda.synchronize()
+    solve["chosen_4_waves_one_by_one"] = {"seconds": time.perf_counter() - t1, "iters": its}
+    t1 = time.perf_counter()
+    torch.cuda.nvtx.range_push("solve_batch4")
+    _, rc, infos = ctx.solve_batch(bw, tol=1e-6, restart=200, max_iter=3000,
+                                   prec_mode=api.BEM_C32, precond=1, time_limit_s=120.0)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    solve["chosen_4_waves_batched"] = {
+        "seconds": time.perf_counter() - t1, "iters": infos[0]["iters"], "status": rc,
+        "resid_true": [i["resid_true"] for i in infos]}
+    # time to solution with the preconditioner's one-off set-up counted: for one right-hand
+    # side, and the number of right-hand sides after which the chosen form (set-up once,
+    # then one chosen solve each) beats plain FP64 GMRES (one plain solve each)
+    su, pl, ch = (solve["precond_setup_s"], solve["plain_fp64"]["seconds"],
+              solve["chosen_fp32_block"]["seconds"])
+    solve["chosen_incl_precond_setup"] = {
+        "seconds_one_rhs": su + ch, "plain_fp64_seconds_one_rhs": pl,
+        "break_even_rhs": (math.ceil(su / (pl - ch)) if pl > ch else None),
+        "note": "set-up of the block-diagonal preconditioner once per structure, then per "
+                "right-hand side one chosen solve against one plain FP64 solve"}
+
+    out["solve"] = solve
+    ctx.close()
+    out["copper_bar"] = copper_bar_numbers(api, synth, torch)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,6 +488,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--bar-array", action="store_true",
+                    help="add the 4x4 copper bar array's solves (learned correction, batches)")
     ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal", "batch"])
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--precision-study", action="store_true")
@@ -395,6 +497,8 @@ def main():
                     help="matvec schedule (aim_matvec_schedule) in --ncu-case internal")
     ap.add_argument("--gemv-shape", default=None,
                     help="kind,ctas_per_sm,split,unroll of the GEMV launch in --ncu-case internal")
+    ap.add_argument("--rings", type=int, default=32,
+                    help="rings per side of the split-ring array (32: the full workload)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -417,7 +521,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
 
-    mesh, grid, freq = synth.bar_array_config(0, 10e9)
+    mesh, grid, freq = synth.srr_array_config(2, args.rings)
     t0 = time.perf_counter()
     ctx = api.Context(mesh, grid, freq)
     torch.cuda.synchronize()
@@ -432,12 +536,24 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(s)
+        for _ in range(reps):
+            fn()
+        ev1.record(s)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
     with ClockSampler(local) as clk:
         # the same matvecs for about a second before the timed steps, so that the 200 ms clock
-        # samples see the GPU under this load (the timed region alone lasts milliseconds)
+        # samples see the GPU under this load
         t_load = time.perf_counter()
         while time.perf_counter() - t_load < 1.0:
-            for _ in range(50):
+            for _ in range(20):
                 ctx.matvec(x, y, prec=api.BEM_C32)
             torch.cuda.synchronize()
         ev0.record(s)
@@ -453,29 +569,23 @@ def main():
         e = torch.empty(ctx.ne, dtype=torch.complex64, device=dev)
         heq = torch.empty_like(e)
         h = x[:ctx.ne].contiguous()
-        for _ in range(3):
-            ctx.internal(h, e, heq, prec=api.BEM_C32)
-        torch.cuda.synchronize()
-        ev0.record(s)
-        for _ in range(args.steps):
-            ctx.internal(h, e, heq, prec=api.BEM_C32)
-        ev1.record(s)
-        torch.cuda.synchronize()
         paired = ctx.matvec_mode == 3
-        gemv_ms = ev0.elapsed_time(ev1) / ((1 if paired else 2) * args.steps)
+        gemv_ms = timed(lambda: ctx.internal(h, e, heq, prec=api.BEM_C32), args.steps) / \
+            (1 if paired else 2)
+        # the AIM external part alone (Sec. III-A: projection, FFT convolution, interpolation,
+        # precorrected near region) for the RWG vector components (L^A) and the charges (L^Phi)
+        ja = x[:ctx.ne].contiguous()
+        qa = x[ctx.ne:].contiguous()
+        ya = torch.empty_like(ja)
+        yp = torch.empty_like(qa)
+        aim_la_ms = timed(lambda: ctx.matvec(ja, ya, which=api.AIM_OP_LA, prec=api.BEM_C32), args.steps)
+        aim_lp_ms = timed(lambda: ctx.matvec(qa, yp, which=api.AIM_OP_LPHI, prec=api.BEM_C32), args.steps)
         # the batched system matvec: 4 right-hand sides per graph launch
         xb = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.n, 500 + r) for r in range(4)])
                               .astype(np.complex64)).to(dev)
         yb = torch.empty_like(xb)
-        for _ in range(3):
-            ctx.matvec_batch(xb, yb, prec=api.BEM_C32)
-        torch.cuda.synchronize()
-        ev0.record(s)
-        for _ in range(args.steps):
-            ctx.matvec_batch(xb, yb, prec=api.BEM_C32)
-        ev1.record(s)
-        torch.cuda.synchronize()
-        batch_ms = ev0.elapsed_time(ev1) / args.steps
+        batch_ms = timed(lambda: ctx.matvec_batch(xb, yb, prec=api.BEM_C32), args.steps)
+        del xb, yb
         # end to end through the host-buffer call: K distinct pinned host inputs, each copied
         # to the device, multiplied and copied back (the copies of neighbouring steps overlap
         # the products)
@@ -499,105 +609,67 @@ def main():
         ev1.record(s)
         torch.cuda.synchronize()
         e2e1_ms = ev0.elapsed_time(ev1) / args.steps
+        del xh, yh
     ms, e2e_ms, batch_ms, e2e1_ms = max_over_ranks([ms, e2e_ms, batch_ms, e2e1_ms], dev)
 
     solve = None
     if not args.no_solve and rank == 0:
-        # time to a true FP64 relative residual of 1e-6 for the plane-wave excitation:
-        # plain = FP64 GMRES without preconditioner; block = FP64 FGMRES with the block-diagonal
-        # preconditioner; chosen = FP32-bulk FGMRES (FP64 Arnoldi) with the same preconditioner
-        solve = {}
-        b = ctx.rhs_plane_wave(prec=api.BEM_C64)
+        # time to a true FP64 relative residual of 1e-6 for a plane wave at normal incidence
+        # (E along x, the gap's axis; propagation along -z): plain = FP64 GMRES without a
+        # preconditioner; chosen = FP32-bulk FGMRES (FP64 Arnoldi and true residual) with the
+        # block-diagonal preconditioner, its one-off set-up timed separately and counted
+        solve = {"excitation": "plane wave, E along x, k along -z"}
+        b = ctx.rhs_plane_wave((1.0, 0.0, 0.0), (0.0, 0.0, -1.0), prec=api.BEM_C64)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ctx.precond(torch.zeros(ctx.n, dtype=torch.complex64, device=dev), prec=api.BEM_C32)
         torch.cuda.synchronize()
         solve["precond_setup_s"] = time.perf_counter() - t1
-        # learned correction: trained on another seed of the same family (the benchmark
-        # structure is unseen), weights carried over
-        t1 = time.perf_counter()
-        tmesh, tgrid, _ = synth.bar_array_config(100, 10e9)
-        tctx = api.Context(tmesh, tgrid, 10e9)
-        tctx.net_init(1)
-        losses = tctx.net_train(steps=args.train_steps, batch=4, lr=2e-3, seed=2)
-        w = tctx.net_weights()
-        tctx.close()
-        ctx.net_weights(w)
-        torch.cuda.synchronize()
-        solve["learned_training"] = {
-            "structure": "4x4 Cu bar array, seed 100", "steps": args.train_steps, "batch": 4,
-            "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
-            "seconds_incl_setup": time.perf_counter() - t1}
-        # untimed warm-up: allocates the context's Krylov workspace and captures the FP64 and
-        # FP32 matvec graphs, as a long-lived solver context has them before its next solve
-        for mode in (api.BEM_C64, api.BEM_C32):
-            ctx.solve(b, tol=1e-6, restart=200, max_iter=2, prec_mode=mode, precond=1)
+        for mode, pc in ((api.BEM_C64, 0), (api.BEM_C32, 1)):  # workspace and graphs
+            ctx.solve(b, tol=1e-6, restart=100, max_iter=2, prec_mode=mode, precond=pc)
         solve["warm"] = "workspace and matvec graphs from an untimed 2-iteration solve"
-        for name, mode, pc in (("plain_fp64", api.BEM_C64, 0), ("block_fp64", api.BEM_C64, 1),
-                               ("chosen_fp32_block", api.BEM_C32, 1),
-                               ("chosen_fp32_block_learned", api.BEM_C32, 2)):
+        for name, mode, pc, lim in (("chosen_fp32_block", api.BEM_C32, 1, 120.0),
+                                    ("plain_fp64", api.BEM_C64, 0, 90.0)):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            torch.cuda.nvtx.range_push("solve_" + name)  # profiler range of this solve
-            xs, info = ctx.solve(b, tol=1e-6, restart=200, max_iter=3000, prec_mode=mode,
-                                 time_limit_s=120.0, precond=pc)
+            torch.cuda.nvtx.range_push("solve_" + name)
+            _, info = ctx.solve(b, tol=1e-6, restart=100, max_iter=100000, prec_mode=mode,
+                                time_limit_s=lim, precond=pc)
             torch.cuda.synchronize()
             torch.cuda.nvtx.range_pop()
             solve[name] = {"seconds": time.perf_counter() - t1, "iters": info["iters"],
-                           "resid_true": info["resid_true"], "status": info["status"]}
-        # four plane waves (polarisation x, y along +z; z, y along +x): solved one after
-        # another with the chosen form, and together with the batched FGMRES
-        waves = [((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)), ((0.0, 1.0, 0.0), (0.0, 0.0, 1.0)),
-                 ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0)), ((0.0, 1.0, 0.0), (1.0, 0.0, 0.0))]
-        bw = torch.cat([ctx.rhs_plane_wave(pol, kh, prec=api.BEM_C64) for pol, kh in waves])
-        ctx.solve_batch(bw, tol=1e-6, restart=200, max_iter=2, prec_mode=api.BEM_C32, precond=1)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        its = []
-        for r in range(4):
-            _, info = ctx.solve(bw[r * ctx.n:(r + 1) * ctx.n].contiguous(), tol=1e-6, restart=200,
-                                max_iter=3000, prec_mode=api.BEM_C32, precond=1)
-            its.append(info["iters"])
-        torch.cuda.synchronize()
-        solve["chosen_4_waves_one_by_one"] = {"seconds": time.perf_counter() - t1, "iters": its}
-        t1 = time.perf_counter()
-        torch.cuda.nvtx.range_push("solve_batch4")
-        _, rc, infos = ctx.solve_batch(bw, tol=1e-6, restart=200, max_iter=3000,
-                                       prec_mode=api.BEM_C32, precond=1, time_limit_s=120.0)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        solve["chosen_4_waves_batched"] = {
-            "seconds": time.perf_counter() - t1, "iters": infos[0]["iters"], "status": rc,
-            "resid_true": [i["resid_true"] for i in infos]}
-        # time to solution with the preconditioner's one-off set-up counted: for one right-hand
-        # side, and the number of right-hand sides after which the chosen form (set-up once,
-        # then one chosen solve each) beats plain FP64 GMRES (one plain solve each)
-        su, pl, ch = (solve["precond_setup_s"], solve["plain_fp64"]["seconds"],
-                      solve["chosen_fp32_block"]["seconds"])
+                           "resid_true": info["resid_true"], "status": info["status"],
+                           "time_limit_s": lim}
+        su, pl, ch = (solve["precond_setup_s"], solve["plain_fp64"], solve["chosen_fp32_block"])
         solve["chosen_incl_precond_setup"] = {
-            "seconds_one_rhs": su + ch, "plain_fp64_seconds_one_rhs": pl,
-            "break_even_rhs": (math.ceil(su / (pl - ch)) if pl > ch else None),
-            "note": "set-up of the block-diagonal preconditioner once per structure, then per "
-                    "right-hand side one chosen solve against one plain FP64 solve"}
-
-    if not args.no_solve and rank == 0:
-        solve["copper_bar"] = copper_bar_numbers(api, synth, torch)
+            "seconds": su + ch["seconds"], "reached_1e-6": ch["resid_true"] <= 1e-6,
+            "plain_fp64_seconds": pl["seconds"], "plain_reached_1e-6": pl["resid_true"] <= 1e-6,
+            "note": "plain FP64 GMRES stops at its time limit when it has not reached 1e-6; "
+                    "status 1 marks that, resid_true is where it stood"}
 
     if rank == 0:
         hbm, src = peaks()
-        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         ZY = ctx.zy_bytes_c32 // 2  # bytes of Z (or C) in FP32
         # algorithmic bytes of one launch: the matrix (both under the paired schedule), x read,
         # the output(s) written
         gemv_bytes = 2 * ZY + 3 * 8 * ctx.ne if paired else ZY + 2 * 8 * ctx.ne
         achieved = gemv_bytes / (gemv_ms * 1e-3) / 1e9
+        # the AIM external part's algorithmic bytes (complex FP32 s = 8, FP32 weights r = 4):
+        # vectors in and out, stencils read by the projection and again by the interpolation,
+        # per grid component 20 N_g values (scatter, FFT read, padded spectra write and read,
+        # inverse output, gather), the octant of the grid kernel, the near-region CSR values and
+        # columns
+        ne, nt, ng = ctx.ne, ctx.nt, ctx.ng
+        gx, gy, gz = ctx.grid_n
+        b_aim = (2 * 8 * (ne + nt) + 2 * (4 * (81 * ne + 27 * nt) + 4 * (ne + nt))
+                 + 4 * 8 * 20 * ng + 8 * (gx + 1) * (gy + 1) * (gz + 1)
+                 + (ctx.nnz_A + ctx.nnz_P) * (8 + 4))
+        aim_ms = aim_la_ms + aim_lp_ms
+        aim_ach = b_aim / (aim_ms * 1e-3) / 1e9
         cpu = None
         if not args.no_cpu:
             cpu = oracle_baseline(seconds=15.0)
         value = replicas_value(ms, world)
-        # per system matvec: 2 projections, 2 x 3 FFT passes, the near region of j, 2 row
-        # kernels, and the internal GEMVs: one paired launch (schedule 3), else the GEMV of j
-        # and that of e (with a y-initialising launch each in the stream form, schedule 2)
         stream_init = 1 if ctx.gemv_kind == 3 else 0
         launches_per_step = 11 + (1 if ctx.matvec_mode == 3 else
                                   2 + stream_init * (2 if ctx.matvec_mode == 2 else 1))
@@ -605,20 +677,23 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "unknowns": ctx.n, "ne": ctx.ne, "nt": ctx.nt,
+            "config": {"workload": WORKLOAD if args.rings == 32 else
+                       WORKLOAD.replace("32x32", f"{args.rings}x{args.rings}"),
+                       "unknowns": ctx.n, "ne": ctx.ne, "nt": ctx.nt,
                        "objects": ctx.nobj, "grid": list(ctx.grid_n), "fft": list(ctx.padded),
                        "nnz_near": [ctx.nnz_A, ctx.nnz_P], "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (Z, Y ~%.0f MB)" % (ctx.zy_bytes_c32 / 1e6),
-                       "setup_s": setup_s,
-                       "reference_arm": "FP64 oracle on the host cores, same workload; its "
-                                        "internal blocks and near-region values are seeded "
-                                        "random numbers of the true sizes and sparsity"},
+                       "l2": "inputs larger than L2 (Z, C %.1f GB)" % (ctx.zy_bytes_c32 / 1e9),
+                       "setup_s": setup_s, "setup_stage_s": ctx.setup_stage_s,
+                       "reference_arm": "FP64 oracle on the host cores on the 8x8 sub-array, "
+                                        "scaled by the ring count; its internal blocks and "
+                                        "near-region values are seeded random numbers of the "
+                                        "true sizes and sparsity"},
             "roofline": {"kernel": ("k_gemv_pair (C = Y_eq Z and Z in one launch)" if paired
                                     else "k_gemv (block-diagonal Z / C)"), "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": src,
-                         "traffic": gemv_traffic(ctx, paired),
-                         "traffic_unit": "DRAM bytes per launch (ncu, profiles/gemv_internal_bar_array.md)",
+                         "traffic": gemv_traffic(ctx, args.rings, paired),
+                         "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                          "bytes_per_launch": gemv_bytes, "ms_per_launch": gemv_ms,
                          "launch": {"kind": {0: "row plan", 1: "flat", 2: "staged", 3: "stream",
                                              5: "Part_Schedule task list",
@@ -626,16 +701,14 @@ def main():
                                     "shape": [ctx.gemv_kind, ctx.gemv_cps,
                                               max(ctx.gemv_split, 1), ctx.gemv_unroll],
                                     "ctas": ctx.gemv_ctas,
-                                    "parts_per_row": 0 if ctx.gemv_kind >= 5 else ctx.gemv_split,
-                                    "rows_per_task": ((4 if ctx.gemv_cps == 16 else 8) * ctx.gemv_split
-                                                      if ctx.gemv_kind >= 5 else None),
-                                    "loads_in_flight": ctx.gemv_unroll,
                                     "autotune_ns_per_launch": ctx.gemv_tune_ns,
-                                    "autotune_table": [[int(v) for v in r[:4]] + [float(r[4])]
-                                                       for r in ctx.gemv_tune_table() if r[0] not in (4, 7)],
-                                    "matvec_schedule": ctx.matvec_mode,
-                                    "matvec_schedules": [[int(v) for v in r[1:4]] + [float(r[4])]
-                                                         for r in ctx.gemv_tune_table() if r[0] == 4]}},
+                                    "matvec_schedule": ctx.matvec_mode}},
+            "roofline_aim": {"part": "AIM external operators L^A (3 components) and L^Phi: "
+                                     "projection, FFT convolution, interpolation, near region",
+                             "bound": "hbm", "achieved": aim_ach, "peak": hbm, "unit": "GB/s",
+                             "frac": aim_ach / hbm, "peak_source": src,
+                             "bytes_per_matvec": b_aim, "ms": aim_ms,
+                             "ms_LA": aim_la_ms, "ms_LPhi": aim_lp_ms},
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n,
                     "call": f"aim_matvec_host: {args.steps} distinct pinned host vectors in one "
@@ -647,8 +720,6 @@ def main():
                                 "one-vector product that `value` times, with its copies"}},
             "batched": {"nrhs": 4, "value": replicas_value(batch_ms / 4, world), "unit": UNIT,
                         "ms_per_launch": batch_ms,
-                        "gemv_shapes_ns": [[int(r[2]), float(r[4])] for r in ctx.gemv_tune_table()
-                                           if r[0] == 7],
                         "note": "aim_matvec_batch: 4 right-hand sides per graph, matvecs/s counted per right-hand side"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": dict(clk.summary(), window="the timed steps plus about 1 s of the "
@@ -656,11 +727,13 @@ def main():
             "solve": solve,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(out))
     ctx.close()
+    if rank == 0 and args.bar_array and not args.no_solve:
+        out["bar_array"] = bar_array_section(args, api, synth, torch, np, dev)
+    if rank == 0:
+        print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()
