@@ -107,6 +107,7 @@ template <typename R> struct PrecBuf {
   V* LP = nullptr;
   V* Ghat = nullptr;   // octant of the scaled FFT of the circulant grid kernel
   V* Gz = nullptr;     // FP32: Ghat per z line [Py][Px][M][L] in the register z pass's lane order
+  V* Gs = nullptr;     // FP32, slab passes: Ghat octant as [fx][fz][fy]
   V* tw[3] = {nullptr, nullptr, nullptr};  // twiddle tables of the three axes
   R* ix = nullptr;     // [ne][4] I_x values
   R* fdE = nullptr;    // [ne][2] (l/A+, l/A-) : (F D)^T rows

@@ -44,6 +44,28 @@ bool make_fft_plan(int P, FftPlan* plan) {
   return true;
 }
 
+// the slab passes' plans: radix-32 stages first (two stages for 1024 points), then the others
+bool make_fft_plan_r32(int P, FftPlan* plan) {
+  plan->P = P;
+  plan->nst = 0;
+  int n = P;
+  const int rads[6] = {32, 8, 4, 2, 3, 5};
+  for (int r : rads)
+    while (n % r == 0) {
+      if (plan->nst >= kMaxStages) return false;
+      plan->rad[plan->nst++] = r;
+      n /= r;
+    }
+  if (n != 1 || P < 1 || P >= 2048) return false;
+  int Ns = 1;
+  for (int s = 0; s < plan->nst; ++s) {
+    plan->mag_m[s] = div_magic(P / plan->rad[s]);
+    plan->mag_ns[s] = div_magic(Ns);
+    Ns *= plan->rad[s];
+  }
+  return true;
+}
+
 int smooth_length(int need) {
   for (int m = std::max(need, 1);; ++m) {
     int n = m;
@@ -142,6 +164,9 @@ struct Lines {
   bool line_fast;
 };
 
+template <typename V, int M>
+__device__ __forceinline__ void dft_reg(V* v, const V* tw, int tstride, bool inv);
+
 template <typename V, int R, bool SWL>
 __device__ __forceinline__ void stage_r(const V* src, V* dst, const V* tw, int P, int Ns,
                                         uint32_t mag_m, uint32_t mag_ns, const Lines& L, bool inv) {
@@ -167,7 +192,8 @@ __device__ __forceinline__ void stage_r(const V* src, V* dst, const V* tw, int P
         v[r] = cmul(v[r], w);
       }
     }
-    if (R == 2) bfly2(v);
+    if constexpr (R == 32) dft_reg<V, 32>(v, tw, P / 32, inv);
+    else if (R == 2) bfly2(v);
     else if (R == 3) bfly3(v, inv);
     else if (R == 4) bfly4(v, inv);
     else if (R == 5) bfly5(v, inv);
@@ -193,6 +219,31 @@ __device__ V* fft_smem(V* a, V* b, const V* tw, const FftPlan& pl, const Lines& 
       case 3: stage_r<V, 3, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
       case 4: stage_r<V, 4, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
       case 5: stage_r<V, 5, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      default: stage_r<V, 8, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+    }
+    __syncthreads();
+    V* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// fft_smem with radix-32 stages as well (the slab passes only: the 32-point butterfly's
+// registers would otherwise count against every kernel that uses fft_smem)
+template <typename V, bool SWL>
+__device__ V* fft_smem_slab(V* a, V* b, const V* tw, const FftPlan& pl, const Lines& L, bool inv) {
+  int Ns = 1;
+  for (int st = 0; st < pl.nst; ++st) {
+    const int R = pl.rad[st];
+    const uint32_t mm = pl.mag_m[st], mn = pl.mag_ns[st];
+    switch (R) {
+      case 2: stage_r<V, 2, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 3: stage_r<V, 3, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 4: stage_r<V, 4, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 5: stage_r<V, 5, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
+      case 32: stage_r<V, 32, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
       default: stage_r<V, 8, SWL>(a, b, tw, pl.P, Ns, mm, mn, L, inv); break;
     }
     __syncthreads();
@@ -355,10 +406,12 @@ template <> struct Split<10> { static constexpr int A = 2, B = 5; };
 template <> struct Split<12> { static constexpr int A = 4, B = 3; };
 template <> struct Split<15> { static constexpr int A = 3, B = 5; };
 template <> struct Split<16> { static constexpr int A = 4, B = 4; };
+template <> struct Split<32> { static constexpr int A = 4, B = 8; };
 
 // natural-order M-point DFT of v in registers (tw: W_P^j, P = M * tstride)
 template <typename V, int M>
 __device__ __forceinline__ void dft_reg(V* v, const V* tw, int tstride, bool inv) {
+  static_assert(M <= 16 || M == 32, "register DFT length");
   if constexpr (M == 2 || M == 3 || M == 4 || M == 5 || M == 8) {
     bfly_r<V, M>(v, inv);
   } else {
@@ -834,6 +887,393 @@ template <typename V> static size_t plane_smem(int Px, int Py) {
   return ((size_t)Px + Py + 2 * (size_t)Py * sw_len(Px)) * sizeof(V);
 }
 
+// ---------------------------------------------------------------------------------------
+// slab passes (FP32, padded x-y planes too large for shared memory; the split-ring array's
+// 1024 x 1024 planes): three passes over a workspace X[c][kx][z][y] that holds, per component,
+// the x-transformed data rows only (Px * nz * ny values):
+//   x forward : RY rows of one data plane per CTA, zero-padded to Px, FFT along x, stored
+//               kx-major so that pass two reads one contiguous nz x ny slab per kx
+//   y-z fused : one kx per CTA (its Ghat slab staged in shared memory): y FFT of the nz data
+//               planes (zero-padded to Py), then per ky a length-Pz DFT in registers over the
+//               zero-padded z values, times Ghat, the inverse DFT, the nz kept planes back, the
+//               inverse y FFT, the ny kept rows stored in place
+//   x inverse : RY rows per CTA, inverse FFT along x, the nx kept values written to phi
+// HBM traffic per component: ng in, 3 (Px nz ny) written and 2 read, ng out (168 MB at 512 x
+// 512 x 8 against 20 ng = 336 MB for passes over the full padded grid).
+// ---------------------------------------------------------------------------------------
+constexpr int kSlabRY = 4;     // rows per CTA in the x passes (three CTAs per SM)
+constexpr int kSlabMaxNz = 16; // data planes held per ky line in registers
+
+struct SlabArgs {
+  int nx, ny, nz, Px, Py, Pz;
+  int64_t ng, P3;
+  FftPlan px, py;
+  int gy, gz;  // octant dims of Ghat along y and z (Py/2+1, Pz/2+1)
+  uint32_t mag_Px, mag_Py, mag_ny, mag_RY;
+};
+
+__global__ void __launch_bounds__(256) k_slab_xfwd(const float2* __restrict__ sigma,
+                                                   float2* __restrict__ ws,
+                                                   const float2* __restrict__ twx, SlabArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* tx = reinterpret_cast<float2*>(smem_raw);
+  const int pitch = sw_len(a.Px);
+  float2* A = tx + a.Px;
+  float2* B = A + kSlabRY * pitch;
+  const int y0 = blockIdx.x * kSlabRY, z = blockIdx.y, c = blockIdx.z;
+  const int nr = min(kSlabRY, a.ny - y0);
+  for (int i = threadIdx.x; i < a.Px; i += blockDim.x) tx[i] = twx[i];
+  const float2* src = sigma + c * a.ng + ((int64_t)z * a.ny + y0) * a.nx;
+  for (int i = threadIdx.x; i < kSlabRY * a.Px; i += blockDim.x) {
+    const int r = udiv(i, a.mag_Px), x = i - r * a.Px;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nr && x < a.nx) v = src[(int64_t)r * a.nx + x];
+    A[r * pitch + sw(x)] = v;
+  }
+  __syncthreads();
+  const Lines rows{kSlabRY, pitch, 1, 0, false};
+  const float2* res = fft_smem_slab<float2, false>(A, B, tx, a.px, rows, false);
+  float2* dst = ws + c * a.P3;
+  for (int i = threadIdx.x; i < kSlabRY * a.Px; i += blockDim.x) {
+    const int kx = udiv(i, a.mag_RY), r = i - kx * kSlabRY;
+    if (r < nr) dst[((int64_t)kx * a.nz + z) * a.ny + y0 + r] = res[r * pitch + sw(kx)];
+  }
+}
+
+// M = Pz when the register DFT supports that length (natural order, dft_reg), else 0: direct
+// DFTs over the nz non-zero values
+template <int M>
+__global__ void __launch_bounds__(256) k_slab_yz(float2* __restrict__ ws,
+                                                 const float2* __restrict__ gs,
+                                                 const float2* __restrict__ twy,
+                                                 const float2* __restrict__ twz, SlabArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* ty = reinterpret_cast<float2*>(smem_raw);
+  float2* tz = ty + a.Py;
+  float2* G = tz + a.Pz;  // this kx's Ghat slab [fz][fy]
+  const int pitch = sw_len(a.Py);
+  float2* A = G + a.gz * a.gy;
+  float2* B = A + a.nz * pitch;
+  const int kx = blockIdx.x, c = blockIdx.y;
+  const int fx = min(kx, a.Px - kx);
+  for (int i = threadIdx.x; i < a.Py; i += blockDim.x) ty[i] = twy[i];
+  for (int i = threadIdx.x; i < a.Pz; i += blockDim.x) tz[i] = twz[i];
+  const float2* g = gs + (int64_t)fx * a.gz * a.gy;
+  for (int i = threadIdx.x; i < a.gz * a.gy; i += blockDim.x) G[i] = g[i];
+  float2* X = ws + c * a.P3 + (int64_t)kx * a.nz * a.ny;  // [z][y]
+  for (int i = threadIdx.x; i < a.nz * a.Py; i += blockDim.x) {
+    const int z = udiv(i, a.mag_Py), y = i - z * a.Py;
+    A[z * pitch + sw(y)] = y < a.ny ? X[(int64_t)z * a.ny + y] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const Lines L{a.nz, pitch, 1, 0, false};
+  float2* r = fft_smem_slab<float2, false>(A, B, ty, a.py, L, false);
+  for (int ky = threadIdx.x; ky < a.Py; ky += blockDim.x) {
+    const int fy = min(ky, a.Py - ky);
+    if constexpr (M > 0) {
+      float2 v[M];
+#pragma unroll
+      for (int z = 0; z < M; ++z)
+        v[z] = z < a.nz ? r[z * pitch + sw(ky)] : make_float2(0.f, 0.f);
+      dft_reg<float2, M>(v, tz, 1, false);
+#pragma unroll
+      for (int kz = 0; kz < M; ++kz) v[kz] = cmul(v[kz], G[min(kz, M - kz) * a.gy + fy]);
+      dft_reg<float2, M>(v, tz, 1, true);
+#pragma unroll
+      for (int z = 0; z < M; ++z)
+        if (z < a.nz) r[z * pitch + sw(ky)] = v[z];
+    } else {
+      float2 v[kSlabMaxNz], o[kSlabMaxNz];
+#pragma unroll
+      for (int z = 0; z < kSlabMaxNz; ++z) {
+        v[z] = z < a.nz ? r[z * pitch + sw(ky)] : make_float2(0.f, 0.f);
+        o[z] = make_float2(0.f, 0.f);
+      }
+      for (int kz = 0; kz < a.Pz; ++kz) {
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int z = 0; z < kSlabMaxNz; ++z)
+          if (z < a.nz) t = cadd(t, cmul(v[z], tz[(z * kz) % a.Pz]));
+        t = cmul(t, G[min(kz, a.Pz - kz) * a.gy + fy]);
+#pragma unroll
+        for (int z = 0; z < kSlabMaxNz; ++z)
+          if (z < a.nz) o[z] = cadd(o[z], cmul(t, cconj(tz[(z * kz) % a.Pz])));
+      }
+#pragma unroll
+      for (int z = 0; z < kSlabMaxNz; ++z)
+        if (z < a.nz) r[z * pitch + sw(ky)] = o[z];
+    }
+  }
+  __syncthreads();
+  float2* o2 = (r == A) ? B : A;
+  r = fft_smem_slab<float2, false>(r, o2, ty, a.py, L, true);
+  for (int i = threadIdx.x; i < a.nz * a.ny; i += blockDim.x) {
+    const int z = udiv(i, a.mag_ny), y = i - z * a.ny;
+    X[(int64_t)z * a.ny + y] = r[z * pitch + sw(y)];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_slab_xinv(const float2* __restrict__ ws,
+                                                   float2* __restrict__ phi,
+                                                   const float2* __restrict__ twx, SlabArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* tx = reinterpret_cast<float2*>(smem_raw);
+  const int pitch = sw_len(a.Px);
+  float2* A = tx + a.Px;
+  float2* B = A + kSlabRY * pitch;
+  const int y0 = blockIdx.x * kSlabRY, z = blockIdx.y, c = blockIdx.z;
+  const int nr = min(kSlabRY, a.ny - y0);
+  for (int i = threadIdx.x; i < a.Px; i += blockDim.x) tx[i] = twx[i];
+  const float2* src = ws + c * a.P3;
+  for (int i = threadIdx.x; i < kSlabRY * a.Px; i += blockDim.x) {
+    const int kx = udiv(i, a.mag_RY), r = i - kx * kSlabRY;
+    A[r * pitch + sw(kx)] = r < nr ? src[((int64_t)kx * a.nz + z) * a.ny + y0 + r]
+                                   : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const Lines rows{kSlabRY, pitch, 1, 0, false};
+  const float2* res = fft_smem_slab<float2, false>(A, B, tx, a.px, rows, true);
+  float2* dst = phi + c * a.ng + ((int64_t)z * a.ny + y0) * a.nx;
+  for (int i = threadIdx.x; i < kSlabRY * a.nx; i += blockDim.x) {
+    const int r = i / a.nx, x = i - r * a.nx;
+    if (r < nr) dst[(int64_t)r * a.nx + x] = res[r * pitch + sw(x)];
+  }
+}
+
+// Warp-line forms of the three slab passes, for planes whose x and y lengths are 32 M points
+// (M = 16 or 32): one warp holds one line, point n = lane + 32 n1 in register n1, and
+// transforms it in registers (the M-point DFTs, the twiddles W_P^(lane k1) read from the table,
+// five xor-shuffle stages across the lanes), leaving X[k1 + M bitrev(lane)] in register k1; the
+// inverse takes that order back. No Stockham passes through shared memory: the x passes keep
+// every value in registers, the y-z pass meets the nz lines of one kx in one shared buffer for
+// the z transforms.
+template <int M>
+__device__ __forceinline__ void wline_fwd(float2* v, const float2* __restrict__ tw, int lane) {
+  constexpr int P = 32 * M;
+  dft_reg<float2, M>(v, tw, P / M, false);
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[lane * k1]));
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int sp = 32 >> (st + 1);
+    const bool top = (lane & sp) == 0;
+    const float sg = top ? 1.f : -1.f;
+    const float2 we = top ? make_float2(1.f, 0.f) : __ldg(&tw[(lane & (sp - 1)) * (M << st)]);
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const float2 p = shfl_x(v[k1], sp);
+      v[k1] = cmul(make_float2(sg * v[k1].x + p.x, sg * v[k1].y + p.y), we);
+    }
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void wline_inv(float2* v, const float2* __restrict__ tw, int lane) {
+  constexpr int P = 32 * M;
+#pragma unroll
+  for (int st = 4; st >= 0; --st) {
+    const int sp = 32 >> (st + 1);
+    const bool top = (lane & sp) == 0;
+    const float sg = top ? 1.f : -1.f;
+    float2 we = make_float2(1.f, 0.f);
+    if (!top) {
+      we = __ldg(&tw[(lane & (sp - 1)) * (M << st)]);
+      we.y = -we.y;
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const float2 own = cmul(v[k1], we);
+      const float2 p = shfl_x(own, sp);
+      v[k1] = make_float2(sg * own.x + p.x, sg * own.y + p.y);
+    }
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < M; ++k1) {
+    float2 w = __ldg(&tw[lane * k1]);
+    w.y = -w.y;
+    v[k1] = cmul(v[k1], w);
+  }
+  dft_reg<float2, M>(v, tw, P / M, true);
+}
+
+// x forward: warp w takes row y0 + w of data plane z; its Px spectrum values go to
+// X[c][kx][z][y] straight from the registers
+template <int M>
+__global__ void __launch_bounds__(256) k_wslab_xfwd(const float2* __restrict__ sigma,
+                                                    float2* __restrict__ ws,
+                                                    const float2* __restrict__ twx, SlabArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = blockIdx.x * 8 + warp, z = blockIdx.y, c = blockIdx.z;
+  if (y >= a.ny) return;  // warp-uniform
+  const float2* src = sigma + c * a.ng + ((int64_t)z * a.ny + y) * a.nx;
+  float2 v[M];
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    const int x = lane + 32 * n1;
+    v[n1] = x < a.nx ? src[x] : make_float2(0.f, 0.f);
+  }
+  wline_fwd<M>(v, twx, lane);
+  float2* dst = ws + c * a.P3 + (int64_t)z * a.ny + y;
+  const int k2 = brev_l<32>(lane);
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) dst[(int64_t)(k1 + M * k2) * a.nz * a.ny] = v[k1];
+}
+
+// y-z fused for one kx: warp z transforms its y line, the nz lines meet in shared memory
+// (position k1 * 32 + lane) for the z DFTs and Ghat, then each warp inverts its line
+template <int M, int MZ>
+__global__ void __launch_bounds__(256) k_wslab_yz(float2* __restrict__ ws,
+                                                  const float2* __restrict__ gs,
+                                                  const float2* __restrict__ twy,
+                                                  const float2* __restrict__ twz, SlabArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* G = reinterpret_cast<float2*>(smem_raw);  // this kx's Ghat slab [fz][fy]
+  float2* S = G + a.gz * a.gy;                       // [z][32 M]
+  constexpr int P = 32 * M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kx = blockIdx.x, c = blockIdx.y;
+  const int fx = min(kx, a.Px - kx);
+  const float2* g = gs + (int64_t)fx * a.gz * a.gy;
+  for (int i = threadIdx.x; i < a.gz * a.gy; i += blockDim.x) G[i] = g[i];
+  float2* X = ws + c * a.P3 + (int64_t)kx * a.nz * a.ny;  // [z][y]
+  for (int z = warp; z < a.nz; z += 8) {
+    float2 v[M];
+#pragma unroll
+    for (int n1 = 0; n1 < M; ++n1) {
+      const int y = lane + 32 * n1;
+      v[n1] = y < a.ny ? X[(int64_t)z * a.ny + y] : make_float2(0.f, 0.f);
+    }
+    wline_fwd<M>(v, twy, lane);
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) S[z * P + k1 * 32 + lane] = v[k1];
+  }
+  __syncthreads();
+  for (int pos = threadIdx.x; pos < P; pos += blockDim.x) {
+    const int ky = (pos >> 5) + M * brev_l<32>(pos & 31);
+    const int fy = min(ky, P - ky);
+    float2 v[MZ];
+#pragma unroll
+    for (int z = 0; z < MZ; ++z) v[z] = z < a.nz ? S[z * P + pos] : make_float2(0.f, 0.f);
+    dft_reg<float2, MZ>(v, twz, 1, false);
+#pragma unroll
+    for (int kz = 0; kz < MZ; ++kz) v[kz] = cmul(v[kz], G[min(kz, MZ - kz) * a.gy + fy]);
+    dft_reg<float2, MZ>(v, twz, 1, true);
+#pragma unroll
+    for (int z = 0; z < MZ; ++z)
+      if (z < a.nz) S[z * P + pos] = v[z];
+  }
+  __syncthreads();
+  for (int z = warp; z < a.nz; z += 8) {
+    float2 v[M];
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) v[k1] = S[z * P + k1 * 32 + lane];
+    wline_inv<M>(v, twy, lane);
+#pragma unroll
+    for (int n1 = 0; n1 < M; ++n1) {
+      const int y = lane + 32 * n1;
+      if (y < a.ny) X[(int64_t)z * a.ny + y] = v[n1];
+    }
+  }
+}
+
+// x inverse: warp w gathers row y0 + w of plane z from X in the transform's order, inverts it
+// and writes the nx kept values
+template <int M>
+__global__ void __launch_bounds__(256) k_wslab_xinv(const float2* __restrict__ ws,
+                                                    float2* __restrict__ phi,
+                                                    const float2* __restrict__ twx, SlabArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = blockIdx.x * 8 + warp, z = blockIdx.y, c = blockIdx.z;
+  if (y >= a.ny) return;  // warp-uniform
+  const float2* src = ws + c * a.P3 + (int64_t)z * a.ny + y;
+  const int k2 = brev_l<32>(lane);
+  float2 v[M];
+#pragma unroll
+  for (int k1 = 0; k1 < M; ++k1) v[k1] = src[(int64_t)(k1 + M * k2) * a.nz * a.ny];
+  wline_inv<M>(v, twx, lane);
+  float2* dst = phi + c * a.ng + ((int64_t)z * a.ny + y) * a.nx;
+#pragma unroll
+  for (int n1 = 0; n1 < M; ++n1) {
+    const int x = lane + 32 * n1;
+    if (x < a.nx) dst[x] = v[n1];
+  }
+}
+
+// Ghat octant [fz][fy][fx] -> [fx][fz][fy] for the y-z pass (one contiguous slab per kx)
+__global__ void k_ghat_slab(const float2* __restrict__ oct, int gx, int gy, int gz, float2* gs) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)gx * gy * gz) return;
+  const int fy = (int)(i % gy);
+  const int64_t t = i / gy;
+  const int fz = (int)(t % gz), fx = (int)(t / gz);
+  gs[i] = oct[((int64_t)fz * gy + fy) * gx + fx];
+}
+
+static size_t slab_x_smem(int Px) { return ((size_t)Px + 2 * (size_t)kSlabRY * sw_len(Px)) * sizeof(float2); }
+static size_t slab_yz_smem(int Py, int nz, int Pz) {
+  return ((size_t)Py + Pz + (size_t)(Pz / 2 + 1) * (Py / 2 + 1) + 2 * (size_t)nz * sw_len(Py)) *
+         sizeof(float2);
+}
+
+typedef void (*SlabYZ)(float2*, const float2*, const float2*, const float2*, SlabArgs);
+static SlabYZ slab_yz_kernel(int Pz) {
+  switch (Pz) {
+    case 8: return k_slab_yz<8>;
+    case 9: return k_slab_yz<9>;
+    case 10: return k_slab_yz<10>;
+    case 12: return k_slab_yz<12>;
+    case 15: return k_slab_yz<15>;
+    case 16: return k_slab_yz<16>;
+    default: return k_slab_yz<0>;
+  }
+}
+
+// the FP32 convolution takes the slab passes when a padded plane does not fit shared memory
+bool slab_path(const aim_ctx* c) {
+  const int Px = c->gp[0], Py = c->gp[1], Pz = c->gp[2], nz = c->gn[2];
+  return plane_smem<float2>(Px, Py) > kSmemBudget && nz <= kSlabMaxNz &&
+         slab_x_smem(Px) <= kSmemBudget && slab_yz_smem(Py, nz, Pz) <= kSmemBudget;
+}
+
+static int slab_conv(aim_ctx* c, PrecBuf<float>& b, const float2* sigma, float2* phi, int ncomp,
+                     float2* ws, cudaStream_t s) {
+  SlabArgs a;
+  a.nx = c->gn[0]; a.ny = c->gn[1]; a.nz = c->gn[2];
+  a.Px = c->gp[0]; a.Py = c->gp[1]; a.Pz = c->gp[2];
+  a.ng = c->ng; a.P3 = (int64_t)a.Px * a.Py * a.Pz;
+  if (!make_fft_plan_r32(a.Px, &a.px) || !make_fft_plan_r32(a.Py, &a.py)) {
+    set_error("slab convolution: no FFT plan for %d x %d", a.Px, a.Py);
+    return BEM_EINVAL;
+  }
+  a.gy = a.Py / 2 + 1; a.gz = a.Pz / 2 + 1;
+  a.mag_Px = div_magic(a.Px); a.mag_Py = div_magic(a.Py); a.mag_ny = div_magic(a.ny);
+  a.mag_RY = div_magic(kSlabRY);
+  // the warp-line forms: both in-plane lengths 1024 (or 512) and a z length the register DFT
+  // takes
+  if (a.Px == a.Py && (a.Px == 1024 || a.Px == 512) && a.nz <= 8 && a.Pz == 15) {
+    const dim3 gw((a.ny + 7) / 8, a.nz, ncomp);
+    const size_t ssm = ((size_t)a.gz * a.gy + (size_t)a.nz * a.Py) * sizeof(float2);
+    if (a.Px == 1024) {
+      k_wslab_xfwd<32><<<gw, 256, 0, s>>>(sigma, ws, b.tw[0], a);
+      k_wslab_yz<32, 15><<<dim3(a.Px, ncomp), 256, ssm, s>>>(ws, b.Gs, b.tw[1], b.tw[2], a);
+      k_wslab_xinv<32><<<gw, 256, 0, s>>>(ws, phi, b.tw[0], a);
+    } else {
+      k_wslab_xfwd<16><<<gw, 256, 0, s>>>(sigma, ws, b.tw[0], a);
+      k_wslab_yz<16, 15><<<dim3(a.Px, ncomp), 256, ssm, s>>>(ws, b.Gs, b.tw[1], b.tw[2], a);
+      k_wslab_xinv<16><<<gw, 256, 0, s>>>(ws, phi, b.tw[0], a);
+    }
+    BEM_CUDA(cudaGetLastError());
+    return BEM_OK;
+  }
+  const dim3 gx((a.ny + kSlabRY - 1) / kSlabRY, a.nz, ncomp);
+  k_slab_xfwd<<<gx, 256, slab_x_smem(a.Px), s>>>(sigma, ws, b.tw[0], a);
+  slab_yz_kernel(a.Pz)<<<dim3(a.Px, ncomp), 256, slab_yz_smem(a.Py, a.nz, a.Pz), s>>>(
+      ws, b.Gs, b.tw[1], b.tw[2], a);
+  k_slab_xinv<<<gx, 256, slab_x_smem(a.Px), s>>>(ws, phi, b.tw[0], a);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
 int fft_init_attrs() {
   const int lim = (int)kSmemBudget;
   BEM_CUDA(cudaFuncSetAttribute(k_lines<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -844,6 +1284,12 @@ int fft_init_attrs() {
   BEM_CUDA(cudaFuncSetAttribute(k_plane_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   BEM_CUDA(cudaFuncSetAttribute(k_zfused<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   BEM_CUDA(cudaFuncSetAttribute(k_zfused<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_slab_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  for (int pz : {8, 9, 10, 12, 15, 16, 0})
+    BEM_CUDA(cudaFuncSetAttribute(slab_yz_kernel(pz), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_wslab_yz<32, 15>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_wslab_yz<16, 15>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_slab_xinv, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return BEM_OK;
 }
 
@@ -916,6 +1362,9 @@ int fft_conv(aim_ctx* c, PrecBuf<R>& b, const typename C2<R>::T* sigma, typename
     if (!inv_done) k_plane_inv<V><<<dim3(nz, ncomp), 512, psm, s>>>(ws, phi, b.tw[0], b.tw[1], a);
     BEM_CUDA(cudaGetLastError());
     return BEM_OK;
+  }
+  if constexpr (sizeof(V) == sizeof(float2)) {
+    if (b.Gs) return slab_conv(c, b, sigma, phi, ncomp, ws, s);
   }
   LinePass p{};
   // X forward
@@ -1029,6 +1478,7 @@ int make_ghat(aim_ctx* c) {
   if (rc == BEM_OK) rc = dalloc_t(c, &c->f32.Ghat, no);
   int zl = 0, zm = 0;
   if (rc == BEM_OK && reg_shape(Pz, &zl, &zm)) rc = dalloc_t(c, &c->f32.Gz, P3);
+  if (rc == BEM_OK && slab_path(c)) rc = dalloc_t(c, &c->f32.Gs, no);
   if (rc == BEM_OK) {
     k_ghat_oct<<<(unsigned)((no + 255) / 256), 256>>>(G, Px, Py, Pz, 1.0 / (double)P3, c->f64.Ghat,
                                                       c->f32.Ghat);
@@ -1038,6 +1488,9 @@ int make_ghat(aim_ctx* c) {
       else if (zl == 16) k_ghat_lines<float2, 16><<<nb, 256>>>(c->f32.Ghat, zm, Px, Py, Pz, c->f32.Gz);
       else k_ghat_lines<float2, 8><<<nb, 256>>>(c->f32.Ghat, zm, Px, Py, Pz, c->f32.Gz);
     }
+    if (c->f32.Gs)
+      k_ghat_slab<<<(unsigned)((no + 255) / 256), 256>>>(c->f32.Ghat, Px / 2 + 1, Py / 2 + 1,
+                                                          Pz / 2 + 1, c->f32.Gs);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       set_error("make_ghat: %s", cudaGetErrorString(e));

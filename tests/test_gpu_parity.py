@@ -141,6 +141,38 @@ def test_grid_convolution(prob, prec, tol):
     assert rel(got, ref) < tol
 
 
+@pytest.mark.parametrize("shape", [(400, 300, 4), (400, 300, 8), (256, 256, 8), (512, 512, 8)])
+@pytest.mark.parametrize("ncomp", [1, 4])
+def test_grid_convolution_large_planes(dev, ncomp, shape):
+    """Grids whose padded x-y plane does not fit shared memory: the FP32 convolution takes the
+    three slab passes (x rows, fused y-z slab per kx with the z DFT in registers, inverse x
+    rows): through shared-memory transforms (radix-32 stages along x) for 800 x 600 planes, as
+    warp-held lines in registers for 512 x 512 and 1024 x 1024 planes (padded z length 15; the
+    split-ring array's grid is 512 x 512 x 8); FP64 takes the batched line passes; both against
+    numpy.fft (pinned to direct summation)."""
+    nx, ny, nz = shape
+    h = 0.5
+    lo = np.zeros(3)
+    hi = np.array([(nx - 3) * h, (ny - 3) * h, 0.5])
+    parts = [synth.box(tuple(lo), (0.5, 0.5, 0.5), (1, 1, 1)),
+             synth.box(tuple(hi - 0.5), (0.5, 0.5, 0.5), (1, 1, 1))]
+    mesh = synth.merge(parts, [synth.SIGMA_CU] * 2)
+    grid = synth.Grid(np.array([-h, -h, -h]) + h / 12, np.array([h, h, h]),
+                      np.array([nx, ny, nz]))
+    ctx = api.Context(mesh, grid, 10e9)
+    assert tuple(ctx.grid_n) == (nx, ny, nz) and ctx.padded[0] >= 2 * nx - 1
+    rw = from_mesh(mesh)
+    A = oaim.Aim(rw, grid.origin, grid.h, grid.n, op.k0_of(10e9))
+    s = np.stack([synth.rand_cvec(ctx.ng, 70 + c) for c in range(ncomp)])
+    ref = np.stack([A.conv(s[c]) for c in range(ncomp)])
+    for prec, tol in ((api.BEM_C32, 2e-6), (api.BEM_C64, 1e-12)):
+        sd = torch.from_numpy(s.ravel()).to(api.cdtype(prec)).cuda()
+        got = ctx.conv(sd, ncomp=ncomp, prec=prec).cpu().numpy().reshape(ncomp, -1)
+        assert rel(got, ref) < tol
+        assert max_rel(got, ref) < 10 * tol
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-11)])
 def test_matvec_LA_LPhi(prob, prec, tol):
     ctx, A, rw = prob["ctx"], prob["aim"], prob["rw"]
