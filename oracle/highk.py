@@ -186,30 +186,50 @@ def inner(r, tri, nrm, diam, k):
     return S0, S1, V
 
 
+def _sub3(a, b):
+    return (a[0] - b[0], a[1] - b[1], a[2] - b[2])
+
+
+def _dot3(a, b):
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+
+
+def _cross3(a, b):
+    return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])
+
+
 def _seg_dist(c, p, q):
-    v = q - p
-    t = np.clip(np.dot(c - p, v) / np.dot(v, v), 0.0, 1.0)
-    return float(np.linalg.norm(c - (p + t * v)))
+    v = _sub3(q, p)
+    t = min(max(_dot3(_sub3(c, p), v) / _dot3(v, v), 0.0), 1.0)
+    e = (c[0] - (p[0] + t * v[0]), c[1] - (p[1] + t * v[1]), c[2] - (p[2] + t * v[2]))
+    return math.sqrt(_dot3(e, e))
 
 
 def _tri_dist(c, tri, nrm):
-    d = float(np.dot(c - tri[0], nrm))
-    rho = c - d * nrm
+    """Distance from the point c to the filled triangle tri (unit normal nrm)."""
+    c = tuple(float(v) for v in c)
+    tri = [tuple(float(v) for v in row) for row in tri]
+    nrm = tuple(float(v) for v in nrm)
+    d = _dot3(_sub3(c, tri[0]), nrm)
+    rho = (c[0] - d * nrm[0], c[1] - d * nrm[1], c[2] - d * nrm[2])
     inside = True
     for i in range(3):
         pa, pb = tri[i], tri[(i + 1) % 3]
-        if np.dot(np.cross(pb - pa, rho - pa), nrm) < 0:
+        if _dot3(_cross3(_sub3(pb, pa), _sub3(rho, pa)), nrm) < 0:
             inside = False
     if inside:
         return abs(d)
     return min(_seg_dist(c, tri[i], tri[(i + 1) % 3]) for i in range(3))
 
 
+def _mid(a, b):
+    return (0.5 * (a[0] + b[0]), 0.5 * (a[1] + b[1]), 0.5 * (a[2] + b[2]))
+
+
 def _sub4(t):
     v0, v1, v2 = t
-    m01, m12, m20 = 0.5 * (v0 + v1), 0.5 * (v1 + v2), 0.5 * (v2 + v0)
-    return [np.array([v0, m01, m20]), np.array([m01, v1, m12]), np.array([m20, m12, v2]),
-            np.array([m01, m12, m20])]
+    m01, m12, m20 = _mid(v0, v1), _mid(v1, v2), _mid(v2, v0)
+    return [(v0, m01, m20), (m01, v1, m12), (m20, m12, v2), (m01, m12, m20)]
 
 
 def coplanar(T, S, nS, diamS):
@@ -238,32 +258,37 @@ def leaves(T, S, nS, diamS, k):
     D = depth_of(k, diamT)
     cop = coplanar(T, S, nS, diamS)
     bary, wr = radon7()
-    pts, wts = [], []
+    Sl = [tuple(float(v) for v in row) for row in S]
+    nSl = tuple(float(v) for v in nS)
+    kim = abs(complex(k).imag)
+    out = []
 
     def dist(c):
         if cop:
-            return min(_seg_dist(c, S[i], S[(i + 1) % 3]) for i in range(3))
-        return _tri_dist(c, S, nS)
-
-    kim = abs(complex(k).imag)
+            return min(_seg_dist(c, Sl[i], Sl[(i + 1) % 3]) for i in range(3))
+        return _tri_dist(c, Sl, nSl)
 
     def rec(t, lev):
-        c = t.mean(axis=0)
+        c = ((t[0][0] + t[1][0] + t[2][0]) / 3.0, (t[0][1] + t[1][1] + t[2][1]) / 3.0,
+             (t[0][2] + t[1][2] + t[2][2]) / 3.0)
         if lev < D:
-            rad = max(np.linalg.norm(t[j] - c) for j in range(3))
-            dm = max(np.linalg.norm(t[1] - t[0]), np.linalg.norm(t[2] - t[1]),
-                     np.linalg.norm(t[0] - t[2]))
+            rad = max(math.sqrt(_dot3(_sub3(t[j], c), _sub3(t[j], c))) for j in range(3))
+            dm = max(math.sqrt(_dot3(_sub3(t[1], t[0]), _sub3(t[1], t[0]))),
+                     math.sqrt(_dot3(_sub3(t[2], t[1]), _sub3(t[2], t[1]))),
+                     math.sqrt(_dot3(_sub3(t[0], t[2]), _sub3(t[0], t[2]))))
             dc = dist(c)
             if dc < rad + SPLIT_MARGIN * dm and (kim == 0.0 or kim * (dc - rad) < SPLIT_DECAY):
                 for ch in _sub4(t):
                     rec(ch, lev + 1)
                 return
-        area = 0.5 * np.linalg.norm(np.cross(t[1] - t[0], t[2] - t[0]))
-        pts.append(bary @ t)
-        wts.append(wr * area)
+        out.append(t)
 
-    rec(np.asarray(T, dtype=np.float64), 0)
-    return np.concatenate(pts), np.concatenate(wts)
+    rec(tuple(tuple(float(v) for v in row) for row in T), 0)
+    L = np.array(out, dtype=np.float64)                       # [nleaf, 3, 3]
+    area = 0.5 * np.linalg.norm(np.cross(L[:, 1] - L[:, 0], L[:, 2] - L[:, 0]), axis=1)
+    pts = np.einsum("qk,lkd->lqd", bary, L).reshape(-1, 3)
+    wts = (wr[None, :] * area[:, None]).ravel()
+    return pts, wts
 
 
 def pair_moments(T, S, nS, diamS, k, want_K=True):

@@ -166,7 +166,9 @@ def rwg_entries(rw: RWG, k, M, N, kind):
     kind "A": int int f_m . f_n G
          "L": int int G [f_m . f_n - k^-2 div f_m div f_n]
          "K": int f_m . PV int grad G x f_n
+    A tuple of kinds returns a tuple of entry arrays from one pass over the triangle pairs.
     """
+    kinds = (kind,) if isinstance(kind, str) else tuple(kind)
     M = np.asarray(M, dtype=np.int64)
     N = np.asarray(N, dtype=np.int64)
     nt = rw.nt
@@ -175,9 +177,8 @@ def rwg_entries(rw: RWG, k, M, N, kind):
     ss = np.stack([rw.et[N, 0], rw.et[N, 1], rw.et[N, 0], rw.et[N, 1]], axis=1)
     key = (tt * nt + ss).ravel()
     ukey, inv = np.unique(key, return_inverse=True)
-    mom = tri_pair_moments(rw, k, ukey // nt, ukey % nt, want_K=(kind == "K"))
+    mom = tri_pair_moments(rw, k, ukey // nt, ukey % nt, want_K=("K" in kinds))
     inv = inv.reshape(-1, 4)
-    out = np.zeros(M.size, dtype=np.complex128)
     MM = np.repeat(M, 4)
     NN = np.repeat(N, 4)
     t = tt.ravel()
@@ -186,31 +187,39 @@ def rwg_entries(rw: RWG, k, M, N, kind):
     sn, vb = _half_rwg(rw, NN, s)
     cf = sm * sn * rw.elen[MM] * rw.elen[NN] / (4.0 * rw.area[t] * rw.area[s])
     ii = inv.ravel()
-    if kind in ("A", "L"):
-        M0 = mom["M0"][ii]
-        val = mom["M2"][ii] - np.einsum("id,id->i", mom["M1"][ii], vb) \
-            - np.einsum("id,id->i", va, mom["M1p"][ii]) + np.einsum("id,id->i", va, vb) * M0
-        val = cf * val
-        if kind == "L":
-            dv = sm * sn * rw.elen[MM] * rw.elen[NN] / (rw.area[t] * rw.area[s])
-            val = val - dv * M0 / (k * k)
-    elif kind == "K":
-        U = mom["U"][ii]
-        Vs = mom["Vs"][ii]
-        val = cf * (np.einsum("id,id->i", U, vb) - np.einsum("id,id->i", U, va)
-                    + np.einsum("id,id->i", Vs, np.cross(vb, va)))
-    else:
-        raise ValueError(kind)
-    np.add.at(out, np.repeat(np.arange(M.size), 4), val)
-    return out
+    res = []
+    for kd in kinds:
+        out = np.zeros(M.size, dtype=np.complex128)
+        if kd in ("A", "L"):
+            M0 = mom["M0"][ii]
+            val = mom["M2"][ii] - np.einsum("id,id->i", mom["M1"][ii], vb) \
+                - np.einsum("id,id->i", va, mom["M1p"][ii]) + np.einsum("id,id->i", va, vb) * M0
+            val = cf * val
+            if kd == "L":
+                dv = sm * sn * rw.elen[MM] * rw.elen[NN] / (rw.area[t] * rw.area[s])
+                val = val - dv * M0 / (k * k)
+        elif kd == "K":
+            U = mom["U"][ii]
+            Vs = mom["Vs"][ii]
+            val = cf * (np.einsum("id,id->i", U, vb) - np.einsum("id,id->i", U, va)
+                        + np.einsum("id,id->i", Vs, np.cross(vb, va)))
+        else:
+            raise ValueError(kd)
+        np.add.at(out, np.repeat(np.arange(M.size), 4), val)
+        res.append(out)
+    return res[0] if isinstance(kind, str) else tuple(res)
 
 
 def dense_rwg(rw: RWG, k, kind, e0=0, e1=None):
-    """Dense RWG Galerkin matrix over the edge range [e0, e1)."""
+    """Dense RWG Galerkin matrix over the edge range [e0, e1) (a tuple of kinds gives a tuple
+    of matrices from one pass over the triangle pairs)."""
     e1 = rw.ne if e1 is None else e1
     idx = np.arange(e0, e1)
     Mi, Ni = np.meshgrid(idx, idx, indexing="ij")
-    return rwg_entries(rw, k, Mi.ravel(), Ni.ravel(), kind).reshape(e1 - e0, e1 - e0)
+    out = rwg_entries(rw, k, Mi.ravel(), Ni.ravel(), kind)
+    if isinstance(kind, str):
+        return out.reshape(e1 - e0, e1 - e0)
+    return tuple(o.reshape(e1 - e0, e1 - e0) for o in out)
 
 
 def pulse_entries(rw: RWG, k, T, S):
@@ -318,11 +327,9 @@ def internal_blocks(rw: RWG, freq, sigma, ix=None, objects=None):
         ixi = ix[e0:e1, e0:e1].toarray()
         epsc = eps_rc(sigma[i], freq)
         ki = k_medium(k0, epsc)
-        Li = dense_rwg(rw, ki, "L", e0, e1)
-        Ki = dense_rwg(rw, ki, "K", e0, e1)
+        Li, Ki = dense_rwg(rw, ki, ("L", "K"), e0, e1)
         Zs.append(-np.linalg.solve(Li, Ki + 0.5 * ixi) / (1j * k0 * epsc))
-        Ll = dense_rwg(rw, k0, "L", e0, e1)
-        Kl = dense_rwg(rw, k0, "K", e0, e1)
+        Ll, Kl = dense_rwg(rw, k0, ("L", "K"), e0, e1)
         Ys.append(np.linalg.solve(Ll, Kl + 0.5 * ixi) / (1j * k0))
     return Zs, Ys
 

@@ -441,7 +441,8 @@ def test_gmres_solve(prob, direct, mode):
     """Device GMRES (plain FP64, and FP32 matvecs with FP64 restarts) reaches a true FP64
     residual of 1e-6. The discrete system has a cluster of small singular values (cond ~ 7e6 on
     this mesh, from the RWG-tested I_x), so at this residual the charge q and the radiated far
-    field are determined (checked to 1e-4 / 1e-3) while h and j are not."""
+    field are determined (both checked to 1e-4, the target for solve outputs) while h and j are
+    not (they are checked after a 1e-11 solve, test_gmres_tight_solve_currents)."""
     ctx = prob["ctx"]
     b = ctx.rhs_plane_wave(prec=api.BEM_C64)
     x, info = ctx.solve(b, tol=1e-6, restart=100, max_iter=3000, prec_mode=mode)
@@ -450,7 +451,7 @@ def test_gmres_solve(prob, direct, mode):
     ne = ctx.ne
     xo = direct[1]
     assert rel(xg[ne:], xo[ne:]) < 1e-4
-    assert rel(_far(prob, xg), _far(prob, xo)) < 1e-3
+    assert rel(_far(prob, xg), _far(prob, xo)) < 1e-4
 
 
 @pytest.mark.parametrize("mode", [api.BEM_C64, api.BEM_C32])
@@ -468,7 +469,7 @@ def test_gmres_block_preconditioned(prob, direct, mode):
     xg = x.cpu().numpy()
     ne = ctx.ne
     assert rel(xg[ne:], direct[1][ne:]) < 1e-4
-    assert rel(_far(prob, xg), _far(prob, direct[1])) < 1e-3
+    assert rel(_far(prob, xg), _far(prob, direct[1])) < 1e-4
 
 
 def test_precond_c32_matches_c64(prob):
@@ -549,7 +550,7 @@ def test_gmres_batch_matches_single(prob, direct, mode):
     """Batched FGMRES (bem_solve_batch, block-diagonal preconditioner): three plane waves of
     different polarisation and direction plus a zero right-hand side, solved in lockstep, each
     reaches a true FP64 residual of 1e-6; the charges and the far field agree with one-vector
-    solves of the same right-hand sides (1e-4, 1e-3) and, for the first, with the oracle's direct
+    solves of the same right-hand sides (1e-4 each) and, for the first, with the oracle's direct
     solution; the zero right-hand side gives x = 0."""
     ctx = prob["ctx"]
     waves = [((1.0, 0.0, 0.0), (0.0, 0.0, 1.0)), ((0.0, 1.0, 0.0), (0.0, 0.0, 1.0)),
@@ -568,7 +569,7 @@ def test_gmres_batch_matches_single(prob, direct, mode):
         assert info["status"] == api.BEM_OK
         x1 = x1.cpu().numpy()
         assert rel(xs[r][ne:], x1[ne:]) < 1e-4
-        assert rel(_far(prob, xs[r]), _far(prob, x1)) < 1e-3
+        assert rel(_far(prob, xs[r]), _far(prob, x1)) < 1e-4
     assert rel(xs[0][ne:], direct[1][ne:]) < 1e-4
     with pytest.raises(api.BemError):
         ctx.solve_batch(torch.cat([bs[0]] * 5), precond=1)

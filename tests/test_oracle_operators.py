@@ -70,6 +70,30 @@ def test_interior_plane_wave_Z(small):
     assert err < 0.12 and bad > 0.5
 
 
+def _p2_error(a):
+    """P2 error of Zhat for the 1 x 1 x 2 um copper box meshed with squares of side a, 10 GHz."""
+    rw = from_mesh(synth.bar_mesh(1.0, 1.0, 2.0, a))
+    freq = 10e9
+    k0 = op.k0_of(freq)
+    epsc = op.eps_rc(5.8e7, freq)
+    k = op.k_medium(k0, epsc)
+    ix = op.ix_matrix(rw).toarray()
+    ce, ch = _plane_wave_coeffs(rw, k, k0)
+    Z = -np.linalg.solve(op.dense_rwg(rw, k, "L"), op.dense_rwg(rw, k, "K") + 0.5 * ix) \
+        / (1j * k0 * epsc)
+    return np.linalg.norm(Z @ ch - ce) / np.linalg.norm(ce)
+
+
+def test_interior_plane_wave_Z_refinement():
+    """P2 under two mesh refinements (0.5, 0.25, 0.125 um squares): the error falls at first
+    order (11.4%, 5.5%, 2.8% measured) and is within 5% on the finest mesh. Its source is the
+    RWG projection of the exact fields and the first-order discretisation, not the integration
+    rules (their changes under refinement are far smaller, test_oracle_highk.py)."""
+    e = [_p2_error(a) for a in (0.5, 0.25, 0.125)]
+    assert e[1] < 0.6 * e[0] and e[2] < 0.6 * e[1]
+    assert e[2] < 0.05
+
+
 def test_interior_plane_wave_Y(small):
     """P2 for Y_eq (Eq. EFIEeqYeq), at a frequency where k0 h is moderate."""
     _, rw = small
