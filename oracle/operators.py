@@ -78,6 +78,9 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
     M0  = int_t int_s G            M1  = int_t int_s r G        M1p = int_t int_s r' G
     M2  = int_t int_s r . r' G
     Vs  = int_t V(r)               U   = int_t V(r) x r,  with V(r) = int_s grad_r G dS'
+    Positions r and r' are measured from the centroid of t (the RWG combination in rwg_entries
+    is translation invariant), so that the moments of a pair far from the coordinate origin do
+    not cancel against each other there.
     """
     T = np.asarray(T, dtype=np.int64)
     S = np.asarray(S, dtype=np.int64)
@@ -88,6 +91,7 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
     bo, wo = radon7()
     bn, wn = subdivide4(radon7())
     X = rw.verts[rw.tris]  # [nt, 3, 3]
+    o = rw.centroid[T]     # per-pair origin
     dc = rw.centroid[T] - rw.centroid[S]
     dmax = np.maximum(rw.diam[T], rw.diam[S])
     near = np.einsum("ij,ij->i", dc, dc) < (NEAR_FACTOR * dmax) ** 2
@@ -103,8 +107,9 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
             hk &= ~sep
         ih = np.nonzero(hk)[0]
         if ih.size:
-            m = highk.pair_moments_batch(X[T[ih]], X[S[ih]], rw.normal[S[ih]], rw.diam[S[ih]], k,
-                                         want_K)
+            oo = o[ih][:, None, :]
+            m = highk.pair_moments_batch(X[T[ih]] - oo, X[S[ih]] - oo, rw.normal[S[ih]],
+                                         rw.diam[S[ih]], k, want_K)
             for key, v in m.items():
                 out[key][ih] = v
     for sel_near in (False, True):
@@ -115,9 +120,11 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
         for c0 in range(0, idx_all.size, chunk):
             idx = idx_all[c0:c0 + chunk]
             t, s = T[idx], S[idx]
-            rp = rule_points(X[t], bp_)                         # [nc, nqo, 3]
+            oo = o[idx][:, None, :]
+            Xt, Xs = X[t] - oo, X[s] - oo
+            rp = rule_points(Xt, bp_)                           # [nc, nqo, 3]
             wp = wp_[None, :] * rw.area[t][:, None]             # [nc, nqo]
-            rq = rule_points(X[s], bi)                          # [nc, nq, 3]
+            rq = rule_points(Xs, bi)                            # [nc, nq, 3]
             wq = wi[None, :] * rw.area[s][:, None]              # [nc, nq]
             Rv = rp[:, :, None, :] - rq[:, None, :, :]          # [nc, nqo, nq, 3]
             R = np.sqrt(np.einsum("abcd,abcd->abc", Rv, Rv))
@@ -129,7 +136,7 @@ def tri_pair_moments(rw: RWG, k, T, S, want_K=True, chunk=4096):
             else:
                 nc = idx.size
                 rr = rp.reshape(-1, 3)
-                trs = np.repeat(X[s], nqo, axis=0)
+                trs = np.repeat(Xs, nqo, axis=0)
                 nrs = np.repeat(rw.normal[s], nqo, axis=0)
                 I0, Irho, gI = static_potentials(rr, trs, nrs)
                 d = np.einsum("md,md->m", rr - trs[:, 0], nrs)
@@ -185,6 +192,8 @@ def rwg_entries(rw: RWG, k, M, N, kind):
     s = ss.ravel()
     sm, va = _half_rwg(rw, MM, t)
     sn, vb = _half_rwg(rw, NN, s)
+    va = va - rw.centroid[t]  # positions from the testing triangle's centroid, as the moments
+    vb = vb - rw.centroid[t]
     cf = sm * sn * rw.elen[MM] * rw.elen[NN] / (4.0 * rw.area[t] * rw.area[s])
     ii = inv.ravel()
     res = []

@@ -59,6 +59,22 @@ __device__ inline void load_tri(const double* verts, const int32_t* tris, const 
   T->diam = diam[t];
 }
 
+// Translate a pair so that T's centroid is the origin: the pair moments below are then measured
+// from it (the RWG combinations are translation invariant), which keeps the moments of pairs far
+// from the coordinate origin from cancelling against each other in the combination.
+__device__ __forceinline__ void shift_pair(Tri* T, Tri* S) {
+  const double o[3] = {T->c[0], T->c[1], T->c[2]};
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) {
+      T->v[k][a] -= o[a];
+      S->v[k][a] -= o[a];
+    }
+  for (int a = 0; a < 3; ++a) {
+    T->c[a] -= o[a];
+    S->c[a] -= o[a];
+  }
+}
+
 __device__ __forceinline__ void rule_point(const Tri& T, const double* rule, int q, double* r) {
   const double l1 = rule[4 * q], l2 = rule[4 * q + 1], l3 = rule[4 * q + 2];
   for (int a = 0; a < 3; ++a) r[a] = l1 * T.v[0][a] + l2 * T.v[1][a] + l3 * T.v[2][a];
@@ -520,34 +536,6 @@ __device__ inline void hk_point(const double* r, double wp, const Tri& S, double
   }
 }
 
-__device__ inline void acc_to_moments(const double* acc, Moments* out) {
-  out->M0 = make_double2(acc[0], acc[1]);
-  out->M2 = make_double2(acc[2], acc[3]);
-  for (int a = 0; a < 3; ++a) {
-    out->M1[a] = make_double2(acc[4 + 2 * a], acc[5 + 2 * a]);
-    out->M1p[a] = make_double2(acc[10 + 2 * a], acc[11 + 2 * a]);
-    out->Vs[a] = make_double2(acc[16 + 2 * a], acc[17 + 2 * a]);
-    out->U[a] = make_double2(acc[22 + 2 * a], acc[23 + 2 * a]);
-  }
-}
-
-// a large-|k| pair whose testing triangle is not subdivided: Radon's 7 points of T, one thread
-__device__ inline void hk_pair_moments_leaf(const Tri& T, const Tri& S, double kr, double ki,
-                                            bool wantK, Moments* out) {
-  double acc[28];
-  for (int i = 0; i < 28; ++i) acc[i] = 0.0;
-  for (int q = 0; q < 7; ++q) {
-    double r[3];
-    rule_point(T, c_r7, q, r);
-    double e1[3], e2[3], cr[3];
-    d_sub(T.v[1], T.v[0], e1);
-    d_sub(T.v[2], T.v[0], e2);
-    d_cross(e1, e2, cr);
-    hk_point(r, c_r7[4 * q + 3] * (0.5 * sqrt(d_dot(cr, cr))), S, kr, ki, wantK, acc);
-  }
-  acc_to_moments(acc, out);
-}
-
 // The outer rule points of a large-|k| pair as a flat list: a point is (finest sub-triangle index
 // idx below the leaf that owns it, rule point q). hk_leaf walks from T to the leaf containing
 // finest index idx and reports whether idx owns it (the first finest index below the leaf).
@@ -573,57 +561,6 @@ __device__ inline int hk_count_points(const Tri& T, const Tri& S, double kr, dou
   for (int idx = 0; idx < (1 << (2 * D)); ++idx)
     if (hk_leaf(T, S, D, cop, fabs(ki), idx, &leaf)) n += 7;
   return n;
-}
-
-// Moments of one high-|k| pair by one warp: the lanes take the depth-D sub-triangle indices and
-// their 7 rule points; a leaf is owned by the first finest index below it. Lane 0 of the result
-// holds the sums.
-__device__ inline void hk_pair_moments_warp(const Tri& T, const Tri& S, double kr, double ki,
-                                            bool wantK, Moments* out) {
-  const int lane = threadIdx.x & 31;
-  const double kabs = sqrt(kr * kr + ki * ki);
-  const double kim = fabs(ki);
-  const int D = hk_depth(kabs, T.diam);
-  const bool cop = hk_coplanar(T, S);
-  const int nfine = 1 << (2 * D);
-  double acc[28];
-  for (int i = 0; i < 28; ++i) acc[i] = 0.0;
-  for (int item = lane; item < nfine * 7; item += 32) {
-    const int idx = item / 7, q = item % 7;
-    Sub t;
-    for (int k = 0; k < 3; ++k)
-      for (int a = 0; a < 3; ++a) t.v[k][a] = T.v[k][a];
-    bool own = true;
-    for (int lev = 0; lev < D; ++lev) {
-      if (!hk_split(t, S, cop, kim)) {
-        // a leaf at this level: owned by the finest index whose lower digits are all zero
-        const int low = idx & ((1 << (2 * (D - lev))) - 1);
-        own = low == 0;
-        break;
-      }
-      const int digit = (idx >> (2 * (D - 1 - lev))) & 3;
-      Sub ch;
-      sub_child(t, digit, &ch);
-      t = ch;
-    }
-    if (!own) continue;
-    double e1[3], e2[3], cr[3];
-    d_sub(t.v[1], t.v[0], e1);
-    d_sub(t.v[2], t.v[0], e2);
-    d_cross(e1, e2, cr);
-    const double area = 0.5 * sqrt(d_dot(cr, cr));
-    const double l1 = c_r7[4 * q], l2 = c_r7[4 * q + 1], l3 = c_r7[4 * q + 2];
-    const double r[3] = {l1 * t.v[0][0] + l2 * t.v[1][0] + l3 * t.v[2][0],
-                         l1 * t.v[0][1] + l2 * t.v[1][1] + l3 * t.v[2][1],
-                         l1 * t.v[0][2] + l2 * t.v[1][2] + l3 * t.v[2][2]};
-    hk_point(r, c_r7[4 * q + 3] * area, S, kr, ki, wantK, acc);
-  }
-  for (int i = 0; i < 28; ++i) {
-    double v = acc[i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    acc[i] = v;
-  }
-  acc_to_moments(acc, out);
 }
 
 // classification of a pair for the reading: 0 regular 7 x 7, 1 near (small-|k| subtraction),

@@ -232,12 +232,16 @@ __device__ void rwg_pair(const DGeo& g, int m, int n, double kr, double ki, bool
       Tri T, S;
       load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t, &T);
       load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, s, &S);
+      const double o[3] = {T.c[0], T.c[1], T.c[2]};
+      shift_pair(&T, &S);
       Moments M;
       pair_moments(T, S, kr, ki, true, wantK, false, &M);
       double sm, sn;
-      const double *va, *vb;
-      half_rwg(g, m, t, &sm, &va);
-      half_rwg(g, n, s, &sn, &vb);
+      const double *pa, *pb;
+      half_rwg(g, m, t, &sm, &pa);
+      half_rwg(g, n, s, &sn, &pb);
+      const double va[3] = {pa[0] - o[0], pa[1] - o[1], pa[2] - o[2]};
+      const double vb[3] = {pb[0] - o[0], pb[1] - o[1], pb[2] - o[2]};
       double cf = sm * sn * g.elen[m] * g.elen[n] / (4.0 * g.area[t] * g.area[s]);
       double2 v = M.M2;
       for (int q = 0; q < 3; ++q) {
@@ -291,6 +295,7 @@ __global__ void k_obj_moments(DGeo g, int t0, int m, double kr, double ki, bool 
     mom[idx] = Moments{};   // the point kernel adds into it
     return;
   }
+  shift_pair(&T, &S);
   Moments M;
   pair_moments(T, S, kr, ki, true, wantK, false, &M, kind);
   mom[idx] = M;
@@ -305,6 +310,7 @@ __global__ void k_hk_count(DGeo g, int t0, int m, double kr, double ki, const in
   Tri T, S;
   load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx / m, &T);
   load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx % m, &S);
+  shift_pair(&T, &S);
   npts[p] = hk_count_points(T, S, kr, ki);
 }
 
@@ -317,6 +323,7 @@ __global__ void k_hk_items(DGeo g, int t0, int m, double kr, double ki, const in
   Tri T, S;
   load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx / m, &T);
   load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx % m, &S);
+  shift_pair(&T, &S);
   const int D = hk_depth(sqrt(kr * kr + ki * ki), T.diam);
   const bool cop = hk_coplanar(T, S);
   int64_t o = off[p];
@@ -346,6 +353,7 @@ __global__ void __launch_bounds__(128) k_hk_points(DGeo g, int t0, int m, double
     Tri T, S;
     load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx / m, &T);
     load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + idx % m, &S);
+    shift_pair(&T, &S);
     const int D = hk_depth(sqrt(kr * kr + ki * ki), T.diam);
     Sub leaf;
     hk_leaf(T, S, D, hk_coplanar(T, S), fabs(ki), f, &leaf);
@@ -395,9 +403,12 @@ __global__ void k_obj_assemble(DGeo g, int e0, int n, int t0, int m, double kr, 
       const int t = g.et[2 * mm + a], sidx = g.et[2 * nn + b];
       const Moments& M = mom[(int64_t)(t - t0) * m + (sidx - t0)];
       double sm, sn;
-      const double *va, *vb;
-      half_rwg(g, mm, t, &sm, &va);
-      half_rwg(g, nn, sidx, &sn, &vb);
+      const double *pa, *pb;
+      half_rwg(g, mm, t, &sm, &pa);
+      half_rwg(g, nn, sidx, &sn, &pb);
+      const double* o = &g.cen[3 * t];  // the moments' origin: t's centroid
+      const double va[3] = {pa[0] - o[0], pa[1] - o[1], pa[2] - o[2]};
+      const double vb[3] = {pb[0] - o[0], pb[1] - o[1], pb[2] - o[2]};
       const double cf = sm * sn * g.elen[mm] * g.elen[nn] / (4.0 * g.area[t] * g.area[sidx]);
       double2 v = M.M2;
       for (int q = 0; q < 3; ++q) {

@@ -438,15 +438,16 @@ def _far(prob, x):
 
 @pytest.mark.parametrize("mode", [api.BEM_C64, api.BEM_C32])
 def test_gmres_solve(prob, direct, mode):
-    """Device GMRES (plain FP64, and FP32 matvecs with FP64 restarts) reaches a true FP64
-    residual of 1e-6. The discrete system has a cluster of small singular values (cond ~ 7e6 on
-    this mesh, from the RWG-tested I_x), so at this residual the charge q and the radiated far
-    field are determined (both checked to 1e-4, the target for solve outputs) while h and j are
-    not (they are checked after a 1e-11 solve, test_gmres_tight_solve_currents)."""
+    """Device GMRES (plain FP64, and FP32 matvecs with FP64 restarts) without a preconditioner
+    reaches a true FP64 residual of 1e-7. The discrete system has a cluster of small singular
+    values (cond ~ 7e6 on this mesh, from the RWG-tested I_x): at that residual the charge q and
+    the radiated far field are within 1e-4 of the oracle's direct solution (the target for solve
+    outputs; at 1e-6 the far field of this unpreconditioned solve is 3.5e-4 off), while h and j
+    need a 1e-11 solve (test_gmres_tight_solve_currents)."""
     ctx = prob["ctx"]
     b = ctx.rhs_plane_wave(prec=api.BEM_C64)
-    x, info = ctx.solve(b, tol=1e-6, restart=100, max_iter=3000, prec_mode=mode)
-    assert info["status"] == api.BEM_OK and info["resid_true"] <= 1e-6
+    x, info = ctx.solve(b, tol=1e-7, restart=100, max_iter=4000, prec_mode=mode)
+    assert info["status"] == api.BEM_OK and info["resid_true"] <= 1e-7
     xg = x.cpu().numpy()
     ne = ctx.ne
     xo = direct[1]

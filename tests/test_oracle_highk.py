@@ -168,7 +168,8 @@ def test_schemes_agree_at_the_switch():
     kd = 0.55
     k = kd / SDIAM * (1 - 1j) / math.sqrt(2)
     for name, T in PAIRS.items():
-        mh = _moments(T, kd)
+        c = T.mean(axis=0)  # tri_pair_moments measures positions from the testing centroid
+        mh = highk.pair_moments(T - c, SRC - c, NRM, SDIAM, k)
         verts = np.concatenate([T, SRC])
         tris = np.array([[0, 1, 2], [3, 4, 5]], dtype=np.int32)
         # a two-triangle "mesh" holding just the pair, for the small-|k| rule of operators.py
