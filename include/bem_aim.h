@@ -41,7 +41,7 @@ extern "C" {
 #define BEM_ESOLVER (-6)  /* singular internal matrix in the LU factorisation */
 
 enum { BEM_C32 = 0, BEM_C64 = 1 };
-enum { AIM_OP_LA = 0, AIM_OP_LPHI = 1, AIM_OP_SYSTEM = 2 };
+enum { AIM_OP_LA = 0, AIM_OP_LPHI = 1, AIM_OP_SYSTEM = 2, AIM_OP_EXT = 3 };
 
 typedef struct aim_ctx aim_ctx;
 
@@ -143,8 +143,11 @@ int aim_matvec_schedule(aim_ctx* ctx, int mode);
 /* y = A x for which = AIM_OP_LA (A = L^A by AIM, vectors of N_E), AIM_OP_LPHI (L^Phi, N_T)
  * or AIM_OP_SYSTEM (the SLIM system of Eq. AEFIEoutJ, vectors of N_E + N_T):
  *   e = Z h, h_eq = Y e, j = h - h_eq,
- *   y1 = j k0 L^A j + I_x e - (F D)^T L^Phi q,  y2 = F D j + j k0 q.
- * x and y must not alias. prec selects the arithmetic (BEM_C32 or BEM_C64). */
+ *   y1 = j k0 L^A j + I_x e - (F D)^T L^Phi q,  y2 = F D j + j k0 q;
+ * or AIM_OP_EXT (both external operators by AIM at once, vectors of N_E + N_T:
+ * y = [L^A j; L^Phi q] for x = [j; q], the two run concurrently as in the system matvec).
+ * x and y must not alias. prec selects the arithmetic (BEM_C32 or BEM_C64). BEM_EINVAL for an
+ * unknown operator. */
 int aim_matvec(aim_ctx* ctx, int which, const void* x, void* y, int prec, void* stream);
 
 /* The system matvec of aim_matvec (AIM_OP_SYSTEM) for nrhs (1..4) right-hand sides at once:

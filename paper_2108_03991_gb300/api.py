@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 BEM_C32, BEM_C64 = 0, 1
-AIM_OP_LA, AIM_OP_LPHI, AIM_OP_SYSTEM = 0, 1, 2
+AIM_OP_LA, AIM_OP_LPHI, AIM_OP_SYSTEM, AIM_OP_EXT = 0, 1, 2, 3
 BEM_OK, BEM_ENOCONV = 0, 1
 ERRORS = {-1: "BEM_EINVAL", -2: "BEM_EMESH", -3: "BEM_EGRID", -4: "BEM_ENOMEM",
           -5: "BEM_ECUDA", -6: "BEM_ESOLVER"}
@@ -327,7 +327,7 @@ class Context:
     # ---- products ----------------------------------------------------------------
     def matvec(self, x, y=None, which=AIM_OP_SYSTEM, prec=BEM_C32):
         import torch
-        n = {AIM_OP_LA: self.ne, AIM_OP_LPHI: self.nt, AIM_OP_SYSTEM: self.n}[which]
+        n = {AIM_OP_LA: self.ne, AIM_OP_LPHI: self.nt, AIM_OP_SYSTEM: self.n, AIM_OP_EXT: self.n}[which]
         if y is None:
             y = torch.empty(n, dtype=cdtype(prec), device=x.device)
         if x.numel() != n or y.numel() != n:
@@ -353,7 +353,7 @@ class Context:
         with the products (aim_matvec_host); pin x and y for asynchronous copies. Ordered on the
         current stream; synchronise it before reading y."""
         import torch
-        n = {AIM_OP_LA: self.ne, AIM_OP_LPHI: self.nt, AIM_OP_SYSTEM: self.n}[which]
+        n = {AIM_OP_LA: self.ne, AIM_OP_LPHI: self.nt, AIM_OP_SYSTEM: self.n, AIM_OP_EXT: self.n}[which]
         if x.device.type != "cpu" or x.dtype != cdtype(prec) or not x.is_contiguous():
             raise ValueError("x must be a contiguous CPU tensor of the precision's complex type")
         if x.numel() % n:

@@ -168,7 +168,7 @@ int aim_matvec_host(aim_ctx* c, int which, const void* x, void* y, int nvec, int
     return BEM_EINVAL;
   }
   const int64_t n = which == AIM_OP_LA ? c->ne : which == AIM_OP_LPHI ? c->nt
-                    : which == AIM_OP_SYSTEM ? (int64_t)c->ne + c->nt : -1;
+                    : (which == AIM_OP_SYSTEM || which == AIM_OP_EXT) ? (int64_t)c->ne + c->nt : -1;
   if (n < 0) {
     set_error("aim_matvec_host: unknown operator %d", which);
     return BEM_EINVAL;
@@ -258,6 +258,10 @@ int aim_matvec(aim_ctx* c, int which, const void* x, void* y, int prec, void* st
   BEM_TRY(check_prec(prec, "aim_matvec"));
   if (!x || !y || x == y) {
     set_error("aim_matvec: x and y must be distinct device pointers");
+    return BEM_EINVAL;
+  }
+  if (which < AIM_OP_LA || which > AIM_OP_EXT) {
+    set_error("aim_matvec: unknown operator %d", which);
     return BEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;

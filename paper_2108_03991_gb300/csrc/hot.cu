@@ -986,6 +986,24 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, s));
     k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x, nt,
                                           nx, ny, y);
+  } else if (which == AIM_OP_EXT) {
+    // both external operators of Eq. AEFIEoutJ, as the system matvec runs them: L^A j on the
+    // main stream, L^Phi q on the side stream, joined at the end
+    const V* q = x + ne;
+    V* sq = b.sigma + 3 * ng;
+    BEM_CUDA(cudaEventRecord(c->ev_fork, s));
+    BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    project_t<R>(c, b.WPT, q, sq, c->side);
+    BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
+    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
+                                                nt, nx, ny, y + ne);
+    BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    project_e<R>(c, b.WAT, x, b.sigma, s);
+    BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
+    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
+                                          x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
+                                          nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr, nullptr);
+    BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   } else if (which == AIM_OP_SYSTEM) {
     // With C = Y_eq Z formed at set-up (Eq. EFIEeqYZ), j = h - C h and e = Z h are
     // independent. The main stream runs j and its AIM chain (projection, convolution, rows);

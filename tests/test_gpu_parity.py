@@ -183,6 +183,12 @@ def test_matvec_LA_LPhi(prob, prec, tol):
     yp = ctx.matvec(torch.from_numpy(q).to(dt).cuda(), which=api.AIM_OP_LPHI, prec=prec).cpu().numpy()
     assert rel(ya, A.LA(j)) < tol
     assert rel(yp, A.LPhi(q)) < tol
+    # both external operators at once (the two branches run concurrently, as in the system
+    # matvec): y = [L^A j; L^Phi q]
+    yx = ctx.matvec(torch.from_numpy(np.concatenate([j, q])).to(dt).cuda(), which=api.AIM_OP_EXT,
+                    prec=prec).cpu().numpy()
+    assert rel(yx[:rw.ne], A.LA(j)) < tol and rel(yx[rw.ne:], A.LPhi(q)) < tol
+    assert rel(yx, np.concatenate([ya, yp])) < 1e-6
 
 
 def _system_input(ctx, case, seed):
