@@ -242,6 +242,40 @@ def ncu_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": "aim", "grid": list(ctx.grid_n), "fft": list(ctx.padded)}))
         return
+    if args.ncu_case == "aim_srr":
+        # the grid convolution (4 components) on the split-ring array's grid (--rings per side;
+        # 32: 512 x 512 x 8, padded 1024 x 1024 x 15), set up on two small gold boxes at opposite
+        # corners of the array (same grid, tiny set-up)
+        g = synth.srr_grid(args.rings)
+        top = 50.0 * args.rings
+        parts = [synth.box((1.0, 1.0, 0.0), (1.0, 1.0, 1.0), (2, 2, 2)),
+                 synth.box((top - 2.0, top - 2.0, 0.0), (1.0, 1.0, 1.0), (2, 2, 2))]
+        mesh = synth.merge(parts, [synth.SIGMA_AU] * 2)
+        ctx = api.Context(mesh, g, 1e12)
+        s = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.ng, c) for c in range(4)])
+                             .astype(np.complex64)).cuda()
+        phi = torch.empty_like(s)
+        for _ in range(args.steps):
+            ctx.conv(s, phi, ncomp=4, prec=api.BEM_C32)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "aim_srr", "grid": list(ctx.grid_n), "fft": list(ctx.padded)}))
+        return
+    if args.ncu_case == "srr":
+        mesh, grid, freq = synth.srr_array_config(2, args.rings)
+        ctx = api.Context(mesh, grid, freq)
+        x = torch.from_numpy(synth.rand_cvec(ctx.n, 1).astype(np.complex64)).cuda()
+        y = torch.empty_like(x)
+        for _ in range(3):
+            ctx.matvec(x, y)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("srr_steps")
+        for _ in range(args.steps):
+            ctx.matvec(x, y)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "srr", "rings": args.rings, "sparse_internal": ctx.sparse_internal,
+                          "nnz_near": [ctx.nnz_A, ctx.nnz_P]}))
+        return
     if args.ncu_case == "batch":
         mesh, grid, freq = synth.bar_array_config(0, 10e9)
         ctx = api.Context(mesh, grid, freq)
@@ -404,7 +438,7 @@ def bar_array_section(args, api, synth, torch, np, dev):
     b = ctx.rhs_plane_wave(prec=api.BEM_C64)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    ctx.precond(torch.zeros(ctx.n, dtype=torch.complex64, device=dev), prec=api.BEM_C32)
+    solve["precond_build"] = ctx.precond_setup(api.BEM_C32)
     torch.cuda.synchronize()
     solve["precond_setup_s"] = time.perf_counter() - t1
     # learned correction: trained on another seed of the same family (the benchmark
@@ -490,7 +524,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--bar-array", action="store_true",
                     help="add the 4x4 copper bar array's solves (learned correction, batches)")
-    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "internal", "batch"])
+    ap.add_argument("--ncu-case", default=None, choices=["gemv", "aim", "aim_srr", "internal", "batch", "srr"])
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--precision-study", action="store_true")
     ap.add_argument("--schedule", type=int, default=None,
@@ -569,9 +603,19 @@ def main():
         e = torch.empty(ctx.ne, dtype=torch.complex64, device=dev)
         heq = torch.empty_like(e)
         h = x[:ctx.ne].contiguous()
-        paired = ctx.matvec_mode == 3
-        gemv_ms = timed(lambda: ctx.internal(h, e, heq, prec=api.BEM_C32), args.steps) / \
-            (1 if paired else 2)
+        sparse = ctx.sparse_internal["on"]
+        paired = ctx.matvec_mode == 3 and not sparse
+        zsp_ms = None
+        if sparse:
+            # the matvec's internal part with the sparse internal operator: j = h - C h, the one
+            # dense block GEMV (the dominant kernel), and e = Z_s h beside it
+            gemv_ms = timed(lambda: ctx.internal(h, None, heq, prec=api.BEM_C32, want_e=False),
+                            args.steps)
+            zsp_ms = timed(lambda: ctx.internal(h, e, None, prec=api.BEM_C32, want_heq=False),
+                           args.steps)
+        else:
+            gemv_ms = timed(lambda: ctx.internal(h, e, heq, prec=api.BEM_C32), args.steps) / \
+                (1 if paired else 2)
         # the AIM external part alone (Sec. III-A: projection, FFT convolution, interpolation,
         # precorrected near region) for the RWG vector components (L^A) and the charges (L^Phi)
         ja = x[:ctx.ne].contiguous()
@@ -620,12 +664,13 @@ def main():
         # time to a true FP64 relative residual of 1e-6 for a plane wave at normal incidence
         # (E along x, the gap's axis; propagation along -z): plain = FP64 GMRES without a
         # preconditioner; chosen = FP32-bulk FGMRES (FP64 Arnoldi and true residual) with the
-        # block-diagonal preconditioner, its one-off set-up timed separately and counted
+        # block-diagonal preconditioner (inverses built in complex FP32, each block checked), its
+        # one-off set-up timed separately and counted
         solve = {"excitation": "plane wave, E along x, k along -z"}
         b = ctx.rhs_plane_wave((1.0, 0.0, 0.0), (0.0, 0.0, -1.0), prec=api.BEM_C64)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        ctx.precond(torch.zeros(ctx.n, dtype=torch.complex64, device=dev), prec=api.BEM_C32)
+        solve["precond_build"] = ctx.precond_setup(api.BEM_C32)
         torch.cuda.synchronize()
         solve["precond_setup_s"] = time.perf_counter() - t1
         for mode, pc in ((api.BEM_C64, 0), (api.BEM_C32, 1)):  # workspace and graphs
@@ -673,8 +718,23 @@ def main():
             cpu = oracle_baseline(seconds=15.0)
         value = replicas_value(ms, world)
         stream_init = 1 if ctx.gemv_kind == 3 else 0
-        launches_per_step = 11 + (1 if ctx.matvec_mode == 3 else
-                                  2 + stream_init * (2 if ctx.matvec_mode == 2 else 1))
+        if sparse:  # C's GEMV, the two kernels of e = Z_s h
+            launches_per_step = 11 + 1 + stream_init + 2
+        else:
+            launches_per_step = 11 + (1 if ctx.matvec_mode == 3 else
+                                      2 + stream_init * (2 if ctx.matvec_mode == 2 else 1))
+        zsp = None
+        if sparse:
+            sp = ctx.sparse_internal
+            # the operator's FP32 bytes (L and U column tables, inverse diagonal, CSR values and
+            # columns of K_s + I_x/2), h gathered, the permuted rows written and read, e written
+            zb = sp["bytes_c32"] + 4 * 8 * ctx.ne
+            zsp = {"kernels": "k_zsp_rows (rows of K_s + I_x/2) + k_zsp_solve (banded L_s^-1, "
+                              "one warp per ring)",
+                   "bytes": zb, "ms": zsp_ms, "achieved": zb / (zsp_ms * 1e-3) / 1e9,
+                   "unit": "GB/s", "frac": zb / (zsp_ms * 1e-3) / 1e9 / hbm,
+                   "half_bandwidth": sp["band"], "setup_check": sp["check"],
+                   "dense_Z_bytes": ZY}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -684,13 +744,17 @@ def main():
                        "unknowns": ctx.n, "ne": ctx.ne, "nt": ctx.nt,
                        "objects": ctx.nobj, "grid": list(ctx.grid_n), "fft": list(ctx.padded),
                        "nnz_near": [ctx.nnz_A, ctx.nnz_P], "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (Z, C %.1f GB)" % (ctx.zy_bytes_c32 / 1e9),
+                       "l2": "inputs larger than L2 (C %.1f GB, %s)" % (
+                           ZY / 1e9, "sparse Z_s %.1f GB" % (ctx.sparse_internal["bytes_c32"] / 1e9)
+                           if sparse else "Z %.1f GB" % (ZY / 1e9)),
+                       "internal": "sparse Z_s (Sec. III-A, high frequency)" if sparse else "dense Z",
                        "setup_s": setup_s, "setup_stage_s": ctx.setup_stage_s,
                        "reference_arm": "FP64 oracle on the host cores on the 8x8 sub-array, "
                                         "scaled by the ring count; its internal blocks and "
                                         "near-region values are seeded random numbers of the "
                                         "true sizes and sparsity"},
             "roofline": {"kernel": ("k_gemv_pair (C = Y_eq Z and Z in one launch)" if paired
+                                    else "block GEMV of C = Y_eq Z" if sparse
                                     else "k_gemv (block-diagonal Z / C)"), "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": src,
@@ -713,6 +777,7 @@ def main():
                              "frac": aim_ach / hbm, "peak_source": src,
                              "bytes_per_matvec": b_aim, "ms": aim_ms,
                              "ms_LA": aim_la_ms, "ms_LPhi": aim_lp_ms},
+            "sparse_internal": zsp,
             "e2e": {"value": replicas_value(e2e_ms, world), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * ctx.n, "d2h_bytes_per_step": 8 * ctx.n,
                     "call": f"aim_matvec_host: {args.steps} distinct pinned host vectors in one "

@@ -106,8 +106,30 @@ const char* bem_last_error(void);
  * (aim_matvec_schedule modes 0-3), [22..31]=wall time in microseconds of the set-up stages:
  * host geometry, projection stencils, internal integrals at k_i (all objects), internal
  * integrals at k0, LU solves, C = Y Z, near region, FFT of the grid kernel, GEMV autotuner,
- * matvec schedule tuner. Writes min(n, 32) entries. */
+ * matvec schedule tuner, [32]=wall time in microseconds of the last preconditioner build (0
+ * before one), [33]=its precision (BEM_C32 or BEM_C64), [34]=blocks it built in FP64,
+ * [35]=its largest FP32 block check (the forward-error estimate of bem_precond_setup) in units
+ * of 1e-12 (-1 if none ran), [36]=wall time in microseconds of the sparse internal operator's
+ * set-up (aim_internal_sparse), [37]=objects on that operator (0: none built), [38]=1 while it
+ * is in use, [39]=its largest half-bandwidth, [40]=its bytes per product in complex FP32,
+ * [41]=its set-up check |Z_s h - Z h| / |Z h| (largest over the objects) in units of 1e-15
+ * (-1: none). Writes min(n, 42) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
+
+/* Sparse internal operator at high frequency (Sec. III-A, third item of the internal problem:
+ * at small skin depth L_{k_i} and K_{k_i} are treated as sparse, physically distant
+ * interactions dropped, and L^{-1} applied by a sparse direct solve). aim_setup builds it when
+ * every object qualifies: a pair of RWG functions is kept when their supports come within
+ * 23 skin depths delta_i = -1/Im k_i (centroid distance less the triangles' centroid-to-vertex
+ * radii, nearest of the 2 x 2 triangle pairs); the kept pattern is ordered by reverse
+ * Cuthill-McKee and L_s factorised as a band without pivoting (FP64, then rounded for the FP32
+ * path); the band and the kept rows must be below half the dense Z's bytes, the half-bandwidth
+ * at most 256, and Z_s h must match the dense Z h to 1e-8 at set-up (FP64, one probe vector).
+ * Then e = Z_s h = -(1/(j k0 eps_rc)) L_s^{-1}(K_s + I_x/2) h replaces e = Z h in aim_matvec,
+ * internal_apply and bem_solve (C = Y_eq Z stays dense), and is on after aim_setup. on = 0
+ * selects the dense Z again, on = 1 the sparse form (BEM_EINVAL when none was built).
+ * Synchronises the device; captured matvec graphs are rebuilt on next use. */
+int aim_internal_sparse(aim_ctx* ctx, int on);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the
  * GPU counterpart of the paper's choice of schedule for the internal products, Sec. III-C):
@@ -171,9 +193,11 @@ int aim_matvec_host(aim_ctx* ctx, int which, const void* x, void* y, int nvec, i
                     void* stream);
 
 /* The internal problem (Sec. II-B, Eqs. MFIEinZin, EFIEeqYeq): e = Z h, h_eq = Y e, for
- * nrhs right-hand sides stored one after another (each N_E long). heq may be NULL. With one
- * right-hand side, both outputs and the paired matvec schedule (aim_matvec_schedule mode 3),
- * the two products are one launch, as in the system matvec. */
+ * nrhs right-hand sides stored one after another (each N_E long). Either output may be NULL
+ * (not both): h_eq alone is the one block GEMV of C = Y_eq Z. With one right-hand side, both
+ * outputs, the dense Z and the paired matvec schedule (aim_matvec_schedule mode 3), the two
+ * products are one launch, as in the system matvec; with the sparse internal operator
+ * (aim_internal_sparse) e = Z_s h. */
 int internal_apply(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, int prec,
                    void* stream);
 
@@ -290,9 +314,17 @@ typedef struct {
  * of Eq. AEFIEoutJ restricted to object i's unknowns [h_i; q_i] with the object's exact dense
  * L^A and L^Phi (the paper's own constraint preconditioner, from Qian 2009, is not given in the
  * paper; this is the fallback). The first call (or the first bem_solve with precond = 1) builds
- * the inverses: FP64 integrals, cuBLAS products and cuSOLVER LU, stored in FP64 and FP32.
+ * the inverses as bem_precond_setup(ctx, BEM_C32) does; they are stored in FP64 and FP32.
  * r, u: device vectors of N_E + N_T in the precision prec; they must not alias. */
 int bem_precond_apply(aim_ctx* ctx, const void* r, void* u, int prec, void* stream);
+
+/* Build (or rebuild) the inverses of bem_precond_apply in the precision build_prec. BEM_C32
+ * (what the first bem_precond_apply or preconditioned bem_solve uses): each A_ii is formed,
+ * LU-factorised and inverted in complex FP32, then checked with four pseudo-random columns V:
+ * the first iterative-refinement correction relative to X V, ||X (A_ii X V - V)||_F /
+ * ||X V||_F, estimates the inverse's forward error; a block above 1e-2 is rebuilt in FP64. BEM_C64: every block in FP64. L^A_ii and L^Phi_ii are FP64 integrals in both cases.
+ * aim_info entries 32-35 report the build. Synchronises the device. */
+int bem_precond_setup(aim_ctx* ctx, int build_prec);
 
 typedef struct {
   int32_t iters;
@@ -350,7 +382,8 @@ int bem_port_matrix(aim_ctx* ctx, int nport, const int32_t* ring_n, const int32_
  * bem_net_train: `steps` Adam steps of lr on batches of `batch` pairs r = A x (x complex normal
  *   from the hash of seed, half of them smoothed on the grid), minimising the grid-projected
  *   error |P (W net(P r) - t)|^2 / |P t|^2 with t = x - M_bd r; losses
- *   (HOST, may be NULL) receives the mean loss of each step. Builds M_bd on first use.
+ *   (HOST, may be NULL) receives the mean loss of each step. Builds M_bd in FP64
+ *   (bem_precond_setup(ctx, BEM_C64)) unless it is so built already: t carries M_bd's own error.
  * bem_net_apply: z = M_bd r + W net(P r) for complex FP32 device vectors of N_E + N_T
  *   (z = W net(P r) alone when correction_only is non-zero).
  * bem_convnet_run: the network alone on an nx x ny x nz grid, for verification: x [8][ng] FP32

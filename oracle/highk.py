@@ -23,7 +23,7 @@ through rho (|P| <= 1e-12 diam) has J1 = J4 = 0 and no angle: the limits from bo
 
 The edge integrals use a graded Gauss-Legendre rule (6 points per interval) in |t|, the
 integrands being even in t: breakpoints at h0 2^j up to the first one above 2 dmax, then steps
-of dmax, with h0 = min(|P| (w if P = 0), 1/|k|)/2, dmax = 2/|k| and w = sqrt(P^2 + a^2); the
+of dmax, with h0 = min(|P| (w if P = 0), 1/|k|)/2, dmax = 6/|k| and w = sqrt(P^2 + a^2); the
 rule stops where |Im k| (R - w) exceeds 18 (exp(-18) ~ 2e-8 of the peak) and skips an edge
 whose |Im k| (w - a) exceeds 18. The edge integrals are then accurate to a few 1e-9, far below
 the outer rule's own error (about 1e-3 at |k| diam = 36, see the refinement study).

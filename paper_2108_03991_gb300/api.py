@@ -25,7 +25,7 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "bem_net_apply", "bem_convnet_run", "aim_gemv_select", "aim_gemv_plan",
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
-           "bem_solve_batch"]
+           "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse"]
 
 
 class BemError(RuntimeError):
@@ -98,6 +98,8 @@ def lib():
         L.bem_port_matrix.argtypes = [vp, C.c_int, C.POINTER(i32), C.POINTER(i32), C.POINTER(d),
                                       C.POINTER(SolveOpts), C.POINTER(d), C.POINTER(SolveInfo), vp]
         L.bem_precond_apply.argtypes = [vp, vp, vp, C.c_int, vp]
+        L.bem_precond_setup.argtypes = [vp, C.c_int]
+        L.aim_internal_sparse.argtypes = [vp, C.c_int]
         fp = C.POINTER(C.c_float)
         L.bem_net_init.argtypes = [vp, C.c_uint64]
         L.bem_net_weights.argtypes = [vp, fp, i64, C.c_int]
@@ -217,8 +219,8 @@ class Context:
         self._read_info()
 
     def _read_info(self):
-        info = (C.c_int64 * 32)()
-        _check(lib().aim_info(self.h, info, 32))
+        info = (C.c_int64 * 42)()
+        _check(lib().aim_info(self.h, info, 42))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -237,6 +239,14 @@ class Context:
         self.setup_stage_s = dict(zip(
             ("geometry", "stencils", "internal_ki", "internal_k0", "lu", "yz", "near", "ghat",
              "gemv_tune", "schedule_tune"), (v * 1e-6 for v in info[22:32])))
+        # last block-diagonal preconditioner build: seconds, precision (-1: none yet), blocks
+        # built in FP64, largest FP32 block check (None: none ran)
+        self.precond_build = {"seconds": info[32] * 1e-6, "prec": info[33], "fp64_blocks": info[34],
+                              "check": None if info[35] < 0 else info[35] * 1e-12}
+        # sparse internal operator at high frequency (aim_internal_sparse)
+        self.sparse_internal = {"setup_s": info[36] * 1e-6, "objects": info[37], "on": bool(info[38]),
+                                "band": info[39], "bytes_c32": info[40],
+                                "check": None if info[41] < 0 else info[41] * 1e-15}
 
     # ---- ports and far field ---------------------------------------------------------
     def port_ring(self, obj, axis, coord, tol=1e-6):
@@ -366,14 +376,15 @@ class Context:
                                      x.numel() // n, prec, _stream()))
         return y
 
-    def internal(self, h, e=None, heq=None, nrhs=1, prec=BEM_C32, want_heq=True):
+    def internal(self, h, e=None, heq=None, nrhs=1, prec=BEM_C32, want_heq=True, want_e=True):
+        """e = Z h and h_eq = Y_eq Z h (internal_apply); either may be left out."""
         import torch
         dt = cdtype(prec)
-        if e is None:
+        if e is None and want_e:
             e = torch.empty_like(h)
         if heq is None and want_heq:
             heq = torch.empty_like(h)
-        _check(lib().internal_apply(self.h, _ptr(h, dt), _ptr(e, dt),
+        _check(lib().internal_apply(self.h, _ptr(h, dt), _ptr(e, dt) if e is not None else None,
                                     _ptr(heq, dt) if heq is not None else None, int(nrhs), prec,
                                     _stream()))
         return e, heq
@@ -393,6 +404,20 @@ class Context:
         k = (C.c_double * 3)(*khat)
         _check(lib().bem_rhs_plane_wave(self.h, p, k, _ptr(b), prec, _stream()))
         return b
+
+    def internal_sparse(self, on):
+        """Use the sparse internal operator Z_s (on=True, when aim_setup built one) or the dense Z
+        for e = Z h; returns sparse_internal."""
+        _check(lib().aim_internal_sparse(self.h, int(bool(on))))
+        self._read_info()
+        return self.sparse_internal
+
+    def precond_setup(self, build_prec=BEM_C32):
+        """Build (or rebuild) the block-diagonal preconditioner's inverses in complex FP32
+        (each block checked; FP64 where the check fails) or FP64; returns precond_build."""
+        _check(lib().bem_precond_setup(self.h, build_prec))
+        self._read_info()
+        return self.precond_build
 
     def precond(self, r, u=None, prec=BEM_C32):
         """u = M_bd r, the block-diagonal preconditioner (built on first use)."""
@@ -444,6 +469,8 @@ class Context:
         inf = SolveInfo()
         rc = _check(lib().bem_solve(self.h, _ptr(b, torch.complex128), _ptr(x, torch.complex128),
                                     C.byref(o), C.byref(inf), _stream()))
+        if precond:
+            self._read_info()  # the first preconditioned solve builds the preconditioner
         return x, {"status": rc, "iters": inf.iters, "resid_est": inf.resid_est,
                    "resid_true": inf.resid_true, "seconds": inf.seconds}
 

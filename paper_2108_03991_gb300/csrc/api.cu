@@ -87,6 +87,7 @@ void aim_destroy(aim_ctx* c) {
   free_net(c);
   free_geo_store(c);
   free_far_geo(c);
+  free_zsp(c);
   if (c->gm_ws) cudaFree(c->gm_ws);
   if (c->gmb_ws) cudaFree(c->gmb_ws);
   delete c;
@@ -110,6 +111,15 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
                    c->tune_rejected, kind, c->gplan.cps, c->z_after};
   for (int i = 0; i < n && i < 22; ++i) info[i] = v[i];
   for (int i = 22; i < n && i < 32; ++i) info[i] = (int64_t)(c->setup_ms[i - 22] * 1e3);
+  const bool pc = c->pc_ready;
+  const int64_t w[4] = {pc ? (int64_t)(c->pc_ms * 1e3) : 0, pc ? c->pc_prec : -1,
+                        pc ? c->pc_nfp64 : 0,
+                        pc && c->pc_prec == BEM_C32 ? (int64_t)(c->pc_resid * 1e12) : -1};
+  for (int i = 32; i < n && i < 36; ++i) info[i] = w[i - 32];
+  int64_t z[5];
+  zsp_stats(c, z);
+  const int64_t zv[6] = {(int64_t)(c->setup_ms[10] * 1e3), z[0], z[1], z[2], z[3], z[4]};
+  for (int i = 36; i < n && i < 42; ++i) info[i] = zv[i - 36];
   return BEM_OK;
 }
 
@@ -271,7 +281,7 @@ int aim_matvec(aim_ctx* c, int which, const void* x, void* y, int prec, void* st
 int internal_apply(aim_ctx* c, const void* h, void* e, void* heq, int nrhs, int prec, void* stream) {
   BEM_TRY(check_ctx(c, "internal_apply"));
   BEM_TRY(check_prec(prec, "internal_apply"));
-  if (!h || !e || nrhs < 1 || h == e || heq == e || heq == h) {
+  if (!h || (!e && !heq) || nrhs < 1 || h == e || heq == e || heq == h) {
     set_error("internal_apply: bad pointers or nrhs");
     return BEM_EINVAL;
   }
@@ -462,6 +472,29 @@ int bem_precond_apply(aim_ctx* c, const void* r, void* u, int prec, void* stream
   BEM_TRY(setup_precond(c));
   cudaStream_t s = (cudaStream_t)stream;
   return prec == BEM_C32 ? precond_apply<float>(c, r, u, s) : precond_apply<double>(c, r, u, s);
+}
+
+int aim_internal_sparse(aim_ctx* c, int on) {
+  BEM_TRY(check_ctx(c, "aim_internal_sparse"));
+  if (on != 0 && on != 1) {
+    set_error("aim_internal_sparse: on must be 0 or 1");
+    return BEM_EINVAL;
+  }
+  if (on && !c->zsp_ready) {
+    set_error("aim_internal_sparse: no sparse internal operator was built for this structure");
+    return BEM_EINVAL;
+  }
+  BEM_CUDA(cudaDeviceSynchronize());
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);  // they hold the old launches
+  c->graphs.clear();
+  c->zsp_on = on != 0;
+  return BEM_OK;
+}
+
+int bem_precond_setup(aim_ctx* c, int build_prec) {
+  BEM_TRY(check_ctx(c, "bem_precond_setup"));
+  BEM_TRY(check_prec(build_prec, "bem_precond_setup"));
+  return setup_precond(c, build_prec);
 }
 
 int bem_solve(aim_ctx* c, const void* b, void* x, const bem_solve_opts* o, bem_solve_info* info,

@@ -256,7 +256,7 @@ struct aim_ctx {
   // wall time of the set-up stages in ms (aim_info entries 22-31): host geometry, stencils,
   // internal integrals at k_i, internal integrals at k0, LU solves, C = Y Z, near region,
   // FFT of the grid kernel, GEMV autotuner, matvec schedule tuner
-  double setup_ms[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double setup_ms[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // [10]: sparse internal operator
   float tune_ms[2] = {0, 0};  // autotuner: best plain, best staged candidate (5 launches, ms)
   int tune_rejected = 0;      // autotuner candidates rejected (wrong product or timed out)
   std::vector<float> tune_table;  // autotuner: (kind, cps, split, unroll, ns) per candidate
@@ -314,6 +314,11 @@ struct aim_ctx {
   // block-diagonal preconditioner: explicit inverses of the per-object blocks A_ii, packed
   // row-major in object-major unknown order ([h_i; q_i] per object), built on first use
   bool pc_ready = false;
+  bool pc_planned = false;  // the GEMV plans over the blocks exist (made by the first build)
+  int pc_prec = 0;          // precision of the last build (BEM_C32 or BEM_C64)
+  int pc_nfp64 = 0;         // blocks built in FP64 by that build
+  double pc_resid = 0;      // largest FP32 block check ||X (A X V - V)||_F / ||X V||_F
+  double pc_ms = 0;         // wall time of that build
   bem::GemvPlan pcplan;
   bem::GemvPlan pcplan64;
   float2* pc32 = nullptr;
@@ -333,6 +338,10 @@ struct aim_ctx {
   void* far_geo = nullptr;
   // learned correction network on the AIM grid (learned.cu)
   void* net = nullptr;
+  // sparse internal operator at high frequency (zsparse.cu): built at set-up when every object
+  // qualifies (zsp_ready), used for e = Z h while zsp_on
+  void* zsp = nullptr;
+  bool zsp_ready = false, zsp_on = false;
 };
 
 namespace bem {
@@ -393,7 +402,13 @@ template <typename R> int make_twiddles(aim_ctx* c, PrecBuf<R>& b);
 int make_ghat(aim_ctx* c);
 int rhs_plane_wave(aim_ctx* c, const double* pol, const double* kh, void* b, int prec,
                    cudaStream_t st);
-int setup_precond(aim_ctx* c);
+// builds (or rebuilds in another precision) the block-diagonal preconditioner; prec: BEM_C32
+// (FP32 blocks, each checked, FP64 where the check fails), BEM_C64, or -1: as it stands if
+// built, else BEM_C32
+int setup_precond(aim_ctx* c, int prec = -1);
+template <typename R> inline PrecBuf<R>& buf(aim_ctx* c);
+template <> inline PrecBuf<float>& buf<float>(aim_ctx* c) { return c->f32; }
+template <> inline PrecBuf<double>& buf<double>(aim_ctx* c) { return c->f64; }
 template <typename R>
 int project_all(aim_ctx* c, const typename C2<R>::T* r, typename C2<R>::T* sigma, cudaStream_t s);
 template <typename R>
@@ -411,6 +426,16 @@ double wall_ms();  // host wall clock in milliseconds
 // (pass 0: k = k_i, pass 1: k = k0), row-major n_i x n_i complex doubles on the host
 int export_LK(aim_ctx* c, int obj, int pass, double2* L_out, double2* K_out);
 void free_far_geo(aim_ctx* c);
+// sparse internal operator at high frequency (zsparse.cu)
+int zsp_prepare(aim_ctx* c, const double* d_verts, const int32_t* d_tris, const double* d_cen);
+int zsp_gather(aim_ctx* c, int obj, const double2* L, const double2* B);
+int zsp_factor(aim_ctx* c);
+int zsp_check(aim_ctx* c);
+void free_zsp(aim_ctx* c);
+void zsp_stats(const aim_ctx* c, int64_t* out);  // objects, in use, max band, FP32 bytes, check
+template <typename R>
+int zsp_apply(aim_ctx* c, const typename C2<R>::T* h, typename C2<R>::T* e, int nrhs, int64_t hs,
+              int64_t es, cudaStream_t s);
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);
 int tune_matvec_schedule(aim_ctx* c);
 double k0_of(double f);

@@ -1120,21 +1120,22 @@ __global__ void __launch_bounds__(256) k_wslab_xfwd(const float2* __restrict__ s
 }
 
 // y-z fused for one kx: warp z transforms its y line, the nz lines meet in shared memory
-// (position k1 * 32 + lane) for the z DFTs and Ghat, then each warp inverts its line
+// (position k1 * 32 + lane) for the z DFTs and Ghat, then each warp inverts its line. Ghat is
+// read where it is used (each value serves the two positions ky and P - ky of this CTA, the
+// slab stays in L2 across kx and Px - kx and the components) rather than staged: without its
+// 33 KB the CTA's shared memory is the 64 KB of its nz lines, three CTAs per SM instead of two.
 template <int M, int MZ>
 __global__ void __launch_bounds__(256) k_wslab_yz(float2* __restrict__ ws,
                                                   const float2* __restrict__ gs,
                                                   const float2* __restrict__ twy,
                                                   const float2* __restrict__ twz, SlabArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  float2* G = reinterpret_cast<float2*>(smem_raw);  // this kx's Ghat slab [fz][fy]
-  float2* S = G + a.gz * a.gy;                       // [z][32 M]
+  float2* S = reinterpret_cast<float2*>(smem_raw);  // [z][32 M]
   constexpr int P = 32 * M;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kx = blockIdx.x, c = blockIdx.y;
   const int fx = min(kx, a.Px - kx);
-  const float2* g = gs + (int64_t)fx * a.gz * a.gy;
-  for (int i = threadIdx.x; i < a.gz * a.gy; i += blockDim.x) G[i] = g[i];
+  const float2* G = gs + (int64_t)fx * a.gz * a.gy;  // this kx's Ghat slab [fz][fy]
   float2* X = ws + c * a.P3 + (int64_t)kx * a.nz * a.ny;  // [z][y]
   for (int z = warp; z < a.nz; z += 8) {
     float2 v[M];
@@ -1156,7 +1157,7 @@ __global__ void __launch_bounds__(256) k_wslab_yz(float2* __restrict__ ws,
     for (int z = 0; z < MZ; ++z) v[z] = z < a.nz ? S[z * P + pos] : make_float2(0.f, 0.f);
     dft_reg<float2, MZ>(v, twz, 1, false);
 #pragma unroll
-    for (int kz = 0; kz < MZ; ++kz) v[kz] = cmul(v[kz], G[min(kz, MZ - kz) * a.gy + fy]);
+    for (int kz = 0; kz < MZ; ++kz) v[kz] = cmul(v[kz], __ldg(&G[min(kz, MZ - kz) * a.gy + fy]));
     dft_reg<float2, MZ>(v, twz, 1, true);
 #pragma unroll
     for (int z = 0; z < MZ; ++z)
@@ -1252,7 +1253,7 @@ static int slab_conv(aim_ctx* c, PrecBuf<float>& b, const float2* sigma, float2*
   // takes
   if (a.Px == a.Py && (a.Px == 1024 || a.Px == 512) && a.nz <= 8 && a.Pz == 15) {
     const dim3 gw((a.ny + 7) / 8, a.nz, ncomp);
-    const size_t ssm = ((size_t)a.gz * a.gy + (size_t)a.nz * a.Py) * sizeof(float2);
+    const size_t ssm = (size_t)a.nz * a.Py * sizeof(float2);
     if (a.Px == 1024) {
       k_wslab_xfwd<32><<<gw, 256, 0, s>>>(sigma, ws, b.tw[0], a);
       k_wslab_yz<32, 15><<<dim3(a.Px, ncomp), 256, ssm, s>>>(ws, b.Gs, b.tw[1], b.tw[2], a);

@@ -886,9 +886,6 @@ __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA
   if (lane == 0) a[m] = acc;
 }
 
-template <typename R> PrecBuf<R>& buf(aim_ctx* c);
-template <> PrecBuf<float>& buf<float>(aim_ctx* c) { return c->f32; }
-template <> PrecBuf<double>& buf<double>(aim_ctx* c) { return c->f64; }
 
 // The system matvec of Eq. AEFIEoutJ for nrhs right-hand sides x_r = [h_r; q_r] (stride
 // N_E + N_T) at once: each block matrix is read once for all of them (the GEMV takes the
@@ -926,7 +923,10 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   k_near_e<R><<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.bj, ne, b.ban,
                                                            N, ne);
   BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
-  BEM_TRY(gemv(b.Z, b.be, nullptr));  // e_r = Z h_r
+  if (c->zsp_on)  // e_r = Z_s h_r, the sparse internal operator
+    BEM_TRY(zsp_apply<R>(c, x, b.be, nrhs, N, N, s));
+  else
+    BEM_TRY(gemv(b.Z, b.be, nullptr));  // e_r = Z h_r
   project_e<R>(c, b.WAT, b.bj, b.bsE, s, nrhs, N);
   BEM_TRY(fft_conv<R>(c, b, b.bsE, b.bsE, 3 * nrhs, b.bwsE, s));
   BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -1012,19 +1012,22 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     // GEMV on the main stream (2), or in one launch with j's GEMV (3). The charge branch
     // p = L^Phi q runs on the side stream, followed there by the near region L^A_NR j once j is
     // out, so that only the interpolation and the combination follow the convolution.
+    // With the sparse internal operator, e = Z_s h runs on its own stream from the start.
     const V* h = x;
     const V* q = x + ne;
     V* sq = b.sigma + 3 * ng;
+    const int za = c->zsp_on ? 0 : c->z_after;
     BEM_CUDA(cudaEventRecord(c->ev_fork, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    if (c->z_after < 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
+    if (za < 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
     k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
                                                 nt, nx, ny, b.p);
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
-    if (c->z_after == 3)  // j = h - C h and e = Z h in one launch
+    if (c->zsp_on) BEM_TRY(zsp_apply<R>(c, h, b.e, 1, ne, ne, c->zside));
+    if (za == 3)  // j = h - C h and e = Z h in one launch
       BEM_TRY(run_gemv_pair<R>(c->gpair, b.C, b.Z, h, b.j, b.e, h, s));
     else
       BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
@@ -1032,14 +1035,14 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
     k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.j, ne, b.anear);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
-    if (c->z_after == 2) {  // e = Z h right after j's GEMV on the main stream, whole GPU
+    if (za == 2) {  // e = Z h right after j's GEMV on the main stream, whole GPU
       BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
-    } else if (c->z_after != 3) {
-      if (c->z_after)  // e = Z h once j is out, beside the AIM chain only
+    } else if (za != 3 && !c->zsp_on) {
+      if (za)  // e = Z h once j is out, beside the AIM chain only
         BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_c, 0));
       BEM_TRY(run_gemv_plan<R>(gb, b.Z, h, b.e, 1, ne, nullptr, c->zside));
     }
-    BEM_CUDA(cudaEventRecord(c->ev_z, c->z_after >= 2 ? s : c->zside));
+    BEM_CUDA(cudaEventRecord(c->ev_z, za >= 2 ? s : c->zside));
     project_e<R>(c, b.WAT, b.j, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -1192,9 +1195,14 @@ int internal(aim_ctx* c, const void* hv, void* ev, void* heqv, int nrhs, cudaStr
   typedef typename C2<R>::T V;
   PrecBuf<R>& b = buf<R>(c);
   const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
-  if (nrhs == 1 && heqv && c->z_after == 3 && c->gpair.ntasks > 0)  // the matvec's paired launch
+  if (!ev) {
+  } else if (c->zsp_on) {  // e = Z_s h, the sparse internal operator
+    BEM_TRY(zsp_apply<R>(c, (const V*)hv, (V*)ev, nrhs, c->ne, c->ne, s));
+  } else if (nrhs == 1 && heqv && c->z_after == 3 && c->gpair.ntasks > 0) {  // the matvec's pair
     return run_gemv_pair<R>(c->gpair, b.C, b.Z, (const V*)hv, (V*)heqv, (V*)ev, nullptr, s);
-  BEM_TRY(run_gemv_plan<R>(gp, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
+  } else {
+    BEM_TRY(run_gemv_plan<R>(gp, b.Z, (const V*)hv, (V*)ev, nrhs, c->ne, nullptr, s));
+  }
   if (heqv) BEM_TRY(run_gemv_plan<R>(gp, b.C, (const V*)hv, (V*)heqv, nrhs, c->ne, nullptr, s));
   return BEM_OK;
 }

@@ -501,7 +501,10 @@ int bem_net_train(aim_ctx* c, int steps, int batch, float lr, uint64_t seed, flo
   int rc = BEM_OK;
   Net* n = get_net(c, &rc);
   if (!n) return rc;
-  BEM_TRY(setup_precond(c));
+  // the targets x - M_bd A x hold M_bd's own error A_ii^{-1} - X_ii: with inverses built in FP32
+  // that is the FP32 LU's error (left residual ~ cond * eps), mesh-scale noise no grid
+  // correction can learn, so training builds them in FP64
+  BEM_TRY(setup_precond(c, BEM_C64));
   cudaStream_t s = (cudaStream_t)stream;
   for (int k = 0; k < steps; ++k) {
     float l = 0;

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <memory>
 
 #include "common.cuh"
 #include "quad.cuh"
@@ -220,6 +221,21 @@ __device__ __forceinline__ void half_rwg(const DGeo& g, int n, int t, double* sg
 }
 
 // kind 0: int int f.f G ; kind 1: L (with -k^-2 div div) ; returns K too when wantK
+// int int (r - a).(r' - b) G dS' dS from the pair moments (origin o): a = va + o, b = vb + o
+// are the free vertices of the two half-RWGs; the vector-potential kernel of L before its
+// l_m l_n / (4 A A') factor
+__device__ __forceinline__ double2 vec_term(const Moments& M, const double* va, const double* vb) {
+  double2 v = M.M2;
+  for (int q = 0; q < 3; ++q) {
+    v.x += -M.M1[q].x * vb[q] - va[q] * M.M1p[q].x;
+    v.y += -M.M1[q].y * vb[q] - va[q] * M.M1p[q].y;
+  }
+  const double vv = d_dot(va, vb);
+  v.x += vv * M.M0.x;
+  v.y += vv * M.M0.y;
+  return v;
+}
+
 __device__ void rwg_pair(const DGeo& g, int m, int n, double kr, double ki, bool isL, bool wantK,
                          double2* Lval, double2* Kval) {
   double2 L = {0, 0}, K = {0, 0};
@@ -243,14 +259,7 @@ __device__ void rwg_pair(const DGeo& g, int m, int n, double kr, double ki, bool
       const double va[3] = {pa[0] - o[0], pa[1] - o[1], pa[2] - o[2]};
       const double vb[3] = {pb[0] - o[0], pb[1] - o[1], pb[2] - o[2]};
       double cf = sm * sn * g.elen[m] * g.elen[n] / (4.0 * g.area[t] * g.area[s]);
-      double2 v = M.M2;
-      for (int q = 0; q < 3; ++q) {
-        v.x += -M.M1[q].x * vb[q] - va[q] * M.M1p[q].x;
-        v.y += -M.M1[q].y * vb[q] - va[q] * M.M1p[q].y;
-      }
-      double vv = d_dot(va, vb);
-      v.x += vv * M.M0.x;
-      v.y += vv * M.M0.y;
+      const double2 v = vec_term(M, va, vb);
       L.x += cf * v.x;
       L.y += cf * v.y;
       if (isL) {
@@ -410,14 +419,7 @@ __global__ void k_obj_assemble(DGeo g, int e0, int n, int t0, int m, double kr, 
       const double va[3] = {pa[0] - o[0], pa[1] - o[1], pa[2] - o[2]};
       const double vb[3] = {pb[0] - o[0], pb[1] - o[1], pb[2] - o[2]};
       const double cf = sm * sn * g.elen[mm] * g.elen[nn] / (4.0 * g.area[t] * g.area[sidx]);
-      double2 v = M.M2;
-      for (int q = 0; q < 3; ++q) {
-        v.x += -M.M1[q].x * vb[q] - va[q] * M.M1p[q].x;
-        v.y += -M.M1[q].y * vb[q] - va[q] * M.M1p[q].y;
-      }
-      const double vv = d_dot(va, vb);
-      v.x += vv * M.M0.x;
-      v.y += vv * M.M0.y;
+      const double2 v = vec_term(M, va, vb);
       L.x += cf * v.x;
       L.y += cf * v.y;
       const double dv = sm * sn * g.elen[mm] * g.elen[nn] / (g.area[t] * g.area[sidx]);
@@ -438,6 +440,41 @@ __global__ void k_obj_assemble(DGeo g, int e0, int n, int t0, int m, double kr, 
     if (ixcol[4 * mm + q] == nn) K.x += 0.5 * ixval[4 * mm + q];
   Lc[idx] = L;
   Bc[idx] = K;
+}
+
+// L^A of object obj (column-major n x n) from its pair moments at k0: the vector-potential part
+// of L alone (Eq. AIM_L's exact counterpart, used by the preconditioner blocks)
+__global__ void k_obj_assemble_A(DGeo g, int e0, int n, int t0, int m,
+                                 const Moments* __restrict__ mom, double2* LAc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int mm = e0 + (int)(idx % n), nn = e0 + (int)(idx / n);
+  double2 L = {0, 0};
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int t = g.et[2 * mm + a], sidx = g.et[2 * nn + b];
+      const Moments& M = mom[(int64_t)(t - t0) * m + (sidx - t0)];
+      double sm, sn;
+      const double *pa, *pb;
+      half_rwg(g, mm, t, &sm, &pa);
+      half_rwg(g, nn, sidx, &sn, &pb);
+      const double* o = &g.cen[3 * t];
+      const double va[3] = {pa[0] - o[0], pa[1] - o[1], pa[2] - o[2]};
+      const double vb[3] = {pb[0] - o[0], pb[1] - o[1], pb[2] - o[2]};
+      const double cf = sm * sn * g.elen[mm] * g.elen[nn] / (4.0 * g.area[t] * g.area[sidx]);
+      const double2 v = vec_term(M, va, vb);
+      L.x += cf * v.x;
+      L.y += cf * v.y;
+    }
+  LAc[idx] = L;
+}
+
+// L^Phi of the object's pulses (column-major m x m): the M0 moment of each triangle pair
+__global__ void k_obj_LP(const Moments* __restrict__ mom, int m, double2* LP) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * m) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  LP[idx] = mom[(int64_t)i * m + j].M0;
 }
 
 // Store alpha * X (column-major) into the packed row-major block (FP64 and FP32 copies).
@@ -1162,15 +1199,15 @@ struct MomentScratch {
   }
 };
 
-// L_k (into L) and K_k + I_x/2 (into B), column-major n x n, for object obj and wavenumber k
-static int object_LK(aim_ctx* c, const DGeo& g, int obj, std::complex<double> k, MomentScratch* ms,
-                     double2* L, double2* B) {
-  const int n = c->e1[obj] - c->e0[obj];
+// pair moments of every triangle pair (T, S) of object obj at wavenumber k into
+// ms->mom[(T - t0) m + (S - t0)]; large-|k| near pairs through the per-point passes
+static int object_moments(aim_ctx* c, const DGeo& g, int obj, std::complex<double> k, bool wantK,
+                          MomentScratch* ms) {
   const int t0 = c->t0[obj], m = c->t1[obj] - c->t0[obj];
   const int64_t pairs = (int64_t)m * m;
   BEM_TRY(ms->reserve(pairs));
   BEM_CUDA(cudaMemset(ms->count, 0, sizeof(int)));
-  k_obj_moments<<<nblk(pairs, 128), 128>>>(g, t0, m, k.real(), k.imag(), true, ms->mom, ms->list,
+  k_obj_moments<<<nblk(pairs, 128), 128>>>(g, t0, m, k.real(), k.imag(), wantK, ms->mom, ms->list,
                                            ms->count);
   BEM_CUDA(cudaGetLastError());
   int nhk = 0;
@@ -1194,10 +1231,19 @@ static int object_LK(aim_ctx* c, const DGeo& g, int obj, std::complex<double> k,
     k_hk_items<<<nblk(nhk, 128), 128>>>(g, t0, m, k.real(), k.imag(), ms->list, nhk, ms->off,
                                          ms->items);
     BEM_CUDA(cudaGetLastError());
-    k_hk_points<<<nblk(tot, 128), 128>>>(g, t0, m, k.real(), k.imag(), true, ms->list, ms->items,
+    k_hk_points<<<nblk(tot, 128), 128>>>(g, t0, m, k.real(), k.imag(), wantK, ms->list, ms->items,
                                           tot, ms->mom);
     BEM_CUDA(cudaGetLastError());
   }
+  return BEM_OK;
+}
+
+// L_k (into L) and K_k + I_x/2 (into B), column-major n x n, for object obj and wavenumber k
+static int object_LK(aim_ctx* c, const DGeo& g, int obj, std::complex<double> k, MomentScratch* ms,
+                     double2* L, double2* B) {
+  const int n = c->e1[obj] - c->e0[obj];
+  const int t0 = c->t0[obj], m = c->t1[obj] - c->t0[obj];
+  BEM_TRY(object_moments(c, g, obj, k, true, ms));
   k_obj_assemble<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[obj], n, t0, m, k.real(), k.imag(),
                                                      ms->mom, c->d_ixcol, c->f64.ix, L, B);
   BEM_CUDA(cudaGetLastError());
@@ -1243,6 +1289,12 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
     rc = BEM_ECUDA;
   }
   const double w = 2.0 * kPi * c->freq;
+  {
+    // pattern and ordering of the sparse internal operator (when every object qualifies)
+    const double tz = wall_ms();
+    if (rc == BEM_OK) rc = zsp_prepare(c, g.verts, g.tris, g.cen);
+    c->setup_ms[10] += wall_ms() - tz;
+  }
   for (int i = 0; i < nobj && rc == BEM_OK; ++i) {
     const int n = c->e1[i] - c->e0[i];
     const bem_material& mt = c->mat[i];
@@ -1256,6 +1308,7 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
       std::complex<double> k = pass == 0 ? ki : std::complex<double>(c->k0, 0.0);
       double t0 = wall_ms();
       rc = object_LK(c, g, i, k, &ms, L, B);
+      if (rc == BEM_OK && pass == 0 && c->zsp) rc = zsp_gather(c, i, L, B);  // before the LU
       if (rc != BEM_OK) break;
       cudaDeviceSynchronize();
       double t1 = wall_ms();
@@ -1303,6 +1356,11 @@ static int setup_internal(aim_ctx* c, const DGeo& g, const int32_t* d_ixcol, con
   }
   cudaDeviceSynchronize();
   c->setup_ms[5] = wall_ms() - tyz;
+  if (rc == BEM_OK && c->zsp) {
+    const double tz = wall_ms();
+    rc = zsp_factor(c);
+    c->setup_ms[10] += wall_ms() - tz;
+  }
   cudaFree(L);
   cudaFree(B);
   cudaFree(ipiv);
@@ -1527,106 +1585,339 @@ int setup_device(aim_ctx* c) {
   c->setup_ms[8] = wall_ms() - tst;
   c->geo_store = new DGeo(g);
   tst = wall_ms();
+  BEM_TRY(zsp_check(c));
+  c->setup_ms[10] += wall_ms() - tst;
+  // the schedule of e = Z h is tuned for the dense form; the sparse one, when built, then
+  // takes its place
+  const bool zsp = c->zsp_on;
+  c->zsp_on = false;
+  tst = wall_ms();
   BEM_TRY(tune_matvec_schedule(c));
   c->setup_ms[9] = wall_ms() - tst;
+  c->zsp_on = zsp;
   return BEM_OK;
 }
 
 // ---------------------------------------------------------------------------------------
 // block-diagonal preconditioner: A_ii, the system of Eq. (AEFIEoutJ) restricted to object i's
 // unknowns [h_i; q_i] with its exact dense L^A_ii and L^Phi_ii,
-//   A_ii = [[j k0 L^A + (-j k0 L^A Y + I_x) Z, -(F D)^T L^Phi], [(F D)(I - Y Z), j k0 I]],
-// inverted explicitly at set-up; the solve applies blockdiag(A_ii^{-1}) on the right.
+//   A_ii = [[j k0 L^A + (-j k0 L^A Y + I_x) Z, -(F D)^T L^Phi], [(F D)(I - Y Z), j k0 I]]
+//        = [[j k0 L^A (I - C) + I_x Z,          -(F D)^T L^Phi], [(F D)(I - C),     j k0 I]]
+// with C = Y Z of Eq. EFIEeqYZ (formed at set-up), inverted explicitly; the solve applies
+// blockdiag(A_ii^{-1}) on the right. L^A and L^Phi come from the FP64 pair moments at k0.
+// Build precision BEM_C32 (the default): each block is formed, LU-factorised and inverted in
+// complex FP32, then its inverse X is checked with four pseudo-random columns V: the first
+// iterative-refinement correction relative to X V, ||X (A X V - V)||_F / ||X V||_F (an estimate
+// of X's forward error, from the FP32 block it inverts), above kPcCheck rebuilds that block in
+// FP64. (The residual ||A X V - V|| itself is no measure here: on badly scaled blocks it is
+// large for the FP64 inverse rounded to FP32 as well.) BEM_C64: every block in FP64.
 // ---------------------------------------------------------------------------------------
-__global__ void k_obj_A(DGeo g, int e0, int n, double k0, double2* LAc) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  int i = (int)(idx % n), j = (int)(idx / n);
-  double2 L;
-  rwg_pair(g, e0 + i, e0 + j, k0, 0.0, false, false, &L, nullptr);
-  LAc[idx] = L;
-}
+constexpr double kPcCheck = 1e-2;
+constexpr int kPcProbe = 4;
 
-__global__ void k_obj_P(DGeo g, int t0, int m, double k0, double2* LPc) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)m * m) return;
-  int i = (int)(idx % m), j = (int)(idx / m);
-  Tri T, S;
-  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + i, &T);
-  load_tri(g.verts, g.tris, g.nrm, g.area, g.diam, g.cen, t0 + j, &S);
-  Moments M;
-  pair_moments(T, S, k0, 0.0, false, false, true, &M);
-  LPc[idx] = M.M0;
-}
+template <typename R> struct CuType;
+template <> struct CuType<float> {
+  static constexpr cudaDataType t = CUDA_C_32F;
+  static constexpr cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
+};
+template <> struct CuType<double> {
+  static constexpr cudaDataType t = CUDA_C_64F;
+  static constexpr cublasComputeType_t ct = CUBLAS_COMPUTE_64F;
+};
 
-// packed row-major (leading dimension ld) -> column-major n x n
-__global__ void k_unpack(const double2* P, int n, int ld, double2* C) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  int r = (int)(idx % n), col = (int)(idx / n);
-  C[idx] = P[(int64_t)r * ld + col];
-}
-
-// dense I_x restricted to the object (column-major), from the 4-per-row sparse table
-__global__ void k_dense_ix(const int32_t* ixcol, const double* ixval, int e0, int n, double2* C) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int q = 0; q < 4; ++q) {
-    int col = ixcol[4 * (e0 + i) + q] - e0;
-    if (col >= 0 && col < n) C[i + (int64_t)col * n] = make_double2(ixval[4 * (e0 + i) + q], 0.0);
-  }
-}
-
-// dense F D restricted to the object (m x n, column-major)
-__global__ void k_dense_fd(const int32_t* tedge, const double* fdT, int t0, int m, int e0, int n,
-                           double2* C) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m) return;
-  for (int q = 0; q < 3; ++q) {
-    int col = tedge[3 * (t0 + t) + q] - e0;
-    if (col >= 0 && col < n) C[t + (int64_t)col * m] = make_double2(fdT[3 * (t0 + t) + q], 0.0);
-  }
-}
-
-// A_full (N = n + m, column-major) from A11 (n x n), A12 (n x m), A21 (m x n), A22 = j k0 I
-__global__ void k_bd_assemble(const double2* A11, const double2* A12, const double2* A21, int n,
-                              int m, double k0, double2* A) {
+// A_ii (column-major N x N, N = n + m) but for the -j k0 L^A C term of A11 (a GEMM adds it):
+//   A11 = j k0 L^A + I_x Z,  A12 = -(F D)^T L^Phi,  A21 = F D (I - C),  A22 = j k0 I.
+// Z and C: the object's packed row-major blocks (leading dimension ld); I_x and F D from their
+// sparse rows (four I_x entries per edge, three F D entries per triangle).
+template <typename R>
+__global__ void k_pc_fill(DGeo g, int e0, int n, int t0, int m, double k0,
+                          const double2* __restrict__ LA, const double2* __restrict__ LP,
+                          const typename C2<R>::T* __restrict__ Z, const typename C2<R>::T* __restrict__ C,
+                          int ld, const int32_t* __restrict__ ixcol, const R* __restrict__ ixval,
+                          const int32_t* __restrict__ tedge, const R* __restrict__ fdT,
+                          typename C2<R>::T* A) {
+  typedef typename C2<R>::T V;
   const int N = n + m;
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)N * N) return;
-  int r = (int)(idx % N), col = (int)(idx / N);
-  double2 v;
-  if (r < n && col < n) v = A11[r + (int64_t)col * n];
-  else if (r < n) v = A12[r + (int64_t)(col - n) * n];
-  else if (col < n) v = A21[(r - n) + (int64_t)col * m];
-  else v = make_double2(0.0, r == col ? k0 : 0.0);
+  const int r = (int)(idx % N), col = (int)(idx / N);
+  R vr = 0, vi = 0;
+  if (r < n && col < n) {
+    const double2 a = LA[r + (int64_t)col * n];
+    vr = (R)(-k0 * a.y);
+    vi = (R)(k0 * a.x);
+    for (int q = 0; q < 4; ++q) {
+      const int k = ixcol[4 * (e0 + r) + q] - e0;
+      if (k >= 0 && k < n) {
+        const R w = ixval[4 * (e0 + r) + q];
+        const V z = Z[(int64_t)k * ld + col];
+        vr += w * z.x;
+        vi += w * z.y;
+      }
+    }
+  } else if (r < n) {
+    const int e = e0 + r, cq = col - n;
+    for (int a = 0; a < 2; ++a) {
+      const int t = g.et[2 * e + a];
+      if (t < t0 || t >= t0 + m) continue;
+      for (int q = 0; q < 3; ++q)
+        if (tedge[3 * t + q] == e) {
+          const R f = fdT[3 * t + q];
+          const double2 p = LP[(t - t0) + (int64_t)cq * m];
+          vr -= f * (R)p.x;
+          vi -= f * (R)p.y;
+        }
+    }
+  } else if (col < n) {
+    const int t = t0 + r - n;
+    for (int q = 0; q < 3; ++q) {
+      const int k = tedge[3 * t + q] - e0;
+      if (k >= 0 && k < n) {
+        const R f = fdT[3 * t + q];
+        const V cc = C[(int64_t)k * ld + col];
+        vr += f * ((k == col ? (R)1 : (R)0) - cc.x);
+        vi -= f * cc.y;
+      }
+    }
+  } else {
+    vi = r == col ? (R)k0 : (R)0;
+  }
+  V v;
+  v.x = vr;
+  v.y = vi;
   A[idx] = v;
 }
 
-__global__ void k_identity(double2* A, int N) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+template <typename V>
+__global__ void k_identity(V* A, int N) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)N * N) return;
-  A[idx] = make_double2((idx % N) == (idx / N) ? 1.0 : 0.0, 0.0);
+  V v;
+  v.x = (idx % N) == (idx / N) ? 1 : 0;
+  v.y = 0;
+  A[idx] = v;
 }
 
-struct BlasHandle {
-  cublasHandle_t h = nullptr;
-  ~BlasHandle() { if (h) cublasDestroy(h); }
-};
+__global__ void k_round_c32(const double2* a, float2* b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
 
-static int zgemm(cublasHandle_t h, cublasOperation_t ta, int M, int N, int K, double2 alpha,
-                 const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C, int ldc) {
-  cuDoubleComplex al = make_cuDoubleComplex(alpha.x, alpha.y), be = make_cuDoubleComplex(beta.x, beta.y);
-  if (cublasZgemm(h, ta, CUBLAS_OP_N, M, N, K, &al, (const cuDoubleComplex*)A, lda,
-                  (const cuDoubleComplex*)B, ldb, &be, (cuDoubleComplex*)C, ldc) != CUBLAS_STATUS_SUCCESS) {
-    set_error("cublasZgemm failed");
+// probe columns: real and imaginary parts uniform in [-1, 1) from a 64-bit mix of the index
+// (the finaliser of MurmurHash3)
+template <typename V>
+__global__ void k_pc_probe(V* P, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  V v;
+  v.x = (double)(h >> 40) / 8388608.0 - 1.0;
+  v.y = (double)((h >> 16) & 0xFFFFFF) / 8388608.0 - 1.0;
+  P[i] = v;
+}
+
+// out = (sum |a|^2, sum |b|^2) in FP64 (one CTA of 256 threads)
+template <typename V>
+__global__ void k_pc_norms(const V* a, const V* b, int64_t n, double* out) {
+  __shared__ double s[2][256];
+  double x = 0, y = 0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    x += (double)a[i].x * a[i].x + (double)a[i].y * a[i].y;
+    y += (double)b[i].x * b[i].x + (double)b[i].y * b[i].y;
+  }
+  s[0][threadIdx.x] = x;
+  s[1][threadIdx.x] = y;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + w];
+      s[1][threadIdx.x] += s[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s[0][0];
+    out[1] = s[1][0];
+  }
+}
+
+// X (column-major N x N) into the packed row-major block of leading dimension ld, both copies
+template <typename V>
+__global__ void k_store_pc(const V* X, int N, int ld, double2* P64, float2* P32) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)N * ld) return;
+  const int r = (int)(idx / ld), col = (int)(idx % ld);
+  double2 v = make_double2(0, 0);
+  if (col < N) {
+    const V x = X[r + (int64_t)col * N];
+    v = make_double2(x.x, x.y);
+  }
+  P64[idx] = v;
+  P32[idx] = make_float2((float)v.x, (float)v.y);
+}
+
+static int gemm_t(cublasHandle_t h, cudaDataType t, cublasComputeType_t ct, cublasOperation_t tb,
+                  int M, int N, int K, const void* alpha, const void* A, int lda, const void* B,
+                  int ldb, const void* beta, void* C, int ldc) {
+  if (cublasGemmEx(h, CUBLAS_OP_N, tb, M, N, K, alpha, A, t, lda, B, t, ldb, beta, C, t, ldc, ct,
+                   CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+    set_error("cublasGemmEx (preconditioner block) failed");
     return BEM_ECUDA;
   }
   return BEM_OK;
 }
 
-int setup_precond(aim_ctx* c) {
-  if (c->pc_ready) return BEM_OK;
+// work arrays of one build precision, sized for the largest object
+template <typename R> struct PcWork {
+  typedef typename C2<R>::T V;
+  V *LAr = nullptr, *A = nullptr, *Ac = nullptr, *X = nullptr, *P = nullptr, *W = nullptr,
+    *Rr = nullptr;
+  double* nrm = nullptr;
+  std::vector<void*> mem;
+  ~PcWork() {
+    for (void* p : mem) cudaFree(p);
+  }
+  int alloc(int nmax, int Nmax) {
+    if (A) return BEM_OK;
+    const size_t NN = (size_t)Nmax * Nmax, NP = (size_t)Nmax * kPcProbe;
+    V** bufs[] = {&LAr, &A, &Ac, &X, &P, &W, &Rr};
+    const size_t sizes[] = {sizeof(R) == 4 ? (size_t)nmax * nmax : 0, NN, NN, NN, NP, NP, NP};
+    for (int k = 0; k < 7; ++k) {
+      if (!sizes[k]) continue;
+      if (cudaMalloc((void**)bufs[k], sizes[k] * sizeof(V)) != cudaSuccess) {
+        set_error("preconditioner scratch (%zu bytes) allocation failed", sizes[k] * sizeof(V));
+        return BEM_ENOMEM;
+      }
+      mem.push_back(*bufs[k]);
+    }
+    BEM_CUDA(cudaMalloc(&nrm, 2 * sizeof(double)));
+    mem.push_back(nrm);
+    return BEM_OK;
+  }
+};
+
+struct PcShared {
+  SolverScratch ss;
+  cublasHandle_t bh = nullptr;
+  int64_t* ipiv = nullptr;
+  int* dinfo = nullptr;
+  void* dwork = nullptr;
+  size_t dwsize = 0;
+  std::vector<char> hwork;
+  ~PcShared() {
+    if (bh) cublasDestroy(bh);
+    if (ipiv) cudaFree(ipiv);
+    if (dinfo) cudaFree(dinfo);
+    if (dwork) cudaFree(dwork);
+  }
+};
+
+// X <- A^{-1} (A overwritten by its LU factors), complex type t
+static int lu_inverse(PcShared& s, cudaDataType t, void* A, void* X, int n) {
+  size_t dws = 0, hws = 0;
+  if (cusolverDnXgetrf_bufferSize(s.ss.h, s.ss.p, n, n, t, A, n, t, &dws, &hws) !=
+      CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnXgetrf_bufferSize failed");
+    return BEM_ECUDA;
+  }
+  if (dws > s.dwsize) {
+    if (s.dwork) cudaFree(s.dwork);
+    s.dwork = nullptr;
+    BEM_CUDA(cudaMalloc(&s.dwork, dws));
+    s.dwsize = dws;
+  }
+  if (hws > s.hwork.size()) s.hwork.resize(hws);
+  if (cusolverDnXgetrf(s.ss.h, s.ss.p, n, n, t, A, n, s.ipiv, t, s.dwork, dws, s.hwork.data(), hws,
+                       s.dinfo) != CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnXgetrf failed");
+    return BEM_ECUDA;
+  }
+  int hinfo = 0;
+  BEM_CUDA(cudaMemcpy(&hinfo, s.dinfo, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hinfo != 0) {
+    set_error("singular preconditioner block (getrf info %d)", hinfo);
+    return BEM_ESOLVER;
+  }
+  if (cusolverDnXgetrs(s.ss.h, s.ss.p, CUBLAS_OP_N, n, n, t, A, n, s.ipiv, t, X, n, s.dinfo) !=
+      CUSOLVER_STATUS_SUCCESS) {
+    set_error("cusolverDnXgetrs failed");
+    return BEM_ECUDA;
+  }
+  return BEM_OK;
+}
+
+// one block in precision R: form, invert, check (FP32), store. *resid: the check's value
+// (-1 when not checked).
+template <typename R>
+static int pc_block(aim_ctx* c, const DGeo& g, int i, const double2* LA, const double2* LP,
+                    PcWork<R>& w, PcShared& s, int ld, int64_t off, bool check, double* resid) {
+  typedef typename C2<R>::T V;
+  const cudaDataType t = CuType<R>::t;
+  const cublasComputeType_t ct = CuType<R>::ct;
+  const PrecBuf<R>& b = buf<R>(c);
+  const int e0 = c->e0[i], t0 = c->t0[i];
+  const int n = c->e1[i] - e0, m = c->t1[i] - t0, N = n + m;
+  const double k0 = c->k0;
+  k_pc_fill<R><<<nblk((int64_t)N * N, 256), 256>>>(g, e0, n, t0, m, k0, LA, LP, b.Z + c->zoff[i],
+                                                    b.C + c->zoff[i], c->zld[i], c->d_ixcol, b.ix,
+                                                    c->d_tedge, b.fdT, w.A);
+  const V* LAr = (const V*)LA;
+  if (sizeof(R) == 4) {
+    k_round_c32<<<nblk((int64_t)n * n, 256), 256>>>(LA, (float2*)w.LAr, (int64_t)n * n);
+    LAr = w.LAr;
+  }
+  BEM_CUDA(cudaGetLastError());
+  // A11 -= j k0 L^A C  (C's packed row-major block is C^T in the column-major view)
+  V al, one, mone, zero;
+  al.x = 0;
+  al.y = -k0;
+  one.x = 1;
+  one.y = 0;
+  mone.x = -1;
+  mone.y = 0;
+  zero.x = 0;
+  zero.y = 0;
+  BEM_TRY(gemm_t(s.bh, t, ct, CUBLAS_OP_T, n, n, n, &al, LAr, n, b.C + c->zoff[i], c->zld[i], &one,
+                 w.A, N));
+  if (check) BEM_CUDA(cudaMemcpy(w.Ac, w.A, (size_t)N * N * sizeof(V), cudaMemcpyDeviceToDevice));
+  k_identity<V><<<nblk((int64_t)N * N, 256), 256>>>(w.X, N);
+  BEM_TRY(lu_inverse(s, t, w.A, w.X, N));
+  *resid = -1;
+  if (check) {
+    const int64_t np = (int64_t)N * kPcProbe;
+    k_pc_probe<V><<<nblk(np, 256), 256>>>(w.P, np);
+    BEM_CUDA(cudaMemcpy(w.Rr, w.P, np * sizeof(V), cudaMemcpyDeviceToDevice));
+    BEM_TRY(gemm_t(s.bh, t, ct, CUBLAS_OP_N, N, kPcProbe, N, &one, w.X, N, w.P, N, &zero, w.W, N));
+    BEM_TRY(gemm_t(s.bh, t, ct, CUBLAS_OP_N, N, kPcProbe, N, &one, w.Ac, N, w.W, N, &mone, w.Rr, N));
+    // the first refinement correction X (A X V - V), into P, against X V
+    BEM_TRY(gemm_t(s.bh, t, ct, CUBLAS_OP_N, N, kPcProbe, N, &one, w.X, N, w.Rr, N, &zero, w.P, N));
+    k_pc_norms<V><<<1, 256>>>(w.P, w.W, np, w.nrm);
+    double h[2];
+    BEM_CUDA(cudaMemcpy(h, w.nrm, sizeof(h), cudaMemcpyDeviceToHost));
+    *resid = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+    if (!(*resid <= kPcCheck)) return BEM_OK;  // the caller rebuilds the block in FP64
+  }
+  k_store_pc<V><<<nblk((int64_t)N * ld, 256), 256>>>(w.X, N, ld, c->pc64 + off, c->pc32 + off);
+  BEM_CUDA(cudaGetLastError());
+  return BEM_OK;
+}
+
+int setup_precond(aim_ctx* c, int prec) {
+  if (prec < 0) {
+    if (c->pc_ready) return BEM_OK;
+    prec = BEM_C32;
+  }
+  if (c->pc_ready && c->pc_prec == prec) return BEM_OK;
+  if (prec != BEM_C32 && prec != BEM_C64) {
+    set_error("preconditioner build precision must be BEM_C32 or BEM_C64");
+    return BEM_EINVAL;
+  }
+  const double tst = wall_ms();
   const DGeo& g = *reinterpret_cast<const DGeo*>(c->geo_store);
   const int nobj = c->nobj;
   std::vector<int32_t> N(nobj), perm;
@@ -1646,98 +1937,58 @@ int setup_precond(aim_ctx* c) {
     for (int k = 0; k < n; ++k) perm.push_back(c->e0[i] + k);
     for (int k = 0; k < m; ++k) perm.push_back(c->ne + c->t0[i] + k);
   }
-  BEM_TRY(dalloc_t(c, &c->pc64, o));
-  BEM_TRY(dalloc_t(c, &c->pc32, o));
-  BEM_TRY(upload(c, &c->d_pcperm, perm.data(), perm.size()));
-  for (int k = 0; k < 2; ++k) {
-    BEM_TRY(dalloc_t(c, &c->pcw32[k], perm.size()));
-    BEM_TRY(dalloc_t(c, &c->pcw64[k], perm.size()));
-  }
-  // scratch (released at the end)
-  const size_t nn = (size_t)nmax * nmax, nm = (size_t)nmax * mmax, mm = (size_t)mmax * mmax,
-               NN = (size_t)Nmax * Nmax;
-  double2 *LA, *LP, *Zc, *Yc, *Ix, *FD, *T1, *T2, *A12, *A21, *Af, *X;
-  double2** bufs[] = {&LA, &LP, &Zc, &Yc, &Ix, &FD, &T1, &T2, &A12, &A21, &Af, &X};
-  size_t sizes[] = {nn, mm, nn, nn, nn, nm, nn, nn, nm, nm, NN, NN};
-  std::vector<void*> scratch;
-  int rc = BEM_OK;
-  for (int k = 0; k < 12 && rc == BEM_OK; ++k) {
-    cudaError_t e = cudaMalloc((void**)bufs[k], sizes[k] * sizeof(double2) + 16);
-    if (e != cudaSuccess) { set_error("preconditioner scratch: %s", cudaGetErrorString(e)); rc = BEM_ENOMEM; }
-    else scratch.push_back(*bufs[k]);
-  }
-  int64_t* ipiv = nullptr;
-  int* dinfo = nullptr;
-  if (rc == BEM_OK && (cudaMalloc(&ipiv, Nmax * sizeof(int64_t)) != cudaSuccess ||
-                       cudaMalloc(&dinfo, sizeof(int)) != cudaSuccess)) {
-    set_error("preconditioner scratch allocation failed");
-    rc = BEM_ENOMEM;
-  }
-  SolverScratch ss;
-  BlasHandle bh;
-  void* dwork = nullptr;
-  size_t dwsize = 0;
-  std::vector<char> hwork;
-  if (rc == BEM_OK && (cusolverDnCreate(&ss.h) != CUSOLVER_STATUS_SUCCESS ||
-                       cusolverDnCreateParams(&ss.p) != CUSOLVER_STATUS_SUCCESS ||
-                       cublasCreate(&bh.h) != CUBLAS_STATUS_SUCCESS)) {
-    set_error("cuSOLVER/cuBLAS handle creation failed");
-    rc = BEM_ECUDA;
-  }
-  const double k0 = c->k0;
-  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
-  for (int i = 0; i < nobj && rc == BEM_OK; ++i) {
-    const int e0 = c->e0[i], t0 = c->t0[i];
-    const int n = c->e1[i] - e0, m = c->t1[i] - t0, Nt = n + m;
-    k_obj_A<<<nblk((int64_t)n * n, 128), 128>>>(g, e0, n, k0, LA);
-    k_obj_P<<<nblk((int64_t)m * m, 128), 128>>>(g, t0, m, k0, LP);
-    k_unpack<<<nblk((int64_t)n * n, 256), 256>>>(c->f64.Z + c->zoff[i], n, c->zld[i], Zc);
-    k_unpack<<<nblk((int64_t)n * n, 256), 256>>>(c->f64.Y + c->zoff[i], n, c->zld[i], Yc);
-    cudaMemset(Ix, 0, (size_t)n * n * sizeof(double2));
-    cudaMemset(FD, 0, (size_t)m * n * sizeof(double2));
-    k_dense_ix<<<nblk(n, 128), 128>>>(c->d_ixcol, c->f64.ix, e0, n, Ix);
-    k_dense_fd<<<nblk(m, 128), 128>>>(c->d_tedge, c->f64.fdT, t0, m, e0, n, FD);
-    if (cudaGetLastError() != cudaSuccess) { set_error("preconditioner kernels failed"); rc = BEM_ECUDA; break; }
-    // T1 = L^A Y ; T2 = I_x - j k0 T1 ; T1 = T2 Z ; T1 += j k0 L^A  -> A11 in T1
-    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, one, LA, n, Yc, n, zero, T1, n);
-    if (rc) break;
-    BEM_CUDA(cudaMemcpy(T2, Ix, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice));
-    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, make_double2(0, -k0), LA, n, Yc, n, one, T2, n);
-    if (rc) break;
-    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, one, T2, n, Zc, n, zero, T1, n);
-    if (rc) break;
-    // T1 += j k0 L^A (as a GEMM with the identity would waste work; use axpy via cuBLAS)
-    {
-      cuDoubleComplex al = make_cuDoubleComplex(0, k0);
-      if (cublasZaxpy(bh.h, n * n, &al, (const cuDoubleComplex*)LA, 1, (cuDoubleComplex*)T1, 1) !=
-          CUBLAS_STATUS_SUCCESS) { set_error("cublasZaxpy failed"); rc = BEM_ECUDA; break; }
+  if (!c->pc64) {
+    BEM_TRY(dalloc_t(c, &c->pc64, o));
+    BEM_TRY(dalloc_t(c, &c->pc32, o));
+    BEM_TRY(upload(c, &c->d_pcperm, perm.data(), perm.size()));
+    for (int k = 0; k < 2; ++k) {
+      BEM_TRY(dalloc_t(c, &c->pcw32[k], perm.size()));
+      BEM_TRY(dalloc_t(c, &c->pcw64[k], perm.size()));
     }
-    // A12 = -(F D)^T L^Phi   (n x m)
-    rc = zgemm(bh.h, CUBLAS_OP_T, n, m, m, make_double2(-1, 0), FD, m, LP, m, zero, A12, n);
-    if (rc) break;
-    // A21 = F D - F D (Y Z)  (m x n): T2 = Y Z ; A21 = FD ; A21 -= FD T2
-    rc = zgemm(bh.h, CUBLAS_OP_N, n, n, n, one, Yc, n, Zc, n, zero, T2, n);
-    if (rc) break;
-    BEM_CUDA(cudaMemcpy(A21, FD, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToDevice));
-    rc = zgemm(bh.h, CUBLAS_OP_N, m, n, n, make_double2(-1, 0), FD, m, T2, n, one, A21, m);
-    if (rc) break;
-    k_bd_assemble<<<nblk((int64_t)Nt * Nt, 256), 256>>>(T1, A12, A21, n, m, k0, Af);
-    k_identity<<<nblk((int64_t)Nt * Nt, 256), 256>>>(X, Nt);
-    rc = lu_solve(ss, Af, X, Nt, ipiv, dinfo, &dwork, &dwsize, &hwork);
-    if (rc) break;
-    k_store_block<<<nblk((int64_t)Nt * ld[i], 256), 256>>>(X, Nt, ld[i], one, c->pc64 + off[i],
-                                                            c->pc32 + off[i]);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) { set_error("preconditioner store: %s", cudaGetErrorString(e)); rc = BEM_ECUDA; }
   }
-  cudaDeviceSynchronize();
-  for (void* p : scratch) cudaFree(p);
-  if (ipiv) cudaFree(ipiv);
-  if (dinfo) cudaFree(dinfo);
-  if (dwork) cudaFree(dwork);
-  if (rc != BEM_OK) return rc;
-  // persistent GEMV plan over the object-major blocks (autotuned launch shape)
-  {
+  c->pc_ready = false;
+  BEM_CUDA(cudaDeviceSynchronize());
+  // FP64 L^A and L^Phi of one object, the pair-moment scratch and the handles
+  double2 *LA = nullptr, *LP = nullptr;
+  BEM_CUDA(cudaMalloc(&LA, (size_t)nmax * nmax * sizeof(double2)));
+  std::unique_ptr<void, decltype(&cudaFree)> hold_la(LA, &cudaFree);
+  BEM_CUDA(cudaMalloc(&LP, (size_t)mmax * mmax * sizeof(double2)));
+  std::unique_ptr<void, decltype(&cudaFree)> hold_lp(LP, &cudaFree);
+  MomentScratch ms;
+  PcShared s;
+  PcWork<float> w32;
+  PcWork<double> w64;
+  if (cusolverDnCreate(&s.ss.h) != CUSOLVER_STATUS_SUCCESS ||
+      cusolverDnCreateParams(&s.ss.p) != CUSOLVER_STATUS_SUCCESS ||
+      cublasCreate(&s.bh) != CUBLAS_STATUS_SUCCESS) {
+    set_error("cuSOLVER/cuBLAS handle creation failed");
+    return BEM_ECUDA;
+  }
+  BEM_CUDA(cudaMalloc(&s.ipiv, Nmax * sizeof(int64_t)));
+  BEM_CUDA(cudaMalloc(&s.dinfo, sizeof(int)));
+  BEM_TRY(prec == BEM_C32 ? w32.alloc(nmax, Nmax) : w64.alloc(nmax, Nmax));
+  c->pc_nfp64 = 0;
+  c->pc_resid = 0;
+  for (int i = 0; i < nobj; ++i) {
+    const int n = c->e1[i] - c->e0[i], m = c->t1[i] - c->t0[i];
+    BEM_TRY(object_moments(c, g, i, std::complex<double>(c->k0, 0.0), false, &ms));
+    k_obj_assemble_A<<<nblk((int64_t)n * n, 128), 128>>>(g, c->e0[i], n, c->t0[i], m, ms.mom, LA);
+    k_obj_LP<<<nblk((int64_t)m * m, 256), 256>>>(ms.mom, m, LP);
+    BEM_CUDA(cudaGetLastError());
+    double r = -1;
+    if (prec == BEM_C32) {
+      BEM_TRY(pc_block<float>(c, g, i, LA, LP, w32, s, ld[i], off[i], true, &r));
+      c->pc_resid = std::max(c->pc_resid, r);
+    }
+    if (prec == BEM_C64 || !(r <= kPcCheck)) {
+      BEM_TRY(w64.alloc(nmax, Nmax));
+      BEM_TRY(pc_block<double>(c, g, i, LA, LP, w64, s, ld[i], off[i], false, &r));
+      c->pc_nfp64 += 1;
+    }
+  }
+  BEM_CUDA(cudaDeviceSynchronize());
+  // persistent GEMV plans over the object-major blocks (autotuned launch shape), made once
+  if (!c->pc_planned) {
     float pc_ms[2];
     BEM_TRY(autotune_gemv(c, N, off, ld, c->pc32, &c->pcplan, &c->pcplan64, pc_ms, nullptr));
     int dev = 0, nsm = 0;
@@ -1746,7 +1997,10 @@ int setup_precond(aim_ctx* c) {
     int* derr = nullptr;
     BEM_TRY(dalloc_t(c, &derr, 1));
     BEM_TRY(make_gemv_plan(c, nullptr, GemvCand{5, 16, 4, 4}, nsm, N, off, ld, derr, &c->pcmr));
+    c->pc_planned = true;
   }
+  c->pc_prec = prec;
+  c->pc_ms = wall_ms() - tst;
   c->pc_ready = true;
   return BEM_OK;
 }

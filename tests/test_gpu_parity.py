@@ -488,6 +488,25 @@ def test_precond_c32_matches_c64(prob):
     assert rel(u32, u64) < 1e-5
 
 
+def test_precond_build_precisions(prob):
+    """Block inverses built in complex FP32 (the default) give the product of the FP64-built ones
+    within the FP32 build's forward error: the blocks here have cond ~ 7e6, mostly from scaling,
+    and the blocks are formed from FP32 Z and C, so the product differs by ~2e-4 (1e-3 allowed),
+    far below what a preconditioner needs; the refinement-correction check stays below 1e-2 and
+    no block falls back to FP64."""
+    ctx = prob["ctx"]
+    rt = torch.from_numpy(synth.rand_cvec(ctx.n, 10)).cuda()
+    b64 = ctx.precond_setup(api.BEM_C64)
+    assert b64["prec"] == api.BEM_C64 and b64["fp64_blocks"] == ctx.nobj and b64["check"] is None
+    u64 = ctx.precond(rt, prec=api.BEM_C64).cpu().numpy()
+    b32 = ctx.precond_setup(api.BEM_C32)
+    assert b32["prec"] == api.BEM_C32 and b32["fp64_blocks"] == 0
+    assert 0 < b32["check"] < 1e-2
+    u32 = ctx.precond(rt, prec=api.BEM_C64).cpu().numpy()
+    assert rel(u32, u64) < 1e-3
+    assert ctx.precond_setup(api.BEM_C32) == b32  # built already: no rebuild
+
+
 def test_gmres_tight_solve_currents(prob, direct):
     """Solved to a 1e-11 residual (plain FP64), the surface currents h and j agree with the
     oracle's direct solution within 1e-4."""

@@ -51,6 +51,27 @@ def srr():
                 Lk=Lk, Kk=Kk, Z=Z, Y=Y, ix=ix, fd=op.fd_matrix(rw))
 
 
+def test_srr_sparse_internal_built(srr):
+    """At 1 THz (skin depth 79 nm, a 25th of the element size) every ring qualifies for the
+    sparse internal operator: it is built, checked against the dense Z at set-up and in use,
+    at under half of the dense Z's bytes; the oracle's sparse product (Sec. III-A, third item)
+    agrees with the dense Z h of the ring to 1e-10."""
+    from oracle import sparse_internal as si
+    ctx = srr["ctx"]
+    sp = ctx.internal_sparse(True)
+    assert sp["objects"] == ctx.nobj and sp["on"] and 0 < sp["band"] <= 256
+    assert sp["check"] is not None and sp["check"] < 1e-8
+    assert sp["bytes_c32"] < 0.5 * ctx.zy_bytes_c32 / 2
+    a, b = srr["rng"]
+    ixr = srr["ix"][a:b, a:b].toarray()
+    S = si.SparseZ(srr["rw"], 1e12, synth.SIGMA_AU, a, b, ix=srr["ix"],
+                   LK=(srr["Lk"], srr["Kk"] - 0.5 * ixr))
+    assert S.density < 0.2
+    h = synth.rand_cvec(b - a, 31)
+    assert rel(S(h), srr["Z"] @ h) < 1e-10
+    srr["S"] = S
+
+
 def test_srr_setup_matrices(srr):
     """L_{k_i} and K_{k_i} + I_x/2 of one ring before the LU (1e-12 of the largest entry), and
     the formed Z and Y_eq (Z well conditioned at this |k_i|: 1e-10; Y_eq 1e-6, the LU of the
@@ -64,9 +85,12 @@ def test_srr_setup_matrices(srr):
     assert rel(ctx.Y(RING), srr["Y"]) < 1e-6
 
 
+@pytest.mark.parametrize("sparse", [True, False])
 @pytest.mark.parametrize("prec,tol_z,tol_y", [(api.BEM_C32, 1e-5, 1e-5), (api.BEM_C64, 1e-10, 1e-6)])
-def test_srr_internal_rows(srr, prec, tol_z, tol_y):
+def test_srr_internal_rows(srr, prec, tol_z, tol_y, sparse):
+    """e = Z h (sparse Z_s or dense Z) and h_eq = Y_eq e on the oracle ring's rows."""
     ctx = srr["ctx"]
+    ctx.internal_sparse(sparse)
     a, b = srr["rng"]
     h = synth.rand_cvec(ctx.ne, 23)
     npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
@@ -76,12 +100,18 @@ def test_srr_internal_rows(srr, prec, tol_z, tol_y):
     e, heq = e.cpu().numpy()[a:b], heq.cpu().numpy()[a:b]
     assert rel(e, eo) < tol_z and max_rel(e, eo) < 3 * tol_z
     assert rel(heq, ho) < tol_y and max_rel(heq, ho) < 3 * tol_y
+    if sparse and "S" in srr:  # against the oracle's own sparse product as well
+        es = srr["S"](h[a:b])
+        assert rel(e, es) < tol_z and max_rel(e, es) < 3 * tol_z
+    ctx.internal_sparse(True)
 
 
+@pytest.mark.parametrize("sparse", [True, False])
 @pytest.mark.parametrize("case", ["both", "q0"])
 @pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-7)])
-def test_srr_system_rows(srr, prec, tol, case):
+def test_srr_system_rows(srr, prec, tol, case, sparse):
     ctx, A, rw, k0 = srr["ctx"], srr["A"], srr["rw"], srr["k0"]
+    ctx.internal_sparse(sparse)
     re, rt = srr["rows_e"], srr["rows_t"]
     a, b = srr["rng"]
     h = np.zeros(ctx.ne, complex)
@@ -99,6 +129,25 @@ def test_srr_system_rows(srr, prec, tol, case):
     y2 = srr["fd"] @ j + 1j * k0 * q
     check_system(np.concatenate([y[re], y[ctx.ne + rt]]), np.concatenate([y1[re], y2[rt]]),
                  ctx.ne, tol, rows=(re, rt))
+    ctx.internal_sparse(True)
+
+
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-6), (api.BEM_C64, 1e-12)])
+def test_srr_sparse_matches_dense_everywhere(srr, prec, tol):
+    """The whole system product and a 3-vector batch with the sparse Z_s against the dense Z on
+    the same device (every ring, not only the oracle's)."""
+    ctx = srr["ctx"]
+    npdt = np.complex64 if prec == api.BEM_C32 else np.complex128
+    x = torch.from_numpy(synth.rand_cvec(ctx.n, 26).astype(npdt)).cuda()
+    xb = torch.from_numpy(np.stack([synth.rand_cvec(ctx.n, 27 + r) for r in range(3)]).astype(npdt)).cuda()
+    out = {}
+    for sparse in (False, True):
+        ctx.internal_sparse(sparse)
+        out[sparse] = (ctx.matvec(x, prec=prec).cpu().numpy(),
+                       ctx.matvec_batch(xb, prec=prec).cpu().numpy())
+    for a, b in zip(out[True], out[False]):
+        for ar, br in zip(a.reshape(-1, ctx.n), b.reshape(-1, ctx.n)):
+            check_system(ar, br, ctx.ne, tol)
 
 
 def test_srr_chosen_solve(srr):
@@ -109,3 +158,5 @@ def test_srr_chosen_solve(srr):
     x, info = ctx.solve(b, tol=1e-6, restart=100, max_iter=500, prec_mode=api.BEM_C32, precond=1)
     assert info["status"] == api.BEM_OK and info["resid_true"] <= 1e-6
     assert info["iters"] < 100
+    pb = ctx.precond_build  # built in FP32 with every block passing its check
+    assert pb["prec"] == api.BEM_C32 and pb["fp64_blocks"] == 0 and pb["check"] < 1e-3
