@@ -243,6 +243,9 @@ struct aim_ctx {
   std::vector<int32_t> anc;                        // [(ne+nt)*3]
   std::vector<int64_t> rowA, rowP;                 // near CSR row pointers
   std::vector<int32_t> colA, colP;
+  // the same columns as one list per anchor node (cl) and each row's offset into it (lst)
+  std::vector<int64_t> lstA, lstP;
+  std::vector<int32_t> clA, clP;
   std::vector<int64_t> zoff;                       // element offset of block i
   std::vector<int32_t> zld;
   int64_t zelems = 0;
@@ -275,7 +278,11 @@ struct aim_ctx {
   int32_t* d_pnodeT = nullptr;  // [ng]
   int32_t nwE = 0, nwT = 0;
   int64_t* d_rowA = nullptr;
-  int32_t* d_colA = nullptr;
+  int32_t* d_colA = nullptr;  // per entry (set-up kernels)
+  int64_t* d_lstA = nullptr;  // per row: offset of its anchor's list in d_clA
+  int32_t* d_clA = nullptr;
+  int64_t* d_lstP = nullptr;
+  int32_t* d_clP = nullptr;
   int64_t* d_rowP = nullptr;
   int32_t* d_colP = nullptr;
   int32_t* d_ixcol = nullptr;  // [ne][4]

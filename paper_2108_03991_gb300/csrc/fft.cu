@@ -1096,27 +1096,40 @@ __device__ __forceinline__ void wline_inv(float2* v, const float2* __restrict__ 
   dft_reg<float2, M>(v, tw, P / M, true);
 }
 
-// x forward: warp w takes row y0 + w of data plane z; its Px spectrum values go to
-// X[c][kx][z][y] straight from the registers
+// x forward: warp w takes row y0 + w of data plane z; its Px spectrum values meet the other
+// seven rows' in a shared tile [row][kx] (every 32nd entry skipped: two lanes per bank at most)
+// and leave as X[c][kx][z][y0 .. y0 + 7], 64-byte runs, instead of one 8-byte value per kx
 template <int M>
 __global__ void __launch_bounds__(256) k_wslab_xfwd(const float2* __restrict__ sigma,
                                                     float2* __restrict__ ws,
                                                     const float2* __restrict__ twx, SlabArgs a) {
+  extern __shared__ float2 tile[];  // [8 rows][TS]
+  constexpr int P = 32 * M, TS = P + P / 32 + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = blockIdx.x * 8 + warp, z = blockIdx.y, c = blockIdx.z;
-  if (y >= a.ny) return;  // warp-uniform
-  const float2* src = sigma + c * a.ng + ((int64_t)z * a.ny + y) * a.nx;
-  float2 v[M];
+  const int y0 = blockIdx.x * 8, y = y0 + warp, z = blockIdx.y, c = blockIdx.z;
+  if (y < a.ny) {  // warp-uniform
+    const float2* src = sigma + c * a.ng + ((int64_t)z * a.ny + y) * a.nx;
+    float2 v[M];
 #pragma unroll
-  for (int n1 = 0; n1 < M; ++n1) {
-    const int x = lane + 32 * n1;
-    v[n1] = x < a.nx ? src[x] : make_float2(0.f, 0.f);
+    for (int n1 = 0; n1 < M; ++n1) {
+      const int x = lane + 32 * n1;
+      v[n1] = x < a.nx ? src[x] : make_float2(0.f, 0.f);
+    }
+    wline_fwd<M>(v, twx, lane);
+    const int k2 = brev_l<32>(lane);
+#pragma unroll
+    for (int k1 = 0; k1 < M; ++k1) {
+      const int kx = k1 + M * k2;
+      tile[warp * TS + kx + (kx >> 5)] = v[k1];
+    }
   }
-  wline_fwd<M>(v, twx, lane);
-  float2* dst = ws + c * a.P3 + (int64_t)z * a.ny + y;
-  const int k2 = brev_l<32>(lane);
-#pragma unroll
-  for (int k1 = 0; k1 < M; ++k1) dst[(int64_t)(k1 + M * k2) * a.nz * a.ny] = v[k1];
+  __syncthreads();
+  const int nr = min(8, a.ny - y0);
+  float2* dst = ws + c * a.P3 + (int64_t)z * a.ny + y0;
+  for (int i = threadIdx.x; i < 8 * P; i += blockDim.x) {
+    const int kx = i >> 3, r = i & 7;
+    if (r < nr) dst[(int64_t)kx * a.nz * a.ny + r] = tile[r * TS + kx + (kx >> 5)];
+  }
 }
 
 // y-z fused for one kx: warp z transforms its y line, the nz lines meet in shared memory
@@ -1177,20 +1190,31 @@ __global__ void __launch_bounds__(256) k_wslab_yz(float2* __restrict__ ws,
   }
 }
 
-// x inverse: warp w gathers row y0 + w of plane z from X in the transform's order, inverts it
-// and writes the nx kept values
+// x inverse: the CTA reads X[c][kx][z][y0 .. y0 + 7] as 64-byte runs into the shared tile; warp
+// w takes row y0 + w from it in the transform's order, inverts it and writes the nx kept values
 template <int M>
 __global__ void __launch_bounds__(256) k_wslab_xinv(const float2* __restrict__ ws,
                                                     float2* __restrict__ phi,
                                                     const float2* __restrict__ twx, SlabArgs a) {
+  extern __shared__ float2 tile[];  // [8 rows][TS]
+  constexpr int P = 32 * M, TS = P + P / 32 + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = blockIdx.x * 8 + warp, z = blockIdx.y, c = blockIdx.z;
+  const int y0 = blockIdx.x * 8, y = y0 + warp, z = blockIdx.y, c = blockIdx.z;
+  const int nr = min(8, a.ny - y0);
+  const float2* src = ws + c * a.P3 + (int64_t)z * a.ny + y0;
+  for (int i = threadIdx.x; i < 8 * P; i += blockDim.x) {
+    const int kx = i >> 3, r = i & 7;
+    if (r < nr) tile[r * TS + kx + (kx >> 5)] = src[(int64_t)kx * a.nz * a.ny + r];
+  }
+  __syncthreads();
   if (y >= a.ny) return;  // warp-uniform
-  const float2* src = ws + c * a.P3 + (int64_t)z * a.ny + y;
   const int k2 = brev_l<32>(lane);
   float2 v[M];
 #pragma unroll
-  for (int k1 = 0; k1 < M; ++k1) v[k1] = src[(int64_t)(k1 + M * k2) * a.nz * a.ny];
+  for (int k1 = 0; k1 < M; ++k1) {
+    const int kx = k1 + M * k2;
+    v[k1] = tile[warp * TS + kx + (kx >> 5)];
+  }
   wline_inv<M>(v, twx, lane);
   float2* dst = phi + c * a.ng + ((int64_t)z * a.ny + y) * a.nx;
 #pragma unroll
@@ -1254,14 +1278,15 @@ static int slab_conv(aim_ctx* c, PrecBuf<float>& b, const float2* sigma, float2*
   if (a.Px == a.Py && (a.Px == 1024 || a.Px == 512) && a.nz <= 8 && a.Pz == 15) {
     const dim3 gw((a.ny + 7) / 8, a.nz, ncomp);
     const size_t ssm = (size_t)a.nz * a.Py * sizeof(float2);
+    const size_t tsm = 8 * (size_t)(a.Px + a.Px / 32 + 1) * sizeof(float2);  // the x passes' tile
     if (a.Px == 1024) {
-      k_wslab_xfwd<32><<<gw, 256, 0, s>>>(sigma, ws, b.tw[0], a);
+      k_wslab_xfwd<32><<<gw, 256, tsm, s>>>(sigma, ws, b.tw[0], a);
       k_wslab_yz<32, 15><<<dim3(a.Px, ncomp), 256, ssm, s>>>(ws, b.Gs, b.tw[1], b.tw[2], a);
-      k_wslab_xinv<32><<<gw, 256, 0, s>>>(ws, phi, b.tw[0], a);
+      k_wslab_xinv<32><<<gw, 256, tsm, s>>>(ws, phi, b.tw[0], a);
     } else {
-      k_wslab_xfwd<16><<<gw, 256, 0, s>>>(sigma, ws, b.tw[0], a);
+      k_wslab_xfwd<16><<<gw, 256, tsm, s>>>(sigma, ws, b.tw[0], a);
       k_wslab_yz<16, 15><<<dim3(a.Px, ncomp), 256, ssm, s>>>(ws, b.Gs, b.tw[1], b.tw[2], a);
-      k_wslab_xinv<16><<<gw, 256, 0, s>>>(ws, phi, b.tw[0], a);
+      k_wslab_xinv<16><<<gw, 256, tsm, s>>>(ws, phi, b.tw[0], a);
     }
     BEM_CUDA(cudaGetLastError());
     return BEM_OK;
@@ -1289,6 +1314,10 @@ int fft_init_attrs() {
   for (int pz : {8, 9, 10, 12, 15, 16, 0})
     BEM_CUDA(cudaFuncSetAttribute(slab_yz_kernel(pz), cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   BEM_CUDA(cudaFuncSetAttribute(k_wslab_yz<32, 15>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_wslab_xfwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_wslab_xinv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_wslab_xfwd<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  BEM_CUDA(cudaFuncSetAttribute(k_wslab_xinv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   BEM_CUDA(cudaFuncSetAttribute(k_wslab_yz<16, 15>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   BEM_CUDA(cudaFuncSetAttribute(k_slab_xinv, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return BEM_OK;

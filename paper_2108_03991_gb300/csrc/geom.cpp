@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -228,7 +229,10 @@ int build_geometry(aim_ctx* c, const bem_mesh* m, const aim_grid* g) {
     }
   }
   // near-region sparsity: pairs whose anchors differ by <= r_near in every axis
-  auto near_csr = [&](int first, int count, std::vector<int64_t>* row, std::vector<int32_t>* col) {
+  // (row, col: the CSR; lst, cl: each row's offset into cl, which holds one column list per
+  // anchor node: rows anchored at the same node have the same near columns)
+  auto near_csr = [&](int first, int count, std::vector<int64_t>* row, std::vector<int32_t>* col,
+                      std::vector<int64_t>* lst, std::vector<int32_t>* cl) {
     std::vector<int64_t> key(count);
     for (int i = 0; i < count; ++i) {
       const int32_t* q = &c->anc[3 * (size_t)(first + i)];
@@ -241,6 +245,9 @@ int build_geometry(aim_ctx* c, const bem_mesh* m, const aim_grid* g) {
     for (int i = 0; i < count; ++i) sk[i] = key[ord[i]];
     row->assign(count + 1, 0);
     col->clear();
+    lst->assign(count, 0);
+    cl->clear();
+    std::unordered_map<int64_t, int64_t> list_of;  // anchor node -> offset of its list in cl
     const int R = c->r_near;
     std::vector<int32_t> buf;
     for (int i = 0; i < count; ++i) {
@@ -258,10 +265,16 @@ int build_geometry(aim_ctx* c, const bem_mesh* m, const aim_grid* g) {
       std::sort(buf.begin(), buf.end());
       col->insert(col->end(), buf.begin(), buf.end());
       (*row)[i + 1] = (int64_t)col->size();
+      auto found = list_of.find(key[i]);
+      if (found == list_of.end()) {
+        found = list_of.emplace(key[i], (int64_t)cl->size()).first;
+        cl->insert(cl->end(), buf.begin(), buf.end());
+      }
+      (*lst)[i] = found->second;
     }
   };
-  near_csr(0, ne, &c->rowA, &c->colA);
-  near_csr(ne, nt, &c->rowP, &c->colP);
+  near_csr(0, ne, &c->rowA, &c->colA, &c->lstA, &c->clA);
+  near_csr(ne, nt, &c->rowP, &c->colP, &c->lstP, &c->clP);
   return BEM_OK;
 }
 

@@ -733,9 +733,12 @@ static void project_t(const aim_ctx* c, const R* WT, const typename C2<R>::T* q,
 template <typename V, typename R>
 __device__ __forceinline__ V jk0(V a, R k0) { return mk(-k0 * a.y, k0 * a.x); }
 
-// acc += sum over the CSR row [i0, i1) of val[i] * x[col[i]], one warp; four independent
-// entries per lane are in flight at a time (the column load and the gather it feeds are a
-// dependent pair, so a plain loop would wait on both for every entry)
+// acc += sum over the CSR row [i0, i1) of val[i] * x[col[i]], one warp (the callers pass the
+// row's values and its anchor node's column list, shared by every row anchored there); four
+// independent entries per lane are in flight at a time (the column load and the gather it feeds
+// are a dependent pair, so a plain loop would wait on both for every entry). Eight per lane,
+// predicated, so that a whole row of up to 256 entries is one round, ran 30% slower (more
+// registers, fewer resident warps).
 template <typename V>
 __device__ __forceinline__ void near_row(const V* __restrict__ val, const int32_t* __restrict__ col,
                                          const V* __restrict__ x, int64_t i0, int64_t i1, int lane,
@@ -758,7 +761,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_rows_t(
     const R* __restrict__ WP, const int32_t* __restrict__ node,
     const typename C2<R>::T* __restrict__ phi, const int64_t* __restrict__ rowP,
-    const int32_t* __restrict__ colP, const typename C2<R>::T* __restrict__ LP,
+    const int64_t* __restrict__ lstP, const int32_t* __restrict__ colP,
+    const typename C2<R>::T* __restrict__ LP,
     const typename C2<R>::T* __restrict__ q, int nt, int nx, int ny,
     typename C2<R>::T* __restrict__ out, int64_t phi_rs = 0, int64_t q_rs = 0, int64_t out_rs = 0) {
   typedef typename C2<R>::T V;
@@ -773,7 +777,7 @@ __global__ void __launch_bounds__(256) k_rows_t(
     const V f = phi[node[t] + node_offset(lane, nx, ny)];
     acc = mk(w * f.x, w * f.y);
   }
-  near_row(LP, colP, q, rowP[t], rowP[t + 1], lane, acc);
+  near_row(LP + rowP[t], colP + lstP[t], q, 0, rowP[t + 1] - rowP[t], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) out[t] = acc;
 }
@@ -790,7 +794,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_rows_e(
     const R* __restrict__ WA, const int32_t* __restrict__ node,
     const typename C2<R>::T* __restrict__ phi, int64_t ng, const int64_t* __restrict__ rowA,
-    const int32_t* __restrict__ colA, const typename C2<R>::T* __restrict__ LA,
+    const int64_t* __restrict__ lstA, const int32_t* __restrict__ colA,
+    const typename C2<R>::T* __restrict__ LA,
     const typename C2<R>::T* __restrict__ j, const R* __restrict__ ix,
     const int32_t* __restrict__ ixcol, const typename C2<R>::T* __restrict__ e,
     const R* __restrict__ fdE, const int32_t* __restrict__ et,
@@ -838,7 +843,7 @@ __global__ void __launch_bounds__(256) k_rows_e(
       acc.y += w * f.y;
     }
   }
-  if (!anear) near_row(LA, colA, j, rowA[m], rowA[m + 1], lane, acc);
+  if (!anear) near_row(LA + rowA[m], colA + lstA[m], j, 0, rowA[m + 1] - rowA[m], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) {
     if (anear) {
@@ -870,6 +875,7 @@ __global__ void __launch_bounds__(256) k_rows_e(
 // matvec's first row that needs only j, run beside the convolution
 template <typename R>
 __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA,
+                                                const int64_t* __restrict__ lstA,
                                                 const int32_t* __restrict__ colA,
                                                 const typename C2<R>::T* __restrict__ LA,
                                                 const typename C2<R>::T* __restrict__ j, int ne,
@@ -881,7 +887,7 @@ __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA
   const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (m >= ne) return;
   V acc = czero<V>();
-  near_row(LA, colA, j, rowA[m], rowA[m + 1], lane, acc);
+  near_row(LA + rowA[m], colA + lstA[m], j, 0, rowA[m + 1] - rowA[m], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) a[m] = acc;
 }
@@ -911,7 +917,7 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
   project_t<R>(c, b.WPT, x + ne, b.bsT, c->side, nrhs, N);
   BEM_TRY(fft_conv<R>(c, b, b.bsT, b.bsT, nrhs, b.bwsT, c->side));
-  k_rows_t<R><<<dim3(nb(nt, 8), nrhs), 256, 0, c->side>>>(b.WP, c->d_nodeT, b.bsT, c->d_rowP, c->d_colP,
+  k_rows_t<R><<<dim3(nb(nt, 8), nrhs), 256, 0, c->side>>>(b.WP, c->d_nodeT, b.bsT, c->d_rowP, c->d_lstP, c->d_clP,
                                                            b.LP, x + ne, nt, nx, ny, b.bp, ng, N, nt);
   auto gemv = [&](const V* A, V* out, const V* hs) -> int {
     return c->gmr.ntasks > 0 ? run_gemv_mr<R>(c->gmr, A, x, out, nrhs, N, hs, s)
@@ -920,7 +926,7 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   BEM_TRY(gemv(b.C, b.bj, x));  // j_r = h_r - C h_r
   BEM_CUDA(cudaEventRecord(c->ev_c, s));
   BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
-  k_near_e<R><<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.bj, ne, b.ban,
+  k_near_e<R><<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.bj, ne, b.ban,
                                                            N, ne);
   BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
   if (c->zsp_on)  // e_r = Z_s h_r, the sparse internal operator
@@ -939,7 +945,7 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   rs.an = ne;
   rs.y = N;
   k_rows_e<R><<<dim3(nb(ne, 8) + nb(nt, 256), nrhs), 256, 0, s>>>(
-      b.WA, c->d_nodeE, b.bsE, ng, c->d_rowA, c->d_colA, b.LA, b.bj, b.ix, c->d_ixcol, b.be, b.fdE,
+      b.WA, c->d_nodeE, b.bsE, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.bj, b.ix, c->d_ixcol, b.be, b.fdE,
       c->d_et, b.bp, ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, x + ne, b.ban, rs);
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
@@ -977,14 +983,14 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
   if (which == AIM_OP_LA) {
     project_e<R>(c, b.WAT, x, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
-    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
+    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA,
                                           x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
                                           nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr, nullptr);
   } else if (which == AIM_OP_LPHI) {
     V* sq = b.sigma + 3 * ng;
     project_t<R>(c, b.WPT, x, sq, s);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, s));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, x, nt,
+    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, x, nt,
                                           nx, ny, y);
   } else if (which == AIM_OP_EXT) {
     // both external operators of Eq. AEFIEoutJ, as the system matvec runs them: L^A j on the
@@ -995,12 +1001,12 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
+    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, q,
                                                 nt, nx, ny, y + ne);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     project_e<R>(c, b.WAT, x, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
-    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA, b.LA,
+    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA,
                                           x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
                                           nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr, nullptr);
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
@@ -1022,7 +1028,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     if (za < 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_colP, b.LP, q,
+    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, q,
                                                 nt, nx, ny, b.p);
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
@@ -1033,7 +1039,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
       BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
     BEM_CUDA(cudaEventRecord(c->ev_c, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
-    k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_colA, b.LA, b.j, ne, b.anear);
+    k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.j, ne, b.anear);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     if (za == 2) {  // e = Z h right after j's GEMV on the main stream, whole GPU
       BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
@@ -1047,7 +1053,7 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_z, 0));
-    k_rows_e<R><<<nb(ne, 8) + nb(nt, 256), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_colA,
+    k_rows_e<R><<<nb(ne, 8) + nb(nt, 256), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA,
                                                b.LA, b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p,
                                                ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q,
                                                b.anear);

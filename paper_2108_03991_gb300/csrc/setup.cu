@@ -1398,6 +1398,9 @@ static int setup_near(aim_ctx* c, const DGeo& g) {
     BEM_TRY(upload(c, &d_rows, rows.data(), rows.size()));
     BEM_TRY(upload(c, &c->d_rowA, c->rowA.data(), c->rowA.size()));
     BEM_TRY(upload(c, &c->d_colA, c->colA.data(), c->colA.size()));
+    BEM_TRY(upload(c, &c->d_lstA, c->lstA.data(), c->lstA.size()));
+    if (c->clA.empty()) c->clA.push_back(0);  // no near pairs: a valid (unread) list
+    BEM_TRY(upload(c, &c->d_clA, c->clA.data(), c->clA.size()));
     BEM_TRY(dalloc_t(c, &c->f64.LA, nnz));
     BEM_TRY(dalloc_t(c, &c->f32.LA, nnz));
     if (nnz)
@@ -1415,6 +1418,9 @@ static int setup_near(aim_ctx* c, const DGeo& g) {
     BEM_TRY(upload(c, &d_rows, rows.data(), rows.size()));
     BEM_TRY(upload(c, &c->d_rowP, c->rowP.data(), c->rowP.size()));
     BEM_TRY(upload(c, &c->d_colP, c->colP.data(), c->colP.size()));
+    BEM_TRY(upload(c, &c->d_lstP, c->lstP.data(), c->lstP.size()));
+    if (c->clP.empty()) c->clP.push_back(0);
+    BEM_TRY(upload(c, &c->d_clP, c->clP.data(), c->clP.size()));
     BEM_TRY(dalloc_t(c, &c->f64.LP, nnz));
     BEM_TRY(dalloc_t(c, &c->f32.LP, nnz));
     if (nnz)
