@@ -200,8 +200,11 @@ def run_reference(args, rank, world):
 
 # DRAM bytes (read + write) per launch of the GEMV shapes captured with ncu on the split-ring
 # array, keyed by (rings per side, "pair" for the paired launch of C and Z, kind, CTAs per SM,
-# split, loads in flight) as aim_info reports them; a launch of another shape reports none
-PROFILED_GEMV: dict = {}
+# split, loads in flight) as aim_info reports them; a launch of another shape reports none.
+# The C GEMV of the 32 x 32 array: captured on the 8 x 8 array in the same launch shape
+# (426,572,032 + 9,975,552 B per launch, profiles/gemv_C_srr_array.md) and scaled by the 16
+# times as many rings (every ring has the same 912 x 912 block)
+PROFILED_GEMV: dict = {(32, "one", 5, 16, 2, 4): 16 * (426572032 + 9975552)}
 
 
 def gemv_traffic(ctx, rings, paired=False):
