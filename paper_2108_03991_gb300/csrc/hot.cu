@@ -832,6 +832,24 @@ __global__ void __launch_bounds__(256) k_rows_e(
   }
   const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (m >= ne) return;
+  // mode 1: the lanes the stencil leaves free take the sparse terms of row 1, each its own
+  // dependent pair of loads, at the same time as the stencil's (lanes 27-30: (I_x e)_m, lane 31:
+  // -((F D)^T p)_m); the row's sum is then one reduction of j k0 (a part) + (these terms)
+  V b = czero<V>();
+  if (mode == 1 && lane >= 27) {
+    if (lane < 31) {
+      const int i = lane - 27;
+      const V ev = e[ixcol[4 * m + i]];
+      const R c = ix[4 * m + i];
+      b.x = c * ev.x;
+      b.y = c * ev.y;
+    } else {
+      const V pp = p[et[2 * m]], pm = p[et[2 * m + 1]];
+      const R cp = fdE[2 * m], cm = fdE[2 * m + 1];
+      b.x = -cp * pp.x + cm * pm.x;
+      b.y = -cp * pp.y + cm * pm.y;
+    }
+  }
   V acc = czero<V>();
   if (lane < 27) {
     const int64_t nd = node[m] + node_offset(lane, nx, ny);
@@ -844,30 +862,20 @@ __global__ void __launch_bounds__(256) k_rows_e(
     }
   }
   if (!anear) near_row(LA + rowA[m], colA + lstA[m], j, 0, rowA[m + 1] - rowA[m], lane, acc);
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    if (anear) {
-      const V an = anear[m];
-      acc.x += an.x;
-      acc.y += an.y;
-    }
-    if (mode == 0) {
-      y[m] = acc;
-    } else {
-      V s = jk0(acc, k0);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const V ev = e[ixcol[4 * m + i]];
-        const R c = ix[4 * m + i];
-        s.x += c * ev.x;
-        s.y += c * ev.y;
-      }
-      const V pp = p[et[2 * m]], pm = p[et[2 * m + 1]];
-      const R cp = fdE[2 * m], cm = fdE[2 * m + 1];
-      s.x += -cp * pp.x + cm * pm.x;
-      s.y += -cp * pp.y + cm * pm.y;
-      y[m] = s;
-    }
+  if (anear && lane == 0) {
+    const V an = anear[m];
+    acc.x += an.x;
+    acc.y += an.y;
+  }
+  if (mode == 0) {
+    acc = warp_sum(acc);
+    if (lane == 0) y[m] = acc;
+  } else {
+    V t = jk0(acc, k0);
+    t.x += b.x;
+    t.y += b.y;
+    t = warp_sum(t);
+    if (lane == 0) y[m] = t;
   }
 }
 
