@@ -404,6 +404,16 @@ int bem_convnet_run(int nx, int ny, int nz, const float* w_host, const float* x,
  * processors per task; returns the schedule length C_max (negative on error). */
 double bem_part_schedule(int ntask, const double* W, int P, int p_cutoff, int32_t* Pi);
 
+/* The ordering behind the sparse internal operator's band (aim_internal_sparse), host only:
+ * reverse Cuthill-McKee (Cuthill and McKee 1969, reversed) of a symmetric pattern of n
+ * vertices given as HOST CSR (rowptr[n + 1], cols[rowptr[n]]; self loops ignored): from each
+ * component's vertex of least degree (lowest index on ties), breadth first with the unvisited
+ * neighbours in increasing degree (ties in the order of the row's columns), the whole sequence
+ * reversed. order[r] (HOST, n) receives the
+ * vertex at position r. Errors: BEM_EINVAL (bad pointers, decreasing row pointers, a column
+ * outside [0, n)). The pattern's symmetry is the caller's to ensure. */
+int bem_rcm_order(int n, const int32_t* rowptr, const int32_t* cols, int32_t* order);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "bem_net_apply", "bem_convnet_run", "aim_gemv_select", "aim_gemv_plan",
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
-           "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse"]
+           "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order"]
 
 
 class BemError(RuntimeError):
@@ -146,6 +146,22 @@ def part_schedule(W, P, p_cutoff=20):
     if cmax < 0:
         raise BemError(-1, lib().bem_last_error().decode())
     return Pi, cmax
+
+
+def rcm_order(rowptr, cols):
+    """Reverse Cuthill-McKee order of a symmetric CSR pattern (bem_rcm_order): order[r] is the
+    vertex at position r."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(cols, dtype=np.int32)
+    n = rp.size - 1
+    order = np.zeros(max(n, 0), dtype=np.int32)
+    L = lib()
+    L.bem_rcm_order.argtypes = [C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_int32)]
+    _check(L.bem_rcm_order(n, rp.ctypes.data_as(C.POINTER(C.c_int32)),
+                           ci.ctypes.data_as(C.POINTER(C.c_int32)),
+                           order.ctypes.data_as(C.POINTER(C.c_int32))))
+    return order
 
 
 def blockdiag_gemv(sizes, A, x, y, nrhs=1, prec=BEM_C32):

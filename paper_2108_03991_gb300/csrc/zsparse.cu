@@ -702,3 +702,28 @@ void zsp_stats(const aim_ctx* c, int64_t* out) {
 }
 
 }  // namespace bem
+
+extern "C" int bem_rcm_order(int n, const int32_t* rowptr, const int32_t* cols, int32_t* order) {
+  if (n < 0 || (n > 0 && (!rowptr || !order || (rowptr[n] > 0 && !cols)))) {
+    bem::set_error("bem_rcm_order: bad arguments");
+    return BEM_EINVAL;
+  }
+  std::vector<int> rp(n + 1, 0), ci;  // the pattern without self loops
+  for (int i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) {
+      bem::set_error("bem_rcm_order: row pointers decrease at row %d", i);
+      return BEM_EINVAL;
+    }
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      if (cols[k] < 0 || cols[k] >= n) {
+        bem::set_error("bem_rcm_order: column %d out of range at row %d", cols[k], i);
+        return BEM_EINVAL;
+      }
+      if (cols[k] != i) ci.push_back(cols[k]);
+    }
+    rp[i + 1] = (int)ci.size();
+  }
+  const std::vector<int> ord = bem::rcm_order(n, rp, ci);
+  for (int i = 0; i < n; ++i) order[i] = ord[i];
+  return BEM_OK;
+}

@@ -61,3 +61,60 @@ def test_part_schedule_rejects_unsorted(L):
 
 def test_last_error_empty_string(L):
     assert isinstance(L.bem_last_error(), bytes)
+
+
+def _bandwidth(rp, ci, order):
+    pos = np.empty(len(order), dtype=np.int64)
+    pos[order] = np.arange(len(order))
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return int(np.max(np.abs(pos[rows] - pos[ci]))) if len(ci) else 0
+
+
+def test_rcm_order_grid_graph(L):
+    """The host ordering behind the sparse internal operator's band, on a 30 x 20 grid graph with
+    shuffled labels: a permutation whose bandwidth is that of a row-by-row ordering (20, up to
+    one), as SciPy's reverse Cuthill-McKee finds."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    nx, ny = 30, 20
+    rng = np.random.default_rng(4)
+    lab = rng.permutation(nx * ny)
+    rows, cols = [], []
+    for x in range(nx):
+        for y in range(ny):
+            for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                if 0 <= x + dx < nx and 0 <= y + dy < ny:
+                    rows.append(lab[x * ny + y])
+                    cols.append(lab[(x + dx) * ny + y + dy])
+    M = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(nx * ny, nx * ny))
+    M.sort_indices()
+    order = api.rcm_order(M.indptr, M.indices)
+    assert np.array_equal(np.sort(order), np.arange(nx * ny))
+    ref = reverse_cuthill_mckee(M, symmetric_mode=True)
+    assert _bandwidth(M.indptr, M.indices, order) <= min(21, _bandwidth(M.indptr, M.indices, ref) + 2)
+
+
+def test_rcm_order_ring_pattern(L):
+    """On the kept pattern of one gold split ring at 1 THz (the oracle's reading: supports within
+    23 skin depths) the half-bandwidth stays near SciPy's (113) and below the product kernel's
+    limit of 192."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    from oracle import operators as op, sparse_internal as si
+    from oracle.rwg import from_mesh
+    from paper_2108_03991_gb300 import synth
+    mesh, _, freq = synth.srr_array_config(2, 1)
+    rw = from_mesh(mesh)
+    delta = si.skin_depth(op.k0_of(freq), op.eps_rc(mesh.sigma[0], freq))
+    M = sp.csr_matrix(si.pattern(rw, 0, rw.ne, delta))
+    M.sort_indices()
+    order = api.rcm_order(M.indptr, M.indices)
+    assert np.array_equal(np.sort(order), np.arange(rw.ne))
+    b = _bandwidth(M.indptr, M.indices, order)
+    bref = _bandwidth(M.indptr, M.indices, reverse_cuthill_mckee(M, symmetric_mode=True))
+    assert b <= 1.1 * bref + 2 and b <= 192
+
+
+def test_rcm_order_rejects_bad_columns(L):
+    with pytest.raises(api.BemError):
+        api.rcm_order(np.array([0, 1, 2]), np.array([1, 5]))
