@@ -113,7 +113,8 @@ const char* bem_last_error(void);
  * set-up (aim_internal_sparse), [37]=objects on that operator (0: none built), [38]=1 while it
  * is in use, [39]=its largest half-bandwidth, [40]=its bytes per product in complex FP32,
  * [41]=its set-up check |Z_s h - Z h| / |Z h| (largest over the objects) in units of 1e-15
- * (-1: none). Writes min(n, 42) entries. */
+ * (-1: none), [42]=1 if one of its products had a bounded wait time out (that product's e is
+ * invalid; reading it synchronises the device). Writes min(n, 43) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Sparse internal operator at high frequency (Sec. III-A, third item of the internal problem:

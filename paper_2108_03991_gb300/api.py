@@ -235,8 +235,8 @@ class Context:
         self._read_info()
 
     def _read_info(self):
-        info = (C.c_int64 * 42)()
-        _check(lib().aim_info(self.h, info, 42))
+        info = (C.c_int64 * 43)()
+        _check(lib().aim_info(self.h, info, 43))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -262,7 +262,8 @@ class Context:
         # sparse internal operator at high frequency (aim_internal_sparse)
         self.sparse_internal = {"setup_s": info[36] * 1e-6, "objects": info[37], "on": bool(info[38]),
                                 "band": info[39], "bytes_c32": info[40],
-                                "check": None if info[41] < 0 else info[41] * 1e-15}
+                                "check": None if info[41] < 0 else info[41] * 1e-15,
+                                "wait_timed_out": bool(info[42])}
 
     # ---- ports and far field ---------------------------------------------------------
     def port_ring(self, obj, axis, coord, tol=1e-6):

@@ -116,10 +116,10 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
                         pc ? c->pc_nfp64 : 0,
                         pc && c->pc_prec == BEM_C32 ? (int64_t)(c->pc_resid * 1e12) : -1};
   for (int i = 32; i < n && i < 36; ++i) info[i] = w[i - 32];
-  int64_t z[5];
+  int64_t z[6];
   zsp_stats(c, z);
-  const int64_t zv[6] = {(int64_t)(c->setup_ms[10] * 1e3), z[0], z[1], z[2], z[3], z[4]};
-  for (int i = 36; i < n && i < 42; ++i) info[i] = zv[i - 36];
+  const int64_t zv[7] = {(int64_t)(c->setup_ms[10] * 1e3), z[0], z[1], z[2], z[3], z[4], z[5]};
+  for (int i = 36; i < n && i < 43; ++i) info[i] = zv[i - 36];
   return BEM_OK;
 }
 

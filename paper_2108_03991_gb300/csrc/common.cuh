@@ -439,7 +439,8 @@ int zsp_gather(aim_ctx* c, int obj, const double2* L, const double2* B);
 int zsp_factor(aim_ctx* c);
 int zsp_check(aim_ctx* c);
 void free_zsp(aim_ctx* c);
-void zsp_stats(const aim_ctx* c, int64_t* out);  // objects, in use, max band, FP32 bytes, check
+// objects, in use, max band, FP32 bytes, check (1e-15), a product's wait timed out (1)
+void zsp_stats(const aim_ctx* c, int64_t* out);
 template <typename R>
 int zsp_apply(aim_ctx* c, const typename C2<R>::T* h, typename C2<R>::T* e, int nrhs, int64_t hs,
               int64_t es, cudaStream_t s);

@@ -56,6 +56,9 @@ struct Zsp {
   float2* v32 = nullptr;   // [kMaxBatch][ne] rows of K_s + I_x/2 h, permuted (product scratch)
   double2* v64 = nullptr;
   double check = -1;  // max over objects of |Z_s h - Z h| / |Z h| at set-up
+  ~Zsp() {
+    if (W) cudaFree(W);
+  }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -461,9 +464,7 @@ static std::vector<int> rcm_order(int n, const std::vector<int>& rp, const std::
 }
 
 void free_zsp(aim_ctx* c) {
-  Zsp* z = static_cast<Zsp*>(c->zsp);
-  if (z && z->W) cudaFree(z->W);
-  delete z;
+  delete static_cast<Zsp*>(c->zsp);
   c->zsp = nullptr;
   c->zsp_ready = false;
   c->zsp_on = false;
@@ -692,6 +693,7 @@ void zsp_stats(const aim_ctx* c, int64_t* out) {
     out[2] = 0;
     out[3] = 0;
     out[4] = -1;
+    out[5] = 0;
     return;
   }
   out[0] = (int64_t)z->obj.size();
@@ -699,6 +701,9 @@ void zsp_stats(const aim_ctx* c, int64_t* out) {
   out[2] = z->bmax;
   out[3] = 2 * z->nband * 8 + (int64_t)c->ne * 8 + z->nnz * 12;
   out[4] = (int64_t)(z->check * 1e15);
+  int err = 0;  // set by a product whose bounded wait timed out
+  if (cudaMemcpy(&err, z->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) err = -1;
+  out[5] = err;
 }
 
 }  // namespace bem
