@@ -30,7 +30,10 @@ constexpr double kZspCut = 23.0;     // R_cut / delta
 constexpr int kZspBandMax = 192;     // largest half-bandwidth of the product kernel
 constexpr size_t kZspSmemMax = 220 * 1024;  // its shared memory (FP64: vector and two slabs)
 constexpr int kZspRows = (kZspBandMax + 31) / 32;  // rows per lane in a block's update
-constexpr int kZspBW = 16;  // columns per block of the substitutions (slab: kZspBW b entries)
+// columns per block of the substitutions (slab: kZspBW b entries). 8: a warp's shared memory
+// (the vector and two slabs) is 22 KB at b = 114, so all the objects' warps are resident at once;
+// 16 and 32 took 30% and 70% longer per product on the 32 x 32 ring array
+constexpr int kZspBW = 8;
 constexpr double kZspCheck = 1e-8;   // set-up check of Z_s h against Z h
 constexpr double kTwoPi = 6.283185307179586476925;
 
