@@ -1,0 +1,135 @@
+"""Pins of the ground-plane (PEC half-space) Green's function and operators of the oracle
+(oracle/ground.py), the first piece of the layered background of the paper's Table I: the
+boundary condition on the plane, the Lorenz gauge between the vector and scalar potentials of
+horizontal and vertical current elements (which fixes every image sign), reciprocity of the
+Galerkin operators, the free-space limit, and the grid form of the image term."""
+import numpy as np
+
+from oracle import ground, operators as op
+from oracle.rwg import from_mesh
+from paper_2108_03991_gb300 import synth
+
+K0 = op.k0_of(30e12)  # 0.63 / um: phase over the test distances
+ZG = -0.7
+
+
+def test_boundary_condition_on_the_plane():
+    """On the plane the tangential vector potential and the scalar potential vanish (so does the
+    tangential E = -j w A - grad Phi), the normal vector potential doubles."""
+    rng = np.random.default_rng(1)
+    rp = rng.uniform(-1, 1, (50, 3))
+    rp[:, 2] = ZG + rng.uniform(0.2, 2.0, 50)
+    r = rng.uniform(-3, 3, (50, 3))
+    r[:, 2] = ZG
+    GA, GP = ground.kernels(K0, r, rp, ZG)
+    g = ground.green(K0, np.linalg.norm(r - rp, axis=1))
+    assert np.max(np.abs(GA[:, :2])) < 1e-13 * np.max(np.abs(g))
+    assert np.max(np.abs(GP)) < 1e-13 * np.max(np.abs(g))
+    assert np.allclose(GA[:, 2], 2 * g, rtol=1e-13)
+
+
+def test_lorenz_gauge_fixes_the_image_signs():
+    """For a current element l at r' (charges +-I/(j w) at its ends) the potentials obey
+    div A + j w mu eps Phi = 0, i.e. div_r (G^A l) = -(l . grad_r') G^Phi, for horizontal and
+    vertical elements (central differences); with the opposite image sign for the vertical
+    vector potential, or for the scalar one, it fails."""
+    rng = np.random.default_rng(2)
+    d = 1e-4
+    for _ in range(20):
+        rp = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), ZG + rng.uniform(0.3, 1.5)])
+        r = np.array([rng.uniform(-2, 2), rng.uniform(-2, 2), ZG + rng.uniform(0.3, 2.0)])
+        for c in range(3):
+            l = np.eye(3)[c]
+            div = 0.0
+            for a in range(3):
+                e = np.eye(3)[a] * d
+                GAp, _ = ground.kernels(K0, r + e, rp, ZG)
+                GAm, _ = ground.kernels(K0, r - e, rp, ZG)
+                div += (GAp[a] * l[a] - GAm[a] * l[a]) / (2 * d)
+            _, Pp = ground.kernels(K0, r, rp + l * d, ZG)
+            _, Pm = ground.kernels(K0, r, rp - l * d, ZG)
+            dphi = (Pp - Pm) / (2 * d)
+            assert abs(div + dphi) < 1e-6 * abs(div), (c, div, dphi)
+            if c == 2:  # the wrong image sign for the vertical vector potential breaks it
+                R = np.linalg.norm(r - rp)
+                rp_i = ground.image(rp, ZG)
+                gi = lambda x: ground.green(K0, np.linalg.norm(x - rp_i))
+                g = lambda x: ground.green(K0, np.linalg.norm(x - rp))
+                e = np.array([0, 0, d])
+                wrong = ((g(r + e) - gi(r + e)) - (g(r - e) - gi(r - e))) / (2 * d)
+                assert abs(wrong + dphi) > 1e-3 * abs(div)
+
+
+def test_ground_operators_reciprocal_and_far_limit():
+    """The image parts of L^A and L^Phi are symmetric (Galerkin with a symmetric kernel and the
+    same rule on both sides; the free-space near-pair rule is symmetric only to its accuracy),
+    sizeable for a box near the plane, and vanish as the plane recedes."""
+    mesh = synth.box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (2, 2, 2))
+    rw = from_mesh(synth.merge([mesh], [synth.SIGMA_CU]))
+    LA0, LP0 = op.dense_rwg(rw, K0, "A"), op.dense_lphi(rw, K0)
+    LA, LP = ground.dense_ground_operators(rw, K0, -0.3)
+    for M in (LA - LA0, LP - LP0):
+        assert np.linalg.norm(M - M.T) < 1e-12 * np.linalg.norm(M)
+    assert np.linalg.norm(LP - LP0) > 0.1 * np.linalg.norm(LP0)
+    assert np.linalg.norm(LA - LA0) > 0.05 * np.linalg.norm(LA0)
+    LAf, LPf = ground.dense_ground_operators(rw, K0, -1e4)
+    assert 0 < np.linalg.norm(LPf - LP0) < 1e-3 * np.linalg.norm(LP0)
+    assert 0 < np.linalg.norm(LAf - LA0) < 1e-3 * np.linalg.norm(LA0)
+
+
+def test_grid_image_term_as_a_convolution():
+    """The image part of the grid convolution (a correlation in z) equals the ordinary
+    zero-padded FFT convolution of the z-reflected sources on the grid extended below the
+    plane: the form a GPU convolution can take."""
+    h = np.array([0.5, 0.4, 0.3])
+    n = (6, 5, 4)
+    zg = -1.0
+    origin = np.array([0.1, -0.2, zg + 2 * h[2]])
+    s = synth.rand_cvec(n[0] * n[1] * n[2], 3)
+    for sign in (1.0, -1.0):
+        a = ground.grid_image_direct(K0, h, n, origin, zg, s, sign)
+        b = ground.grid_image_fft(K0, h, n, origin, zg, s, sign)
+        assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(a)
+
+
+def test_image_parts_use_the_pinned_kernels():
+    """Entries of the operators' image parts recomputed from ground.kernels (whose signs the
+    gauge test fixes) minus the free-space kernel, with the same 7-point rule on both
+    triangles (pairs that share no triangle, where the free-space kernel is finite at every
+    pair of rule points)."""
+    from oracle.quad import radon7, rule_points
+    mesh = synth.box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (2, 2, 2))
+    rw = from_mesh(synth.merge([mesh], [synth.SIGMA_CU]))
+    zg = -0.3
+    LA, LP = ground.dense_ground_operators(rw, K0, zg)
+    LA0, LP0 = op.dense_rwg(rw, K0, "A"), op.dense_lphi(rw, K0)
+    b, w = radon7()
+    rq = rule_points(rw.verts[rw.tris], b)
+
+    def half(m, t):  # RWG m on triangle t at the rule points: [7, 3]
+        a = [i for i in range(3) if rw.t_edges[t, i] == m][0]
+        c = rw.t_esign[t, a] * rw.elen[m] / (2 * rw.area[t])
+        return c * (rq[t] - rw.verts[rw.t_evert[t, a]])
+
+    rng = np.random.default_rng(6)
+    pairs = [(m, n) for m, n in rng.integers(0, rw.ne, (40, 2))
+             if not set(rw.et[m]) & set(rw.et[n])][:6]
+    assert len(pairs) == 6
+    for m, n in pairs:
+        v = 0.0
+        for t in rw.et[m]:
+            for s in rw.et[n]:
+                r, rp = rq[t][:, None, :], rq[s][None, :, :]
+                GA, _ = ground.kernels(K0, r, rp, zg)
+                g = ground.green(K0, np.linalg.norm(r - rp, axis=-1))
+                img = GA - g[..., None]
+                fm, fn = half(m, t), half(n, s)
+                v += rw.area[t] * rw.area[s] * np.einsum(
+                    "q,p,qd,qpd,pd->", w, w, fm, img, fn)
+        assert abs(v - (LA - LA0)[m, n]) < 1e-12 * abs(LA - LA0).max()
+    for t, s in [(t, s) for t, s in rng.integers(0, rw.nt, (20, 2)) if t != s][:6]:
+        r, rp = rq[t][:, None, :], rq[s][None, :, :]
+        _, GP = ground.kernels(K0, r, rp, zg)
+        g = ground.green(K0, np.linalg.norm(r - rp, axis=-1))
+        v = rw.area[t] * rw.area[s] * np.einsum("q,p,qp->", w, w, GP - g)
+        assert abs(v - (LP - LP0)[t, s]) < 1e-12 * abs(LP - LP0).max()
