@@ -133,3 +133,45 @@ def test_image_parts_use_the_pinned_kernels():
         g = ground.green(K0, np.linalg.norm(r - rp, axis=-1))
         v = rw.area[t] * rw.area[s] * np.einsum("q,p,qp->", w, w, GP - g)
         assert abs(v - (LP - LP0)[t, s]) < 1e-12 * abs(LP - LP0).max()
+
+
+def test_mirror_geometry_identity():
+    """Image theory restated with the free-space oracle: the ground-plane operator between two
+    RWG functions equals the free-space one between f_m and f_n minus the free-space one between
+    f_m and the mirrored function D f_n(M r) (M: the reflection in the plane), the mirror box
+    meshed as a second object (its triangles reversed to stay outward). Two independent codes:
+    the free-space oracle's rules against the image parts' 7-point rule, 1e-10 with the plane
+    far enough for both to use the regular rule."""
+    V, F = synth.box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (2, 2, 2))
+    zg = -2.0
+    Vm = ground.image(V, zg)
+    Fm = F[:, ::-1]  # the reflection reverses orientation: reverse to keep the normals outward
+    mesh2 = synth.merge([(V, F), (Vm, Fm)], [synth.SIGMA_CU] * 2)
+    rw1 = from_mesh(synth.merge([(V, F)], [synth.SIGMA_CU]))
+    rw2 = from_mesh(mesh2)
+    LA, LP = ground.dense_ground_operators(rw1, K0, zg)
+    LA2, LP2 = op.dense_rwg(rw2, K0, "A"), op.dense_lphi(rw2, K0)
+    ne, nt, nv = rw1.ne, rw1.nt, V.shape[0]
+    # the mirrored function of edge n: edge (a + nv, b + nv) of the second object, with the sign
+    # that makes f'_n'(r) = D f_n(M r) (compared at the centroid of the mirrored T+)
+    key = {tuple(e): i for i, e in enumerate(rw2.ev)}
+    mir, sgn = np.zeros(ne, int), np.zeros(ne)
+    for n in range(ne):
+        a, b = rw1.ev[n]
+        n2 = key[(a + nv, b + nv)]
+        t = rw1.et[n, 0]
+        c = rw1.centroid[t]
+        f = rw1.elen[n] / (2 * rw1.area[t]) * (c - rw1.verts[rw1.eopp[n, 0]])
+        cm = ground.image(c, zg)
+        k = 0 if np.allclose(rw2.centroid[rw2.et[n2, 0]], cm) else 1
+        tm = rw2.et[n2, k]
+        s2 = 1.0 if k == 0 else -1.0
+        f2 = s2 * rw2.elen[n2] / (2 * rw2.area[tm]) * (cm - rw2.verts[rw2.eopp[n2, k]])
+        mir[n] = n2
+        sgn[n] = 1.0 if np.allclose(f2, ground.D_IMG * f) else -1.0
+        assert np.allclose(sgn[n] * f2, ground.D_IMG * f)
+    ref = LA2[:ne, :ne] - LA2[:ne, mir] * sgn[None, :]
+    assert np.linalg.norm(LA - ref) < 1e-10 * np.linalg.norm(ref)
+    # pulses: the mirrored triangle of t is t + nt (same order), the image charge opposite
+    refP = LP2[:nt, :nt] - LP2[:nt, nt:]
+    assert np.linalg.norm(LP - refP) < 1e-10 * np.linalg.norm(refP)
