@@ -133,3 +133,63 @@ def grid_image_fft(k0, h, n, origin, zg, sigma, sign):
               np.arange(-nx + 1, nx) % shape[2])] = K
     full = np.fft.ifftn(np.fft.fftn(Kc) * np.fft.fftn(ext, s=shape, axes=(0, 1, 2)))
     return sign * full[off:off + nz, :ny, :nx].ravel()
+
+
+class GroundAim:
+    """The AIM external operators above the ground plane (O-AIM with images): the projection
+    and interpolation of oracle/aim.py, the grid convolution plus its image part (sign -1 for
+    the x and y components and for the charges, +1 for z; grid_image_fft), and the near region
+    precorrected for both,
+        L_NR = L_exact,ground - sum_c P_c^T (G_grid + s_c G_grid,image) P_c
+    on the near pairs (anchors within r_near). zg must be a node plane below the grid."""
+
+    SIGN = (-1.0, -1.0, 1.0)
+
+    def __init__(self, rw: RWG, origin, h, n, k0, zg, r_near=2):
+        from .aim import Aim
+        self.A = Aim(rw, origin, h, n, k0, r_near)
+        self.zg = zg
+        self.LNR_A = None
+        self.LNR_P = None
+
+    def conv(self, sigma, sign):
+        A = self.A
+        return A.conv(sigma) + grid_image_fft(A.k0, A.h, A.n, A.origin, self.zg, sigma, sign)
+
+    def image_precorrection(self, W_m, W_n, anc_m, anc_n, sign):
+        """sign * sum_{a,b} W_m[a] G(|x_a - image(x_b)|) W_n[b] per pair (x: stencil nodes)."""
+        from .aim import OFFS
+        A = self.A
+        xa = A.origin + (anc_m[:, None, :] + OFFS[None, :, :]) * A.h      # [P, 27, 3]
+        xb = image(A.origin + (anc_n[:, None, :] + OFFS[None, :, :]) * A.h, self.zg)
+        R = np.linalg.norm(xa[:, :, None, :] - xb[:, None, :, :], axis=-1)
+        return sign * np.einsum("pa,pab,pb->p", W_m, green(A.k0, R), W_n)
+
+    def build_near(self, LA_exact, LP_exact):
+        """Near-region matrices from dense exact ground-plane operators (small meshes)."""
+        import scipy.sparse as sps
+        A, rw = self.A, self.A.rw
+        M, N = A.near_e
+        pre = sum(A.precorrection(A.WA[M, c, :], A.WA[N, c, :], A.anc_e[M], A.anc_e[N])
+                  + self.image_precorrection(A.WA[M, c, :], A.WA[N, c, :], A.anc_e[M],
+                                             A.anc_e[N], self.SIGN[c]) for c in range(3))
+        self.LNR_A = sps.csr_matrix((LA_exact[M, N] - pre, (M, N)), shape=(rw.ne, rw.ne))
+        T, S = A.near_t
+        pre = A.precorrection(A.WP[T], A.WP[S], A.anc_t[T], A.anc_t[S]) + \
+            self.image_precorrection(A.WP[T], A.WP[S], A.anc_t[T], A.anc_t[S], -1.0)
+        self.LNR_P = sps.csr_matrix((LP_exact[T, S] - pre, (T, S)), shape=(rw.nt, rw.nt))
+        return self
+
+    def far_A(self, j):
+        A = self.A
+        return sum(A.PA[c] @ self.conv(A.PA[c].T @ j, self.SIGN[c]) for c in range(3))
+
+    def far_P(self, q):
+        A = self.A
+        return A.PP @ self.conv(A.PP.T @ q, -1.0)
+
+    def LA(self, j):
+        return self.far_A(j) + self.LNR_A @ j
+
+    def LPhi(self, q):
+        return self.far_P(q) + self.LNR_P @ q
