@@ -67,6 +67,27 @@ def test_modified_vs_original_on_interposer_shape():
     assert worst < 0.15
 
 
+
+def test_modified_vs_original_on_srr_array_shape():
+    """Sec. III-C-2 and the schedule-length comparison of Sec. IV-C's split-ring array: 1,488
+    objects of three element sizes (scale 1, 1/2, 1/4) and 1,281,975 edges in all. Reading: a
+    third of the objects per size, edges in proportion to the element's scale (a ring meshed at
+    a fixed number of elements per unit length), 2% seeded jitter. Both algorithms stay above
+    the ideal length sum W / P (a lower bound) and within 15% of each other; with these many
+    similar objects few get more than one process and the two schedules coincide."""
+    rng = np.random.default_rng(11)
+    per = 1281975 / (496 * 1.75)
+    n = np.concatenate([np.full(496, per * f) for f in (1.0, 0.5, 0.25)])
+    W = np.sort(np.round(n * rng.uniform(0.98, 1.02, 1488)) ** 2)[::-1]
+    for P in (40, 160, 640, 1280):
+        Pm, _, cm = sched.part_schedule(W, P, p_cutoff=20)
+        Po, _, co = sched.part_schedule(W, P)
+        ideal = W.sum() / P
+        assert cm >= ideal * (1 - 1e-12) and co >= ideal * (1 - 1e-12)
+        assert cm / co - 1 < 0.15
+        assert all(sched.is_approx_square(int(p)) for p in Pm if p > 20)
+
+
 def bus_rows():
     """The high-speed bus structures of Sec. IV-B (tests/golden/bus_processes_per_conductor.txt):
     (conductors, P, N_E) per row."""
