@@ -114,7 +114,9 @@ const char* bem_last_error(void);
  * is in use, [39]=its largest half-bandwidth, [40]=its bytes per product in complex FP32,
  * [41]=its set-up check |Z_s h - Z h| / |Z h| (largest over the objects) in units of 1e-15
  * (-1: none), [42]=1 if one of its products had a bounded wait time out (that product's e is
- * invalid; reading it synchronises the device). Writes min(n, 43) entries. */
+ * invalid; reading it synchronises the device), [43]=calls of aim_internal_tc, [44]=1 if one
+ * of its products had a bounded wait time out, 0 if none did, -1 before its first call (reading
+ * it synchronises the device). Writes min(n, 45) entries. */
 int aim_info(const aim_ctx* ctx, int64_t* info, int n);
 
 /* Sparse internal operator at high frequency (Sec. III-A, third item of the internal problem:
@@ -201,6 +203,21 @@ int aim_matvec_host(aim_ctx* ctx, int which, const void* x, void* y, int nvec, i
  * (aim_internal_sparse) e = Z_s h. */
 int internal_apply(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, int prec,
                    void* stream);
+
+/* The internal products of many right-hand sides at once on the tensor cores: e_r = Z h_r and
+ * h_eq,r = C h_r (C = Y_eq Z; Eqs. MFIEinZin, EFIEeqYZ, block diagonal over the objects as in
+ * Sec. II-C) for r < nrhs, complex FP32 (interleaved re, im), the right-hand sides stored one
+ * after another, each N_E long, in the conductor-contiguous order of aim_matvec. Every block is
+ * streamed from device memory once per 128 right-hand sides: each complex block product is one
+ * real GEMM (TF32 tensor cores, hi/lo split of both operands for FP32 accuracy). Always the
+ * dense Z, also while the sparse internal operator is on. Either output may be NULL (not both);
+ * h, e and h_eq must not alias. Asynchronous on `stream`; the first call builds the per-object
+ * operand descriptors and the packed right-hand-side workspace (2 x 2 x NP x sum ld_i FP32
+ * values, NP = 2 nrhs rounded up to 32, 64, 128 or 256; it grows and synchronises `stream` when
+ * a later call needs more). A bounded wait that times out leaves that product invalid and
+ * shows in aim_info[44]. Errors: BEM_EINVAL (bad pointers, nrhs < 1, no FP32 blocks),
+ * BEM_ENOMEM, BEM_ECUDA (the driver has no tensor-map encoder, or a launch failed). */
+int aim_internal_tc(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, void* stream);
 
 /* The grid step H of Eq. AIM_L alone: phi_c = sum_b G_grid(a - b) sigma_c(b) (linear
  * convolution) for ncomp (1..4) grids of n[0]*n[1]*n[2] points (x fastest) stored one after

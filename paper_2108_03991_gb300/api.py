@@ -25,7 +25,8 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "bem_net_apply", "bem_convnet_run", "aim_gemv_select", "aim_gemv_plan",
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
-           "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order"]
+           "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order",
+           "aim_internal_tc"]
 
 
 class BemError(RuntimeError):
@@ -87,6 +88,7 @@ def lib():
                                        C.POINTER(d), vp]
         L.bem_farfield.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(d), C.POINTER(d), vp]
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
+        L.aim_internal_tc.argtypes = [vp, vp, vp, vp, C.c_int, vp]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv_noalloc.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int,
@@ -235,8 +237,8 @@ class Context:
         self._read_info()
 
     def _read_info(self):
-        info = (C.c_int64 * 43)()
-        _check(lib().aim_info(self.h, info, 43))
+        info = (C.c_int64 * 45)()
+        _check(lib().aim_info(self.h, info, 45))
         self.info = list(info)
         self.ne, self.nt, self.nobj = info[0], info[1], info[2]
         self.n = self.ne + self.nt
@@ -264,6 +266,9 @@ class Context:
                                 "band": info[39], "bytes_c32": info[40],
                                 "check": None if info[41] < 0 else info[41] * 1e-15,
                                 "wait_timed_out": bool(info[42])}
+        # many right-hand sides on the tensor cores (aim_internal_tc): calls, and whether a
+        # bounded wait timed out (None before the first call)
+        self.tensor_core = {"calls": info[43], "wait_timed_out": None if info[44] < 0 else bool(info[44])}
 
     # ---- ports and far field ---------------------------------------------------------
     def port_ring(self, obj, axis, coord, tol=1e-6):
@@ -405,6 +410,25 @@ class Context:
                                     _ptr(heq, dt) if heq is not None else None, int(nrhs), prec,
                                     _stream()))
         return e, heq
+
+    def internal_tc(self, h, e=None, heq=None, nrhs=1, want_heq=True, want_e=True):
+        """e_r = Z h_r and h_eq,r = C h_r for nrhs complex64 right-hand sides at once on the
+        tensor cores (aim_internal_tc); either may be left out."""
+        import torch
+        dt = torch.complex64
+        if e is None and want_e:
+            e = torch.empty_like(h)
+        if heq is None and want_heq:
+            heq = torch.empty_like(h)
+        _check(lib().aim_internal_tc(self.h, _ptr(h, dt), _ptr(e, dt) if e is not None else None,
+                                     _ptr(heq, dt) if heq is not None else None, int(nrhs),
+                                     _stream()))
+        return e, heq
+
+    def tensor_core_status(self):
+        """aim_internal_tc's calls and wait status (reading it synchronises the device)."""
+        self._read_info()
+        return self.tensor_core
 
     def conv(self, sigma, phi=None, ncomp=1, prec=BEM_C32):
         import torch

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libbem_aim.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "geom.cpp", "sched.cpp", "setup.cu", "fft.cu", "hot.cu", "gmres.cu",
-           "noalloc.cu", "learned.cu", "gemv_tma.cu", "post.cu", "zsparse.cu"]
+           "noalloc.cu", "learned.cu", "gemv_tma.cu", "post.cu", "zsparse.cu",
+           "zgemm_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-rdc=false"]

@@ -88,6 +88,7 @@ void aim_destroy(aim_ctx* c) {
   free_geo_store(c);
   free_far_geo(c);
   free_zsp(c);
+  free_tc(c);
   if (c->gm_ws) cudaFree(c->gm_ws);
   if (c->gmb_ws) cudaFree(c->gmb_ws);
   delete c;
@@ -120,6 +121,9 @@ int aim_info(const aim_ctx* c, int64_t* info, int n) {
   zsp_stats(c, z);
   const int64_t zv[7] = {(int64_t)(c->setup_ms[10] * 1e3), z[0], z[1], z[2], z[3], z[4], z[5]};
   for (int i = 36; i < n && i < 43; ++i) info[i] = zv[i - 36];
+  int64_t tv[2];
+  tc_stats(c, tv);
+  for (int i = 43; i < n && i < 45; ++i) info[i] = tv[i - 43];
   return BEM_OK;
 }
 
@@ -287,6 +291,15 @@ int internal_apply(aim_ctx* c, const void* h, void* e, void* heq, int nrhs, int 
   }
   cudaStream_t s = (cudaStream_t)stream;
   return prec == BEM_C32 ? internal<float>(c, h, e, heq, nrhs, s) : internal<double>(c, h, e, heq, nrhs, s);
+}
+
+int aim_internal_tc(aim_ctx* c, const void* h, void* e, void* heq, int nrhs, void* stream) {
+  BEM_TRY(check_ctx(c, "aim_internal_tc"));
+  if (!h || (!e && !heq) || nrhs < 1 || h == e || heq == e || heq == h) {
+    set_error("aim_internal_tc: bad pointers or nrhs");
+    return BEM_EINVAL;
+  }
+  return internal_tc(c, (const float2*)h, (float2*)e, (float2*)heq, nrhs, (cudaStream_t)stream);
 }
 
 int aim_conv(aim_ctx* c, const void* sigma, void* phi, int ncomp, int prec, void* stream) {

@@ -349,6 +349,8 @@ struct aim_ctx {
   // qualifies (zsp_ready), used for e = Z h while zsp_on
   void* zsp = nullptr;
   bool zsp_ready = false, zsp_on = false;
+  // many right-hand sides through Z and C on the tensor cores (zgemm_tc.cu), made on first use
+  void* tc = nullptr;
 };
 
 namespace bem {
@@ -444,6 +446,11 @@ void zsp_stats(const aim_ctx* c, int64_t* out);
 template <typename R>
 int zsp_apply(aim_ctx* c, const typename C2<R>::T* h, typename C2<R>::T* e, int nrhs, int64_t hs,
               int64_t es, cudaStream_t s);
+// many right-hand sides through the FP32 Z and C on the tensor cores (zgemm_tc.cu)
+int internal_tc(aim_ctx* c, const float2* h, float2* e, float2* heq, int nrhs, cudaStream_t s);
+void free_tc(aim_ctx* c);
+// products made, a wait timed out (1) or not (0), -1 when never used
+void tc_stats(const aim_ctx* c, int64_t* out);
 int set_gemv_shape(aim_ctx* c, int kind, int cps, int split, int unroll);
 int tune_matvec_schedule(aim_ctx* c);
 double k0_of(double f);
