@@ -1,5 +1,6 @@
-"""The C-ABI library loads, exports every symbol include/bem_aim.h declares, and its host-only
-scheduler (Sec. III-C, Alg. 2) matches the oracle. No GPU needed."""
+"""The C-ABI library loads, exports every symbol include/bem_aim.h declares, its host-only
+scheduler (Sec. III-C, Alg. 2) matches the oracle, its reverse Cuthill-McKee ordering is valid,
+and aim_setup rejects invalid structures with the documented codes. No GPU needed."""
 import ctypes
 import os
 import re
@@ -118,3 +119,73 @@ def test_rcm_order_ring_pattern(L):
 def test_rcm_order_rejects_bad_columns(L):
     with pytest.raises(api.BemError):
         api.rcm_order(np.array([0, 1, 2]), np.array([1, 5]))
+
+
+# ---------------------------------------------------------------------------------------
+# invalid structures: aim_setup rejects them in its host-side checks, before any device work,
+# with the documented error codes (so these run without a GPU)
+# ---------------------------------------------------------------------------------------
+def _box():
+    from paper_2108_03991_gb300 import synth
+    m = synth.small_bars(1, 2.0)
+    return m, synth.grid_box(m, 0.5)
+
+
+def _setup_code(mesh, grid, freq=10e9, why=""):
+    with pytest.raises(api.BemError) as ei:
+        api.Context(mesh, grid, freq)
+    assert why in str(ei.value)
+    return ei.value.code
+
+
+def _with(m, **kw):
+    from dataclasses import replace
+    return replace(m, **kw)
+
+
+def test_setup_rejects_bad_values(L):
+    m, g = _box()
+    v = m.verts.copy()
+    v[3, 1] = np.nan
+    assert _setup_code(_with(m, verts=v), g, why="non-finite") == -1
+    assert _setup_code(m, g, 0.0, why="frequency") == -1
+    assert _setup_code(m, g, float("nan")) == -1
+    assert _setup_code(_with(m, sigma=np.array([-1.0])), g, why="material") == -1
+    t = m.tris.copy()
+    t[5, 2] = m.verts.shape[0]
+    assert _setup_code(_with(m, tris=t), g, why="out of range") == -1
+
+
+def test_setup_rejects_bad_surfaces(L):
+    m, g = _box()
+    assert _setup_code(_with(m, tris=m.tris[:-1], obj=m.obj[:-1]), g, why="has 1 triangles") == -2
+    t = m.tris.copy()
+    t[7] = t[7][[0, 2, 1]]
+    assert _setup_code(_with(m, tris=t), g, why="orientation") == -2  # one turned over
+    extra = np.stack([m.tris[0], m.tris[0][[0, 2, 1]]])
+    t = np.concatenate([m.tris, extra])
+    assert _setup_code(_with(m, tris=t, obj=np.zeros(len(t), np.int32)), g,
+                        why="has 4 triangles") == -2  # non-manifold
+    v = m.verts.copy()
+    a, b, _ = m.tris[3]
+    v[b] = v[a]
+    assert _setup_code(_with(m, verts=v), g, why="degenerate") == -2
+
+
+def test_setup_rejects_bad_object_lists(L):
+    m, g = _box()
+    half = len(m.tris) // 2
+    two = np.concatenate([np.zeros(half, np.int32), np.ones(len(m.tris) - half, np.int32)])
+    # one closed surface cut into two objects: an edge joins them
+    assert _setup_code(_with(m, obj=two, nobj=2, sigma=np.array([m.sigma[0]] * 2)), g,
+                        why="joins two objects") == -2
+    assert _setup_code(_with(m, obj=two[::-1].copy(), nobj=2,
+                             sigma=np.array([m.sigma[0]] * 2)), g, why="non-decreasing") == -1
+
+
+def test_setup_rejects_bad_grids(L):
+    from dataclasses import replace
+    m, g = _box()
+    assert _setup_code(m, replace(g, origin=g.origin + 0.75), why="outside the grid") == -3
+    assert _setup_code(m, replace(g, h=np.array([0.5, 0.0, 0.5])), why="axis 1") == -3
+    assert _setup_code(m, replace(g, n=np.array([2, 9, 9])), why="axis 0") == -3
