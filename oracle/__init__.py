@@ -20,6 +20,14 @@ Modules
   ports      delta-gap port excitation and port currents
   sched      LPT (Alg. 1) and modified Part_Schedule (Alg. 2)
   blockops   block-diagonal GEMV (Sec. II-C, block diagonal Z and Y_eq)
+  precond    block-diagonal preconditioner (the fallback of the constraint preconditioner)
+  highk      large-|k_i| integrals of the lossy conductors (Sec. II-B)
+  convnet    the learned correction's conv net
+  sparse_internal  sparse internal operator at high frequency (Sec. III-A)
+  sibc       surface-impedance boundary condition (the comparison model of Sec. I)
+  ground     a PEC ground plane under the background, by images (Table I's bottom layer)
+  layered    Green's functions of Table I's stratified backgrounds (same-layer, Toeplitz +
+             Hankel in z) and the grid step inside a layer
 
 Parity pins: every function is pinned in tests/test_oracle_*.py against closed forms,
 exactness on polynomials, brute force on tiny inputs, invariants or the Mie series. No function
