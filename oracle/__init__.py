@@ -21,6 +21,7 @@ Modules
   sched      LPT (Alg. 1) and modified Part_Schedule (Alg. 2)
   blockops   block-diagonal GEMV (Sec. II-C, block diagonal Z and Y_eq)
   precond    block-diagonal preconditioner (the fallback of the constraint preconditioner)
+  constraint the constraint preconditioner (near-field system, sparse LU)
   highk      large-|k_i| integrals of the lossy conductors (Sec. II-B)
   convnet    the learned correction's conv net
   sparse_internal  sparse internal operator at high frequency (Sec. III-A)
