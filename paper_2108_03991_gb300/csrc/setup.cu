@@ -608,19 +608,6 @@ __global__ void k_rhs_pw(DGeo g, int ne, int nt, double k0, double px, double py
   b[m] = mk((decltype(b[m].x))acc.x, (decltype(b[m].x))acc.y);
 }
 
-// ---------------------------------------------------------------------------------------
-// Persistent GEMV plans: upload a byte-balanced row plan into the context.
-// ---------------------------------------------------------------------------------------
-static int upload_plan(aim_ctx* c, const std::vector<RowInfo>& rows, const std::vector<int2>& segs,
-                       const std::vector<int32_t>& cseg, GemvPlan* p) {
-  BEM_TRY(upload(c, &p->rows, rows.data(), rows.size()));
-  BEM_TRY(upload(c, &p->segs, segs.data(), segs.size()));
-  BEM_TRY(upload(c, &p->cta_seg, cseg.data(), cseg.size()));
-  p->ncta = (int)cseg.size() - 1;
-  p->nrows = (int)rows.size();
-  return BEM_OK;
-}
-
 struct TunePlan {  // a candidate plan held in temporary device memory
   GemvPlan p;
   std::vector<void*> mem;
