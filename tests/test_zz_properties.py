@@ -41,7 +41,9 @@ def _dt(prec):
     return np.complex64 if prec == api.BEM_C32 else np.complex128
 
 
-@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-12)])
+# tolerances: a few times the products' own rounding (FP32 parity with the oracle is 1e-5;
+# j = h - C h and the FFTs cancel), far below what a broken term or object mix-up leaves
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 5e-5), (api.BEM_C64, 1e-10)])
 def test_system_matvec_is_linear(dev, prec, tol):
     mesh = _bars([0, 1, 2])
     ctx = api.Context(mesh, synth.grid_box(mesh, 0.5), 10e9)
@@ -54,7 +56,7 @@ def test_system_matvec_is_linear(dev, prec, tol):
     assert rel(Az, a * Ax + b * Ay) < tol
 
 
-@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 1e-5), (api.BEM_C64, 1e-11)])
+@pytest.mark.parametrize("prec,tol", [(api.BEM_C32, 5e-5), (api.BEM_C64, 1e-9)])
 def test_object_order_invariance(dev, prec, tol):
     order_b = [2, 0, 1]
     mA, mB = _bars([0, 1, 2]), _bars(order_b)
