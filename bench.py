@@ -517,6 +517,47 @@ def bar_array_section(args, api, synth, torch, np, dev):
     return out
 
 
+def tensor_core_section(ctx, api, synth, torch, np, dev, hbm, reps=10):
+    """h_eq = C h for R right-hand sides at once (C = Y_eq Z, complex FP32): the tensor-core
+    product (one pass over C per 128 right-hand sides, TF32 with the hi/lo split) against the
+    block GEMV (one pass per 4), both through the library; the two agree to FP32 rounding. Per
+    R: ms per product, C's bytes over that time, and the complex flops 8 sum n_i^2 R over it."""
+    ZY = ctx.zy_bytes_c32 // 2
+    n2 = ZY / 8  # sum of n_i ld_i complex entries of C
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record(s)
+        for _ in range(reps):
+            fn()
+        ev1.record(s)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    rows = []
+    for R in (4, 8, 16, 32, 64, 128):
+        h = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.ne, 700 + r) for r in range(R)])
+                             .astype(np.complex64)).to(dev)
+        y_tc = torch.empty_like(h)
+        y_mv = torch.empty_like(h)
+        t_tc = timed(lambda: ctx.internal_tc(h, None, y_tc, nrhs=R, want_e=False))
+        t_mv = timed(lambda: ctx.internal(h, None, y_mv, nrhs=R, prec=api.BEM_C32, want_e=False))
+        d = float(torch.linalg.vector_norm(y_tc - y_mv) / torch.linalg.vector_norm(y_mv))
+        rows.append({"nrhs": R, "ms_tensor_core": t_tc, "ms_block_gemv": t_mv,
+                     "speedup": t_mv / t_tc, "rel_diff": d,
+                     "tensor_core_GBps": ZY / (t_tc * 1e-3) / 1e9,
+                     "tensor_core_frac_hbm": ZY / (t_tc * 1e-3) / 1e9 / hbm,
+                     "tensor_core_TFLOPs": 8 * n2 * R / (t_tc * 1e-3) / 1e12})
+        del h, y_tc, y_mv
+    st = ctx.tensor_core_status()
+    cross = next((r["nrhs"] for r in rows if r["speedup"] > 1), None)
+    return {"product": "h_eq = C h, R right-hand sides (aim_internal_tc vs internal_apply)",
+            "rows": rows, "crossover_nrhs": cross, "wait_timed_out": st["wait_timed_out"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,6 +577,9 @@ def main():
                     help="kind,ctas_per_sm,split,unroll of the GEMV launch in --ncu-case internal")
     ap.add_argument("--rings", type=int, default=32,
                     help="rings per side of the split-ring array (32: the full workload)")
+    ap.add_argument("--tensor-core", action="store_true",
+                    help="add h_eq = C h for 4..128 right-hand sides at once: the tensor-core "
+                         "product (aim_internal_tc) against the block GEMV (internal_apply)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -799,6 +843,8 @@ def main():
             "solve": solve,
             "cpu_baseline": cpu,
         }
+    if rank == 0 and args.tensor_core:
+        out["tensor_core"] = tensor_core_section(ctx, api, synth, torch, np, dev, peaks()[0])
     ctx.close()
     if rank == 0 and args.bar_array and not args.no_solve:
         out["bar_array"] = bar_array_section(args, api, synth, torch, np, dev)
