@@ -6,7 +6,7 @@ each object's exact dense operators, cuts them further: DESIGN records both)."""
 import numpy as np
 import pytest
 
-from oracle import aim as oaim, constraint, gmres, operators as op
+from oracle import aim as oaim, constraint, gmres, operators as op, precond
 from oracle.rwg import from_mesh
 from paper_2108_03991_gb300 import synth
 
@@ -53,7 +53,10 @@ def test_constraint_row_is_exact(two_bars):
     assert np.linalg.norm((M.P @ x)[ne:] - y) <= 1e-12 * np.linalg.norm(y)
 
 
-def test_constraint_preconditioner_cuts_iterations():
+def test_preconditioners_cut_iterations():
+    """Plane-wave solve of three bars with 0.75 um gaps (near pairs across the objects), GMRES
+    to 1e-6: the block-diagonal preconditioner (reading 7) needs at most 10 iterations and at
+    least 10x fewer than none; the constraint preconditioner at least 4x fewer than none."""
     mesh = synth.small_bars(3, 3.0, pitch=1.75)
     grid = synth.grid_box(mesh, 0.5)
     freq = 10e9
@@ -63,10 +66,15 @@ def test_constraint_preconditioner_cuts_iterations():
     A = oaim.Aim(rw, grid.origin, grid.h, grid.n, k0).build_near(LA, LP)
     Zs, Ys = op.internal_blocks(rw, freq, mesh.sigma)
     S = op.SlimSystem(rw, freq, Zs, Ys, A.LA, A.LPhi)
-    M = constraint.ConstraintPrecond(rw, freq, Zs, Ys, constraint.near_part(LA, A.near_e, rw.ne),
-                                     constraint.near_part(LP, A.near_t, rw.nt))
+    Mb = precond.BlockDiagPrecond(rw, freq, Zs, Ys)
+    Mc = constraint.ConstraintPrecond(rw, freq, Zs, Ys, constraint.near_part(LA, A.near_e, rw.ne),
+                                      constraint.near_part(LP, A.near_t, rw.nt))
     b = np.concatenate([op.plane_wave_rhs(rw, k0) / op.ETA0, np.zeros(rw.nt)])
     _, it0, _ = gmres.gmres(S.matvec, b, tol=1e-6, restart=200, max_iter=3000)
-    x1, it1, _ = gmres.gmres(S.matvec, b, tol=1e-6, restart=200, max_iter=3000, precond=M)
-    assert np.linalg.norm(S.matvec(x1) - b) <= 1e-6 * np.linalg.norm(b)
-    assert it1 * 4 <= it0
+    its = []
+    for M in (Mb, Mc):
+        x, it, _ = gmres.gmres(S.matvec, b, tol=1e-6, restart=200, max_iter=3000, precond=M)
+        assert np.linalg.norm(S.matvec(x) - b) <= 1e-6 * np.linalg.norm(b)
+        its.append(it)
+    assert its[0] <= 10 and it0 >= 10 * its[0]
+    assert its[1] * 4 <= it0
