@@ -145,25 +145,22 @@ class Stack:
               ([] if self.ground else [self.bottom_eps])]
         return max(ks)
 
-    def sommerfeld(self, f, rho, zeta):
-        """(1/2 pi) int_0^inf f(k) J0(k rho) k dk for a spectral function f decaying at least as
-        e^{-k zeta} (zeta > 0) along the real axis; rho a scalar or an array (one path for all,
-        set by the largest rho)."""
+    def path(self, rmax, zeta):
+        """Nodes and weights of the integration path for rho <= rmax and a decay e^{-k zeta}:
+        a half-ellipse k(t) = a/2 (1 - cos t) + j b sin t (t in [0, pi], 64 panels of 16 points,
+        a = twice the largest wavenumber, b <= 1/rmax keeps |J0| below e), then the real axis
+        from a in panels no longer than a quarter period of J0, a fifth of the decay length or a
+        fifth of the distance from the origin, up to where e^{-k zeta} < 1e-18."""
         if zeta <= 0:
             raise ValueError("the reflected terms need zeta > 0")
-        rho = np.atleast_1d(np.asarray(rho, dtype=float))
-        rmax = float(rho.max())
         a = 2.0 * self._kmax()
-        b = min(a / 2.0, 1.0 / rmax) if rmax > 0 else a / 2.0   # keeps |J0| below e
-        # half-ellipse k(t) = a/2 (1 - cos t) + j b sin t, t in [0, pi], 64 panels of 16 points
+        b = min(a / 2.0, 1.0 / rmax) if rmax > 0 else a / 2.0
         edges = np.linspace(0.0, math.pi, 65)
         t = (0.5 * (edges[1:] - edges[:-1])[:, None] * _GL_X[None, :] +
              0.5 * (edges[1:] + edges[:-1])[:, None]).ravel()
         wt = (0.5 * (edges[1:] - edges[:-1])[:, None] * _GL_W[None, :]).ravel()
         k1 = 0.5 * a * (1 - np.cos(t)) + 1j * b * np.sin(t)
         w1 = (0.5 * a * np.sin(t) + 1j * b * np.cos(t)) * wt
-        # real axis from a: panels no longer than a quarter period of J0, a fifth of the decay
-        # length, or a fifth of the distance from the origin; stop where e^{-k zeta} < 1e-18
         kend = a + 42.0 / zeta
         step_cap = min(0.25 * math.pi / rmax if rmax > 0 else np.inf, 0.2 / zeta)
         lo = a
@@ -176,11 +173,25 @@ class Stack:
         los, his = np.array(los), np.array(his)
         k2 = (0.5 * (his - los)[:, None] * _GL_X[None, :] + 0.5 * (his + los)[:, None]).ravel()
         w2 = (0.5 * (his - los)[:, None] * _GL_W[None, :]).ravel()
-        k = np.concatenate([k1, k2.astype(complex)])
-        w = np.concatenate([w1, w2.astype(complex)])
+        return np.concatenate([k1, k2.astype(complex)]), np.concatenate([w1, w2.astype(complex)])
+
+    def sommerfeld(self, f, rho, zeta):
+        """(1/2 pi) int_0^inf f(k) J0(k rho) k dk for a spectral function f decaying at least as
+        e^{-k zeta} (zeta > 0) along the real axis; rho a scalar or an array (one path for all,
+        set by the largest rho)."""
+        rho = np.atleast_1d(np.asarray(rho, dtype=float))
+        k, w = self.path(float(rho.max()), zeta)
         fk = f(k) * k * w
         out = np.array([np.sum(fk * jv(0, k * r)) for r in rho]) / (2.0 * math.pi)
         return out if out.size > 1 else out[0]
+
+    def sommerfeld_many(self, fs, rho, zeta):
+        """The same for several spectral functions on one path (zeta: the smallest decay among
+        them): [len(fs), len(rho)]."""
+        rho = np.atleast_1d(np.asarray(rho, dtype=float))
+        k, w = self.path(float(rho.max()), zeta)
+        J = jv(0, k[:, None] * rho[None, :]) * (k * w)[:, None] / (2.0 * math.pi)
+        return np.stack([f(k) @ J for f in fs])
 
     # ---- spatial Green's functions --------------------------------------------------------
     def toeplitz(self, n, rho, u, kind):
@@ -231,14 +242,20 @@ class LayeredGrid:
         rho = np.hypot(dx * self.h[0], dy * self.h[1])
         ur, inv = np.unique(np.round(rho, 12), return_inverse=True)
         inv = inv.reshape(rho.shape)
-        self.T = np.zeros((2 * nz - 1, ny, nx), dtype=complex)   # dz = -(nz-1) .. nz-1
-        for i, dz in enumerate(range(-(nz - 1), nz)):
-            vals = stack.toeplitz(self.layer, ur, dz * self.h[2], kind)
-            self.T[i] = np.atleast_1d(vals)[inv]
-        self.H = np.zeros((2 * nz - 1, ny, nx), dtype=complex)   # s = 0 .. 2nz-2
-        for s in range(2 * nz - 1):
-            vals = stack.hankel(self.layer, ur, 2 * z0 + s * self.h[2], kind)
-            self.H[s] = np.atleast_1d(vals)[inv]
+        n_, hz = self.layer, self.h[2]
+        d, zb, zt = stack.d[n_], stack.z[n_], stack.z[n_ + 1]
+        dzs = np.arange(-(nz - 1), nz)
+        # reflected parts on one integration path per part (the smallest decay among the rows)
+        Tr = stack.sommerfeld_many([lambda kr, u=dz * hz: stack.spectral(n_, kr, "T", u, kind)
+                                    for dz in dzs], ur, 2 * d - (nz - 1) * hz)
+        vs = 2 * z0 + np.arange(2 * nz - 1) * hz
+        Hr = stack.sommerfeld_many([lambda kr, v=v: stack.spectral(n_, kr, "H", v, kind)
+                                    for v in vs], ur, min(vs[0] - 2 * zb, 2 * zt - vs[-1]))
+        R = np.hypot(ur[None, :], dzs[:, None] * hz)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            direct = np.where(R > 0, green(stack.k(stack.eps[n_]), R), 0.0)
+        self.T = (direct + Tr)[:, inv]          # [2nz-1, ny, nx], dz = -(nz-1) .. nz-1
+        self.H = Hr[:, inv]                     # [2nz-1, ny, nx], s = 0 .. 2nz-2
 
     def kernel(self, ia, ib):
         """G between nodes ia, ib (index triples (x, y, z))."""
@@ -280,3 +297,154 @@ class LayeredGrid:
         out = conv(full_xy(self.T), s, nz - 1)
         out += conv(full_xy(self.H), s[::-1], nz - 1)
         return out.ravel()
+
+
+# ---------------------------------------------------------------------------------------
+# Galerkin operators and the AIM inside a layer
+# ---------------------------------------------------------------------------------------
+class ReflectedTable:
+    """The reflected (smooth) part of one Green's function of layer n, G_T,refl(rho, u) +
+    G_H(rho, v), tabulated on tensor grids of spacing `step` and interpolated by cubic
+    splines in each variable (real and imaginary parts apart). Ranges: rho in [0, rho_max],
+    u = z - z' in [-du, du], v = z + z' in [v_lo, v_hi]."""
+
+    def __init__(self, stack: Stack, n, kind, rho_max, du, v_lo, v_hi, step):
+        from scipy.interpolate import RegularGridInterpolator as RGI
+        d = stack.d[n]
+        if du >= d or v_lo <= 2 * stack.z[n] or v_hi >= 2 * stack.z[n + 1]:
+            raise ValueError("table ranges must stay inside the layer")
+
+        def axis(lo, hi):
+            m = max(4, int(math.ceil((hi - lo) / step)) + 1)
+            return np.linspace(lo, hi, m)
+
+        self.rho = axis(0.0, rho_max)
+        self.u = axis(-du, du)
+        self.v = axis(v_lo, v_hi)
+        T = stack.sommerfeld_many([lambda kr, u=u: stack.spectral(n, kr, "T", u, kind)
+                                   for u in self.u], self.rho, 2 * d - du).T          # [rho, u]
+        zeta_h = min(v_lo - 2 * stack.z[n], 2 * stack.z[n + 1] - v_hi)
+        H = stack.sommerfeld_many([lambda kr, v=v: stack.spectral(n, kr, "H", v, kind)
+                                   for v in self.v], self.rho, zeta_h).T
+        self._T = [RGI((self.rho, self.u), T.real, method="cubic"),
+                   RGI((self.rho, self.u), T.imag, method="cubic")]
+        self._H = [RGI((self.rho, self.v), H.real, method="cubic"),
+                   RGI((self.rho, self.v), H.imag, method="cubic")]
+
+    def __call__(self, rho, u, v):
+        pu = np.stack([np.ravel(rho), np.ravel(u)], axis=-1)
+        pv = np.stack([np.ravel(rho), np.ravel(v)], axis=-1)
+        out = self._T[0](pu) + 1j * self._T[1](pu) + self._H[0](pv) + 1j * self._H[1](pv)
+        return out.reshape(np.shape(rho))
+
+
+def reflected_parts(rw, tables):
+    """Reflected parts of L^A (RWG x RWG; G^A_xx on the x and y components, G^A_zz on z) and
+    L^Phi (triangle x triangle), Radon's 7-point rule on both triangles; `tables` maps 'xx',
+    'zz', 'phi' to callables (rho, u, v) -> value."""
+    from .quad import radon7, rule_points
+    b, w = radon7()
+    X = rw.verts[rw.tris]
+    rq = rule_points(X, b)                              # [nt, 7, 3]
+    wq = rw.area[:, None] * w[None, :]
+    nt, ne = rw.nt, rw.ne
+    p = rq.reshape(-1, 3)
+    rho = np.hypot(p[:, None, 0] - p[None, :, 0], p[:, None, 1] - p[None, :, 1])
+    u = p[:, None, 2] - p[None, :, 2]
+    v = p[:, None, 2] + p[None, :, 2]
+    G = {k: tables[k](rho, u, v).reshape(nt, 7, nt, 7) for k in ("xx", "zz", "phi")}
+    LP = np.einsum("tq,tqsp,sp->ts", wq, G["phi"], wq)
+    LA = np.zeros((ne, ne), dtype=np.complex128)
+    for i in range(3):
+        mi = rw.t_edges[:, i]
+        ci = rw.t_esign[:, i] * rw.elen[mi] / (2.0 * rw.area)
+        fi = ci[:, None, None] * (rq - rw.verts[rw.t_evert[:, i]][:, None, :]) * wq[:, :, None]
+        for j in range(3):
+            nj = rw.t_edges[:, j]
+            cj = rw.t_esign[:, j] * rw.elen[nj] / (2.0 * rw.area)
+            fj = cj[:, None, None] * (rq - rw.verts[rw.t_evert[:, j]][:, None, :]) * wq[:, :, None]
+            vals = (np.einsum("tqd,spd,tqsp->ts", fi[..., :2], fj[..., :2], G["xx"]) +
+                    np.einsum("tq,sp,tqsp->ts", fi[..., 2], fj[..., 2], G["zz"]))
+            np.add.at(LA, (mi[:, None], nj[None, :]), vals)
+    return LA, LP
+
+
+def dense_layered_operators(rw, stack: Stack, step=None):
+    """Dense L^A and L^Phi of objects inside one layer of the stack: the direct term (the
+    free-space operators at the layer's wavenumber, singular rules included) plus the
+    reflected parts."""
+    from .operators import dense_lphi, dense_rwg
+    z = rw.verts[:, 2]
+    n = stack.layer_of(float(z.min()))
+    if stack.layer_of(float(z.max())) != n:
+        raise ValueError("the objects must lie inside one layer")
+    lo, hi = float(z.min()), float(z.max())
+    span = np.ptp(rw.verts[:, :2], axis=0)
+    rho_max = float(np.hypot(*span)) * 1.001 + 1e-9
+    zeta = min(2 * lo - 2 * stack.z[n], 2 * stack.z[n + 1] - 2 * hi)
+    step = step or zeta / 32.0
+    tabs = {k: ReflectedTable(stack, n, k, rho_max, (hi - lo) * 1.001 + 1e-9, 2 * lo - 1e-9,
+                              2 * hi + 1e-9, step) for k in ("xx", "zz", "phi")}
+    k = stack.k(stack.eps[n])
+    LAr, LPr = reflected_parts(rw, tabs)
+    return dense_rwg(rw, k, "A") + LAr, dense_lphi(rw, k) + LPr
+
+
+class LayeredAim:
+    """The AIM external operators inside one layer: the projection and interpolation of
+    oracle/aim.py, the grid step of LayeredGrid per component (G^A_xx for the x and y
+    components, G^A_zz for z, G^Phi for the charges), and the near region precorrected for
+    that grid step: L_NR = L_exact - sum_c P_c^T G_grid,c P_c on the near pairs."""
+
+    KIND = ("xx", "xx", "zz")
+
+    def __init__(self, rw, stack: Stack, origin, h, n, r_near=2):
+        from .aim import Aim
+        z0 = float(np.asarray(origin)[2])
+        self.layer = stack.layer_of(z0)
+        k = stack.k(stack.eps[self.layer])
+        self.A = Aim(rw, origin, h, n, k, r_near)
+        self.grids = {kind: LayeredGrid(stack, kind, origin, h, n) for kind in ("xx", "zz", "phi")}
+        self.LNR_A = self.LNR_P = None
+
+    def _grid_pairs(self, grid, W_m, W_n, anc_m, anc_n):
+        """sum_{a,b} W_m[a] G_grid(x_a, x_b) W_n[b] per pair, from the grid's tables."""
+        from .aim import OFFS
+        nz = grid.n[2]
+        out = np.zeros(len(anc_m), dtype=np.complex128)
+        for c0 in range(0, len(anc_m), 2048):
+            sl = slice(c0, c0 + 2048)
+            na = anc_m[sl][:, None, :] + OFFS[None, :, :]        # [P, 27, 3] (x, y, z)
+            nb = anc_n[sl][:, None, :] + OFFS[None, :, :]
+            dx = np.abs(na[:, :, None, 0] - nb[:, None, :, 0])
+            dy = np.abs(na[:, :, None, 1] - nb[:, None, :, 1])
+            dz = na[:, :, None, 2] - nb[:, None, :, 2]
+            sz = na[:, :, None, 2] + nb[:, None, :, 2]
+            G = grid.T[dz + nz - 1, dy, dx] + grid.H[sz, dy, dx]
+            out[sl] = np.einsum("pa,pab,pb->p", W_m[sl], G, W_n[sl])
+        return out
+
+    def build_near(self, LA_exact, LP_exact):
+        import scipy.sparse as sps
+        A, rw = self.A, self.A.rw
+        M, N = A.near_e
+        pre = sum(self._grid_pairs(self.grids[self.KIND[c]], A.WA[M, c, :], A.WA[N, c, :],
+                                   A.anc_e[M], A.anc_e[N]) for c in range(3))
+        self.LNR_A = sps.csr_matrix((LA_exact[M, N] - pre, (M, N)), shape=(rw.ne, rw.ne))
+        T, S = A.near_t
+        pre = self._grid_pairs(self.grids["phi"], A.WP[T], A.WP[S], A.anc_t[T], A.anc_t[S])
+        self.LNR_P = sps.csr_matrix((LP_exact[T, S] - pre, (T, S)), shape=(rw.nt, rw.nt))
+        return self
+
+    def far_A(self, j):
+        A = self.A
+        return sum(A.PA[c] @ self.grids[self.KIND[c]].apply(A.PA[c].T @ j) for c in range(3))
+
+    def far_P(self, q):
+        return self.A.PP @ self.grids["phi"].apply(self.A.PP.T @ q)
+
+    def LA(self, j):
+        return self.far_A(j) + self.LNR_A @ j
+
+    def LPhi(self, q):
+        return self.far_P(q) + self.LNR_P @ q
