@@ -31,6 +31,12 @@ and the surface-wave poles, which lie on or below the real axis for exp(j w t)),
 axis, where the reflected terms decay as e^{-k_rho zeta} (zeta > 0 for points strictly inside
 the layer), in Gauss-Legendre panels no longer than a fraction of the oscillation period of J0
 and of the decay length.
+
+On top of these: the grid step of the AIM inside a layer (LayeredGrid: Toeplitz tables by FFT
+convolution, Hankel tables by convolution of the z-reversed sources), the Galerkin operators
+of objects inside a layer (the free-space operators at the layer's wavenumber for the direct
+term, the reflected parts by a 7-point rule on both triangles with tabulated, spline-
+interpolated Green's functions), and the layered O-AIM with its precorrected near region.
 """
 from __future__ import annotations
 
