@@ -432,6 +432,37 @@ double bem_part_schedule(int ntask, const double* W, int P, int p_cutoff, int32_
  * outside [0, n)). The pattern's symmetry is the caller's to ensure. */
 int bem_rcm_order(int n, const int32_t* rowptr, const int32_t* cols, int32_t* order);
 
+/* A planar stratified background (the layered media of Table I): nlayer layers bottom-up,
+ * each a thickness in um and a complex relative permittivity (re, im; exp(j w t), so im <= 0
+ * in a lossy layer: eps_r - j sigma / (w eps0)); a half-space of top_eps above; under layer 0
+ * a perfectly conducting plane at z = 0 (ground = 1) or a half-space of bottom_eps
+ * (ground = 0). Non-magnetic. The caller owns the arrays. */
+typedef struct {
+  int32_t nlayer;
+  const double* thickness;   /* [nlayer] um */
+  const double* eps;         /* [nlayer][2] */
+  double top_eps[2];
+  int32_t ground;
+  double bottom_eps[2];
+} bem_stack;
+
+/* Set-up of the AIM grid step inside one layer of a stratified background (Table I): the
+ * tables of phi(a) = sum_b [G_T(rho_ab, z_a - z_b) + G_H(rho_ab, z_a + z_b)] sigma(b) for the
+ * grid of nodes origin + (i, j, k) h, i < n[0], j < n[1], k < n[2], whose node planes must lie
+ * strictly inside one layer. kind 0: G^A_xx (= G^A_yy, the x and y current components), 1:
+ * G^A_zz, 2: G^Phi (times the layer's relative permittivity); each equals G(k_n, R) =
+ * e^{-j k_n R} / (4 pi R) in a homogeneous medium of the layer's wavenumber k_n. Green's
+ * functions of the transmission-line form of the stratified medium for sources and observers
+ * in the same layer (no x-z coupling of horizontal currents); Sommerfeld integrals of the
+ * reflected terms. Outputs (HOST, caller-owned, complex double as (re, im) pairs):
+ * T[dz + n[2] - 1][dy][dx] for dz = -(n[2]-1) .. n[2]-1 (the direct term included, 0 at
+ * R = 0) and H[s][dy][dx] for s = k_a + k_b = 0 .. 2 n[2] - 2, dx < n[0], dy < n[1]: each
+ * (2 n[2] - 1) n[1] n[0] complex values. Host computation only; its cost grows with
+ * n[0] n[1] (at most 65536) times the integration path's length. Errors: BEM_EINVAL (bad
+ * arguments or layers), BEM_EGRID (bad grid, or node planes not inside one layer). */
+int bem_layered_grid_tables(const bem_stack* stack, double freq_hz, const double* origin,
+                            const double* h, const int32_t* n, int kind, double* T, double* H);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,13 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
            "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order",
-           "aim_internal_tc"]
+           "aim_internal_tc", "bem_layered_grid_tables"]
+
+
+class StackC(C.Structure):
+    _fields_ = [("nlayer", C.c_int32), ("thickness", C.POINTER(C.c_double)),
+                ("eps", C.POINTER(C.c_double)), ("top_eps", C.c_double * 2),
+                ("ground", C.c_int32), ("bottom_eps", C.c_double * 2)]
 
 
 class BemError(RuntimeError):
@@ -89,6 +95,8 @@ def lib():
         L.bem_farfield.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(d), C.POINTER(d), vp]
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_internal_tc.argtypes = [vp, vp, vp, vp, C.c_int, vp]
+        L.bem_layered_grid_tables.argtypes = [C.POINTER(StackC), d, C.POINTER(d), C.POINTER(d),
+                                              C.POINTER(i32), C.c_int, C.POINTER(d), C.POINTER(d)]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int, C.c_int, vp]
         L.bem_blockdiag_gemv_noalloc.argtypes = [C.c_int, C.POINTER(i32), vp, vp, vp, C.c_int,
@@ -138,6 +146,29 @@ def _ptr(t, dtype=None):
 def cdtype(prec):
     import torch
     return torch.complex64 if prec == BEM_C32 else torch.complex128
+
+
+def layered_grid_tables(layers, freq, origin, h, n, kind, top_eps=1.0, ground=True,
+                        bottom_eps=1.0):
+    """bem_layered_grid_tables: the Toeplitz and Hankel tables of the grid step inside one layer
+    of a stratified background. layers: [(thickness um, complex eps_r)] bottom-up; kind 0
+    G^A_xx, 1 G^A_zz, 2 G^Phi. Returns (T, H), complex arrays [2 n_z - 1, n_y, n_x]."""
+    th = np.array([float(t) for t, _ in layers], dtype=np.float64)
+    ep = np.array([[complex(e).real, complex(e).imag] for _, e in layers], dtype=np.float64)
+    te, be = complex(top_eps), complex(bottom_eps)
+    st = StackC(len(layers), th.ctypes.data_as(C.POINTER(C.c_double)),
+                ep.ctypes.data_as(C.POINTER(C.c_double)), (C.c_double * 2)(te.real, te.imag),
+                1 if ground else 0, (C.c_double * 2)(be.real, be.imag))
+    nx, ny, nz = (int(v) for v in n)
+    T = np.zeros((2 * nz - 1, ny, nx), dtype=np.complex128)
+    H = np.zeros_like(T)
+    o = (C.c_double * 3)(*[float(v) for v in origin])
+    hh = (C.c_double * 3)(*[float(v) for v in h])
+    nn = (C.c_int32 * 3)(nx, ny, nz)
+    _check(lib().bem_layered_grid_tables(C.byref(st), float(freq), o, hh, nn, int(kind),
+                                         T.ctypes.data_as(C.POINTER(C.c_double)),
+                                         H.ctypes.data_as(C.POINTER(C.c_double))))
+    return T, H
 
 
 def part_schedule(W, P, p_cutoff=20):

@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "libbem_aim.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "geom.cpp", "sched.cpp", "setup.cu", "fft.cu", "hot.cu", "gmres.cu",
            "noalloc.cu", "learned.cu", "gemv_tma.cu", "post.cu", "zsparse.cu",
-           "zgemm_tc.cu"]
+           "zgemm_tc.cu", "layered.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-rdc=false"]
