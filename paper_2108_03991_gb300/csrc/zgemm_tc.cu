@@ -26,8 +26,10 @@
 // per instruction) into one TMEM accumulator of NP columns; all threads split the stage's A
 // tile into hi and lo parts in shared memory while the previous stage's MMAs run. The epilogue
 // reads TMEM lane by lane (warp w owns rows 32w..32w+31) and writes y_r coalesced along rows.
-// Every wait is bounded: on a timeout the CTA records an error in *err, waits (bounded) for its
-// own MMAs and copies in flight, frees its TMEM and leaves; the results are then invalid.
+// Every wait is bounded: on a timeout the CTA records an error (err[0], kept across products)
+// and raises the launch's abort flag (err[1], cleared before each launch), waits (with a short
+// limit) for its own MMAs and copies in flight, frees its TMEM and leaves; the other CTAs see
+// the flag in their waits, or before they start, and leave too. The results are then invalid.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -121,6 +123,26 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
 
+// Bounded wait on an mbarrier phase that also gives up as soon as any CTA of the launch has
+// recorded a failure in *err (polled every 256 tries), so that one stuck CTA does not make
+// every later CTA wait out its own limit.
+constexpr uint32_t kTcSpin = 1u << 22;
+constexpr uint32_t kTcSpinCleanup = 1u << 16;
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const int* err, uint32_t spins) {
+  for (uint32_t it = 0; it < spins; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255 && *(const volatile int*)err) return false;
+  }
+  return false;
+}
+
 // B from x, hi and lo parts: rows 2r and 2r + 1 for right-hand side r < R (zero rows up to NP),
 // columns 2u and 2u + 1 for padded slot u (slot[u] = its unknown, -1 in a block's padding).
 // Grid: x over the slots, y over the NP / 2 row pairs.
@@ -172,6 +194,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const TcObj o = objs[t.obj];
   const CUtensorMap* mA = ma + t.obj;
   const int nk = (2 * o.n + kTcK - 1) / kTcK;
+  int* const abort_flag = err + 1;  // set by any CTA of this launch that gave up
+
+  // a CTA that starts after another one gave up leaves at once (one decision for the block)
+  __shared__ int s_skip;
+  if (tid == 0) s_skip = *(const volatile int*)abort_flag;
+  __syncthreads();
+  if (s_skip) return;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -208,7 +237,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int kc_fail = -1;  // block-uniform: the chunk whose wait timed out for some thread
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc % S;
-    const bool ok = mbar_wait(&full[s], (kc / S) & 1);
+    const bool ok = tc_wait(&full[s], (kc / S) & 1, abort_flag, kTcSpin);
     if (ok) {  // split the A tile: hi in place, lo beside it (same offsets, same swizzle)
       float4* a = reinterpret_cast<float4*>(base + s * L::kStage);
       float4* al = reinterpret_cast<float4*>(base + s * L::kStage + kTcAtile);
@@ -241,7 +270,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // the previous chunk's stage takes chunk kc - 1 + S once that chunk's MMAs are done
       const int nxt = kc - 1 + S;
       if (kc >= 1 && nxt < nk && !stalled) {
-        if (mbar_wait(&empty[(kc - 1) % S], ((kc - 1) / S) & 1)) load(nxt);
+        if (tc_wait(&empty[(kc - 1) % S], ((kc - 1) / S) & 1, abort_flag, kTcSpin)) load(nxt);
         else stalled = true;  // the loop's next wait on chunk nxt times out for every thread
       }
     }
@@ -250,15 +279,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   bool ok = kc_fail < 0;
   if (ok) {
     if (tid == 0) tc_commit(done);
-    ok = !__syncthreads_or(!mbar_wait(done, 0));
+    ok = !__syncthreads_or(!tc_wait(done, 0, abort_flag, kTcSpin));
     if (!ok) kc_fail = nk;
   }
   if (!ok) {  // leave cleanly: error code, MMAs and copies in flight waited for (bounded)
     if (tid == 0) {
       atomicExch(err, 1);
+      atomicExch(abort_flag, 1);
       if (kc_fail < nk) tc_commit(done);
-      mbar_wait(done, 0);
-      for (int c = max(kc_fail, 0); c < issued; ++c) mbar_wait(&full[c % S], (c / S) & 1);
+      const int none = 0;  // the cleanup waits run their own short limit to the end
+      tc_wait(done, 0, &none, kTcSpinCleanup);
+      for (int c = max(kc_fail, 0); c < issued; ++c) tc_wait(&full[c % S], (c / S) & 1, &none, kTcSpinCleanup);
     }
     tc_fence_before();
     __syncthreads();
@@ -302,7 +333,7 @@ struct TcState {
   int64_t nslot = 0;          // sum of ld_i
   float *bh = nullptr, *bl = nullptr;  // packed B, [np_cap][2 nslot] each
   int np_cap = 0;
-  int* err = nullptr;
+  int* err = nullptr;         // [2]: a wait timed out in some product (sticky); this launch gave up
   int64_t calls = 0;
   ~TcState() {
     for (void* p : {(void*)mz, (void*)mc, (void*)tiles, (void*)objs, (void*)slot, (void*)bh,
@@ -398,8 +429,8 @@ static int tc_prepare(aim_ctx* c, TcState** out) {
   up((void**)&t->tiles, tiles.data(), tiles.size() * sizeof(TcTile));
   up((void**)&t->objs, objs.data(), objs.size() * sizeof(TcObj));
   up((void**)&t->slot, slot.data(), slot.size() * sizeof(int32_t));
-  const int zero = 0;
-  up((void**)&t->err, &zero, sizeof(int));
+  const int zero[2] = {0, 0};  // [0]: a wait timed out in some product; [1]: this launch gave up
+  up((void**)&t->err, zero, sizeof(zero));
   if (rc != BEM_OK) {
     delete t;
     return rc;
@@ -419,6 +450,7 @@ static int tc_launch(TcState* t, const CUtensorMap& mbh, const CUtensorMap& mbl,
     BEM_CUDA(cudaFuncSetAttribute(k_zgemm_tc<NP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
     attr = true;
   }
+  BEM_CUDA(cudaMemsetAsync(t->err + 1, 0, sizeof(int), s));
   k_zgemm_tc<NP, S><<<t->ntiles, kTcThreads, kSmem, s>>>(mbh, mbl, ma, t->tiles, t->objs, y, vstride, R,
                                                         t->err);
   BEM_CUDA(cudaGetLastError());
