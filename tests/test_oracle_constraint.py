@@ -2,7 +2,7 @@
 the near region it is the dense SLIM system itself; its second block row (the continuity
 equation, the constraint) is the system's at any near radius; and on three bars it cuts the
 GMRES iterations of the plane-wave solve several-fold (the block-diagonal preconditioner, with
-each object's exact dense operators, cuts them further: DESIGN records both)."""
+each object's exact dense operators, cuts them further; both are checked on one structure)."""
 import numpy as np
 import pytest
 
