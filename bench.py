@@ -577,6 +577,8 @@ def main():
                     help="kind,ctas_per_sm,split,unroll of the GEMV launch in --ncu-case internal")
     ap.add_argument("--rings", type=int, default=32,
                     help="rings per side of the split-ring array (32: the full workload)")
+    ap.add_argument("--rows-variant", type=int, default=None, choices=[0, 1],
+                    help="form of the near-region sums (aim_rows_variant) for the timed matvecs")
     ap.add_argument("--tensor-core", action="store_true",
                     help="add h_eq = C h for 4..128 right-hand sides at once: the tensor-core "
                          "product (aim_internal_tc) against the block GEMV (internal_apply)")
@@ -607,6 +609,8 @@ def main():
     ctx = api.Context(mesh, grid, freq)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    if args.rows_variant is not None:
+        ctx.rows_variant(args.rows_variant)
     s = torch.cuda.current_stream()
     x = torch.from_numpy(synth.rand_cvec(ctx.n, 1 + rank)).to(torch.complex64).to(dev)
     y = torch.empty_like(x)
@@ -795,6 +799,7 @@ def main():
                            ZY / 1e9, "sparse Z_s %.1f GB" % (ctx.sparse_internal["bytes_c32"] / 1e9)
                            if sparse else "Z %.1f GB" % (ZY / 1e9)),
                        "internal": "sparse Z_s (Sec. III-A, high frequency)" if sparse else "dense Z",
+                       "rows_variant": args.rows_variant or 0,
                        "setup_s": setup_s, "setup_stage_s": ctx.setup_stage_s,
                        "reference_arm": "FP64 oracle on the host cores on the 8x8 sub-array, "
                                         "scaled by the ring count; its internal blocks and "

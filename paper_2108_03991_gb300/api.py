@@ -26,7 +26,7 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
            "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order",
-           "aim_internal_tc", "bem_layered_grid_tables"]
+           "aim_internal_tc", "bem_layered_grid_tables", "aim_rows_variant"]
 
 
 class StackC(C.Structure):
@@ -95,6 +95,7 @@ def lib():
         L.bem_farfield.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(d), C.POINTER(d), vp]
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_internal_tc.argtypes = [vp, vp, vp, vp, C.c_int, vp]
+        L.aim_rows_variant.argtypes = [vp, C.c_int]
         L.bem_layered_grid_tables.argtypes = [C.POINTER(StackC), d, C.POINTER(d), C.POINTER(d),
                                               C.POINTER(i32), C.c_int, C.POINTER(d), C.POINTER(d)]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
@@ -476,6 +477,11 @@ class Context:
         k = (C.c_double * 3)(*khat)
         _check(lib().bem_rhs_plane_wave(self.h, p, k, _ptr(b), prec, _stream()))
         return b
+
+    def rows_variant(self, variant):
+        """Form of the near-region sums (aim_rows_variant): 0 the default, 1 predicated; the
+        products are the same bits either way."""
+        _check(lib().aim_rows_variant(self.h, int(variant)))
 
     def internal_sparse(self, on):
         """Use the sparse internal operator Z_s (on=True, when aim_setup built one) or the dense Z

@@ -756,8 +756,40 @@ __device__ __forceinline__ void near_row(const V* __restrict__ val, const int32_
   for (; i < i1; i += 32) cfma(acc, val[i], x[col[i]]);
 }
 
-// p_t = (W_Phi phi)_t + (L^Phi_NR q)_t, written to out[t] (y for L^Phi alone, p in the system)
-template <typename R>
+// The same sum with the lane's last group predicated instead of taken one entry at a time: a lane
+// with 1-3 entries left issues their loads together (a missing entry repeats the group's first
+// column, with value 0), so every lane's share of a row of up to 256 entries takes at most two
+// rounds of dependent loads. The entries, their lanes and each lane's order of accumulation are
+// those of near_row, and the missing entries add exact zeros: the sums are the same bits.
+template <typename V>
+__device__ __forceinline__ void near_row_p(const V* __restrict__ val, const int32_t* __restrict__ col,
+                                           const V* __restrict__ x, int64_t i0, int64_t i1, int lane,
+                                           V& acc) {
+  for (int64_t i = i0 + lane; i < i1; i += 128) {
+    const bool p1 = i + 32 < i1, p2 = i + 64 < i1, p3 = i + 96 < i1;
+    const int c0 = col[i];
+    const int c1 = p1 ? col[i + 32] : c0, c2 = p2 ? col[i + 64] : c0, c3 = p3 ? col[i + 96] : c0;
+    const V a0 = val[i];
+    const V a1 = p1 ? val[i + 32] : czero<V>(), a2 = p2 ? val[i + 64] : czero<V>();
+    const V a3 = p3 ? val[i + 96] : czero<V>();
+    const V x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    cfma(acc, a0, x0);
+    cfma(acc, a1, x1);
+    cfma(acc, a2, x2);
+    cfma(acc, a3, x3);
+  }
+}
+template <int PV, typename V>
+__device__ __forceinline__ void near_row_v(const V* __restrict__ val, const int32_t* __restrict__ col,
+                                           const V* __restrict__ x, int64_t i0, int64_t i1, int lane,
+                                           V& acc) {
+  if constexpr (PV == 1) near_row_p(val, col, x, i0, i1, lane, acc);
+  else near_row(val, col, x, i0, i1, lane, acc);
+}
+
+// p_t = (W_Phi phi)_t + (L^Phi_NR q)_t, written to out[t] (y for L^Phi alone, p in the system);
+// PV selects the near-row form (0: near_row, 1: near_row_p)
+template <typename R, int PV = 0>
 __global__ void __launch_bounds__(256) k_rows_t(
     const R* __restrict__ WP, const int32_t* __restrict__ node,
     const typename C2<R>::T* __restrict__ phi, const int64_t* __restrict__ rowP,
@@ -777,7 +809,7 @@ __global__ void __launch_bounds__(256) k_rows_t(
     const V f = phi[node[t] + node_offset(lane, nx, ny)];
     acc = mk(w * f.x, w * f.y);
   }
-  near_row(LP + rowP[t], colP + lstP[t], q, 0, rowP[t + 1] - rowP[t], lane, acc);
+  near_row_v<PV>(LP + rowP[t], colP + lstP[t], q, 0, rowP[t + 1] - rowP[t], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) out[t] = acc;
 }
@@ -881,7 +913,7 @@ __global__ void __launch_bounds__(256) k_rows_e(
 
 // a = L^A_NR j (the near region of the RWG rows), one warp per row: the part of the system
 // matvec's first row that needs only j, run beside the convolution
-template <typename R>
+template <typename R, int PV = 0>
 __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA,
                                                 const int64_t* __restrict__ lstA,
                                                 const int32_t* __restrict__ colA,
@@ -895,11 +927,19 @@ __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA
   const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (m >= ne) return;
   V acc = czero<V>();
-  near_row(LA + rowA[m], colA + lstA[m], j, 0, rowA[m + 1] - rowA[m], lane, acc);
+  near_row_v<PV>(LA + rowA[m], colA + lstA[m], j, 0, rowA[m + 1] - rowA[m], lane, acc);
   acc = warp_sum(acc);
   if (lane == 0) a[m] = acc;
 }
 
+
+// the near-row form the context selects (aim_rows_variant)
+template <typename R> static decltype(&k_rows_t<R, 0>) rows_t_kernel(const aim_ctx* c) {
+  return c->rows_variant == 1 ? &k_rows_t<R, 1> : &k_rows_t<R, 0>;
+}
+template <typename R> static decltype(&k_near_e<R, 0>) near_e_kernel(const aim_ctx* c) {
+  return c->rows_variant == 1 ? &k_near_e<R, 1> : &k_near_e<R, 0>;
+}
 
 // The system matvec of Eq. AEFIEoutJ for nrhs right-hand sides x_r = [h_r; q_r] (stride
 // N_E + N_T) at once: each block matrix is read once for all of them (the GEMV takes the
@@ -925,7 +965,7 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
   project_t<R>(c, b.WPT, x + ne, b.bsT, c->side, nrhs, N);
   BEM_TRY(fft_conv<R>(c, b, b.bsT, b.bsT, nrhs, b.bwsT, c->side));
-  k_rows_t<R><<<dim3(nb(nt, 8), nrhs), 256, 0, c->side>>>(b.WP, c->d_nodeT, b.bsT, c->d_rowP, c->d_lstP, c->d_clP,
+  rows_t_kernel<R>(c)<<<dim3(nb(nt, 8), nrhs), 256, 0, c->side>>>(b.WP, c->d_nodeT, b.bsT, c->d_rowP, c->d_lstP, c->d_clP,
                                                            b.LP, x + ne, nt, nx, ny, b.bp, ng, N, nt);
   auto gemv = [&](const V* A, V* out, const V* hs) -> int {
     return c->gmr.ntasks > 0 ? run_gemv_mr<R>(c->gmr, A, x, out, nrhs, N, hs, s)
@@ -934,7 +974,7 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   BEM_TRY(gemv(b.C, b.bj, x));  // j_r = h_r - C h_r
   BEM_CUDA(cudaEventRecord(c->ev_c, s));
   BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
-  k_near_e<R><<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.bj, ne, b.ban,
+  near_e_kernel<R>(c)<<<dim3(nb(ne, 8), nrhs), 256, 0, c->side>>>(c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.bj, ne, b.ban,
                                                            N, ne);
   BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
   if (c->zsp_on)  // e_r = Z_s h_r, the sparse internal operator
@@ -998,8 +1038,8 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     V* sq = b.sigma + 3 * ng;
     project_t<R>(c, b.WPT, x, sq, s);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, s));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, x, nt,
-                                          nx, ny, y);
+    rows_t_kernel<R>(c)<<<nb(nt, 8), 256, 0, s>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, x, nt,
+                                          nx, ny, y, 0, 0, 0);
   } else if (which == AIM_OP_EXT) {
     // both external operators of Eq. AEFIEoutJ, as the system matvec runs them: L^A j on the
     // main stream, L^Phi q on the side stream, joined at the end
@@ -1009,8 +1049,8 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, q,
-                                                nt, nx, ny, y + ne);
+    rows_t_kernel<R>(c)<<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, q,
+                                                nt, nx, ny, y + ne, 0, 0, 0);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     project_e<R>(c, b.WAT, x, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
@@ -1036,8 +1076,8 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     if (za < 2) BEM_CUDA(cudaStreamWaitEvent(c->zside, c->ev_fork, 0));
     project_t<R>(c, b.WPT, q, sq, c->side);
     BEM_TRY(fft_conv<R>(c, b, sq, sq, 1, b.ws + 3 * P3, c->side));
-    k_rows_t<R><<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, q,
-                                                nt, nx, ny, b.p);
+    rows_t_kernel<R>(c)<<<nb(nt, 8), 256, 0, c->side>>>(b.WP, c->d_nodeT, sq, c->d_rowP, c->d_lstP, c->d_clP, b.LP, q,
+                                                nt, nx, ny, b.p, 0, 0, 0);
     const GemvPlan& gp = sizeof(R) == 4 ? c->gplan : c->gplan64;
     const GemvPlan& gb = sizeof(R) == 4 ? c->gbg32 : c->gbg64;
     if (c->zsp_on) BEM_TRY(zsp_apply<R>(c, h, b.e, 1, ne, ne, c->zside));
@@ -1047,7 +1087,8 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
       BEM_TRY(run_gemv_plan<R>(gp, b.C, h, b.j, 1, ne, h, s));
     BEM_CUDA(cudaEventRecord(c->ev_c, s));
     BEM_CUDA(cudaStreamWaitEvent(c->side, c->ev_c, 0));
-    k_near_e<R><<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.j, ne, b.anear);
+    near_e_kernel<R>(c)<<<nb(ne, 8), 256, 0, c->side>>>(c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.j, ne, b.anear,
+                                                      0, 0);
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     if (za == 2) {  // e = Z h right after j's GEMV on the main stream, whole GPU
       BEM_TRY(run_gemv_plan<R>(gp, b.Z, h, b.e, 1, ne, nullptr, s));
