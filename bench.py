@@ -577,8 +577,8 @@ def main():
                     help="kind,ctas_per_sm,split,unroll of the GEMV launch in --ncu-case internal")
     ap.add_argument("--rings", type=int, default=32,
                     help="rings per side of the split-ring array (32: the full workload)")
-    ap.add_argument("--rows-variant", type=int, default=None, choices=[0, 1],
-                    help="form of the near-region sums (aim_rows_variant) for the timed matvecs")
+    ap.add_argument("--rows-variant", type=int, default=None, choices=[0, 1, 2],
+                    help="form of the row kernels (aim_rows_variant) for the timed matvecs")
     ap.add_argument("--tensor-core", action="store_true",
                     help="add h_eq = C h for 4..128 right-hand sides at once: the tensor-core "
                          "product (aim_internal_tc) against the block GEMV (internal_apply)")

@@ -134,12 +134,14 @@ int aim_info(const aim_ctx* ctx, int64_t* info, int n);
  * Synchronises the device; captured matvec graphs are rebuilt on next use. */
 int aim_internal_sparse(aim_ctx* ctx, int on);
 
-/* Form of the near-region sums (the precorrected rows of L^A_NR and L^Phi_NR, Sec. III-A item
- * 1) in the kernels of aim_matvec, aim_matvec_batch and bem_solve: 0 (after aim_setup) takes
- * each warp lane's entries four at a time while four remain and the rest one at a time; 1
- * predicates the lane's last group so that its loads are issued together. Both add the same
- * entries in the same order: the products are the same bits (up to the sign of zero). Drops
- * the cached matvec graphs; synchronises the device. Errors: BEM_EINVAL. */
+/* Form of the row kernels of aim_matvec, aim_matvec_batch and bem_solve (the precorrected
+ * near-region rows of L^A_NR and L^Phi_NR and the interpolation W, Sec. III-A item 1): 0 (after
+ * aim_setup) takes each warp lane's near-region entries four at a time while four remain and
+ * the rest one at a time, one row per warp; 1 predicates the lane's last group so that its
+ * loads are issued together; 2 does the same and interpolates two RWG rows per warp. All add
+ * the same terms in the same order: 1 gives the same bits as 0 (up to the sign of zero), 2 the
+ * same up to rounding. Drops the cached matvec graphs; synchronises the device. Errors:
+ * BEM_EINVAL. */
 int aim_rows_variant(aim_ctx* ctx, int variant);
 
 /* Select the FP32 block-GEMV launch used by aim_matvec, internal_apply and bem_solve (the

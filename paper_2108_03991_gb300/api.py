@@ -479,8 +479,8 @@ class Context:
         return b
 
     def rows_variant(self, variant):
-        """Form of the near-region sums (aim_rows_variant): 0 the default, 1 predicated; the
-        products are the same bits either way."""
+        """Form of the row kernels (aim_rows_variant): 0 the default, 1 predicated near-region
+        sums (the same bits), 2 the same with two interpolation rows per warp."""
         _check(lib().aim_rows_variant(self.h, int(variant)))
 
     def internal_sparse(self, on):

@@ -489,8 +489,8 @@ int bem_precond_apply(aim_ctx* c, const void* r, void* u, int prec, void* stream
 
 int aim_rows_variant(aim_ctx* c, int variant) {
   BEM_TRY(check_ctx(c, "aim_rows_variant"));
-  if (variant != 0 && variant != 1) {
-    set_error("aim_rows_variant: variant must be 0 or 1");
+  if (variant < 0 || variant > 2) {
+    set_error("aim_rows_variant: variant must be 0, 1 or 2");
     return BEM_EINVAL;
   }
   BEM_CUDA(cudaDeviceSynchronize());

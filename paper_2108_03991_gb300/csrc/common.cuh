@@ -351,8 +351,8 @@ struct aim_ctx {
   bool zsp_ready = false, zsp_on = false;
   // many right-hand sides through Z and C on the tensor cores (zgemm_tc.cu), made on first use
   void* tc = nullptr;
-  // near-row form of the near-region kernels (aim_rows_variant): 0 four-deep with a one-entry
-  // tail, 1 four-deep predicated
+  // form of the row kernels (aim_rows_variant): 0 near sums four-deep with a one-entry tail,
+  // 1 four-deep predicated, 2 predicated and two interpolation rows per warp (k_rows_e2)
   int rows_variant = 0;
 };
 

@@ -911,6 +911,127 @@ __global__ void __launch_bounds__(256) k_rows_e(
   }
 }
 
+// The same rows, two per warp: each lane issues the loads of both rows' stencil node (and its
+// near-region entries, predicated) before it sums either, so twice the loads are in flight per
+// warp. Every row's terms, their lanes and their order are those of k_rows_e (near_row_p's sums
+// are near_row's bits), so the outputs are the same bits. 16 rows per block of 8 warps; the
+// pulse rows of mode 1 follow as in k_rows_e.
+template <typename R>
+__global__ void __launch_bounds__(256) k_rows_e2(
+    const R* __restrict__ WA, const int32_t* __restrict__ node,
+    const typename C2<R>::T* __restrict__ phi, int64_t ng, const int64_t* __restrict__ rowA,
+    const int64_t* __restrict__ lstA, const int32_t* __restrict__ colA,
+    const typename C2<R>::T* __restrict__ LA,
+    const typename C2<R>::T* __restrict__ j, const R* __restrict__ ix,
+    const int32_t* __restrict__ ixcol, const typename C2<R>::T* __restrict__ e,
+    const R* __restrict__ fdE, const int32_t* __restrict__ et,
+    const typename C2<R>::T* __restrict__ p, int ne, int nx, int ny, R k0, int mode,
+    typename C2<R>::T* __restrict__ y, int nt, const R* __restrict__ fdT,
+    const int32_t* __restrict__ tedge, const typename C2<R>::T* __restrict__ q,
+    const typename C2<R>::T* __restrict__ anear, RowsStride rs = RowsStride()) {
+  typedef typename C2<R>::T V;
+  {
+    const int64_t r = blockIdx.y;
+    phi += r * rs.phi;
+    j += r * rs.j;
+    if (e) e += r * rs.e;
+    if (p) p += r * rs.p;
+    if (q) q += r * rs.q;
+    if (anear) anear += r * rs.an;
+    y += r * rs.y;
+  }
+  const int nbE = (ne + 15) >> 4;  // blocks of the RWG rows (two per warp); then the pulse rows
+  if ((int)blockIdx.x >= nbE) {
+    const int t = (blockIdx.x - nbE) * blockDim.x + threadIdx.x;
+    if (mode == 1 && t < nt) {
+      V s = jk0(q[t], k0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const V jj = j[tedge[3 * t + i]];
+        const R c = fdT[3 * t + i];
+        s.x += c * jj.x;
+        s.y += c * jj.y;
+      }
+      y[ne + t] = s;
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int m0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 2;
+  if (m0 >= ne) return;
+  const bool two = m0 + 1 < ne;
+  const int m1 = two ? m0 + 1 : m0;
+  // mode 1: lanes 27-31 take the sparse terms of row 1 for both rows
+  V b0 = czero<V>(), b1 = czero<V>();
+  if (mode == 1 && lane >= 27) {
+    if (lane < 31) {
+      const int i = lane - 27;
+      const V e0 = e[ixcol[4 * m0 + i]], e1 = e[ixcol[4 * m1 + i]];
+      const R c0 = ix[4 * m0 + i], c1 = ix[4 * m1 + i];
+      b0.x = c0 * e0.x;
+      b0.y = c0 * e0.y;
+      b1.x = c1 * e1.x;
+      b1.y = c1 * e1.y;
+    } else {
+      const V pp0 = p[et[2 * m0]], pm0 = p[et[2 * m0 + 1]];
+      const V pp1 = p[et[2 * m1]], pm1 = p[et[2 * m1 + 1]];
+      const R cp0 = fdE[2 * m0], cm0 = fdE[2 * m0 + 1], cp1 = fdE[2 * m1], cm1 = fdE[2 * m1 + 1];
+      b0.x = -cp0 * pp0.x + cm0 * pm0.x;
+      b0.y = -cp0 * pp0.y + cm0 * pm0.y;
+      b1.x = -cp1 * pp1.x + cm1 * pm1.x;
+      b1.y = -cp1 * pp1.y + cm1 * pm1.y;
+    }
+  }
+  V acc0 = czero<V>(), acc1 = czero<V>();
+  if (lane < 27) {
+    const int64_t off = node_offset(lane, nx, ny);
+    const int64_t nd0 = node[m0] + off, nd1 = node[m1] + off;
+    R w0[3], w1[3];
+    V f0[3], f1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w0[c] = WA[(int64_t)m0 * 81 + c * 27 + lane];
+      w1[c] = WA[(int64_t)m1 * 81 + c * 27 + lane];
+      f0[c] = phi[c * ng + nd0];
+      f1[c] = phi[c * ng + nd1];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc0.x += w0[c] * f0[c].x;
+      acc0.y += w0[c] * f0[c].y;
+      acc1.x += w1[c] * f1[c].x;
+      acc1.y += w1[c] * f1[c].y;
+    }
+  }
+  if (!anear) {
+    near_row_p(LA + rowA[m0], colA + lstA[m0], j, 0, rowA[m0 + 1] - rowA[m0], lane, acc0);
+    near_row_p(LA + rowA[m1], colA + lstA[m1], j, 0, rowA[m1 + 1] - rowA[m1], lane, acc1);
+  }
+  if (anear && lane == 0) {
+    const V an0 = anear[m0], an1 = anear[m1];
+    acc0.x += an0.x;
+    acc0.y += an0.y;
+    acc1.x += an1.x;
+    acc1.y += an1.y;
+  }
+  if (mode == 0) {
+    acc0 = warp_sum(acc0);
+    acc1 = warp_sum(acc1);
+  } else {
+    V t0 = jk0(acc0, k0), t1 = jk0(acc1, k0);
+    t0.x += b0.x;
+    t0.y += b0.y;
+    t1.x += b1.x;
+    t1.y += b1.y;
+    acc0 = warp_sum(t0);
+    acc1 = warp_sum(t1);
+  }
+  if (lane == 0) {
+    y[m0] = acc0;
+    if (two) y[m1] = acc1;
+  }
+}
+
 // a = L^A_NR j (the near region of the RWG rows), one warp per row: the part of the system
 // matvec's first row that needs only j, run beside the convolution
 template <typename R, int PV = 0>
@@ -933,13 +1054,19 @@ __global__ void __launch_bounds__(256) k_near_e(const int64_t* __restrict__ rowA
 }
 
 
-// the near-row form the context selects (aim_rows_variant)
+// the row kernels' form the context selects (aim_rows_variant)
 template <typename R> static decltype(&k_rows_t<R, 0>) rows_t_kernel(const aim_ctx* c) {
-  return c->rows_variant == 1 ? &k_rows_t<R, 1> : &k_rows_t<R, 0>;
+  return c->rows_variant >= 1 ? &k_rows_t<R, 1> : &k_rows_t<R, 0>;
 }
 template <typename R> static decltype(&k_near_e<R, 0>) near_e_kernel(const aim_ctx* c) {
-  return c->rows_variant == 1 ? &k_near_e<R, 1> : &k_near_e<R, 0>;
+  return c->rows_variant >= 1 ? &k_near_e<R, 1> : &k_near_e<R, 0>;
 }
+// (k_rows_e keeps near_row in form 1: its near sums run only for L^A alone, and near_row_p
+// there would cost the system matvec's interpolation rows registers for nothing)
+template <typename R> static decltype(&k_rows_e<R>) rows_e_kernel(const aim_ctx* c) {
+  return c->rows_variant == 2 ? &k_rows_e2<R> : &k_rows_e<R>;
+}
+static inline int rows_e_per_block(const aim_ctx* c) { return c->rows_variant == 2 ? 16 : 8; }
 
 // The system matvec of Eq. AEFIEoutJ for nrhs right-hand sides x_r = [h_r; q_r] (stride
 // N_E + N_T) at once: each block matrix is read once for all of them (the GEMV takes the
@@ -992,7 +1119,7 @@ int matvec_batch(aim_ctx* c, const void* xv, void* yv, int nrhs, cudaStream_t s)
   rs.q = N;
   rs.an = ne;
   rs.y = N;
-  k_rows_e<R><<<dim3(nb(ne, 8) + nb(nt, 256), nrhs), 256, 0, s>>>(
+  rows_e_kernel<R>(c)<<<dim3(nb(ne, rows_e_per_block(c)) + nb(nt, 256), nrhs), 256, 0, s>>>(
       b.WA, c->d_nodeE, b.bsE, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.bj, b.ix, c->d_ixcol, b.be, b.fdE,
       c->d_et, b.bp, ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, x + ne, b.ban, rs);
   BEM_CUDA(cudaGetLastError());
@@ -1031,9 +1158,10 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
   if (which == AIM_OP_LA) {
     project_e<R>(c, b.WAT, x, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
-    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA,
-                                          x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
-                                          nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr, nullptr);
+    rows_e_kernel<R>(c)<<<nb(ne, rows_e_per_block(c)), 256, 0, s>>>(
+        b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA, x, b.ix, c->d_ixcol,
+        nullptr, b.fdE, c->d_et, nullptr, ne, nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr,
+        nullptr, RowsStride());
   } else if (which == AIM_OP_LPHI) {
     V* sq = b.sigma + 3 * ng;
     project_t<R>(c, b.WPT, x, sq, s);
@@ -1054,9 +1182,10 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_CUDA(cudaEventRecord(c->ev_join, c->side));
     project_e<R>(c, b.WAT, x, b.sigma, s);
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
-    k_rows_e<R><<<nb(ne, 8), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA,
-                                          x, b.ix, c->d_ixcol, nullptr, b.fdE, c->d_et, nullptr, ne,
-                                          nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr, nullptr);
+    rows_e_kernel<R>(c)<<<nb(ne, rows_e_per_block(c)), 256, 0, s>>>(
+        b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA, x, b.ix, c->d_ixcol,
+        nullptr, b.fdE, c->d_et, nullptr, ne, nx, ny, k0, 0, y, nt, b.fdT, c->d_tedge, nullptr,
+        nullptr, RowsStride());
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   } else if (which == AIM_OP_SYSTEM) {
     // With C = Y_eq Z formed at set-up (Eq. EFIEeqYZ), j = h - C h and e = Z h are
@@ -1102,10 +1231,10 @@ int matvec(aim_ctx* c, int which, const void* xv, void* yv, cudaStream_t s) {
     BEM_TRY(fft_conv<R>(c, b, b.sigma, b.sigma, 3, b.ws, s));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     BEM_CUDA(cudaStreamWaitEvent(s, c->ev_z, 0));
-    k_rows_e<R><<<nb(ne, 8) + nb(nt, 256), 256, 0, s>>>(b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA,
-                                               b.LA, b.j, b.ix, c->d_ixcol, b.e, b.fdE, c->d_et, b.p,
-                                               ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q,
-                                               b.anear);
+    rows_e_kernel<R>(c)<<<nb(ne, rows_e_per_block(c)) + nb(nt, 256), 256, 0, s>>>(
+        b.WA, c->d_nodeE, b.sigma, ng, c->d_rowA, c->d_lstA, c->d_clA, b.LA, b.j, b.ix, c->d_ixcol,
+        b.e, b.fdE, c->d_et, b.p, ne, nx, ny, k0, 1, y, nt, b.fdT, c->d_tedge, q, b.anear,
+        RowsStride());
   } else {
     set_error("aim_matvec: unknown operator %d", which);
     return BEM_EINVAL;
