@@ -473,6 +473,17 @@ typedef struct {
 int bem_layered_grid_tables(const bem_stack* stack, double freq_hz, const double* origin,
                             const double* h, const int32_t* n, int kind, double* T, double* H);
 
+/* The reflected part of one of a layer's Green's functions (kind as above) on a tensor grid,
+ * for interpolation where sources and observers are not grid nodes (the near-region entries
+ * of objects inside the layer): part 0, the doubly reflected (Toeplitz) terms at arg = z - z'
+ * (|arg| below the layer's thickness); part 1, the singly reflected (Hankel) terms at
+ * arg = z + z' (strictly between twice the layer's bottom and top). out[j][i] (HOST,
+ * caller-owned, complex double as (re, im) pairs) at rho[i] >= 0 and arg[j], nrho narg at most
+ * 2^26. The direct term is not included. Host computation only. Errors: BEM_EINVAL. */
+int bem_layered_kernel_table(const bem_stack* stack, double freq_hz, int layer, int kind,
+                             int part, int nrho, const double* rho, int narg, const double* arg,
+                             double* out);
+
 #ifdef __cplusplus
 }
 #endif

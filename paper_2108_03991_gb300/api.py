@@ -26,7 +26,8 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "aim_matvec_schedule", "aim_matvec_host", "bem_port_ring", "bem_rhs_port",
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
            "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order",
-           "aim_internal_tc", "bem_layered_grid_tables", "aim_rows_variant"]
+           "aim_internal_tc", "bem_layered_grid_tables", "aim_rows_variant",
+           "bem_layered_kernel_table"]
 
 
 class StackC(C.Structure):
@@ -96,6 +97,9 @@ def lib():
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_internal_tc.argtypes = [vp, vp, vp, vp, C.c_int, vp]
         L.aim_rows_variant.argtypes = [vp, C.c_int]
+        L.bem_layered_kernel_table.argtypes = [C.POINTER(StackC), d, C.c_int, C.c_int, C.c_int,
+                                               C.c_int, C.POINTER(d), C.c_int, C.POINTER(d),
+                                               C.POINTER(d)]
         L.bem_layered_grid_tables.argtypes = [C.POINTER(StackC), d, C.POINTER(d), C.POINTER(d),
                                               C.POINTER(i32), C.c_int, C.POINTER(d), C.POINTER(d)]
         L.aim_conv.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
@@ -149,17 +153,24 @@ def cdtype(prec):
     return torch.complex64 if prec == BEM_C32 else torch.complex128
 
 
-def layered_grid_tables(layers, freq, origin, h, n, kind, top_eps=1.0, ground=True,
-                        bottom_eps=1.0):
-    """bem_layered_grid_tables: the Toeplitz and Hankel tables of the grid step inside one layer
-    of a stratified background. layers: [(thickness um, complex eps_r)] bottom-up; kind 0
-    G^A_xx, 1 G^A_zz, 2 G^Phi. Returns (T, H), complex arrays [2 n_z - 1, n_y, n_x]."""
+def _stack(layers, top_eps, ground, bottom_eps):
+    """The bem_stack of a layer list [(thickness um, complex eps_r)] bottom-up, with the arrays
+    it points to (keep them alive while it is used)."""
     th = np.array([float(t) for t, _ in layers], dtype=np.float64)
     ep = np.array([[complex(e).real, complex(e).imag] for _, e in layers], dtype=np.float64)
     te, be = complex(top_eps), complex(bottom_eps)
     st = StackC(len(layers), th.ctypes.data_as(C.POINTER(C.c_double)),
                 ep.ctypes.data_as(C.POINTER(C.c_double)), (C.c_double * 2)(te.real, te.imag),
                 1 if ground else 0, (C.c_double * 2)(be.real, be.imag))
+    return st, (th, ep)
+
+
+def layered_grid_tables(layers, freq, origin, h, n, kind, top_eps=1.0, ground=True,
+                        bottom_eps=1.0):
+    """bem_layered_grid_tables: the Toeplitz and Hankel tables of the grid step inside one layer
+    of a stratified background. layers: [(thickness um, complex eps_r)] bottom-up; kind 0
+    G^A_xx, 1 G^A_zz, 2 G^Phi. Returns (T, H), complex arrays [2 n_z - 1, n_y, n_x]."""
+    st, keep = _stack(layers, top_eps, ground, bottom_eps)
     nx, ny, nz = (int(v) for v in n)
     T = np.zeros((2 * nz - 1, ny, nx), dtype=np.complex128)
     H = np.zeros_like(T)
@@ -170,6 +181,22 @@ def layered_grid_tables(layers, freq, origin, h, n, kind, top_eps=1.0, ground=Tr
                                          T.ctypes.data_as(C.POINTER(C.c_double)),
                                          H.ctypes.data_as(C.POINTER(C.c_double))))
     return T, H
+
+
+def layered_kernel_table(layers, freq, layer, kind, part, rho, arg, top_eps=1.0, ground=True,
+                         bottom_eps=1.0):
+    """bem_layered_kernel_table: the reflected part (part 0 Toeplitz at arg = z - z', 1 Hankel
+    at arg = z + z') of one of a layer's Green's functions at rho x arg. Returns a complex array
+    [len(arg), len(rho)]."""
+    st, keep = _stack(layers, top_eps, ground, bottom_eps)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    arg = np.ascontiguousarray(arg, dtype=np.float64)
+    out = np.zeros((arg.size, rho.size), dtype=np.complex128)
+    _check(lib().bem_layered_kernel_table(C.byref(st), float(freq), int(layer), int(kind), int(part),
+                                          rho.size, rho.ctypes.data_as(C.POINTER(C.c_double)),
+                                          arg.size, arg.ctypes.data_as(C.POINTER(C.c_double)),
+                                          out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
 
 
 def part_schedule(W, P, p_cutoff=20):

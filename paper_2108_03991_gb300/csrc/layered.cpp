@@ -204,6 +204,29 @@ static void sommerfeld_rows(const LayerStack& st, const std::vector<double>& rho
   }
 }
 
+// the stack of the C description, checked
+static int make_stack(const bem_stack* s, double freq_hz, const char* who, LayerStack* st) {
+  if (!s || s->nlayer < 1 || !s->thickness || !s->eps || !(freq_hz > 0) || !std::isfinite(freq_hz)) {
+    set_error("%s: bad arguments", who);
+    return BEM_EINVAL;
+  }
+  st->k0 = k0_of(freq_hz);
+  st->z.assign(1, 0.0);
+  for (int l = 0; l < s->nlayer; ++l) {
+    if (!(s->thickness[l] > 0) || !std::isfinite(s->eps[2 * l]) || !std::isfinite(s->eps[2 * l + 1])) {
+      set_error("%s: bad layer %d", who, l);
+      return BEM_EINVAL;
+    }
+    st->d.push_back(s->thickness[l]);
+    st->z.push_back(st->z.back() + s->thickness[l]);
+    st->eps.push_back(cd(s->eps[2 * l], s->eps[2 * l + 1]));
+  }
+  st->top = cd(s->top_eps[0], s->top_eps[1]);
+  st->bottom = cd(s->bottom_eps[0], s->bottom_eps[1]);
+  st->ground = s->ground != 0;
+  return BEM_OK;
+}
+
 }  // namespace bem
 
 using namespace bem;
@@ -211,26 +234,12 @@ using namespace bem;
 extern "C" int bem_layered_grid_tables(const bem_stack* s, double freq_hz, const double* origin,
                                        const double* h, const int32_t* n, int kind, double* T,
                                        double* H) {
-  if (!s || !origin || !h || !n || !T || !H || s->nlayer < 1 || !s->thickness || !s->eps ||
-      kind < 0 || kind > 2 || !(freq_hz > 0) || !std::isfinite(freq_hz)) {
+  if (!origin || !h || !n || !T || !H || kind < 0 || kind > 2) {
     set_error("bem_layered_grid_tables: bad arguments");
     return BEM_EINVAL;
   }
   LayerStack st;
-  st.k0 = k0_of(freq_hz);
-  st.z.push_back(0.0);
-  for (int l = 0; l < s->nlayer; ++l) {
-    if (!(s->thickness[l] > 0) || !std::isfinite(s->eps[2 * l]) || !std::isfinite(s->eps[2 * l + 1])) {
-      set_error("bem_layered_grid_tables: bad layer %d", l);
-      return BEM_EINVAL;
-    }
-    st.d.push_back(s->thickness[l]);
-    st.z.push_back(st.z.back() + s->thickness[l]);
-    st.eps.push_back(cd(s->eps[2 * l], s->eps[2 * l + 1]));
-  }
-  st.top = cd(s->top_eps[0], s->top_eps[1]);
-  st.bottom = cd(s->bottom_eps[0], s->bottom_eps[1]);
-  st.ground = s->ground != 0;
+  BEM_TRY(make_stack(s, freq_hz, "bem_layered_grid_tables", &st));
   const int nx = n[0], ny = n[1], nz = n[2];
   if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny > 65536 || !(h[0] > 0) || !(h[1] > 0) || !(h[2] > 0)) {
     set_error("bem_layered_grid_tables: bad grid (at most 65536 x-y offsets)");
@@ -267,5 +276,49 @@ extern "C" int bem_layered_grid_tables(const bem_stack* s, double freq_hz, const
       H[2 * o + 1] = hr[r][i].imag();
     }
   }
+  return BEM_OK;
+}
+
+extern "C" int bem_layered_kernel_table(const bem_stack* s, double freq_hz, int layer, int kind,
+                                        int part, int nrho, const double* rho, int narg,
+                                        const double* arg, double* out) {
+  if (!rho || !arg || !out || kind < 0 || kind > 2 || part < 0 || part > 1 || nrho < 1 ||
+      narg < 1 || (int64_t)nrho * narg > (1 << 26)) {
+    set_error("bem_layered_kernel_table: bad arguments");
+    return BEM_EINVAL;
+  }
+  LayerStack st;
+  BEM_TRY(make_stack(s, freq_hz, "bem_layered_kernel_table", &st));
+  if (layer < 0 || layer >= (int)st.d.size()) {
+    set_error("bem_layered_kernel_table: no layer %d", layer);
+    return BEM_EINVAL;
+  }
+  const double d = st.d[layer], zb = st.z[layer], zt = st.z[layer + 1];
+  double zeta = 1e300;
+  for (int j = 0; j < narg; ++j) {  // the smallest decay among the rows sets the path
+    const double a = arg[j];
+    const double zj = part == 0 ? 2 * d - std::fabs(a) : std::min(a - 2 * zb, 2 * zt - a);
+    const bool inside = part == 0 ? std::fabs(a) < d : zj > 0;
+    if (!inside || !std::isfinite(a)) {
+      set_error("bem_layered_kernel_table: argument %d outside the layer", j);
+      return BEM_EINVAL;
+    }
+    zeta = std::min(zeta, zj);
+  }
+  std::vector<double> r(rho, rho + nrho);
+  for (double v : r)
+    if (!(v >= 0) || !std::isfinite(v)) {
+      set_error("bem_layered_kernel_table: negative or non-finite rho");
+      return BEM_EINVAL;
+    }
+  std::vector<std::vector<cd>> rows;
+  sommerfeld_rows(st, r, zeta, narg,
+                  [&](int j, cd kr) { return st.spectral(layer, kr, kind, part == 1, arg[j]); }, &rows);
+  for (int j = 0; j < narg; ++j)
+    for (int i = 0; i < nrho; ++i) {
+      const size_t o = (size_t)j * nrho + i;
+      out[2 * o] = rows[j][i].real();
+      out[2 * o + 1] = rows[j][i].imag();
+    }
   return BEM_OK;
 }

@@ -77,3 +77,29 @@ def test_errors(lib):
     with pytest.raises(api.BemError) as ei:
         api.layered_grid_tables(layers, 1e10, (0, 0, 1.5), (0.3, 0.3, 0.3), (3, 3, 2), 3)
     assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("kind,name", KINDS)
+def test_kernel_tables_match_the_oracle(lib, kind, name):
+    """The reflected parts at arbitrary (rho, z - z') and (rho, z + z') points, the tables the
+    near-region entries of objects inside a layer interpolate: 1e-11 of the largest entry, in
+    the middle layer of the lossy three-layer stack."""
+    freq = 2e13
+    layers = [(1.0, 4.0 - 0.2j), (2.0, 2.2), (0.7, 11.9 - 3j)]
+    st = L.Stack(op.k0_of(freq), layers, top_eps=1.0)
+    rho = np.linspace(0.0, 2.7, 11)
+    for part, arg in ((0, np.linspace(-1.7, 1.7, 7)), (1, np.linspace(2.3, 5.7, 7))):
+        got = api.layered_kernel_table(layers, freq, 1, kind, part, rho, arg)
+        # the layer: z from 1 to 3 um (thickness 2); decay of each row's reflected terms
+        zeta = [min(a - 2 * 1.0, 2 * 3.0 - a) if part == 1 else 2 * 2.0 - abs(a) for a in arg]
+        ref = np.stack([st.sommerfeld(lambda kr, a=a: st.spectral(1, kr, "TH"[part], a, name),
+                                      rho, z) for a, z in zip(arg, zeta)])
+        assert np.max(np.abs(got - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_kernel_table_rejects_points_outside_the_layer(lib):
+    layers = [(1.0, 4.0), (2.0, 2.2)]
+    for part, arg in ((0, [2.5]), (1, [1.5])):
+        with pytest.raises(api.BemError) as ei:
+            api.layered_kernel_table(layers, 1e10, 1, 0, part, [0.0, 1.0], arg)
+        assert ei.value.code == -1
