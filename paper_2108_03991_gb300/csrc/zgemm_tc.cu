@@ -445,11 +445,8 @@ static int tc_launch(TcState* t, const CUtensorMap& mbh, const CUtensorMap& mbl,
                      float2* y, int64_t vstride, int R, cudaStream_t s) {
   constexpr uint32_t kSmem = TcSmem<NP, S>::kBytes;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
-  static bool attr = false;
-  if (!attr) {
-    BEM_CUDA(cudaFuncSetAttribute(k_zgemm_tc<NP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-    attr = true;
-  }
+  // per call: the attribute belongs to the current device (cheap next to the product)
+  BEM_CUDA(cudaFuncSetAttribute(k_zgemm_tc<NP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   BEM_CUDA(cudaMemsetAsync(t->err + 1, 0, sizeof(int), s));
   k_zgemm_tc<NP, S><<<t->ntiles, kTcThreads, kSmem, s>>>(mbh, mbl, ma, t->tiles, t->objs, y, vstride, R,
                                                         t->err);
