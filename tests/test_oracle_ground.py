@@ -6,7 +6,7 @@ Galerkin operators, the free-space limit, and the grid form of the image term.""
 import numpy as np
 import pytest
 
-from oracle import ground, operators as op
+from oracle import ground, operators as op, ports
 from oracle.rwg import from_mesh
 from paper_2108_03991_gb300 import synth
 
@@ -227,3 +227,42 @@ def test_ground_aim_restores_exact_near_entries(ground_aim):
         col = G.LPhi(e)
         rows = T[S == c]
         assert np.max(np.abs(col[rows] - LP[rows, c])) < 1e-12 * np.abs(LP).max()
+
+
+def test_port_current_over_ground_is_image_theory():
+    """The whole SLIM system above the ground plane (Eq. AEFIEoutJ with the ground-plane L^A and
+    L^Phi; the internal problems unchanged) against image theory at the level of a solve: a
+    copper bar 1 um above the plane, along x, driven by a delta-gap port at its middle (10 GHz),
+    carries the port current that the same bar carries in free space beside its mirror image
+    driven in antiphase (the image of an x-directed gap field is reversed), both systems solved
+    densely (1e-10; 2e-16 measured). The plane changes the current by 1.7%, an in-phase image
+    by 3.2%."""
+    freq = 10e9
+    k0 = op.k0_of(freq)
+    V, F = synth.box((0.0, 0.0, 2.0), (2.0, 1.0, 1.0), (4, 2, 2))
+    zg = 1.0
+    m1 = synth.merge([(V, F)], [synth.SIGMA_CU])
+    rw1 = from_mesh(m1)
+    Zs, Ys = op.internal_blocks(rw1, freq, m1.sigma)
+    LA, LP = ground.dense_ground_operators(rw1, k0, zg)
+    S1 = op.SlimSystem(rw1, freq, Zs, Ys, lambda v: LA @ v, lambda v: LP @ v)
+    e1, s1 = ports.ring_edges(rw1, 0, 1.0, axis=0)
+    x = np.linalg.solve(S1.dense(), np.concatenate([ports.port_rhs(rw1, e1, s1), np.zeros(rw1.nt)]))
+    Ig = ports.port_current(rw1, e1, s1, x[:rw1.ne])
+    m2 = synth.merge([(V, F), (ground.image(V, zg), F[:, ::-1])], [synth.SIGMA_CU] * 2)
+    rw2 = from_mesh(m2)
+    S2, _, _ = op.dense_system(rw2, freq, m2.sigma)
+    A2 = S2.dense()
+    ea, sa = ports.ring_edges(rw2, 0, 1.0, axis=0)
+    eb, sb = ports.ring_edges(rw2, 1, 1.0, axis=0)
+    cur = {}
+    for sgn in (-1.0, 1.0):
+        b = np.concatenate([ports.port_rhs(rw2, ea, sa) + sgn * ports.port_rhs(rw2, eb, sb),
+                            np.zeros(rw2.nt)])
+        x2 = np.linalg.solve(A2, b)
+        cur[sgn] = ports.port_current(rw2, ea, sa, x2[:rw2.ne])
+    assert abs(cur[-1.0] - Ig) < 1e-10 * abs(Ig)
+    assert abs(cur[1.0] - Ig) > 1e-2 * abs(Ig)
+    S0, _, _ = op.dense_system(rw1, freq, m1.sigma)
+    x0 = np.linalg.solve(S0.dense(), np.concatenate([ports.port_rhs(rw1, e1, s1), np.zeros(rw1.nt)]))
+    assert abs(ports.port_current(rw1, e1, s1, x0[:rw1.ne]) - Ig) > 1e-2 * abs(Ig)
