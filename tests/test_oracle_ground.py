@@ -2,7 +2,8 @@
 (oracle/ground.py), the first piece of the layered background of the paper's Table I: the
 boundary condition on the plane, the Lorenz gauge between the vector and scalar potentials of
 horizontal and vertical current elements (which fixes every image sign), reciprocity of the
-Galerkin operators, the free-space limit, and the grid form of the image term."""
+Galerkin operators, the free-space limit, the grid form of the image term, and image theory
+at the level of a port solve of the whole system."""
 import numpy as np
 import pytest
 
