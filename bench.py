@@ -546,8 +546,13 @@ def tensor_core_section(ctx, api, synth, torch, np, dev, hbm, reps=10):
         t_tc = timed(lambda: ctx.internal_tc(h, None, y_tc, nrhs=R, want_e=False))
         t_mv = timed(lambda: ctx.internal(h, None, y_mv, nrhs=R, prec=api.BEM_C32, want_e=False))
         d = float(torch.linalg.vector_norm(y_tc - y_mv) / torch.linalg.vector_norm(y_mv))
-        rows.append({"nrhs": R, "ms_tensor_core": t_tc, "ms_block_gemv": t_mv,
-                     "speedup": t_mv / t_tc, "rel_diff": d,
+        ctx.tc_variant(1)  # the raw right-hand sides split in shared memory (half the packed bytes)
+        t_raw = timed(lambda: ctx.internal_tc(h, None, y_tc, nrhs=R, want_e=False))
+        ctx.tc_variant(0)
+        d_raw = float(torch.linalg.vector_norm(y_tc - y_mv) / torch.linalg.vector_norm(y_mv))
+        rows.append({"nrhs": R, "ms_tensor_core": t_tc, "ms_tensor_core_raw_b": t_raw,
+                     "ms_block_gemv": t_mv,
+                     "speedup": t_mv / t_tc, "rel_diff": d, "rel_diff_raw_b": d_raw,
                      "tensor_core_GBps": ZY / (t_tc * 1e-3) / 1e9,
                      "tensor_core_frac_hbm": ZY / (t_tc * 1e-3) / 1e9 / hbm,
                      "tensor_core_TFLOPs": 8 * n2 * R / (t_tc * 1e-3) / 1e12})

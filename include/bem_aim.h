@@ -229,6 +229,12 @@ int internal_apply(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, in
  * BEM_ENOMEM, BEM_ECUDA (the driver has no tensor-map encoder, or a launch failed). */
 int aim_internal_tc(aim_ctx* ctx, const void* h, void* e, void* heq, int nrhs, void* stream);
 
+/* Form of aim_internal_tc's product: 0 (after aim_setup) packs B's TF32 hi and lo parts in
+ * device memory and loads both per stage; 1 packs the raw FP32 values (half the bytes) and
+ * splits them in shared memory as it does the matrix. The same arithmetic: the results agree
+ * to rounding. Takes effect at the next call. Errors: BEM_EINVAL. */
+int aim_tc_variant(aim_ctx* ctx, int variant);
+
 /* The grid step H of Eq. AIM_L alone: phi_c = sum_b G_grid(a - b) sigma_c(b) (linear
  * convolution) for ncomp (1..4) grids of n[0]*n[1]*n[2] points (x fastest) stored one after
  * another. sigma and phi may alias. */

@@ -27,7 +27,7 @@ SYMBOLS = ["aim_setup", "aim_destroy", "bem_last_error", "aim_info", "aim_matvec
            "bem_port_current", "bem_port_matrix", "bem_farfield", "aim_matvec_batch",
            "bem_solve_batch", "bem_precond_setup", "aim_internal_sparse", "bem_rcm_order",
            "aim_internal_tc", "bem_layered_grid_tables", "aim_rows_variant",
-           "bem_layered_kernel_table"]
+           "bem_layered_kernel_table", "aim_tc_variant"]
 
 
 class StackC(C.Structure):
@@ -97,6 +97,7 @@ def lib():
         L.internal_apply.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp]
         L.aim_internal_tc.argtypes = [vp, vp, vp, vp, C.c_int, vp]
         L.aim_rows_variant.argtypes = [vp, C.c_int]
+        L.aim_tc_variant.argtypes = [vp, C.c_int]
         L.bem_layered_kernel_table.argtypes = [C.POINTER(StackC), d, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.POINTER(d), C.c_int, C.POINTER(d),
                                                C.POINTER(d)]
@@ -483,6 +484,11 @@ class Context:
                                      _ptr(heq, dt) if heq is not None else None, int(nrhs),
                                      _stream()))
         return e, heq
+
+    def tc_variant(self, variant):
+        """Form of the tensor-core product (aim_tc_variant): 0 hi/lo packed, 1 raw B split in
+        shared memory."""
+        _check(lib().aim_tc_variant(self.h, int(variant)))
 
     def tensor_core_status(self):
         """aim_internal_tc's calls and wait status (reading it synchronises the device)."""

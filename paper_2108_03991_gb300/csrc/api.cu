@@ -487,6 +487,16 @@ int bem_precond_apply(aim_ctx* c, const void* r, void* u, int prec, void* stream
   return prec == BEM_C32 ? precond_apply<float>(c, r, u, s) : precond_apply<double>(c, r, u, s);
 }
 
+int aim_tc_variant(aim_ctx* c, int variant) {
+  BEM_TRY(check_ctx(c, "aim_tc_variant"));
+  if (variant != 0 && variant != 1) {
+    set_error("aim_tc_variant: variant must be 0 or 1");
+    return BEM_EINVAL;
+  }
+  c->tc_variant = variant;
+  return BEM_OK;
+}
+
 int aim_rows_variant(aim_ctx* c, int variant) {
   BEM_TRY(check_ctx(c, "aim_rows_variant"));
   if (variant < 0 || variant > 2) {

@@ -351,6 +351,9 @@ struct aim_ctx {
   bool zsp_ready = false, zsp_on = false;
   // many right-hand sides through Z and C on the tensor cores (zgemm_tc.cu), made on first use
   void* tc = nullptr;
+  // form of that product (aim_tc_variant): 0 B's hi and lo packed in device memory, 1 the raw B
+  // packed and split in shared memory
+  int tc_variant = 0;
   // form of the row kernels (aim_rows_variant): 0 near sums four-deep with a one-entry tail,
   // 1 four-deep predicated, 2 predicated and two interpolation rows per warp (k_rows_e2)
   int rows_variant = 0;

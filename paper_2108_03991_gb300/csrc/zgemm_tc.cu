@@ -143,9 +143,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const in
   return false;
 }
 
-// B from x, hi and lo parts: rows 2r and 2r + 1 for right-hand side r < R (zero rows up to NP),
-// columns 2u and 2u + 1 for padded slot u (slot[u] = its unknown, -1 in a block's padding).
-// Grid: x over the slots, y over the NP / 2 row pairs.
+// B from x, hi and lo parts (or, with bl null, the raw FP32 values into bh): rows 2r and 2r + 1
+// for right-hand side r < R (zero rows up to NP), columns 2u and 2u + 1 for padded slot u
+// (slot[u] = its unknown, -1 in a block's padding). Grid: x over the slots, y over the NP / 2
+// row pairs.
 __global__ void k_tc_pack(const float2* __restrict__ x, int64_t vstride, int R,
                           const int32_t* __restrict__ slot, int64_t nslot, float* __restrict__ bh,
                           float* __restrict__ bl) {
@@ -159,6 +160,11 @@ __global__ void k_tc_pack(const float2* __restrict__ x, int64_t vstride, int R,
   const float2 re = make_float2(v.x, -v.y), im = make_float2(v.y, v.x);
   const float2 reh = make_float2(tf32_hi(re.x), tf32_hi(re.y)), imh = make_float2(tf32_hi(im.x), tf32_hi(im.y));
   const int64_t o0 = (2 * r) * ktot + 2 * u, o1 = o0 + ktot;
+  if (!bl) {  // the raw values: the product splits them in shared memory
+    *reinterpret_cast<float2*>(bh + o0) = re;
+    *reinterpret_cast<float2*>(bh + o1) = im;
+    return;
+  }
   *reinterpret_cast<float2*>(bh + o0) = reh;
   *reinterpret_cast<float2*>(bh + o1) = imh;
   *reinterpret_cast<float2*>(bl + o0) = make_float2(re.x - reh.x, re.y - reh.y);
@@ -174,14 +180,16 @@ template <int NP, int S> struct TcSmem {
   static constexpr uint32_t kBytes = kBars + 8 * (2 * S + 1) + 8 + 1024;  // + alignment slack
 };
 
-template <int NP, int S>
+// BS = 0: B's hi and lo parts arrive packed (two TMA loads a stage); BS = 1: the raw B arrives
+// (one load) and is split in shared memory like A
+template <int NP, int S, int BS = 0>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_zgemm_tc(const __grid_constant__ CUtensorMap mbh, const __grid_constant__ CUtensorMap mbl,
                const CUtensorMap* __restrict__ ma, const TcTile* __restrict__ tiles,
                const TcObj* __restrict__ objs, float2* __restrict__ y, int64_t vstride, int R,
                int* err) {
   typedef TcSmem<NP, S> L;
-  constexpr uint32_t kTx = kTcAtile + 2 * L::kBtile;  // bytes landing per stage
+  constexpr uint32_t kTx = kTcAtile + (BS ? 1 : 2) * L::kBtile;  // bytes landing per stage
   constexpr uint32_t kIdesc = tf32_idesc(kTcM, NP);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mbar_arrive_tx(&full[s], kTx);
     tma_load_2d(st, mA, kc * kTcK, t.row0, &full[s]);
     tma_load_2d(st + 2 * kTcAtile, &mbh, kx, 0, &full[s]);
-    tma_load_2d(st + 2 * kTcAtile + L::kBtile, &mbl, kx, 0, &full[s]);
+    if constexpr (BS == 0) tma_load_2d(st + 2 * kTcAtile + L::kBtile, &mbl, kx, 0, &full[s]);
     issued = kc + 1;
   };
   if (tid == 0) {
@@ -247,6 +255,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
         a[i] = h;
         al[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+      }
+      if constexpr (BS == 1) {  // the same split of the raw B tile
+        float4* b = reinterpret_cast<float4*>(base + s * L::kStage + 2 * kTcAtile);
+        float4* bl = reinterpret_cast<float4*>(base + s * L::kStage + 2 * kTcAtile + L::kBtile);
+#pragma unroll 4
+        for (int i = tid; i < (int)(L::kBtile / 16); i += kTcThreads) {
+          const float4 v = b[i];
+          const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+          b[i] = h;
+          bl[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -440,16 +459,16 @@ static int tc_prepare(aim_ctx* c, TcState** out) {
   return BEM_OK;
 }
 
-template <int NP, int S>
+template <int NP, int S, int BS>
 static int tc_launch(TcState* t, const CUtensorMap& mbh, const CUtensorMap& mbl, const CUtensorMap* ma,
                      float2* y, int64_t vstride, int R, cudaStream_t s) {
   constexpr uint32_t kSmem = TcSmem<NP, S>::kBytes;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
   // per call: the attribute belongs to the current device (cheap next to the product)
-  BEM_CUDA(cudaFuncSetAttribute(k_zgemm_tc<NP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+  BEM_CUDA(cudaFuncSetAttribute(k_zgemm_tc<NP, S, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
   BEM_CUDA(cudaMemsetAsync(t->err + 1, 0, sizeof(int), s));
-  k_zgemm_tc<NP, S><<<t->ntiles, kTcThreads, kSmem, s>>>(mbh, mbl, ma, t->tiles, t->objs, y, vstride, R,
-                                                        t->err);
+  k_zgemm_tc<NP, S, BS><<<t->ntiles, kTcThreads, kSmem, s>>>(mbh, mbl, ma, t->tiles, t->objs, y, vstride,
+                                                            R, t->err);
   BEM_CUDA(cudaGetLastError());
   return BEM_OK;
 }
@@ -477,23 +496,29 @@ int internal_tc(aim_ctx* c, const float2* h, float2* e, float2* heq, int nrhs, c
       }
       t->np_cap = NP;
     }
+    // form 1 packs the raw values only (B split in shared memory); the second map is then unused
+    const bool raw = c->tc_variant == 1;
     CUtensorMap mbh, mbl;
     BEM_TRY(tc_map(enc, &mbh, t->bh, 2 * t->nslot, NP, 2 * t->nslot * (int64_t)sizeof(float), NP));
     BEM_TRY(tc_map(enc, &mbl, t->bl, 2 * t->nslot, NP, 2 * t->nslot * (int64_t)sizeof(float), NP));
     const dim3 pg((unsigned)((t->nslot + 255) / 256), NP / 2);
-    k_tc_pack<<<pg, 256, 0, s>>>(h + r0 * ne, ne, R, t->slot, t->nslot, t->bh, t->bl);
+    k_tc_pack<<<pg, 256, 0, s>>>(h + r0 * ne, ne, R, t->slot, t->nslot, t->bh, raw ? nullptr : t->bl);
     BEM_CUDA(cudaGetLastError());
     for (int w = 0; w < 2; ++w) {
       float2* y = w == 0 ? e : heq;
       if (!y) continue;
       const CUtensorMap* ma = w == 0 ? t->mz : t->mc;
       y += r0 * ne;
+#define BEM_TC(NPV, SV)                                                               \
+  BEM_TRY(raw ? (tc_launch<NPV, SV, 1>(t, mbh, mbl, ma, y, ne, R, s))                 \
+              : (tc_launch<NPV, SV, 0>(t, mbh, mbl, ma, y, ne, R, s)))
       switch (NP) {
-        case 32: BEM_TRY((tc_launch<32, 5>(t, mbh, mbl, ma, y, ne, R, s))); break;
-        case 64: BEM_TRY((tc_launch<64, 4>(t, mbh, mbl, ma, y, ne, R, s))); break;
-        case 128: BEM_TRY((tc_launch<128, 3>(t, mbh, mbl, ma, y, ne, R, s))); break;
-        default: BEM_TRY((tc_launch<256, 2>(t, mbh, mbl, ma, y, ne, R, s))); break;
+        case 32: BEM_TC(32, 5); break;
+        case 64: BEM_TC(64, 4); break;
+        case 128: BEM_TC(128, 3); break;
+        default: BEM_TC(256, 2); break;
       }
+#undef BEM_TC
     }
   }
   ++t->calls;

@@ -91,3 +91,23 @@ def test_tensor_core_matches_block_gemv(bars):
     _, ht = ctx.internal_tc(h, nrhs=nrhs, want_e=False)
     eg, hg, et, ht = (v.cpu().numpy() for v in (eg, hg, et, ht))
     assert rel(et, eg) < 1e-5 and rel(ht, hg) < 1e-5
+
+
+def test_tensor_core_forms_agree(short_bars):
+    """aim_tc_variant 1 (the raw right-hand sides packed and split in shared memory) gives the
+    same products as form 0 (hi and lo packed in device memory): the same arithmetic, the same
+    bits; 5 and 33 right-hand sides."""
+    ctx = short_bars["ctx"]
+    try:
+        for nrhs in (5, 33):
+            h = torch.from_numpy(np.concatenate([synth.rand_cvec(ctx.ne, 500 + r) for r in range(nrhs)])
+                                 .astype(np.complex64)).cuda()
+            out = []
+            for v in (0, 1):
+                ctx.tc_variant(v)
+                e, heq = ctx.internal_tc(h, nrhs=nrhs)
+                out.append((e.cpu().numpy(), heq.cpu().numpy()))
+            assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        assert ctx.tensor_core_status()["wait_timed_out"] is False
+    finally:
+        ctx.tc_variant(0)
